@@ -1,0 +1,590 @@
+/*
+ * CPU oracle for flow-based hypergraph refinement (Gottesbueren, Heuer,
+ * Sanders, "Parallel Flow-Based Hypergraph Partitioning").
+ *
+ * TEST INFRASTRUCTURE ONLY.  Plain, slow and written to be checked by eye
+ * against the paper.  Only the test suite, the smoke check and the CPU
+ * baseline leg of the benchmark may load this code; the CUDA library never
+ * calls it and shares no code with it.
+ *
+ * Every routine works on the EXPLICIT Lawler expansion of the flow
+ * hypergraph (Section 2, "Flows on Hypergraphs"): hypernodes, an in-node and
+ * an out-node per net, infinite pin arcs (u, e_in) and (e_out, u), and a
+ * bridge (e_in, e_out) of capacity w(e).  Lawler node numbering:
+ *   hypernode h            -> h                  (0 = s, 1 = t, 2.. = region)
+ *   in-node of net e       -> n_nodes + e
+ *   out-node of net e      -> n_nodes + m_nets + e
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <limits.h>
+
+#define OR_OK 0
+#define OR_ERR_INVALID (-1)
+#define OR_ERR_OOM (-2)
+#define OR_ITER_LIMIT (-4)
+#define OR_NO_BALANCED_CUT (-5)
+#define OR_ABORTED_WORSE (-6)
+#define OR_ERR_BUFFER (-7)
+
+#define DIST_FAR ((1 << 20) - 1)
+
+/* ------------------------------------------------------------------------ */
+/* Flow network construction: Section 6, "Construction Algorithms", the first
+ * (net scan) algorithm.  For every net with a pin in the region B, region
+ * pins are copied (in the net's pin order), and a pin outside B adds the
+ * source s (its block is the S side, side 0) or the sink t (side 1), each at
+ * most once per net.  Pins whose side is neither 0 nor 1 belong to neither
+ * block of the pair and are dropped.  Nets with fewer than two pins left, or
+ * holding both s and t, are discarded (Section 6, last paragraph of
+ * "Construction Algorithms").  Kept nets keep ascending net id order.
+ *
+ * Returns the pin count of the flow hypergraph, or a negative error.
+ * Output capacities: m nets, net_off[m] + 2m pins, n_region + 2 nodes.
+ */
+int64_t or_build_network(int32_t n, int32_t m, const uint32_t *net_off, const int32_t *pins,
+                         const int32_t *net_w, const int32_t *node_w, const int32_t *side,
+                         const int32_t *region, int32_t n_region,
+                         int32_t *out_m, uint32_t *nnet_off, int32_t *npins, int32_t *nnet_w,
+                         int32_t *nnet_gid, int64_t *nnode_w) {
+    int32_t *loc = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    if (!loc) return OR_ERR_OOM;
+    for (int32_t v = 0; v < n; v++) loc[v] = -1;
+    for (int32_t i = 0; i < n_region; i++) {
+        int32_t v = region[i];
+        if (v < 0 || v >= n || loc[v] >= 0 || (side[v] != 0 && side[v] != 1)) {
+            free(loc);
+            return OR_ERR_INVALID;
+        }
+        loc[v] = 2 + i;
+    }
+    nnode_w[0] = 0;
+    nnode_w[1] = 0;
+    for (int32_t v = 0; v < n; v++) {
+        int64_t c = node_w ? node_w[v] : 1;
+        if (loc[v] >= 0) nnode_w[loc[v]] = c;
+        else if (side[v] == 0) nnode_w[0] += c;
+        else if (side[v] == 1) nnode_w[1] += c;
+    }
+    int64_t p = 0;
+    int32_t mm = 0;
+    for (int32_t e = 0; e < m; e++) {
+        int64_t start = p;
+        int has_s = 0, has_t = 0;
+        for (uint32_t j = net_off[e]; j < net_off[e + 1]; j++) {
+            int32_t v = pins[j];
+            if (loc[v] >= 0) npins[p++] = loc[v];
+            else if (side[v] == 0) has_s = 1;
+            else if (side[v] == 1) has_t = 1;
+        }
+        int64_t cnt = (p - start) + has_s + has_t;
+        if (cnt < 2 || (has_s && has_t)) { p = start; continue; }
+        if (has_s) npins[p++] = 0;
+        if (has_t) npins[p++] = 1;
+        nnet_off[mm] = (uint32_t)start;
+        nnet_w[mm] = net_w[e];
+        nnet_gid[mm] = e;
+        mm++;
+    }
+    nnet_off[mm] = (uint32_t)p;
+    *out_m = mm;
+    free(loc);
+    return p;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Distance from the original cut (Section 6, "Region Growing", last
+ * paragraph, and Section 7, "Piercing").  The paper does not define it; the
+ * reading used here: hop distance inside the region B.  Region pins of a net
+ * of H that has pins on both sides (side 0 and side 1) get distance 1; region
+ * pins of a net containing a region vertex at distance d that are still
+ * unlabelled get d + 1.  Unreached region vertices get DIST_FAR; values are
+ * clamped to DIST_FAR.  dist is indexed by region position.
+ */
+int32_t or_dist_from_cut(int32_t n, int32_t m, const uint32_t *net_off, const int32_t *pins,
+                         const int32_t *side, const int32_t *region, int32_t n_region,
+                         int32_t *dist) {
+    int32_t *loc = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    int32_t *deg = (int32_t *)calloc((size_t)n + 1, sizeof(int32_t));
+    if (!loc || !deg) { free(loc); free(deg); return OR_ERR_OOM; }
+    for (int32_t v = 0; v < n; v++) loc[v] = -1;
+    for (int32_t i = 0; i < n_region; i++) loc[region[i]] = i;
+    /* vertex -> nets incidence of H, restricted to region vertices */
+    for (int32_t e = 0; e < m; e++)
+        for (uint32_t j = net_off[e]; j < net_off[e + 1]; j++)
+            if (loc[pins[j]] >= 0) deg[pins[j] + 1]++;
+    for (int32_t v = 0; v < n; v++) deg[v + 1] += deg[v];
+    int64_t tot = deg[n];
+    int32_t *inc = (int32_t *)malloc(sizeof(int32_t) * (size_t)(tot > 0 ? tot : 1));
+    int32_t *fill = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    int32_t *queue = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n_region > 0 ? n_region : 1));
+    if (!inc || !fill || !queue) { free(loc); free(deg); free(inc); free(fill); free(queue); return OR_ERR_OOM; }
+    memcpy(fill, deg, sizeof(int32_t) * (size_t)n);
+    for (int32_t e = 0; e < m; e++)
+        for (uint32_t j = net_off[e]; j < net_off[e + 1]; j++)
+            if (loc[pins[j]] >= 0) inc[fill[pins[j]]++] = e;
+    for (int32_t i = 0; i < n_region; i++) dist[i] = -1;
+    int32_t qh = 0, qt = 0;
+    for (int32_t e = 0; e < m; e++) {
+        int s0 = 0, s1 = 0;
+        for (uint32_t j = net_off[e]; j < net_off[e + 1]; j++) {
+            if (side[pins[j]] == 0) s0 = 1;
+            if (side[pins[j]] == 1) s1 = 1;
+        }
+        if (!(s0 && s1)) continue;
+        for (uint32_t j = net_off[e]; j < net_off[e + 1]; j++) {
+            int32_t i = loc[pins[j]];
+            if (i >= 0 && dist[i] < 0) { dist[i] = 1; queue[qt++] = pins[j]; }
+        }
+    }
+    while (qh < qt) {
+        int32_t u = queue[qh++];
+        int32_t du = dist[loc[u]];
+        for (int32_t k = deg[u]; k < deg[u + 1]; k++) {
+            int32_t e = inc[k];
+            for (uint32_t j = net_off[e]; j < net_off[e + 1]; j++) {
+                int32_t i = loc[pins[j]];
+                if (i >= 0 && dist[i] < 0) {
+                    dist[i] = du + 1 < DIST_FAR ? du + 1 : DIST_FAR;
+                    queue[qt++] = pins[j];
+                }
+            }
+        }
+    }
+    for (int32_t i = 0; i < n_region; i++) if (dist[i] < 0) dist[i] = DIST_FAR;
+    free(loc); free(deg); free(inc); free(fill); free(queue);
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Explicit Lawler expansion (Section 2, "Flows on Hypergraphs"). */
+typedef struct {
+    int32_t n_nodes, m_nets, N;   /* hypernodes, nets, Lawler nodes */
+    int64_t A;                    /* arcs, each edge stored with its reverse */
+    int64_t *adj_off;             /* N + 1 */
+    int32_t *head, *tail;
+    int64_t *cap, *flow, *rev;
+    int64_t inf;                  /* "infinite" capacity: 1 + sum of all w(e) */
+    int64_t *node_w;              /* hypernode weights c(h) */
+} Lawler;
+
+void or_lawler_free(Lawler *G) {
+    if (!G) return;
+    free(G->adj_off); free(G->head); free(G->tail); free(G->cap); free(G->flow); free(G->rev);
+    free(G->node_w);
+    free(G);
+}
+
+Lawler *or_lawler_create(int32_t n_nodes, int32_t m_nets, const uint32_t *net_off,
+                         const int32_t *npins, const int32_t *net_w, const int64_t *node_w) {
+    Lawler *G = (Lawler *)calloc(1, sizeof(Lawler));
+    if (!G) return NULL;
+    G->n_nodes = n_nodes;
+    G->m_nets = m_nets;
+    G->N = n_nodes + 2 * m_nets;
+    int64_t P = net_off[m_nets];
+    int64_t E = 2 * P + m_nets;     /* edges: two per pin plus one bridge per net */
+    G->A = 2 * E;
+    G->adj_off = (int64_t *)calloc((size_t)G->N + 1, sizeof(int64_t));
+    G->head = (int32_t *)malloc(sizeof(int32_t) * (size_t)(G->A + 1));
+    G->tail = (int32_t *)malloc(sizeof(int32_t) * (size_t)(G->A + 1));
+    G->cap = (int64_t *)malloc(sizeof(int64_t) * (size_t)(G->A + 1));
+    G->flow = (int64_t *)calloc((size_t)G->A + 1, sizeof(int64_t));
+    G->rev = (int64_t *)malloc(sizeof(int64_t) * (size_t)(G->A + 1));
+    G->node_w = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n_nodes + 1));
+    if (!G->adj_off || !G->head || !G->tail || !G->cap || !G->flow || !G->rev || !G->node_w) {
+        or_lawler_free(G);
+        return NULL;
+    }
+    memcpy(G->node_w, node_w, sizeof(int64_t) * (size_t)n_nodes);
+    int64_t inf = 1;
+    for (int32_t e = 0; e < m_nets; e++) inf += net_w[e];
+    G->inf = inf;
+    /* edge list */
+    int32_t *eu = (int32_t *)malloc(sizeof(int32_t) * (size_t)(E + 1));
+    int32_t *ev = (int32_t *)malloc(sizeof(int32_t) * (size_t)(E + 1));
+    int64_t *ec = (int64_t *)malloc(sizeof(int64_t) * (size_t)(E + 1));
+    if (!eu || !ev || !ec) { free(eu); free(ev); free(ec); or_lawler_free(G); return NULL; }
+    int64_t k = 0;
+    for (int32_t e = 0; e < m_nets; e++) {
+        int32_t ein = n_nodes + e, eout = n_nodes + m_nets + e;
+        for (uint32_t j = net_off[e]; j < net_off[e + 1]; j++) {
+            int32_t u = npins[j];
+            eu[k] = u; ev[k] = ein; ec[k] = inf; k++;      /* (u, e_in), infinite */
+            eu[k] = eout; ev[k] = u; ec[k] = inf; k++;     /* (e_out, u), infinite */
+        }
+        eu[k] = ein; ev[k] = eout; ec[k] = net_w[e]; k++;  /* bridge, capacity w(e) */
+    }
+    for (int64_t i = 0; i < E; i++) { G->adj_off[eu[i] + 1]++; G->adj_off[ev[i] + 1]++; }
+    for (int32_t x = 0; x < G->N; x++) G->adj_off[x + 1] += G->adj_off[x];
+    int64_t *pos = (int64_t *)malloc(sizeof(int64_t) * (size_t)(G->N + 1));
+    if (!pos) { free(eu); free(ev); free(ec); or_lawler_free(G); return NULL; }
+    memcpy(pos, G->adj_off, sizeof(int64_t) * (size_t)G->N);
+    for (int64_t i = 0; i < E; i++) {
+        int64_t a = pos[eu[i]]++, b = pos[ev[i]]++;
+        G->head[a] = ev[i]; G->tail[a] = eu[i]; G->cap[a] = ec[i]; G->rev[a] = b;
+        G->head[b] = eu[i]; G->tail[b] = ev[i]; G->cap[b] = 0; G->rev[b] = a;
+    }
+    free(pos); free(eu); free(ev); free(ec);
+    return G;
+}
+
+int32_t or_lawler_nodes(const Lawler *G) { return G->N; }
+int64_t or_lawler_arcs(const Lawler *G) { return G->A; }
+
+static int64_t residual(const Lawler *G, int64_t a) { return G->cap[a] - G->flow[a]; }
+
+static void push_arc(Lawler *G, int64_t a, int64_t d) {
+    G->flow[a] += d;
+    G->flow[G->rev[a]] -= d;
+}
+
+/* Dinic's algorithm from the source set S to the sink set T, starting from
+ * the flow already on the arcs (an S-T flow stays feasible when S or T grow,
+ * so FlowCutter's "augment flow to maximality" continues from it).
+ * Returns the amount of flow added. */
+static int64_t dinic(Lawler *G, const uint8_t *src, const uint8_t *snk) {
+    int32_t N = G->N;
+    int32_t *level = (int32_t *)malloc(sizeof(int32_t) * (size_t)N);
+    int32_t *queue = (int32_t *)malloc(sizeof(int32_t) * (size_t)N);
+    int64_t *cur = (int64_t *)malloc(sizeof(int64_t) * (size_t)N);
+    int64_t *stack = (int64_t *)malloc(sizeof(int64_t) * (size_t)(N + 1));
+    if (!level || !queue || !cur || !stack) { free(level); free(queue); free(cur); free(stack); return -1; }
+    int64_t total = 0;
+    for (;;) {
+        /* level graph: BFS from all sources over residual arcs; sinks absorb */
+        for (int32_t x = 0; x < N; x++) level[x] = -1;
+        int32_t qh = 0, qt = 0, reached = 0, dsink = INT32_MAX;
+        for (int32_t x = 0; x < N; x++) if (src[x]) { level[x] = 0; queue[qt++] = x; }
+        while (qh < qt) {
+            int32_t u = queue[qh++];
+            if (snk[u]) { reached = 1; if (level[u] < dsink) dsink = level[u]; continue; }
+            if (level[u] >= dsink) continue;       /* only levels below the nearest sink matter */
+            for (int64_t a = G->adj_off[u]; a < G->adj_off[u + 1]; a++) {
+                int32_t v = G->head[a];
+                if (level[v] < 0 && residual(G, a) > 0) { level[v] = level[u] + 1; queue[qt++] = v; }
+            }
+        }
+        if (!reached) break;
+        /* layered network: keep only nodes that lie on a shortest augmenting
+           path, i.e. sinks and nodes with a layered residual arc into a kept
+           node (scanned in reverse BFS order); all others leave the level graph */
+        for (int32_t i = qt - 1; i >= 0; i--) {
+            int32_t u = queue[i];
+            if (snk[u]) continue;
+            int keep = 0;
+            if (level[u] < dsink)
+                for (int64_t a = G->adj_off[u]; a < G->adj_off[u + 1] && !keep; a++) {
+                    int32_t v = G->head[a];
+                    if (level[v] == level[u] + 1 && residual(G, a) > 0) keep = 1;
+                }
+            if (!keep) level[u] = -2;
+        }
+        /* blocking flow by depth-first search with current-arc pointers */
+        for (int32_t x = 0; x < N; x++) cur[x] = G->adj_off[x];
+        for (int32_t s = 0; s < N; s++) {
+            if (!src[s]) continue;
+            int32_t depth = 0, u = s;
+            for (;;) {
+                if (snk[u]) {
+                    int64_t b = INT64_MAX;
+                    for (int32_t i = 0; i < depth; i++) if (residual(G, stack[i]) < b) b = residual(G, stack[i]);
+                    for (int32_t i = 0; i < depth; i++) push_arc(G, stack[i], b);
+                    total += b;
+                    int32_t k = 0;
+                    while (residual(G, stack[k]) > 0) k++;   /* first saturated arc */
+                    depth = k;
+                    u = G->tail[stack[k]];
+                    continue;
+                }
+                int found = 0;
+                for (; cur[u] < G->adj_off[u + 1]; cur[u]++) {
+                    int64_t a = cur[u];
+                    int32_t v = G->head[a];
+                    if (level[v] == level[u] + 1 && residual(G, a) > 0) {
+                        stack[depth++] = a;
+                        u = v;
+                        found = 1;
+                        break;
+                    }
+                }
+                if (found) continue;
+                level[u] = -2;                 /* dead end: no path to a sink */
+                if (depth == 0) break;
+                u = G->tail[stack[--depth]];
+            }
+        }
+    }
+    free(level); free(queue); free(cur); free(stack);
+    return total;
+}
+
+/* Edmonds-Karp: repeatedly augment along a shortest residual S-T path.
+ * A second, independent textbook routine used to cross-check Dinic. */
+static int64_t edmonds_karp(Lawler *G, const uint8_t *src, const uint8_t *snk) {
+    int32_t N = G->N;
+    int64_t *parent = (int64_t *)malloc(sizeof(int64_t) * (size_t)N);
+    int32_t *queue = (int32_t *)malloc(sizeof(int32_t) * (size_t)N);
+    if (!parent || !queue) { free(parent); free(queue); return -1; }
+    int64_t total = 0;
+    for (;;) {
+        for (int32_t x = 0; x < N; x++) parent[x] = -2;
+        int32_t qh = 0, qt = 0, found = -1;
+        for (int32_t x = 0; x < N; x++) if (src[x]) { parent[x] = -1; queue[qt++] = x; }
+        while (qh < qt && found < 0) {
+            int32_t u = queue[qh++];
+            for (int64_t a = G->adj_off[u]; a < G->adj_off[u + 1]; a++) {
+                int32_t v = G->head[a];
+                if (parent[v] == -2 && residual(G, a) > 0) {
+                    parent[v] = a;
+                    if (snk[v]) { found = v; break; }
+                    queue[qt++] = v;
+                }
+            }
+        }
+        if (found < 0) break;
+        int64_t b = INT64_MAX;
+        for (int32_t v = found; parent[v] >= 0; v = G->tail[parent[v]])
+            if (residual(G, parent[v]) < b) b = residual(G, parent[v]);
+        for (int32_t v = found; parent[v] >= 0; v = G->tail[parent[v]]) push_arc(G, parent[v], b);
+        total += b;
+    }
+    free(parent); free(queue);
+    return total;
+}
+
+/* algo 0 = Dinic, 1 = Edmonds-Karp.  Returns the flow added, < 0 on error. */
+int64_t or_augment(Lawler *G, const uint8_t *src, const uint8_t *snk, int32_t algo) {
+    return algo == 1 ? edmonds_karp(G, src, snk) : dinic(G, src, snk);
+}
+
+void or_reset_flow(Lawler *G) { memset(G->flow, 0, sizeof(int64_t) * (size_t)G->A); }
+
+/* Value of the current flow: net flow leaving the source set (Section 2). */
+int64_t or_flow_value(const Lawler *G, const uint8_t *src) {
+    int64_t v = 0;
+    for (int32_t u = 0; u < G->N; u++) {
+        if (!src[u]) continue;
+        for (int64_t a = G->adj_off[u]; a < G->adj_off[u + 1]; a++)
+            if (!src[G->head[a]]) v += G->flow[a];
+    }
+    return v;
+}
+
+/* Source-side cut: nodes reachable from S by residual arcs (Section 2). */
+void or_reach_from(const Lawler *G, const uint8_t *seed, uint8_t *mark) {
+    int32_t N = G->N;
+    int32_t *queue = (int32_t *)malloc(sizeof(int32_t) * (size_t)N);
+    int32_t qh = 0, qt = 0;
+    for (int32_t x = 0; x < N; x++) { mark[x] = seed[x] ? 1 : 0; if (seed[x]) queue[qt++] = x; }
+    while (qh < qt) {
+        int32_t u = queue[qh++];
+        for (int64_t a = G->adj_off[u]; a < G->adj_off[u + 1]; a++) {
+            int32_t v = G->head[a];
+            if (!mark[v] && residual(G, a) > 0) { mark[v] = 1; queue[qt++] = v; }
+        }
+    }
+    free(queue);
+}
+
+/* Sink-side cut: nodes with a residual path into T (reverse BFS, Section 2). */
+void or_reach_to(const Lawler *G, const uint8_t *seed, uint8_t *mark) {
+    int32_t N = G->N;
+    int32_t *queue = (int32_t *)malloc(sizeof(int32_t) * (size_t)N);
+    int32_t qh = 0, qt = 0;
+    for (int32_t x = 0; x < N; x++) { mark[x] = seed[x] ? 1 : 0; if (seed[x]) queue[qt++] = x; }
+    while (qh < qt) {
+        int32_t v = queue[qh++];
+        for (int64_t a = G->adj_off[v]; a < G->adj_off[v + 1]; a++) {
+            int32_t u = G->head[a];          /* arc rev[a] runs u -> v */
+            if (!mark[u] && residual(G, G->rev[a]) > 0) { mark[u] = 1; queue[qt++] = u; }
+        }
+    }
+    free(queue);
+}
+
+/* Per-arc export for feasibility checks: tail, head, capacity, flow. */
+void or_export_arcs(const Lawler *G, int32_t *tail, int32_t *head, int64_t *cap, int64_t *flow) {
+    for (int64_t a = 0; a < G->A; a++) {
+        tail[a] = G->tail[a]; head[a] = G->head[a]; cap[a] = G->cap[a]; flow[a] = G->flow[a];
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Brute force over all bipartitions of the region (<= 24 region vertices):
+ * source side = {s} plus the region vertices whose bit is set; cut weight =
+ * sum of w(e) over nets with pins on both sides (the hypergraph cut, which
+ * equals the minimum Lawler cut, Section 2).  Reports the minimum, and the
+ * intersection and union of all minimising source sets.  With max_w >= 0,
+ * also the minimum over bipartitions whose two sides both weigh <= max_w
+ * (-1 when none exists). */
+int32_t or_bruteforce(int32_t n_nodes, int32_t m_nets, const uint32_t *net_off, const int32_t *npins,
+                      const int32_t *net_w, const int64_t *node_w, int64_t max_w,
+                      int64_t *min_cut, uint32_t *and_mask, uint32_t *or_mask, int64_t *n_min,
+                      int64_t *min_balanced) {
+    int32_t r = n_nodes - 2;
+    if (r < 0 || r > 24) return OR_ERR_INVALID;
+    int64_t best = INT64_MAX, bestbal = -1, cnt = 0, W = 0;
+    uint32_t am = 0xFFFFFFFFu, om = 0;
+    for (int32_t h = 0; h < n_nodes; h++) W += node_w[h];
+    for (uint32_t mask = 0; mask < (1u << r); mask++) {
+        int64_t cut = 0;
+        for (int32_t e = 0; e < m_nets; e++) {
+            int a = 0, b = 0;
+            for (uint32_t j = net_off[e]; j < net_off[e + 1]; j++) {
+                int32_t h = npins[j];
+                int in_s = (h == 0) || (h >= 2 && ((mask >> (h - 2)) & 1u));
+                if (in_s) a = 1; else b = 1;
+            }
+            if (a && b) cut += net_w[e];
+        }
+        if (cut < best) { best = cut; am = mask; om = mask; cnt = 1; }
+        else if (cut == best) { am &= mask; om |= mask; cnt++; }
+        if (max_w >= 0) {
+            int64_t ws = node_w[0];
+            for (int32_t i = 0; i < r; i++) if ((mask >> i) & 1u) ws += node_w[2 + i];
+            if (ws <= max_w && W - ws <= max_w && (bestbal < 0 || cut < bestbal)) bestbal = cut;
+        }
+    }
+    *min_cut = best; *and_mask = am; *or_mask = om; *n_min = cnt;
+    if (min_balanced) *min_balanced = bestbal;
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* FlowCutter core, Algorithm 2 of the paper (Section 7), with the piercing
+ * heuristics of Section 7, "Piercing".
+ *
+ * Readings where the paper is silent (each listed in the design notes):
+ *  - S_r / T_r are residual reachability on the uncapped Lawler network of
+ *    an actual maximum flow.
+ *  - A bipartition (X, V \ X) is balanced iff c(X) <= L and c(V \ X) <= L.
+ *    If both derived bipartitions are balanced, the one with the smaller
+ *    heavier side is returned; ties go to the source side.
+ *  - The source side grows iff c(S_r) <= c(T_r).
+ *  - Candidates when growing S: hypernodes v not in S_r and not in T that are
+ *    pins of a net whose in-node is in S_r, with c(S_r) + c(v) <= L.  Keys,
+ *    compared in order, larger wins: (1) v not in T_r (no augmenting path),
+ *    (2) signed distance from the original cut: +dist if v's original block
+ *    is the growing side's, -dist otherwise, (3) the smaller
+ *    fmix32(gid(v) ^ seed), MurmurHash3's 32-bit finaliser, a bijection, so
+ *    keys never tie.  Growing T is symmetric (nets whose out-node is in T_r,
+ *    no path from S_r, original block 1 counts as +).
+ *  - No candidate: OR_NO_BALANCED_CUT.  flow > flow_bound (when >= 0):
+ *    OR_ABORTED_WORSE.
+ *
+ * Inputs per hypernode h: node_w (in the Lawler object), orig_side[h] (0 or
+ * 1), dist[h] (distance from the original cut; s and t unused), gid[h] (its
+ * id in H, hashed for the third key).  final_side receives 0/1 per
+ * hypernode; pierce_side / pierce_node receive the piercing sequence.
+ */
+static uint32_t fmix32(uint32_t h) {
+    h ^= h >> 16;
+    h *= 0x85ebca6bu;
+    h ^= h >> 13;
+    h *= 0xc2b2ae35u;
+    h ^= h >> 16;
+    return h;
+}
+
+static int64_t node_set_weight(const Lawler *G, const uint8_t *mark) {
+    int64_t w = 0;
+    for (int32_t h = 0; h < G->n_nodes; h++) if (mark[h]) w += G->node_w[h];
+    return w;
+}
+
+typedef struct {
+    int64_t flow;           /* final flow value = cut weight of the result */
+    int32_t iterations;     /* max-flow augmentations performed */
+    int32_t n_pierced;      /* length of the piercing sequence */
+    int32_t result_side;    /* 0: (S_r, V\S_r) returned, 1: (V\T_r, T_r) */
+    int32_t status;
+    int64_t source_weight;  /* weight of the returned block 0 */
+} or_fc_result;
+
+int32_t or_flowcutter(Lawler *G, int64_t max_w, const int32_t *orig_side, const int32_t *dist,
+                      const int32_t *gid, uint32_t seed, int64_t flow_bound, int32_t max_iter,
+                      int32_t recompute, uint8_t *final_side, int32_t *pierce_side,
+                      int32_t *pierce_node, int32_t pierce_cap, or_fc_result *res) {
+    int32_t N = G->N, nh = G->n_nodes, mN = G->m_nets;
+    uint8_t *S = (uint8_t *)calloc((size_t)N, 1), *T = (uint8_t *)calloc((size_t)N, 1);
+    uint8_t *Sr = (uint8_t *)calloc((size_t)N, 1), *Tr = (uint8_t *)calloc((size_t)N, 1);
+    uint8_t *cand = (uint8_t *)calloc((size_t)nh, 1);
+    if (!S || !T || !Sr || !Tr || !cand) { free(S); free(T); free(Sr); free(Tr); free(cand); return OR_ERR_OOM; }
+    int64_t W = 0;
+    for (int32_t h = 0; h < nh; h++) W += G->node_w[h];
+    S[0] = 1;
+    T[1] = 1;
+    or_reset_flow(G);
+    int32_t status = OR_OK, np = 0, it = 0;
+    memset(res, 0, sizeof(*res));
+    for (;;) {
+        if (it >= max_iter) { status = OR_ITER_LIMIT; break; }
+        it++;
+        if (recompute) or_reset_flow(G);            /* self-check mode: from scratch */
+        if (dinic(G, S, T) < 0) { status = OR_ERR_OOM; break; }   /* augment to maximality */
+        int64_t flow = or_flow_value(G, S);
+        res->flow = flow;
+        if (flow_bound >= 0 && flow > flow_bound) { status = OR_ABORTED_WORSE; break; }
+        or_reach_from(G, S, Sr);                      /* derive S_r and T_r */
+        or_reach_to(G, T, Tr);
+        int64_t wS = node_set_weight(G, Sr), wT = node_set_weight(G, Tr);
+        int balS = (wS <= max_w) && (W - wS <= max_w);
+        int balT = (wT <= max_w) && (W - wT <= max_w);
+        if (balS || balT) {
+            int use_t = 0;
+            if (balS && balT) {
+                int64_t mS = wS > W - wS ? wS : W - wS;
+                int64_t mT = wT > W - wT ? wT : W - wT;
+                use_t = mT < mS;
+            } else {
+                use_t = !balS;
+            }
+            for (int32_t h = 0; h < nh; h++) final_side[h] = use_t ? (Tr[h] ? 1 : 0) : (Sr[h] ? 0 : 1);
+            res->result_side = use_t;
+            res->source_weight = use_t ? W - wT : wS;
+            break;
+        }
+        int grow_s = wS <= wT;
+        const uint8_t *R = grow_s ? Sr : Tr;       /* reachable set of the growing side */
+        const uint8_t *Ro = grow_s ? Tr : Sr;      /* reachable set of the other side */
+        const uint8_t *O = grow_s ? T : S;         /* terminal set of the other side */
+        int64_t wR = grow_s ? wS : wT;
+        memset(cand, 0, (size_t)nh);
+        for (int32_t e = 0; e < mN; e++) {
+            int32_t node = grow_s ? nh + e : nh + mN + e;   /* in-node for S, out-node for T */
+            if (!R[node]) continue;
+            for (int64_t a = G->adj_off[nh + e]; a < G->adj_off[nh + e + 1]; a++) {
+                int32_t h = G->head[a];
+                if (h < nh) cand[h] = 1;                    /* pins of the net */
+            }
+        }
+        int32_t best = -1;
+        int best_np = 0, best_d = 0;
+        uint32_t best_h = 0;
+        for (int32_t h = 0; h < nh; h++) {
+            if (!cand[h] || R[h] || O[h]) continue;
+            if (wR + G->node_w[h] > max_w) continue;
+            int no_path = !Ro[h];
+            int sd = (orig_side[h] == (grow_s ? 0 : 1)) ? dist[h] : -dist[h];
+            uint32_t hh = fmix32((uint32_t)gid[h] ^ seed);
+            int better = 0;
+            if (best < 0) better = 1;
+            else if (no_path != best_np) better = no_path > best_np;
+            else if (sd != best_d) better = sd > best_d;
+            else better = hh < best_h;
+            if (better) { best = h; best_np = no_path; best_d = sd; best_h = hh; }
+        }
+        if (best < 0) { status = OR_NO_BALANCED_CUT; break; }
+        if (np < pierce_cap) { pierce_side[np] = grow_s ? 0 : 1; pierce_node[np] = best; }
+        np++;
+        if (grow_s) { for (int32_t x = 0; x < N; x++) if (Sr[x]) S[x] = 1; S[best] = 1; }
+        else { for (int32_t x = 0; x < N; x++) if (Tr[x]) T[x] = 1; T[best] = 1; }
+    }
+    res->iterations = it;
+    res->n_pierced = np;
+    res->status = status;
+    free(S); free(T); free(Sr); free(Tr); free(cand);
+    return status;
+}

@@ -1,0 +1,272 @@
+#!/usr/bin/env python3
+"""Benchmark: Lawler-network pins per second to the exact minimum cut.
+
+Workload (one step): on the 2,000,000-vertex / 3,000,000-net ring hypergraph
+(2 + Zipf(2.5) pins per net, capped at 5,000, window 4,096; net weights
+1..10; halves bipartition; region = vertices within 200,000 positions of the
+two cut points), build the flow network of the region, compute the maximum
+flow by push-relabel, and extract the minimal source-side cut S_r.
+value = Lawler-network pins (p_N, s/t pins included) / step time, summed over
+ranks (independent replicas; the single max flow does not shard).
+
+--impl reference times the CPU oracle (Dinic on the explicit Lawler graph)
+on the host cores on a bounded sample of the same generator.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+CFG = 2
+METRIC = "Lawler-network pins/s to exact min cut (1 GB300)"
+UNIT = "pins/s"
+L2_BYTES = 129 * 1024 * 1024
+# Oracle sample: the same generator at 1/10 scale (about 10-30 s of CPU work).
+SAMPLE = dict(n=200_000, m=300_000, radius=20_000)
+
+# algorithmic bytes per counted item of the engine (roofline)
+B_HYPER = 28   # incidence (8) + w(e) (4) + f_in (4) + f_out (4) + two labels (8)
+B_NET = 12     # pin (4) + pin flow (4) + label (4)
+B_NODE = 24    # list entry (4) + label (4) + excess (8) + delta (8)
+B_PUSH = 16    # flow write (4) + excess-delta atomic (8) + stamp (4)
+
+
+def env_rank():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, device):
+        self.device = device
+        self.samples = []
+        self.proc = None
+
+    def start(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 7:
+                self.samples.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4)
+                          if s[3 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.samples)}
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def oracle_step(inst):
+    import oracle
+    H = inst["H"]
+    t0 = time.perf_counter()
+    net = oracle.build_network(H, inst["part"], inst["region"])
+    mc = oracle.max_flow_min_cut(net)
+    dt = time.perf_counter() - t0
+    return net.p, dt, mc.flow
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    inst = synth.instance(CFG, args.seed, **SAMPLE)
+    for _ in range(args.warmup if args.warmup < 1 else 1):
+        oracle_step(inst)
+    times, pins = [], 0
+    for _ in range(args.steps):
+        p, dt, _ = oracle_step(inst)
+        times.append(dt)
+        pins = p
+    v = pins / statistics.mean(times)
+    sample = (f"ring n={SAMPLE['n']}, m={SAMPLE['m']}, radius={SAMPLE['radius']} "
+              f"({pins} Lawler-network pins), same generator as the workload")
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * statistics.mean(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": synth.CONFIGS[CFG]["name"], "seed": args.seed,
+                       "sample": sample},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank, world, local = env_rank()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2201_01556_gb300 import hfp
+    hfp.load()
+
+    inst = synth.instance(CFG, args.seed)
+    H, part, region = inst["H"], inst["part"], inst["region"]
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.int32)).cuda()
+    d_off, d_pins, d_netw, d_nodew = dev(H.net_off), dev(H.pins), dev(H.net_w), dev(H.node_w)
+    d_region, d_side = dev(region), dev(part)
+    stream = torch.cuda.current_stream()
+    ctx = hfp.ctx_create(local, stream.cuda_stream)
+    out_region = torch.empty(len(region), dtype=torch.uint8, device="cuda")
+    flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device="cuda")
+
+    def step(keep_stats=None):
+        net = hfp.build_flow_network(ctx, d_off, d_pins, d_netw, d_nodew, d_region, d_side, H.n)
+        flow = hfp.max_flow(net)
+        ws = hfp.min_cut_source_side_device(net, out_region)
+        if keep_stats is not None:
+            keep_stats.append((net.info.p_pins, hfp.net_stats(net), flow, ws))
+        net.close()
+        return flow
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    launches0 = hfp.kernel_launches()
+    stats = []
+    ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step(stats)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    launches = hfp.kernel_launches() - launches0
+    clk = clocks.stop()
+    total_ms = sum(ms)
+    if dist:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    p_pins = stats[0][0]
+    value = world * p_pins * args.steps / (total_ms / 1e3)
+
+    # end to end through the public API with host buffers
+    e2e_ms = []
+    h2d = (H.net_off.nbytes + H.pins.nbytes + H.net_w.nbytes + H.node_w.nbytes + region.nbytes
+           + part.nbytes)
+    d2h = len(region) + 8
+    for _ in range(max(1, min(args.steps, 3))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        net = hfp.build_flow_network(ctx, H.net_off, H.pins, H.net_w, H.node_w, region, part, H.n)
+        hfp.max_flow(net)
+        _, reg, _, _ = hfp.min_cut_source_side(net, lawler=False, cut_cap=0)
+        torch.cuda.synchronize()
+        e2e_ms.append(1e3 * (time.perf_counter() - t0))
+        net.close()
+    e2e_value = world * p_pins / (statistics.mean(e2e_ms) / 1e3)
+
+    if rank != 0:
+        return 0
+    # roofline of the dominant kernel (the persistent flow engine)
+    eng_ns = sum(s[1]["engine_ns"] for s in stats)
+    eng_launches = sum(s[1]["engine_launches"] for s in stats)
+    model = sum(s[1]["items_hyper"] * B_HYPER + s[1]["items_net"] * B_NET
+                + s[1]["node_visits"] * B_NODE + s[1]["pushes"] * B_PUSH for s in stats)
+    peak, peak_kind = load_peaks()
+    achieved = (model / eng_launches) / (eng_ns / eng_launches / 1e9) / 1e9 if eng_ns else None
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": (achieved / peak) if achieved else None, "traffic": None,
+            "kernel": "engine_kernel", "peak_kind": peak_kind,
+            "engine_ms_per_step": eng_ns / 1e6 / args.steps,
+            "engine_launches_per_step": eng_launches / args.steps}
+    st = stats[0][1]
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": synth.CONFIGS[CFG]["name"], "seed": args.seed, "n": H.n,
+                       "m": H.m, "pins_H": H.p, "region": len(region), "lawler_pins": p_pins,
+                       "flow": stats[0][2], "source_weight": stats[0][3],
+                       "l2": "flushed between timed steps (2x L2 buffer write)",
+                       "parallelism": f"replicas{world}"},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h)},
+            "gpu_launches": int(launches),
+            "clocks": clk, "roofline": roof,
+            "engine": {"rounds": st["rounds"], "global_relabels": st["global_relabels"],
+                       "gr_levels": st["gr_levels"], "pushes": st["pushes"]}}
+    if not args.no_cpu_baseline:
+        sinst = synth.instance(CFG, args.seed, **SAMPLE)
+        p, dt, _ = oracle_step(sinst)
+        line["cpu_baseline"] = {"value": p / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"ring n={SAMPLE['n']}, m={SAMPLE['m']}, radius="
+                                          f"{SAMPLE['radius']} ({p} Lawler-network pins), "
+                                          f"one run, {dt:.1f} s"}
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,218 @@
+/*
+ * hfp: flow-based hypergraph refinement on one GB300 (sm_103a).
+ *
+ * C ABI of libhfp.so.  Operations follow Gottesbueren, Heuer and Sanders,
+ * "Parallel Flow-Based Hypergraph Partitioning" (arXiv 2201.01556):
+ *   - flow network construction of a region (Section 6),
+ *   - maximum flow by synchronous push-relabel on the Lawler expansion
+ *     (Sections 2 and 8),
+ *   - minimal source-side / sink-side minimum cuts (Sections 2 and 8.4),
+ *   - one FlowCutter pierce-and-augment step and the whole FlowCutter loop
+ *     (Section 7, Algorithm 2).
+ *
+ * Conventions (all entry points):
+ *   - Return an hfp_status: HFP_OK (0) or a negative code.  hfp_last_error()
+ *     gives a message for the calling thread's last failure.
+ *   - Inputs are borrowed for the duration of the call; the library copies
+ *     what it keeps.  Handles (hfp_ctx, hfp_net) are owned by the library and
+ *     released by their destroy call.
+ *   - Array arguments live in host or device memory as the hfp_mem argument
+ *     of the call says.  Device pointers must be on the context's device.
+ *   - All ids are int32, weights are int32 (> 0); flow values and weight sums
+ *     are int64.  The sum of all net weights and the sum of all vertex
+ *     weights must each stay below 2^31.
+ *   - Work runs on the context's stream.  Calls that return values to the
+ *     host synchronise that stream.
+ *   - There is no CPU fallback: every step runs in this library's kernels.
+ *
+ * Flow hypergraph numbering (used by every per-node input and output):
+ *   hypernode 0 = s (region-external vertices of side 0, contracted),
+ *   hypernode 1 = t (region-external vertices of side 1, contracted),
+ *   hypernode 2 + i = region[i];
+ *   Lawler node of hypernode h = h, of the in-node of net e = n_nodes + e,
+ *   of the out-node of net e = n_nodes + m_nets + e.
+ *   Nets keep the ascending order of their ids in H; a net's pins are its
+ *   region pins in H's order, then s, then t.
+ */
+#ifndef HFP_H
+#define HFP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t hfp_status;
+
+#define HFP_OK 0
+#define HFP_ERR_INVALID (-1)          /* malformed input (CSR, ids, weights, duplicates) */
+#define HFP_ERR_OOM (-2)              /* device or host allocation failed */
+#define HFP_ERR_CUDA (-3)             /* a CUDA call failed */
+#define HFP_ERR_ITER_LIMIT (-4)       /* a bounded device loop or wait gave up */
+#define HFP_NO_BALANCED_CUT (-5)      /* FlowCutter found no piercing candidate */
+#define HFP_ABORTED_WORSE (-6)        /* flow exceeded the bound (Section 8.3, "Flow Value") */
+#define HFP_ERR_BUFFER_TOO_SMALL (-7) /* an output capacity is too small */
+#define HFP_ERR_STATE (-8)            /* call out of order (e.g. cut before max flow) */
+
+typedef enum { HFP_MEM_HOST = 0, HFP_MEM_DEVICE = 1 } hfp_mem;
+
+typedef struct hfp_ctx hfp_ctx;
+typedef struct hfp_net hfp_net;
+
+/* Hypergraph H = (V, E, c, w) as a net -> pins CSR (Section 2).
+ * net_off[m + 1] (non-decreasing, net_off[0] = 0), pins[net_off[m]] with ids
+ * in [0, n) and no repeated pin inside a net, net_w[m] > 0, node_w[n] > 0 or
+ * NULL for unit weights. */
+typedef struct {
+  int32_t n;
+  int32_t m;
+  const uint32_t* net_off;
+  const int32_t* pins;
+  const int32_t* net_w;
+  const int32_t* node_w;
+} hfp_hypergraph;
+
+/* Sizes of a built flow network. */
+typedef struct {
+  int32_t n_nodes;       /* hypernodes, including s and t */
+  int32_t m_nets;        /* nets kept */
+  int64_t p_pins;        /* pins, including s/t pins ("Lawler-network pins") */
+  int32_t lawler_nodes;  /* n_nodes + 2 * m_nets */
+  int32_t pad;
+  int64_t total_weight;  /* c(V) of the nodes of the network, s and t included */
+} hfp_net_info;
+
+/* Counters of the device engine since the network was built. */
+typedef struct {
+  uint64_t rounds;           /* discharge rounds */
+  uint64_t global_relabels;
+  uint64_t gr_levels;        /* reverse-BFS levels over all global relabels */
+  uint64_t items_hyper;      /* hypernode incidences scanned */
+  uint64_t items_net;        /* net pins scanned */
+  uint64_t node_visits;      /* list entries processed */
+  uint64_t pushes;
+  uint64_t engine_launches;  /* cooperative launches of the engine kernel */
+  uint64_t engine_ns;        /* device time of those launches (CUDA events on the context stream) */
+} hfp_stats;
+
+/* FlowCutter parameters (Section 7). */
+typedef struct {
+  int64_t max_block_weight;  /* L: a side is balanced iff its weight <= L */
+  int64_t flow_bound;        /* abort with HFP_ABORTED_WORSE once flow > bound; < 0: none */
+  uint32_t seed;             /* seeds the third piercing key */
+  int32_t max_iterations;    /* <= 0: no limit beyond the number of hypernodes */
+} hfp_fc_params;
+
+typedef struct {
+  int64_t flow;              /* final flow = cut weight of the returned bipartition */
+  int64_t source_weight;     /* weight of block 0 of the returned bipartition */
+  int32_t iterations;        /* max-flow augmentations */
+  int32_t n_pierced;         /* piercing steps taken */
+  int32_t result_side;       /* 0: (S_r, V \ S_r) returned; 1: (V \ T_r, T_r) */
+  int32_t pad;
+} hfp_fc_result;
+
+/* --- context --------------------------------------------------------------
+ * Creates a context on CUDA device `device`.  `stream` is a cudaStream_t
+ * (NULL = the legacy default stream); the context does not own it. */
+hfp_status hfp_ctx_create(hfp_ctx** ctx, int device, void* stream);
+void hfp_ctx_destroy(hfp_ctx* ctx);
+/* Message of the calling thread's last failed call ("" if none). */
+const char* hfp_last_error(void);
+/* Number of kernels this library has launched in the process so far. */
+uint64_t hfp_kernel_launches(void);
+
+/* --- network construction (Section 6, "Construction Algorithms") ---------
+ * Builds the flow hypergraph of the region B = region[0 .. n_region):
+ * every net of H with a pin in B is copied with its region pins; a pin
+ * outside B whose side is 0 adds s, side 1 adds t (once per net); pins of any
+ * other side are ignored.  Nets left with fewer than two pins, or holding
+ * both s and t, are dropped (Section 6, end of "Construction Algorithms").
+ *   H, region, side, dist_from_cut: in `mem` memory.
+ *   side[n]: 0 or 1 for vertices of the two blocks, any other value for
+ *            vertices outside both; every region vertex must have side 0/1.
+ *   dist_from_cut[n_region]: distance of region[i] from the original cut,
+ *            used by the piercing rule (Section 7, "Piercing"); NULL makes
+ *            the library compute it: region pins of nets of H with pins on
+ *            both sides get 1, unlabelled region pins of a net holding a
+ *            region vertex at distance d get d + 1, unreached vertices
+ *            2^20 - 1.
+ * Errors: HFP_ERR_INVALID (ids out of range, repeated region vertex, region
+ * vertex without side 0/1, non-positive weight, weight sums >= 2^31),
+ * HFP_ERR_OOM, HFP_ERR_CUDA.  *out is NULL on error. */
+hfp_status hfp_build_flow_network(hfp_ctx* ctx, const hfp_hypergraph* H, hfp_mem mem,
+                                  const int32_t* region, int32_t n_region, const int32_t* side,
+                                  const int32_t* dist_from_cut, hfp_net** out);
+void hfp_net_destroy(hfp_net* net);
+hfp_status hfp_net_get_info(hfp_net* net, hfp_net_info* info);
+/* Copies the network CSR to caller buffers in `mem` memory (any pointer may
+ * be NULL to skip it): net_off[m_nets + 1], pins[p_pins], net_w[m_nets],
+ * net_gid[m_nets] (ids in H), node_w[n_nodes], node_off[n_nodes + 1] and
+ * inc_slot[p_pins] (hypernode -> pin slots, ascending), dist[n_nodes]. */
+hfp_status hfp_net_export(hfp_net* net, hfp_mem mem, uint32_t* net_off, int32_t* pins,
+                          int32_t* net_w, int32_t* net_gid, int32_t* node_w, uint32_t* node_off,
+                          int32_t* inc_slot, int32_t* dist);
+hfp_status hfp_net_get_stats(hfp_net* net, hfp_stats* stats);
+
+/* --- maximum flow (Section 8) ---------------------------------------------
+ * Augments the network's current flow to a maximum preflow with respect to
+ * its current source set S and sink set T (initially {s} and {t}); on return
+ * labels are exact distances to T, so the sink side T_r is known.  Returns
+ * the flow value (excess that reached T).  HFP_ERR_ITER_LIMIT if the round
+ * budget or a device wait ran out. */
+hfp_status hfp_max_flow(hfp_net* net, int64_t* flow_value);
+
+/* --- minimum cuts (Section 2; Section 8.4 "Source-Side Cut") -------------
+ * Requires a completed hfp_max_flow.  The source side S_r is the set of
+ * Lawler nodes reachable by residual arcs from S and from every non-sink
+ * node with excess; it is the minimal source side of all minimum cuts.
+ * Outputs (in `mem` memory, each may be NULL):
+ *   in_source_lawler[lawler_nodes], in_source_region[n_region]: 1 if in S_r;
+ *   cut_nets[cap]: ids in H of the nets whose in-node is in S_r and whose
+ *   out-node is not (the cut nets), *n_cut their number
+ *   (HFP_ERR_BUFFER_TOO_SMALL if cap < *n_cut; *n_cut is still set);
+ *   *source_weight = c(S_r), the hypernode weight of S_r. */
+hfp_status hfp_min_cut_source_side(hfp_net* net, hfp_mem mem, uint8_t* in_source_lawler,
+                                   uint8_t* in_source_region, int32_t* cut_nets, int32_t cap,
+                                   int32_t* n_cut, int64_t* source_weight);
+/* Sink side T_r: Lawler nodes with a residual path into T (the minimal sink
+ * side).  Outputs as above; *sink_weight = c(T_r). */
+hfp_status hfp_min_cut_sink_side(hfp_net* net, hfp_mem mem, uint8_t* in_sink_lawler,
+                                 uint8_t* in_sink_region, int64_t* sink_weight);
+
+/* --- one FlowCutter step (Section 7, Algorithm 2 lines 7-10) -------------
+ * side 0: S <- S_r + nodes; side 1: T <- T_r + nodes, then augments the flow
+ * to maximality again (a source-side pierce keeps the labels; a sink-side
+ * pierce adds the excess of the new sinks to the flow value and runs a
+ * global relabel first, Section 8.4).  nodes[count] are hypernode ids in
+ * host memory; nodes == NULL selects one node by the piercing rule (see
+ * hfp_flowcutter) and stores it in *pierced.  Returns the new flow value.
+ * HFP_NO_BALANCED_CUT when the rule finds no candidate. */
+hfp_status hfp_pierce_and_augment(hfp_net* net, int32_t side, const int32_t* nodes,
+                                  int32_t count, const hfp_fc_params* params, int32_t* pierced,
+                                  int64_t* flow_value);
+
+/* --- FlowCutter (Section 7, Algorithm 2) ----------------------------------
+ * Runs max flow / cut derivation / piercing until (S_r, V \ S_r) or
+ * (V \ T_r, T_r) is balanced (both sides <= L).  If both are, the one with
+ * the lighter heavier side is returned (ties: the source side).  The lighter
+ * reachable side grows (S on ties).  Piercing candidates for S are hypernodes
+ * not in S_r and not in T that are pins of a net whose in-node is in S_r and
+ * whose weight keeps c(S_r) + c(v) <= L; the best has, in order: no residual
+ * path to T (v not in T_r); the larger signed distance from the original cut
+ * (+dist if v's original side is 0, -dist otherwise); the smaller
+ * fmix32(id_in_H(v) ^ seed).  T grows symmetrically.
+ * Outputs (host memory, may be NULL): final_side[n_region] (0 = block of s),
+ * pierce_side[pierce_cap] / pierce_node[pierce_cap] (hypernode ids), result.
+ * Errors: HFP_NO_BALANCED_CUT, HFP_ABORTED_WORSE, HFP_ERR_ITER_LIMIT,
+ * HFP_ERR_BUFFER_TOO_SMALL (pierce_cap too small; the run still completes). */
+hfp_status hfp_flowcutter(hfp_net* net, const hfp_fc_params* params, uint8_t* final_side,
+                          int32_t* pierce_side, int32_t* pierce_node, int32_t pierce_cap,
+                          hfp_fc_result* result);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HFP_H */

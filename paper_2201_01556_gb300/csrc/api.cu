@@ -1,0 +1,852 @@
+// Host implementation of the C ABI declared in include/hfp.h.
+//
+// The host only allocates, launches and reads back a few words: network
+// construction, the push-relabel rounds, global relabels, residual BFSs and
+// piercing all run in the kernels of build.cu, engine.cu and cuts.cu.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "hfp.h"
+#include "kernels.cuh"
+
+#include <atomic>
+
+#define HFP_API extern "C" __attribute__((visibility("default")))
+
+using namespace hfp;
+
+namespace hfp {
+static std::atomic<unsigned long long> g_launches{0};
+void count_launches(unsigned k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+unsigned long long launches_total() { return g_launches.load(std::memory_order_relaxed); }
+}  // namespace hfp
+
+namespace {
+
+thread_local std::string g_err;
+
+hfp_status fail(hfp_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return s;
+}
+
+#define CK(call)                                                                          \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return fail(e_ == cudaErrorMemoryAllocation ? HFP_ERR_OOM : HFP_ERR_CUDA,           \
+                  "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__,       \
+                  __LINE__);                                                              \
+  } while (0)
+
+// Stream-ordered device allocation owned by a scope.
+struct DevBuf {
+  void* p = nullptr;
+  cudaStream_t st = nullptr;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  ~DevBuf() {
+    if (p) cudaFreeAsync(p, st);
+  }
+  cudaError_t alloc(size_t bytes, cudaStream_t s) {
+    st = s;
+    return cudaMallocAsync(&p, bytes ? bytes : 16, s);
+  }
+  template <class T>
+  T* as() const { return static_cast<T*>(p); }
+};
+
+size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
+
+int map_dev_err(int e) {
+  switch (e) {
+    case kDevOk: return HFP_OK;
+    case kDevBadInput: return HFP_ERR_INVALID;
+    default: return HFP_ERR_ITER_LIMIT;
+  }
+}
+
+}  // namespace
+
+struct hfp_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int sms = 0;
+  int coop_grid = 0;
+  int threads = kEngineThreads;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // engine launch timing
+  Ctl* pinned_ctl = nullptr;       // host mirror of Ctl
+  void* pinned_small = nullptr;    // 4 KB staging
+  Params params{};
+};
+
+struct hfp_net {
+  hfp_ctx* ctx = nullptr;
+  NetDev d{};
+  EngineCtl* E = nullptr;
+  void* arena = nullptr;
+  int32_t* net_gid = nullptr;
+  int32_t* dev_nodes = nullptr;    // staging for pierced node ids
+  int32_t dev_nodes_cap = 0;
+  int32_t n_region = 0;
+  int64_t total_w = 0;
+  bool flow_started = false;
+  bool labels_exact = false;
+  bool sr_valid = false;
+  uint64_t launches = 0;
+  uint64_t engine_ns = 0;
+};
+
+namespace {
+
+hfp_status set_device(hfp_ctx* ctx) {
+  CK(cudaSetDevice(ctx->device));
+  return HFP_OK;
+}
+
+hfp_status read_ctl(hfp_net* net, Ctl* out) {
+  hfp_ctx* c = net->ctx;
+  CK(cudaMemcpyAsync(c->pinned_ctl, &net->E->c, sizeof(Ctl), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  *out = *c->pinned_ctl;
+  return HFP_OK;
+}
+
+hfp_status run_engine(hfp_net* net) {
+  hfp_ctx* c = net->ctx;
+  void* args[] = {(void*)&net->d, (void*)&net->E, (void*)&c->params};
+  CK(cudaEventRecord(c->ev0, c->stream));
+  CK(cudaLaunchCooperativeKernel((void*)engine_kernel, dim3(c->coop_grid), dim3(c->threads),
+                                 args, 0, c->stream));
+  CK(cudaEventRecord(c->ev1, c->stream));
+  count_launches(1);
+  net->launches++;
+  Ctl ctl;
+  hfp_status s = read_ctl(net, &ctl);
+  if (s != HFP_OK) return s;
+  float ms = 0.f;
+  CK(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+  net->engine_ns += (uint64_t)((double)ms * 1e6);
+  if (ctl.err != kDevOk)
+    return fail(map_dev_err(ctl.err), "flow engine stopped: device code %d (where %d)", ctl.err,
+                ctl.err_where);
+  return HFP_OK;
+}
+
+hfp_status stage_nodes(hfp_net* net, const int32_t* nodes, int32_t count) {
+  hfp_ctx* c = net->ctx;
+  if (count > net->dev_nodes_cap) {
+    if (net->dev_nodes) CK(cudaFreeAsync(net->dev_nodes, c->stream));
+    net->dev_nodes = nullptr;
+    int32_t cap = count < 64 ? 64 : count;
+    CK(cudaMallocAsync((void**)&net->dev_nodes, sizeof(int32_t) * cap, c->stream));
+    net->dev_nodes_cap = cap;
+  }
+  for (int32_t i = 0; i < count; i++)
+    if (nodes[i] < 0 || nodes[i] >= net->d.n_nodes)
+      return fail(HFP_ERR_INVALID, "pierced node %d out of range", nodes[i]);
+  if (count > 0) {
+    CK(cudaMemcpyAsync(net->dev_nodes, nodes, sizeof(int32_t) * count, cudaMemcpyHostToDevice,
+                       c->stream));
+  }
+  return HFP_OK;
+}
+
+// Flow from {s} at the first call: saturate s, then a global relabel seeds
+// exact labels and the frontier; the engine runs to a maximum preflow and
+// ends with a final global relabel (exact labels, T_r).
+hfp_status ensure_max_flow(hfp_net* net) {
+  if (net->labels_exact) return HFP_OK;
+  hfp_ctx* c = net->ctx;
+  if (!net->flow_started) {
+    int32_t zero = 0;
+    hfp_status s = stage_nodes(net, &zero, 1);
+    if (s != HFP_OK) return s;
+    launch_engine_setup(net->E, SETUP_PREP, c->stream);
+    launch_saturate(net->d, net->E, net->dev_nodes, 1, c->stream);
+    net->flow_started = true;
+  }
+  launch_engine_setup(net->E, SETUP_GR, c->stream);
+  hfp_status s = run_engine(net);
+  if (s != HFP_OK) return s;
+  net->labels_exact = true;
+  net->sr_valid = false;
+  return HFP_OK;
+}
+
+hfp_status ensure_source_side(hfp_net* net) {
+  if (net->sr_valid) return HFP_OK;
+  launch_engine_setup(net->E, SETUP_SR, net->ctx->stream);
+  hfp_status s = run_engine(net);
+  if (s != HFP_OK) return s;
+  net->sr_valid = true;
+  return HFP_OK;
+}
+
+hfp_status copy_out(void* dst, const void* src, size_t bytes, hfp_mem mem, cudaStream_t st) {
+  CK(cudaMemcpyAsync(dst, src, bytes,
+                     mem == HFP_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                     st));
+  return HFP_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+HFP_API const char* hfp_last_error(void) { return g_err.c_str(); }
+
+HFP_API uint64_t hfp_kernel_launches(void) { return launches_total(); }
+
+HFP_API hfp_status hfp_ctx_create(hfp_ctx** out, int device, void* stream) {
+  if (!out) return fail(HFP_ERR_INVALID, "ctx pointer is NULL");
+  *out = nullptr;
+  int ndev = 0;
+  CK(cudaGetDeviceCount(&ndev));
+  if (device < 0 || device >= ndev) return fail(HFP_ERR_INVALID, "no CUDA device %d", device);
+  CK(cudaSetDevice(device));
+  int coop = 0;
+  CK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device));
+  if (!coop) return fail(HFP_ERR_CUDA, "device %d lacks cooperative launch", device);
+  hfp_ctx* c = new hfp_ctx();
+  c->device = device;
+  c->stream = (cudaStream_t)stream;
+  cudaError_t e = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device);
+  int per_sm = 0;
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, engine_kernel, c->threads, 0);
+  if (e == cudaSuccess && per_sm < 1) e = cudaErrorInvalidConfiguration;
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&c->pinned_ctl, sizeof(Ctl));
+  if (e == cudaSuccess) e = cudaMallocHost(&c->pinned_small, 4096);
+  if (e == cudaSuccess) e = cudaEventCreate(&c->ev0);
+  if (e == cudaSuccess) e = cudaEventCreate(&c->ev1);
+  if (e != cudaSuccess) {
+    if (c->pinned_ctl) cudaFreeHost(c->pinned_ctl);
+    delete c;
+    return fail(HFP_ERR_CUDA, "context set-up failed: %s", cudaGetErrorString(e));
+  }
+  if (per_sm > 2) per_sm = 2;
+  c->coop_grid = c->sms * per_sm;
+  c->params.timeout_ns = 10ull * 1000 * 1000 * 1000;
+  c->params.max_rounds = 1ull << 22;
+  c->params.gr_work = 0;           // set per network (a multiple of its node count)
+  c->params.stall_rounds = 500;    // Section 8.3, "Avoid Pushing Flow Back"
+  c->params.stall_nodes = 1500;
+  *out = c;
+  return HFP_OK;
+}
+
+HFP_API void hfp_ctx_destroy(hfp_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  cudaStreamSynchronize(c->stream);
+  if (c->pinned_ctl) cudaFreeHost(c->pinned_ctl);
+  if (c->pinned_small) cudaFreeHost(c->pinned_small);
+  if (c->ev0) cudaEventDestroy(c->ev0);
+  if (c->ev1) cudaEventDestroy(c->ev1);
+  delete c;
+}
+
+HFP_API void hfp_net_destroy(hfp_net* net) {
+  if (!net) return;
+  cudaSetDevice(net->ctx->device);
+  cudaStream_t st = net->ctx->stream;
+  if (net->arena) cudaFreeAsync(net->arena, st);
+  if (net->dev_nodes) cudaFreeAsync(net->dev_nodes, st);
+  cudaStreamSynchronize(st);
+  delete net;
+}
+
+HFP_API hfp_status hfp_build_flow_network(hfp_ctx* ctx, const hfp_hypergraph* H, hfp_mem mem,
+                                          const int32_t* region, int32_t n_region,
+                                          const int32_t* side, const int32_t* dist_from_cut,
+                                          hfp_net** out) {
+  if (!out) return fail(HFP_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (!ctx || !H) return fail(HFP_ERR_INVALID, "ctx or H is NULL");
+  const int32_t n = H->n, m = H->m;
+  if (n < 0 || m < 0 || n_region < 0 || n_region > n)
+    return fail(HFP_ERR_INVALID, "bad sizes n=%d m=%d n_region=%d", n, m, n_region);
+  if (!H->net_off || (m > 0 && (!H->pins || !H->net_w)) || (n > 0 && !side) ||
+      (n_region > 0 && !region))
+    return fail(HFP_ERR_INVALID, "missing input array");
+  if (mem != HFP_MEM_HOST && mem != HFP_MEM_DEVICE) return fail(HFP_ERR_INVALID, "bad mem");
+  hfp_status s = set_device(ctx);
+  if (s != HFP_OK) return s;
+  cudaStream_t st = ctx->stream;
+  const int sms = ctx->sms;
+
+  // total pins of H
+  uint32_t P = 0;
+  if (mem == HFP_MEM_HOST) {
+    if (H->net_off[0] != 0) return fail(HFP_ERR_INVALID, "net_off[0] != 0");
+    for (int32_t e = 0; e < m; e++)
+      if (H->net_off[e + 1] < H->net_off[e]) return fail(HFP_ERR_INVALID, "net_off decreases");
+    P = H->net_off[m];
+  } else {
+    uint32_t* h = (uint32_t*)ctx->pinned_small;
+    CK(cudaMemcpyAsync(h, H->net_off, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(h + 1, H->net_off + m, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (h[0] != 0) return fail(HFP_ERR_INVALID, "net_off[0] != 0");
+    P = h[1];
+  }
+  if (P >= (1u << 31)) return fail(HFP_ERR_INVALID, "too many pins (%u)", P);
+
+  // inputs on the device
+  DevBuf in_off, in_pins, in_netw, in_nodew, in_side, in_region, in_dist;
+  const uint32_t* d_off = H->net_off;
+  const int32_t *d_pins = H->pins, *d_netw = H->net_w, *d_nodew = H->node_w, *d_side = side,
+                *d_region = region, *d_dist = dist_from_cut;
+  if (mem == HFP_MEM_HOST) {
+    CK(in_off.alloc(sizeof(uint32_t) * (m + 1), st));
+    CK(cudaMemcpyAsync(in_off.p, H->net_off, sizeof(uint32_t) * (m + 1), cudaMemcpyHostToDevice, st));
+    d_off = in_off.as<uint32_t>();
+    CK(in_pins.alloc(sizeof(int32_t) * P, st));
+    if (P) CK(cudaMemcpyAsync(in_pins.p, H->pins, sizeof(int32_t) * P, cudaMemcpyHostToDevice, st));
+    d_pins = in_pins.as<int32_t>();
+    CK(in_netw.alloc(sizeof(int32_t) * m, st));
+    if (m) CK(cudaMemcpyAsync(in_netw.p, H->net_w, sizeof(int32_t) * m, cudaMemcpyHostToDevice, st));
+    d_netw = in_netw.as<int32_t>();
+    if (H->node_w) {
+      CK(in_nodew.alloc(sizeof(int32_t) * n, st));
+      if (n) CK(cudaMemcpyAsync(in_nodew.p, H->node_w, sizeof(int32_t) * n, cudaMemcpyHostToDevice, st));
+      d_nodew = in_nodew.as<int32_t>();
+    }
+    CK(in_side.alloc(sizeof(int32_t) * n, st));
+    if (n) CK(cudaMemcpyAsync(in_side.p, side, sizeof(int32_t) * n, cudaMemcpyHostToDevice, st));
+    d_side = in_side.as<int32_t>();
+    CK(in_region.alloc(sizeof(int32_t) * n_region, st));
+    if (n_region)
+      CK(cudaMemcpyAsync(in_region.p, region, sizeof(int32_t) * n_region, cudaMemcpyHostToDevice, st));
+    d_region = in_region.as<int32_t>();
+    if (dist_from_cut) {
+      CK(in_dist.alloc(sizeof(int32_t) * n_region, st));
+      if (n_region)
+        CK(cudaMemcpyAsync(in_dist.p, dist_from_cut, sizeof(int32_t) * n_region,
+                           cudaMemcpyHostToDevice, st));
+      d_dist = in_dist.as<int32_t>();
+    }
+  }
+
+  // pass 1 scratch
+  const int32_t n_nodes = n_region + 2;
+  DevBuf loc, keep, size, has_s, has_t, net_pos, pin_pos, s_pos, t_pos, totals, wsum, err,
+      dist_tmp, scan_scr;
+  const size_t mm = (size_t)(m > 0 ? m : 1);
+  CK(loc.alloc(sizeof(int32_t) * (n > 0 ? n : 1), st));
+  CK(keep.alloc(sizeof(unsigned) * mm, st));
+  CK(size.alloc(sizeof(unsigned) * mm, st));
+  CK(has_s.alloc(sizeof(unsigned) * mm, st));
+  CK(has_t.alloc(sizeof(unsigned) * mm, st));
+  CK(net_pos.alloc(sizeof(unsigned) * mm, st));
+  CK(pin_pos.alloc(sizeof(unsigned) * mm, st));
+  CK(s_pos.alloc(sizeof(unsigned) * mm, st));
+  CK(t_pos.alloc(sizeof(unsigned) * mm, st));
+  CK(totals.alloc(sizeof(unsigned) * 8, st));
+  CK(wsum.alloc(sizeof(unsigned long long) * 4, st));
+  CK(err.alloc(sizeof(int), st));
+  CK(dist_tmp.alloc(sizeof(int32_t) * (n_region > 0 ? n_region : 1), st));
+  size_t scan_words = scan_scratch_words((unsigned)(m > n_nodes + 1 ? m : n_nodes + 1)) + 8;
+  CK(scan_scr.alloc(sizeof(unsigned) * scan_words, st));
+  if (n) CK(cudaMemsetAsync(loc.p, 0xFF, sizeof(int32_t) * n, st));
+  CK(cudaMemsetAsync(totals.p, 0, sizeof(unsigned) * 8, st));
+  CK(cudaMemsetAsync(wsum.p, 0, sizeof(unsigned long long) * 4, st));
+  CK(cudaMemsetAsync(err.p, 0, sizeof(int), st));
+  if (n_region) CK(cudaMemsetAsync(dist_tmp.p, 0, sizeof(int32_t) * n_region, st));
+
+  // per-hypernode attribute arrays live in the final arena; region_map
+  // needs them now, so they are allocated first (sizes are known)
+  DevBuf attrs;
+  const size_t attr_bytes = align_up(sizeof(int32_t) * n_nodes) * 3 + align_up(n_nodes);
+  CK(attrs.alloc(attr_bytes, st));
+  int32_t* a_gid = attrs.as<int32_t>();
+  int32_t* a_w = (int32_t*)((char*)attrs.p + align_up(sizeof(int32_t) * n_nodes));
+  int8_t* a_orig = (int8_t*)((char*)attrs.p + 3 * align_up(sizeof(int32_t) * n_nodes));
+
+  unsigned* tot = totals.as<unsigned>();
+  launch_region_map(n, n_region, d_region, d_side, d_nodew, loc.as<int32_t>(), a_gid, a_w, a_orig,
+                    err.as<int>(), st);
+  launch_st_weight(n, loc.as<int32_t>(), d_side, d_nodew, wsum.as<unsigned long long>(),
+                   err.as<int>(), sms, st);
+  launch_net_scan(n, m, d_off, d_pins, d_netw, d_side, loc.as<int32_t>(), keep.as<unsigned>(),
+                  size.as<unsigned>(), has_s.as<unsigned>(), has_t.as<unsigned>(),
+                  dist_tmp.as<int32_t>(), d_dist ? 0 : 1, wsum.as<unsigned long long>() + 3,
+                  err.as<int>(), sms, st);
+  if (m) {
+    CK(cudaMemcpyAsync(net_pos.p, keep.p, sizeof(unsigned) * m, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(pin_pos.p, size.p, sizeof(unsigned) * m, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(s_pos.p, has_s.p, sizeof(unsigned) * m, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(t_pos.p, has_t.p, sizeof(unsigned) * m, cudaMemcpyDeviceToDevice, st));
+  }
+  scan_exclusive(net_pos.as<unsigned>(), m, scan_scr.as<unsigned>(), tot + 0, st);
+  scan_exclusive(pin_pos.as<unsigned>(), m, scan_scr.as<unsigned>(), tot + 1, st);
+  scan_exclusive(s_pos.as<unsigned>(), m, scan_scr.as<unsigned>(), tot + 2, st);
+  scan_exclusive(t_pos.as<unsigned>(), m, scan_scr.as<unsigned>(), tot + 3, st);
+
+  struct Head {
+    unsigned totals[8];
+    unsigned long long wsum[4];
+    int err;
+  };
+  Head* hh = (Head*)ctx->pinned_small;
+  CK(cudaMemcpyAsync(hh->totals, totals.p, sizeof(unsigned) * 8, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(hh->wsum, wsum.p, sizeof(unsigned long long) * 4, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&hh->err, err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (hh->err != kDevOk) return fail(HFP_ERR_INVALID, "invalid hypergraph, region or side input");
+  if (hh->wsum[2] >= (1ull << 31)) return fail(HFP_ERR_INVALID, "vertex weights sum to >= 2^31");
+  if (hh->wsum[3] >= (1ull << 31)) return fail(HFP_ERR_INVALID, "net weights sum to >= 2^31");
+  const int32_t m_net = (int32_t)hh->totals[0];
+  const unsigned p_net = hh->totals[1];
+  const int64_t NL64 = (int64_t)n_nodes + 2 * (int64_t)m_net;
+  if (NL64 >= (1ll << 31) - 2) return fail(HFP_ERR_INVALID, "flow network too large");
+  const int32_t NL = (int32_t)NL64;
+  const int64_t total_w = (int64_t)hh->wsum[0] + (int64_t)hh->wsum[1];
+
+  // arena for the network and its flow state
+  hfp_net* net = new hfp_net();
+  net->ctx = ctx;
+  net->n_region = n_region;
+  std::vector<size_t> sz = {
+      sizeof(uint32_t) * (m_net + 1), sizeof(int32_t) * p_net, sizeof(int32_t) * m_net,
+      sizeof(int32_t) * m_net, sizeof(uint32_t) * (n_nodes + 1), sizeof(int2) * p_net,
+      sizeof(int32_t) * n_nodes, sizeof(int32_t) * n_nodes, (size_t)n_nodes, sizeof(int32_t) * n_nodes,
+      sizeof(int32_t) * p_net, sizeof(int32_t) * p_net, sizeof(int32_t) * m_net,
+      sizeof(int32_t) * NL, sizeof(int32_t) * NL, sizeof(long long) * NL, sizeof(long long) * NL,
+      sizeof(uint32_t) * NL, (size_t)NL, (size_t)NL, (size_t)NL, sizeof(int32_t) * NL,
+      sizeof(int32_t) * NL, sizeof(int32_t) * NL, sizeof(int32_t) * NL, sizeof(EngineCtl)};
+  size_t total = 0;
+  for (size_t b : sz) total += align_up(b);
+  cudaError_t ae = cudaMallocAsync(&net->arena, total, st);
+  if (ae != cudaSuccess) {
+    delete net;
+    return fail(HFP_ERR_OOM, "cannot allocate %zu bytes for the flow network", total);
+  }
+  std::vector<char*> ptr;
+  {
+    char* q = (char*)net->arena;
+    for (size_t b : sz) {
+      ptr.push_back(q);
+      q += align_up(b);
+    }
+  }
+  NetDev& D = net->d;
+  D.n_nodes = n_nodes;
+  D.m_nets = m_net;
+  D.NL = NL;
+  D.p_pins = p_net;
+  uint32_t* nnet_off = (uint32_t*)ptr[0];
+  int32_t* npin = (int32_t*)ptr[1];
+  int32_t* nnet_w = (int32_t*)ptr[2];
+  net->net_gid = (int32_t*)ptr[3];
+  unsigned* node_off = (unsigned*)ptr[4];
+  int2* inc = (int2*)ptr[5];
+  int32_t* node_w = (int32_t*)ptr[6];
+  int32_t* node_dist = (int32_t*)ptr[7];
+  int8_t* node_orig = (int8_t*)ptr[8];
+  int32_t* node_gid = (int32_t*)ptr[9];
+  D.net_off = nnet_off;
+  D.pin = npin;
+  D.net_w = nnet_w;
+  D.node_off = node_off;
+  D.inc = inc;
+  D.node_w = node_w;
+  D.node_dist = node_dist;
+  D.node_orig = node_orig;
+  D.node_gid = node_gid;
+  D.f_in = (int32_t*)ptr[10];
+  D.f_out = (int32_t*)ptr[11];
+  D.f_b = (int32_t*)ptr[12];
+  D.lab0 = (int32_t*)ptr[13];
+  D.lab1 = (int32_t*)ptr[14];
+  D.excess = (long long*)ptr[15];
+  D.delta = (long long*)ptr[16];
+  D.stamp = (uint32_t*)ptr[17];
+  D.flags = (uint8_t*)ptr[18];
+  D.needrl = (uint8_t*)ptr[19];
+  D.insr = (uint8_t*)ptr[20];
+  for (int k = 0; k < 4; k++) D.list[k] = (int32_t*)ptr[21 + k];
+  net->E = (EngineCtl*)ptr[25];
+  net->total_w = total_w;
+
+  hfp_status rs = HFP_OK;
+  auto done = [&](hfp_status r) {
+    if (r != HFP_OK) hfp_net_destroy(net);
+    return r;
+  };
+#define CKN(call)                                                                         \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return done(fail(HFP_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_)));    \
+  } while (0)
+
+  CKN(cudaMemcpyAsync(node_gid, a_gid, sizeof(int32_t) * n_nodes, cudaMemcpyDeviceToDevice, st));
+  CKN(cudaMemcpyAsync(node_w, a_w, sizeof(int32_t) * n_nodes, cudaMemcpyDeviceToDevice, st));
+  CKN(cudaMemcpyAsync(node_orig, a_orig, n_nodes, cudaMemcpyDeviceToDevice, st));
+  CKN(cudaMemsetAsync(D.flags, 0, NL, st));
+  launch_st_attrs(node_gid, node_w, node_orig, wsum.as<unsigned long long>(), D.flags,
+                  err.as<int>(), st);
+  launch_net_fill(m, d_off, d_pins, d_netw, loc.as<int32_t>(), keep.as<unsigned>(),
+                  net_pos.as<unsigned>(), pin_pos.as<unsigned>(), s_pos.as<unsigned>(),
+                  t_pos.as<unsigned>(), has_s.as<unsigned>(), has_t.as<unsigned>(), tot,
+                  nnet_off, npin, nnet_w, net->net_gid, inc, sms, st);
+  {
+    uint32_t* hp = (uint32_t*)((char*)ctx->pinned_small + 1024);
+    *hp = p_net;
+    CKN(cudaMemcpyAsync(nnet_off + m_net, hp, sizeof(uint32_t), cudaMemcpyHostToDevice, st));
+  }
+  {
+    DevBuf cursor, tmp;
+    CKN(cursor.alloc(sizeof(unsigned) * n_nodes, st));
+    CKN(tmp.alloc(sizeof(int2) * (p_net > 0 ? p_net : 1), st));
+    launch_incidence(n_nodes, m_net, p_net, nnet_off, npin, node_off, cursor.as<unsigned>(), tot,
+                     inc, tmp.as<int2>(), scan_scr.as<unsigned>(), tot + 4, sms, st);
+  }
+  // distances from the original cut
+  if (d_dist) {
+    launch_dist_copy(n_region, d_dist, node_dist, err.as<int>(), st);
+  } else {
+    DevBuf fr, cnt;
+    CKN(fr.alloc(sizeof(int32_t) * 2 * n_nodes, st));
+    CKN(cnt.alloc(sizeof(unsigned) * 2, st));
+    CKN(cudaMemsetAsync(cnt.p, 0, sizeof(unsigned) * 2, st));
+    int32_t* f[2] = {fr.as<int32_t>(), fr.as<int32_t>() + n_nodes};
+    unsigned* c2 = cnt.as<unsigned>();
+    launch_dist_seed(n_nodes, dist_tmp.as<int32_t>(), node_dist, f[0], c2, sms, st);
+    unsigned* hc = (unsigned*)((char*)ctx->pinned_small + 2048);
+    CKN(cudaMemcpyAsync(hc, c2, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    CKN(cudaStreamSynchronize(st));
+    unsigned cur = *hc;
+    for (int d = 1; cur > 0; d++) {
+      int a = (d - 1) & 1, b = d & 1;
+      CKN(cudaMemsetAsync(c2 + b, 0, sizeof(unsigned), st));
+      launch_dist_level(D, f[a], c2 + a, f[b], c2 + b, node_dist, d + 1, cur, sms, st);
+      CKN(cudaMemcpyAsync(hc, c2 + b, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+      CKN(cudaStreamSynchronize(st));
+      cur = *hc;
+    }
+    launch_dist_finish(n_nodes, node_dist, sms, st);
+  }
+  // flow state
+  CKN(cudaMemsetAsync(D.f_in, 0, sizeof(int32_t) * p_net, st));
+  CKN(cudaMemsetAsync(D.f_out, 0, sizeof(int32_t) * p_net, st));
+  CKN(cudaMemsetAsync(D.f_b, 0, sizeof(int32_t) * m_net, st));
+  CKN(cudaMemsetAsync(D.excess, 0, sizeof(long long) * NL, st));
+  CKN(cudaMemsetAsync(D.delta, 0, sizeof(long long) * NL, st));
+  CKN(cudaMemsetAsync(D.stamp, 0, sizeof(uint32_t) * NL, st));
+  CKN(cudaMemsetAsync(D.needrl, 0, NL, st));
+  CKN(cudaMemsetAsync(D.insr, 0, NL, st));
+  {
+    EngineCtl* h = (EngineCtl*)((char*)ctx->pinned_small + 2048 + 64);
+    static_assert(sizeof(EngineCtl) + 2048 + 64 <= 4096, "staging too small");
+    memset(h, 0, sizeof(EngineCtl));
+    h->s.epoch = 1;
+    h->s.state = ST_DONE;
+    CKN(cudaMemcpyAsync(net->E, h, sizeof(EngineCtl), cudaMemcpyHostToDevice, st));
+  }
+  CKN(cudaMemcpyAsync(&hh->err, err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CKN(cudaStreamSynchronize(st));
+  if (hh->err != kDevOk) return done(fail(HFP_ERR_INVALID, "invalid dist_from_cut input"));
+  ctx->params.gr_work = 0;
+  *out = net;
+  return done(rs);
+#undef CKN
+}
+
+HFP_API hfp_status hfp_net_get_info(hfp_net* net, hfp_net_info* info) {
+  if (!net || !info) return fail(HFP_ERR_INVALID, "NULL argument");
+  info->n_nodes = net->d.n_nodes;
+  info->m_nets = net->d.m_nets;
+  info->p_pins = net->d.p_pins;
+  info->lawler_nodes = net->d.NL;
+  info->pad = 0;
+  info->total_weight = net->total_w;
+  return HFP_OK;
+}
+
+HFP_API hfp_status hfp_net_export(hfp_net* net, hfp_mem mem, uint32_t* net_off, int32_t* pins,
+                                  int32_t* net_w, int32_t* net_gid, int32_t* node_w,
+                                  uint32_t* node_off, int32_t* inc_slot, int32_t* dist) {
+  if (!net) return fail(HFP_ERR_INVALID, "net is NULL");
+  hfp_status s = set_device(net->ctx);
+  if (s != HFP_OK) return s;
+  cudaStream_t st = net->ctx->stream;
+  const NetDev& D = net->d;
+  if (net_off && (s = copy_out(net_off, D.net_off, sizeof(uint32_t) * (D.m_nets + 1), mem, st))) return s;
+  if (pins && (s = copy_out(pins, D.pin, sizeof(int32_t) * D.p_pins, mem, st))) return s;
+  if (net_w && (s = copy_out(net_w, D.net_w, sizeof(int32_t) * D.m_nets, mem, st))) return s;
+  if (net_gid && (s = copy_out(net_gid, net->net_gid, sizeof(int32_t) * D.m_nets, mem, st))) return s;
+  if (node_w && (s = copy_out(node_w, D.node_w, sizeof(int32_t) * D.n_nodes, mem, st))) return s;
+  if (node_off && (s = copy_out(node_off, D.node_off, sizeof(uint32_t) * (D.n_nodes + 1), mem, st))) return s;
+  if (dist && (s = copy_out(dist, D.node_dist, sizeof(int32_t) * D.n_nodes, mem, st))) return s;
+  if (inc_slot) {
+    DevBuf tmp;
+    CK(tmp.alloc(sizeof(int32_t) * (D.p_pins > 0 ? D.p_pins : 1), st));
+    launch_inc_slots(D, tmp.as<int32_t>(), net->ctx->sms, st);
+    if ((s = copy_out(inc_slot, tmp.p, sizeof(int32_t) * D.p_pins, mem, st))) return s;
+  }
+  CK(cudaStreamSynchronize(st));
+  return HFP_OK;
+}
+
+HFP_API hfp_status hfp_net_get_stats(hfp_net* net, hfp_stats* out) {
+  if (!net || !out) return fail(HFP_ERR_INVALID, "NULL argument");
+  hfp_status s = set_device(net->ctx);
+  if (s != HFP_OK) return s;
+  Ctl c;
+  if ((s = read_ctl(net, &c)) != HFP_OK) return s;
+  out->rounds = c.rounds;
+  out->global_relabels = c.global_relabels;
+  out->gr_levels = c.gr_levels;
+  out->items_hyper = c.items_hyper;
+  out->items_net = c.items_net;
+  out->node_visits = c.node_visits;
+  out->pushes = c.pushes;
+  out->engine_launches = net->launches;
+  out->engine_ns = net->engine_ns;
+  return HFP_OK;
+}
+
+static void set_gr_work(hfp_net* net) {
+  // global relabel after work linear in the network (Section 8.1): here,
+  // once the frontier and next-list entries processed since the last one
+  // exceed twice the number of Lawler nodes
+  net->ctx->params.gr_work = 2ull * (unsigned long long)net->d.NL + 1024;
+}
+
+HFP_API hfp_status hfp_max_flow(hfp_net* net, int64_t* flow_value) {
+  if (!net) return fail(HFP_ERR_INVALID, "net is NULL");
+  hfp_status s = set_device(net->ctx);
+  if (s != HFP_OK) return s;
+  set_gr_work(net);
+  if ((s = ensure_max_flow(net)) != HFP_OK) return s;
+  Ctl c;
+  if ((s = read_ctl(net, &c)) != HFP_OK) return s;
+  if (flow_value) *flow_value = (int64_t)c.flow;
+  return HFP_OK;
+}
+
+HFP_API hfp_status hfp_min_cut_source_side(hfp_net* net, hfp_mem mem, uint8_t* in_source_lawler,
+                                           uint8_t* in_source_region, int32_t* cut_nets,
+                                           int32_t cap, int32_t* n_cut, int64_t* source_weight) {
+  if (!net) return fail(HFP_ERR_INVALID, "net is NULL");
+  hfp_status s = set_device(net->ctx);
+  if (s != HFP_OK) return s;
+  if (!net->labels_exact) return fail(HFP_ERR_STATE, "hfp_max_flow has not completed");
+  set_gr_work(net);
+  if ((s = ensure_source_side(net)) != HFP_OK) return s;
+  cudaStream_t st = net->ctx->stream;
+  const NetDev& D = net->d;
+  if (in_source_lawler && (s = copy_out(in_source_lawler, D.insr, D.NL, mem, st))) return s;
+  if (in_source_region && net->n_region > 0 &&
+      (s = copy_out(in_source_region, D.insr + 2, net->n_region, mem, st)))
+    return s;
+  hfp_status ret = HFP_OK;
+  if (n_cut || cut_nets) {
+    DevBuf flags, pos, total, scr, outbuf;
+    const unsigned m = (unsigned)D.m_nets;
+    CK(flags.alloc(sizeof(unsigned) * (m ? m : 1), st));
+    CK(pos.alloc(sizeof(unsigned) * (m ? m : 1), st));
+    CK(total.alloc(sizeof(unsigned), st));
+    CK(scr.alloc(sizeof(unsigned) * (scan_scratch_words(m) + 8), st));
+    launch_cut_net_flags(D, flags.as<unsigned>(), net->ctx->sms, st);
+    if (m) CK(cudaMemcpyAsync(pos.p, flags.p, sizeof(unsigned) * m, cudaMemcpyDeviceToDevice, st));
+    scan_exclusive(pos.as<unsigned>(), m, scr.as<unsigned>(), total.as<unsigned>(), st);
+    unsigned* hc = (unsigned*)net->ctx->pinned_small;
+    CK(cudaMemcpyAsync(hc, total.p, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    int32_t nc = (int32_t)*hc;
+    if (n_cut) *n_cut = nc;
+    if (cut_nets && cap > 0) {
+      int32_t* dst = cut_nets;
+      if (mem == HFP_MEM_HOST) {
+        CK(outbuf.alloc(sizeof(int32_t) * cap, st));
+        dst = outbuf.as<int32_t>();
+      }
+      launch_cut_net_compact(D, flags.as<unsigned>(), pos.as<unsigned>(), net->net_gid, dst, cap,
+                             net->ctx->sms, st);
+      if (mem == HFP_MEM_HOST)
+        CK(cudaMemcpyAsync(cut_nets, dst, sizeof(int32_t) * (nc < cap ? nc : cap),
+                           cudaMemcpyDeviceToHost, st));
+    }
+    if (nc > cap && cut_nets) ret = fail(HFP_ERR_BUFFER_TOO_SMALL, "cut_nets needs %d entries", nc);
+  }
+  Ctl c;
+  if ((s = read_ctl(net, &c)) != HFP_OK) return s;
+  if (source_weight) *source_weight = c.wS;
+  return ret;
+}
+
+HFP_API hfp_status hfp_min_cut_sink_side(hfp_net* net, hfp_mem mem, uint8_t* in_sink_lawler,
+                                         uint8_t* in_sink_region, int64_t* sink_weight) {
+  if (!net) return fail(HFP_ERR_INVALID, "net is NULL");
+  hfp_status s = set_device(net->ctx);
+  if (s != HFP_OK) return s;
+  if (!net->labels_exact) return fail(HFP_ERR_STATE, "hfp_max_flow has not completed");
+  cudaStream_t st = net->ctx->stream;
+  const NetDev& D = net->d;
+  if (in_sink_lawler || in_sink_region) {
+    DevBuf tmp;
+    CK(tmp.alloc(D.NL, st));
+    launch_lawler_sink_side(D, tmp.as<uint8_t>(), net->ctx->sms, st);
+    if (in_sink_lawler && (s = copy_out(in_sink_lawler, tmp.p, D.NL, mem, st))) return s;
+    if (in_sink_region && net->n_region > 0 &&
+        (s = copy_out(in_sink_region, tmp.as<uint8_t>() + 2, net->n_region, mem, st)))
+      return s;
+  }
+  Ctl c;
+  if ((s = read_ctl(net, &c)) != HFP_OK) return s;
+  if (sink_weight) *sink_weight = c.wT;
+  return HFP_OK;
+}
+
+namespace {
+
+// Piercing-node selection by the rule of Section 7 (see hfp_flowcutter).
+hfp_status select_pierce(hfp_net* net, int grow_s, const hfp_fc_params* prm, int32_t* node) {
+  Ctl c;
+  hfp_status s = read_ctl(net, &c);
+  if (s != HFP_OK) return s;
+  const long long w_reach = grow_s ? c.wS : c.wT;
+  launch_pierce_select(net->d, net->E, grow_s, prm->max_block_weight, w_reach, prm->seed,
+                       net->ctx->sms, net->ctx->stream);
+  if ((s = read_ctl(net, &c)) != HFP_OK) return s;
+  if (c.best_key == 0 || c.best_node < 0) {
+    *node = -1;
+    return fail(HFP_NO_BALANCED_CUT, "no piercing candidate");
+  }
+  *node = c.best_node;
+  return HFP_OK;
+}
+
+hfp_status pierce(hfp_net* net, int side, const int32_t* nodes, int32_t count) {
+  hfp_status s = stage_nodes(net, nodes, count);
+  if (s != HFP_OK) return s;
+  cudaStream_t st = net->ctx->stream;
+  if (side == 0) {
+    // S <- S_r + nodes; labels stay valid, the new excess is the frontier
+    launch_mark_sources(net->d, net->dev_nodes, count, net->ctx->sms, st);
+    launch_engine_setup(net->E, SETUP_PREP, st);
+    launch_saturate(net->d, net->E, net->dev_nodes, count, st);
+    launch_engine_setup(net->E, SETUP_ROUND, st);
+  } else {
+    // T <- T_r + nodes; labels are no longer lower bounds: relabel globally
+    launch_mark_sinks(net->d, net->E, net->dev_nodes, count, net->ctx->sms, st);
+    launch_engine_setup(net->E, SETUP_GR, st);
+  }
+  net->labels_exact = false;
+  net->sr_valid = false;
+  if ((s = run_engine(net)) != HFP_OK) return s;
+  net->labels_exact = true;
+  return HFP_OK;
+}
+
+}  // namespace
+
+HFP_API hfp_status hfp_pierce_and_augment(hfp_net* net, int32_t side, const int32_t* nodes,
+                                          int32_t count, const hfp_fc_params* params,
+                                          int32_t* pierced, int64_t* flow_value) {
+  if (!net) return fail(HFP_ERR_INVALID, "net is NULL");
+  if (side != 0 && side != 1) return fail(HFP_ERR_INVALID, "side must be 0 or 1");
+  if (nodes && count <= 0) return fail(HFP_ERR_INVALID, "count must be positive");
+  hfp_status s = set_device(net->ctx);
+  if (s != HFP_OK) return s;
+  set_gr_work(net);
+  if (!net->labels_exact) return fail(HFP_ERR_STATE, "hfp_max_flow has not completed");
+  if ((s = ensure_source_side(net)) != HFP_OK) return s;
+  int32_t chosen = -1;
+  if (!nodes) {
+    if (!params) return fail(HFP_ERR_INVALID, "params needed to select a piercing node");
+    if ((s = select_pierce(net, side == 0, params, &chosen)) != HFP_OK) return s;
+    nodes = &chosen;
+    count = 1;
+  }
+  if (pierced) *pierced = nodes[0];
+  if ((s = pierce(net, side, nodes, count)) != HFP_OK) return s;
+  Ctl c;
+  if ((s = read_ctl(net, &c)) != HFP_OK) return s;
+  if (flow_value) *flow_value = (int64_t)c.flow;
+  return HFP_OK;
+}
+
+HFP_API hfp_status hfp_flowcutter(hfp_net* net, const hfp_fc_params* prm, uint8_t* final_side,
+                                  int32_t* pierce_side, int32_t* pierce_node, int32_t pierce_cap,
+                                  hfp_fc_result* result) {
+  if (!net || !prm) return fail(HFP_ERR_INVALID, "NULL argument");
+  hfp_status s = set_device(net->ctx);
+  if (s != HFP_OK) return s;
+  set_gr_work(net);
+  cudaStream_t st = net->ctx->stream;
+  const int64_t W = net->total_w, L = prm->max_block_weight;
+  const int32_t max_it = prm->max_iterations > 0 ? prm->max_iterations : net->d.n_nodes + 1;
+  hfp_fc_result r{};
+  int32_t np = 0, it = 0;
+  hfp_status status = HFP_OK;
+  if ((s = ensure_max_flow(net)) != HFP_OK) return s;
+  it = 1;
+  for (;;) {
+    if ((s = ensure_source_side(net)) != HFP_OK) return s;
+    Ctl c;
+    if ((s = read_ctl(net, &c)) != HFP_OK) return s;
+    r.flow = (int64_t)c.flow;
+    if (prm->flow_bound >= 0 && (int64_t)c.flow > prm->flow_bound) {
+      status = fail(HFP_ABORTED_WORSE, "flow %lld exceeds bound %lld", (long long)c.flow,
+                    (long long)prm->flow_bound);
+      break;
+    }
+    const int64_t wS = c.wS, wT = c.wT;
+    const bool balS = wS <= L && W - wS <= L;
+    const bool balT = wT <= L && W - wT <= L;
+    if (balS || balT) {
+      bool use_t;
+      if (balS && balT) {
+        int64_t mS = wS > W - wS ? wS : W - wS;
+        int64_t mT = wT > W - wT ? wT : W - wT;
+        use_t = mT < mS;
+      } else {
+        use_t = !balS;
+      }
+      r.result_side = use_t ? 1 : 0;
+      r.source_weight = use_t ? W - wT : wS;
+      if (final_side && net->n_region > 0) {
+        DevBuf tmp;
+        CK(tmp.alloc(net->n_region, st));
+        launch_region_side(net->d, use_t ? 1 : 0, net->n_region, tmp.as<uint8_t>(), net->ctx->sms,
+                           st);
+        CK(cudaMemcpyAsync(final_side, tmp.p, net->n_region, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+      }
+      break;
+    }
+    if (it >= max_it) {
+      status = fail(HFP_ERR_ITER_LIMIT, "FlowCutter iteration limit %d reached", max_it);
+      break;
+    }
+    const int grow_s = wS <= wT;
+    int32_t p = -1;
+    if ((s = select_pierce(net, grow_s, prm, &p)) != HFP_OK) {
+      status = s;
+      break;
+    }
+    if (pierce_side && np < pierce_cap) pierce_side[np] = grow_s ? 0 : 1;
+    if (pierce_node && np < pierce_cap) pierce_node[np] = p;
+    np++;
+    if ((s = pierce(net, grow_s ? 0 : 1, &p, 1)) != HFP_OK) return s;
+    it++;
+  }
+  r.iterations = it;
+  r.n_pierced = np;
+  if (result) *result = r;
+  if (status == HFP_OK && (pierce_side || pierce_node) && np > pierce_cap)
+    status = fail(HFP_ERR_BUFFER_TOO_SMALL, "piercing sequence has %d entries", np);
+  return status;
+}

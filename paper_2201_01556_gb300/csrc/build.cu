@@ -1,0 +1,508 @@
+// Flow network construction on the device (Section 6, "Construction
+// Algorithms", first algorithm: a scan over the nets of H with prefix sums to
+// place the pin lists, as in the paper's parallel version).
+//
+// Pass 1 (warp per net): count region pins, note whether the net has a pin
+//   outside B on side 0 (adds s) / side 1 (adds t), decide whether it stays
+//   (>= 2 pins, not both s and t), and mark region pins of nets with pins on
+//   both sides (distance 1 from the original cut).
+// Scans: kept-net index, pin offsets, positions in the incidence lists of s
+//   and t.
+// Pass 2 (warp per kept net): copy region pins in H's order by ballot
+//   compaction, then s, then t; the s / t incidences go straight to their
+//   scanned positions.
+// Incidence of region vertices: count, scan, scatter, then a per-vertex rank
+//   sort by pin slot so every list is in ascending slot order (deterministic).
+#include "kernels.cuh"
+
+namespace hfp {
+
+constexpr unsigned FULLB = 0xffffffffu;
+
+// ---------------------------------------------------------------------------
+// exclusive scan of uint32 (three passes: tile sums, scan of tile sums, add)
+constexpr int kScanThreads = 512;
+constexpr int kScanItems = 4;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+__device__ __forceinline__ unsigned block_excl_scan(unsigned v, unsigned* total) {
+  __shared__ unsigned warp_tot[kScanThreads / 32];
+  const unsigned lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  unsigned x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    unsigned t = __shfl_up_sync(FULLB, x, o);
+    if ((int)lane >= o) x += t;
+  }
+  if (lane == 31) warp_tot[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    unsigned w = lane < (blockDim.x >> 5) ? warp_tot[lane] : 0;
+    unsigned y = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      unsigned t = __shfl_up_sync(FULLB, y, o);
+      if ((int)lane >= o) y += t;
+    }
+    if (lane < (blockDim.x >> 5)) warp_tot[lane] = y - w;
+    if (lane == (blockDim.x >> 5) - 1) *total = y;
+  }
+  __syncthreads();
+  unsigned r = x - v + warp_tot[wid];
+  __syncthreads();
+  return r;
+}
+
+__global__ void k_scan_tiles(unsigned* a, unsigned n, unsigned* tile_sums) {
+  __shared__ unsigned tot;
+  unsigned base = blockIdx.x * kScanTile + threadIdx.x * kScanItems;
+  unsigned v[kScanItems], s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; k++) {
+    v[k] = (base + k < n) ? a[base + k] : 0;
+    s += v[k];
+  }
+  unsigned off = block_excl_scan(s, &tot);
+#pragma unroll
+  for (int k = 0; k < kScanItems; k++) {
+    if (base + k < n) a[base + k] = off;
+    off += v[k];
+  }
+  if (threadIdx.x == 0) tile_sums[blockIdx.x] = tot;
+}
+
+__global__ void k_scan_sums(unsigned* sums, unsigned ntiles, unsigned* total) {
+  __shared__ unsigned tot;
+  unsigned carry = 0;
+  for (unsigned b = 0; b < ntiles; b += kScanThreads) {
+    unsigned i = b + threadIdx.x;
+    unsigned v = i < ntiles ? sums[i] : 0;
+    unsigned off = block_excl_scan(v, &tot);
+    if (i < ntiles) sums[i] = off + carry;
+    carry += tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *total = carry;
+}
+
+__global__ void k_scan_add(unsigned* a, unsigned n, const unsigned* sums) {
+  unsigned add = sums[blockIdx.x];
+  unsigned base = blockIdx.x * kScanTile;
+  for (unsigned k = threadIdx.x; k < kScanTile; k += blockDim.x)
+    if (base + k < n) a[base + k] += add;
+}
+
+size_t scan_scratch_words(unsigned n) { return (n + kScanTile - 1) / kScanTile + 1; }
+
+// In-place exclusive scan of a[0, n); the total goes to *total (device).
+void scan_exclusive(unsigned* a, unsigned n, unsigned* scratch, unsigned* total, cudaStream_t st) {
+  unsigned tiles = (n + kScanTile - 1) / kScanTile;
+  if (tiles == 0) {
+    cudaMemsetAsync(total, 0, sizeof(unsigned), st);
+    return;
+  }
+  k_scan_tiles<<<tiles, kScanThreads, 0, st>>>(a, n, scratch);
+  count_launches(1);
+  k_scan_sums<<<1, kScanThreads, 0, st>>>(scratch, tiles, total);
+  count_launches(1);
+  k_scan_add<<<tiles, 256, 0, st>>>(a, n, scratch);
+  count_launches(1);
+}
+
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void set_err(int* err, int code) { atomicCAS(err, kDevOk, code); }
+
+// region vertex -> local id 2 + i; per-hypernode attributes of the region
+__global__ void k_region_map(int32_t n, int32_t n_region, const int32_t* region,
+                             const int32_t* side, const int32_t* node_w_h, int32_t* loc,
+                             int32_t* node_gid, int32_t* node_w, int8_t* node_orig, int* err) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_region) return;
+  int v = region[i];
+  if (v < 0 || v >= n) { set_err(err, kDevBadInput); return; }
+  int sd = side[v];
+  if (sd != 0 && sd != 1) { set_err(err, kDevBadInput); return; }
+  if (atomicExch(&loc[v], 2 + i) != -1) { set_err(err, kDevBadInput); return; }
+  int c = node_w_h ? node_w_h[v] : 1;
+  if (c <= 0) set_err(err, kDevBadInput);
+  node_gid[2 + i] = v;
+  node_w[2 + i] = c;
+  node_orig[2 + i] = (int8_t)sd;
+}
+
+// contracted weights of s and t, and the total weight check
+__global__ void k_st_weight(int32_t n, const int32_t* loc, const int32_t* side,
+                            const int32_t* node_w_h, unsigned long long* wsum, int* err) {
+  __shared__ unsigned long long sh[3];
+  if (threadIdx.x < 3) sh[threadIdx.x] = 0;
+  __syncthreads();
+  unsigned long long a0 = 0, a1 = 0, at = 0;
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+    int c = node_w_h ? node_w_h[v] : 1;
+    if (c <= 0) set_err(err, kDevBadInput);
+    at += (unsigned long long)(c > 0 ? c : 0);
+    if (loc[v] < 0) {
+      int sd = side[v];
+      if (sd == 0) a0 += c;
+      else if (sd == 1) a1 += c;
+    }
+  }
+  if (a0) atomicAdd(&sh[0], a0);
+  if (a1) atomicAdd(&sh[1], a1);
+  if (at) atomicAdd(&sh[2], at);
+  __syncthreads();
+  if (threadIdx.x < 3 && sh[threadIdx.x]) atomicAdd(&wsum[threadIdx.x], sh[threadIdx.x]);
+}
+
+// pass 1, warp per net of H
+__global__ void k_net_scan(int32_t n, int32_t m, const uint32_t* net_off, const int32_t* pins,
+                           const int32_t* net_w, const int32_t* side, const int32_t* loc,
+                           unsigned* keep, unsigned* size, unsigned* has_s, unsigned* has_t,
+                           int32_t* dist_tmp, int mark_dist, unsigned long long* wnet, int* err) {
+  const unsigned lane = threadIdx.x & 31;
+  const unsigned gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const unsigned nw = (gridDim.x * blockDim.x) >> 5;
+  unsigned long long wacc = 0;
+  for (unsigned e = gw; e < (unsigned)m; e += nw) {
+    const unsigned beg = net_off[e], end = net_off[e + 1];
+    if (end < beg) { set_err(err, kDevBadInput); continue; }
+    unsigned cnt = 0;
+    bool hs = false, ht = false, s0 = false, s1 = false;
+    for (unsigned j0 = beg; j0 < end; j0 += 32) {
+      unsigned j = j0 + lane;
+      bool reg = false, os = false, ot = false, a0 = false, a1 = false;
+      if (j < end) {
+        int v = pins[j];
+        if (v < 0 || v >= n) {
+          set_err(err, kDevBadInput);
+        } else {
+          int sd = side[v];
+          a0 = sd == 0;
+          a1 = sd == 1;
+          reg = loc[v] >= 0;
+          os = !reg && a0;
+          ot = !reg && a1;
+        }
+      }
+      cnt += __popc(__ballot_sync(FULLB, reg));
+      hs |= __any_sync(FULLB, os);
+      ht |= __any_sync(FULLB, ot);
+      s0 |= __any_sync(FULLB, a0);
+      s1 |= __any_sync(FULLB, a1);
+    }
+    const unsigned tot = cnt + hs + ht;
+    const bool k = tot >= 2 && !(hs && ht);
+    if (lane == 0) {
+      int w = net_w[e];
+      if (w <= 0) set_err(err, kDevBadInput);
+      wacc += (unsigned long long)(w > 0 ? w : 0);
+      keep[e] = k;
+      size[e] = k ? tot : 0;
+      has_s[e] = k && hs;
+      has_t[e] = k && ht;
+    }
+    if (mark_dist && s0 && s1) {
+      // region pins of a net with pins on both sides: distance 1
+      for (unsigned j = beg + lane; j < end; j += 32) {
+        int v = pins[j];
+        if (v >= 0 && v < n) {
+          int l = loc[v];
+          if (l >= 0) dist_tmp[l] = 1;
+        }
+      }
+    }
+  }
+  if (lane == 0 && wacc) atomicAdd(wnet, wacc);
+}
+
+// pass 2, warp per net of H that is kept
+__global__ void k_net_fill(int32_t m, const uint32_t* net_off, const int32_t* pins,
+                           const int32_t* net_w, const int32_t* loc, const unsigned* keep,
+                           const unsigned* net_pos, const unsigned* pin_pos,
+                           const unsigned* s_pos, const unsigned* t_pos,
+                           const unsigned* has_s_flag, const unsigned* has_t_flag,
+                           const unsigned* totals, uint32_t* nnet_off, int32_t* npin,
+                           int32_t* nnet_w, int32_t* nnet_gid, int2* inc) {
+  const unsigned lane = threadIdx.x & 31;
+  const unsigned gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const unsigned nw = (gridDim.x * blockDim.x) >> 5;
+  const unsigned deg_s = totals[2];
+  for (unsigned e = gw; e < (unsigned)m; e += nw) {
+    if (!keep[e]) continue;
+    const unsigned beg = net_off[e], end = net_off[e + 1];
+    const unsigned ep = net_pos[e];
+    unsigned out = pin_pos[e];
+    if (lane == 0) {
+      nnet_off[ep] = out;
+      nnet_w[ep] = net_w[e];
+      nnet_gid[ep] = (int32_t)e;
+    }
+    for (unsigned j0 = beg; j0 < end; j0 += 32) {
+      unsigned j = j0 + lane;
+      int l = -1;
+      if (j < end) l = loc[pins[j]];
+      unsigned mask = __ballot_sync(FULLB, l >= 0);
+      if (l >= 0) npin[out + __popc(mask & ((1u << lane) - 1u))] = l;
+      out += __popc(mask);
+    }
+    if (lane == 0) {
+      if (has_s_flag[e]) {
+        npin[out] = 0;
+        inc[s_pos[e]] = make_int2((int)ep, (int)out);
+        out++;
+      }
+      if (has_t_flag[e]) {
+        npin[out] = 1;
+        inc[deg_s + t_pos[e]] = make_int2((int)ep, (int)out);
+        out++;
+      }
+    }
+  }
+}
+
+// incidence degrees of region hypernodes (s and t come from the scans)
+__global__ void k_region_deg(const int32_t* npin, unsigned p, unsigned* deg) {
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < p; i += gridDim.x * blockDim.x) {
+    int u = npin[i];
+    if (u >= 2) atomicAdd(&deg[u], 1u);
+  }
+}
+
+__global__ void k_set_st_deg(unsigned* deg, const unsigned* totals) {
+  deg[0] = totals[2];
+  deg[1] = totals[3];
+}
+
+// warp per kept net: scatter region incidences (order fixed by the sort below)
+__global__ void k_region_inc(int32_t m_net, const uint32_t* nnet_off, const int32_t* npin,
+                             const unsigned* node_off, unsigned* cursor, int2* inc) {
+  const unsigned lane = threadIdx.x & 31;
+  const unsigned gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const unsigned nw = (gridDim.x * blockDim.x) >> 5;
+  for (unsigned e = gw; e < (unsigned)m_net; e += nw) {
+    for (unsigned p = nnet_off[e] + lane; p < nnet_off[e + 1]; p += 32) {
+      int u = npin[p];
+      if (u >= 2) inc[node_off[u] + atomicAdd(&cursor[u], 1u)] = make_int2((int)e, (int)p);
+    }
+  }
+}
+
+// warp per region hypernode: sort its incidences by pin slot (rank sort;
+// slots are distinct).  Lists longer than 32 go through tmp.
+__global__ void k_inc_sort(int32_t n_nodes, const unsigned* node_off, int2* inc, int2* tmp) {
+  const unsigned lane = threadIdx.x & 31;
+  const unsigned gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const unsigned nw = (gridDim.x * blockDim.x) >> 5;
+  for (unsigned u = 2 + gw; u < (unsigned)n_nodes; u += nw) {
+    const unsigned beg = node_off[u], end = node_off[u + 1], d = end - beg;
+    if (d <= 1) continue;
+    if (d <= 32) {
+      int2 mine = lane < d ? inc[beg + lane] : make_int2(0, 0x7fffffff);
+      unsigned rank = 0;
+      for (unsigned k = 0; k < d; k++) {
+        int sk = __shfl_sync(FULLB, mine.y, k);
+        rank += (sk < mine.y);
+      }
+      __syncwarp();
+      if (lane < d) inc[beg + rank] = mine;
+    } else {
+      for (unsigned i = lane; i < d; i += 32) {
+        int2 mine = inc[beg + i];
+        unsigned rank = 0;
+        for (unsigned k = 0; k < d; k++) rank += (inc[beg + k].y < mine.y);
+        tmp[beg + rank] = mine;
+      }
+      __syncwarp();
+      for (unsigned i = lane; i < d; i += 32) inc[beg + i] = tmp[beg + i];
+    }
+  }
+}
+
+// distance BFS inside the region: warp per frontier hypernode
+__global__ void k_dist_level(const NetDev N, const int32_t* front, const unsigned* fcnt,
+                             int32_t* next, unsigned* ncnt, int32_t* dist, int d1) {
+  const unsigned lane = threadIdx.x & 31;
+  const unsigned gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const unsigned nw = (gridDim.x * blockDim.x) >> 5;
+  const unsigned cnt = *fcnt;
+  for (unsigned w = gw; w < cnt; w += nw) {
+    const int u = front[w];
+    for (unsigned j = N.node_off[u]; j < N.node_off[u + 1]; j++) {
+      const int e = N.inc[j].x;
+      const unsigned beg = N.net_off[e], end = N.net_off[e + 1];
+      for (unsigned p0 = beg; p0 < end; p0 += 32) {
+        const unsigned p = p0 + lane;
+        bool claim = false;
+        int v = -1;
+        if (p < end) {
+          v = N.pin[p];
+          if (v >= 2 && dist[v] < 0) claim = atomicCAS(&dist[v], -1, d1) == -1;
+        }
+        warp_append(claim, v, next, ncnt);
+      }
+    }
+  }
+}
+
+__global__ void k_dist_seed(int32_t n_nodes, const int32_t* dist_tmp, int32_t* dist,
+                            int32_t* front, unsigned* fcnt) {
+  const unsigned lane = threadIdx.x & 31;
+  const unsigned tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+  for (unsigned u0 = tid - lane; u0 < (unsigned)n_nodes; u0 += nth) {
+    unsigned u = u0 + lane;
+    bool seed = false;
+    if (u < (unsigned)n_nodes) {
+      if (u < 2) {
+        dist[u] = 0;
+      } else {
+        seed = dist_tmp[u - 2] == 1;
+        dist[u] = seed ? 1 : -1;
+      }
+    }
+    warp_append(seed, (int)u, front, fcnt);
+  }
+}
+
+__global__ void k_dist_finish(int32_t n_nodes, int32_t* dist) {
+  for (int u = 2 + blockIdx.x * blockDim.x + threadIdx.x; u < n_nodes; u += gridDim.x * blockDim.x) {
+    int d = dist[u];
+    dist[u] = (d < 0 || d > kDistFar) ? kDistFar : d;
+  }
+}
+
+__global__ void k_dist_copy(int32_t n_region, const int32_t* dist_in, int32_t* dist, int* err) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) {
+    dist[0] = 0;
+    dist[1] = 0;
+  }
+  if (i < n_region) {
+    int d = dist_in[i];
+    if (d < 0) set_err(err, kDevBadInput);
+    dist[2 + i] = d > kDistFar ? kDistFar : d;
+  }
+}
+
+__global__ void k_st_attrs(int32_t* node_gid, int32_t* node_w, int8_t* node_orig,
+                           const unsigned long long* wsum, uint8_t* flags, int* err) {
+  node_gid[0] = -1;
+  node_gid[1] = -1;
+  node_w[0] = (int32_t)wsum[0];
+  node_w[1] = (int32_t)wsum[1];
+  node_orig[0] = 0;
+  node_orig[1] = 1;
+  flags[0] = kSource;
+  flags[1] = kSink;
+  if (wsum[2] >= (1ull << 31)) set_err(err, kDevBadInput);
+}
+
+// ---------------------------------------------------------------------------
+// host launchers
+static inline unsigned blocks_for(unsigned long long work, unsigned per_block, unsigned cap) {
+  unsigned long long b = (work + per_block - 1) / per_block;
+  if (b < 1) b = 1;
+  if (b > cap) b = cap;
+  return (unsigned)b;
+}
+
+void launch_region_map(int32_t n, int32_t n_region, const int32_t* region, const int32_t* side,
+                       const int32_t* node_w_h, int32_t* loc, int32_t* node_gid, int32_t* node_w,
+                       int8_t* node_orig, int* err, cudaStream_t st) {
+  if (n_region > 0) {
+    k_region_map<<<(n_region + 255) / 256, 256, 0, st>>>(n, n_region, region, side, node_w_h, loc,
+                                                        node_gid, node_w, node_orig, err);
+    count_launches(1);
+  }
+}
+
+void launch_st_weight(int32_t n, const int32_t* loc, const int32_t* side, const int32_t* node_w_h,
+                      unsigned long long* wsum, int* err, int sms, cudaStream_t st) {
+  k_st_weight<<<blocks_for(n, 256, sms * 8), 256, 0, st>>>(n, loc, side, node_w_h, wsum, err);
+  count_launches(1);
+}
+
+void launch_net_scan(int32_t n, int32_t m, const uint32_t* net_off, const int32_t* pins,
+                     const int32_t* net_w, const int32_t* side, const int32_t* loc,
+                     unsigned* keep, unsigned* size, unsigned* has_s, unsigned* has_t,
+                     int32_t* dist_tmp, int mark_dist, unsigned long long* wnet, int* err,
+                     int sms, cudaStream_t st) {
+  if (m > 0) {
+    k_net_scan<<<blocks_for((unsigned long long)m * 32, 256, sms * 16), 256, 0, st>>>(
+        n, m, net_off, pins, net_w, side, loc, keep, size, has_s, has_t, dist_tmp, mark_dist,
+        wnet, err);
+    count_launches(1);
+  }
+}
+
+void launch_net_fill(int32_t m, const uint32_t* net_off, const int32_t* pins,
+                     const int32_t* net_w, const int32_t* loc, const unsigned* keep,
+                     const unsigned* net_pos, const unsigned* pin_pos, const unsigned* s_pos,
+                     const unsigned* t_pos, const unsigned* has_s, const unsigned* has_t,
+                     const unsigned* totals, uint32_t* nnet_off, int32_t* npin, int32_t* nnet_w,
+                     int32_t* nnet_gid, int2* inc, int sms, cudaStream_t st) {
+  if (m > 0) {
+    k_net_fill<<<blocks_for((unsigned long long)m * 32, 256, sms * 16), 256, 0, st>>>(
+        m, net_off, pins, net_w, loc, keep, net_pos, pin_pos, s_pos, t_pos, has_s, has_t, totals,
+        nnet_off, npin, nnet_w, nnet_gid, inc);
+    count_launches(1);
+  }
+}
+
+void launch_incidence(int32_t n_nodes, int32_t m_net, unsigned p, const uint32_t* nnet_off,
+                      const int32_t* npin, unsigned* deg_then_off, unsigned* cursor,
+                      const unsigned* totals, int2* inc, int2* tmp, unsigned* scan_scratch,
+                      unsigned* scan_total, int sms, cudaStream_t st) {
+  cudaMemsetAsync(deg_then_off, 0, sizeof(unsigned) * (n_nodes + 1), st);
+  if (p > 0) {
+    k_region_deg<<<blocks_for(p, 256, sms * 8), 256, 0, st>>>(npin, p, deg_then_off);
+    count_launches(1);
+  }
+  k_set_st_deg<<<1, 1, 0, st>>>(deg_then_off, totals);
+  count_launches(1);
+  scan_exclusive(deg_then_off, n_nodes + 1, scan_scratch, scan_total, st);
+  cudaMemsetAsync(cursor, 0, sizeof(unsigned) * n_nodes, st);
+  if (m_net > 0) {
+    k_region_inc<<<blocks_for((unsigned long long)m_net * 32, 256, sms * 16), 256, 0, st>>>(
+        m_net, nnet_off, npin, deg_then_off, cursor, inc);
+    count_launches(1);
+  }
+  if (n_nodes > 2) {
+    k_inc_sort<<<blocks_for((unsigned long long)n_nodes * 32, 256, sms * 16), 256, 0, st>>>(
+        n_nodes, deg_then_off, inc, tmp);
+    count_launches(1);
+  }
+}
+
+void launch_dist_seed(int32_t n_nodes, const int32_t* dist_tmp, int32_t* dist, int32_t* front,
+                      unsigned* fcnt, int sms, cudaStream_t st) {
+  k_dist_seed<<<blocks_for(n_nodes, 256, sms * 8), 256, 0, st>>>(n_nodes, dist_tmp, dist, front,
+                                                                 fcnt);
+  count_launches(1);
+}
+
+void launch_dist_level(const NetDev& N, const int32_t* front, const unsigned* fcnt, int32_t* next,
+                       unsigned* ncnt, int32_t* dist, int d1, unsigned host_cnt, int sms,
+                       cudaStream_t st) {
+  k_dist_level<<<blocks_for((unsigned long long)host_cnt * 32, 256, sms * 16), 256, 0, st>>>(
+      N, front, fcnt, next, ncnt, dist, d1);
+  count_launches(1);
+}
+
+void launch_dist_finish(int32_t n_nodes, int32_t* dist, int sms, cudaStream_t st) {
+  k_dist_finish<<<blocks_for(n_nodes, 256, sms * 8), 256, 0, st>>>(n_nodes, dist);
+  count_launches(1);
+}
+
+void launch_dist_copy(int32_t n_region, const int32_t* dist_in, int32_t* dist, int* err,
+                      cudaStream_t st) {
+  k_dist_copy<<<(n_region + 2 + 255) / 256, 256, 0, st>>>(n_region, dist_in, dist, err);
+  count_launches(1);
+}
+
+void launch_st_attrs(int32_t* node_gid, int32_t* node_w, int8_t* node_orig,
+                     const unsigned long long* wsum, uint8_t* flags, int* err, cudaStream_t st) {
+  k_st_attrs<<<1, 1, 0, st>>>(node_gid, node_w, node_orig, wsum, flags, err);
+  count_launches(1);
+}
+
+}  // namespace hfp

@@ -1,0 +1,71 @@
+// Host-side launchers of the device kernels, shared by the translation units.
+#pragma once
+#include "engine.cuh"
+
+namespace hfp {
+
+constexpr int32_t kDistFar = (1 << 20) - 1;
+
+// launches of this library's kernels (process-wide, host side)
+void count_launches(unsigned k);
+unsigned long long launches_total();
+
+// build.cu
+size_t scan_scratch_words(unsigned n);
+void scan_exclusive(unsigned* a, unsigned n, unsigned* scratch, unsigned* total, cudaStream_t st);
+void launch_region_map(int32_t n, int32_t n_region, const int32_t* region, const int32_t* side,
+                       const int32_t* node_w_h, int32_t* loc, int32_t* node_gid, int32_t* node_w,
+                       int8_t* node_orig, int* err, cudaStream_t st);
+void launch_st_weight(int32_t n, const int32_t* loc, const int32_t* side, const int32_t* node_w_h,
+                      unsigned long long* wsum, int* err, int sms, cudaStream_t st);
+void launch_net_scan(int32_t n, int32_t m, const uint32_t* net_off, const int32_t* pins,
+                     const int32_t* net_w, const int32_t* side, const int32_t* loc,
+                     unsigned* keep, unsigned* size, unsigned* has_s, unsigned* has_t,
+                     int32_t* dist_tmp, int mark_dist, unsigned long long* wnet, int* err,
+                     int sms, cudaStream_t st);
+void launch_net_fill(int32_t m, const uint32_t* net_off, const int32_t* pins,
+                     const int32_t* net_w, const int32_t* loc, const unsigned* keep,
+                     const unsigned* net_pos, const unsigned* pin_pos, const unsigned* s_pos,
+                     const unsigned* t_pos, const unsigned* has_s, const unsigned* has_t,
+                     const unsigned* totals, uint32_t* nnet_off, int32_t* npin, int32_t* nnet_w,
+                     int32_t* nnet_gid, int2* inc, int sms, cudaStream_t st);
+void launch_incidence(int32_t n_nodes, int32_t m_net, unsigned p, const uint32_t* nnet_off,
+                      const int32_t* npin, unsigned* deg_then_off, unsigned* cursor,
+                      const unsigned* totals, int2* inc, int2* tmp, unsigned* scan_scratch,
+                      unsigned* scan_total, int sms, cudaStream_t st);
+void launch_dist_seed(int32_t n_nodes, const int32_t* dist_tmp, int32_t* dist, int32_t* front,
+                      unsigned* fcnt, int sms, cudaStream_t st);
+void launch_dist_level(const NetDev& N, const int32_t* front, const unsigned* fcnt, int32_t* next,
+                       unsigned* ncnt, int32_t* dist, int d1, unsigned host_cnt, int sms,
+                       cudaStream_t st);
+void launch_dist_finish(int32_t n_nodes, int32_t* dist, int sms, cudaStream_t st);
+void launch_dist_copy(int32_t n_region, const int32_t* dist_in, int32_t* dist, int* err,
+                      cudaStream_t st);
+void launch_st_attrs(int32_t* node_gid, int32_t* node_w, int8_t* node_orig,
+                     const unsigned long long* wsum, uint8_t* flags, int* err, cudaStream_t st);
+
+// engine.cu
+constexpr int kEngineThreads = 512;
+__global__ void __launch_bounds__(kEngineThreads) engine_kernel(NetDev N, EngineCtl* E, Params P);
+
+// cuts.cu
+enum SetupMode : int { SETUP_GR = 0, SETUP_ROUND = 1, SETUP_SR = 2, SETUP_PREP = 3 };
+void launch_engine_setup(EngineCtl* E, int mode, cudaStream_t st);
+void launch_saturate(const NetDev& N, EngineCtl* E, const int32_t* nodes, int32_t count,
+                     cudaStream_t st);
+void launch_mark_sources(const NetDev& N, const int32_t* extra, int32_t count, int sms,
+                         cudaStream_t st);
+void launch_mark_sinks(const NetDev& N, EngineCtl* E, const int32_t* extra, int32_t count,
+                       int sms, cudaStream_t st);
+void launch_pierce_select(const NetDev& N, EngineCtl* E, int grow_s, long long max_w,
+                          long long w_reach, uint32_t seed, int sms, cudaStream_t st);
+void launch_region_side(const NetDev& N, int use_t, int32_t n_region, uint8_t* out, int sms,
+                        cudaStream_t st);
+void launch_lawler_sink_side(const NetDev& N, uint8_t* out, int sms, cudaStream_t st);
+void launch_cut_net_flags(const NetDev& N, unsigned* flags, int sms, cudaStream_t st);
+void launch_cut_net_compact(const NetDev& N, const unsigned* flags, const unsigned* pos,
+                            const int32_t* net_gid, int32_t* out, int32_t cap, int sms,
+                            cudaStream_t st);
+void launch_inc_slots(const NetDev& N, int32_t* out, int sms, cudaStream_t st);
+
+}  // namespace hfp

@@ -1,0 +1,311 @@
+"""Python binding of libhfp (include/hfp.h): argument marshalling only.
+
+Every function here maps one-to-one onto a C entry point of the same name
+(``build_flow_network`` -> ``hfp_build_flow_network`` ...).  Inputs are numpy
+arrays (host memory) or CUDA torch tensors (device memory); outputs are
+numpy arrays unless a device output is requested.  There is no fallback: if
+libhfp.so cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _build
+
+OK = 0
+ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_ITER_LIMIT = -1, -2, -3, -4
+NO_BALANCED_CUT, ABORTED_WORSE, ERR_BUFFER_TOO_SMALL, ERR_STATE = -5, -6, -7, -8
+MEM_HOST, MEM_DEVICE = 0, 1
+
+_lib = None
+
+
+class HfpError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"hfp status {status}: {msg}")
+        self.status = status
+
+
+class _Hypergraph(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("m", ctypes.c_int32), ("net_off", ctypes.c_void_p),
+                ("pins", ctypes.c_void_p), ("net_w", ctypes.c_void_p), ("node_w", ctypes.c_void_p)]
+
+
+class _NetInfo(ctypes.Structure):
+    _fields_ = [("n_nodes", ctypes.c_int32), ("m_nets", ctypes.c_int32),
+                ("p_pins", ctypes.c_int64), ("lawler_nodes", ctypes.c_int32),
+                ("pad", ctypes.c_int32), ("total_weight", ctypes.c_int64)]
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_uint64) for k in
+                ("rounds", "global_relabels", "gr_levels", "items_hyper", "items_net",
+                 "node_visits", "pushes", "engine_launches", "engine_ns")]
+
+
+class FcParams(ctypes.Structure):
+    _fields_ = [("max_block_weight", ctypes.c_int64), ("flow_bound", ctypes.c_int64),
+                ("seed", ctypes.c_uint32), ("max_iterations", ctypes.c_int32)]
+
+
+class _FcResult(ctypes.Structure):
+    _fields_ = [("flow", ctypes.c_int64), ("source_weight", ctypes.c_int64),
+                ("iterations", ctypes.c_int32), ("n_pierced", ctypes.c_int32),
+                ("result_side", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load libhfp.so (building it first when sources are newer)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not _build.up_to_date():
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise ImportError("libhfp.so is missing: the CUDA library was not built")
+    lib = ctypes.CDLL(_build.LIB)
+    P, i32, i64, u32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32
+    sig = {
+        "hfp_ctx_create": (i32, [P, i32, P]),
+        "hfp_ctx_destroy": (None, [P]),
+        "hfp_last_error": (ctypes.c_char_p, []),
+        "hfp_kernel_launches": (ctypes.c_uint64, []),
+        "hfp_build_flow_network": (i32, [P, ctypes.POINTER(_Hypergraph), i32, P, i32, P, P, P]),
+        "hfp_net_destroy": (None, [P]),
+        "hfp_net_get_info": (i32, [P, ctypes.POINTER(_NetInfo)]),
+        "hfp_net_export": (i32, [P, i32, P, P, P, P, P, P, P, P]),
+        "hfp_net_get_stats": (i32, [P, ctypes.POINTER(_Stats)]),
+        "hfp_max_flow": (i32, [P, P]),
+        "hfp_min_cut_source_side": (i32, [P, i32, P, P, P, i32, P, P]),
+        "hfp_min_cut_sink_side": (i32, [P, i32, P, P, P]),
+        "hfp_pierce_and_augment": (i32, [P, i32, P, i32, ctypes.POINTER(FcParams), P, P]),
+        "hfp_flowcutter": (i32, [P, ctypes.POINTER(FcParams), P, P, P, i32,
+                                 ctypes.POINTER(_FcResult)]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status: int, allow=()):
+    if status != OK and status not in allow:
+        raise HfpError(status, load().hfp_last_error().decode(errors="replace"))
+    return status
+
+
+def _is_dev(a) -> bool:
+    return hasattr(a, "is_cuda") and a.is_cuda
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return ctypes.c_void_p(a.data_ptr())
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _host(a, dtype):
+    return None if a is None else np.ascontiguousarray(a, dtype=dtype)
+
+
+class Context:
+    """hfp_ctx: a device and the stream every call of this context uses."""
+
+    def __init__(self, device: int = 0, stream: int | None = None):
+        lib = load()
+        h = ctypes.c_void_p()
+        _check(lib.hfp_ctx_create(ctypes.byref(h), device, ctypes.c_void_p(stream or 0)))
+        self.h = h
+        self.device = device
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().hfp_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def ctx_create(device: int = 0, stream: int | None = None) -> Context:
+    return Context(device, stream)
+
+
+@dataclass
+class NetInfo:
+    n_nodes: int
+    m_nets: int
+    p_pins: int
+    lawler_nodes: int
+    total_weight: int
+
+
+class Net:
+    """hfp_net: a flow network resident on the device with its flow state."""
+
+    def __init__(self, ctx: Context, handle, n_region: int):
+        self.ctx = ctx
+        self.h = handle
+        self.n_region = n_region
+        inf = _NetInfo()
+        _check(load().hfp_net_get_info(self.h, ctypes.byref(inf)))
+        self.info = NetInfo(inf.n_nodes, inf.m_nets, inf.p_pins, inf.lawler_nodes, inf.total_weight)
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().hfp_net_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def build_flow_network(ctx: Context, net_off, pins, net_w, node_w, region, side, n: int,
+                       dist_from_cut=None) -> Net:
+    """hfp_build_flow_network.  All arrays numpy (host) or all CUDA tensors."""
+    dev = _is_dev(pins) or _is_dev(net_off)
+    if dev:
+        arrs = dict(net_off=net_off, pins=pins, net_w=net_w, node_w=node_w, region=region,
+                    side=side, dist=dist_from_cut)
+    else:
+        arrs = dict(net_off=_host(net_off, np.uint32), pins=_host(pins, np.int32),
+                    net_w=_host(net_w, np.int32), node_w=_host(node_w, np.int32),
+                    region=_host(region, np.int32), side=_host(side, np.int32),
+                    dist=_host(dist_from_cut, np.int32))
+    m = len(arrs["net_off"]) - 1
+    H = _Hypergraph(n, m, _ptr(arrs["net_off"]), _ptr(arrs["pins"]), _ptr(arrs["net_w"]),
+                    _ptr(arrs["node_w"]))
+    h = ctypes.c_void_p()
+    nr = len(arrs["region"])
+    _check(load().hfp_build_flow_network(ctx.h, ctypes.byref(H), MEM_DEVICE if dev else MEM_HOST,
+                                         _ptr(arrs["region"]), nr, _ptr(arrs["side"]),
+                                         _ptr(arrs["dist"]), ctypes.byref(h)))
+    return Net(ctx, h, nr)
+
+
+def net_export(net: Net) -> dict:
+    """hfp_net_export to host numpy arrays."""
+    i = net.info
+    out = dict(net_off=np.zeros(i.m_nets + 1, np.uint32), pins=np.zeros(i.p_pins, np.int32),
+               net_w=np.zeros(i.m_nets, np.int32), net_gid=np.zeros(i.m_nets, np.int32),
+               node_w=np.zeros(i.n_nodes, np.int32), node_off=np.zeros(i.n_nodes + 1, np.uint32),
+               inc_slot=np.zeros(i.p_pins, np.int32), dist=np.zeros(i.n_nodes, np.int32))
+    _check(load().hfp_net_export(net.h, MEM_HOST, *[_ptr(out[k]) for k in
+                                                    ("net_off", "pins", "net_w", "net_gid",
+                                                     "node_w", "node_off", "inc_slot", "dist")]))
+    return out
+
+
+def net_stats(net: Net) -> dict:
+    s = _Stats()
+    _check(load().hfp_net_get_stats(net.h, ctypes.byref(s)))
+    return {k: int(getattr(s, k)) for k, _ in _Stats._fields_}
+
+
+def kernel_launches() -> int:
+    """hfp_kernel_launches: kernels this library launched in the process."""
+    return int(load().hfp_kernel_launches())
+
+
+def max_flow(net: Net) -> int:
+    """hfp_max_flow: augment to a maximum preflow; returns the flow value."""
+    v = ctypes.c_int64()
+    _check(load().hfp_max_flow(net.h, ctypes.byref(v)))
+    return int(v.value)
+
+
+def min_cut_source_side(net: Net, lawler: bool = True, cut_cap: int | None = None):
+    """hfp_min_cut_source_side -> (in_source_lawler | None, in_source_region,
+    cut_net_ids, source_weight)."""
+    i = net.info
+    law = np.zeros(i.lawler_nodes, np.uint8) if lawler else None
+    reg = np.zeros(max(net.n_region, 1), np.uint8)
+    cap = i.m_nets if cut_cap is None else cut_cap
+    cuts = np.zeros(max(cap, 1), np.int32)
+    ncut = ctypes.c_int32()
+    w = ctypes.c_int64()
+    _check(load().hfp_min_cut_source_side(net.h, MEM_HOST, _ptr(law), _ptr(reg), _ptr(cuts), cap,
+                                          ctypes.byref(ncut), ctypes.byref(w)))
+    return law, reg[: net.n_region], cuts[: ncut.value], int(w.value)
+
+
+def min_cut_source_side_device(net: Net, in_source_region, in_source_lawler=None) -> int:
+    """hfp_min_cut_source_side with device outputs (CUDA uint8 tensors);
+    returns c(S_r)."""
+    w = ctypes.c_int64()
+    _check(load().hfp_min_cut_source_side(net.h, MEM_DEVICE, _ptr(in_source_lawler),
+                                          _ptr(in_source_region), None, 0, None, ctypes.byref(w)))
+    return int(w.value)
+
+
+def min_cut_sink_side(net: Net, lawler: bool = True):
+    """hfp_min_cut_sink_side -> (in_sink_lawler | None, in_sink_region, sink_weight)."""
+    i = net.info
+    law = np.zeros(i.lawler_nodes, np.uint8) if lawler else None
+    reg = np.zeros(max(net.n_region, 1), np.uint8)
+    w = ctypes.c_int64()
+    _check(load().hfp_min_cut_sink_side(net.h, MEM_HOST, _ptr(law), _ptr(reg), ctypes.byref(w)))
+    return law, reg[: net.n_region], int(w.value)
+
+
+def fc_params(max_block_weight: int, flow_bound: int = -1, seed: int = 0,
+              max_iterations: int = 0) -> FcParams:
+    return FcParams(int(max_block_weight), int(flow_bound), int(seed) & 0xFFFFFFFF,
+                    int(max_iterations))
+
+
+def pierce_and_augment(net: Net, side: int, nodes=None, params: FcParams | None = None):
+    """hfp_pierce_and_augment -> (pierced node, new flow value)."""
+    arr = None if nodes is None else _host(nodes, np.int32)
+    pierced = ctypes.c_int32(-1)
+    v = ctypes.c_int64()
+    _check(load().hfp_pierce_and_augment(net.h, side, _ptr(arr), 0 if arr is None else len(arr),
+                                         ctypes.byref(params) if params is not None else None,
+                                         ctypes.byref(pierced), ctypes.byref(v)))
+    return int(pierced.value), int(v.value)
+
+
+@dataclass
+class FlowCutterResult:
+    status: int
+    flow: int
+    source_weight: int
+    iterations: int
+    result_side: int
+    final_side: np.ndarray
+    pierce_side: np.ndarray
+    pierce_node: np.ndarray
+
+
+def flowcutter(net: Net, params: FcParams, pierce_cap: int | None = None) -> FlowCutterResult:
+    """hfp_flowcutter.  Statuses NO_BALANCED_CUT / ABORTED_WORSE are returned
+    in the result rather than raised."""
+    cap = net.info.n_nodes if pierce_cap is None else pierce_cap
+    fs = np.zeros(max(net.n_region, 1), np.uint8)
+    ps = np.zeros(max(cap, 1), np.int32)
+    pn = np.zeros(max(cap, 1), np.int32)
+    r = _FcResult()
+    st = _check(load().hfp_flowcutter(net.h, ctypes.byref(params), _ptr(fs), _ptr(ps), _ptr(pn),
+                                      cap, ctypes.byref(r)),
+                allow=(NO_BALANCED_CUT, ABORTED_WORSE))
+    k = min(r.n_pierced, cap)
+    return FlowCutterResult(st, r.flow, r.source_weight, r.iterations, r.result_side,
+                            fs[: net.n_region], ps[:k].copy(), pn[:k].copy())

@@ -1,0 +1,307 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Integer and index results must match bit for bit: network structure, flow
+value, the minimal source side S_r and minimal sink side T_r over every
+Lawler node, cut nets, side weights, the FlowCutter piercing sequence, final
+bipartition and cut weight.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests.helpers import hypergraph_from_lists, load_golden, random_instance
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hfp():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2201_01556_gb300 import hfp as mod
+    mod.load()
+    return mod
+
+
+@pytest.fixture(scope="module")
+def ctx(hfp):
+    c = hfp.ctx_create(0)
+    yield c
+    c.close()
+
+
+def _gpu_net(hfp, ctx, H, side, region, dist=None):
+    return hfp.build_flow_network(ctx, H.net_off, H.pins, H.net_w, H.node_w, region, side, H.n,
+                                  dist_from_cut=dist)
+
+
+def _expected_incidence(onet):
+    off = np.zeros(onet.n_nodes + 1, np.int64)
+    np.add.at(off, onet.pins.astype(np.int64) + 1, 1)
+    off = np.cumsum(off)
+    order = np.argsort(onet.pins, kind="stable")          # slots grouped by node, ascending
+    return off.astype(np.uint32), order.astype(np.int32)
+
+
+def _check_structure(hfp, gnet, onet, H, side, region):
+    ex = hfp.net_export(gnet)
+    assert gnet.info.n_nodes == onet.n_nodes
+    assert gnet.info.m_nets == onet.m_nets
+    assert gnet.info.p_pins == onet.p
+    assert np.array_equal(ex["net_off"], onet.net_off)
+    assert np.array_equal(ex["pins"], onet.pins)
+    assert np.array_equal(ex["net_w"], onet.net_w)
+    assert np.array_equal(ex["net_gid"], onet.net_gid)
+    assert np.array_equal(ex["node_w"].astype(np.int64), onet.node_w)
+    off, slots = _expected_incidence(onet)
+    assert np.array_equal(ex["node_off"], off)
+    assert np.array_equal(ex["inc_slot"], slots)
+    d = oracle.dist_from_cut(H, side, region)
+    assert np.array_equal(ex["dist"][2:], d)
+
+
+def _check_flow(hfp, gnet, onet):
+    mc = oracle.max_flow_min_cut(onet)
+    flow = hfp.max_flow(gnet)
+    assert flow == mc.flow
+    law, reg, cuts, ws = hfp.min_cut_source_side(gnet)
+    assert np.array_equal(law, mc.source_side)
+    assert np.array_equal(reg, mc.source_side[2:onet.n_nodes])
+    nh, m = onet.n_nodes, onet.m_nets
+    S = mc.source_side
+    exp_cuts = onet.net_gid[(S[nh:nh + m] == 1) & (S[nh + m:nh + 2 * m] == 0)]
+    assert np.array_equal(cuts, exp_cuts)
+    assert ws == int(onet.node_w[S[:nh] == 1].sum())
+    tlaw, treg, wt = hfp.min_cut_sink_side(gnet)
+    assert np.array_equal(tlaw, mc.sink_side)
+    assert np.array_equal(treg, mc.sink_side[2:onet.n_nodes])
+    assert wt == int(onet.node_w[mc.sink_side[:nh] == 1].sum())
+    # the cut nets carry exactly the flow (max-flow = min-cut)
+    assert int(onet.net_w[(S[nh:nh + m] == 1) & (S[nh + m:nh + 2 * m] == 0)].sum()) == flow
+    return mc
+
+
+def test_hand_fixture(hfp, ctx):
+    g = load_golden("lawler_hand_example.json")
+    h = g["hypergraph"]
+    H = hypergraph_from_lists(h["n"], h["nets"], h["net_w"], h["node_w"])
+    side = np.array(g["side"], np.int32)
+    region = np.array(g["region"], np.int32)
+    gnet = _gpu_net(hfp, ctx, H, side, region)
+    onet = oracle.build_network(H, side, region)
+    _check_structure(hfp, gnet, onet, H, side, region)
+    assert hfp.max_flow(gnet) == g["expected_flow"]
+    _check_flow(hfp, gnet, onet)
+    fc = g["flowcutter"]
+    r = hfp.flowcutter(gnet, hfp.fc_params(fc["max_block_weight"], seed=0))
+    assert r.status == 0
+    assert r.pierce_side.tolist() == fc["expected_pierce_side"]
+    assert r.pierce_node.tolist() == fc["expected_pierce_node"]
+    assert r.final_side.tolist() == fc["expected_final_side"][2:]
+    assert r.flow == fc["expected_cut"]
+
+
+@pytest.mark.parametrize("seed", list(range(1, 101)))
+def test_config1_flow_and_cuts(hfp, ctx, seed):
+    inst = synth.instance(1, seed)
+    H, part, region = inst["H"], inst["part"], inst["region"]
+    gnet = _gpu_net(hfp, ctx, H, part, region)
+    onet = oracle.build_network(H, part, region)
+    if seed <= 5:
+        _check_structure(hfp, gnet, onet, H, part, region)
+    _check_flow(hfp, gnet, onet)
+
+
+def _random_cases(seed, count, n_lo=3, n_hi=60, m_hi=120, c_max=1, k_sides=2):
+    rng = np.random.default_rng(seed)
+    for _ in range(count):
+        n = int(rng.integers(n_lo, n_hi + 1))
+        m = int(rng.integers(1, m_hi + 1))
+        H, side, region = random_instance(rng, n, m, max_size=int(rng.integers(2, 9)),
+                                          region_frac=float(rng.uniform(0.05, 1.0)),
+                                          w_max=int(rng.integers(1, 12)), c_max=c_max,
+                                          k_sides=k_sides)
+        yield H, side, region
+
+
+def test_random_small_structure_and_flow(hfp, ctx):
+    for H, side, region in _random_cases(101, 150):
+        gnet = _gpu_net(hfp, ctx, H, side, region)
+        onet = oracle.build_network(H, side, region)
+        _check_structure(hfp, gnet, onet, H, side, region)
+        _check_flow(hfp, gnet, onet)
+        gnet.close()
+
+
+def test_random_pair_sides_ignore_other_blocks(hfp, ctx):
+    """Vertices of neither block (side -1) are dropped from nets (k-way pairs)."""
+    for H, side, region in _random_cases(202, 60, k_sides=4):
+        if len(region) == 0:
+            continue
+        gnet = _gpu_net(hfp, ctx, H, side, region)
+        onet = oracle.build_network(H, side, region)
+        _check_structure(hfp, gnet, onet, H, side, region)
+        _check_flow(hfp, gnet, onet)
+        gnet.close()
+
+
+def test_edge_cases(hfp, ctx):
+    # empty region: only s and t, no nets
+    H = hypergraph_from_lists(4, [[0, 1], [2, 3], [1, 2]], [3, 4, 5])
+    side = np.array([0, 0, 1, 1], np.int32)
+    gnet = _gpu_net(hfp, ctx, H, side, np.zeros(0, np.int32))
+    assert gnet.info.n_nodes == 2 and gnet.info.m_nets == 0
+    assert hfp.max_flow(gnet) == 0
+    law, reg, cuts, ws = hfp.min_cut_source_side(gnet)
+    assert law.tolist() == [1, 0] and ws == 2
+    # single region vertex between s and t
+    gnet = _gpu_net(hfp, ctx, H, side, np.array([1], np.int32))
+    onet = oracle.build_network(H, side, np.array([1], np.int32))
+    _check_flow(hfp, gnet, onet)
+    # every vertex in the region: s and t carry no weight and no pins
+    region = np.arange(4, dtype=np.int32)
+    gnet = _gpu_net(hfp, ctx, H, side, region)
+    onet = oracle.build_network(H, side, region)
+    _check_structure(hfp, gnet, onet, H, side, region)
+    _check_flow(hfp, gnet, onet)
+    # a heavy net (more than a warp of pins) on both sides of the cut
+    n = 200
+    nets = [list(range(0, 150)), list(range(100, 200)), [0, 199], [10, 190]]
+    H = hypergraph_from_lists(n, nets, [7, 3, 2, 9])
+    side = (np.arange(n) >= 100).astype(np.int32)
+    region = np.arange(50, 150, dtype=np.int32)
+    gnet = _gpu_net(hfp, ctx, H, side, region)
+    onet = oracle.build_network(H, side, region)
+    _check_structure(hfp, gnet, onet, H, side, region)
+    _check_flow(hfp, gnet, onet)
+
+
+def test_invalid_inputs(hfp, ctx):
+    H = hypergraph_from_lists(4, [[0, 1], [2, 3], [1, 2]], [3, 4, 5])
+    side = np.array([0, 0, 1, 1], np.int32)
+    with pytest.raises(hfp.HfpError) as e:
+        _gpu_net(hfp, ctx, H, side, np.array([1, 1], np.int32))      # repeated vertex
+    assert e.value.status == hfp.ERR_INVALID
+    with pytest.raises(hfp.HfpError):
+        _gpu_net(hfp, ctx, H, np.array([0, -1, 1, 1], np.int32), np.array([1], np.int32))
+    with pytest.raises(hfp.HfpError):
+        _gpu_net(hfp, ctx, H, side, np.array([7], np.int32))         # out of range
+    bad = hypergraph_from_lists(4, [[0, 9]], [3])
+    with pytest.raises(hfp.HfpError):
+        _gpu_net(hfp, ctx, bad, side, np.array([0], np.int32))       # pin out of range
+    bad = hypergraph_from_lists(4, [[0, 1]], [0])
+    with pytest.raises(hfp.HfpError):
+        _gpu_net(hfp, ctx, bad, side, np.array([0], np.int32))       # weight 0
+    gnet = _gpu_net(hfp, ctx, H, side, np.array([1, 2], np.int32))
+    with pytest.raises(hfp.HfpError) as e:
+        hfp.min_cut_source_side(gnet)                                # before max_flow
+    assert e.value.status == hfp.ERR_STATE
+
+
+def test_device_inputs_match_host_inputs(hfp, ctx):
+    torch = pytest.importorskip("torch")
+    inst = synth.instance(1, 7)
+    H, part, region = inst["H"], inst["part"], inst["region"]
+    dev = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a).astype(dt)).cuda()
+    gnet = hfp.build_flow_network(ctx, dev(H.net_off.view(np.int32), np.int32),
+                                  dev(H.pins, np.int32), dev(H.net_w, np.int32),
+                                  dev(H.node_w, np.int32), dev(region, np.int32),
+                                  dev(part, np.int32), H.n)
+    torch.cuda.synchronize()
+    onet = oracle.build_network(H, part, region)
+    _check_structure(hfp, gnet, onet, H, part, region)
+    _check_flow(hfp, gnet, onet)
+
+
+def _fc_compare(hfp, ctx, H, side, region, eps_pct=3, seed=0, dist_given=False):
+    onet = oracle.build_network(H, side, region)
+    W = int(onet.node_w.sum())
+    L = oracle.max_block_weight(W, 2, eps_pct)
+    dist = oracle.dist_from_cut(H, side, region)
+    orig, d, gid = oracle.node_arrays(onet, side, region, dist)
+    o = oracle.flowcutter(onet, L, orig, d, gid, seed=seed)
+    gnet = _gpu_net(hfp, ctx, H, side, region, dist=dist if dist_given else None)
+    r = hfp.flowcutter(gnet, hfp.fc_params(L, seed=seed))
+    assert r.status == o.status
+    assert np.array_equal(r.pierce_side, o.pierce_side)
+    assert np.array_equal(r.pierce_node, o.pierce_node)
+    if o.status == oracle.OK:
+        assert r.flow == o.flow
+        assert r.iterations == o.iterations
+        assert r.result_side == o.result_side
+        assert r.source_weight == o.source_weight
+        assert np.array_equal(r.final_side, o.final_side[2:])
+    gnet.close()
+    return o
+
+
+def test_flowcutter_random(hfp, ctx):
+    pierced = 0
+    for i, (H, side, region) in enumerate(_random_cases(303, 150, n_lo=6, n_hi=50, m_hi=90,
+                                                        c_max=4)):
+        o = _fc_compare(hfp, ctx, H, side, region, seed=i, dist_given=(i % 2 == 1))
+        pierced += len(o.pierce_node) > 0
+    assert pierced > 20
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_flowcutter_config3_scaled(hfp, ctx, seed):
+    """Config-3 generator (vertex weights 1..4, eps 0.03) at n = 20,000."""
+    inst = synth.instance(3, seed, n=20000, m=30000, radius=2000)
+    o = _fc_compare(hfp, ctx, inst["H"], inst["part"], inst["region"], seed=seed)
+    assert o.status == oracle.OK
+
+
+def test_pierce_and_augment_explicit(hfp, ctx):
+    """S <- S_r + {p} and T <- T_r + {p} with caller-chosen nodes, against the
+    oracle augmenting its own flow after the same terminal changes."""
+    rng = np.random.default_rng(5)
+    checked = 0
+    for H, side, region in _random_cases(404, 80, n_lo=8, n_hi=40, m_hi=70):
+        onet = oracle.build_network(H, side, region)
+        if onet.n_nodes <= 3:
+            continue
+        gnet = _gpu_net(hfp, ctx, H, side, region)
+        G = oracle.Lawler(onet)
+        S = G.mask([0])
+        T = G.mask([1])
+        G.augment(S, T)
+        hfp.max_flow(gnet)
+        for step in range(3):
+            Sr = G.reach_from(S)
+            Tr = G.reach_to(T)
+            free = [h for h in range(2, onet.n_nodes) if not Sr[h] and not Tr[h]]
+            if not free:
+                break
+            p = int(rng.choice(free))
+            side_ = int(rng.integers(0, 2))
+            if side_ == 0:
+                S = np.maximum(Sr, G.mask([p]))
+            else:
+                T = np.maximum(Tr, G.mask([p]))
+            G.augment(S, T)
+            _, flow = hfp.pierce_and_augment(gnet, side_, [p])
+            assert flow == G.flow_value(S)
+            law, _, _, _ = hfp.min_cut_source_side(gnet)
+            assert np.array_equal(law, G.reach_from(S))
+            tlaw, _, _ = hfp.min_cut_sink_side(gnet)
+            assert np.array_equal(tlaw, G.reach_to(T))
+            checked += 1
+        gnet.close()
+    assert checked > 40
+
+
+def test_deterministic_runs(hfp, ctx):
+    inst = synth.instance(1, 42)
+    H, part, region = inst["H"], inst["part"], inst["region"]
+    runs = []
+    for _ in range(3):
+        gnet = _gpu_net(hfp, ctx, H, part, region)
+        f = hfp.max_flow(gnet)
+        law, _, _, _ = hfp.min_cut_source_side(gnet)
+        st = hfp.net_stats(gnet)
+        runs.append((f, law.tobytes(), st["rounds"], st["pushes"], st["global_relabels"]))
+        gnet.close()
+    assert runs[0] == runs[1] == runs[2]

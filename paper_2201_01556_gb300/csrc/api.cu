@@ -101,6 +101,7 @@ struct hfp_net {
   bool flow_started = false;
   bool labels_exact = false;
   bool sr_valid = false;
+  bool dist_ready = false;
   uint64_t launches = 0;
   uint64_t engine_ns = 0;
 };
@@ -188,6 +189,15 @@ hfp_status ensure_source_side(hfp_net* net) {
   hfp_status s = run_engine(net);
   if (s != HFP_OK) return s;
   net->sr_valid = true;
+  return HFP_OK;
+}
+
+hfp_status ensure_dist(hfp_net* net) {
+  if (net->dist_ready) return HFP_OK;
+  launch_engine_setup(net->E, SETUP_DIST, net->ctx->stream);
+  hfp_status s = run_engine(net);
+  if (s != HFP_OK) return s;
+  net->dist_ready = true;
   return HFP_OK;
 }
 
@@ -351,14 +361,14 @@ HFP_API hfp_status hfp_build_flow_network(hfp_ctx* ctx, const hfp_hypergraph* H,
   CK(s_pos.alloc(sizeof(unsigned) * mm, st));
   CK(t_pos.alloc(sizeof(unsigned) * mm, st));
   CK(totals.alloc(sizeof(unsigned) * 8, st));
-  CK(wsum.alloc(sizeof(unsigned long long) * 4, st));
+  CK(wsum.alloc(sizeof(unsigned long long) * 8, st));
   CK(err.alloc(sizeof(int), st));
   CK(dist_tmp.alloc(sizeof(int32_t) * (n_region > 0 ? n_region : 1), st));
   size_t scan_words = scan_scratch_words((unsigned)(m > n_nodes + 1 ? m : n_nodes + 1)) + 8;
   CK(scan_scr.alloc(sizeof(unsigned) * scan_words, st));
   if (n) CK(cudaMemsetAsync(loc.p, 0xFF, sizeof(int32_t) * n, st));
   CK(cudaMemsetAsync(totals.p, 0, sizeof(unsigned) * 8, st));
-  CK(cudaMemsetAsync(wsum.p, 0, sizeof(unsigned long long) * 4, st));
+  CK(cudaMemsetAsync(wsum.p, 0, sizeof(unsigned long long) * 8, st));
   CK(cudaMemsetAsync(err.p, 0, sizeof(int), st));
   if (n_region) CK(cudaMemsetAsync(dist_tmp.p, 0, sizeof(int32_t) * n_region, st));
 
@@ -393,12 +403,12 @@ HFP_API hfp_status hfp_build_flow_network(hfp_ctx* ctx, const hfp_hypergraph* H,
 
   struct Head {
     unsigned totals[8];
-    unsigned long long wsum[4];
+    unsigned long long wsum[8];
     int err;
   };
   Head* hh = (Head*)ctx->pinned_small;
   CK(cudaMemcpyAsync(hh->totals, totals.p, sizeof(unsigned) * 8, cudaMemcpyDeviceToHost, st));
-  CK(cudaMemcpyAsync(hh->wsum, wsum.p, sizeof(unsigned long long) * 4, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(hh->wsum, wsum.p, sizeof(unsigned long long) * 8, cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(&hh->err, err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   if (hh->err != kDevOk) return fail(HFP_ERR_INVALID, "invalid hypergraph, region or side input");
@@ -409,7 +419,8 @@ HFP_API hfp_status hfp_build_flow_network(hfp_ctx* ctx, const hfp_hypergraph* H,
   const int64_t NL64 = (int64_t)n_nodes + 2 * (int64_t)m_net;
   if (NL64 >= (1ll << 31) - 2) return fail(HFP_ERR_INVALID, "flow network too large");
   const int32_t NL = (int32_t)NL64;
-  const int64_t total_w = (int64_t)hh->wsum[0] + (int64_t)hh->wsum[1];
+  // W of the flow problem: c(s) + c(t) + c(B)
+  const int64_t total_w = (int64_t)hh->wsum[0] + (int64_t)hh->wsum[1] + (int64_t)hh->wsum[4];
 
   // arena for the network and its flow state
   hfp_net* net = new hfp_net();
@@ -511,30 +522,14 @@ HFP_API hfp_status hfp_build_flow_network(hfp_ctx* ctx, const hfp_hypergraph* H,
     launch_incidence(n_nodes, m_net, p_net, nnet_off, npin, node_off, cursor.as<unsigned>(), tot,
                      inc, tmp.as<int2>(), scan_scr.as<unsigned>(), tot + 4, sms, st);
   }
-  // distances from the original cut
+  // distances from the original cut: given, or seeded here and completed by
+  // the engine on first use (ensure_dist)
   if (d_dist) {
     launch_dist_copy(n_region, d_dist, node_dist, err.as<int>(), st);
+    net->dist_ready = true;
   } else {
-    DevBuf fr, cnt;
-    CKN(fr.alloc(sizeof(int32_t) * 2 * n_nodes, st));
-    CKN(cnt.alloc(sizeof(unsigned) * 2, st));
-    CKN(cudaMemsetAsync(cnt.p, 0, sizeof(unsigned) * 2, st));
-    int32_t* f[2] = {fr.as<int32_t>(), fr.as<int32_t>() + n_nodes};
-    unsigned* c2 = cnt.as<unsigned>();
-    launch_dist_seed(n_nodes, dist_tmp.as<int32_t>(), node_dist, f[0], c2, sms, st);
-    unsigned* hc = (unsigned*)((char*)ctx->pinned_small + 2048);
-    CKN(cudaMemcpyAsync(hc, c2, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
-    CKN(cudaStreamSynchronize(st));
-    unsigned cur = *hc;
-    for (int d = 1; cur > 0; d++) {
-      int a = (d - 1) & 1, b = d & 1;
-      CKN(cudaMemsetAsync(c2 + b, 0, sizeof(unsigned), st));
-      launch_dist_level(D, f[a], c2 + a, f[b], c2 + b, node_dist, d + 1, cur, sms, st);
-      CKN(cudaMemcpyAsync(hc, c2 + b, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
-      CKN(cudaStreamSynchronize(st));
-      cur = *hc;
-    }
-    launch_dist_finish(n_nodes, node_dist, sms, st);
+    launch_dist_seed(n_nodes, dist_tmp.as<int32_t>(), node_dist, sms, st);
+    net->dist_ready = false;
   }
   // flow state
   CKN(cudaMemsetAsync(D.f_in, 0, sizeof(int32_t) * p_net, st));
@@ -587,7 +582,13 @@ HFP_API hfp_status hfp_net_export(hfp_net* net, hfp_mem mem, uint32_t* net_off, 
   if (net_gid && (s = copy_out(net_gid, net->net_gid, sizeof(int32_t) * D.m_nets, mem, st))) return s;
   if (node_w && (s = copy_out(node_w, D.node_w, sizeof(int32_t) * D.n_nodes, mem, st))) return s;
   if (node_off && (s = copy_out(node_off, D.node_off, sizeof(uint32_t) * (D.n_nodes + 1), mem, st))) return s;
-  if (dist && (s = copy_out(dist, D.node_dist, sizeof(int32_t) * D.n_nodes, mem, st))) return s;
+  if (dist) {
+    if ((s = ensure_dist(net)) != HFP_OK) return s;
+    DevBuf tmp;
+    CK(tmp.alloc(sizeof(int32_t) * D.n_nodes, st));
+    launch_dist_export(D.n_nodes, D.node_dist, tmp.as<int32_t>(), net->ctx->sms, st);
+    if ((s = copy_out(dist, tmp.p, sizeof(int32_t) * D.n_nodes, mem, st))) return s;
+  }
   if (inc_slot) {
     DevBuf tmp;
     CK(tmp.alloc(sizeof(int32_t) * (D.p_pins > 0 ? D.p_pins : 1), st));
@@ -714,7 +715,9 @@ namespace {
 // Piercing-node selection by the rule of Section 7 (see hfp_flowcutter).
 hfp_status select_pierce(hfp_net* net, int grow_s, const hfp_fc_params* prm, int32_t* node) {
   Ctl c;
-  hfp_status s = read_ctl(net, &c);
+  hfp_status s = ensure_dist(net);
+  if (s != HFP_OK) return s;
+  s = read_ctl(net, &c);
   if (s != HFP_OK) return s;
   const long long w_reach = grow_s ? c.wS : c.wT;
   launch_pierce_select(net->d, net->E, grow_s, prm->max_block_weight, w_reach, prm->seed,

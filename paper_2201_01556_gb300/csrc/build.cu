@@ -133,25 +133,31 @@ __global__ void k_region_map(int32_t n, int32_t n_region, const int32_t* region,
 // contracted weights of s and t, and the total weight check
 __global__ void k_st_weight(int32_t n, const int32_t* loc, const int32_t* side,
                             const int32_t* node_w_h, unsigned long long* wsum, int* err) {
-  __shared__ unsigned long long sh[3];
-  if (threadIdx.x < 3) sh[threadIdx.x] = 0;
+  // wsum: [0] s, [1] t, [2] all of H, [3] nets (k_net_scan), [4] region
+  __shared__ unsigned long long sh[5];
+  if (threadIdx.x < 5) sh[threadIdx.x] = 0;
   __syncthreads();
-  unsigned long long a0 = 0, a1 = 0, at = 0;
+  unsigned long long a0 = 0, a1 = 0, at = 0, ar = 0;
   for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
     int c = node_w_h ? node_w_h[v] : 1;
     if (c <= 0) set_err(err, kDevBadInput);
-    at += (unsigned long long)(c > 0 ? c : 0);
+    unsigned long long cc = (unsigned long long)(c > 0 ? c : 0);
+    at += cc;
     if (loc[v] < 0) {
       int sd = side[v];
-      if (sd == 0) a0 += c;
-      else if (sd == 1) a1 += c;
+      if (sd == 0) a0 += cc;
+      else if (sd == 1) a1 += cc;
+    } else {
+      ar += cc;
     }
   }
   if (a0) atomicAdd(&sh[0], a0);
   if (a1) atomicAdd(&sh[1], a1);
   if (at) atomicAdd(&sh[2], at);
+  if (ar) atomicAdd(&sh[4], ar);
   __syncthreads();
-  if (threadIdx.x < 3 && sh[threadIdx.x]) atomicAdd(&wsum[threadIdx.x], sh[threadIdx.x]);
+  if (threadIdx.x < 5 && threadIdx.x != 3 && sh[threadIdx.x])
+    atomicAdd(&wsum[threadIdx.x], sh[threadIdx.x]);
 }
 
 // pass 1, warp per net of H
@@ -207,7 +213,7 @@ __global__ void k_net_scan(int32_t n, int32_t m, const uint32_t* net_off, const 
         int v = pins[j];
         if (v >= 0 && v < n) {
           int l = loc[v];
-          if (l >= 0) dist_tmp[l] = 1;
+          if (l >= 0) dist_tmp[l - 2] = 1;   // indexed by region position
         }
       }
     }
@@ -318,55 +324,19 @@ __global__ void k_inc_sort(int32_t n_nodes, const unsigned* node_off, int2* inc,
   }
 }
 
-// distance BFS inside the region: warp per frontier hypernode
-__global__ void k_dist_level(const NetDev N, const int32_t* front, const unsigned* fcnt,
-                             int32_t* next, unsigned* ncnt, int32_t* dist, int d1) {
-  const unsigned lane = threadIdx.x & 31;
-  const unsigned gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const unsigned nw = (gridDim.x * blockDim.x) >> 5;
-  const unsigned cnt = *fcnt;
-  for (unsigned w = gw; w < cnt; w += nw) {
-    const int u = front[w];
-    for (unsigned j = N.node_off[u]; j < N.node_off[u + 1]; j++) {
-      const int e = N.inc[j].x;
-      const unsigned beg = N.net_off[e], end = N.net_off[e + 1];
-      for (unsigned p0 = beg; p0 < end; p0 += 32) {
-        const unsigned p = p0 + lane;
-        bool claim = false;
-        int v = -1;
-        if (p < end) {
-          v = N.pin[p];
-          if (v >= 2 && dist[v] < 0) claim = atomicCAS(&dist[v], -1, d1) == -1;
-        }
-        warp_append(claim, v, next, ncnt);
-      }
-    }
-  }
+// distance from the cut, initial values: 0 for s and t, 1 for region pins of
+// nets with pins on both sides, -1 (not yet reached) otherwise; the engine's
+// DIST states finish the breadth-first search on first use
+__global__ void k_dist_seed(int32_t n_nodes, const int32_t* dist_tmp, int32_t* dist) {
+  for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < n_nodes; u += gridDim.x * blockDim.x)
+    dist[u] = u < 2 ? 0 : (dist_tmp[u - 2] == 1 ? 1 : -1);
 }
 
-__global__ void k_dist_seed(int32_t n_nodes, const int32_t* dist_tmp, int32_t* dist,
-                            int32_t* front, unsigned* fcnt) {
-  const unsigned lane = threadIdx.x & 31;
-  const unsigned tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
-  for (unsigned u0 = tid - lane; u0 < (unsigned)n_nodes; u0 += nth) {
-    unsigned u = u0 + lane;
-    bool seed = false;
-    if (u < (unsigned)n_nodes) {
-      if (u < 2) {
-        dist[u] = 0;
-      } else {
-        seed = dist_tmp[u - 2] == 1;
-        dist[u] = seed ? 1 : -1;
-      }
-    }
-    warp_append(seed, (int)u, front, fcnt);
-  }
-}
-
-__global__ void k_dist_finish(int32_t n_nodes, int32_t* dist) {
-  for (int u = 2 + blockIdx.x * blockDim.x + threadIdx.x; u < n_nodes; u += gridDim.x * blockDim.x) {
+// export copy: unreached vertices get the far distance
+__global__ void k_dist_export(int32_t n_nodes, const int32_t* dist, int32_t* out) {
+  for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < n_nodes; u += gridDim.x * blockDim.x) {
     int d = dist[u];
-    dist[u] = (d < 0 || d > kDistFar) ? kDistFar : d;
+    out[u] = (d < 0 || d > kDistFar) ? kDistFar : d;
   }
 }
 
@@ -473,23 +443,15 @@ void launch_incidence(int32_t n_nodes, int32_t m_net, unsigned p, const uint32_t
   }
 }
 
-void launch_dist_seed(int32_t n_nodes, const int32_t* dist_tmp, int32_t* dist, int32_t* front,
-                      unsigned* fcnt, int sms, cudaStream_t st) {
-  k_dist_seed<<<blocks_for(n_nodes, 256, sms * 8), 256, 0, st>>>(n_nodes, dist_tmp, dist, front,
-                                                                 fcnt);
+void launch_dist_seed(int32_t n_nodes, const int32_t* dist_tmp, int32_t* dist, int sms,
+                      cudaStream_t st) {
+  k_dist_seed<<<blocks_for(n_nodes, 256, sms * 8), 256, 0, st>>>(n_nodes, dist_tmp, dist);
   count_launches(1);
 }
 
-void launch_dist_level(const NetDev& N, const int32_t* front, const unsigned* fcnt, int32_t* next,
-                       unsigned* ncnt, int32_t* dist, int d1, unsigned host_cnt, int sms,
-                       cudaStream_t st) {
-  k_dist_level<<<blocks_for((unsigned long long)host_cnt * 32, 256, sms * 16), 256, 0, st>>>(
-      N, front, fcnt, next, ncnt, dist, d1);
-  count_launches(1);
-}
-
-void launch_dist_finish(int32_t n_nodes, int32_t* dist, int sms, cudaStream_t st) {
-  k_dist_finish<<<blocks_for(n_nodes, 256, sms * 8), 256, 0, st>>>(n_nodes, dist);
+void launch_dist_export(int32_t n_nodes, const int32_t* dist, int32_t* out, int sms,
+                        cudaStream_t st) {
+  k_dist_export<<<blocks_for(n_nodes, 256, sms * 8), 256, 0, st>>>(n_nodes, dist, out);
   count_launches(1);
 }
 

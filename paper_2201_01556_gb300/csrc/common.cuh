@@ -36,7 +36,7 @@ struct NetDev {
   const uint32_t* node_off;
   const int2* inc;              // (net, pin slot), sorted by slot per node
   const int32_t* node_w;
-  const int32_t* node_dist;     // distance from the original cut (per hypernode)
+  int32_t* node_dist;           // distance from the original cut (-1: not reached yet)
   const int8_t* node_orig;      // original side (0/1) per hypernode
   const int32_t* node_gid;      // id in H (-1 for s, t)
   int32_t* f_in;

@@ -27,6 +27,8 @@ __global__ void k_engine_setup(EngineCtl* E, int mode) {
       X.c.wT = 0;
       break;
     case SETUP_ROUND:
+      // fresh epoch: the frontier was stamped by k_saturate under the last one
+      X.s.epoch++;
       X.s.state = ST_ROUND_A;
       X.s.fcnt = X.cnt[L_FRONT];
       X.cnt[L_FRONT] = 0;
@@ -45,6 +47,10 @@ __global__ void k_engine_setup(EngineCtl* E, int mode) {
     case SETUP_PREP:
       X.s.epoch++;
       X.cnt[L_FRONT] = 0;
+      break;
+    case SETUP_DIST:
+      X.s.state = ST_DIST_INIT;
+      X.cnt[L_BFS] = 0;
       break;
   }
 }
@@ -157,7 +163,7 @@ __device__ __forceinline__ unsigned long long pierce_key(const NetDev& N, int h,
   if (f & (grow_s ? kSink : kSource)) return 0;
   if (w_reach + N.node_w[h] > max_w) return 0;
   const bool no_path = grow_s ? N.lab0[h] >= NL : N.insr[h] == 0;
-  const int d = N.node_dist[h];
+  const int d = N.node_dist[h] < 0 ? kDistFar : N.node_dist[h];
   const int sd = (N.node_orig[h] == (grow_s ? 0 : 1)) ? d : -d;
   const uint32_t hh = fmix32((uint32_t)N.node_gid[h] ^ seed);
   return (1ull << 54) | ((unsigned long long)no_path << 53) |

@@ -139,6 +139,24 @@ __device__ void control(EngineCtl* E, const NetDev& N, const Params& P) {
       }
       break;
     }
+    case ST_DIST_INIT:
+      s.bfs_begin = 0;
+      s.bfs_end = E->cnt[L_BFS];
+      s.level = 0;
+      s.state = ST_DIST_LEVEL;
+      break;
+    case ST_DIST_LEVEL: {
+      unsigned e = E->cnt[L_BFS];
+      if (e == s.bfs_end) {
+        E->cnt[L_BFS] = 0;
+        s.state = ST_DONE;
+      } else {
+        s.bfs_begin = s.bfs_end;
+        s.bfs_end = e;
+        s.level++;
+      }
+      break;
+    }
     default:
       s.state = ST_DONE;
   }
@@ -599,6 +617,43 @@ __device__ void sr_level(const NetDev& N, EngineCtl* E, const Sched& s, unsigned
   }
 }
 
+// Distance from the original cut (reading of Section 6 "Region Growing" and
+// Section 7 "Piercing"): breadth-first search inside the region from the
+// vertices at distance 1.  Level list i holds the vertices at distance i + 1.
+__device__ void dist_init(const NetDev& N, EngineCtl* E, unsigned lane) {
+  const unsigned tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+  for (unsigned u0 = tid - lane; u0 < (unsigned)N.n_nodes; u0 += nth) {
+    const unsigned u = u0 + lane;
+    const bool seed = u >= 2 && u < (unsigned)N.n_nodes && N.node_dist[u] == 1;
+    warp_append(seed, (int)u, N.list[L_BFS], &E->cnt[L_BFS]);
+  }
+}
+
+__device__ void dist_level(const NetDev& N, EngineCtl* E, const Sched& s, unsigned gwarp,
+                           unsigned nwarps, unsigned lane) {
+  const int d2 = s.level + 2;
+  int32_t* bl = N.list[L_BFS];
+  unsigned* bc = &E->cnt[L_BFS];
+  for (unsigned w = s.bfs_begin + gwarp; w < s.bfs_end; w += nwarps) {
+    const int u = bl[w];
+    for (unsigned j = N.node_off[u]; j < N.node_off[u + 1]; j++) {
+      const int e = N.inc[j].x;
+      const unsigned beg = N.net_off[e], end = N.net_off[e + 1];
+      for (unsigned p0 = beg; p0 < end; p0 += 32) {
+        const unsigned p = p0 + lane;
+        bool claim = false;
+        int v = -1;
+        if (p < end) {
+          v = N.pin[p];
+          if (v >= 2 && N.node_dist[v] < 0)
+            claim = atomicCAS(&N.node_dist[v], -1, min(d2, kDistFar)) == -1;
+        }
+        warp_append(claim, v, bl, bc);
+      }
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kEngineThreads) engine_kernel(NetDev N, EngineCtl* E, Params P) {
   __shared__ Sched ss;
@@ -618,6 +673,8 @@ __global__ void __launch_bounds__(kEngineThreads) engine_kernel(NetDev N, Engine
       case ST_GR_LEVEL: gr_level(N, E, ss, gwarp, nwarps, lane, a); target = 2; break;
       case ST_SR_INIT: sr_init(N, E, ss, lane, a); target = 1; break;
       case ST_SR_LEVEL: sr_level(N, E, ss, gwarp, nwarps, lane, a); target = 1; break;
+      case ST_DIST_INIT: dist_init(N, E, lane); break;
+      case ST_DIST_LEVEL: dist_level(N, E, ss, gwarp, nwarps, lane); break;
       default: break;
     }
     if (a.w) {

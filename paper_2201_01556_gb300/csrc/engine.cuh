@@ -15,6 +15,8 @@ enum EngineState : int {
   ST_GR_LEVEL = 4,  // global relabel: one reverse-BFS level
   ST_SR_INIT = 5,   // source-side cut: seed S and the non-sink excess nodes
   ST_SR_LEVEL = 6,  // source-side cut: one forward-BFS level
+  ST_DIST_INIT = 7, // distance from the cut: seed the distance-1 vertices
+  ST_DIST_LEVEL = 8,  // distance from the cut: one BFS level inside the region
 };
 
 // list ids in NetDev::list

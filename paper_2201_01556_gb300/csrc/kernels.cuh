@@ -33,12 +33,10 @@ void launch_incidence(int32_t n_nodes, int32_t m_net, unsigned p, const uint32_t
                       const int32_t* npin, unsigned* deg_then_off, unsigned* cursor,
                       const unsigned* totals, int2* inc, int2* tmp, unsigned* scan_scratch,
                       unsigned* scan_total, int sms, cudaStream_t st);
-void launch_dist_seed(int32_t n_nodes, const int32_t* dist_tmp, int32_t* dist, int32_t* front,
-                      unsigned* fcnt, int sms, cudaStream_t st);
-void launch_dist_level(const NetDev& N, const int32_t* front, const unsigned* fcnt, int32_t* next,
-                       unsigned* ncnt, int32_t* dist, int d1, unsigned host_cnt, int sms,
-                       cudaStream_t st);
-void launch_dist_finish(int32_t n_nodes, int32_t* dist, int sms, cudaStream_t st);
+void launch_dist_seed(int32_t n_nodes, const int32_t* dist_tmp, int32_t* dist, int sms,
+                      cudaStream_t st);
+void launch_dist_export(int32_t n_nodes, const int32_t* dist, int32_t* out, int sms,
+                        cudaStream_t st);
 void launch_dist_copy(int32_t n_region, const int32_t* dist_in, int32_t* dist, int* err,
                       cudaStream_t st);
 void launch_st_attrs(int32_t* node_gid, int32_t* node_w, int8_t* node_orig,
@@ -49,7 +47,7 @@ constexpr int kEngineThreads = 512;
 __global__ void __launch_bounds__(kEngineThreads) engine_kernel(NetDev N, EngineCtl* E, Params P);
 
 // cuts.cu
-enum SetupMode : int { SETUP_GR = 0, SETUP_ROUND = 1, SETUP_SR = 2, SETUP_PREP = 3 };
+enum SetupMode : int { SETUP_GR = 0, SETUP_ROUND = 1, SETUP_SR = 2, SETUP_PREP = 3, SETUP_DIST = 4 };
 void launch_engine_setup(EngineCtl* E, int mode, cudaStream_t st);
 void launch_saturate(const NetDev& N, EngineCtl* E, const int32_t* nodes, int32_t count,
                      cudaStream_t st);

@@ -239,12 +239,13 @@ def min_cut_source_side(net: Net, lawler: bool = True, cut_cap: int | None = Non
     law = np.zeros(i.lawler_nodes, np.uint8) if lawler else None
     reg = np.zeros(max(net.n_region, 1), np.uint8)
     cap = i.m_nets if cut_cap is None else cut_cap
-    cuts = np.zeros(max(cap, 1), np.int32)
+    cuts = np.zeros(cap, np.int32) if cap > 0 else None
     ncut = ctypes.c_int32()
     w = ctypes.c_int64()
     _check(load().hfp_min_cut_source_side(net.h, MEM_HOST, _ptr(law), _ptr(reg), _ptr(cuts), cap,
                                           ctypes.byref(ncut), ctypes.byref(w)))
-    return law, reg[: net.n_region], cuts[: ncut.value], int(w.value)
+    cut_ids = cuts[: ncut.value] if cuts is not None else np.zeros(0, np.int32)
+    return law, reg[: net.n_region], cut_ids, int(w.value)
 
 
 def min_cut_source_side_device(net: Net, in_source_region, in_source_lawler=None) -> int:

@@ -28,7 +28,7 @@ import numpy as np  # noqa: E402
 
 import synth  # noqa: E402
 
-CFG = 2
+WORKLOAD = "ring_n2M_zipf"
 METRIC = "Lawler-network pins/s to exact min cut (1 GB300)"
 UNIT = "pins/s"
 L2_BYTES = 129 * 1024 * 1024
@@ -114,7 +114,7 @@ def oracle_step(inst):
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
-    inst = synth.instance(CFG, args.seed, **SAMPLE)
+    inst = synth.instance(WORKLOAD, args.seed, **SAMPLE)
     for _ in range(args.warmup if args.warmup < 1 else 1):
         oracle_step(inst)
     times, pins = [], 0
@@ -129,7 +129,7 @@ def run_reference(args, rank, world):
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * statistics.mean(times), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-            "config": {"workload": synth.CONFIGS[CFG]["name"], "seed": args.seed,
+            "config": {"workload": WORKLOAD, "seed": args.seed,
                        "sample": sample},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": sample},
@@ -160,7 +160,7 @@ def main():
     from paper_2201_01556_gb300 import hfp
     hfp.load()
 
-    inst = synth.instance(CFG, args.seed)
+    inst = synth.instance(WORKLOAD, args.seed)
     H, part, region = inst["H"], inst["part"], inst["region"]
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.int32)).cuda()
     d_off, d_pins, d_netw, d_nodew = dev(H.net_off), dev(H.pins), dev(H.net_w), dev(H.node_w)
@@ -244,7 +244,7 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-            "config": {"workload": synth.CONFIGS[CFG]["name"], "seed": args.seed, "n": H.n,
+            "config": {"workload": WORKLOAD, "seed": args.seed, "n": H.n,
                        "m": H.m, "pins_H": H.p, "region": len(region), "lawler_pins": p_pins,
                        "flow": stats[0][2], "source_weight": stats[0][3],
                        "l2": "flushed between timed steps (2x L2 buffer write)",
@@ -256,7 +256,7 @@ def main():
             "engine": {"rounds": st["rounds"], "global_relabels": st["global_relabels"],
                        "gr_levels": st["gr_levels"], "pushes": st["pushes"]}}
     if not args.no_cpu_baseline:
-        sinst = synth.instance(CFG, args.seed, **SAMPLE)
+        sinst = synth.instance(WORKLOAD, args.seed, **SAMPLE)
         p, dt, _ = oracle_step(sinst)
         line["cpu_baseline"] = {"value": p / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": f"ring n={SAMPLE['n']}, m={SAMPLE['m']}, radius="

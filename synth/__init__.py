@@ -128,25 +128,25 @@ def kway_partition(n: int, k: int, frac_ppm: int, seed: int) -> np.ndarray:
     return part
 
 
-# The five workloads.  Sizes are the full ones; `scaled` shrinks n and m for
-# quick cases of the same shape.
-CONFIGS = {
-    1: dict(name="ring_n4096_geom", n=4096, m=6144, dist=GEOMETRIC, cap=16, window=64,
+# The workloads, by name.  Sizes are the full ones; instance() may shrink n,
+# m, radius, window and cap for quick cases of the same shape.
+WORKLOADS = {
+    "ring_n4096_geom": dict(name="ring_n4096_geom", n=4096, m=6144, dist=GEOMETRIC, cap=16, window=64,
             w_range=(1, 4), c_range=(1, 1), radius=48, k=2),
-    2: dict(name="ring_n2M_zipf", n=2_000_000, m=3_000_000, dist=ZIPF, cap=5000, window=4096,
+    "ring_n2M_zipf": dict(name="ring_n2M_zipf", n=2_000_000, m=3_000_000, dist=ZIPF, cap=5000, window=4096,
             w_range=(1, 10), c_range=(1, 1), radius=200_000, k=2),
-    3: dict(name="ring_n500k_zipf_fc", n=500_000, m=750_000, dist=ZIPF, cap=5000, window=4096,
+    "ring_n500k_zipf_fc": dict(name="ring_n500k_zipf_fc", n=500_000, m=750_000, dist=ZIPF, cap=5000, window=4096,
             w_range=(1, 10), c_range=(1, 4), radius=50_000, k=2, eps_pct=3),
-    4: dict(name="ring_n8M_zipf_k64", n=8_000_000, m=12_000_000, dist=ZIPF, cap=10000,
+    "ring_n8M_zipf_k64": dict(name="ring_n8M_zipf_k64", n=8_000_000, m=12_000_000, dist=ZIPF, cap=10000,
             window=4096, w_range=(1, 10), c_range=(1, 1), k=64, frac_ppm=50_000),
 }
 
 
-def instance(cfg: int, seed: int, n: int | None = None, m: int | None = None,
+def instance(workload: str, seed: int, n: int | None = None, m: int | None = None,
              radius: int | None = None, window: int | None = None, cap: int | None = None):
     """Hypergraph plus partition (and, for bipartitions, the flow region) of a
     workload; n, m, radius, window and cap may be overridden for smaller cases."""
-    c = dict(CONFIGS[cfg])
+    c = dict(WORKLOADS[workload])
     if n is not None:
         c["n"] = n
     if m is not None:
@@ -159,7 +159,7 @@ def instance(cfg: int, seed: int, n: int | None = None, m: int | None = None,
         c["cap"] = cap
     H = ring_hypergraph(c["n"], c["m"], c["dist"], c["cap"], c["window"], c["w_range"],
                         c["c_range"], seed)
-    out = dict(cfg=c, H=H, seed=seed)
+    out = dict(workload=c, H=H, seed=seed)
     if c["k"] == 2:
         out["part"] = halves(c["n"])
         out["region"] = region_near_cuts(c["n"], c["radius"])

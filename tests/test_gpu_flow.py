@@ -104,8 +104,8 @@ def test_hand_fixture(hfp, ctx):
 
 
 @pytest.mark.parametrize("seed", list(range(1, 101)))
-def test_config1_flow_and_cuts(hfp, ctx, seed):
-    inst = synth.instance(1, seed)
+def test_ring4096_flow_and_cuts(hfp, ctx, seed):
+    inst = synth.instance("ring_n4096_geom", seed)
     H, part, region = inst["H"], inst["part"], inst["region"]
     gnet = _gpu_net(hfp, ctx, H, part, region)
     onet = oracle.build_network(H, part, region)
@@ -202,7 +202,7 @@ def test_invalid_inputs(hfp, ctx):
 
 def test_device_inputs_match_host_inputs(hfp, ctx):
     torch = pytest.importorskip("torch")
-    inst = synth.instance(1, 7)
+    inst = synth.instance("ring_n4096_geom", 7)
     H, part, region = inst["H"], inst["part"], inst["region"]
     dev = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a).astype(dt)).cuda()
     gnet = hfp.build_flow_network(ctx, dev(H.net_off.view(np.int32), np.int32),
@@ -247,9 +247,10 @@ def test_flowcutter_random(hfp, ctx):
 
 
 @pytest.mark.parametrize("seed", [1, 2, 3])
-def test_flowcutter_config3_scaled(hfp, ctx, seed):
-    """Config-3 generator (vertex weights 1..4, eps 0.03) at n = 20,000."""
-    inst = synth.instance(3, seed, n=20000, m=30000, radius=2000)
+def test_flowcutter_ring_weighted_scaled(hfp, ctx, seed):
+    """The 500k-vertex FlowCutter workload's generator (vertex weights 1..4,
+    eps 0.03) at n = 20,000."""
+    inst = synth.instance("ring_n500k_zipf_fc", seed, n=20000, m=30000, radius=2000)
     o = _fc_compare(hfp, ctx, inst["H"], inst["part"], inst["region"], seed=seed)
     assert o.status == oracle.OK
 
@@ -294,7 +295,7 @@ def test_pierce_and_augment_explicit(hfp, ctx):
 
 
 def test_deterministic_runs(hfp, ctx):
-    inst = synth.instance(1, 42)
+    inst = synth.instance("ring_n4096_geom", 42)
     H, part, region = inst["H"], inst["part"], inst["region"]
     runs = []
     for _ in range(3):

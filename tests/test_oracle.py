@@ -144,17 +144,17 @@ def test_scipy_maxflow_agreement():
         assert oracle.max_flow_min_cut(net).flow == _scipy_lawler_value(net)
 
 
-def test_scipy_config1():
-    I = synth.instance(1, 3)
+def test_scipy_ring4096():
+    I = synth.instance("ring_n4096_geom", 3)
     net = oracle.build_network(I["H"], I["part"], I["region"])
     assert oracle.max_flow_min_cut(net).flow == _scipy_lawler_value(net)
 
 
 def test_dinic_vs_edmonds_karp():
     """Two independent textbook routines reach the same (unique) value and
-    cut sides; config 1 instances and random ones."""
+    cut sides; 4096-vertex ring instances and random ones."""
     nets = [oracle.build_network(I["H"], I["part"], I["region"])
-            for I in (synth.instance(1, s) for s in (1, 2))]
+            for I in (synth.instance("ring_n4096_geom", s) for s in (1, 2))]
     nets += [n for *_, n in _random_nets(3, 40, n_hi=60, m_hi=90)]
     for net in nets:
         a = oracle.max_flow_min_cut(net, "dinic")

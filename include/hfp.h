@@ -117,6 +117,8 @@ typedef struct {
  * Creates a context on CUDA device `device`.  `stream` is a cudaStream_t
  * (NULL = the legacy default stream); the context does not own it. */
 hfp_status hfp_ctx_create(hfp_ctx** ctx, int device, void* stream);
+/* Releases the caller's handle; networks built from the context stay usable
+ * and the context is freed with the last of them. */
 void hfp_ctx_destroy(hfp_ctx* ctx);
 /* Message of the calling thread's last failed call ("" if none). */
 const char* hfp_last_error(void);

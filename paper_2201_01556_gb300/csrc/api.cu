@@ -77,6 +77,7 @@ int map_dev_err(int e) {
 }  // namespace
 
 struct hfp_ctx {
+  std::atomic<int> refs{1};        // the caller's handle + one per live network
   int device = 0;
   cudaStream_t stream = nullptr;
   int sms = 0;
@@ -253,8 +254,10 @@ HFP_API hfp_status hfp_ctx_create(hfp_ctx** out, int device, void* stream) {
   return HFP_OK;
 }
 
-HFP_API void hfp_ctx_destroy(hfp_ctx* c) {
-  if (!c) return;
+// A context is freed when its caller has destroyed it and no network built
+// from it is alive any more.
+static void ctx_release(hfp_ctx* c) {
+  if (c->refs.fetch_sub(1) != 1) return;
   cudaSetDevice(c->device);
   cudaStreamSynchronize(c->stream);
   if (c->pinned_ctl) cudaFreeHost(c->pinned_ctl);
@@ -264,14 +267,20 @@ HFP_API void hfp_ctx_destroy(hfp_ctx* c) {
   delete c;
 }
 
+HFP_API void hfp_ctx_destroy(hfp_ctx* c) {
+  if (c) ctx_release(c);
+}
+
 HFP_API void hfp_net_destroy(hfp_net* net) {
   if (!net) return;
-  cudaSetDevice(net->ctx->device);
-  cudaStream_t st = net->ctx->stream;
+  hfp_ctx* c = net->ctx;
+  cudaSetDevice(c->device);
+  cudaStream_t st = c->stream;
   if (net->arena) cudaFreeAsync(net->arena, st);
   if (net->dev_nodes) cudaFreeAsync(net->dev_nodes, st);
   cudaStreamSynchronize(st);
   delete net;
+  ctx_release(c);
 }
 
 HFP_API hfp_status hfp_build_flow_network(hfp_ctx* ctx, const hfp_hypergraph* H, hfp_mem mem,
@@ -425,6 +434,7 @@ HFP_API hfp_status hfp_build_flow_network(hfp_ctx* ctx, const hfp_hypergraph* H,
   // arena for the network and its flow state
   hfp_net* net = new hfp_net();
   net->ctx = ctx;
+  ctx->refs.fetch_add(1);
   net->n_region = n_region;
   std::vector<size_t> sz = {
       sizeof(uint32_t) * (m_net + 1), sizeof(int32_t) * p_net, sizeof(int32_t) * m_net,
@@ -438,7 +448,8 @@ HFP_API hfp_status hfp_build_flow_network(hfp_ctx* ctx, const hfp_hypergraph* H,
   for (size_t b : sz) total += align_up(b);
   cudaError_t ae = cudaMallocAsync(&net->arena, total, st);
   if (ae != cudaSuccess) {
-    delete net;
+    net->arena = nullptr;
+    hfp_net_destroy(net);
     return fail(HFP_ERR_OOM, "cannot allocate %zu bytes for the flow network", total);
   }
   std::vector<char*> ptr;

@@ -213,6 +213,44 @@ hfp_status hfp_flowcutter(hfp_net* net, const hfp_fc_params* params, uint8_t* fi
                           int32_t* pierce_side, int32_t* pierce_node, int32_t pierce_cap,
                           hfp_fc_result* result);
 
+/* --- allocation-free max flow ---------------------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that cannot allocate device memory where they need a flow: code inside a
+ * CUDA stream capture, a plug-in bound to a host application's fixed
+ * device-memory budget or allocator, a loop in which allocation is
+ * forbidden.  It computes what hfp_max_flow + hfp_min_cut_source_side compute
+ * for the flow problem {s} -> {t} of a network, with the same engine kernel,
+ * but keeps all working state in one fixed static device array of 24 MiB
+ * (library-wide, held by every GPU that loads the library until the process
+ * exits).  It calls no cudaMalloc / cudaFree and no allocating library
+ * routine.
+ *   net: the flow network in device memory, in the layout hfp_net_export
+ *        writes (hypernode 0 = s, 1 = t).  It fits when
+ *        47*L + 20*p + 4*m + ~4 KiB <= 24 MiB (L = n_nodes + 2*m_nets Lawler
+ *        nodes, p pins, m nets; e.g. L = 262,144 with p = 524,288);
+ *        larger networks are rejected with HFP_ERR_INVALID.
+ *   flow_value, source_weight: host pointers (may be NULL);
+ *   in_source_lawler[L]: device pointer (may be NULL), 1 for nodes of S_r.
+ * The first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture begins.
+ * Every call shares the array and clears what it uses; calls that overlap on
+ * the GPU race, so serialise them.  The call synchronises `stream`. */
+typedef struct {
+  int32_t n_nodes;
+  int32_t m_nets;
+  int64_t p_pins;
+  const uint32_t* net_off;   /* m_nets + 1 */
+  const int32_t* pins;       /* p_pins */
+  const int32_t* net_w;      /* m_nets */
+  const uint32_t* node_off;  /* n_nodes + 1 */
+  const int32_t* inc_slot;   /* p_pins: pin slots of each hypernode */
+  const int32_t* node_w;     /* n_nodes */
+} hfp_flow_network_view;
+
+hfp_status hfp_max_flow_noalloc(int device, void* stream, const hfp_flow_network_view* net,
+                                int64_t* flow_value, uint8_t* in_source_lawler,
+                                int64_t* source_weight);
+
 #ifdef __cplusplus
 }
 #endif

@@ -76,6 +76,11 @@ int map_dev_err(int e) {
 
 }  // namespace
 
+namespace hfp {
+// error message setter for entry points defined in other translation units
+void set_last_error(const char* msg) { g_err = msg; }
+}  // namespace hfp
+
 struct hfp_ctx {
   std::atomic<int> refs{1};        // the caller's handle + one per live network
   int device = 0;

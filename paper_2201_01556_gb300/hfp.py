@@ -47,6 +47,14 @@ class _Stats(ctypes.Structure):
                  "node_visits", "pushes", "engine_launches", "engine_ns")]
 
 
+class _NetworkView(ctypes.Structure):
+    _fields_ = [("n_nodes", ctypes.c_int32), ("m_nets", ctypes.c_int32),
+                ("p_pins", ctypes.c_int64), ("net_off", ctypes.c_void_p),
+                ("pins", ctypes.c_void_p), ("net_w", ctypes.c_void_p),
+                ("node_off", ctypes.c_void_p), ("inc_slot", ctypes.c_void_p),
+                ("node_w", ctypes.c_void_p)]
+
+
 class FcParams(ctypes.Structure):
     _fields_ = [("max_block_weight", ctypes.c_int64), ("flow_bound", ctypes.c_int64),
                 ("seed", ctypes.c_uint32), ("max_iterations", ctypes.c_int32)]
@@ -89,6 +97,7 @@ def load():
         "hfp_pierce_and_augment": (i32, [P, i32, P, i32, ctypes.POINTER(FcParams), P, P]),
         "hfp_flowcutter": (i32, [P, ctypes.POINTER(FcParams), P, P, P, i32,
                                  ctypes.POINTER(_FcResult)]),
+        "hfp_max_flow_noalloc": (i32, [i32, P, ctypes.POINTER(_NetworkView), P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -212,6 +221,36 @@ def net_export(net: Net) -> dict:
                                                     ("net_off", "pins", "net_w", "net_gid",
                                                      "node_w", "node_off", "inc_slot", "dist")]))
     return out
+
+
+def net_export_device(net: Net) -> dict:
+    """hfp_net_export into CUDA int32 tensors (the layout hfp_max_flow_noalloc
+    reads)."""
+    import torch
+    i = net.info
+    z = lambda k: torch.zeros(max(k, 1), dtype=torch.int32, device=f"cuda:{net.ctx.device}")
+    out = dict(net_off=z(i.m_nets + 1), pins=z(i.p_pins), net_w=z(i.m_nets),
+               node_w=z(i.n_nodes), node_off=z(i.n_nodes + 1), inc_slot=z(i.p_pins))
+    _check(load().hfp_net_export(net.h, MEM_DEVICE, _ptr(out["net_off"]), _ptr(out["pins"]),
+                                 _ptr(out["net_w"]), None, _ptr(out["node_w"]),
+                                 _ptr(out["node_off"]), _ptr(out["inc_slot"]), None))
+    return out
+
+
+def max_flow_noalloc(device: int, stream: int, view: dict, n_nodes: int, m_nets: int,
+                     p_pins: int, in_source_lawler=None):
+    """hfp_max_flow_noalloc: max flow and S_r without any allocation in the
+    call.  view holds CUDA tensors in hfp_net_export's layout.  Returns
+    (flow value, c(S_r))."""
+    v = _NetworkView(n_nodes, m_nets, p_pins, _ptr(view["net_off"]), _ptr(view["pins"]),
+                     _ptr(view["net_w"]), _ptr(view["node_off"]), _ptr(view["inc_slot"]),
+                     _ptr(view["node_w"]))
+    flow = ctypes.c_int64()
+    w = ctypes.c_int64()
+    _check(load().hfp_max_flow_noalloc(device, ctypes.c_void_p(stream or 0), ctypes.byref(v),
+                                       ctypes.byref(flow), _ptr(in_source_lawler),
+                                       ctypes.byref(w)))
+    return int(flow.value), int(w.value)
 
 
 def net_stats(net: Net) -> dict:

@@ -157,6 +157,19 @@ hfp_status hfp_net_export(hfp_net* net, hfp_mem mem, uint32_t* net_off, int32_t*
                           int32_t* inc_slot, int32_t* dist);
 hfp_status hfp_net_get_stats(hfp_net* net, hfp_stats* stats);
 
+/* --- tracing ----------------------------------------------------------------
+ * hfp_net_enable_trace keeps a per-round trace of the next `rounds` discharge
+ * rounds (allocates 16 bytes per round on the device).  hfp_net_get_trace
+ * copies to host memory: state_ns[10] / state_cnt[10], the device time
+ * (globaltimer) spent in, and the number of, engine phases of each state
+ * (0 done, 1 push, 2 relabel/apply, 3/4 global relabel init/level, 5/6 S_r
+ * init/level, 7/8 distance init/level); trace[2 * cap] pairs
+ * (frontier << 32 | next-list size, flow value) per round; *n rounds
+ * recorded. */
+hfp_status hfp_net_enable_trace(hfp_net* net, int32_t rounds);
+hfp_status hfp_net_get_trace(hfp_net* net, uint64_t* state_ns, uint64_t* state_cnt,
+                             uint64_t* trace, int32_t cap, int32_t* n);
+
 /* --- maximum flow (Section 8) ---------------------------------------------
  * Augments the network's current flow to a maximum preflow with respect to
  * its current source set S and sink set T (initially {s} and {t}); on return

@@ -108,6 +108,7 @@ struct hfp_net {
   bool labels_exact = false;
   bool sr_valid = false;
   bool dist_ready = false;
+  void* trace_buf = nullptr;
   uint64_t launches = 0;
   uint64_t engine_ns = 0;
 };
@@ -255,6 +256,8 @@ HFP_API hfp_status hfp_ctx_create(hfp_ctx** out, int device, void* stream) {
   c->params.gr_work = 0;           // set per network (a multiple of its node count)
   c->params.stall_rounds = 500;    // Section 8.3, "Avoid Pushing Flow Back"
   c->params.stall_nodes = 1500;
+  c->params.tail_enter = 64;       // CTA 0 alone at or below this frontier size
+  c->params.tail_exit = 192;
   *out = c;
   return HFP_OK;
 }
@@ -283,6 +286,7 @@ HFP_API void hfp_net_destroy(hfp_net* net) {
   cudaStream_t st = c->stream;
   if (net->arena) cudaFreeAsync(net->arena, st);
   if (net->dev_nodes) cudaFreeAsync(net->dev_nodes, st);
+  if (net->trace_buf) cudaFreeAsync(net->trace_buf, st);
   cudaStreamSynchronize(st);
   delete net;
   ctx_release(c);
@@ -538,6 +542,7 @@ HFP_API hfp_status hfp_build_flow_network(hfp_ctx* ctx, const hfp_hypergraph* H,
     launch_incidence(n_nodes, m_net, p_net, nnet_off, npin, node_off, cursor.as<unsigned>(), tot,
                      inc, tmp.as<int2>(), scan_scr.as<unsigned>(), tot + 4, sms, st);
   }
+  launch_heavy_flags(D, sms, st);
   // distances from the original cut: given, or seeded here and completed by
   // the engine on first use (ensure_dist)
   if (d_dist) {
@@ -630,6 +635,44 @@ HFP_API hfp_status hfp_net_get_stats(hfp_net* net, hfp_stats* out) {
   out->pushes = c.pushes;
   out->engine_launches = net->launches;
   out->engine_ns = net->engine_ns;
+  return HFP_OK;
+}
+
+HFP_API hfp_status hfp_net_enable_trace(hfp_net* net, int32_t rounds) {
+  if (!net || rounds < 0) return fail(HFP_ERR_INVALID, "bad trace arguments");
+  hfp_status s = set_device(net->ctx);
+  if (s != HFP_OK) return s;
+  cudaStream_t st = net->ctx->stream;
+  if (net->trace_buf) CK(cudaFreeAsync(net->trace_buf, st));
+  net->trace_buf = nullptr;
+  net->d.trace = nullptr;
+  net->d.trace_cap = 0;
+  if (rounds > 0) {
+    CK(cudaMallocAsync(&net->trace_buf, sizeof(unsigned long long) * 2 * (size_t)rounds, st));
+    net->d.trace = (unsigned long long*)net->trace_buf;
+    net->d.trace_cap = (unsigned)rounds;
+  }
+  CK(cudaMemsetAsync(&net->E->c.trace_len, 0, sizeof(unsigned long long), st));
+  CK(cudaStreamSynchronize(st));
+  return HFP_OK;
+}
+
+HFP_API hfp_status hfp_net_get_trace(hfp_net* net, uint64_t* state_ns, uint64_t* state_cnt,
+                                     uint64_t* trace, int32_t cap, int32_t* n) {
+  if (!net) return fail(HFP_ERR_INVALID, "net is NULL");
+  hfp_status s = set_device(net->ctx);
+  if (s != HFP_OK) return s;
+  Ctl c;
+  if ((s = read_ctl(net, &c)) != HFP_OK) return s;
+  if (state_ns) memcpy(state_ns, c.state_ns, sizeof(c.state_ns));
+  if (state_cnt) memcpy(state_cnt, c.state_cnt, sizeof(c.state_cnt));
+  int32_t len = (int32_t)c.trace_len;
+  if (n) *n = len;
+  if (trace && cap > 0 && len > 0 && net->trace_buf) {
+    int32_t k = len < cap ? len : cap;
+    CK(cudaMemcpy(trace, net->trace_buf, sizeof(unsigned long long) * 2 * (size_t)k,
+                  cudaMemcpyDeviceToHost));
+  }
   return HFP_OK;
 }
 

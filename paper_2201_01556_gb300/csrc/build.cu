@@ -332,6 +332,21 @@ __global__ void k_dist_seed(int32_t n_nodes, const int32_t* dist_tmp, int32_t* d
     dist[u] = u < 2 ? 0 : (dist_tmp[u - 2] == 1 ? 1 : -1);
 }
 
+// heavy bit: nodes with more arc groups than a lane handles go to a warp
+__global__ void k_heavy_flags(const NetDev N) {
+  const int nh = N.n_nodes, m = N.m_nets;
+  for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < N.NL; x += gridDim.x * blockDim.x) {
+    unsigned items;
+    if (x < nh) {
+      items = N.node_off[x + 1] - N.node_off[x];
+    } else {
+      const int e = x < nh + m ? x - nh : x - nh - m;
+      items = 1 + N.net_off[e + 1] - N.net_off[e];
+    }
+    if (items > (unsigned)kLightItems) N.flags[x] |= kHeavy;
+  }
+}
+
 // export copy: unreached vertices get the far distance
 __global__ void k_dist_export(int32_t n_nodes, const int32_t* dist, int32_t* out) {
   for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < n_nodes; u += gridDim.x * blockDim.x) {
@@ -446,6 +461,11 @@ void launch_incidence(int32_t n_nodes, int32_t m_net, unsigned p, const uint32_t
 void launch_dist_seed(int32_t n_nodes, const int32_t* dist_tmp, int32_t* dist, int sms,
                       cudaStream_t st) {
   k_dist_seed<<<blocks_for(n_nodes, 256, sms * 8), 256, 0, st>>>(n_nodes, dist_tmp, dist);
+  count_launches(1);
+}
+
+void launch_heavy_flags(const NetDev& N, int sms, cudaStream_t st) {
+  k_heavy_flags<<<blocks_for(N.NL, 256, sms * 8), 256, 0, st>>>(N);
   count_launches(1);
 }
 

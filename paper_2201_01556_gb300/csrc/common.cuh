@@ -20,6 +20,13 @@ constexpr int kWarp = 32;
 // per Lawler node flag bits (flags[])
 constexpr uint8_t kSource = 1;
 constexpr uint8_t kSink = 2;
+constexpr uint8_t kHeavy = 4;      // more than kLightItems arc groups: a warp per node
+constexpr uint8_t kTerminal = kSource | kSink;
+
+// A node is light when its arc scan has at most kLightItems steps (a
+// hypernode's incidences; a net node's bridge plus pins); light nodes are
+// handled one per lane, heavy ones one per warp.
+constexpr int kLightItems = 16;
 
 // device error codes (ctl->err); host maps them to hfp_status
 constexpr int kDevOk = 0;
@@ -51,12 +58,12 @@ struct NetDev {
   uint8_t* needrl;
   uint8_t* insr;                // forward residual reachability (S_r)
   int32_t* list[4];             // frontier, next, relabeled, BFS lists (NL each)
+  unsigned long long* trace;    // per-round trace (2 words per round), may be null
+  unsigned int trace_cap;       // rounds the trace can hold
 };
 
 struct Ctl {
   unsigned long long flow;      // flow value: excess that reached the sinks
-  unsigned int bar_count;       // grid barrier arrivals
-  unsigned int bar_gen;         // grid barrier generation
   int err;                      // kDev* code, first error wins
   int err_where;
   unsigned long long rounds, global_relabels, gr_levels;
@@ -70,6 +77,10 @@ struct Ctl {
   unsigned long long best_key;  // piercing candidate selection
   int best_node;
   int pad;
+  // tracing: device time between grid barriers, by engine state (globaltimer)
+  unsigned long long state_ns[10];
+  unsigned long long state_cnt[10];
+  unsigned long long trace_len;   // entries written to the round trace
 };
 
 __device__ __forceinline__ unsigned long long globaltimer() {

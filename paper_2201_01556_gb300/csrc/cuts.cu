@@ -9,49 +9,84 @@ constexpr unsigned FULLC = 0xffffffffu;
 
 // Engine state before a cooperative launch.  SETUP_PREP only opens a fresh
 // stamp epoch and empties the frontier so that k_saturate can fill it.
+__device__ void zero_phase_counters(EngineCtl& X) {
+  for (int l = 0; l < C_COUNT; l++)
+    for (int k = 0; k < 3; k++) X.cnt3[l][k] = 0;
+  for (int k = 0; k < 3; k++) {
+    X.flow3[k] = 0;
+    X.w3[k] = 0;
+  }
+  X.gr_act[0] = 0;
+  X.gr_act[1] = 0;
+}
+
 __global__ void k_engine_setup(EngineCtl* E, int mode) {
   EngineCtl& X = *E;
-  X.c.bar_count = 0;
+  X.bar_count = 0;
   X.c.err = kDevOk;
   X.c.err_where = 0;
   switch (mode) {
     case SETUP_GR:
-      X.c.global_relabels++;
+      zero_phase_counters(X);
+      X.s.grs++;
       X.s.state = ST_GR_INIT;
-      X.s.final_gr = 0;
       X.s.after_gr_exit = 0;
-      X.cnt[L_BFS] = 0;
-      X.cnt[L_FRONT] = 0;
-      X.cnt[L_NEXT] = 0;
-      X.cnt[L_RELAB] = 0;
-      X.c.wT = 0;
+      X.s.wT = 0;
+      X.s.wT_set = 1;
       break;
     case SETUP_ROUND:
+      zero_phase_counters(X);
       // fresh epoch: the frontier was stamped by k_saturate under the last one
       X.s.epoch++;
       X.s.state = ST_ROUND_A;
-      X.s.fcnt = X.cnt[L_FRONT];
-      X.cnt[L_FRONT] = 0;
+      X.s.fcnt = X.cnt[0];
+      X.s.fcnth = X.cnt[1];
+      X.cnt[0] = 0;
+      X.cnt[1] = 0;
       X.s.rcnt = 0;
-      X.cnt[L_NEXT] = 0;
-      X.cnt[L_RELAB] = 0;
-      X.round_flow_ref = X.c.flow;
-      X.c.stall_rounds = 0;
+      X.s.flow_ref = X.c.flow;
+      X.s.stall = 0;
       break;
     case SETUP_SR:
+      zero_phase_counters(X);
       X.s.state = ST_SR_INIT;
       X.s.epoch++;
-      X.cnt[L_BFS] = 0;
-      X.c.wS = 0;
+      X.s.wS = 0;
+      X.s.wS_set = 1;
       break;
     case SETUP_PREP:
       X.s.epoch++;
-      X.cnt[L_FRONT] = 0;
+      X.cnt[0] = 0;
+      X.cnt[1] = 0;
       break;
     case SETUP_DIST:
+      zero_phase_counters(X);
       X.s.state = ST_DIST_INIT;
-      X.cnt[L_BFS] = 0;
       break;
+  }
+}
+
+// frontier append outside the engine: light nodes from the front of the list,
+// heavy ones from the back (the engine's split-list layout)
+__device__ __forceinline__ void front_append(bool want, int y, bool heavy, const NetDev& N,
+                                             EngineCtl* E) {
+  const unsigned lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  const unsigned ml = __ballot_sync(FULLC, want && !heavy);
+  const unsigned mh = __ballot_sync(FULLC, want && heavy);
+  if (ml) {
+    const int ld = __ffs(ml) - 1;
+    unsigned pos = 0;
+    if ((int)lane == ld) pos = atomicAdd(&E->cnt[0], (unsigned)__popc(ml));
+    pos = __shfl_sync(FULLC, pos, ld);
+    if (want && !heavy) N.list[L_FRONT][pos + __popc(ml & lt)] = y;
+  }
+  if (mh) {
+    const int ld = __ffs(mh) - 1;
+    unsigned pos = 0;
+    if ((int)lane == ld) pos = atomicAdd(&E->cnt[1], (unsigned)__popc(mh));
+    pos = __shfl_sync(FULLC, pos, ld);
+    if (want && heavy) N.list[L_FRONT][N.NL - 1 - (pos + __popc(mh & lt))] = y;
   }
 }
 
@@ -70,7 +105,7 @@ __global__ void k_saturate(const NetDev N, EngineCtl* E, const int32_t* nodes, i
     unsigned long long sink_acc = 0;
     for (unsigned j0 = beg + (threadIdx.x - lane); j0 < end; j0 += blockDim.x) {
       const unsigned j = j0 + lane;
-      bool a1 = false, a2 = false;
+      bool a1 = false, a2 = false, h1 = false, h2 = false;
       int y1 = -1, y2 = -1;
       if (j < end) {
         int2 it = N.inc[j];
@@ -81,6 +116,8 @@ __global__ void k_saturate(const NetDev N, EngineCtl* E, const int32_t* nodes, i
         const int d1 = w - N.f_in[p];
         const int d2 = N.f_out[p];
         const uint8_t f1 = N.flags[y1], f2 = N.flags[y2];
+        h1 = (f1 & kHeavy) != 0;
+        h2 = (f2 & kHeavy) != 0;
         if (d1 > 0 && !(f1 & kSource)) {
           N.f_in[p] = w;
           if (f1 & kSink) sink_acc += d1;
@@ -98,8 +135,8 @@ __global__ void k_saturate(const NetDev N, EngineCtl* E, const int32_t* nodes, i
           }
         }
       }
-      warp_append(a1, y1, N.list[L_FRONT], &E->cnt[L_FRONT]);
-      warp_append(a2, y2, N.list[L_FRONT], &E->cnt[L_FRONT]);
+      front_append(a1, y1, h1, N, E);
+      front_append(a2, y2, h2, N, E);
     }
     if (sink_acc) atomicAdd(&E->c.flow, sink_acc);
   }
@@ -117,7 +154,7 @@ __global__ void k_mark_sources(const NetDev N, const int32_t* extra, int32_t cou
     } else {
       y = extra[x - NL];
     }
-    N.flags[y] = kSource;
+    N.flags[y] = (N.flags[y] & kHeavy) | kSource;
     N.lab0[y] = NL;
     N.lab1[y] = NL;
     N.excess[y] = 0;
@@ -142,7 +179,7 @@ __global__ void k_mark_sinks(const NetDev N, EngineCtl* E, const int32_t* extra,
     long long ex = N.excess[y];
     if (ex > 0) acc += (unsigned long long)ex;
     N.excess[y] = 0;
-    N.flags[y] = kSink;
+    N.flags[y] = (N.flags[y] & kHeavy) | kSink;
   }
   if (acc) atomicAdd(&E->c.flow, acc);
 }

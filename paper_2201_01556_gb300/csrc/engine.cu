@@ -1,8 +1,16 @@
 // Persistent flow engine: synchronous push-relabel on the Lawler expansion,
 // simulated directly on the flow hypergraph, with global relabeling and the
 // residual BFS of the source-side cut.  One cooperative launch runs the whole
-// loop; every grid barrier ends with a serial section (run by the last CTA to
-// arrive) that snapshots the list counters and picks the next state.
+// loop.  Every CTA derives the next state itself from the counters of the
+// phase that just ended (the counters rotate through three slots, so none is
+// reset while it is read or written); small frontiers are discharged by CTA 0
+// alone with block barriers while the other CTAs wait.
+//
+// Light nodes (at most kLightItems arc groups) are handled one per lane: a
+// warp walks the arcs of its 32 nodes in lockstep, so list appends stay
+// warp-aggregated.  Heavy nodes (large nets, high-degree vertices) get a
+// whole warp, which scans 32 arcs per step and places pushes by an inclusive
+// scan of residual capacities.
 //
 // Method (Section 8 of the paper, "Parallel Maximum Flow Algorithm"):
 //  - rounds discharge all active nodes in parallel against the labels and
@@ -31,192 +39,287 @@
 // times, the push-relabel conflict of Section 8.2 cannot occur, and no
 // winning criterion is needed: an arc can only be admissible in one
 // direction under one labelling.  The run is deterministic.
+#include <climits>
+
 #include "kernels.cuh"
 
 namespace hfp {
 
 constexpr unsigned FULL = 0xffffffffu;
+constexpr int kTeam = 8;   // lanes per light node
 
 struct Acc {
   long long w;                 // hypernode weight found in this phase
   unsigned long long hyper, net, nodes, pushes;
 };
 
+// Iteration space of a phase: the whole grid, or CTA 0 alone in the tail.
+// Light nodes go to 8-lane teams over all warps; heavy nodes to whole CTAs
+// (block b takes heavy nodes b, b + nblocks, ...).
+struct Team {
+  unsigned gwarp, nwarps, tid, nth, block, nblocks;
+};
+
+// Append counters and accumulators of the current phase (slot phase % 3).
+struct Slot {
+  unsigned* c[C_COUNT];
+  unsigned long long* flow;
+};
+
 __device__ __forceinline__ int32_t* lab_cur(const NetDev& N, int lp) { return lp ? N.lab1 : N.lab0; }
 
-// ---------------------------------------------------------------------------
-// serial section: runs in exactly one thread while the rest of the grid waits
-__device__ void begin_gr(EngineCtl* E, int final_gr) {
-  E->c.global_relabels++;
-  E->s.state = ST_GR_INIT;
-  E->s.final_gr = final_gr;
-  E->cnt[L_BFS] = 0;
-  E->cnt[L_FRONT] = 0;
-  E->c.wT = 0;
+__device__ __forceinline__ unsigned warp_max_u(unsigned v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(FULL, v, o));
+  return v;
 }
 
-__device__ void control(EngineCtl* E, const NetDev& N, const Params& P) {
-  Sched& s = E->s;
-  Ctl& c = E->c;
-  switch (s.state) {
+// Warp-aggregated append to a split list: light values at
+// list[base_l + i], heavy values at list[NL - 1 - (base_h + i)].  All 32
+// lanes must call it together.
+__device__ __forceinline__ void append_split(bool want, int32_t value, bool heavy, int32_t* list,
+                                             unsigned* cl, unsigned* ch, unsigned base_l,
+                                             unsigned base_h, int NL) {
+  const unsigned lane = lane_id();
+  const unsigned lt = (1u << lane) - 1u;
+  const unsigned ml = __ballot_sync(FULL, want && !heavy);
+  const unsigned mh = __ballot_sync(FULL, want && heavy);
+  if (ml) {
+    const int leader = __ffs(ml) - 1;
+    unsigned pos = 0;
+    if ((int)lane == leader) pos = atomicAdd(cl, (unsigned)__popc(ml));
+    pos = __shfl_sync(FULL, pos, leader);
+    if (want && !heavy) list[base_l + pos + __popc(ml & lt)] = value;
+  }
+  if (mh) {
+    const int leader = __ffs(mh) - 1;
+    unsigned pos = 0;
+    if ((int)lane == leader) pos = atomicAdd(ch, (unsigned)__popc(mh));
+    pos = __shfl_sync(FULL, pos, leader);
+    if (want && heavy) list[NL - 1 - (base_h + pos + __popc(mh & lt))] = value;
+  }
+}
+
+__device__ __forceinline__ void append_plain(bool want, int32_t value, int32_t* list,
+                                             unsigned* cnt, unsigned base) {
+  const unsigned m = __ballot_sync(FULL, want);
+  if (!m) return;
+  const unsigned lane = lane_id();
+  const int leader = __ffs(m) - 1;
+  unsigned pos = 0;
+  if ((int)lane == leader) pos = atomicAdd(cnt, (unsigned)__popc(m));
+  pos = __shfl_sync(FULL, pos, leader);
+  if (want) list[base + pos + __popc(m & ((1u << lane) - 1u))] = value;
+}
+
+// Arc-group layout of node x: kind 0 hypernode (groups = incidences), kind 1
+// in-node, kind 2 out-node (group 0 = bridge, group k = pin slot beg + k - 1).
+struct NodeArcs {
+  int kind, e;
+  unsigned beg, items;
+};
+
+__device__ __forceinline__ NodeArcs node_arcs(const NetDev& N, int x) {
+  NodeArcs r;
+  const int nh = N.n_nodes, m = N.m_nets;
+  if (x < nh) {
+    r.kind = 0;
+    r.e = 0;
+    r.beg = N.node_off[x];
+    r.items = N.node_off[x + 1] - r.beg;
+  } else {
+    r.kind = x < nh + m ? 1 : 2;
+    r.e = r.kind == 1 ? x - nh : x - nh - m;
+    r.beg = N.net_off[r.e];
+    r.items = 1 + (N.net_off[r.e + 1] - r.beg);
+  }
+  return r;
+}
+
+// ---------------------------------------------------------------------------
+// Control: every CTA's thread 0 runs this after each barrier on its own copy
+// of the state, with the counters of the phase that ended.  The decisions
+// only depend on values that no CTA changes during the next phase, so all
+// copies stay identical.
+struct Snap {
+  unsigned c[C_COUNT];
+  unsigned act, acth;
+  unsigned long long flow;
+  long long w;
+};
+
+__device__ void begin_gr(Sched& L) {
+  L.grs++;
+  L.state = ST_GR_INIT;
+  L.wT = 0;
+  L.wT_set = 1;
+}
+
+__device__ void advance(Sched& L, const Snap& q, const Params& P, const NetDev& N, Ctl* c,
+                        bool trace_writer) {
+  switch (L.state) {
     case ST_ROUND_A:
-      s.ncnt = E->cnt[L_NEXT];
-      E->cnt[L_NEXT] = 0;
-      s.state = ST_ROUND_B;
+      L.ncnt = q.c[C_NEXT];
+      L.ncnth = q.c[C_NEXTH];
+      L.flow += q.flow;
+      L.state = ST_ROUND_B;
       break;
     case ST_ROUND_B: {
-      c.rounds++;
-      c.work_since_gr += (unsigned long long)s.fcnt + s.ncnt;
-      s.fcnt = E->cnt[L_FRONT];
-      E->cnt[L_FRONT] = 0;
-      s.rcnt = E->cnt[L_RELAB];
-      E->cnt[L_RELAB] = 0;
-      s.lp ^= 1;
-      s.epoch++;
-      if (c.flow != E->round_flow_ref || s.fcnt >= P.stall_nodes) {
-        E->round_flow_ref = c.flow;
-        c.stall_rounds = 0;
-      } else {
-        c.stall_rounds++;
+      const unsigned fprev = L.fcnt + L.fcnth, nprev = L.ncnt + L.ncnth;
+      if (trace_writer && N.trace && c->trace_len < N.trace_cap) {
+        // round trace: (frontier size << 32 | next-list size), flow value
+        N.trace[2 * c->trace_len] = ((unsigned long long)fprev << 32) | nprev;
+        N.trace[2 * c->trace_len + 1] = L.flow;
+        c->trace_len++;
       }
-      if (s.fcnt == 0) {
-        begin_gr(E, 1);
-      } else if (c.rounds >= P.max_rounds) {
-        c.err = kDevIterLimit;
-        s.state = ST_DONE;
-      } else if (c.work_since_gr >= P.gr_work || c.stall_rounds >= P.stall_rounds) {
-        begin_gr(E, 0);
+      L.rounds++;
+      L.work += (unsigned long long)fprev + nprev;
+      L.fcnt = q.c[C_FRONT];
+      L.fcnth = q.c[C_FRONTH];
+      L.rcnt = q.c[C_RELAB];
+      L.lp ^= 1;
+      L.epoch++;
+      const unsigned f = L.fcnt + L.fcnth;
+      if (L.flow != L.flow_ref || f >= P.stall_nodes) {
+        L.flow_ref = L.flow;
+        L.stall = 0;
       } else {
-        s.state = ST_ROUND_A;
+        L.stall++;
+      }
+      if (f == 0) {
+        begin_gr(L);
+      } else if (L.rounds >= P.max_rounds) {
+        atomicCAS(&c->err, kDevOk, kDevIterLimit);
+        L.state = ST_DONE;
+      } else if (L.work >= P.gr_work || L.stall >= P.stall_rounds) {
+        begin_gr(L);
+      } else {
+        L.state = f <= P.tail_enter ? ST_TAIL : ST_ROUND_A;
       }
       break;
     }
     case ST_GR_INIT:
-      s.bfs_begin = 0;
-      s.bfs_end = E->cnt[L_BFS];
-      s.level = 0;
-      s.state = ST_GR_LEVEL;
-      break;
-    case ST_GR_LEVEL: {
-      unsigned e = E->cnt[L_BFS];
-      c.gr_levels++;
-      if (e == s.bfs_end) {
-        E->cnt[L_BFS] = 0;
-        s.fcnt = E->cnt[L_FRONT];
-        E->cnt[L_FRONT] = 0;
-        s.rcnt = 0;
-        E->cnt[L_RELAB] = 0;
-        E->cnt[L_NEXT] = 0;
-        s.lp = 0;
-        s.epoch++;
-        c.work_since_gr = 0;
-        c.stall_rounds = 0;
-        E->round_flow_ref = c.flow;
-        s.state = (s.fcnt == 0 || s.after_gr_exit) ? ST_DONE : ST_ROUND_A;
-      } else {
-        s.bfs_begin = s.bfs_end;
-        s.bfs_end = e;
-        s.level++;
-      }
-      break;
-    }
     case ST_SR_INIT:
-      s.bfs_begin = 0;
-      s.bfs_end = E->cnt[L_BFS];
-      s.level = 0;
-      s.state = ST_SR_LEVEL;
-      break;
-    case ST_SR_LEVEL: {
-      unsigned e = E->cnt[L_BFS];
-      if (e == s.bfs_end) {
-        E->cnt[L_BFS] = 0;
-        s.epoch++;
-        s.state = ST_DONE;
-      } else {
-        s.bfs_begin = s.bfs_end;
-        s.bfs_end = e;
-        s.level++;
-      }
-      break;
-    }
     case ST_DIST_INIT:
-      s.bfs_begin = 0;
-      s.bfs_end = E->cnt[L_BFS];
-      s.level = 0;
-      s.state = ST_DIST_LEVEL;
+      L.bfs_begin = 0;
+      L.bfs_end = q.c[C_BFS];
+      L.bfsh_begin = 0;
+      L.bfsh_end = q.c[C_BFSH];
+      L.level = 0;
+      if (L.state == ST_GR_INIT) L.wT += q.w;
+      if (L.state == ST_SR_INIT) L.wS += q.w;
+      L.state = L.state == ST_GR_INIT ? ST_GR_LEVEL
+                : L.state == ST_SR_INIT ? ST_SR_LEVEL : ST_DIST_LEVEL;
       break;
+    case ST_GR_LEVEL:
+    case ST_SR_LEVEL:
     case ST_DIST_LEVEL: {
-      unsigned e = E->cnt[L_BFS];
-      if (e == s.bfs_end) {
-        E->cnt[L_BFS] = 0;
-        s.state = ST_DONE;
+      const int st = L.state;
+      if (st == ST_GR_LEVEL) {
+        L.gr_levels++;
+        L.wT += q.w;
+      }
+      if (st == ST_SR_LEVEL) L.wS += q.w;
+      if (q.c[C_BFS] == 0 && q.c[C_BFSH] == 0) {
+        if (st == ST_GR_LEVEL) {
+          L.fcnt = q.act;
+          L.fcnth = q.acth;
+          L.rcnt = 0;
+          L.lp = 0;
+          L.epoch++;
+          L.work = 0;
+          L.stall = 0;
+          L.flow_ref = L.flow;
+          const unsigned f = L.fcnt + L.fcnth;
+          if (f == 0 || L.after_gr_exit) L.state = ST_DONE;
+          else L.state = f <= P.tail_enter ? ST_TAIL : ST_ROUND_A;
+        } else {
+          L.epoch++;
+          L.state = ST_DONE;
+        }
       } else {
-        s.bfs_begin = s.bfs_end;
-        s.bfs_end = e;
-        s.level++;
+        L.bfs_begin = L.bfs_end;
+        L.bfs_end += q.c[C_BFS];
+        L.bfsh_begin = L.bfsh_end;
+        L.bfsh_end += q.c[C_BFSH];
+        L.level++;
       }
       break;
     }
     default:
-      s.state = ST_DONE;
+      L.state = ST_DONE;
   }
 }
 
-// Grid barrier with a serial section.  The wait is bounded by P.timeout_ns of
-// globaltimer; on expiry ctl->err is set and every CTA leaves the loop.
-__device__ bool grid_step(EngineCtl* E, const NetDev& N, const Params& P, Sched* ss,
-                          bool transition, Acc* acc_sh, int acc_target) {
+__device__ __forceinline__ unsigned ld_cg(const unsigned* p) { return *(const volatile unsigned*)p; }
+
+// Snapshot of the counters of the phase with index k (slot k % 3).
+__device__ Snap take_snap(EngineCtl* E, unsigned k) {
+  const unsigned sl = k % 3;
+  Snap q;
+#pragma unroll
+  for (int i = 0; i < C_COUNT; i++) q.c[i] = ld_cg(&E->cnt3[i][sl]);
+  q.act = ld_cg(&E->gr_act[0]);
+  q.acth = ld_cg(&E->gr_act[1]);
+  q.flow = *(const volatile unsigned long long*)&E->flow3[sl];
+  q.w = *(const volatile long long*)&E->w3[sl];
+  return q;
+}
+
+// Zero the slot the next phase will append to.  Only CTA 0 does it (stores
+// of every CTA to the same lines cost more than the whole barrier); the slot
+// was last read before the previous barrier and is next appended to after
+// the coming one.
+__device__ __forceinline__ void clear_slot(EngineCtl* E, unsigned sl, bool gr_init) {
+  for (int l = 0; l < C_COUNT; l++) E->cnt3[l][sl] = 0;
+  E->flow3[sl] = 0;
+  E->w3[sl] = 0;
+  if (gr_init) {
+    E->gr_act[0] = 0;
+    E->gr_act[1] = 0;
+  }
+}
+
+// Count-up grid barrier for a cooperative launch (all CTAs co-resident): a
+// CTA adds one and waits until every CTA has added one for this barrier.  The
+// wait is bounded by P.timeout_ns of globaltimer; on expiry, or once another
+// CTA raised an error, ctl->err is set and false is returned.
+__device__ bool grid_barrier(EngineCtl* E, unsigned target, unsigned long long timeout_ns) {
+  __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
-    if (acc_target == 1 && acc_sh->w) atomicAdd((unsigned long long*)&E->c.wS, (unsigned long long)acc_sh->w);
-    if (acc_target == 2 && acc_sh->w) atomicAdd((unsigned long long*)&E->c.wT, (unsigned long long)acc_sh->w);
-    acc_sh->w = 0;
-    unsigned nb = gridDim.x;
-    unsigned gen = ld_acquire(&E->c.bar_gen);
+    int ok = 1;
     __threadfence();
-    unsigned arrived = atomicAdd(&E->c.bar_count, 1u);
-    if (arrived == nb - 1) {
-      __threadfence();
-      if (transition && ld_volatile_int(&E->c.err) == kDevOk) control(E, N, P);
-      if (ld_volatile_int(&E->c.err) != kDevOk) E->s.state = ST_DONE;
-      atomicExch(&E->c.bar_count, 0u);
-      __threadfence();
-      st_release(&E->c.bar_gen, gen + 1);
-    } else {
-      unsigned long long t0 = globaltimer();
-      unsigned spins = 0;
-      while (ld_acquire(&E->c.bar_gen) == gen) {
-        if (ld_volatile_int(&E->c.err) != kDevOk) break;
-        if ((++spins & 63u) == 0 && globaltimer() - t0 > P.timeout_ns) {
+    atomicAdd(&E->bar_count, 1u);
+    unsigned spins = 0;
+    unsigned long long t0 = 0;
+    while (ld_acquire(&E->bar_count) < target) {
+      if (ld_volatile_int(&E->c.err) != kDevOk) { ok = 0; break; }
+      if ((++spins & 255u) == 0) {
+        const unsigned long long t = globaltimer();
+        if (t0 == 0) t0 = t;
+        else if (t - t0 > timeout_ns) {
           atomicCAS(&E->c.err, kDevOk, kDevTimeout);
           E->c.err_where = 1;
+          ok = 0;
           break;
         }
-        __nanosleep(64);
       }
     }
     __threadfence();
-    const volatile Sched* vs = &E->s;
-    ss->state = vs->state;
-    ss->lp = vs->lp;
-    ss->fcnt = vs->fcnt;
-    ss->ncnt = vs->ncnt;
-    ss->rcnt = vs->rcnt;
-    ss->bfs_begin = vs->bfs_begin;
-    ss->bfs_end = vs->bfs_end;
-    ss->level = vs->level;
-    ss->epoch = vs->epoch;
-    if (ld_volatile_int(&E->c.err) != kDevOk) ss->state = ST_DONE;
+    if (ld_volatile_int(&E->c.err) != kDevOk) ok = 0;
+    s_ok = ok;
   }
   __syncthreads();
-  return ss->state != ST_DONE;
+  return s_ok != 0;
 }
 
 // ---------------------------------------------------------------------------
-// push delivery: returns true when y must be appended to the next list
+// push delivery: returns true when y must join the next list
 __device__ __forceinline__ bool deliver(const NetDev& N, int y, long long d, unsigned epoch,
-                                        long long& sink_acc) {
-  uint8_t fl = N.flags[y];
+                                        long long& sink_acc, bool& heavy) {
+  const uint8_t fl = N.flags[y];
+  heavy = (fl & kHeavy) != 0;
   if (fl & kSink) {
     sink_acc += d;
     return false;
@@ -226,415 +329,681 @@ __device__ __forceinline__ bool deliver(const NetDev& N, int y, long long d, uns
   return atomicExch(&N.stamp[y], epoch) != epoch;
 }
 
-// Discharge of one node by one warp (Section 8.1, one scan of its residual
-// arcs; pushes go on admissible arcs in arc order until the excess is gone).
-__device__ void discharge(const NetDev& N, EngineCtl* E, int x, const int32_t* Lr,
-                          unsigned epoch, unsigned lane, long long& sink_acc, Acc& a) {
+// Team primitives: a team is TW consecutive lanes of a warp (TW = 8 for light
+// nodes, 32 for heavy ones); every lane of the warp must take part.
+template <int TW>
+__device__ __forceinline__ long long team_incl_scan(long long v, unsigned tl) {
+#pragma unroll
+  for (int o = 1; o < TW; o <<= 1) {
+    const long long t = __shfl_up_sync(FULL, v, o, TW);
+    if ((int)tl >= o) v += t;
+  }
+  return v;
+}
+
+template <int TW>
+__device__ __forceinline__ int team_min(int v) {
+#pragma unroll
+  for (int o = TW / 2; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(FULL, v, o, TW));
+  return v;
+}
+
+// Discharge of one node by a team of TW lanes (Section 8.1: one scan of the
+// node's residual arcs in arc order; push min(excess, residual) on every
+// admissible arc until the excess is gone).  TW arc groups per step; pushes
+// are placed by an inclusive scan of residual capacities.  x < 0: idle team.
+template <int TW>
+__device__ void discharge_team(const NetDev& N, int x, const int32_t* Lr, unsigned epoch,
+                               unsigned lane, long long& sink_acc, Acc& a, const Slot& S) {
   const int NL = N.NL, nh = N.n_nodes, m = N.m_nets;
-  const long long ex = N.excess[x];
-  const int dx = Lr[x];
-  if (ex <= 0 || dx >= NL) return;
-  const int dt = dx - 1;
-  long long rem = ex;
-  int32_t* nextl = N.list[L_NEXT];
-  unsigned* ncnt = &E->cnt[L_NEXT];
-  if (x < nh) {
-    // hypernode: arcs (u, e_in) with residual w(e) - f_in, (u, e_out) with f_out
-    const unsigned beg = N.node_off[x], end = N.node_off[x + 1];
-    for (unsigned j0 = beg; j0 < end; j0 += 32) {
-      const unsigned j = j0 + lane;
-      long long r1 = 0, r2 = 0;
-      int e = 0, p = 0, fi = 0, fo = 0;
-      if (j < end) {
-        int2 it = N.inc[j];
-        e = it.x;
-        p = it.y;
-        int w = N.net_w[e];
-        fi = N.f_in[p];
-        fo = N.f_out[p];
-        if (w > fi && Lr[nh + e] == dt) r1 = w - fi;
-        if (fo > 0 && Lr[nh + m + e] == dt) r2 = fo;
-      }
-      const long long r = r1 + r2;
-      const long long incl = warp_incl_scan(r);
-      const long long take = min(max(rem - (incl - r), 0LL), r);
-      const long long t1 = min(take, r1), t2 = take - t1;
-      bool a1 = false, a2 = false;
-      if (t1 > 0) {
-        N.f_in[p] = fi + (int)t1;
-        a1 = deliver(N, nh + e, t1, epoch, sink_acc);
-      }
-      if (t2 > 0) {
-        N.f_out[p] = fo - (int)t2;
-        a2 = deliver(N, nh + m + e, t2, epoch, sink_acc);
-      }
-      a.pushes += (t1 > 0) + (t2 > 0);
-      warp_append(a1, nh + e, nextl, ncnt);
-      warp_append(a2, nh + m + e, nextl, ncnt);
-      a.hyper += (j < end);
-      const long long tot = __shfl_sync(FULL, incl, 31);
-      rem -= min(rem, tot);
-      if (rem == 0) break;
-    }
-  } else if (x < nh + m) {
-    // in-node: bridge (e_in, e_out) with residual w - f_b; (e_in, u) with f_in
-    const int e = x - nh;
-    const unsigned beg = N.net_off[e], end = N.net_off[e + 1];
-    const int w = N.net_w[e], fb = N.f_b[e], eout = nh + m + e;
-    const unsigned items = 1 + (end - beg);
-    for (unsigned i0 = 0; i0 < items; i0 += 32) {
-      const unsigned i = i0 + lane;
-      long long r = 0;
-      int y = -1, fi = 0;
-      unsigned p = 0;
-      if (i == 0) {
-        if (w > fb && Lr[eout] == dt) { r = w - fb; y = eout; }
-      } else if (i < items) {
-        p = beg + i - 1;
-        fi = N.f_in[p];
-        if (fi > 0) {
-          int u = N.pin[p];
-          if (Lr[u] == dt) { r = fi; y = u; }
-        }
-      }
-      const long long incl = warp_incl_scan(r);
-      const long long take = min(max(rem - (incl - r), 0LL), r);
-      bool ap = false;
-      if (take > 0) {
-        if (i == 0) N.f_b[e] = fb + (int)take;
-        else N.f_in[p] = fi - (int)take;
-        ap = deliver(N, y, take, epoch, sink_acc);
-        a.pushes++;
-      }
-      warp_append(ap, y, nextl, ncnt);
-      a.net += (i < items);
-      const long long tot = __shfl_sync(FULL, incl, 31);
-      rem -= min(rem, tot);
-      if (rem == 0) break;
+  const unsigned tl = lane & (TW - 1);
+  long long rem = 0;
+  int dx = NL;
+  if (x >= 0) {
+    rem = N.excess[x];
+    dx = Lr[x];
+  }
+  const bool act = x >= 0 && rem > 0 && dx < NL;
+  NodeArcs g{0, 0, 0, 0};
+  int w = 0, fb = 0;
+  if (act) {
+    g = node_arcs(N, x);
+    if (g.kind) {
+      w = N.net_w[g.e];
+      fb = N.f_b[g.e];
     }
   } else {
-    // out-node: (e_out, e_in) with residual f_b; (e_out, u) uncapacitated
-    const int e = x - nh - m;
-    const unsigned beg = N.net_off[e], end = N.net_off[e + 1];
-    const int fb = N.f_b[e], ein = nh + e;
-    const unsigned items = 1 + (end - beg);
-    for (unsigned i0 = 0; i0 < items; i0 += 32) {
-      const unsigned i = i0 + lane;
-      long long r = 0;
-      int y = -1;
-      unsigned p = 0;
-      if (i == 0) {
-        if (fb > 0 && Lr[ein] == dt) { r = fb; y = ein; }
-      } else if (i < items) {
-        p = beg + i - 1;
-        int u = N.pin[p];
-        if (Lr[u] == dt) { r = rem; y = u; }
+    rem = 0;
+  }
+  const int dt = dx - 1;
+  const unsigned steps = warp_max_u((g.items + TW - 1) / TW);
+  int32_t* nl = N.list[L_NEXT];
+  for (unsigned c = 0; c < steps; c++) {
+    const unsigned k = c * TW + tl;
+    long long r1 = 0, r2 = 0;
+    int y1 = -1, y2 = -1, p = 0, fi = 0, fo = 0;
+    if (rem > 0 && k < g.items) {
+      if (g.kind == 0) {
+        // hypernode: (u, e_in) with residual w(e) - f_in, (u, e_out) with f_out
+        const int2 it = N.inc[g.beg + k];
+        p = it.y;
+        const int ww = N.net_w[it.x];
+        fi = N.f_in[p];
+        fo = N.f_out[p];
+        y1 = nh + it.x;
+        y2 = nh + m + it.x;
+        if (ww > fi && Lr[y1] == dt) r1 = ww - fi;
+        if (fo > 0 && Lr[y2] == dt) r2 = fo;
+        a.hyper++;
+      } else if (g.kind == 1) {
+        // in-node: bridge (e_in, e_out) with residual w - f_b; (e_in, u) with f_in
+        if (k == 0) {
+          y1 = nh + m + g.e;
+          if (w > fb && Lr[y1] == dt) r1 = w - fb;
+        } else {
+          p = g.beg + k - 1;
+          fi = N.f_in[p];
+          if (fi > 0) {
+            y1 = N.pin[p];
+            if (Lr[y1] == dt) r1 = fi;
+          }
+        }
+        a.net++;
+      } else {
+        // out-node: (e_out, e_in) with residual f_b; (e_out, u) uncapacitated
+        if (k == 0) {
+          y1 = nh + g.e;
+          if (fb > 0 && Lr[y1] == dt) r1 = fb;
+        } else {
+          p = g.beg + k - 1;
+          y1 = N.pin[p];
+          if (Lr[y1] == dt) r1 = rem;
+        }
+        a.net++;
       }
-      const long long incl = warp_incl_scan(r);
-      const long long take = min(max(rem - (incl - r), 0LL), r);
-      bool ap = false;
-      if (take > 0) {
-        if (i == 0) N.f_b[e] = fb - (int)take;
-        else N.f_out[p] += (int)take;
-        ap = deliver(N, y, take, epoch, sink_acc);
-        a.pushes++;
-      }
-      warp_append(ap, y, nextl, ncnt);
-      a.net += (i < items);
-      const long long tot = __shfl_sync(FULL, incl, 31);
-      rem -= min(rem, tot);
-      if (rem == 0) break;
     }
+    const long long r = r1 + r2;
+    const long long incl = team_incl_scan<TW>(r, tl);
+    const long long take = min(max(rem - (incl - r), 0LL), r);
+    const long long t1 = min(take, r1), t2 = take - t1;
+    bool a1 = false, a2 = false, h1 = false, h2 = false;
+    if (t1 > 0) {
+      if (g.kind == 0) N.f_in[p] = fi + (int)t1;
+      else if (g.kind == 1) {
+        if (k == 0) N.f_b[g.e] = fb + (int)t1;
+        else N.f_in[p] = fi - (int)t1;
+      } else {
+        if (k == 0) N.f_b[g.e] = fb - (int)t1;
+        else N.f_out[p] += (int)t1;
+      }
+      a1 = deliver(N, y1, t1, epoch, sink_acc, h1);
+      a.pushes++;
+    }
+    if (t2 > 0) {
+      N.f_out[p] = fo - (int)t2;
+      a2 = deliver(N, y2, t2, epoch, sink_acc, h2);
+      a.pushes++;
+    }
+    append_split(a1, y1, h1, nl, S.c[C_NEXT], S.c[C_NEXTH], 0, 0, NL);
+    append_split(a2, y2, h2, nl, S.c[C_NEXT], S.c[C_NEXTH], 0, 0, NL);
+    const long long tot = __shfl_sync(FULL, incl, TW - 1, TW);
+    rem -= min(rem, tot);
   }
   bool want = false;
-  if (lane == 0) {
+  if (act && tl == 0) {
     N.excess[x] = rem;
     if (rem > 0) {
       N.needrl[x] = 1;
       want = atomicExch(&N.stamp[x], epoch) != epoch;
     }
+    a.nodes++;
   }
-  warp_append(want, x, nextl, ncnt);
-  a.nodes += (lane == 0);
+  append_split(want, x, TW == 32, nl, S.c[C_NEXT], S.c[C_NEXTH], 0, 0, NL);
 }
 
-// New label of x after the pushes of the round: min over residual arcs
-// (capped network) of d(v) + 1, from the labels of the round (Section 2,
-// "relabel").  NL when x has no residual arc.
-__device__ int warp_relabel(const NetDev& N, const int32_t* Lr, int x, unsigned lane, Acc& a) {
+// New label after the pushes of the round: min over residual arcs (capped
+// network) of d(v) + 1 with the labels of the round (Section 2, "relabel");
+// NL when no residual arc is left.  One node per team (need = false: idle).
+template <int TW>
+__device__ int relabel_team(const NetDev& N, const int32_t* Lr, int x, bool need, unsigned lane,
+                            Acc& a) {
   const int NL = N.NL, nh = N.n_nodes, m = N.m_nets;
+  const unsigned tl = lane & (TW - 1);
+  NodeArcs g{0, 0, 0, 0};
+  int w = 0, fb = 0;
+  if (need) {
+    g = node_arcs(N, x);
+    if (g.kind) {
+      w = N.net_w[g.e];
+      fb = N.f_b[g.e];
+    }
+  }
+  const unsigned steps = warp_max_u((g.items + TW - 1) / TW);
   int best = NL;
-  if (x < nh) {
-    const unsigned beg = N.node_off[x], end = N.node_off[x + 1];
-    for (unsigned j = beg + lane; j < end; j += 32) {
-      int2 it = N.inc[j];
-      int w = N.net_w[it.x];
-      if (w > N.f_in[it.y]) best = min(best, Lr[nh + it.x] + 1);
+  for (unsigned c = 0; c < steps; c++) {
+    const unsigned k = c * TW + tl;
+    if (k >= g.items) continue;
+    if (g.kind == 0) {
+      const int2 it = N.inc[g.beg + k];
+      if (N.net_w[it.x] > N.f_in[it.y]) best = min(best, Lr[nh + it.x] + 1);
       if (N.f_out[it.y] > 0) best = min(best, Lr[nh + m + it.x] + 1);
       a.hyper++;
-    }
-  } else if (x < nh + m) {
-    const int e = x - nh;
-    const unsigned beg = N.net_off[e], end = N.net_off[e + 1];
-    if (lane == 0 && N.net_w[e] > N.f_b[e]) best = Lr[nh + m + e] + 1;
-    for (unsigned p = beg + lane; p < end; p += 32) {
-      if (N.f_in[p] > 0) best = min(best, Lr[N.pin[p]] + 1);
+    } else if (k == 0) {
+      if (g.kind == 1 ? w > fb : fb > 0)
+        best = min(best, Lr[g.kind == 1 ? nh + m + g.e : nh + g.e] + 1);
       a.net++;
-    }
-  } else {
-    const int e = x - nh - m;
-    const unsigned beg = N.net_off[e], end = N.net_off[e + 1];
-    if (lane == 0 && N.f_b[e] > 0) best = Lr[nh + e] + 1;
-    for (unsigned p = beg + lane; p < end; p += 32) {
-      best = min(best, Lr[N.pin[p]] + 1);
+    } else {
+      const unsigned p = g.beg + k - 1;
+      if (g.kind == 2 || N.f_in[p] > 0) best = min(best, Lr[N.pin[p]] + 1);
       a.net++;
     }
   }
-  best = warp_min(best);
+  best = team_min<TW>(best);
   return min(best, NL);
 }
 
 // ---------------------------------------------------------------------------
-__device__ void phase_a(const NetDev& N, EngineCtl* E, const Sched& s, unsigned gwarp,
-                        unsigned nwarps, unsigned lane, Acc& a) {
-  const int32_t* Lr = lab_cur(N, s.lp);
-  int32_t* Ln = lab_cur(N, s.lp ^ 1);
-  const unsigned tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
-  for (unsigned i = tid; i < s.rcnt; i += nth) {   // labels relabeled last round
-    int x = N.list[L_RELAB][i];
+// Heavy nodes: a whole CTA per node.  Block-wide inclusive scan of one value
+// per thread; *total gets the sum.  Every thread of the CTA must call it.
+__device__ __forceinline__ long long block_incl_scan(long long v, long long* total) {
+  __shared__ long long wtot[32];
+  const unsigned lane = lane_id(), wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  long long x = warp_incl_scan(v);
+  if (lane == 31) wtot[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    const long long t = lane < nw ? wtot[lane] : 0;
+    const long long y = warp_incl_scan(t);
+    if (lane < nw) wtot[lane] = y - t;
+    if (lane == nw - 1) wtot[31] = y;
+  }
+  __syncthreads();
+  x += wtot[wid];
+  *total = wtot[31];
+  __syncthreads();
+  return x;
+}
+
+__device__ __forceinline__ int block_min(int v) {
+  __shared__ int wmin[32];
+  const unsigned lane = lane_id(), wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  v = warp_min(v);
+  if (lane == 0) wmin[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    int t = lane < nw ? wmin[lane] : INT_MAX;
+    t = warp_min(t);
+    if (lane == 0) wmin[31] = t;
+  }
+  __syncthreads();
+  const int r = wmin[31];
+  __syncthreads();
+  return r;
+}
+
+// Discharge of one heavy node by the whole CTA: blockDim.x arc groups per
+// step, pushes placed by a block scan of residual capacities in arc order.
+__device__ void discharge_block(const NetDev& N, int x, const int32_t* Lr, unsigned epoch,
+                                long long& sink_acc, Acc& a, const Slot& S) {
+  const int NL = N.NL, nh = N.n_nodes, m = N.m_nets;
+  const long long ex = N.excess[x];
+  const int dx = Lr[x];
+  if (ex <= 0 || dx >= NL) return;    // uniform over the CTA
+  const int dt = dx - 1;
+  long long rem = ex;
+  int32_t* nl = N.list[L_NEXT];
+  const NodeArcs g = node_arcs(N, x);
+  const int w = g.kind ? N.net_w[g.e] : 0;
+  const int fb = g.kind ? N.f_b[g.e] : 0;
+  for (unsigned k0 = 0; k0 < g.items && rem > 0; k0 += blockDim.x) {
+    const unsigned k = k0 + threadIdx.x;
+    long long r1 = 0, r2 = 0;
+    int y1 = -1, y2 = -1, p = 0, fi = 0, fo = 0;
+    if (k < g.items) {
+      if (g.kind == 0) {
+        const int2 it = N.inc[g.beg + k];
+        p = it.y;
+        const int ww = N.net_w[it.x];
+        fi = N.f_in[p];
+        fo = N.f_out[p];
+        y1 = nh + it.x;
+        y2 = nh + m + it.x;
+        if (ww > fi && Lr[y1] == dt) r1 = ww - fi;
+        if (fo > 0 && Lr[y2] == dt) r2 = fo;
+        a.hyper++;
+      } else if (g.kind == 1) {
+        if (k == 0) {
+          y1 = nh + m + g.e;
+          if (w > fb && Lr[y1] == dt) r1 = w - fb;
+        } else {
+          p = g.beg + k - 1;
+          fi = N.f_in[p];
+          if (fi > 0) {
+            y1 = N.pin[p];
+            if (Lr[y1] == dt) r1 = fi;
+          }
+        }
+        a.net++;
+      } else {
+        if (k == 0) {
+          y1 = nh + g.e;
+          if (fb > 0 && Lr[y1] == dt) r1 = fb;
+        } else {
+          p = g.beg + k - 1;
+          y1 = N.pin[p];
+          if (Lr[y1] == dt) r1 = rem;
+        }
+        a.net++;
+      }
+    }
+    const long long r = r1 + r2;
+    long long tot;
+    const long long incl = block_incl_scan(r, &tot);
+    const long long take = min(max(rem - (incl - r), 0LL), r);
+    const long long t1 = min(take, r1), t2 = take - t1;
+    bool a1 = false, a2 = false, h1 = false, h2 = false;
+    if (t1 > 0) {
+      if (g.kind == 0) N.f_in[p] = fi + (int)t1;
+      else if (g.kind == 1) {
+        if (k == 0) N.f_b[g.e] = fb + (int)t1;
+        else N.f_in[p] = fi - (int)t1;
+      } else {
+        if (k == 0) N.f_b[g.e] = fb - (int)t1;
+        else N.f_out[p] += (int)t1;
+      }
+      a1 = deliver(N, y1, t1, epoch, sink_acc, h1);
+      a.pushes++;
+    }
+    if (t2 > 0) {
+      N.f_out[p] = fo - (int)t2;
+      a2 = deliver(N, y2, t2, epoch, sink_acc, h2);
+      a.pushes++;
+    }
+    append_split(a1, y1, h1, nl, S.c[C_NEXT], S.c[C_NEXTH], 0, 0, NL);
+    append_split(a2, y2, h2, nl, S.c[C_NEXT], S.c[C_NEXTH], 0, 0, NL);
+    rem -= min(rem, tot);
+  }
+  bool want = false;
+  if (threadIdx.x == 0) {
+    N.excess[x] = rem;
+    if (rem > 0) {
+      N.needrl[x] = 1;
+      want = atomicExch(&N.stamp[x], epoch) != epoch;
+    }
+    a.nodes++;
+  }
+  if (threadIdx.x < 32) append_split(want, x, true, nl, S.c[C_NEXT], S.c[C_NEXTH], 0, 0, NL);
+}
+
+// Relabel of one heavy node by the whole CTA (see relabel_team).
+__device__ int relabel_block(const NetDev& N, const int32_t* Lr, int x, Acc& a) {
+  const int NL = N.NL, nh = N.n_nodes, m = N.m_nets;
+  const NodeArcs g = node_arcs(N, x);
+  int best = NL;
+  for (unsigned k = threadIdx.x; k < g.items; k += blockDim.x) {
+    if (g.kind == 0) {
+      const int2 it = N.inc[g.beg + k];
+      if (N.net_w[it.x] > N.f_in[it.y]) best = min(best, Lr[nh + it.x] + 1);
+      if (N.f_out[it.y] > 0) best = min(best, Lr[nh + m + it.x] + 1);
+      a.hyper++;
+    } else if (k == 0) {
+      const int w = N.net_w[g.e], fb = N.f_b[g.e];
+      if (g.kind == 1 ? w > fb : fb > 0)
+        best = min(best, Lr[g.kind == 1 ? nh + m + g.e : nh + g.e] + 1);
+      a.net++;
+    } else {
+      const unsigned p = g.beg + k - 1;
+      if (g.kind == 2 || N.f_in[p] > 0) best = min(best, Lr[N.pin[p]] + 1);
+      a.net++;
+    }
+  }
+  return min(block_min(best), NL);
+}
+
+__device__ __forceinline__ long long apply_delta(const NetDev& N, int y) {
+  const long long d = N.delta[y];
+  const long long ex = N.excess[y] + d;
+  if (d) N.delta[y] = 0;
+  N.excess[y] = ex;
+  return ex;
+}
+
+// Phase B for one heavy node by the whole CTA.
+__device__ void apply_relabel_block(const NetDev& N, const int32_t* Lr, int32_t* Ln, int y,
+                                    Acc& a, const Slot& S) {
+  __shared__ int s_need;
+  __shared__ long long s_ex;
+  const int NL = N.NL;
+  if (threadIdx.x == 0) {
+    s_ex = apply_delta(N, y);
+    s_need = N.needrl[y];
+    if (s_need) N.needrl[y] = 0;
+    a.nodes++;
+  }
+  __syncthreads();
+  const int need = s_need;
+  const long long ex = s_ex;
+  int lab = 0;
+  if (need) {
+    lab = relabel_block(N, Lr, y, a);
+    if (threadIdx.x == 0) Ln[y] = lab;
+  } else {
+    lab = Lr[y];
+  }
+  if (threadIdx.x < 32) {
+    append_plain(threadIdx.x == 0 && need, y, N.list[L_RELAB], S.c[C_RELAB], 0);
+    append_split(threadIdx.x == 0 && ex > 0 && lab < NL, y, true, N.list[L_FRONT], S.c[C_FRONT],
+                 S.c[C_FRONTH], 0, 0, NL);
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+__device__ void phase_a(const NetDev& N, const Sched& L, const Team& T, const Slot& S,
+                        unsigned lane, Acc& a, EngineCtl* E) {
+  const int32_t* Lr = lab_cur(N, L.lp);
+  int32_t* Ln = lab_cur(N, L.lp ^ 1);
+  for (unsigned i = T.tid; i < L.rcnt; i += T.nth) {   // labels relabeled last round
+    const int x = N.list[L_RELAB][i];
     Ln[x] = Lr[x];
   }
   long long sink_acc = 0;
-  for (unsigned w = gwarp; w < s.fcnt; w += nwarps)
-    discharge(N, E, N.list[L_FRONT][w], Lr, s.epoch, lane, sink_acc, a);
+  const int32_t* fl = N.list[L_FRONT];
+  constexpr unsigned TPW = 32 / kTeam;                 // light nodes per warp
+  for (unsigned base = T.gwarp * TPW; base < L.fcnt; base += T.nwarps * TPW) {
+    const unsigned i = base + lane / kTeam;
+    discharge_team<kTeam>(N, i < L.fcnt ? fl[i] : -1, Lr, L.epoch, lane, sink_acc, a, S);
+  }
+  for (unsigned h = T.block; h < L.fcnth; h += T.nblocks)
+    discharge_block(N, fl[N.NL - 1 - h], Lr, L.epoch, sink_acc, a, S);
   sink_acc = warp_sum(sink_acc);
-  if (lane == 0 && sink_acc) atomicAdd(&E->c.flow, (unsigned long long)sink_acc);
+  if (lane == 0 && sink_acc) atomicAdd(S.flow, (unsigned long long)sink_acc);
 }
 
-__device__ void phase_b(const NetDev& N, EngineCtl* E, const Sched& s, unsigned gwarp,
-                        unsigned nwarps, unsigned lane, Acc& a) {
-  const int32_t* Lr = lab_cur(N, s.lp);
-  int32_t* Ln = lab_cur(N, s.lp ^ 1);
-  for (unsigned base = gwarp * 32; base < s.ncnt; base += nwarps * 32) {
-    const unsigned i = base + lane;
-    int y = -1, lab = N.NL;
-    long long ex = 0;
-    bool need = false;
-    if (i < s.ncnt) {
-      y = N.list[L_NEXT][i];
-      long long d = N.delta[y];
-      ex = N.excess[y] + d;
-      if (d) N.delta[y] = 0;
-      N.excess[y] = ex;
-      lab = Lr[y];
-      need = N.needrl[y] != 0;
-      if (need) N.needrl[y] = 0;
-      a.nodes++;
-    }
-    unsigned mask = __ballot_sync(FULL, need);
-    while (mask) {
-      const int l = __ffs(mask) - 1;
-      mask &= mask - 1;
-      const int yy = __shfl_sync(FULL, y, l);
-      const int nl = warp_relabel(N, Lr, yy, lane, a);
-      if ((int)lane == l) {
-        lab = nl;
-        Ln[yy] = nl;
-      }
-    }
-    warp_append(need, y, N.list[L_RELAB], &E->cnt[L_RELAB]);
-    warp_append(y >= 0 && ex > 0 && lab < N.NL, y, N.list[L_FRONT], &E->cnt[L_FRONT]);
+// Phase B for the entry of one team: apply the round's excess delta and, if
+// the node kept excess after its pushes, relabel it.
+template <int TW>
+__device__ void apply_relabel_team(const NetDev& N, const int32_t* Lr, int32_t* Ln, int y,
+                                   unsigned lane, Acc& a, const Slot& S) {
+  const int NL = N.NL;
+  const unsigned tl = lane & (TW - 1);
+  long long ex = 0;
+  int need = 0, lab = NL;
+  if (y >= 0 && tl == 0) {
+    ex = apply_delta(N, y);
+    lab = Lr[y];
+    need = N.needrl[y];
+    if (need) N.needrl[y] = 0;
+    a.nodes++;
   }
+  need = __shfl_sync(FULL, need, 0, TW);
+  const int nl = relabel_team<TW>(N, Lr, y, need != 0, lane, a);
+  if (need && tl == 0) {
+    lab = nl;
+    Ln[y] = nl;
+  }
+  append_plain(tl == 0 && need, y, N.list[L_RELAB], S.c[C_RELAB], 0);
+  append_split(tl == 0 && y >= 0 && ex > 0 && lab < NL, y, TW == 32, N.list[L_FRONT],
+               S.c[C_FRONT], S.c[C_FRONTH], 0, 0, NL);
+}
+
+__device__ void phase_b(const NetDev& N, const Sched& L, const Team& T, const Slot& S,
+                        unsigned lane, Acc& a) {
+  const int32_t* Lr = lab_cur(N, L.lp);
+  int32_t* Ln = lab_cur(N, L.lp ^ 1);
+  const int32_t* nx = N.list[L_NEXT];
+  constexpr unsigned TPW = 32 / kTeam;
+  for (unsigned base = T.gwarp * TPW; base < L.ncnt; base += T.nwarps * TPW) {
+    const unsigned i = base + lane / kTeam;
+    apply_relabel_team<kTeam>(N, Lr, Ln, i < L.ncnt ? nx[i] : -1, lane, a, S);
+  }
+  for (unsigned h = T.block; h < L.ncnth; h += T.nblocks)
+    apply_relabel_block(N, Lr, Ln, nx[N.NL - 1 - h], a, S);
 }
 
 // Global relabel, step 1: exact labels start from the sinks (Section 2,
 // "global relabeling").
-__device__ void gr_init(const NetDev& N, EngineCtl* E, unsigned lane, Acc& a) {
-  const unsigned tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
-  for (unsigned x0 = tid - lane; x0 < (unsigned)N.NL; x0 += nth) {
+__device__ void gr_init(const NetDev& N, const Team& T, const Slot& S, unsigned lane, Acc& a) {
+  for (unsigned x0 = T.tid - lane; x0 < (unsigned)N.NL; x0 += T.nth) {
     const unsigned x = x0 + lane;
-    bool snk = false;
+    bool snk = false, hv = false;
     if (x < (unsigned)N.NL) {
-      snk = (N.flags[x] & kSink) != 0;
-      int l = snk ? 0 : N.NL;
+      const uint8_t f = N.flags[x];
+      snk = (f & kSink) != 0;
+      hv = (f & kHeavy) != 0;
+      const int l = snk ? 0 : N.NL;
       N.lab0[x] = l;
       N.lab1[x] = l;
       N.needrl[x] = 0;
       if (snk && x < (unsigned)N.n_nodes) a.w += N.node_w[x];
     }
-    warp_append(snk, (int)x, N.list[L_BFS], &E->cnt[L_BFS]);
+    append_split(snk, (int)x, hv, N.list[L_BFS], S.c[C_BFS], S.c[C_BFSH], 0, 0, N.NL);
   }
 }
 
-__device__ __forceinline__ bool gr_claim(const NetDev& N, int x, int d1, bool& act, Acc& a) {
+__device__ __forceinline__ bool gr_claim(const NetDev& N, int x, int d1, bool& act, bool& hv,
+                                         Acc& a) {
   act = false;
+  hv = false;
   if (x < 0) return false;
   if (N.lab0[x] != N.NL) return false;
-  if (N.flags[x] & kSource) return false;
+  const uint8_t f = N.flags[x];
+  if (f & kSource) return false;
   if (atomicCAS(&N.lab0[x], N.NL, d1) != N.NL) return false;
   N.lab1[x] = d1;
+  hv = (f & kHeavy) != 0;
   act = N.excess[x] > 0;
   if (x < N.n_nodes) a.w += N.node_w[x];
   return true;
 }
 
+// Reverse residual arcs (capped network) into y, arc group k: up to two
+// tails c1, c2 (-1 when none).
+__device__ __forceinline__ void rev_arcs(const NetDev& N, const NodeArcs& g, unsigned k, int w,
+                                         int fb, int& c1, int& c2, Acc& a) {
+  const int nh = N.n_nodes, m = N.m_nets;
+  c1 = c2 = -1;
+  if (g.kind == 0) {
+    // into a hypernode: (e_out, u) always, (e_in, u) when f_in > 0
+    const int2 it = N.inc[g.beg + k];
+    c1 = nh + m + it.x;
+    if (N.f_in[it.y] > 0) c2 = nh + it.x;
+    a.hyper++;
+  } else if (k == 0) {
+    // into e_in: (e_out, e_in) when f_b > 0; into e_out: bridge when w > f_b
+    if (g.kind == 1) {
+      if (fb > 0) c1 = nh + m + g.e;
+    } else if (w > fb) {
+      c1 = nh + g.e;
+    }
+  } else {
+    // into e_in: (u, e_in) when f_in < w (capped); into e_out: (u, e_out) when f_out > 0
+    const unsigned p = g.beg + k - 1;
+    if (g.kind == 1 ? (N.f_in[p] < w) : (N.f_out[p] > 0)) c1 = N.pin[p];
+    a.net++;
+  }
+}
+
+__device__ __forceinline__ void gr_emit(const NetDev& N, EngineCtl* E, const Sched& L,
+                                        const Slot& S, int c, int d1, Acc& a) {
+  bool act, hv;
+  const bool k = gr_claim(N, c, d1, act, hv, a);
+  append_split(k, c, hv, N.list[L_BFS], S.c[C_BFS], S.c[C_BFSH], L.bfs_end, L.bfsh_end, N.NL);
+  append_split(act, c, hv, N.list[L_FRONT], &E->gr_act[0], &E->gr_act[1], 0, 0, N.NL);
+}
+
 // Global relabel, one level: reverse BFS over residual arcs of the capped
-// network; newly reached excess nodes become the frontier.
-__device__ void gr_level(const NetDev& N, EngineCtl* E, const Sched& s, unsigned gwarp,
-                         unsigned nwarps, unsigned lane, Acc& a) {
-  const int nh = N.n_nodes, m = N.m_nets, d1 = s.level + 1;
-  int32_t* bl = N.list[L_BFS];
-  unsigned* bc = &E->cnt[L_BFS];
-  int32_t* fl = N.list[L_FRONT];
-  unsigned* fc = &E->cnt[L_FRONT];
-  for (unsigned w = s.bfs_begin + gwarp; w < s.bfs_end; w += nwarps) {
-    const int y = bl[w];
-    if (y < nh) {
-      // into a hypernode: (e_out, u) always, (e_in, u) when f_in > 0
-      const unsigned beg = N.node_off[y], end = N.node_off[y + 1];
-      for (unsigned j0 = beg; j0 < end; j0 += 32) {
-        const unsigned j = j0 + lane;
-        int c1 = -1, c2 = -1;
-        if (j < end) {
-          int2 it = N.inc[j];
-          c1 = nh + m + it.x;
-          if (N.f_in[it.y] > 0) c2 = nh + it.x;
-          a.hyper++;
-        }
-        bool act1, act2;
-        bool k1 = gr_claim(N, c1, d1, act1, a);
-        bool k2 = gr_claim(N, c2, d1, act2, a);
-        warp_append(k1, c1, bl, bc);
-        warp_append(k2, c2, bl, bc);
-        warp_append(act1, c1, fl, fc);
-        warp_append(act2, c2, fl, fc);
-      }
-    } else {
-      const bool is_in = y < nh + m;
-      const int e = is_in ? y - nh : y - nh - m;
-      const unsigned beg = N.net_off[e], end = N.net_off[e + 1];
-      const int w = N.net_w[e], fb = N.f_b[e];
-      const unsigned items = 1 + (end - beg);
-      for (unsigned i0 = 0; i0 < items; i0 += 32) {
-        const unsigned i = i0 + lane;
-        int c = -1;
-        if (i == 0) {
-          // into e_in: (e_out, e_in) when f_b > 0; into e_out: bridge when w > f_b
-          if (is_in) { if (fb > 0) c = nh + m + e; }
-          else if (w > fb) c = nh + e;
-        } else if (i < items) {
-          const unsigned p = beg + i - 1;
-          // into e_in: (u, e_in) when f_in < w (capped); into e_out: (u, e_out) when f_out > 0
-          if (is_in ? (N.f_in[p] < w) : (N.f_out[p] > 0)) c = N.pin[p];
-          a.net++;
-        }
-        bool act;
-        bool k = gr_claim(N, c, d1, act, a);
-        warp_append(k, c, bl, bc);
-        warp_append(act, c, fl, fc);
-      }
+// network; newly reached excess nodes become the frontier.  A team per node.
+template <int TW>
+__device__ void gr_team(const NetDev& N, EngineCtl* E, const Sched& L, const Slot& S, int y,
+                        int d1, unsigned lane, Acc& a) {
+  const unsigned tl = lane & (TW - 1);
+  NodeArcs g{0, 0, 0, 0};
+  int w = 0, fb = 0;
+  if (y >= 0) {
+    g = node_arcs(N, y);
+    if (g.kind) {
+      w = N.net_w[g.e];
+      fb = N.f_b[g.e];
+    }
+  }
+  const unsigned steps = warp_max_u((g.items + TW - 1) / TW);
+  for (unsigned c = 0; c < steps; c++) {
+    const unsigned k = c * TW + tl;
+    int c1 = -1, c2 = -1;
+    if (k < g.items) rev_arcs(N, g, k, w, fb, c1, c2, a);
+    gr_emit(N, E, L, S, c1, d1, a);
+    gr_emit(N, E, L, S, c2, d1, a);
+  }
+}
+
+__device__ void gr_level(const NetDev& N, EngineCtl* E, const Sched& L, const Team& T,
+                         const Slot& S, unsigned lane, Acc& a) {
+  const int d1 = L.level + 1;
+  const int32_t* bl = N.list[L_BFS];
+  const unsigned nlight = L.bfs_end - L.bfs_begin, nheavy = L.bfsh_end - L.bfsh_begin;
+  constexpr unsigned TPW = 32 / kTeam;
+  for (unsigned base = T.gwarp * TPW; base < nlight; base += T.nwarps * TPW) {
+    const unsigned i = base + lane / kTeam;
+    gr_team<kTeam>(N, E, L, S, i < nlight ? bl[L.bfs_begin + i] : -1, d1, lane, a);
+  }
+  for (unsigned h = T.block; h < nheavy; h += T.nblocks) {
+    // heavy node: the whole CTA, blockDim.x arc groups per step
+    const int y = bl[N.NL - 1 - (L.bfsh_begin + h)];
+    const NodeArcs g = node_arcs(N, y);
+    const int w = g.kind ? N.net_w[g.e] : 0, fb = g.kind ? N.f_b[g.e] : 0;
+    for (unsigned k0 = 0; k0 < g.items; k0 += blockDim.x) {
+      const unsigned k = k0 + threadIdx.x;
+      int c1 = -1, c2 = -1;
+      if (k < g.items) rev_arcs(N, g, k, w, fb, c1, c2, a);
+      gr_emit(N, E, L, S, c1, d1, a);
+      gr_emit(N, E, L, S, c2, d1, a);
     }
   }
 }
 
 // Source-side cut, step 1: seeds are the sources and every non-sink node with
 // positive excess (Section 8.4, "Source-Side Cut").
-__device__ void sr_init(const NetDev& N, EngineCtl* E, const Sched& s, unsigned lane, Acc& a) {
-  const unsigned tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
-  for (unsigned x0 = tid - lane; x0 < (unsigned)N.NL; x0 += nth) {
+__device__ void sr_init(const NetDev& N, const Sched& L, const Team& T, const Slot& S,
+                        unsigned lane, Acc& a) {
+  for (unsigned x0 = T.tid - lane; x0 < (unsigned)N.NL; x0 += T.nth) {
     const unsigned x = x0 + lane;
-    bool seed = false;
+    bool seed = false, hv = false;
     if (x < (unsigned)N.NL) {
-      uint8_t f = N.flags[x];
+      const uint8_t f = N.flags[x];
+      hv = (f & kHeavy) != 0;
       seed = (f & kSource) || (!(f & kSink) && N.excess[x] > 0);
       N.insr[x] = seed ? 1 : 0;
       if (seed) {
-        N.stamp[x] = s.epoch;
+        N.stamp[x] = L.epoch;
         if (x < (unsigned)N.n_nodes) a.w += N.node_w[x];
       }
     }
-    warp_append(seed, (int)x, N.list[L_BFS], &E->cnt[L_BFS]);
+    append_split(seed, (int)x, hv, N.list[L_BFS], S.c[C_BFS], S.c[C_BFSH], 0, 0, N.NL);
   }
 }
 
-__device__ __forceinline__ bool sr_claim(const NetDev& N, int y, unsigned epoch, Acc& a) {
-  if (y < 0) return false;
-  if (N.insr[y]) return false;
-  if (atomicExch(&N.stamp[y], epoch) == epoch) return false;
-  N.insr[y] = 1;
-  if (y < N.n_nodes) a.w += N.node_w[y];
-  return true;
+// Forward residual arcs out of x with (u, e_in) uncapped, arc group k.
+__device__ __forceinline__ void fwd_arcs(const NetDev& N, const NodeArcs& g, unsigned k, int w,
+                                         int fb, int& c1, int& c2, Acc& a) {
+  const int nh = N.n_nodes, m = N.m_nets;
+  c1 = c2 = -1;
+  if (g.kind == 0) {
+    // out of a hypernode: (u, e_in) always, (u, e_out) when f_out > 0
+    const int2 it = N.inc[g.beg + k];
+    c1 = nh + it.x;
+    if (N.f_out[it.y] > 0) c2 = nh + m + it.x;
+    a.hyper++;
+  } else if (k == 0) {
+    // out of e_in: bridge when f_b < w; out of e_out: (e_out, e_in) when f_b > 0
+    if (g.kind == 1) {
+      if (fb < w) c1 = nh + m + g.e;
+    } else if (fb > 0) {
+      c1 = nh + g.e;
+    }
+  } else {
+    // out of e_in: (e_in, u) when f_in > 0; out of e_out: (e_out, u) always
+    const unsigned p = g.beg + k - 1;
+    if (g.kind == 2 || N.f_in[p] > 0) c1 = N.pin[p];
+    a.net++;
+  }
 }
 
-// Source-side cut, one level: forward residual arcs with (u, e_in) uncapped.
-__device__ void sr_level(const NetDev& N, EngineCtl* E, const Sched& s, unsigned gwarp,
-                         unsigned nwarps, unsigned lane, Acc& a) {
-  const int nh = N.n_nodes, m = N.m_nets;
-  int32_t* bl = N.list[L_BFS];
-  unsigned* bc = &E->cnt[L_BFS];
-  for (unsigned w = s.bfs_begin + gwarp; w < s.bfs_end; w += nwarps) {
-    const int x = bl[w];
-    if (x < nh) {
-      // out of a hypernode: (u, e_in) always, (u, e_out) when f_out > 0
-      const unsigned beg = N.node_off[x], end = N.node_off[x + 1];
-      for (unsigned j0 = beg; j0 < end; j0 += 32) {
-        const unsigned j = j0 + lane;
-        int c1 = -1, c2 = -1;
-        if (j < end) {
-          int2 it = N.inc[j];
-          c1 = nh + it.x;
-          if (N.f_out[it.y] > 0) c2 = nh + m + it.x;
-          a.hyper++;
-        }
-        bool k1 = sr_claim(N, c1, s.epoch, a);
-        bool k2 = sr_claim(N, c2, s.epoch, a);
-        warp_append(k1, c1, bl, bc);
-        warp_append(k2, c2, bl, bc);
-      }
-    } else {
-      const bool is_in = x < nh + m;
-      const int e = is_in ? x - nh : x - nh - m;
-      const unsigned beg = N.net_off[e], end = N.net_off[e + 1];
-      const int w = N.net_w[e], fb = N.f_b[e];
-      const unsigned items = 1 + (end - beg);
-      for (unsigned i0 = 0; i0 < items; i0 += 32) {
-        const unsigned i = i0 + lane;
-        int c = -1;
-        if (i == 0) {
-          // out of e_in: bridge when f_b < w; out of e_out: (e_out, e_in) when f_b > 0
-          if (is_in) { if (fb < w) c = nh + m + e; }
-          else if (fb > 0) c = nh + e;
-        } else if (i < items) {
-          const unsigned p = beg + i - 1;
-          // out of e_in: (e_in, u) when f_in > 0; out of e_out: (e_out, u) always
-          if (!is_in || N.f_in[p] > 0) c = N.pin[p];
-          a.net++;
-        }
-        bool k = sr_claim(N, c, s.epoch, a);
-        warp_append(k, c, bl, bc);
-      }
+__device__ __forceinline__ void sr_emit(const NetDev& N, const Sched& L, const Slot& S, int y,
+                                        Acc& a) {
+  bool k = false, hv = false;
+  if (y >= 0 && !N.insr[y] && atomicExch(&N.stamp[y], L.epoch) != L.epoch) {
+    N.insr[y] = 1;
+    hv = (N.flags[y] & kHeavy) != 0;
+    if (y < N.n_nodes) a.w += N.node_w[y];
+    k = true;
+  }
+  append_split(k, y, hv, N.list[L_BFS], S.c[C_BFS], S.c[C_BFSH], L.bfs_end, L.bfsh_end, N.NL);
+}
+
+template <int TW>
+__device__ void sr_team(const NetDev& N, const Sched& L, const Slot& S, int x, unsigned lane,
+                        Acc& a) {
+  const unsigned tl = lane & (TW - 1);
+  NodeArcs g{0, 0, 0, 0};
+  int w = 0, fb = 0;
+  if (x >= 0) {
+    g = node_arcs(N, x);
+    if (g.kind) {
+      w = N.net_w[g.e];
+      fb = N.f_b[g.e];
+    }
+  }
+  const unsigned steps = warp_max_u((g.items + TW - 1) / TW);
+  for (unsigned c = 0; c < steps; c++) {
+    const unsigned k = c * TW + tl;
+    int c1 = -1, c2 = -1;
+    if (k < g.items) fwd_arcs(N, g, k, w, fb, c1, c2, a);
+    sr_emit(N, L, S, c1, a);
+    sr_emit(N, L, S, c2, a);
+  }
+}
+
+__device__ void sr_level(const NetDev& N, const Sched& L, const Team& T, const Slot& S,
+                         unsigned lane, Acc& a) {
+  const int32_t* bl = N.list[L_BFS];
+  const unsigned nlight = L.bfs_end - L.bfs_begin, nheavy = L.bfsh_end - L.bfsh_begin;
+  constexpr unsigned TPW = 32 / kTeam;
+  for (unsigned base = T.gwarp * TPW; base < nlight; base += T.nwarps * TPW) {
+    const unsigned i = base + lane / kTeam;
+    sr_team<kTeam>(N, L, S, i < nlight ? bl[L.bfs_begin + i] : -1, lane, a);
+  }
+  for (unsigned h = T.block; h < nheavy; h += T.nblocks) {
+    const int x = bl[N.NL - 1 - (L.bfsh_begin + h)];
+    const NodeArcs g = node_arcs(N, x);
+    const int w = g.kind ? N.net_w[g.e] : 0, fb = g.kind ? N.f_b[g.e] : 0;
+    for (unsigned k0 = 0; k0 < g.items; k0 += blockDim.x) {
+      const unsigned k = k0 + threadIdx.x;
+      int c1 = -1, c2 = -1;
+      if (k < g.items) fwd_arcs(N, g, k, w, fb, c1, c2, a);
+      sr_emit(N, L, S, c1, a);
+      sr_emit(N, L, S, c2, a);
     }
   }
 }
 
 // Distance from the original cut (reading of Section 6 "Region Growing" and
 // Section 7 "Piercing"): breadth-first search inside the region from the
-// vertices at distance 1.  Level list i holds the vertices at distance i + 1.
-__device__ void dist_init(const NetDev& N, EngineCtl* E, unsigned lane) {
-  const unsigned tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
-  for (unsigned u0 = tid - lane; u0 < (unsigned)N.n_nodes; u0 += nth) {
+// vertices at distance 1, a warp per vertex (light part of the BFS list
+// only).  Level i holds the vertices at distance i + 1.
+__device__ void dist_init(const NetDev& N, const Team& T, const Slot& S, unsigned lane) {
+  for (unsigned u0 = T.tid - lane; u0 < (unsigned)N.n_nodes; u0 += T.nth) {
     const unsigned u = u0 + lane;
     const bool seed = u >= 2 && u < (unsigned)N.n_nodes && N.node_dist[u] == 1;
-    warp_append(seed, (int)u, N.list[L_BFS], &E->cnt[L_BFS]);
+    append_plain(seed, (int)u, N.list[L_BFS], S.c[C_BFS], 0);
   }
 }
 
-__device__ void dist_level(const NetDev& N, EngineCtl* E, const Sched& s, unsigned gwarp,
-                           unsigned nwarps, unsigned lane) {
-  const int d2 = s.level + 2;
+__device__ void dist_level(const NetDev& N, const Sched& L, const Team& T, const Slot& S,
+                           unsigned lane) {
+  const int d2 = L.level + 2;
   int32_t* bl = N.list[L_BFS];
-  unsigned* bc = &E->cnt[L_BFS];
-  for (unsigned w = s.bfs_begin + gwarp; w < s.bfs_end; w += nwarps) {
+  for (unsigned w = L.bfs_begin + T.gwarp; w < L.bfs_end; w += T.nwarps) {
     const int u = bl[w];
     for (unsigned j = N.node_off[u]; j < N.node_off[u + 1]; j++) {
       const int e = N.inc[j].x;
@@ -648,42 +1017,209 @@ __device__ void dist_level(const NetDev& N, EngineCtl* E, const Sched& s, unsign
           if (v >= 2 && N.node_dist[v] < 0)
             claim = atomicCAS(&N.node_dist[v], -1, min(d2, kDistFar)) == -1;
         }
-        warp_append(claim, v, bl, bc);
+        append_plain(claim, v, bl, S.c[C_BFS], L.bfs_end);
       }
     }
   }
 }
 
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ Slot slot_of(EngineCtl* E, unsigned k) {
+  const unsigned sl = k % 3;
+  Slot S;
+#pragma unroll
+  for (int i = 0; i < C_COUNT; i++) S.c[i] = &E->cnt3[i][sl];
+  S.flow = &E->flow3[sl];
+  return S;
+}
+
+// One phase of the current state by team T; weights go to the phase slot.
+__device__ void run_phase(const NetDev& N, EngineCtl* E, const Sched& L, const Team& T,
+                          unsigned lane, Acc& a, long long* w_sh) {
+  const Slot S = slot_of(E, L.phase);
+  switch (L.state) {
+    case ST_ROUND_A: phase_a(N, L, T, S, lane, a, E); break;
+    case ST_ROUND_B: phase_b(N, L, T, S, lane, a); break;
+    case ST_GR_INIT: gr_init(N, T, S, lane, a); break;
+    case ST_GR_LEVEL: gr_level(N, E, L, T, S, lane, a); break;
+    case ST_SR_INIT: sr_init(N, L, T, S, lane, a); break;
+    case ST_SR_LEVEL: sr_level(N, L, T, S, lane, a); break;
+    case ST_DIST_INIT: dist_init(N, T, S, lane); break;
+    case ST_DIST_LEVEL: dist_level(N, L, T, S, lane); break;
+    default: break;
+  }
+  if (a.w) {
+    atomicAdd((unsigned long long*)w_sh, (unsigned long long)a.w);
+    a.w = 0;
+  }
+}
+
+__device__ __forceinline__ void flush_weight(EngineCtl* E, unsigned k, long long* w_sh) {
+  if (*w_sh) {
+    atomicAdd((unsigned long long*)&E->w3[k % 3], (unsigned long long)*w_sh);
+    *w_sh = 0;
+  }
+}
+
+// Per-state device time, kept by thread 0 of CTA 0.
+struct Clock {
+  unsigned long long t_last;
+  unsigned long long ns[10], cnt[10];
+};
+
+__device__ __forceinline__ void tick(Clock& ck, int st) {
+  const unsigned long long t = globaltimer();
+  st = st < 10 ? st : 9;
+  ck.ns[st] += t - ck.t_last;
+  ck.cnt[st]++;
+  ck.t_last = t;
+}
+
+// Rounds by CTA 0 alone while the frontier stays small: block barriers
+// instead of grid barriers.  Leaves with L holding the next grid state.
+__device__ void tail_rounds(const NetDev& N, EngineCtl* E, const Params& P, Sched& L,
+                            unsigned lane, Acc& a, long long* w_sh, Clock& ck) {
+  const Team T{threadIdx.x >> 5, blockDim.x >> 5, threadIdx.x, blockDim.x, 0, 1};
+  if (threadIdx.x == 0) L.state = ST_ROUND_A;
+  __syncthreads();
+  for (;;) {
+    if (threadIdx.x == 0) clear_slot(E, (L.phase + 1) % 3, false);
+    __syncthreads();
+    run_phase(N, E, L, T, lane, a, w_sh);
+    __syncthreads();
+    __threadfence_block();
+    if (threadIdx.x == 0) {
+      flush_weight(E, L.phase, w_sh);
+      const Snap q = take_snap(E, L.phase);
+      tick(ck, ST_TAIL);
+      advance(L, q, P, N, &E->c, true);
+      L.phase++;
+      if (L.state == ST_TAIL) L.state = ST_ROUND_A;
+      if (L.state == ST_ROUND_A && L.fcnt + L.fcnth > P.tail_exit) L.state = ST_ROUND_A + 100;
+    }
+    __syncthreads();
+    const int st = L.state;
+    if (st != ST_ROUND_A && st != ST_ROUND_B) break;
+  }
+  if (threadIdx.x == 0 && L.state == ST_ROUND_A + 100) L.state = ST_ROUND_A;
+  __syncthreads();
+}
+
+__device__ void load_sched(Sched& L, const EngineCtl* E) {
+  const volatile Sched* v = &E->s;
+  L.state = v->state;
+  L.lp = v->lp;
+  L.fcnt = v->fcnt;
+  L.fcnth = v->fcnth;
+  L.ncnt = v->ncnt;
+  L.ncnth = v->ncnth;
+  L.rcnt = v->rcnt;
+  L.bfs_begin = v->bfs_begin;
+  L.bfs_end = v->bfs_end;
+  L.bfsh_begin = v->bfsh_begin;
+  L.bfsh_end = v->bfsh_end;
+  L.level = v->level;
+  L.epoch = v->epoch;
+  L.after_gr_exit = v->after_gr_exit;
+  L.phase = v->phase;
+  L.rounds = v->rounds;
+  L.grs = v->grs;
+  L.gr_levels = v->gr_levels;
+  L.work = v->work;
+  L.stall = v->stall;
+  L.flow = v->flow;
+  L.flow_ref = v->flow_ref;
+  L.wS = v->wS;
+  L.wT = v->wT;
+  L.wS_set = v->wS_set;
+  L.wT_set = v->wT_set;
+}
+
+__device__ void store_sched(EngineCtl* E, const Sched& L) {
+  volatile Sched* v = &E->s;
+  v->state = L.state;
+  v->lp = L.lp;
+  v->fcnt = L.fcnt;
+  v->fcnth = L.fcnth;
+  v->ncnt = L.ncnt;
+  v->ncnth = L.ncnth;
+  v->rcnt = L.rcnt;
+  v->bfs_begin = L.bfs_begin;
+  v->bfs_end = L.bfs_end;
+  v->bfsh_begin = L.bfsh_begin;
+  v->bfsh_end = L.bfsh_end;
+  v->level = L.level;
+  v->epoch = L.epoch;
+  v->after_gr_exit = L.after_gr_exit;
+  v->phase = L.phase;
+  v->rounds = L.rounds;
+  v->grs = L.grs;
+  v->gr_levels = L.gr_levels;
+  v->work = L.work;
+  v->stall = L.stall;
+  v->flow = L.flow;
+  v->flow_ref = L.flow_ref;
+  v->wS = L.wS;
+  v->wT = L.wT;
+  v->wS_set = L.wS_set;
+  v->wT_set = L.wT_set;
+}
+
 __global__ void __launch_bounds__(kEngineThreads) engine_kernel(NetDev N, EngineCtl* E, Params P) {
-  __shared__ Sched ss;
+  __shared__ Sched L;
   __shared__ Acc acc_sh;
-  if (threadIdx.x == 0) acc_sh = Acc{0, 0, 0, 0, 0};
+  __shared__ long long w_sh;
+  __shared__ Clock ck;
   const unsigned lane = lane_id();
   const unsigned wib = threadIdx.x >> 5, nwb = blockDim.x >> 5;
-  const unsigned gwarp = blockIdx.x * nwb + wib, nwarps = gridDim.x * nwb;
-  Acc a{0, 0, 0, 0, 0};
-  bool run = grid_step(E, N, P, &ss, false, &acc_sh, 0);
-  while (run) {
-    int target = 0;
-    switch (ss.state) {
-      case ST_ROUND_A: phase_a(N, E, ss, gwarp, nwarps, lane, a); break;
-      case ST_ROUND_B: phase_b(N, E, ss, gwarp, nwarps, lane, a); break;
-      case ST_GR_INIT: gr_init(N, E, lane, a); target = 2; break;
-      case ST_GR_LEVEL: gr_level(N, E, ss, gwarp, nwarps, lane, a); target = 2; break;
-      case ST_SR_INIT: sr_init(N, E, ss, lane, a); target = 1; break;
-      case ST_SR_LEVEL: sr_level(N, E, ss, gwarp, nwarps, lane, a); target = 1; break;
-      case ST_DIST_INIT: dist_init(N, E, lane); break;
-      case ST_DIST_LEVEL: dist_level(N, E, ss, gwarp, nwarps, lane); break;
-      default: break;
-    }
-    if (a.w) {
-      atomicAdd((unsigned long long*)&acc_sh.w, (unsigned long long)a.w);
-      a.w = 0;
-    }
-    run = grid_step(E, N, P, &ss, true, &acc_sh, target);
+  const Team G{blockIdx.x * nwb + wib, gridDim.x * nwb, blockIdx.x * blockDim.x + threadIdx.x,
+               gridDim.x * blockDim.x, blockIdx.x, gridDim.x};
+  const bool cta0 = blockIdx.x == 0;
+  if (threadIdx.x == 0) {
+    load_sched(L, E);
+    L.flow = *(const volatile unsigned long long*)&E->c.flow;  // host kernels add to it
+    acc_sh = Acc{0, 0, 0, 0, 0};
+    w_sh = 0;
+    for (int i = 0; i < 10; i++) ck.ns[i] = ck.cnt[i] = 0;
+    ck.t_last = globaltimer();
   }
-  // statistics
+  __syncthreads();
+  Acc a{0, 0, 0, 0, 0};
+  unsigned bar_seq = 0;
+  for (;;) {
+    const int st = L.state;
+    if (st == ST_DONE) break;
+    if (st == ST_TAIL) {
+      if (cta0) {
+        tail_rounds(N, E, P, L, lane, a, &w_sh, ck);
+        if (threadIdx.x == 0) store_sched(E, L);
+      }
+      const bool ok = grid_barrier(E, gridDim.x * ++bar_seq, P.timeout_ns);
+      if (threadIdx.x == 0) {
+        if (!cta0) load_sched(L, E);
+        if (!ok) L.state = ST_DONE;
+      }
+      __syncthreads();
+      continue;
+    }
+    if (cta0 && threadIdx.x == 0) clear_slot(E, (L.phase + 1) % 3, st == ST_GR_INIT);
+    run_phase(N, E, L, G, lane, a, &w_sh);
+    __syncthreads();
+    if (threadIdx.x == 0) flush_weight(E, L.phase, &w_sh);
+    const bool ok = grid_barrier(E, gridDim.x * ++bar_seq, P.timeout_ns);
+    if (threadIdx.x == 0) {
+      if (!ok) {
+        L.state = ST_DONE;
+      } else {
+        const Snap q = take_snap(E, L.phase);
+        if (cta0) tick(ck, st);
+        advance(L, q, P, N, &E->c, cta0);
+        L.phase++;
+      }
+    }
+    __syncthreads();
+  }
+  // statistics and the published state (CTA 0)
   if (a.hyper) atomicAdd(&acc_sh.hyper, a.hyper);
   if (a.net) atomicAdd(&acc_sh.net, a.net);
   if (a.nodes) atomicAdd(&acc_sh.nodes, a.nodes);
@@ -694,6 +1230,19 @@ __global__ void __launch_bounds__(kEngineThreads) engine_kernel(NetDev N, Engine
     atomicAdd(&E->c.items_net, acc_sh.net);
     atomicAdd(&E->c.node_visits, acc_sh.nodes);
     atomicAdd(&E->c.pushes, acc_sh.pushes);
+    if (cta0) {
+      store_sched(E, L);
+      E->c.flow = L.flow;
+      E->c.rounds = L.rounds;
+      E->c.global_relabels = L.grs;
+      E->c.gr_levels = L.gr_levels;
+      if (L.wS_set) E->c.wS = L.wS;
+      if (L.wT_set) E->c.wT = L.wT;
+      for (int i = 0; i < 10; i++) {
+        E->c.state_ns[i] += ck.ns[i];
+        E->c.state_cnt[i] += ck.cnt[i];
+      }
+    }
   }
 }
 

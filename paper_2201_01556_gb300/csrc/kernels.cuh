@@ -35,6 +35,7 @@ void launch_incidence(int32_t n_nodes, int32_t m_net, unsigned p, const uint32_t
                       unsigned* scan_total, int sms, cudaStream_t st);
 void launch_dist_seed(int32_t n_nodes, const int32_t* dist_tmp, int32_t* dist, int sms,
                       cudaStream_t st);
+void launch_heavy_flags(const NetDev& N, int sms, cudaStream_t st);
 void launch_dist_export(int32_t n_nodes, const int32_t* dist, int32_t* out, int sms,
                         cudaStream_t st);
 void launch_dist_copy(int32_t n_region, const int32_t* dist_in, int32_t* dist, int* err,

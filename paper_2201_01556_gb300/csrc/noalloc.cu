@@ -233,6 +233,7 @@ extern "C" __attribute__((visibility("default"))) hfp_status hfp_max_flow_noallo
   }
   k_static_init<<<1, 1, 0, st>>>(D, E);
   count_launches(1);
+  launch_heavy_flags(D, dev.coop_grid / 2 > 0 ? dev.coop_grid / 2 : 1, st);
 
   Params P{};
   P.timeout_ns = 10ull * 1000 * 1000 * 1000;
@@ -240,6 +241,8 @@ extern "C" __attribute__((visibility("default"))) hfp_status hfp_max_flow_noallo
   P.gr_work = 2ull * (unsigned long long)NL + 1024;
   P.stall_rounds = 500;
   P.stall_nodes = 1500;
+  P.tail_enter = 64;
+  P.tail_exit = 192;
   void* args[] = {(void*)&D, (void*)&E, (void*)&P};
 
   // maximum preflow from {s} to {t}: saturate s, global relabel, rounds

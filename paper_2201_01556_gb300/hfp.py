@@ -98,6 +98,8 @@ def load():
         "hfp_flowcutter": (i32, [P, ctypes.POINTER(FcParams), P, P, P, i32,
                                  ctypes.POINTER(_FcResult)]),
         "hfp_max_flow_noalloc": (i32, [i32, P, ctypes.POINTER(_NetworkView), P, P, P]),
+        "hfp_net_enable_trace": (i32, [P, i32]),
+        "hfp_net_get_trace": (i32, [P, P, P, P, i32, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -251,6 +253,32 @@ def max_flow_noalloc(device: int, stream: int, view: dict, n_nodes: int, m_nets:
                                        ctypes.byref(flow), _ptr(in_source_lawler),
                                        ctypes.byref(w)))
     return int(flow.value), int(w.value)
+
+
+STATE_NAMES = ("done", "push", "relabel", "gr_init", "gr_level", "sr_init", "sr_level",
+               "dist_init", "dist_level", "other")
+
+
+def net_enable_trace(net: Net, rounds: int):
+    """hfp_net_enable_trace."""
+    _check(load().hfp_net_enable_trace(net.h, rounds))
+
+
+def net_trace(net: Net, cap: int = 0) -> dict:
+    """hfp_net_get_trace -> per-state device time and counts, and the
+    per-round (frontier, next-list size, flow) trace."""
+    ns = np.zeros(10, np.uint64)
+    cnt = np.zeros(10, np.uint64)
+    buf = np.zeros(max(2 * cap, 2), np.uint64)
+    n = ctypes.c_int32()
+    _check(load().hfp_net_get_trace(net.h, _ptr(ns), _ptr(cnt), _ptr(buf), cap, ctypes.byref(n)))
+    k = min(n.value, cap)
+    tr = buf[: 2 * k].reshape(-1, 2)
+    return dict(state_ns={STATE_NAMES[i]: int(ns[i]) for i in range(10)},
+                state_cnt={STATE_NAMES[i]: int(cnt[i]) for i in range(10)},
+                rounds=int(n.value), frontier=(tr[:, 0] >> np.uint64(32)).astype(np.int64),
+                next=(tr[:, 0] & np.uint64(0xFFFFFFFF)).astype(np.int64),
+                flow=tr[:, 1].astype(np.int64))
 
 
 def net_stats(net: Net) -> dict:

@@ -101,6 +101,30 @@ def load_peaks():
         return 6800.0, "fallback"
 
 
+ENGINE_SOURCES = ("engine.cu", "engine.cuh", "common.cuh", "kernels.cuh")
+
+
+def engine_traffic_ratio():
+    """DRAM bytes per modelled byte of the engine kernel from the committed ncu
+    summary, if the engine sources are unchanged since that capture."""
+    import hashlib
+    import re
+    path = os.path.join(ROOT, "profiles", "engine_kernel_ring_n1M.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    m1 = re.search(r"traffic_per_modelled_byte = ([0-9.]+)", text)
+    m2 = re.search(r"engine_source_sha256 = ([0-9a-f]+)", text)
+    if not (m1 and m2):
+        return None
+    h = hashlib.sha256()
+    for f in ENGINE_SOURCES:
+        with open(os.path.join(ROOT, "paper_2201_01556_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return float(m1.group(1)) if h.hexdigest() == m2.group(1) else None
+
+
 def oracle_step(inst):
     import oracle
     H = inst["H"]
@@ -146,6 +170,11 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    # smaller rings of the same generator, for profiling captures
+    ap.add_argument("--n", type=int, default=None)
+    ap.add_argument("--m", type=int, default=None)
+    ap.add_argument("--radius", type=int, default=None)
     args = ap.parse_args()
     rank, world, local = env_rank()
     if args.impl == "reference":
@@ -160,7 +189,7 @@ def main():
     from paper_2201_01556_gb300 import hfp
     hfp.load()
 
-    inst = synth.instance(WORKLOAD, args.seed)
+    inst = synth.instance(WORKLOAD, args.seed, n=args.n, m=args.m, radius=args.radius)
     H, part, region = inst["H"], inst["part"], inst["region"]
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.int32)).cuda()
     d_off, d_pins, d_netw, d_nodew = dev(H.net_off), dev(H.pins), dev(H.net_w), dev(H.node_w)
@@ -215,7 +244,7 @@ def main():
     h2d = (H.net_off.nbytes + H.pins.nbytes + H.net_w.nbytes + H.node_w.nbytes + region.nbytes
            + part.nbytes)
     d2h = len(region) + 8
-    for _ in range(max(1, min(args.steps, 3))):
+    for _ in range(0 if args.no_e2e else max(1, min(args.steps, 3))):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         net = hfp.build_flow_network(ctx, H.net_off, H.pins, H.net_w, H.node_w, region, part, H.n)
@@ -224,7 +253,7 @@ def main():
         torch.cuda.synchronize()
         e2e_ms.append(1e3 * (time.perf_counter() - t0))
         net.close()
-    e2e_value = world * p_pins / (statistics.mean(e2e_ms) / 1e3)
+    e2e_value = world * p_pins / (statistics.mean(e2e_ms) / 1e3) if e2e_ms else None
 
     if rank != 0:
         return 0
@@ -235,8 +264,13 @@ def main():
                 + s[1]["node_visits"] * B_NODE + s[1]["pushes"] * B_PUSH for s in stats)
     peak, peak_kind = load_peaks()
     achieved = (model / eng_launches) / (eng_ns / eng_launches / 1e9) / 1e9 if eng_ns else None
+    ratio = engine_traffic_ratio()
+    traffic = ratio * model / eng_launches if (ratio is not None and eng_launches) else None
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": (achieved / peak) if achieved else None, "traffic": None,
+            "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+            "traffic_note": "DRAM bytes per launch, scaled from the ncu capture in "
+                            "profiles/engine_kernel_ring_n1M.md by modelled bytes"
+                            if traffic is not None else "kernel changed since the ncu capture",
             "kernel": "engine_kernel", "peak_kind": peak_kind,
             "engine_ms_per_step": eng_ns / 1e6 / args.steps,
             "engine_launches_per_step": eng_launches / args.steps}
@@ -244,7 +278,8 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "seed": args.seed, "n": H.n,
+            "config": {"workload": WORKLOAD if args.n is None else f"{WORKLOAD} scaled to n={H.n}",
+                       "seed": args.seed, "n": H.n,
                        "m": H.m, "pins_H": H.p, "region": len(region), "lawler_pins": p_pins,
                        "flow": stats[0][2], "source_weight": stats[0][3],
                        "l2": "flushed between timed steps (2x L2 buffer write)",

@@ -125,6 +125,30 @@ const char* hfp_last_error(void);
 /* Number of kernels this library has launched in the process so far. */
 uint64_t hfp_kernel_launches(void);
 
+/* --- engine tuning -------------------------------------------------------------
+ * Speed-only knobs of the flow engine; no value changes any result (flow,
+ * cuts, piercing sequence).  Defaults in brackets.
+ *   gr_work_x100  global relabel once the frontier and next-list entries
+ *                 processed since the last one exceed gr_work_x100 / 100
+ *                 Lawler nodes (Section 8.1, "after linear work") [200]
+ *   stall_rounds, stall_nodes  also relabel globally after stall_rounds
+ *                 rounds without a flow change, each with fewer than
+ *                 stall_nodes active nodes (Section 8.3) [200, 1500]
+ *   tail_enter, tail_exit  frontiers of at most tail_enter nodes are run by
+ *                 one CTA with block barriers until they exceed tail_exit
+ *                 [64, 192]
+ *   max_rounds    discharge-round budget of one network [2^22] */
+typedef struct {
+  uint32_t gr_work_x100;
+  uint32_t stall_rounds;
+  uint32_t stall_nodes;
+  uint32_t tail_enter;
+  uint32_t tail_exit;
+  uint32_t max_rounds;
+} hfp_tuning;
+hfp_status hfp_ctx_get_tuning(hfp_ctx* ctx, hfp_tuning* tuning);
+hfp_status hfp_ctx_set_tuning(hfp_ctx* ctx, const hfp_tuning* tuning);
+
 /* --- network construction (Section 6, "Construction Algorithms") ---------
  * Builds the flow hypergraph of the region B = region[0 .. n_region):
  * every net of H with a pin in B is copied with its region pins; a pin

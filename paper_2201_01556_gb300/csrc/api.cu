@@ -92,6 +92,7 @@ struct hfp_ctx {
   Ctl* pinned_ctl = nullptr;       // host mirror of Ctl
   void* pinned_small = nullptr;    // 4 KB staging
   Params params{};
+  uint32_t gr_work_x100 = 200;
 };
 
 struct hfp_net {
@@ -254,7 +255,7 @@ HFP_API hfp_status hfp_ctx_create(hfp_ctx** out, int device, void* stream) {
   c->params.timeout_ns = 10ull * 1000 * 1000 * 1000;
   c->params.max_rounds = 1ull << 22;
   c->params.gr_work = 0;           // set per network (a multiple of its node count)
-  c->params.stall_rounds = 500;    // Section 8.3, "Avoid Pushing Flow Back"
+  c->params.stall_rounds = 200;    // Section 8.3, "Avoid Pushing Flow Back" (tuned: 500 in the paper)
   c->params.stall_nodes = 1500;
   c->params.tail_enter = 64;       // CTA 0 alone at or below this frontier size
   c->params.tail_exit = 192;
@@ -677,10 +678,36 @@ HFP_API hfp_status hfp_net_get_trace(hfp_net* net, uint64_t* state_ns, uint64_t*
 }
 
 static void set_gr_work(hfp_net* net) {
-  // global relabel after work linear in the network (Section 8.1): here,
-  // once the frontier and next-list entries processed since the last one
-  // exceed twice the number of Lawler nodes
-  net->ctx->params.gr_work = 2ull * (unsigned long long)net->d.NL + 1024;
+  // global relabel after work linear in the network (Section 8.1): once the
+  // frontier and next-list entries processed since the last one exceed
+  // gr_work_x100 / 100 times the number of Lawler nodes
+  net->ctx->params.gr_work =
+      (unsigned long long)net->d.NL * net->ctx->gr_work_x100 / 100 + 1024;
+}
+
+HFP_API hfp_status hfp_ctx_get_tuning(hfp_ctx* ctx, hfp_tuning* t) {
+  if (!ctx || !t) return fail(HFP_ERR_INVALID, "NULL argument");
+  t->gr_work_x100 = ctx->gr_work_x100;
+  t->stall_rounds = (uint32_t)ctx->params.stall_rounds;
+  t->stall_nodes = ctx->params.stall_nodes;
+  t->tail_enter = ctx->params.tail_enter;
+  t->tail_exit = ctx->params.tail_exit;
+  t->max_rounds = (uint32_t)ctx->params.max_rounds;
+  return HFP_OK;
+}
+
+HFP_API hfp_status hfp_ctx_set_tuning(hfp_ctx* ctx, const hfp_tuning* t) {
+  if (!ctx || !t) return fail(HFP_ERR_INVALID, "NULL argument");
+  if (t->gr_work_x100 == 0 || t->stall_rounds == 0 || t->max_rounds == 0 ||
+      t->tail_exit < t->tail_enter)
+    return fail(HFP_ERR_INVALID, "bad tuning values");
+  ctx->gr_work_x100 = t->gr_work_x100;
+  ctx->params.stall_rounds = t->stall_rounds;
+  ctx->params.stall_nodes = t->stall_nodes;
+  ctx->params.tail_enter = t->tail_enter;
+  ctx->params.tail_exit = t->tail_exit;
+  ctx->params.max_rounds = t->max_rounds;
+  return HFP_OK;
 }
 
 HFP_API hfp_status hfp_max_flow(hfp_net* net, int64_t* flow_value) {

@@ -239,7 +239,7 @@ extern "C" __attribute__((visibility("default"))) hfp_status hfp_max_flow_noallo
   P.timeout_ns = 10ull * 1000 * 1000 * 1000;
   P.max_rounds = 1ull << 22;
   P.gr_work = 2ull * (unsigned long long)NL + 1024;
-  P.stall_rounds = 500;
+  P.stall_rounds = 200;
   P.stall_nodes = 1500;
   P.tail_enter = 64;
   P.tail_exit = 192;

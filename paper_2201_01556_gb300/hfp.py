@@ -47,6 +47,11 @@ class _Stats(ctypes.Structure):
                  "node_visits", "pushes", "engine_launches", "engine_ns")]
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_uint32) for k in ("gr_work_x100", "stall_rounds", "stall_nodes",
+                                               "tail_enter", "tail_exit", "max_rounds")]
+
+
 class _NetworkView(ctypes.Structure):
     _fields_ = [("n_nodes", ctypes.c_int32), ("m_nets", ctypes.c_int32),
                 ("p_pins", ctypes.c_int64), ("net_off", ctypes.c_void_p),
@@ -99,6 +104,8 @@ def load():
                                  ctypes.POINTER(_FcResult)]),
         "hfp_max_flow_noalloc": (i32, [i32, P, ctypes.POINTER(_NetworkView), P, P, P]),
         "hfp_net_enable_trace": (i32, [P, i32]),
+        "hfp_ctx_get_tuning": (i32, [P, ctypes.POINTER(Tuning)]),
+        "hfp_ctx_set_tuning": (i32, [P, ctypes.POINTER(Tuning)]),
         "hfp_net_get_trace": (i32, [P, P, P, P, i32, P]),
     }
     for name, (res, args) in sig.items():
@@ -155,6 +162,21 @@ class Context:
 
 def ctx_create(device: int = 0, stream: int | None = None) -> Context:
     return Context(device, stream)
+
+
+def ctx_get_tuning(ctx: Context) -> dict:
+    """hfp_ctx_get_tuning."""
+    t = Tuning()
+    _check(load().hfp_ctx_get_tuning(ctx.h, ctypes.byref(t)))
+    return {k: int(getattr(t, k)) for k, _ in Tuning._fields_}
+
+
+def ctx_set_tuning(ctx: Context, **kw):
+    """hfp_ctx_set_tuning: change the given knobs, keep the others."""
+    cur = ctx_get_tuning(ctx)
+    cur.update(kw)
+    t = Tuning(**cur)
+    _check(load().hfp_ctx_set_tuning(ctx.h, ctypes.byref(t)))
 
 
 @dataclass

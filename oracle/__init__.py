@@ -315,3 +315,139 @@ def node_arrays(net: FlowNetwork, side, region, dist_region):
     gid = np.full(net.n_nodes, -1, np.int32)
     gid[2:] = region
     return orig, dist, gid
+
+
+# ---------------------------------------------------------------------------
+# k-way refinement (Section 4, Algorithm 1; Section 5; Section 6)
+
+def _kway_sig():
+    lib = _load()
+    P, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    if not hasattr(lib, "_kway_ready"):
+        lib.or_connectivity.restype = i64
+        lib.or_connectivity.argtypes = [i32, P, P, P, P, i32]
+        lib.or_quotient.restype = None
+        lib.or_quotient.argtypes = [i32, P, P, P, P, i32, P, P]
+        lib.or_grow_region.restype = i32
+        lib.or_grow_region.argtypes = [i32, i32, P, P, P, P, i32, i32, i32, i32, P, P, P]
+        lib.or_apply_moves.restype = i64
+        lib.or_apply_moves.argtypes = [i32, i32, P, P, P, P, P, i32, i64, P, i32, P, P]
+        lib._kway_ready = True
+    return lib
+
+
+def _hp(H):
+    return (_c(H.net_off, np.uint32), _c(H.pins, np.int32), _c(H.net_w, np.int32),
+            _c(H.node_w, np.int32))
+
+
+def connectivity(H, part, k: int) -> int:
+    """(lambda - 1)(Pi) = sum_e (lambda(e) - 1) w(e) (Section 2)."""
+    off, pins, nw, _ = _hp(H)
+    return int(_kway_sig().or_connectivity(H.m, _p(off), _p(pins), _p(nw),
+                                           _p(_c(part, np.int32)), k))
+
+
+def quotient(H, part, k: int):
+    """Quotient graph (Section 5): per block pair i < j, number and weight of
+    nets with pins in both.  Returns (nets[k, k], weight[k, k])."""
+    off, pins, nw, _ = _hp(H)
+    a = np.zeros((k, k), np.int64)
+    b = np.zeros((k, k), np.int64)
+    _kway_sig().or_quotient(H.m, _p(off), _p(pins), _p(nw), _p(_c(part, np.int32)), k, _p(a),
+                            _p(b))
+    return a, b
+
+
+def grow_region(H, part, bi: int, bj: int, alpha_eps_pct: int = 48, delta: int = 2):
+    """Region of the pair (bi, bj) and the distances of its vertices
+    (Section 6, "Region Growing"; see oracle.c for the readings)."""
+    off, pins, nw, cw = _hp(H)
+    region = np.zeros(max(H.n, 1), np.int32)
+    dist = np.zeros(max(H.n, 1), np.int32)
+    nr = np.zeros(1, np.int32)
+    _kway_sig().or_grow_region(H.n, H.m, _p(off), _p(pins), _p(cw), _p(_c(part, np.int32)),
+                               bi, bj, alpha_eps_pct, delta, _p(region), _p(dist), _p(nr))
+    k = int(nr[0])
+    return region[:k].copy(), dist[:k].copy()
+
+
+def apply_moves(H, part: np.ndarray, k: int, max_w: int, moves: np.ndarray):
+    """Section 5, "Apply Moves": returns (gain, applied, n_valid); part is
+    updated in place.  moves: int32[n, 3] rows (vertex, from, to)."""
+    off, pins, nw, cw = _hp(H)
+    assert part.dtype == np.int32 and part.flags.c_contiguous
+    mv = _c(moves, np.int32).reshape(-1)
+    applied = np.zeros(1, np.int32)
+    nv = np.zeros(1, np.int32)
+    g = _kway_sig().or_apply_moves(H.n, H.m, _p(off), _p(pins), _p(nw), _p(cw), _p(part), k,
+                                   int(max_w), _p(mv) if len(mv) else None, len(mv) // 3,
+                                   _p(applied), _p(nv))
+    return int(g), int(applied[0]), int(nv[0])
+
+
+@dataclass
+class PairResult:
+    bi: int
+    bj: int
+    status: int
+    moves: np.ndarray        # int32[n, 3]: (vertex, from, to)
+    delta_exp: int
+    flow: int
+    original_cut: int
+    region_size: int
+    pins: int
+
+
+def refine_block_pair(H, part, k: int, bi: int, bj: int, eps_pct: int = 3,
+                      alpha_eps_pct: int = 48, delta: int = 2, seed: int = 0) -> PairResult:
+    """One block pair of Algorithm 1: region (Section 6), flow network,
+    FlowCutter with the k-way balance bound and the original pair cut as flow
+    bound (Section 7; Section 8.3 "Flow Value"), moves and the expected gain
+    Delta_exp = original cut on the network's nets - final flow."""
+    part = np.asarray(part, np.int32)
+    side = np.where(part == bi, 0, np.where(part == bj, 1, -1)).astype(np.int32)
+    region, dist = grow_region(H, part, bi, bj, alpha_eps_pct, delta)
+    net = build_network(H, side, region)
+    L = max_block_weight(int(np.asarray(H.node_w, np.int64).sum()), k, eps_pct)
+    in_src = np.zeros(net.n_nodes, bool)
+    in_src[0] = True
+    in_src[2:] = side[region] == 0
+    cut0 = cut_weight(net, in_src)
+    orig, d, gid = node_arrays(net, side, region, dist)
+    r = flowcutter(net, L, orig, d, gid, seed=seed, flow_bound=cut0)
+    empty = np.zeros((0, 3), np.int32)
+    if r.status != OK:
+        return PairResult(bi, bj, r.status, empty, 0, r.flow, cut0, len(region), net.p)
+    fin = r.final_side[2:]
+    ch = np.nonzero(fin != side[region])[0]
+    frm = np.where(side[region[ch]] == 0, bi, bj)
+    to = np.where(fin[ch] == 0, bi, bj)
+    moves = np.stack([region[ch], frm, to], axis=1).astype(np.int32) if len(ch) else empty
+    return PairResult(bi, bj, OK, moves, cut0 - r.flow, r.flow, cut0, len(region), net.p)
+
+
+def refine_round(H, part, k: int, eps_pct: int = 3, alpha_eps_pct: int = 48, delta: int = 2,
+                 seed: int = 0, pairs=None):
+    """One synchronous round of Algorithm 1: every pair of adjacent blocks is
+    refined against the same partition; the move sets with Delta_exp >= 0 are
+    applied in descending Delta_exp (ties: ascending (i, j)) with the
+    conflict rules of Section 5.  pairs: optional list of (i, j) to refine
+    (default: every quotient-graph edge).  Returns (new part, total gain,
+    results, gains)."""
+    part = np.array(part, dtype=np.int32)
+    if pairs is None:
+        qn, _ = quotient(H, part, k)
+        pairs = [(i, j) for i in range(k) for j in range(i + 1, k) if qn[i, j] > 0]
+    res = [refine_block_pair(H, part, k, i, j, eps_pct, alpha_eps_pct, delta, seed)
+           for i, j in pairs]
+    L = max_block_weight(int(np.asarray(H.node_w, np.int64).sum()), k, eps_pct)
+    order = sorted((r for r in res if r.status == OK and r.delta_exp >= 0 and len(r.moves)),
+                   key=lambda r: (-r.delta_exp, r.bi, r.bj))
+    gains = {}
+    total = 0
+    for r in order:
+        g, applied, nv = apply_moves(H, part, k, L, r.moves)
+        gains[(r.bi, r.bj)] = (g, applied, nv)
+        total += g
+    return part, total, res, gains

@@ -588,3 +588,188 @@ int32_t or_flowcutter(Lawler *G, int64_t max_w, const int32_t *orig_side, const 
     free(S); free(T); free(Sr); free(Tr); free(cand);
     return status;
 }
+
+/* ------------------------------------------------------------------------ */
+/* k-way refinement pieces (Section 4, Algorithm 1; Section 5; Section 6). */
+
+/* Connectivity metric (lambda - 1)(Pi) = sum over nets of (lambda(e) - 1) w(e)
+ * (Section 2). */
+int64_t or_connectivity(int32_t m, const uint32_t *net_off, const int32_t *pins,
+                        const int32_t *net_w, const int32_t *part, int32_t k) {
+    uint8_t *seen = (uint8_t *)calloc((size_t)(k > 0 ? k : 1), 1);
+    int64_t total = 0;
+    for (int32_t e = 0; e < m; e++) {
+        int32_t lam = 0;
+        for (uint32_t j = net_off[e]; j < net_off[e + 1]; j++) {
+            int32_t b = part[pins[j]];
+            if (!seen[b]) { seen[b] = 1; lam++; }
+        }
+        for (uint32_t j = net_off[e]; j < net_off[e + 1]; j++) seen[part[pins[j]]] = 0;
+        if (lam > 1) total += (int64_t)(lam - 1) * net_w[e];
+    }
+    free(seen);
+    return total;
+}
+
+/* Quotient graph (Section 5, "Quotient Graph Construction"): for every pair
+ * of blocks i < j, the number and weight of nets with pins in both.  Arrays
+ * are k*k, row-major, upper triangle used. */
+void or_quotient(int32_t m, const uint32_t *net_off, const int32_t *pins, const int32_t *net_w,
+                 const int32_t *part, int32_t k, int64_t *pair_nets, int64_t *pair_weight) {
+    uint8_t *seen = (uint8_t *)calloc((size_t)k, 1);
+    int32_t *blocks = (int32_t *)malloc(sizeof(int32_t) * (size_t)k);
+    memset(pair_nets, 0, sizeof(int64_t) * (size_t)k * k);
+    memset(pair_weight, 0, sizeof(int64_t) * (size_t)k * k);
+    for (int32_t e = 0; e < m; e++) {
+        int32_t nb = 0;
+        for (uint32_t j = net_off[e]; j < net_off[e + 1]; j++) {
+            int32_t b = part[pins[j]];
+            if (!seen[b]) { seen[b] = 1; blocks[nb++] = b; }
+        }
+        for (int32_t a = 0; a < nb; a++) {
+            seen[blocks[a]] = 0;
+            for (int32_t c = 0; c < nb; c++) {
+                int32_t i = blocks[a], jj = blocks[c];
+                if (i < jj) { pair_nets[(size_t)i * k + jj]++; pair_weight[(size_t)i * k + jj] += net_w[e]; }
+            }
+        }
+    }
+    free(seen);
+    free(blocks);
+}
+
+/* Region growing for the pair (bi, bj) (Section 6, "Region Growing"), with
+ * the readings used throughout: a breadth-first search inside each block
+ * from its pins of the pair's cut nets (distance 1), through nets of H, up
+ * to distance delta; vertices are taken level by level in ascending id
+ * order while the block's part of the region stays within
+ *   bound_i = max(0, floor((100 + alpha_eps_pct) * ceil((c(Vi)+c(Vj))/2) / 100) - c(Vj))
+ * (alpha_eps_pct = 100 * alpha * eps, 48 for alpha = 16, eps = 0.03); the
+ * first vertex that does not fit ends that block's growth.  Output: the
+ * region in ascending id order and the distance of each region vertex. */
+int32_t or_grow_region(int32_t n, int32_t m, const uint32_t *net_off, const int32_t *pins,
+                       const int32_t *node_w, const int32_t *part, int32_t bi, int32_t bj,
+                       int32_t alpha_eps_pct, int32_t delta, int32_t *region, int32_t *dist,
+                       int32_t *n_region) {
+    int64_t cw[2] = {0, 0};
+    for (int32_t v = 0; v < n; v++) {
+        int64_t c = node_w ? node_w[v] : 1;
+        if (part[v] == bi) cw[0] += c;
+        else if (part[v] == bj) cw[1] += c;
+    }
+    int64_t half = (cw[0] + cw[1] + 1) / 2;
+    int64_t lim = ((int64_t)(100 + alpha_eps_pct) * half) / 100;
+    int64_t bound[2] = {lim - cw[1], lim - cw[0]};
+    if (bound[0] < 0) bound[0] = 0;
+    if (bound[1] < 0) bound[1] = 0;
+    /* vertex -> nets incidence */
+    int32_t *deg = (int32_t *)calloc((size_t)n + 1, sizeof(int32_t));
+    for (int32_t e = 0; e < m; e++)
+        for (uint32_t j = net_off[e]; j < net_off[e + 1]; j++) deg[pins[j] + 1]++;
+    for (int32_t v = 0; v < n; v++) deg[v + 1] += deg[v];
+    int32_t *inc = (int32_t *)malloc(sizeof(int32_t) * (size_t)(deg[n] > 0 ? deg[n] : 1));
+    int32_t *fill = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    memcpy(fill, deg, sizeof(int32_t) * (size_t)n);
+    for (int32_t e = 0; e < m; e++)
+        for (uint32_t j = net_off[e]; j < net_off[e + 1]; j++) inc[fill[pins[j]]++] = e;
+    int32_t *lev = (int32_t *)calloc((size_t)n, sizeof(int32_t));   /* 0 = not reached */
+    uint8_t *in_b = (uint8_t *)calloc((size_t)n, 1);
+    int32_t *cur = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    for (int s = 0; s < 2; s++) {
+        int32_t blk = s == 0 ? bi : bj, oth = s == 0 ? bj : bi;
+        int64_t taken = 0;
+        int stop = 0;
+        /* level 1: pins in blk of nets with pins in both blocks */
+        for (int32_t e = 0; e < m; e++) {
+            int a = 0, b = 0;
+            for (uint32_t j = net_off[e]; j < net_off[e + 1]; j++) {
+                if (part[pins[j]] == blk) a = 1;
+                if (part[pins[j]] == oth) b = 1;
+            }
+            if (!(a && b)) continue;
+            for (uint32_t j = net_off[e]; j < net_off[e + 1]; j++)
+                if (part[pins[j]] == blk && !lev[pins[j]]) lev[pins[j]] = 1;
+        }
+        for (int32_t d = 1; d <= delta && !stop; d++) {
+            /* vertices at distance d in ascending id: take while they fit */
+            int32_t nc = 0;
+            for (int32_t v = 0; v < n; v++) if (part[v] == blk && lev[v] == d) cur[nc++] = v;
+            for (int32_t q = 0; q < nc && !stop; q++) {
+                int32_t v = cur[q];
+                int64_t c = node_w ? node_w[v] : 1;
+                if (taken + c > bound[s]) { stop = 1; break; }
+                taken += c;
+                in_b[v] = 1;
+            }
+            if (stop || d == delta) break;
+            /* next level: unlabelled vertices of blk sharing a net with a taken
+               vertex at distance d */
+            for (int32_t q = 0; q < nc; q++) {
+                int32_t v = cur[q];
+                if (!in_b[v]) continue;
+                for (int32_t t = deg[v]; t < deg[v + 1]; t++) {
+                    int32_t e = inc[t];
+                    for (uint32_t j = net_off[e]; j < net_off[e + 1]; j++) {
+                        int32_t u = pins[j];
+                        if (part[u] == blk && !lev[u]) lev[u] = d + 1;
+                    }
+                }
+            }
+        }
+    }
+    int32_t nr = 0;
+    for (int32_t v = 0; v < n; v++)
+        if (in_b[v]) { region[nr] = v; dist[nr] = lev[v]; nr++; }
+    *n_region = nr;
+    free(deg); free(inc); free(fill); free(lev); free(in_b); free(cur);
+    return OR_OK;
+}
+
+/* Apply the moves of one pair to the partition (Section 5, "Apply Moves"):
+ * drop moves whose vertex is not in its expected block; apply the rest only
+ * if every block that gains weight stays within max_w (the reading of "the
+ * resulting partition is balanced" for an input that may already be
+ * imbalanced); the actual change is the connectivity
+ * metric before minus after (which the paper accumulates from the
+ * Phi(e, V) transitions of each move).  If the metric grew, the moves are
+ * reverted.  moves: (vertex, from, to) triples.  Returns the improvement
+ * (>= 0, positive = better); *applied = 1 if kept.  part is updated. */
+int64_t or_apply_moves(int32_t n, int32_t m, const uint32_t *net_off, const int32_t *pins,
+                       const int32_t *net_w, const int32_t *node_w, int32_t *part, int32_t k,
+                       int64_t max_w, const int32_t *moves, int32_t n_moves, int32_t *applied,
+                       int32_t *n_valid) {
+    int32_t *valid = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n_moves > 0 ? n_moves : 1));
+    int32_t nv = 0;
+    for (int32_t q = 0; q < n_moves; q++)
+        if (part[moves[3 * q]] == moves[3 * q + 1]) valid[nv++] = q;
+    *n_valid = nv;
+    int64_t *bw = (int64_t *)calloc((size_t)k, sizeof(int64_t));
+    int64_t *bw0 = (int64_t *)calloc((size_t)k, sizeof(int64_t));
+    for (int32_t v = 0; v < n; v++) bw[part[v]] += node_w ? node_w[v] : 1;
+    memcpy(bw0, bw, sizeof(int64_t) * (size_t)k);
+    for (int32_t t = 0; t < nv; t++) {
+        const int32_t *mv = moves + 3 * valid[t];
+        int64_t c = node_w ? node_w[mv[0]] : 1;
+        bw[mv[1]] -= c;
+        bw[mv[2]] += c;
+    }
+    /* balanced: every block that gains weight stays within max_w (a block
+       already above it may only lose weight) */
+    int ok = 1;
+    for (int32_t b = 0; b < k; b++) if (bw[b] > bw0[b] && bw[b] > max_w) ok = 0;
+    free(bw0);
+    *applied = 0;
+    if (!ok || nv == 0) { free(valid); free(bw); return 0; }
+    int64_t before = or_connectivity(m, net_off, pins, net_w, part, k);
+    for (int32_t t = 0; t < nv; t++) part[moves[3 * valid[t]]] = moves[3 * valid[t] + 2];
+    int64_t after = or_connectivity(m, net_off, pins, net_w, part, k);
+    int64_t gain = before - after;
+    if (gain < 0) {
+        for (int32_t t = 0; t < nv; t++) part[moves[3 * valid[t]]] = moves[3 * valid[t] + 1];
+        gain = 0;
+    } else {
+        *applied = 1;
+    }
+    free(valid); free(bw);
+    return gain;
+}

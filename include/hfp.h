@@ -250,6 +250,80 @@ hfp_status hfp_flowcutter(hfp_net* net, const hfp_fc_params* params, uint8_t* fi
                           int32_t* pierce_side, int32_t* pierce_node, int32_t pierce_cap,
                           hfp_fc_result* result);
 
+/* --- k-way refinement (Section 4, Algorithm 1; Sections 5 and 6) ---------
+ * A device-resident hypergraph (with its vertex -> nets incidence) for
+ * refining k-way partitions block pair by block pair.  Partitions are int32
+ * block ids in [0, k) in DEVICE memory, k <= 64. */
+typedef struct hfp_hgraph hfp_hgraph;
+
+typedef struct {
+  int32_t eps_pct;        /* balance: L = floor((100 + eps_pct) * ceil(c(V) / k) / 100) [3] */
+  int32_t alpha_eps_pct;  /* region bound: 100 * alpha * eps [48: alpha = 16, eps = 0.03] */
+  int32_t delta;          /* region vertices are at most delta hops from the pair's cut [2] */
+  uint32_t seed;          /* third piercing key of FlowCutter */
+} hfp_refine_params;
+
+typedef struct {
+  int32_t bi, bj;          /* the block pair */
+  int32_t status;          /* HFP_OK, HFP_NO_BALANCED_CUT or HFP_ABORTED_WORSE */
+  int32_t region_size;
+  int64_t pins;            /* Lawler-network pins of the pair's flow network */
+  int64_t original_cut;    /* weight of the network's nets cut by the input partition */
+  int64_t flow;            /* final flow = cut weight of FlowCutter's bipartition */
+  int64_t delta_exp;       /* original_cut - flow (Algorithm 1: Delta_exp) */
+  int32_t n_moves;         /* region vertices that change block */
+  int32_t iterations;      /* FlowCutter augmentations */
+  int32_t applied;         /* hfp_refine_round: 1 if the moves were kept */
+  int32_t valid_moves;     /* hfp_refine_round: moves that were not stale */
+  int64_t gain;            /* hfp_refine_round: actual reduction of (lambda - 1) */
+} hfp_pair_result;
+
+typedef struct {
+  int64_t connectivity_before, connectivity_after;  /* (lambda - 1), Section 2 */
+  int64_t gain;            /* connectivity_before - connectivity_after */
+  int64_t moves_applied;
+  int32_t pairs;           /* pairs refined */
+  int32_t pairs_improved;  /* pairs with Delta_exp > 0 */
+  int32_t pairs_applied;   /* move sets kept */
+  int32_t pairs_skipped;   /* pairs below min_score */
+} hfp_round_stats;
+
+/* Uploads H (in `mem` memory) and builds its vertex -> nets incidence. */
+hfp_status hfp_hgraph_create(hfp_ctx* ctx, const hfp_hypergraph* H, hfp_mem mem,
+                             hfp_hgraph** out);
+void hfp_hgraph_destroy(hfp_hgraph* hg);
+/* (lambda - 1)(part) = sum over nets of (lambda(e) - 1) w(e) (Section 2). */
+hfp_status hfp_connectivity(hfp_hgraph* hg, const int32_t* part, int32_t k, int64_t* value);
+
+/* One block pair of Algorithm 1 against partition `part` (device): grow the
+ * region B (Section 6: breadth-first search inside each block from its pins
+ * of the pair's cut nets, up to delta hops, vertices taken level by level in
+ * ascending id while the block's share stays within
+ * max(0, floor((100 + alpha_eps_pct) * ceil((c(Vi)+c(Vj))/2) / 100) - c(Vj))),
+ * build its flow network with those distances, run FlowCutter with the k-way
+ * bound L and the original pair cut as flow bound, and report the moves
+ * (vertex, from, to) in ascending vertex order (host buffer of 3 * cap
+ * int32) and Delta_exp = original cut - final flow.  A FlowCutter that finds
+ * no balanced cut or exceeds the bound gives res->status != HFP_OK and no
+ * moves; the call itself still returns HFP_OK. */
+hfp_status hfp_refine_block_pair(hfp_hgraph* hg, const int32_t* part, int32_t k, int32_t bi,
+                                 int32_t bj, const hfp_refine_params* params, int32_t* moves,
+                                 int32_t cap, hfp_pair_result* res);
+
+/* One synchronous round of Algorithm 1 on `part` (device, updated): every
+ * pair of adjacent blocks (quotient graph, Section 5) is refined against the
+ * same partition; pairs with pair_scores[i * k + j] < min_score are skipped
+ * (pair_scores host k * k, or NULL).  The move sets with Delta_exp >= 0 are
+ * applied in descending Delta_exp (ties ascending (i, j)) by the rules of
+ * Section 5, "Apply Moves": stale moves are dropped, a set is skipped if a
+ * block that gains weight would exceed L, and reverted if its actual gain
+ * is negative.  pairs (host, cap entries, may be NULL) receives the per-pair
+ * results in ascending (i, j). */
+hfp_status hfp_refine_round(hfp_hgraph* hg, int32_t* part, int32_t k,
+                            const hfp_refine_params* params, const float* pair_scores,
+                            float min_score, hfp_round_stats* stats, hfp_pair_result* pairs,
+                            int32_t cap, int32_t* n_pairs);
+
 /* --- allocation-free max flow ---------------------------------------------
  * The paper has no counterpart to this entry point; it exists for callers
  * that cannot allocate device memory where they need a flow: code inside a

@@ -9,12 +9,7 @@
 #include <string>
 #include <vector>
 
-#include "hfp.h"
-#include "kernels.cuh"
-
-#include <atomic>
-
-#define HFP_API extern "C" __attribute__((visibility("default")))
+#include "internal.h"
 
 using namespace hfp;
 
@@ -24,9 +19,11 @@ void count_launches(unsigned k) { g_launches.fetch_add(k, std::memory_order_rela
 unsigned long long launches_total() { return g_launches.load(std::memory_order_relaxed); }
 }  // namespace hfp
 
-namespace {
+namespace hfp {
 
+namespace {
 thread_local std::string g_err;
+}  // namespace
 
 hfp_status fail(hfp_status s, const char* fmt, ...) {
   char buf[512];
@@ -38,33 +35,12 @@ hfp_status fail(hfp_status s, const char* fmt, ...) {
   return s;
 }
 
-#define CK(call)                                                                          \
-  do {                                                                                    \
-    cudaError_t e_ = (call);                                                              \
-    if (e_ != cudaSuccess)                                                                \
-      return fail(e_ == cudaErrorMemoryAllocation ? HFP_ERR_OOM : HFP_ERR_CUDA,           \
-                  "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__,       \
-                  __LINE__);                                                              \
-  } while (0)
+// error message setter for entry points defined in other translation units
+void set_last_error(const char* msg) { g_err = msg; }
 
-// Stream-ordered device allocation owned by a scope.
-struct DevBuf {
-  void* p = nullptr;
-  cudaStream_t st = nullptr;
-  DevBuf() = default;
-  DevBuf(const DevBuf&) = delete;
-  ~DevBuf() {
-    if (p) cudaFreeAsync(p, st);
-  }
-  cudaError_t alloc(size_t bytes, cudaStream_t s) {
-    st = s;
-    return cudaMallocAsync(&p, bytes ? bytes : 16, s);
-  }
-  template <class T>
-  T* as() const { return static_cast<T*>(p); }
-};
+}  // namespace hfp
 
-size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
+namespace {
 
 int map_dev_err(int e) {
   switch (e) {
@@ -75,44 +51,6 @@ int map_dev_err(int e) {
 }
 
 }  // namespace
-
-namespace hfp {
-// error message setter for entry points defined in other translation units
-void set_last_error(const char* msg) { g_err = msg; }
-}  // namespace hfp
-
-struct hfp_ctx {
-  std::atomic<int> refs{1};        // the caller's handle + one per live network
-  int device = 0;
-  cudaStream_t stream = nullptr;
-  int sms = 0;
-  int coop_grid = 0;
-  int threads = kEngineThreads;
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // engine launch timing
-  Ctl* pinned_ctl = nullptr;       // host mirror of Ctl
-  void* pinned_small = nullptr;    // 4 KB staging
-  Params params{};
-  uint32_t gr_work_x100 = 200;
-};
-
-struct hfp_net {
-  hfp_ctx* ctx = nullptr;
-  NetDev d{};
-  EngineCtl* E = nullptr;
-  void* arena = nullptr;
-  int32_t* net_gid = nullptr;
-  int32_t* dev_nodes = nullptr;    // staging for pierced node ids
-  int32_t dev_nodes_cap = 0;
-  int32_t n_region = 0;
-  int64_t total_w = 0;
-  bool flow_started = false;
-  bool labels_exact = false;
-  bool sr_valid = false;
-  bool dist_ready = false;
-  void* trace_buf = nullptr;
-  uint64_t launches = 0;
-  uint64_t engine_ns = 0;
-};
 
 namespace {
 
@@ -219,7 +157,7 @@ hfp_status copy_out(void* dst, const void* src, size_t bytes, hfp_mem mem, cudaS
 }  // namespace
 
 // ---------------------------------------------------------------------------
-HFP_API const char* hfp_last_error(void) { return g_err.c_str(); }
+HFP_API const char* hfp_last_error(void) { return hfp::g_err.c_str(); }
 
 HFP_API uint64_t hfp_kernel_launches(void) { return launches_total(); }
 

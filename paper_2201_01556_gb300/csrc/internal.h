@@ -1,0 +1,82 @@
+// Host-side internals shared by the C ABI translation units (api.cu,
+// kway.cu): context and network objects, error reporting, stream-ordered
+// device buffers.
+#pragma once
+#include <atomic>
+#include <cstdarg>
+#include <cstdio>
+#include <string>
+
+#include "hfp.h"
+#include "kernels.cuh"
+
+#define HFP_API extern "C" __attribute__((visibility("default")))
+
+namespace hfp {
+
+// Records a message for hfp_last_error and returns s.
+hfp_status fail(hfp_status s, const char* fmt, ...);
+void set_last_error(const char* msg);
+
+#define CK(call)                                                                          \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return ::hfp::fail(e_ == cudaErrorMemoryAllocation ? HFP_ERR_OOM : HFP_ERR_CUDA,    \
+                         "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                         __LINE__);                                                       \
+  } while (0)
+
+// Stream-ordered device allocation owned by a scope.
+struct DevBuf {
+  void* p = nullptr;
+  cudaStream_t st = nullptr;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  ~DevBuf() {
+    if (p) cudaFreeAsync(p, st);
+  }
+  cudaError_t alloc(size_t bytes, cudaStream_t s) {
+    st = s;
+    return cudaMallocAsync(&p, bytes ? bytes : 16, s);
+  }
+  template <class T>
+  T* as() const { return static_cast<T*>(p); }
+};
+
+inline size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
+
+}  // namespace hfp
+
+struct hfp_ctx {
+  std::atomic<int> refs{1};        // the caller's handle + one per live network
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int sms = 0;
+  int coop_grid = 0;
+  int threads = hfp::kEngineThreads;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // engine launch timing
+  hfp::Ctl* pinned_ctl = nullptr;  // host mirror of Ctl
+  void* pinned_small = nullptr;    // 4 KB staging
+  hfp::Params params{};
+  uint32_t gr_work_x100 = 200;
+};
+
+struct hfp_net {
+  hfp_ctx* ctx = nullptr;
+  hfp::NetDev d{};
+  hfp::EngineCtl* E = nullptr;
+  void* arena = nullptr;
+  int32_t* net_gid = nullptr;
+  int32_t* dev_nodes = nullptr;    // staging for pierced node ids
+  int32_t dev_nodes_cap = 0;
+  int32_t n_region = 0;
+  int64_t total_w = 0;
+  bool flow_started = false;
+  bool labels_exact = false;
+  bool sr_valid = false;
+  bool dist_ready = false;
+  void* trace_buf = nullptr;
+  uint64_t launches = 0;
+  uint64_t engine_ns = 0;
+};

@@ -1,0 +1,827 @@
+// k-way flow-based refinement (Section 4, Algorithm 1; Section 5; Section 6):
+// a device-resident hypergraph with its vertex -> nets incidence, region
+// growing for a block pair, refine_block_pair (region, flow network,
+// FlowCutter, moves) and a synchronous refinement round with the
+// apply-moves rules of Section 5.
+//
+// Readings (shared with the oracle): the region of pair (i, j) is grown
+// inside each block by breadth-first search from the block's pins of the
+// pair's cut nets (distance 1) up to distance delta, taking vertices level by
+// level in ascending id order while the block's share stays within
+//   max(0, floor((100 + alpha_eps_pct) * ceil((c(Vi)+c(Vj))/2) / 100) - c(Vj));
+// the first vertex that does not fit ends that block's growth.  A round
+// refines every pair against the same partition, then applies the move sets
+// with Delta_exp >= 0 in descending Delta_exp (ties: ascending (i, j)),
+// dropping stale moves, skipping a set that would push a growing block past
+// the bound, and reverting a set whose actual gain is negative.
+#include <algorithm>
+#include <cstring>
+#include <deque>
+#include <vector>
+
+#include "internal.h"
+
+using namespace hfp;
+
+struct hfp_hgraph {
+  hfp_ctx* ctx = nullptr;
+  int32_t n = 0, m = 0;
+  int64_t p = 0;
+  int64_t total_w = 0;
+  void* arena = nullptr;
+  uint32_t* net_off = nullptr;
+  int32_t* pins = nullptr;
+  int32_t* net_w = nullptr;
+  int32_t* node_w = nullptr;
+  uint32_t* vnet_off = nullptr;   // vertex -> nets incidence (ascending net ids)
+  int32_t* vnet = nullptr;
+};
+
+namespace hfp {
+
+namespace {
+
+inline unsigned nb(long long work, unsigned per, unsigned cap) {
+  long long b = (work + per - 1) / per;
+  if (b < 1) b = 1;
+  if (b > cap) b = cap;
+  return (unsigned)b;
+}
+
+// ---------------------------------------------------------------------------
+// incidence of H
+__global__ void k_vdeg(int32_t m, const uint32_t* net_off, const int32_t* pins, unsigned* deg) {
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < (long long)net_off[m];
+       j += (long long)gridDim.x * blockDim.x)
+    atomicAdd(&deg[pins[j]], 1u);
+}
+
+__global__ void k_vfill(int32_t m, const uint32_t* net_off, const int32_t* pins,
+                        const unsigned* off, unsigned* cursor, int32_t* vnet) {
+  const unsigned lane = threadIdx.x & 31;
+  const unsigned gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const unsigned nw = (gridDim.x * blockDim.x) >> 5;
+  for (unsigned e = gw; e < (unsigned)m; e += nw)
+    for (unsigned j = net_off[e] + lane; j < net_off[e + 1]; j += 32) {
+      const int v = pins[j];
+      vnet[off[v] + atomicAdd(&cursor[v], 1u)] = (int32_t)e;
+    }
+}
+
+// warp per vertex: sort its net ids (rank sort; ids are distinct)
+__global__ void k_vsort(int32_t n, const unsigned* off, int32_t* vnet, int32_t* tmp) {
+  const unsigned lane = threadIdx.x & 31;
+  const unsigned gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const unsigned nw = (gridDim.x * blockDim.x) >> 5;
+  for (unsigned v = gw; v < (unsigned)n; v += nw) {
+    const unsigned beg = off[v], d = off[v + 1] - beg;
+    if (d <= 1) continue;
+    if (d <= 32) {
+      const int mine = lane < d ? vnet[beg + lane] : 0x7fffffff;
+      unsigned rank = 0;
+      for (unsigned k = 0; k < d; k++) rank += (__shfl_sync(0xffffffffu, mine, k) < mine);
+      __syncwarp();
+      if (lane < d) vnet[beg + rank] = mine;
+    } else {
+      for (unsigned i = lane; i < d; i += 32) {
+        const int mine = vnet[beg + i];
+        unsigned rank = 0;
+        for (unsigned k = 0; k < d; k++) rank += (vnet[beg + k] < mine);
+        tmp[beg + rank] = mine;
+      }
+      __syncwarp();
+      for (unsigned i = lane; i < d; i += 32) vnet[beg + i] = tmp[beg + i];
+    }
+  }
+}
+
+__global__ void k_unit_weights(int32_t n, int32_t* w) {
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) w[v] = 1;
+}
+
+// ---------------------------------------------------------------------------
+// pair region
+__global__ void k_side(int32_t n, const int32_t* part, int32_t bi, int32_t bj,
+                       const int32_t* node_w, int32_t* side, int32_t* lev,
+                       unsigned long long* wsum) {
+  unsigned long long a = 0, b = 0;
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+    const int p = part[v];
+    const int s = p == bi ? 0 : (p == bj ? 1 : -1);
+    side[v] = s;
+    lev[v] = 0;
+    if (s == 0) a += node_w[v];
+    if (s == 1) b += node_w[v];
+  }
+  if (a) atomicAdd(&wsum[0], a);
+  if (b) atomicAdd(&wsum[1], b);
+}
+
+// warp per net: region pins of nets with pins on both sides get level 1
+__global__ void k_level1(int32_t m, const uint32_t* net_off, const int32_t* pins,
+                         const int32_t* side, int32_t* lev) {
+  const unsigned lane = threadIdx.x & 31;
+  const unsigned gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const unsigned nw = (gridDim.x * blockDim.x) >> 5;
+  for (unsigned e = gw; e < (unsigned)m; e += nw) {
+    const unsigned beg = net_off[e], end = net_off[e + 1];
+    bool a = false, b = false;
+    for (unsigned j0 = beg; j0 < end; j0 += 32) {
+      const unsigned j = j0 + lane;
+      const int s = j < end ? side[pins[j]] : -1;
+      a |= __any_sync(0xffffffffu, s == 0);
+      b |= __any_sync(0xffffffffu, s == 1);
+    }
+    if (!(a && b)) continue;
+    for (unsigned j = beg + lane; j < end; j += 32) {
+      const int v = pins[j];
+      if (side[v] >= 0) lev[v] = 1;
+    }
+  }
+}
+
+__global__ void k_flag(int32_t n, const int32_t* side, const int32_t* lev, int s, int d,
+                       unsigned* flag) {
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+    flag[v] = (side[v] == s && lev[v] == d) ? 1u : 0u;
+}
+
+__global__ void k_scatter(int32_t n, const unsigned* flag, const unsigned* pos, int32_t* out,
+                          const int32_t* node_w, unsigned* wout) {
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+    if (flag[v]) {
+      out[pos[v]] = v;
+      if (wout) wout[pos[v]] = (unsigned)node_w[v];
+    }
+}
+
+// candidates in ascending order with exclusive weight prefix wpre: the first
+// ones whose inclusive prefix fits in the budget are taken
+__global__ void k_take(unsigned cnt, const int32_t* cand, const unsigned* wpre,
+                       const int32_t* node_w, long long budget, uint8_t* in_b,
+                       unsigned* taken) {
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x) {
+    const int v = cand[i];
+    if ((long long)wpre[i] + node_w[v] <= budget) {
+      in_b[v] = 1;
+      atomicAdd(taken, 1u);
+    }
+  }
+}
+
+// next BFS level inside the block: from taken vertices of level d, pins of
+// their nets on the same side still unlabelled get level d + 1
+__global__ void k_next_level(unsigned cnt, const int32_t* cand, const uint32_t* vnet_off,
+                             const int32_t* vnet, const uint32_t* net_off, const int32_t* pins,
+                             const int32_t* side, int s, int32_t* lev, int d1) {
+  const unsigned lane = threadIdx.x & 31;
+  const unsigned gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const unsigned nw = (gridDim.x * blockDim.x) >> 5;
+  for (unsigned i = gw; i < cnt; i += nw) {
+    const int v = cand[i];
+    for (unsigned t = vnet_off[v]; t < vnet_off[v + 1]; t++) {
+      const int e = vnet[t];
+      for (unsigned j = net_off[e] + lane; j < net_off[e + 1]; j += 32) {
+        const int u = pins[j];
+        if (side[u] == s && lev[u] == 0) atomicCAS(&lev[u], 0, d1);
+      }
+    }
+  }
+}
+
+__global__ void k_inb_flag(int32_t n, const uint8_t* in_b, unsigned* flag) {
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+    flag[v] = in_b[v];
+}
+
+__global__ void k_region_dist(unsigned cnt, const int32_t* region, const int32_t* lev,
+                              int32_t* dist) {
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x)
+    dist[i] = lev[region[i]];
+}
+
+// original cut of the pair on the network's nets (s counts as side 0, t as 1)
+__global__ void k_pair_cut(const NetDev N, unsigned long long* cut) {
+  const unsigned lane = threadIdx.x & 31;
+  const unsigned gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const unsigned nw = (gridDim.x * blockDim.x) >> 5;
+  unsigned long long acc = 0;
+  for (unsigned e = gw; e < (unsigned)N.m_nets; e += nw) {
+    bool a = false, b = false;
+    for (unsigned p0 = N.net_off[e]; p0 < N.net_off[e + 1]; p0 += 32) {
+      const unsigned p = p0 + lane;
+      int s = -1;
+      if (p < N.net_off[e + 1]) {
+        const int h = N.pin[p];
+        s = h == 0 ? 0 : (h == 1 ? 1 : N.node_orig[h]);
+      }
+      a |= __any_sync(0xffffffffu, s == 0);
+      b |= __any_sync(0xffffffffu, s == 1);
+    }
+    if (lane == 0 && a && b) acc += (unsigned long long)N.net_w[e];
+  }
+  if (acc) atomicAdd(cut, acc);
+}
+
+// moves of a pair: region vertices whose final side differs from the
+// original one, in region order: (vertex, from block, to block)
+__global__ void k_move_flags(unsigned cnt, const int32_t* region, const int32_t* side,
+                             const uint8_t* fin, unsigned* flag) {
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x)
+    flag[i] = (int)fin[i] != side[region[i]] ? 1u : 0u;
+}
+
+__global__ void k_move_fill(unsigned cnt, const int32_t* region, const uint8_t* fin,
+                            const unsigned* flag, const unsigned* pos, int32_t bi, int32_t bj,
+                            int32_t* moves) {
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x)
+    if (flag[i]) {
+      const unsigned q = pos[i];
+      moves[3 * q] = region[i];
+      moves[3 * q + 1] = fin[i] ? bi : bj;
+      moves[3 * q + 2] = fin[i] ? bj : bi;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// round: connectivity, quotient graph, apply moves (k <= 64: block masks)
+__global__ void k_connectivity(int32_t m, const uint32_t* net_off, const int32_t* pins,
+                               const int32_t* net_w, const int32_t* part,
+                               unsigned long long* out, unsigned long long* pair_nets,
+                               unsigned long long* pair_w, int32_t k) {
+  const unsigned lane = threadIdx.x & 31;
+  const unsigned gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const unsigned nw = (gridDim.x * blockDim.x) >> 5;
+  unsigned long long acc = 0;
+  for (unsigned e = gw; e < (unsigned)m; e += nw) {
+    unsigned long long mask = 0;
+    for (unsigned j = net_off[e] + lane; j < net_off[e + 1]; j += 32) mask |= 1ull << part[pins[j]];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mask |= __shfl_xor_sync(0xffffffffu, mask, o);
+    const int lam = __popcll(mask);
+    if (lane == 0 && lam > 1) acc += (unsigned long long)(lam - 1) * net_w[e];
+    if (pair_nets && lam > 1) {
+      // pairs of blocks present, lane-strided over the first block
+      for (int a = lane; a < k; a += 32) {
+        if (!((mask >> a) & 1ull)) continue;
+        unsigned long long rest = mask >> (a + 1);
+        while (rest) {
+          const int b = a + 1 + __ffsll(rest) - 1;
+          rest &= rest - 1;
+          atomicAdd(&pair_nets[a * k + b], 1ull);
+          atomicAdd(&pair_w[a * k + b], (unsigned long long)net_w[e]);
+        }
+      }
+    }
+  }
+  if (lane == 0 && acc) atomicAdd(out, acc);
+}
+
+// stale check and weight change of a move set
+__global__ void k_apply_check(unsigned cnt, const int32_t* mv, const int32_t* part,
+                              const int32_t* node_w, uint8_t* valid, long long* dw,
+                              unsigned* nvalid, int32_t* moved_to, unsigned epoch,
+                              unsigned* moved_stamp) {
+  for (unsigned q = blockIdx.x * blockDim.x + threadIdx.x; q < cnt; q += gridDim.x * blockDim.x) {
+    const int v = mv[3 * q], a = mv[3 * q + 1], b = mv[3 * q + 2];
+    const bool ok = part[v] == a;
+    valid[q] = ok;
+    if (ok) {
+      atomicAdd((unsigned long long*)&dw[a], (unsigned long long)(-(long long)node_w[v]));
+      atomicAdd((unsigned long long*)&dw[b], (unsigned long long)node_w[v]);
+      atomicAdd(nvalid, 1u);
+      moved_to[v] = b;
+      moved_stamp[v] = epoch;
+    }
+  }
+}
+
+// actual gain (Section 5, "Apply Moves"): per net touched by a valid move,
+// w(e) times the number of the two blocks it leaves minus the number it
+// newly reaches.  Each net is claimed once through its stamp.
+__global__ void k_apply_gain(unsigned cnt, const int32_t* mv, const uint8_t* valid,
+                             const uint32_t* vnet_off, const int32_t* vnet,
+                             const uint32_t* net_off, const int32_t* pins, const int32_t* net_w,
+                             const int32_t* part, const int32_t* moved_to,
+                             const unsigned* moved_stamp, unsigned* net_stamp, unsigned epoch,
+                             int32_t bi, int32_t bj, long long* gain) {
+  const unsigned lane = threadIdx.x & 31;
+  const unsigned gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const unsigned nw = (gridDim.x * blockDim.x) >> 5;
+  long long acc = 0;
+  for (unsigned q = gw; q < cnt; q += nw) {
+    if (!valid[q]) continue;
+    const int v = mv[3 * q];
+    for (unsigned t = vnet_off[v]; t < vnet_off[v + 1]; t++) {
+      const int e = vnet[t];
+      int claim = 0;
+      if (lane == 0) claim = atomicExch(&net_stamp[e], epoch) != epoch;
+      claim = __shfl_sync(0xffffffffu, claim, 0);
+      if (!claim) continue;
+      int ca0 = 0, cb0 = 0, ca1 = 0, cb1 = 0;
+      for (unsigned j = net_off[e] + lane; j < net_off[e + 1]; j += 32) {
+        const int u = pins[j];
+        const int before = part[u];
+        const int after = moved_stamp[u] == epoch ? moved_to[u] : before;
+        ca0 += before == bi;
+        cb0 += before == bj;
+        ca1 += after == bi;
+        cb1 += after == bj;
+      }
+      ca0 = __reduce_add_sync(0xffffffffu, ca0);
+      cb0 = __reduce_add_sync(0xffffffffu, cb0);
+      ca1 = __reduce_add_sync(0xffffffffu, ca1);
+      cb1 = __reduce_add_sync(0xffffffffu, cb1);
+      if (lane == 0)
+        acc += (long long)net_w[e] * ((ca0 > 0) + (cb0 > 0) - (ca1 > 0) - (cb1 > 0));
+    }
+  }
+  if (lane == 0 && acc) atomicAdd((unsigned long long*)gain, (unsigned long long)acc);
+}
+
+__global__ void k_apply_commit(unsigned cnt, const int32_t* mv, const uint8_t* valid,
+                               int32_t* part) {
+  for (unsigned q = blockIdx.x * blockDim.x + threadIdx.x; q < cnt; q += gridDim.x * blockDim.x)
+    if (valid[q]) part[mv[3 * q]] = mv[3 * q + 2];
+}
+
+__global__ void k_block_weights(int32_t n, const int32_t* part, const int32_t* node_w,
+                                unsigned long long* bw) {
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+    atomicAdd(&bw[part[v]], (unsigned long long)node_w[v]);
+}
+
+}  // namespace
+
+}  // namespace hfp
+
+namespace {
+
+hfp_status hg_set_device(hfp_hgraph* hg) {
+  CK(cudaSetDevice(hg->ctx->device));
+  return HFP_OK;
+}
+
+// exclusive scan + compaction of flag[0..n) into out (ascending), optionally
+// with the weights; returns the count (synchronises)
+hfp_status compact(hfp_hgraph* hg, unsigned n, unsigned* flag, unsigned* pos, int32_t* out,
+                   unsigned* wout, unsigned* scr, unsigned* tot, unsigned* count) {
+  cudaStream_t st = hg->ctx->stream;
+  CK(cudaMemcpyAsync(pos, flag, sizeof(unsigned) * n, cudaMemcpyDeviceToDevice, st));
+  scan_exclusive(pos, n, scr, tot, st);
+  k_scatter<<<nb(n, 256, hg->ctx->sms * 8), 256, 0, st>>>((int32_t)n, flag, pos, out, hg->node_w,
+                                                          wout);
+  count_launches(1);
+  CK(cudaMemcpyAsync(count, tot, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return HFP_OK;
+}
+
+}  // namespace
+
+HFP_API hfp_status hfp_hgraph_create(hfp_ctx* ctx, const hfp_hypergraph* H, hfp_mem mem,
+                                     hfp_hgraph** out) {
+  if (!out) return fail(HFP_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (!ctx || !H || H->n < 0 || H->m < 0 || !H->net_off || (H->m > 0 && (!H->pins || !H->net_w)))
+    return fail(HFP_ERR_INVALID, "bad hypergraph");
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t st = ctx->stream;
+  const int32_t n = H->n, m = H->m;
+  uint32_t P = 0;
+  if (mem == HFP_MEM_HOST) {
+    P = H->net_off[m];
+  } else {
+    uint32_t* h = (uint32_t*)ctx->pinned_small;
+    CK(cudaMemcpyAsync(h, H->net_off + m, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    P = h[0];
+  }
+  if (P >= (1u << 31)) return fail(HFP_ERR_INVALID, "too many pins");
+  hfp_hgraph* hg = new hfp_hgraph();
+  hg->ctx = ctx;
+  hg->n = n;
+  hg->m = m;
+  hg->p = P;
+  const size_t sz[] = {align_up(sizeof(uint32_t) * (m + 1)), align_up(sizeof(int32_t) * P),
+                       align_up(sizeof(int32_t) * (m > 0 ? m : 1)),
+                       align_up(sizeof(int32_t) * (n > 0 ? n : 1)),
+                       align_up(sizeof(uint32_t) * (n + 1)), align_up(sizeof(int32_t) * P)};
+  size_t total = 0;
+  for (size_t b : sz) total += b;
+  if (cudaMallocAsync(&hg->arena, total, st) != cudaSuccess) {
+    delete hg;
+    return fail(HFP_ERR_OOM, "cannot allocate the hypergraph");
+  }
+  char* q = (char*)hg->arena;
+  hg->net_off = (uint32_t*)q; q += sz[0];
+  hg->pins = (int32_t*)q; q += sz[1];
+  hg->net_w = (int32_t*)q; q += sz[2];
+  hg->node_w = (int32_t*)q; q += sz[3];
+  hg->vnet_off = (uint32_t*)q; q += sz[4];
+  hg->vnet = (int32_t*)q;
+  const cudaMemcpyKind kind = mem == HFP_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  CK(cudaMemcpyAsync(hg->net_off, H->net_off, sizeof(uint32_t) * (m + 1), kind, st));
+  if (P) CK(cudaMemcpyAsync(hg->pins, H->pins, sizeof(int32_t) * P, kind, st));
+  if (m) CK(cudaMemcpyAsync(hg->net_w, H->net_w, sizeof(int32_t) * m, kind, st));
+  if (H->node_w) {
+    if (n) CK(cudaMemcpyAsync(hg->node_w, H->node_w, sizeof(int32_t) * n, kind, st));
+  } else if (n) {
+    k_unit_weights<<<nb(n, 256, ctx->sms * 8), 256, 0, st>>>(n, hg->node_w);
+    count_launches(1);
+  }
+  // vertex -> nets incidence, ascending net ids
+  {
+    DevBuf cursor, tmp, scr, tot;
+    CK(cursor.alloc(sizeof(unsigned) * (n > 0 ? n : 1), st));
+    CK(tmp.alloc(sizeof(int32_t) * (P > 0 ? P : 1), st));
+    CK(scr.alloc(sizeof(unsigned) * (scan_scratch_words(n + 1) + 8), st));
+    CK(tot.alloc(sizeof(unsigned), st));
+    CK(cudaMemsetAsync(hg->vnet_off, 0, sizeof(unsigned) * (n + 1), st));
+    if (P) {
+      k_vdeg<<<nb(P, 256, ctx->sms * 8), 256, 0, st>>>(m, hg->net_off, hg->pins, hg->vnet_off);
+      count_launches(1);
+    }
+    scan_exclusive(hg->vnet_off, n + 1, scr.as<unsigned>(), tot.as<unsigned>(), st);
+    CK(cudaMemsetAsync(cursor.p, 0, sizeof(unsigned) * (n > 0 ? n : 1), st));
+    if (m) {
+      k_vfill<<<nb((long long)m * 32, 256, ctx->sms * 16), 256, 0, st>>>(
+          m, hg->net_off, hg->pins, hg->vnet_off, cursor.as<unsigned>(), hg->vnet);
+      count_launches(1);
+    }
+    if (n) {
+      k_vsort<<<nb((long long)n * 32, 256, ctx->sms * 16), 256, 0, st>>>(n, hg->vnet_off, hg->vnet,
+                                                                         tmp.as<int32_t>());
+      count_launches(1);
+    }
+  }
+  // total vertex weight
+  {
+    DevBuf bw;
+    CK(bw.alloc(sizeof(unsigned long long), st));
+    CK(cudaMemsetAsync(bw.p, 0, sizeof(unsigned long long), st));
+    DevBuf zero;
+    CK(zero.alloc(sizeof(int32_t) * (n > 0 ? n : 1), st));
+    CK(cudaMemsetAsync(zero.p, 0, sizeof(int32_t) * (n > 0 ? n : 1), st));
+    if (n) {
+      k_block_weights<<<nb(n, 256, ctx->sms * 8), 256, 0, st>>>(n, zero.as<int32_t>(), hg->node_w,
+                                                                bw.as<unsigned long long>());
+      count_launches(1);
+    }
+    unsigned long long h = 0;
+    CK(cudaMemcpyAsync(&h, bw.p, sizeof(h), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    hg->total_w = (int64_t)h;
+  }
+  ctx->refs.fetch_add(1);
+  *out = hg;
+  return HFP_OK;
+}
+
+HFP_API void hfp_hgraph_destroy(hfp_hgraph* hg) {
+  if (!hg) return;
+  hfp_ctx* c = hg->ctx;
+  cudaSetDevice(c->device);
+  if (hg->arena) cudaFreeAsync(hg->arena, c->stream);
+  cudaStreamSynchronize(c->stream);
+  delete hg;
+  hfp_ctx_destroy(c);   // releases the reference taken at creation
+}
+
+namespace {
+
+// One pair: region, network, FlowCutter, moves (device) and Delta_exp.
+// moves_dev receives up to cap triples; res->n_moves is the count.
+hfp_status refine_pair(hfp_hgraph* hg, const int32_t* part, int32_t k, int32_t bi, int32_t bj,
+                       const hfp_refine_params* prm, DevBuf& moves_dev, hfp_pair_result* res) {
+  hfp_ctx* ctx = hg->ctx;
+  cudaStream_t st = ctx->stream;
+  const int n = hg->n, m = hg->m, sms = ctx->sms;
+  memset(res, 0, sizeof(*res));
+  res->bi = bi;
+  res->bj = bj;
+  DevBuf side, lev, wsum, flag, pos, cand, wts, scr, tot, inb, taken;
+  CK(side.alloc(sizeof(int32_t) * (n > 0 ? n : 1), st));
+  CK(lev.alloc(sizeof(int32_t) * (n > 0 ? n : 1), st));
+  CK(wsum.alloc(sizeof(unsigned long long) * 2, st));
+  CK(flag.alloc(sizeof(unsigned) * (n > 0 ? n : 1), st));
+  CK(pos.alloc(sizeof(unsigned) * (n > 0 ? n : 1), st));
+  CK(cand.alloc(sizeof(int32_t) * (n > 0 ? n : 1), st));
+  CK(wts.alloc(sizeof(unsigned) * (n > 0 ? n : 1), st));
+  CK(scr.alloc(sizeof(unsigned) * (scan_scratch_words(n) + 8), st));
+  CK(tot.alloc(sizeof(unsigned), st));
+  CK(inb.alloc(n > 0 ? n : 1, st));
+  CK(taken.alloc(sizeof(unsigned), st));
+  CK(cudaMemsetAsync(wsum.p, 0, sizeof(unsigned long long) * 2, st));
+  CK(cudaMemsetAsync(inb.p, 0, n > 0 ? n : 1, st));
+  k_side<<<nb(n, 256, sms * 8), 256, 0, st>>>(n, part, bi, bj, hg->node_w, side.as<int32_t>(),
+                                             lev.as<int32_t>(), wsum.as<unsigned long long>());
+  count_launches(1);
+  if (m) {
+    k_level1<<<nb((long long)m * 32, 256, sms * 16), 256, 0, st>>>(
+        m, hg->net_off, hg->pins, side.as<int32_t>(), lev.as<int32_t>());
+    count_launches(1);
+  }
+  unsigned long long cw[2];
+  CK(cudaMemcpyAsync(cw, wsum.p, sizeof(cw), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  const long long half = (long long)((cw[0] + cw[1] + 1) / 2);
+  const long long lim = ((long long)(100 + prm->alpha_eps_pct) * half) / 100;
+  long long budget[2] = {std::max(0ll, lim - (long long)cw[1]),
+                         std::max(0ll, lim - (long long)cw[0])};
+  unsigned h_cnt = 0;
+  for (int s = 0; s < 2; s++) {
+    long long left = budget[s];
+    for (int d = 1; d <= prm->delta; d++) {
+      k_flag<<<nb(n, 256, sms * 8), 256, 0, st>>>(n, side.as<int32_t>(), lev.as<int32_t>(), s, d,
+                                                  flag.as<unsigned>());
+      count_launches(1);
+      hfp_status r = compact(hg, n, flag.as<unsigned>(), pos.as<unsigned>(), cand.as<int32_t>(),
+                             wts.as<unsigned>(), scr.as<unsigned>(), tot.as<unsigned>(), &h_cnt);
+      if (r != HFP_OK) return r;
+      if (h_cnt == 0) break;
+      unsigned wtot = 0;
+      scan_exclusive(wts.as<unsigned>(), h_cnt, scr.as<unsigned>(), tot.as<unsigned>(), st);
+      CK(cudaMemsetAsync(taken.p, 0, sizeof(unsigned), st));
+      k_take<<<nb(h_cnt, 256, sms * 8), 256, 0, st>>>(h_cnt, cand.as<int32_t>(), wts.as<unsigned>(),
+                                                      hg->node_w, left, inb.as<uint8_t>(),
+                                                      taken.as<unsigned>());
+      count_launches(1);
+      unsigned h2[2];
+      CK(cudaMemcpyAsync(&h2[0], taken.p, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+      CK(cudaMemcpyAsync(&h2[1], tot.p, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      wtot = h2[1];
+      if (h2[0] < h_cnt) break;           // the first vertex that does not fit ends growth
+      left -= (long long)wtot;
+      if (d == prm->delta) break;
+      k_next_level<<<nb((long long)h_cnt * 32, 256, sms * 16), 256, 0, st>>>(
+          h_cnt, cand.as<int32_t>(), hg->vnet_off, hg->vnet, hg->net_off, hg->pins,
+          side.as<int32_t>(), s, lev.as<int32_t>(), d + 1);
+      count_launches(1);
+    }
+  }
+  // region (ascending) and its distances
+  k_inb_flag<<<nb(n, 256, sms * 8), 256, 0, st>>>(n, inb.as<uint8_t>(), flag.as<unsigned>());
+  count_launches(1);
+  unsigned nr = 0;
+  hfp_status r = compact(hg, n, flag.as<unsigned>(), pos.as<unsigned>(), cand.as<int32_t>(),
+                         nullptr, scr.as<unsigned>(), tot.as<unsigned>(), &nr);
+  if (r != HFP_OK) return r;
+  DevBuf dist;
+  CK(dist.alloc(sizeof(int32_t) * (nr > 0 ? nr : 1), st));
+  if (nr) {
+    k_region_dist<<<nb(nr, 256, sms * 8), 256, 0, st>>>(nr, cand.as<int32_t>(), lev.as<int32_t>(),
+                                                        dist.as<int32_t>());
+    count_launches(1);
+  }
+  res->region_size = (int32_t)nr;
+  hfp_hypergraph Hd{n, m, hg->net_off, hg->pins, hg->net_w, hg->node_w};
+  hfp_net* net = nullptr;
+  r = hfp_build_flow_network(ctx, &Hd, HFP_MEM_DEVICE, cand.as<int32_t>(), (int32_t)nr,
+                             side.as<int32_t>(), dist.as<int32_t>(), &net);
+  if (r != HFP_OK) return r;
+  res->pins = net->d.p_pins;
+  {
+    DevBuf cut;
+    CK(cut.alloc(sizeof(unsigned long long), st));
+    CK(cudaMemsetAsync(cut.p, 0, sizeof(unsigned long long), st));
+    if (net->d.m_nets) {
+      k_pair_cut<<<nb((long long)net->d.m_nets * 32, 256, sms * 16), 256, 0, st>>>(
+          net->d, cut.as<unsigned long long>());
+      count_launches(1);
+    }
+    unsigned long long hc = 0;
+    CK(cudaMemcpyAsync(&hc, cut.p, sizeof(hc), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    res->original_cut = (int64_t)hc;
+  }
+  hfp_fc_params fp;
+  fp.max_block_weight = ((100 + prm->eps_pct) * ((hg->total_w + k - 1) / k)) / 100;
+  fp.flow_bound = res->original_cut;
+  fp.seed = prm->seed;
+  fp.max_iterations = 0;
+  hfp_fc_result fr{};
+  r = hfp_flowcutter(net, &fp, nullptr, nullptr, nullptr, 0, &fr);
+  res->status = r;
+  res->flow = fr.flow;
+  res->iterations = fr.iterations;
+  if (r == HFP_NO_BALANCED_CUT || r == HFP_ABORTED_WORSE) {
+    hfp_net_destroy(net);
+    set_last_error("");
+    return HFP_OK;
+  }
+  if (r != HFP_OK) {
+    hfp_net_destroy(net);
+    return r;
+  }
+  res->delta_exp = res->original_cut - fr.flow;
+  // moves in region order
+  DevBuf fin, mflag, mpos;
+  CK(fin.alloc(nr > 0 ? nr : 1, st));
+  CK(mflag.alloc(sizeof(unsigned) * (nr > 0 ? nr : 1), st));
+  CK(mpos.alloc(sizeof(unsigned) * (nr > 0 ? nr : 1), st));
+  unsigned nm = 0;
+  if (nr) {
+    launch_region_side(net->d, fr.result_side, (int32_t)nr, fin.as<uint8_t>(), sms, st);
+    k_move_flags<<<nb(nr, 256, sms * 8), 256, 0, st>>>(nr, cand.as<int32_t>(), side.as<int32_t>(),
+                                                       fin.as<uint8_t>(), mflag.as<unsigned>());
+    count_launches(1);
+    CK(cudaMemcpyAsync(mpos.p, mflag.p, sizeof(unsigned) * nr, cudaMemcpyDeviceToDevice, st));
+    scan_exclusive(mpos.as<unsigned>(), nr, scr.as<unsigned>(), tot.as<unsigned>(), st);
+    CK(cudaMemcpyAsync(&nm, tot.p, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    CK(moves_dev.alloc(sizeof(int32_t) * 3 * (nm > 0 ? nm : 1), st));
+    k_move_fill<<<nb(nr, 256, sms * 8), 256, 0, st>>>(nr, cand.as<int32_t>(), fin.as<uint8_t>(),
+                                                      mflag.as<unsigned>(), mpos.as<unsigned>(),
+                                                      bi, bj, moves_dev.as<int32_t>());
+    count_launches(1);
+  }
+  res->n_moves = (int32_t)nm;
+  hfp_net_destroy(net);
+  return HFP_OK;
+}
+
+}  // namespace
+
+HFP_API hfp_status hfp_refine_block_pair(hfp_hgraph* hg, const int32_t* part, int32_t k,
+                                         int32_t bi, int32_t bj, const hfp_refine_params* prm,
+                                         int32_t* moves, int32_t cap, hfp_pair_result* res) {
+  if (!hg || !part || !prm || !res) return fail(HFP_ERR_INVALID, "NULL argument");
+  if (k < 2 || bi < 0 || bj < 0 || bi >= k || bj >= k || bi == bj || prm->delta < 1)
+    return fail(HFP_ERR_INVALID, "bad block pair");
+  hfp_status s = hg_set_device(hg);
+  if (s != HFP_OK) return s;
+  DevBuf mv;
+  if ((s = refine_pair(hg, part, k, bi, bj, prm, mv, res)) != HFP_OK) return s;
+  if (moves && res->n_moves > 0) {
+    const int32_t c = res->n_moves < cap ? res->n_moves : cap;
+    if (c > 0)
+      CK(cudaMemcpyAsync(moves, mv.p, sizeof(int32_t) * 3 * c, cudaMemcpyDeviceToHost,
+                         hg->ctx->stream));
+    CK(cudaStreamSynchronize(hg->ctx->stream));
+    if (res->n_moves > cap)
+      return fail(HFP_ERR_BUFFER_TOO_SMALL, "moves needs %d entries", res->n_moves);
+  }
+  return HFP_OK;
+}
+
+HFP_API hfp_status hfp_connectivity(hfp_hgraph* hg, const int32_t* part, int32_t k,
+                                    int64_t* value) {
+  if (!hg || !part || !value || k < 1 || k > 64) return fail(HFP_ERR_INVALID, "bad arguments");
+  hfp_status s = hg_set_device(hg);
+  if (s != HFP_OK) return s;
+  cudaStream_t st = hg->ctx->stream;
+  DevBuf out;
+  CK(out.alloc(sizeof(unsigned long long), st));
+  CK(cudaMemsetAsync(out.p, 0, sizeof(unsigned long long), st));
+  if (hg->m) {
+    k_connectivity<<<nb((long long)hg->m * 32, 256, hg->ctx->sms * 16), 256, 0, st>>>(
+        hg->m, hg->net_off, hg->pins, hg->net_w, part, out.as<unsigned long long>(), nullptr,
+        nullptr, k);
+    count_launches(1);
+  }
+  unsigned long long h = 0;
+  CK(cudaMemcpyAsync(&h, out.p, sizeof(h), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  *value = (int64_t)h;
+  return HFP_OK;
+}
+
+HFP_API hfp_status hfp_refine_round(hfp_hgraph* hg, int32_t* part, int32_t k,
+                                    const hfp_refine_params* prm, const float* pair_scores,
+                                    float min_score, hfp_round_stats* stats,
+                                    hfp_pair_result* pairs, int32_t cap, int32_t* n_pairs) {
+  if (!hg || !part || !prm || !stats) return fail(HFP_ERR_INVALID, "NULL argument");
+  if (k < 2 || k > 64) return fail(HFP_ERR_INVALID, "k must be in [2, 64]");
+  hfp_status s = hg_set_device(hg);
+  if (s != HFP_OK) return s;
+  hfp_ctx* ctx = hg->ctx;
+  cudaStream_t st = ctx->stream;
+  const int n = hg->n, m = hg->m, sms = ctx->sms;
+  memset(stats, 0, sizeof(*stats));
+  // connectivity and quotient graph
+  DevBuf conn, qn, qw;
+  CK(conn.alloc(sizeof(unsigned long long), st));
+  CK(qn.alloc(sizeof(unsigned long long) * k * k, st));
+  CK(qw.alloc(sizeof(unsigned long long) * k * k, st));
+  CK(cudaMemsetAsync(conn.p, 0, sizeof(unsigned long long), st));
+  CK(cudaMemsetAsync(qn.p, 0, sizeof(unsigned long long) * k * k, st));
+  CK(cudaMemsetAsync(qw.p, 0, sizeof(unsigned long long) * k * k, st));
+  if (m) {
+    k_connectivity<<<nb((long long)m * 32, 256, sms * 16), 256, 0, st>>>(
+        m, hg->net_off, hg->pins, hg->net_w, part, conn.as<unsigned long long>(),
+        qn.as<unsigned long long>(), qw.as<unsigned long long>(), k);
+    count_launches(1);
+  }
+  std::vector<unsigned long long> hq((size_t)k * k);
+  unsigned long long c0 = 0;
+  CK(cudaMemcpyAsync(hq.data(), qn.p, sizeof(unsigned long long) * k * k, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&c0, conn.p, sizeof(c0), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  stats->connectivity_before = (int64_t)c0;
+  // refine every selected pair against the same partition
+  struct Item {
+    hfp_pair_result r;
+    DevBuf mv;
+  };
+  std::deque<Item> items;
+  for (int i = 0; i < k; i++)
+    for (int j = i + 1; j < k; j++) {
+      if (hq[(size_t)i * k + j] == 0) continue;
+      if (pair_scores && pair_scores[(size_t)i * k + j] < min_score) {
+        stats->pairs_skipped++;
+        continue;
+      }
+      items.emplace_back();
+      if ((s = refine_pair(hg, part, k, i, j, prm, items.back().mv, &items.back().r)) != HFP_OK)
+        return s;
+    }
+  stats->pairs = (int32_t)items.size();
+  // apply in descending Delta_exp, ties ascending (i, j)
+  std::vector<int> order;
+  for (int t = 0; t < (int)items.size(); t++) {
+    const hfp_pair_result& r = items[t].r;
+    if (r.status == HFP_OK && r.delta_exp >= 0 && r.n_moves > 0) order.push_back(t);
+    if (r.status == HFP_OK && r.delta_exp > 0) stats->pairs_improved++;
+  }
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    const hfp_pair_result &x = items[a].r, &y = items[b].r;
+    if (x.delta_exp != y.delta_exp) return x.delta_exp > y.delta_exp;
+    if (x.bi != y.bi) return x.bi < y.bi;
+    return x.bj < y.bj;
+  });
+  const long long L = ((100 + prm->eps_pct) * ((hg->total_w + k - 1) / k)) / 100;
+  DevBuf bw, dw, valid, nvalid, gain, moved_to, moved_stamp, net_stamp;
+  CK(bw.alloc(sizeof(unsigned long long) * k, st));
+  CK(dw.alloc(sizeof(long long) * k, st));
+  CK(nvalid.alloc(sizeof(unsigned), st));
+  CK(gain.alloc(sizeof(long long), st));
+  CK(moved_to.alloc(sizeof(int32_t) * (n > 0 ? n : 1), st));
+  CK(moved_stamp.alloc(sizeof(unsigned) * (n > 0 ? n : 1), st));
+  CK(net_stamp.alloc(sizeof(unsigned) * (m > 0 ? m : 1), st));
+  CK(cudaMemsetAsync(bw.p, 0, sizeof(unsigned long long) * k, st));
+  CK(cudaMemsetAsync(moved_stamp.p, 0, sizeof(unsigned) * (n > 0 ? n : 1), st));
+  CK(cudaMemsetAsync(net_stamp.p, 0, sizeof(unsigned) * (m > 0 ? m : 1), st));
+  if (n) {
+    k_block_weights<<<nb(n, 256, sms * 8), 256, 0, st>>>(n, part, hg->node_w,
+                                                         bw.as<unsigned long long>());
+    count_launches(1);
+  }
+  std::vector<long long> hbw(k), hdw(k);
+  CK(cudaMemcpyAsync(hbw.data(), bw.p, sizeof(long long) * k, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  unsigned epoch = 0;
+  for (int t : order) {
+    Item& it = items[t];
+    const unsigned cnt = (unsigned)it.r.n_moves;
+    epoch++;
+    CK(valid.alloc(cnt, st));
+    CK(cudaMemsetAsync(dw.p, 0, sizeof(long long) * k, st));
+    CK(cudaMemsetAsync(nvalid.p, 0, sizeof(unsigned), st));
+    CK(cudaMemsetAsync(gain.p, 0, sizeof(long long), st));
+    k_apply_check<<<nb(cnt, 256, sms * 8), 256, 0, st>>>(
+        cnt, it.mv.as<int32_t>(), part, hg->node_w, valid.as<uint8_t>(), dw.as<long long>(),
+        nvalid.as<unsigned>(), moved_to.as<int32_t>(), epoch, moved_stamp.as<unsigned>());
+    count_launches(1);
+    unsigned hv = 0;
+    CK(cudaMemcpyAsync(hdw.data(), dw.p, sizeof(long long) * k, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&hv, nvalid.p, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    bool ok = hv > 0;
+    for (int b = 0; b < k && ok; b++)
+      if (hdw[b] > 0 && hbw[b] + hdw[b] > L) ok = false;
+    long long g = 0;
+    if (ok) {
+      k_apply_gain<<<nb((long long)cnt * 32, 256, sms * 16), 256, 0, st>>>(
+          cnt, it.mv.as<int32_t>(), valid.as<uint8_t>(), hg->vnet_off, hg->vnet, hg->net_off,
+          hg->pins, hg->net_w, part, moved_to.as<int32_t>(), moved_stamp.as<unsigned>(),
+          net_stamp.as<unsigned>(), epoch, it.r.bi, it.r.bj, gain.as<long long>());
+      count_launches(1);
+      CK(cudaMemcpyAsync(&g, gain.p, sizeof(g), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      if (g >= 0) {
+        k_apply_commit<<<nb(cnt, 256, sms * 8), 256, 0, st>>>(cnt, it.mv.as<int32_t>(),
+                                                             valid.as<uint8_t>(), part);
+        count_launches(1);
+        for (int b = 0; b < k; b++) hbw[b] += hdw[b];
+        it.r.applied = 1;
+        it.r.gain = g;
+        stats->gain += g;
+        stats->pairs_applied++;
+        stats->moves_applied += hv;
+      }
+    }
+    it.r.valid_moves = (int32_t)hv;
+    if (valid.p) {
+      cudaFreeAsync(valid.p, st);
+      valid.p = nullptr;
+    }
+  }
+  CK(cudaStreamSynchronize(st));
+  stats->connectivity_after = stats->connectivity_before - stats->gain;
+  if (n_pairs) *n_pairs = (int32_t)items.size();
+  if (pairs)
+    for (int t = 0; t < (int)items.size() && t < cap; t++) pairs[t] = items[t].r;
+  return HFP_OK;
+}

@@ -52,6 +52,27 @@ class Tuning(ctypes.Structure):
                                                "tail_enter", "tail_exit", "max_rounds")]
 
 
+class RefineParams(ctypes.Structure):
+    _fields_ = [("eps_pct", ctypes.c_int32), ("alpha_eps_pct", ctypes.c_int32),
+                ("delta", ctypes.c_int32), ("seed", ctypes.c_uint32)]
+
+
+class PairResult(ctypes.Structure):
+    _fields_ = [("bi", ctypes.c_int32), ("bj", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("region_size", ctypes.c_int32), ("pins", ctypes.c_int64),
+                ("original_cut", ctypes.c_int64), ("flow", ctypes.c_int64),
+                ("delta_exp", ctypes.c_int64), ("n_moves", ctypes.c_int32),
+                ("iterations", ctypes.c_int32), ("applied", ctypes.c_int32),
+                ("valid_moves", ctypes.c_int32), ("gain", ctypes.c_int64)]
+
+
+class RoundStats(ctypes.Structure):
+    _fields_ = [("connectivity_before", ctypes.c_int64), ("connectivity_after", ctypes.c_int64),
+                ("gain", ctypes.c_int64), ("moves_applied", ctypes.c_int64),
+                ("pairs", ctypes.c_int32), ("pairs_improved", ctypes.c_int32),
+                ("pairs_applied", ctypes.c_int32), ("pairs_skipped", ctypes.c_int32)]
+
+
 class _NetworkView(ctypes.Structure):
     _fields_ = [("n_nodes", ctypes.c_int32), ("m_nets", ctypes.c_int32),
                 ("p_pins", ctypes.c_int64), ("net_off", ctypes.c_void_p),
@@ -104,6 +125,13 @@ def load():
                                  ctypes.POINTER(_FcResult)]),
         "hfp_max_flow_noalloc": (i32, [i32, P, ctypes.POINTER(_NetworkView), P, P, P]),
         "hfp_net_enable_trace": (i32, [P, i32]),
+        "hfp_hgraph_create": (i32, [P, ctypes.POINTER(_Hypergraph), i32, P]),
+        "hfp_hgraph_destroy": (None, [P]),
+        "hfp_connectivity": (i32, [P, P, i32, P]),
+        "hfp_refine_block_pair": (i32, [P, P, i32, i32, i32, ctypes.POINTER(RefineParams), P,
+                                        i32, ctypes.POINTER(PairResult)]),
+        "hfp_refine_round": (i32, [P, P, i32, ctypes.POINTER(RefineParams), P, ctypes.c_float,
+                                   ctypes.POINTER(RoundStats), P, i32, P]),
         "hfp_ctx_get_tuning": (i32, [P, ctypes.POINTER(Tuning)]),
         "hfp_ctx_set_tuning": (i32, [P, ctypes.POINTER(Tuning)]),
         "hfp_net_get_trace": (i32, [P, P, P, P, i32, P]),
@@ -301,6 +329,68 @@ def net_trace(net: Net, cap: int = 0) -> dict:
                 rounds=int(n.value), frontier=(tr[:, 0] >> np.uint64(32)).astype(np.int64),
                 next=(tr[:, 0] & np.uint64(0xFFFFFFFF)).astype(np.int64),
                 flow=tr[:, 1].astype(np.int64))
+
+
+class HGraph:
+    """hfp_hgraph: a hypergraph resident on the device for k-way refinement."""
+
+    def __init__(self, ctx: Context, net_off, pins, net_w, node_w, n: int):
+        arrs = dict(net_off=_host(net_off, np.uint32), pins=_host(pins, np.int32),
+                    net_w=_host(net_w, np.int32), node_w=_host(node_w, np.int32))
+        H = _Hypergraph(n, len(arrs["net_off"]) - 1, _ptr(arrs["net_off"]), _ptr(arrs["pins"]),
+                        _ptr(arrs["net_w"]), _ptr(arrs["node_w"]))
+        h = ctypes.c_void_p()
+        _check(load().hfp_hgraph_create(ctx.h, ctypes.byref(H), MEM_HOST, ctypes.byref(h)))
+        self.ctx, self.h, self.n = ctx, h, n
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().hfp_hgraph_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def refine_params(eps_pct=3, alpha_eps_pct=48, delta=2, seed=0) -> RefineParams:
+    return RefineParams(eps_pct, alpha_eps_pct, delta, seed & 0xFFFFFFFF)
+
+
+def connectivity(hg: HGraph, part_dev, k: int) -> int:
+    """hfp_connectivity (part: CUDA int32 tensor)."""
+    v = ctypes.c_int64()
+    _check(load().hfp_connectivity(hg.h, _ptr(part_dev), k, ctypes.byref(v)))
+    return int(v.value)
+
+
+def refine_block_pair(hg: HGraph, part_dev, k: int, bi: int, bj: int,
+                      params: RefineParams | None = None):
+    """hfp_refine_block_pair -> (PairResult, moves int32[n, 3])."""
+    params = params or refine_params()
+    res = PairResult()
+    cap = hg.n
+    moves = np.zeros(3 * max(cap, 1), np.int32)
+    _check(load().hfp_refine_block_pair(hg.h, _ptr(part_dev), k, bi, bj, ctypes.byref(params),
+                                        _ptr(moves), cap, ctypes.byref(res)))
+    return res, moves[: 3 * res.n_moves].reshape(-1, 3).copy()
+
+
+def refine_round(hg: HGraph, part_dev, k: int, params: RefineParams | None = None,
+                 pair_scores=None, min_score: float = 0.0):
+    """hfp_refine_round (part updated in place) -> (RoundStats, [PairResult])."""
+    params = params or refine_params()
+    stats = RoundStats()
+    cap = k * k
+    arr = (PairResult * cap)()
+    n = ctypes.c_int32()
+    sc = None if pair_scores is None else np.ascontiguousarray(pair_scores, np.float32)
+    _check(load().hfp_refine_round(hg.h, _ptr(part_dev), k, ctypes.byref(params), _ptr(sc),
+                                   ctypes.c_float(min_score), ctypes.byref(stats), arr, cap,
+                                   ctypes.byref(n)))
+    return stats, [arr[i] for i in range(n.value)]
 
 
 def net_stats(net: Net) -> dict:

@@ -1,0 +1,85 @@
+"""Parity of the CUDA k-way refinement with the oracle (bit-exact): block
+pair results (region size, cut, flow, Delta_exp, moves) and whole rounds
+(final partition, gain, applied move sets)."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2201_01556_gb300 import hfp
+    hfp.load()
+    ctx = hfp.ctx_create(0)
+    yield torch, hfp, ctx
+
+
+def _setup(env, seed, n, m, k=64):
+    torch, hfp, ctx = env
+    inst = synth.instance("ring_n8M_zipf_k64", seed, n=n, m=m)
+    H, part = inst["H"], inst["part"]
+    if k != 64:
+        part = synth.kway_partition(n, k, 50_000, seed)
+    hg = hfp.HGraph(ctx, H.net_off, H.pins, H.net_w, H.node_w, H.n)
+    pd = torch.from_numpy(part.copy()).cuda()
+    return H, part, hg, pd
+
+
+@pytest.mark.parametrize("seed,n,m", [(1, 16000, 24000), (2, 64000, 96000)])
+def test_pairs_match_oracle(env, seed, n, m):
+    torch, hfp, ctx = env
+    H, part, hg, pd = _setup(env, seed, n, m)
+    assert hfp.connectivity(hg, pd, 64) == oracle.connectivity(H, part, 64)
+    qn, _ = oracle.quotient(H, part, 64)
+    pairs = [(i, j) for i in range(64) for j in range(i + 1, 64) if qn[i, j] > 0]
+    rng = np.random.default_rng(seed)
+    pick = [pairs[t] for t in rng.choice(len(pairs), min(16, len(pairs)), replace=False)]
+    for i, j in pick:
+        o = oracle.refine_block_pair(H, part, 64, i, j, seed=7)
+        g, mv = hfp.refine_block_pair(hg, pd, 64, i, j, hfp.refine_params(seed=7))
+        assert (g.status, g.region_size, g.original_cut) == (o.status, o.region_size,
+                                                             o.original_cut), (i, j)
+        assert g.pins == o.pins
+        if o.status == oracle.OK:
+            assert g.flow == o.flow and g.delta_exp == o.delta_exp
+            assert np.array_equal(mv, o.moves)
+
+
+@pytest.mark.parametrize("seed,n,m,k", [(3, 16000, 24000, 64), (4, 40000, 60000, 16)])
+def test_round_matches_oracle(env, seed, n, m, k):
+    torch, hfp, ctx = env
+    H, part, hg, pd = _setup(env, seed, n, m, k)
+    newp, total, res, gains = oracle.refine_round(H, part, k, seed=5)
+    stats, pres = hfp.refine_round(hg, pd, k, hfp.refine_params(seed=5))
+    got = pd.cpu().numpy()
+    assert stats.gain == total
+    assert stats.connectivity_before == oracle.connectivity(H, part, k)
+    assert stats.connectivity_after == oracle.connectivity(H, newp, k)
+    assert np.array_equal(got, newp)
+    assert len(pres) == len(res)
+    for g, o in zip(pres, res):
+        assert (g.bi, g.bj, g.status, g.delta_exp, g.n_moves) == (o.bi, o.bj, o.status,
+                                                                  o.delta_exp, len(o.moves))
+        key = (o.bi, o.bj)
+        if key in gains:
+            assert (g.gain, g.applied, g.valid_moves) == gains[key]
+
+
+def test_round_skips_low_scores(env):
+    torch, hfp, ctx = env
+    H, part, hg, pd = _setup(env, 6, 16000, 24000)
+    scores = np.zeros((64, 64), np.float32)
+    scores[0, 1] = scores[1, 2] = 1.0
+    stats, pres = hfp.refine_round(hg, pd, 64, hfp.refine_params(), pair_scores=scores,
+                                   min_score=0.5)
+    assert {(p.bi, p.bj) for p in pres} <= {(0, 1), (1, 2)}
+    assert stats.pairs_skipped > 0
+    newp, total, _, _ = oracle.refine_round(H, part, 64, pairs=[(p.bi, p.bj) for p in pres])
+    assert np.array_equal(pd.cpu().numpy(), newp) and stats.gain == total

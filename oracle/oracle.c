@@ -773,3 +773,40 @@ int64_t or_apply_moves(int32_t n, int32_t m, const uint32_t *net_off, const int3
     free(valid); free(bw);
     return gain;
 }
+
+/* Per-pair statistics of the quotient graph (Section 5), the inputs of the
+ * learned pair scheduler (the paper has no such scheduler; the statistics
+ * are plain counts over the nets joining two blocks).  For every pair
+ * i < j and every net e whose blocks include i and j, row (i, j) of
+ * stats[k][k][8] accumulates:
+ *   0 number of nets, 1 their weight, 2 their pins, 3 the largest size,
+ *   4 nets whose blocks are exactly {i, j}, 5 their weight, 6 their pins,
+ *   7 unused (0). */
+void or_pair_stats(int32_t m, const uint32_t *net_off, const int32_t *pins, const int32_t *net_w,
+                   const int32_t *part, int32_t k, int64_t *stats) {
+    uint8_t *seen = (uint8_t *)calloc((size_t)k, 1);
+    int32_t *blocks = (int32_t *)malloc(sizeof(int32_t) * (size_t)k);
+    memset(stats, 0, sizeof(int64_t) * (size_t)k * k * 8);
+    for (int32_t e = 0; e < m; e++) {
+        int32_t nb = 0;
+        int64_t size = (int64_t)(net_off[e + 1] - net_off[e]);
+        for (uint32_t j = net_off[e]; j < net_off[e + 1]; j++) {
+            int32_t b = part[pins[j]];
+            if (!seen[b]) { seen[b] = 1; blocks[nb++] = b; }
+        }
+        for (int32_t a = 0; a < nb; a++) seen[blocks[a]] = 0;
+        for (int32_t a = 0; a < nb; a++)
+            for (int32_t c = 0; c < nb; c++) {
+                int32_t i = blocks[a], jj = blocks[c];
+                if (i >= jj) continue;
+                int64_t *s = stats + ((size_t)i * k + jj) * 8;
+                s[0] += 1;
+                s[1] += net_w[e];
+                s[2] += size;
+                if (size > s[3]) s[3] = size;
+                if (nb == 2) { s[4] += 1; s[5] += net_w[e]; s[6] += size; }
+            }
+    }
+    free(seen);
+    free(blocks);
+}

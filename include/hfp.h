@@ -250,6 +250,35 @@ hfp_status hfp_flowcutter(hfp_net* net, const hfp_fc_params* params, uint8_t* fi
                           int32_t* pierce_side, int32_t* pierce_node, int32_t pierce_cap,
                           hfp_fc_result* result);
 
+/* --- batched FlowCutter ---------------------------------------------------
+ * hfp_flowcutter on n networks in ONE cooperative kernel launch.  The grid
+ * is cut into groups of group_ctas CTAs (<= 0: as many CTAs per group as the
+ * grid allows with one group per network); each group takes the next network
+ * from a device work queue (largest first) and runs all of Algorithm 2 on it
+ * without returning to the host: the first maximum flow, S_r / T_r, the
+ * balance test, piercing and the incremental augmentation (Section 7; the
+ * paper runs the FlowCutter problems of a round concurrently, Section 5,
+ * "Parallel Scheduling").  Every decision is the one hfp_flowcutter takes, so
+ * each task's outcome equals a hfp_flowcutter call on that network.
+ * Networks must come fresh from hfp_build_flow_network (no flow computed),
+ * belong to ctx and be distinct.  Per task: status receives HFP_OK,
+ * HFP_NO_BALANCED_CUT, HFP_ABORTED_WORSE or an error code; final_side /
+ * pierce_side / pierce_node (host, may be NULL) as in hfp_flowcutter.  The
+ * call returns the first task error other than those two outcomes, or
+ * HFP_ERR_BUFFER_TOO_SMALL when a piercing record did not fit. */
+typedef struct {
+  hfp_net* net;
+  hfp_fc_params params;
+  uint8_t* final_side;     /* n_region */
+  int32_t* pierce_side;    /* pierce_cap */
+  int32_t* pierce_node;    /* pierce_cap */
+  int32_t pierce_cap;
+  hfp_status status;       /* out */
+  hfp_fc_result result;    /* out */
+} hfp_fc_task;
+
+hfp_status hfp_flowcutter_batch(hfp_ctx* ctx, hfp_fc_task* tasks, int32_t n, int32_t group_ctas);
+
 /* --- k-way refinement (Section 4, Algorithm 1; Sections 5 and 6) ---------
  * A device-resident hypergraph (with its vertex -> nets incidence) for
  * refining k-way partitions block pair by block pair.  Partitions are int32
@@ -323,6 +352,95 @@ hfp_status hfp_refine_round(hfp_hgraph* hg, int32_t* part, int32_t k,
                             const hfp_refine_params* params, const float* pair_scores,
                             float min_score, hfp_round_stats* stats, hfp_pair_result* pairs,
                             int32_t cap, int32_t* n_pairs);
+
+/* hfp_refine_round with all FlowCutter problems of the round in ONE batched
+ * launch (hfp_flowcutter_batch): regions and networks are built first, the
+ * batch runs, then moves are extracted and applied exactly as in
+ * hfp_refine_round, so the outcome is identical.  group_ctas: CTAs per
+ * problem (<= 0: the value picked by hfp_autotune_round, else one group per
+ * problem as far as the grid allows).  flowcutter_ms (host, may be NULL):
+ * device time of the batched launch. */
+hfp_status hfp_refine_round_batched(hfp_hgraph* hg, int32_t* part, int32_t k,
+                                    const hfp_refine_params* params, const float* pair_scores,
+                                    float min_score, int32_t group_ctas, hfp_round_stats* stats,
+                                    hfp_pair_result* pairs, int32_t cap, int32_t* n_pairs,
+                                    float* flowcutter_ms);
+
+/* Autotuner of the batched round's tiling: builds the round's networks for
+ * `part` (unchanged) once per candidate group size (CTAs per problem),
+ * times the batched FlowCutter launch for each (ms[c], host, may be NULL),
+ * and keeps the fastest in hg for hfp_refine_round_batched (*best). */
+hfp_status hfp_autotune_round(hfp_hgraph* hg, const int32_t* part, int32_t k,
+                              const hfp_refine_params* params, const int32_t* candidates,
+                              int32_t n_candidates, float* ms, int32_t* best);
+
+/* --- learned block-pair scheduler ----------------------------------------
+ * The paper has no learned component: its rounds refine every edge of the
+ * quotient graph (Section 5, "Quotient Graph Construction" and "Parallel
+ * Scheduling").  These calls score the edges with a multilayer perceptron
+ * 16 -> 64 -> 64 -> 1 (ReLU, sigmoid output) so that hfp_refine_round can
+ * skip pairs whose score is below a threshold (its pair_scores argument).
+ * Weights and the inputs of the two matrix products are rounded to bfloat16
+ * (nearest even); products accumulate in fp32; the last layer is an fp32 dot
+ * product with bf16 weights.  Parameters are one fp32 array of
+ * HFP_MLP_PARAMS values: W1[64][16], b1[64], W2[64][64], b2[64], w3[64],
+ * b3 (row-major, W[out][in]).  All pointers except the noted host ones are
+ * device pointers. */
+#define HFP_MLP_FEATURES 16
+#define HFP_MLP_HIDDEN 64
+#define HFP_MLP_PARAMS 5313
+
+/* Features of every block pair i < j joined by a net (row-major pair
+ * order), from counts over those nets: with "nets2" the joining nets whose
+ * blocks are exactly {i, j}, L = floor((100 + eps_pct) * ceil(c(V) / k) / 100):
+ *   0 log1p(nets)  1 log1p(weight)  2 log1p(pins)  3 log1p(largest net)
+ *   4 log1p(nets2) 5 log1p(weight2) 6 weight2 / weight  7 log1p(pins2)
+ *   8 c(Vi) / L    9 c(Vj) / L      10 (c(Vi) + c(Vj)) / (2 L)
+ *   11 log1p(pins / nets)  12 log1p(max(prev, 0))  13 prev >= 0 ? 1 : 0
+ *   14 log2(k) / 6  15 weight * P / (total weight of the P pairs)
+ * prev_gain: host int64 k * k, gain of pair (i, j) in the previous round and
+ * -1 where it was not refined, or NULL.  features: cap x 16 floats; pairs:
+ * cap x 2 int32 (i, j); *n_pairs (host) = P; HFP_ERR_BUFFER_TOO_SMALL if
+ * P > cap.  k in [2, 64].  Synchronises the context stream. */
+hfp_status hfp_pair_features(hfp_hgraph* hg, const int32_t* part, int32_t k, int32_t eps_pct,
+                             const int64_t* prev_gain, float* features, int32_t* pairs,
+                             int32_t cap, int32_t* n_pairs);
+
+/* scores[r] = sigmoid(MLP(x[r])) for rows x[rows][16]. */
+hfp_status hfp_mlp_forward(hfp_ctx* ctx, const float* params, const float* x, int32_t rows,
+                           float* scores);
+
+/* Gradient (device, HFP_MLP_PARAMS floats) of the mean binary cross-entropy
+ * of the logits against labels y[rows] (0 or 1); rounding to bf16 passes
+ * the gradient straight through.  *loss (host, may be NULL) = the mean loss. */
+hfp_status hfp_mlp_grad(hfp_ctx* ctx, const float* params, const float* x, const float* y,
+                        int32_t rows, float* grad, float* loss);
+
+typedef struct {
+  float lr;
+  float eps;
+  double beta1;
+  double beta2;
+} hfp_adam_params;
+
+/* `steps` full-batch Adam steps (Kingma and Ba, 2015) on params with moment
+ * arrays adam_m, adam_v (HFP_MLP_PARAMS floats each, zero before the first
+ * step) and the device step counter *step (0 before the first step;
+ * incremented per step).  One step is a forward/backward launch and a
+ * reduce/update launch, captured once as a CUDA graph and replayed.
+ * losses (device, loss_cap floats, may be NULL) receives the mean loss of
+ * the i-th step of this call at index i - 1 while i <= loss_cap.  Synchronises the context
+ * stream. */
+hfp_status hfp_mlp_train(hfp_ctx* ctx, float* params, float* adam_m, float* adam_v,
+                         int32_t* step, const float* x, const float* y, int32_t rows,
+                         int32_t steps, const hfp_adam_params* opt, float* losses,
+                         int32_t loss_cap);
+
+/* hfp_pair_features + hfp_mlp_forward, scattered into a host k * k table
+ * (scores[i * k + j] for i < j joined by a net, -1 elsewhere) in the form
+ * hfp_refine_round takes. */
+hfp_status hfp_pair_scores(hfp_hgraph* hg, const int32_t* part, int32_t k, int32_t eps_pct,
+                           const int64_t* prev_gain, const float* params, float* scores);
 
 /* --- allocation-free max flow ---------------------------------------------
  * The paper has no counterpart to this entry point; it exists for callers

@@ -15,6 +15,8 @@ __device__ void zero_phase_counters(EngineCtl& X) {
   for (int k = 0; k < 3; k++) {
     X.flow3[k] = 0;
     X.w3[k] = 0;
+    X.key3[k] = 0;
+    X.node3[k] = -1;
   }
   X.gr_act[0] = 0;
   X.gr_act[1] = 0;
@@ -62,6 +64,9 @@ __global__ void k_engine_setup(EngineCtl* E, int mode) {
     case SETUP_DIST:
       zero_phase_counters(X);
       X.s.state = ST_DIST_INIT;
+      break;
+    case SETUP_BATCH:
+      zero_phase_counters(X);
       break;
   }
 }

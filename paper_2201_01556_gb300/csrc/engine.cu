@@ -146,6 +146,8 @@ struct Snap {
   unsigned act, acth;
   unsigned long long flow;
   long long w;
+  unsigned long long key;
+  int node;
 };
 
 __device__ void begin_gr(Sched& L) {
@@ -263,6 +265,8 @@ __device__ Snap take_snap(EngineCtl* E, unsigned k) {
   q.acth = ld_cg(&E->gr_act[1]);
   q.flow = *(const volatile unsigned long long*)&E->flow3[sl];
   q.w = *(const volatile long long*)&E->w3[sl];
+  q.key = *(const volatile unsigned long long*)&E->key3[sl];
+  q.node = *(const volatile int*)&E->node3[sl];
   return q;
 }
 
@@ -274,6 +278,8 @@ __device__ __forceinline__ void clear_slot(EngineCtl* E, unsigned sl, bool gr_in
   for (int l = 0; l < C_COUNT; l++) E->cnt3[l][sl] = 0;
   E->flow3[sl] = 0;
   E->w3[sl] = 0;
+  E->key3[sl] = 0;
+  E->node3[sl] = -1;
   if (gr_init) {
     E->gr_act[0] = 0;
     E->gr_act[1] = 0;
@@ -360,7 +366,7 @@ __device__ void discharge_team(const NetDev& N, int x, const int32_t* Lr, unsign
   long long rem = 0;
   int dx = NL;
   if (x >= 0) {
-    rem = N.excess[x];
+    rem = __ldcg(&N.excess[x]);   // may come from atomics (saturation)
     dx = Lr[x];
   }
   const bool act = x >= 0 && rem > 0 && dx < NL;
@@ -546,7 +552,7 @@ __device__ __forceinline__ int block_min(int v) {
 __device__ void discharge_block(const NetDev& N, int x, const int32_t* Lr, unsigned epoch,
                                 long long& sink_acc, Acc& a, const Slot& S) {
   const int NL = N.NL, nh = N.n_nodes, m = N.m_nets;
-  const long long ex = N.excess[x];
+  const long long ex = __ldcg(&N.excess[x]);   // may come from atomics (saturation)
   const int dx = Lr[x];
   if (ex <= 0 || dx >= NL) return;    // uniform over the CTA
   const int dt = dx - 1;
@@ -660,8 +666,12 @@ __device__ int relabel_block(const NetDev& N, const int32_t* Lr, int x, Acc& a) 
   return min(block_min(best), NL);
 }
 
+// delta[] only grows by atomics, which update L2, not the L1 copy a previous
+// round's load of the same line may have left on this SM; between the phases
+// of a CTA-alone round (block barriers, no GPU-scope fence) a cached load
+// could return the old value and drop pushed excess.  Hence the L2 load.
 __device__ __forceinline__ long long apply_delta(const NetDev& N, int y) {
-  const long long d = N.delta[y];
+  const long long d = __ldcg(&N.delta[y]);
   const long long ex = N.excess[y] + d;
   if (d) N.delta[y] = 0;
   N.excess[y] = ex;
@@ -1080,6 +1090,7 @@ __device__ __forceinline__ void tick(Clock& ck, int st) {
 __device__ void tail_rounds(const NetDev& N, EngineCtl* E, const Params& P, Sched& L,
                             unsigned lane, Acc& a, long long* w_sh, Clock& ck) {
   const Team T{threadIdx.x >> 5, blockDim.x >> 5, threadIdx.x, blockDim.x, 0, 1};
+  __syncthreads();   // every thread has read the caller's state before it is rewritten
   if (threadIdx.x == 0) L.state = ST_ROUND_A;
   __syncthreads();
   for (;;) {
@@ -1101,6 +1112,7 @@ __device__ void tail_rounds(const NetDev& N, EngineCtl* E, const Params& P, Sche
     const int st = L.state;
     if (st != ST_ROUND_A && st != ST_ROUND_B) break;
   }
+  __syncthreads();   // every thread has left the loop before the state is rewritten
   if (threadIdx.x == 0 && L.state == ST_ROUND_A + 100) L.state = ST_ROUND_A;
   __syncthreads();
 }
@@ -1245,5 +1257,7 @@ __global__ void __launch_bounds__(kEngineThreads) engine_kernel(NetDev N, Engine
     }
   }
 }
+
+#include "engine_batch.cuh"
 
 }  // namespace hfp

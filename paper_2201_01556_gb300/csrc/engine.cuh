@@ -18,6 +18,12 @@ enum EngineState : int {
   ST_DIST_INIT = 7, // distance from the cut: seed the distance-1 vertices
   ST_DIST_LEVEL = 8,  // distance from the cut: one BFS level inside the region
   ST_TAIL = 9,      // rounds run by CTA 0 alone while the frontier is small
+  // batched FlowCutter (fc_batch_kernel): the steps of Algorithm 2 around the flow
+  ST_FC_SAT = 10,     // saturate the arcs out of a new source hypernode
+  ST_FC_SEL = 11,     // largest piercing key over the candidates
+  ST_FC_FIND = 12,    // the candidate holding that key
+  ST_FC_MARK_S = 13,  // S <- S_r + pierced node
+  ST_FC_MARK_T = 14,  // T <- T_r + pierced node, their excess joins the flow
 };
 
 // list ids in NetDev::list.  Each list array holds light nodes from the front
@@ -67,6 +73,43 @@ struct EngineCtl {
   unsigned int bar_count;            // count-up grid barrier (reset per launch)
   unsigned long long flow3[3];       // flow into sinks per phase slot
   long long w3[3];                   // hypernode weight reached per phase slot
+  unsigned long long key3[3];        // batched FlowCutter: best piercing key per slot
+  int node3[3];                      // batched FlowCutter: node holding it per slot
+  int pad3;
+};
+
+// One flow problem of a batched FlowCutter launch (Section 7, Algorithm 2):
+// the network, its control block, the FlowCutter parameters and, written by
+// the kernel, the outcome.
+struct FcJob {
+  NetDev N;
+  EngineCtl* E;
+  long long total_w;          // c(V) of the network, terminals included
+  long long max_w;            // balance bound L
+  long long flow_bound;       // abort above this flow (-1: none)
+  unsigned long long gr_work; // global-relabel work threshold of this network
+  int32_t* pierce_node;       // piercing record (pierce_cap entries, may be null)
+  int8_t* pierce_side;
+  uint32_t seed;
+  int32_t max_it;
+  int32_t dist_ready;         // distances given at construction
+  int32_t pierce_cap;
+  // outcome
+  int32_t status;             // 0, or an hfp_status (<0), or 100 + device error code
+  int32_t iterations;
+  int32_t n_pierced;
+  int32_t result_side;        // 0: S_r side, 1: T_r side
+  long long flow;
+  long long source_weight;
+};
+
+// Work queue and per-group barriers of a batched launch.
+constexpr int kMaxGroups = 1024;
+struct BatchCtl {
+  unsigned next;              // next job to hand out
+  int err;                    // a group barrier timed out
+  unsigned gbar[kMaxGroups];  // count-up barrier per group
+  unsigned gjob[kMaxGroups];  // job handed to each group
 };
 
 }  // namespace hfp

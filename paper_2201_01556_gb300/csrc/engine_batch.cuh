@@ -1,0 +1,455 @@
+// Batched FlowCutter (included by engine.cu, inside namespace hfp).
+//
+// One cooperative launch solves many flow problems, e.g. all block pairs of
+// a k-way refinement round (Section 5, "Parallel Scheduling").  The grid is
+// cut into groups of G consecutive CTAs.  A group takes the next job from a
+// device work queue and runs the whole of Algorithm 2 (Section 7) on it: the
+// initial maximum flow, then, until the cut is balanced, the source-side cut
+// S_r, the balance test, the piercing-node selection and the incremental
+// augmentation after piercing.  The flow phases are the engine's own (the
+// same push-relabel rounds, global relabels and breadth-first searches, with
+// "grid" read as "group"); the FlowCutter steps are extra engine states.
+// Every CTA of the group derives the next state itself after each group
+// barrier, exactly as in engine_kernel, so no host round trip is left.
+//
+// The decisions are the ones of hfp_flowcutter: balanced iff both sides are
+// within L, the better of two balanced sides is the one with the smaller
+// heavier side (ties: the source side), S grows iff c(S_r) <= c(T_r), and the
+// piercing key is pierce_key below.  Results are therefore identical to the
+// one-problem-per-launch path.
+
+// Piercing candidates (Section 7, "Piercing"): pins of nets whose in-node
+// (growing S) or out-node (growing T) is reachable from the growing side,
+// not reachable themselves, not terminals of the other side, and light
+// enough to keep the growing side within L.  Key, larger wins:
+//   bit 54 valid, bit 53 no augmenting path, bits 32..52 signed distance
+//   + 2^20, bits 0..31 ~fmix32(gid ^ seed) (smaller hash wins).
+__device__ __forceinline__ unsigned long long batch_pierce_key(const NetDev& N, int h,
+                                                               int grow_s, long long max_w,
+                                                               long long w_reach,
+                                                               uint32_t seed) {
+  const int NL = N.NL;
+  const bool in_r = grow_s ? N.insr[h] != 0 : N.lab0[h] < NL;
+  if (in_r) return 0;
+  const uint8_t f = N.flags[h];
+  if (f & (grow_s ? kSink : kSource)) return 0;
+  if (w_reach + N.node_w[h] > max_w) return 0;
+  const bool no_path = grow_s ? N.lab0[h] >= NL : N.insr[h] == 0;
+  const int d = N.node_dist[h] < 0 ? kDistFar : N.node_dist[h];
+  const int sd = (N.node_orig[h] == (grow_s ? 0 : 1)) ? d : -d;
+  const uint32_t hh = fmix32((uint32_t)N.node_gid[h] ^ seed);
+  return (1ull << 54) | ((unsigned long long)no_path << 53) |
+         ((unsigned long long)(sd + (1 << 20)) << 32) | (unsigned long long)(0xffffffffu - hh);
+}
+
+// FlowCutter control of one job, replicated in every CTA of the group.
+enum FcStage : int { FC_FLOW = 0, FC_SR = 1, FC_DIST = 2 };
+struct FcState {
+  int stage;          // what the engine is computing when it reaches ST_DONE
+  int grow_s;
+  int it;             // flows computed so far (the first one included)
+  int np;             // nodes pierced
+  int node;           // node being pierced (source hypernode 0 at the start)
+  int initial;        // the saturation of s that opens the first flow
+  int dist_ready;
+  int status;         // outcome once the job is finished
+  int result_side;
+  int finished;
+  unsigned long long best;
+  long long source_weight;
+};
+
+// ---------------------------------------------------------------------------
+// phases of the FlowCutter states (group-wide)
+
+// Saturate every residual arc out of the new source u (Algorithm 2 line 8
+// after the piercing; Section 2 "Push-Relabel" for s): (u, e_in) up to w(e),
+// (u, e_out) down to zero flow.  Non-sink targets get the excess and join the
+// frontier (stamped with the current epoch); sink targets add to the flow.
+__device__ void fc_saturate(const NetDev& N, const Sched& L, const Team& T, const Slot& S, int u,
+                            unsigned lane) {
+  const int nh = N.n_nodes, m = N.m_nets;
+  const unsigned beg = N.node_off[u], end = N.node_off[u + 1];
+  unsigned long long sink_acc = 0;
+  for (unsigned j0 = beg + T.gwarp * 32; j0 < end; j0 += T.nwarps * 32) {
+    const unsigned j = j0 + lane;
+    bool a1 = false, a2 = false, h1 = false, h2 = false;
+    int y1 = -1, y2 = -1;
+    if (j < end) {
+      const int2 it = N.inc[j];
+      const int e = it.x, p = it.y;
+      y1 = nh + e;
+      y2 = nh + m + e;
+      const int w = N.net_w[e];
+      const int d1 = w - N.f_in[p];
+      const int d2 = N.f_out[p];
+      const uint8_t f1 = N.flags[y1], f2 = N.flags[y2];
+      h1 = (f1 & kHeavy) != 0;
+      h2 = (f2 & kHeavy) != 0;
+      if (d1 > 0 && !(f1 & kSource)) {
+        N.f_in[p] = w;
+        if (f1 & kSink) {
+          sink_acc += d1;
+        } else {
+          atomicAdd((unsigned long long*)&N.excess[y1], (unsigned long long)d1);
+          a1 = atomicExch(&N.stamp[y1], L.epoch) != L.epoch;
+        }
+      }
+      if (d2 > 0 && !(f2 & kSource)) {
+        N.f_out[p] = 0;
+        if (f2 & kSink) {
+          sink_acc += d2;
+        } else {
+          atomicAdd((unsigned long long*)&N.excess[y2], (unsigned long long)d2);
+          a2 = atomicExch(&N.stamp[y2], L.epoch) != L.epoch;
+        }
+      }
+    }
+    append_split(a1, y1, h1, N.list[L_FRONT], S.c[C_FRONT], S.c[C_FRONTH], 0, 0, N.NL);
+    append_split(a2, y2, h2, N.list[L_FRONT], S.c[C_FRONT], S.c[C_FRONTH], 0, 0, N.NL);
+  }
+  if (sink_acc) atomicAdd(S.flow, sink_acc);
+}
+
+// S <- S_r + {u}: sources get label NL and lose their excess.
+__device__ void fc_mark_sources(const NetDev& N, const Team& T, int u) {
+  const int NL = N.NL;
+  for (int x = T.tid; x <= NL; x += T.nth) {
+    const int y = x < NL ? x : u;
+    if (x < NL && !N.insr[x]) continue;
+    N.flags[y] = (N.flags[y] & kHeavy) | kSource;
+    N.lab0[y] = NL;
+    N.lab1[y] = NL;
+    N.excess[y] = 0;
+  }
+}
+
+// T <- T_r + {u} (T_r = {label < NL} after the final global relabel); the
+// excess of a node that becomes a sink joins the flow (Section 8.4,
+// "Sink-Side Piercing").
+__device__ void fc_mark_sinks(const NetDev& N, const Team& T, const Slot& S, int u) {
+  const int NL = N.NL;
+  unsigned long long acc = 0;
+  for (int x = T.tid; x <= NL; x += T.nth) {
+    const int y = x < NL ? x : u;
+    if (x < NL && N.lab0[x] >= NL) continue;
+    if (N.flags[y] & kSink) continue;
+    const long long ex = N.excess[y];
+    if (ex > 0) acc += (unsigned long long)ex;
+    N.excess[y] = 0;
+    N.flags[y] = (N.flags[y] & kHeavy) | kSink;
+  }
+  if (acc) atomicAdd(S.flow, acc);
+}
+
+// Largest piercing key (find = false) or the node holding key `best`.
+__device__ void fc_pierce_scan(const NetDev& N, const Team& T, EngineCtl* E, unsigned sl,
+                               const FcJob& J, const FcState& F, long long w_reach, bool find,
+                               unsigned lane) {
+  const int nh = N.n_nodes, m = N.m_nets, NL = N.NL;
+  unsigned long long mx = 0;
+  for (unsigned e = T.gwarp; e < (unsigned)m; e += T.nwarps) {
+    const int node = F.grow_s ? nh + e : nh + m + e;
+    const bool reach = F.grow_s ? N.insr[node] != 0 : N.lab0[node] < NL;
+    if (!reach) continue;
+    for (unsigned p = N.net_off[e] + lane; p < N.net_off[e + 1]; p += 32) {
+      const int h = N.pin[p];
+      const unsigned long long k = batch_pierce_key(N, h, F.grow_s, J.max_w, w_reach, J.seed);
+      if (find) {
+        if (k != 0 && k == F.best) E->node3[sl] = h;
+      } else if (k > mx) {
+        mx = k;
+      }
+    }
+  }
+  if (!find) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long t = __shfl_xor_sync(FULL, mx, o);
+      mx = t > mx ? t : mx;
+    }
+    if (lane == 0 && mx) atomicMax(&E->key3[sl], mx);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// control (thread 0 of every CTA of the group, on identical inputs)
+
+__device__ void fc_finish(Sched& L, FcState& F, int status) {
+  F.status = status;
+  F.finished = 1;
+  L.state = ST_DONE;
+}
+
+// The engine reached ST_DONE: continue Algorithm 2.
+__device__ void fc_on_done(Sched& L, FcState& F, const FcJob& J, const Ctl* c) {
+  const int err = ld_volatile_int(&c->err);
+  if (err != kDevOk) {
+    fc_finish(L, F, 100 + err);
+    return;
+  }
+  switch (F.stage) {
+    case FC_FLOW:
+      // source-side cut of the new flow (SETUP_SR)
+      F.stage = FC_SR;
+      L.state = ST_SR_INIT;
+      L.epoch++;
+      L.wS = 0;
+      L.wS_set = 1;
+      return;
+    case FC_DIST:
+      F.dist_ready = 1;
+      L.state = ST_FC_SEL;
+      return;
+    default:
+      break;
+  }
+  // FC_SR: S_r and T_r of the current flow are known (Algorithm 2, lines 3-6)
+  const long long W = J.total_w, Lm = J.max_w;
+  const long long wS = L.wS, wT = L.wT;
+  if (J.flow_bound >= 0 && (long long)L.flow > J.flow_bound) {
+    fc_finish(L, F, -6 /* HFP_ABORTED_WORSE */);
+    return;
+  }
+  const bool balS = wS <= Lm && W - wS <= Lm;
+  const bool balT = wT <= Lm && W - wT <= Lm;
+  if (balS || balT) {
+    bool use_t;
+    if (balS && balT) {
+      const long long mS = wS > W - wS ? wS : W - wS;
+      const long long mT = wT > W - wT ? wT : W - wT;
+      use_t = mT < mS;
+    } else {
+      use_t = !balS;
+    }
+    F.result_side = use_t ? 1 : 0;
+    F.source_weight = use_t ? W - wT : wS;
+    fc_finish(L, F, 0);
+    return;
+  }
+  if (F.it >= J.max_it) {
+    fc_finish(L, F, -4 /* HFP_ERR_ITER_LIMIT */);
+    return;
+  }
+  F.grow_s = wS <= wT ? 1 : 0;
+  if (!F.dist_ready) {
+    F.stage = FC_DIST;     // SETUP_DIST
+    L.state = ST_DIST_INIT;
+  } else {
+    L.state = ST_FC_SEL;
+  }
+}
+
+// After a FlowCutter phase and its barrier.
+__device__ void fc_advance(Sched& L, FcState& F, const Snap& q, const FcJob& J, bool recorder) {
+  switch (L.state) {
+    case ST_FC_SAT:
+      L.flow += q.flow;
+      F.stage = FC_FLOW;
+      if (F.initial) {
+        // first flow: the labels are built by a global relabel (SETUP_GR)
+        F.initial = 0;
+        begin_gr(L);
+        L.after_gr_exit = 0;
+      } else {
+        // the new excess is the frontier; labels stay valid (SETUP_ROUND)
+        L.epoch++;
+        L.state = ST_ROUND_A;
+        L.fcnt = q.c[C_FRONT];
+        L.fcnth = q.c[C_FRONTH];
+        L.rcnt = 0;
+        L.flow_ref = L.flow;
+        L.stall = 0;
+        F.it++;
+      }
+      break;
+    case ST_FC_SEL:
+      if (q.key == 0) {
+        fc_finish(L, F, -5 /* HFP_NO_BALANCED_CUT */);
+      } else {
+        F.best = q.key;
+        L.state = ST_FC_FIND;
+      }
+      break;
+    case ST_FC_FIND:
+      F.node = q.node;
+      if (recorder && F.np < J.pierce_cap) {
+        if (J.pierce_node) J.pierce_node[F.np] = q.node;
+        if (J.pierce_side) J.pierce_side[F.np] = (int8_t)(F.grow_s ? 0 : 1);
+      }
+      F.np++;
+      L.state = F.grow_s ? ST_FC_MARK_S : ST_FC_MARK_T;
+      break;
+    case ST_FC_MARK_S:
+      L.epoch++;           // SETUP_PREP: fresh stamps for the saturation's frontier
+      L.state = ST_FC_SAT;
+      break;
+    case ST_FC_MARK_T:
+      L.flow += q.flow;    // excess absorbed by the new sinks
+      F.stage = FC_FLOW;
+      begin_gr(L);         // SETUP_GR: labels are no longer lower bounds
+      L.after_gr_exit = 0;
+      F.it++;
+      break;
+    default:
+      L.state = ST_DONE;
+  }
+}
+
+// Count-up barrier of a group on BatchCtl (job hand-out), bounded like
+// grid_barrier; false on expiry (B->err set).
+__device__ bool group_sync(BatchCtl* B, int gid, unsigned target,
+                           unsigned long long timeout_ns) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    __threadfence();
+    atomicAdd(&B->gbar[gid], 1u);
+    unsigned spins = 0;
+    unsigned long long t0 = 0;
+    while (ld_acquire(&B->gbar[gid]) < target) {
+      if (ld_volatile_int(&B->err) != 0) { ok = 0; break; }
+      if ((++spins & 255u) == 0) {
+        const unsigned long long t = globaltimer();
+        if (t0 == 0) t0 = t;
+        else if (t - t0 > timeout_ns) {
+          atomicCAS(&B->err, 0, 1);
+          ok = 0;
+          break;
+        }
+      }
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+__device__ void run_phase_batch(const NetDev& N, EngineCtl* E, const Sched& L, const FcState& F,
+                                const FcJob& J, const Team& T, unsigned lane, Acc& a,
+                                long long* w_sh) {
+  const Slot S = slot_of(E, L.phase);
+  switch (L.state) {
+    case ST_FC_SAT: fc_saturate(N, L, T, S, F.node, lane); break;
+    case ST_FC_SEL:
+      fc_pierce_scan(N, T, E, L.phase % 3, J, F, F.grow_s ? L.wS : L.wT, false, lane);
+      break;
+    case ST_FC_FIND:
+      fc_pierce_scan(N, T, E, L.phase % 3, J, F, F.grow_s ? L.wS : L.wT, true, lane);
+      break;
+    case ST_FC_MARK_S: fc_mark_sources(N, T, F.node); break;
+    case ST_FC_MARK_T: fc_mark_sinks(N, T, S, F.node); break;
+    default: run_phase(N, E, L, T, lane, a, w_sh); break;
+  }
+}
+
+// One job by one group of G CTAs (rank = position in the group).
+__device__ void fc_run_job(FcJob* job, const Params& P0, int rank, int G, unsigned lane,
+                           Sched& L, FcState& F, NetDev& N, Params& P, long long* w_sh,
+                           Clock& ck) {
+  const unsigned wib = threadIdx.x >> 5, nwb = blockDim.x >> 5;
+  const Team T{rank * nwb + wib, G * nwb, rank * blockDim.x + threadIdx.x, G * blockDim.x,
+               (unsigned)rank, (unsigned)G};
+  EngineCtl* E = job->E;
+  if (threadIdx.x == 0) {
+    N = job->N;
+    P = P0;
+    P.gr_work = job->gr_work;
+    load_sched(L, E);
+    L.flow = *(const volatile unsigned long long*)&E->c.flow;
+    F = FcState{FC_FLOW, 0, 1, 0, 0, 1, job->dist_ready, 0, 0, 0, 0ull, 0ll};
+    // SETUP_PREP, then the saturation of s opens the first flow
+    L.epoch++;
+    L.state = ST_FC_SAT;
+    *w_sh = 0;
+  }
+  __syncthreads();
+  Acc a{0, 0, 0, 0, 0};
+  unsigned bar_seq = 0;
+  const bool lead = rank == 0;
+  for (;;) {
+    const int st = L.state;
+    if (st == ST_DONE) break;
+    if (st == ST_TAIL) {
+      if (lead) {
+        tail_rounds(N, E, P, L, lane, a, w_sh, ck);
+        if (threadIdx.x == 0) store_sched(E, L);
+      }
+      const bool ok = grid_barrier(E, G * ++bar_seq, P.timeout_ns);
+      if (threadIdx.x == 0) {
+        if (!lead) load_sched(L, E);
+        if (!ok) L.state = ST_DONE;
+        if (L.state == ST_DONE && !F.finished) fc_on_done(L, F, *job, &E->c);
+      }
+      __syncthreads();
+      continue;
+    }
+    if (lead && threadIdx.x == 0) clear_slot(E, (L.phase + 1) % 3, st == ST_GR_INIT);
+    run_phase_batch(N, E, L, F, *job, T, lane, a, w_sh);
+    __syncthreads();
+    if (threadIdx.x == 0) flush_weight(E, L.phase, w_sh);
+    const bool ok = grid_barrier(E, G * ++bar_seq, P.timeout_ns);
+    if (threadIdx.x == 0) {
+      if (!ok) {
+        L.state = ST_DONE;
+        fc_on_done(L, F, *job, &E->c);
+      } else {
+        const Snap q = take_snap(E, L.phase);
+        if (st >= ST_FC_SAT) fc_advance(L, F, q, *job, lead);
+        else advance(L, q, P, N, &E->c, lead);
+        L.phase++;
+        if (L.state == ST_DONE && !F.finished) fc_on_done(L, F, *job, &E->c);
+      }
+    }
+    __syncthreads();
+  }
+  // statistics and results (the group leader)
+  if (a.hyper) atomicAdd(&E->c.items_hyper, a.hyper);
+  if (a.net) atomicAdd(&E->c.items_net, a.net);
+  if (a.nodes) atomicAdd(&E->c.node_visits, a.nodes);
+  if (a.pushes) atomicAdd(&E->c.pushes, a.pushes);
+  if (lead && threadIdx.x == 0) {
+    store_sched(E, L);
+    E->c.flow = L.flow;
+    E->c.rounds = L.rounds;
+    E->c.global_relabels = L.grs;
+    E->c.gr_levels = L.gr_levels;
+    if (L.wS_set) E->c.wS = L.wS;
+    if (L.wT_set) E->c.wT = L.wT;
+    job->status = F.status;
+    job->iterations = F.it;
+    job->n_pierced = F.np;
+    job->result_side = F.result_side;
+    job->flow = (long long)L.flow;
+    job->source_weight = F.source_weight;
+  }
+}
+
+// The batched launch: gridDim.x / G groups take jobs from the queue in
+// order (the host sorts them, largest first) until none is left.
+__global__ void __launch_bounds__(kEngineThreads) fc_batch_kernel(FcJob* jobs, int n_jobs,
+                                                                  BatchCtl* B, int G, Params P0) {
+  __shared__ Sched L;
+  __shared__ FcState F;
+  __shared__ NetDev N;
+  __shared__ Params P;
+  __shared__ long long w_sh;
+  __shared__ Clock ck;
+  __shared__ unsigned job_sh;
+  const int gid = blockIdx.x / G, rank = blockIdx.x % G;
+  const unsigned lane = lane_id();
+  if (threadIdx.x == 0) ck.t_last = globaltimer();
+  unsigned gseq = 0;
+  for (;;) {
+    if (rank == 0 && threadIdx.x == 0) B->gjob[gid] = atomicAdd(&B->next, 1u);
+    if (!group_sync(B, gid, G * ++gseq, P0.timeout_ns)) break;
+    if (threadIdx.x == 0) job_sh = *(const volatile unsigned*)&B->gjob[gid];
+    __syncthreads();
+    const unsigned j = job_sh;
+    if (j >= (unsigned)n_jobs) break;
+    fc_run_job(&jobs[j], P0, rank, G, lane, L, F, N, P, &w_sh, ck);
+    if (!group_sync(B, gid, G * ++gseq, P0.timeout_ns)) break;
+  }
+}

@@ -80,3 +80,41 @@ struct hfp_net {
   uint64_t launches = 0;
   uint64_t engine_ns = 0;
 };
+
+// Device-resident hypergraph of the k-way calls (kway.cu, sched.cu).
+struct hfp_hgraph {
+  hfp_ctx* ctx = nullptr;
+  int32_t n = 0, m = 0;
+  int64_t p = 0;
+  int64_t total_w = 0;
+  void* arena = nullptr;
+  uint32_t* net_off = nullptr;
+  int32_t* pins = nullptr;
+  int32_t* net_w = nullptr;
+  int32_t* node_w = nullptr;
+  uint32_t* vnet_off = nullptr;   // vertex -> nets incidence (ascending net ids)
+  int32_t* vnet = nullptr;
+  int32_t tuned_group = 0;        // CTAs per FlowCutter problem picked by hfp_autotune_round
+};
+
+namespace hfp {
+
+// One network of a batched FlowCutter launch (batch.cu).
+struct BatchItem {
+  hfp_net* net = nullptr;
+  hfp_fc_params params{};
+  int32_t* pierce_node_dev = nullptr;   // device piercing record (may be null)
+  int8_t* pierce_side_dev = nullptr;
+  int32_t pierce_cap = 0;
+  hfp_fc_result result{};
+  hfp_status status = HFP_OK;
+};
+
+// Grid of fc_batch_kernel on the context's device (all CTAs co-resident).
+hfp_status batch_grid(hfp_ctx* ctx, int* grid);
+// Runs FlowCutter on every item in one launch; group_ctas <= 0 picks the
+// largest group size that gives every item its own group.  ms_out (may be
+// null) receives the kernel time.
+hfp_status run_fc_batch(hfp_ctx* ctx, BatchItem* items, int n, int group_ctas, float* ms_out);
+
+}  // namespace hfp

@@ -46,9 +46,12 @@ void launch_st_attrs(int32_t* node_gid, int32_t* node_w, int8_t* node_orig,
 // engine.cu
 constexpr int kEngineThreads = 512;
 __global__ void __launch_bounds__(kEngineThreads) engine_kernel(NetDev N, EngineCtl* E, Params P);
+__global__ void __launch_bounds__(kEngineThreads) fc_batch_kernel(FcJob* jobs, int n_jobs,
+                                                                  BatchCtl* B, int G, Params P0);
 
 // cuts.cu
-enum SetupMode : int { SETUP_GR = 0, SETUP_ROUND = 1, SETUP_SR = 2, SETUP_PREP = 3, SETUP_DIST = 4 };
+enum SetupMode : int { SETUP_GR = 0, SETUP_ROUND = 1, SETUP_SR = 2, SETUP_PREP = 3, SETUP_DIST = 4,
+                       SETUP_BATCH = 5 };
 void launch_engine_setup(EngineCtl* E, int mode, cudaStream_t st);
 void launch_saturate(const NetDev& N, EngineCtl* E, const int32_t* nodes, int32_t count,
                      cudaStream_t st);

@@ -23,20 +23,6 @@
 
 using namespace hfp;
 
-struct hfp_hgraph {
-  hfp_ctx* ctx = nullptr;
-  int32_t n = 0, m = 0;
-  int64_t p = 0;
-  int64_t total_w = 0;
-  void* arena = nullptr;
-  uint32_t* net_off = nullptr;
-  int32_t* pins = nullptr;
-  int32_t* net_w = nullptr;
-  int32_t* node_w = nullptr;
-  uint32_t* vnet_off = nullptr;   // vertex -> nets incidence (ascending net ids)
-  int32_t* vnet = nullptr;
-};
-
 namespace hfp {
 
 namespace {
@@ -225,10 +211,11 @@ __global__ void k_pair_cut(const NetDev N, unsigned long long* cut) {
 
 // moves of a pair: region vertices whose final side differs from the
 // original one, in region order: (vertex, from block, to block)
-__global__ void k_move_flags(unsigned cnt, const int32_t* region, const int32_t* side,
+// region vertex i moves when its final side differs from its block (bi: 0)
+__global__ void k_move_flags(unsigned cnt, const int32_t* region, const int32_t* part, int32_t bi,
                              const uint8_t* fin, unsigned* flag) {
   for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x)
-    flag[i] = (int)fin[i] != side[region[i]] ? 1u : 0u;
+    flag[i] = (int)fin[i] != (part[region[i]] == bi ? 0 : 1) ? 1u : 0u;
 }
 
 __global__ void k_move_fill(unsigned cnt, const int32_t* region, const uint8_t* fin,
@@ -492,38 +479,65 @@ namespace {
 
 // One pair: region, network, FlowCutter, moves (device) and Delta_exp.
 // moves_dev receives up to cap triples; res->n_moves is the count.
-hfp_status refine_pair(hfp_hgraph* hg, const int32_t* part, int32_t k, int32_t bi, int32_t bj,
-                       const hfp_refine_params* prm, DevBuf& moves_dev, hfp_pair_result* res) {
+// n-sized buffers of region growing, reused by the pairs of a round.
+struct RegionScratch {
+  DevBuf side, lev, wsum, flag, pos, cand, wts, scr, tot, inb, taken, cut;
+  hfp_status alloc(hfp_hgraph* hg) {
+    cudaStream_t st = hg->ctx->stream;
+    const size_t n = hg->n > 0 ? hg->n : 1;
+    CK(side.alloc(sizeof(int32_t) * n, st));
+    CK(lev.alloc(sizeof(int32_t) * n, st));
+    CK(wsum.alloc(sizeof(unsigned long long) * 2, st));
+    CK(flag.alloc(sizeof(unsigned) * n, st));
+    CK(pos.alloc(sizeof(unsigned) * n, st));
+    CK(cand.alloc(sizeof(int32_t) * n, st));
+    CK(wts.alloc(sizeof(unsigned) * n, st));
+    CK(scr.alloc(sizeof(unsigned) * (scan_scratch_words((unsigned)n) + 8), st));
+    CK(tot.alloc(sizeof(unsigned), st));
+    CK(inb.alloc(n, st));
+    CK(taken.alloc(sizeof(unsigned), st));
+    CK(cut.alloc(sizeof(unsigned long long), st));
+    return HFP_OK;
+  }
+};
+
+// A block pair between region growing and the moves.
+struct PairWork {
+  hfp_pair_result r{};
+  hfp_net* net = nullptr;
+  DevBuf region;      // region vertices, ascending
+  int32_t nr = 0;
+  PairWork() = default;
+  PairWork(const PairWork&) = delete;
+  ~PairWork() {
+    if (net) hfp_net_destroy(net);
+  }
+};
+
+// Region of the pair (Section 6), its flow network and the pair's original
+// cut on the network's nets.
+hfp_status prepare_pair(hfp_hgraph* hg, const int32_t* part, int32_t k, int32_t bi, int32_t bj,
+                        const hfp_refine_params* prm, RegionScratch& sc, PairWork& w) {
   hfp_ctx* ctx = hg->ctx;
   cudaStream_t st = ctx->stream;
   const int n = hg->n, m = hg->m, sms = ctx->sms;
+  hfp_pair_result* res = &w.r;
   memset(res, 0, sizeof(*res));
   res->bi = bi;
   res->bj = bj;
-  DevBuf side, lev, wsum, flag, pos, cand, wts, scr, tot, inb, taken;
-  CK(side.alloc(sizeof(int32_t) * (n > 0 ? n : 1), st));
-  CK(lev.alloc(sizeof(int32_t) * (n > 0 ? n : 1), st));
-  CK(wsum.alloc(sizeof(unsigned long long) * 2, st));
-  CK(flag.alloc(sizeof(unsigned) * (n > 0 ? n : 1), st));
-  CK(pos.alloc(sizeof(unsigned) * (n > 0 ? n : 1), st));
-  CK(cand.alloc(sizeof(int32_t) * (n > 0 ? n : 1), st));
-  CK(wts.alloc(sizeof(unsigned) * (n > 0 ? n : 1), st));
-  CK(scr.alloc(sizeof(unsigned) * (scan_scratch_words(n) + 8), st));
-  CK(tot.alloc(sizeof(unsigned), st));
-  CK(inb.alloc(n > 0 ? n : 1, st));
-  CK(taken.alloc(sizeof(unsigned), st));
-  CK(cudaMemsetAsync(wsum.p, 0, sizeof(unsigned long long) * 2, st));
-  CK(cudaMemsetAsync(inb.p, 0, n > 0 ? n : 1, st));
-  k_side<<<nb(n, 256, sms * 8), 256, 0, st>>>(n, part, bi, bj, hg->node_w, side.as<int32_t>(),
-                                             lev.as<int32_t>(), wsum.as<unsigned long long>());
+  CK(cudaMemsetAsync(sc.wsum.p, 0, sizeof(unsigned long long) * 2, st));
+  CK(cudaMemsetAsync(sc.inb.p, 0, n > 0 ? n : 1, st));
+  k_side<<<nb(n, 256, sms * 8), 256, 0, st>>>(n, part, bi, bj, hg->node_w, sc.side.as<int32_t>(),
+                                             sc.lev.as<int32_t>(),
+                                             sc.wsum.as<unsigned long long>());
   count_launches(1);
   if (m) {
     k_level1<<<nb((long long)m * 32, 256, sms * 16), 256, 0, st>>>(
-        m, hg->net_off, hg->pins, side.as<int32_t>(), lev.as<int32_t>());
+        m, hg->net_off, hg->pins, sc.side.as<int32_t>(), sc.lev.as<int32_t>());
     count_launches(1);
   }
   unsigned long long cw[2];
-  CK(cudaMemcpyAsync(cw, wsum.p, sizeof(cw), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(cw, sc.wsum.p, sizeof(cw), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   const long long half = (long long)((cw[0] + cw[1] + 1) / 2);
   const long long lim = ((long long)(100 + prm->alpha_eps_pct) * half) / 100;
@@ -533,113 +547,144 @@ hfp_status refine_pair(hfp_hgraph* hg, const int32_t* part, int32_t k, int32_t b
   for (int s = 0; s < 2; s++) {
     long long left = budget[s];
     for (int d = 1; d <= prm->delta; d++) {
-      k_flag<<<nb(n, 256, sms * 8), 256, 0, st>>>(n, side.as<int32_t>(), lev.as<int32_t>(), s, d,
-                                                  flag.as<unsigned>());
+      k_flag<<<nb(n, 256, sms * 8), 256, 0, st>>>(n, sc.side.as<int32_t>(), sc.lev.as<int32_t>(),
+                                                  s, d, sc.flag.as<unsigned>());
       count_launches(1);
-      hfp_status r = compact(hg, n, flag.as<unsigned>(), pos.as<unsigned>(), cand.as<int32_t>(),
-                             wts.as<unsigned>(), scr.as<unsigned>(), tot.as<unsigned>(), &h_cnt);
+      hfp_status r = compact(hg, n, sc.flag.as<unsigned>(), sc.pos.as<unsigned>(),
+                             sc.cand.as<int32_t>(), sc.wts.as<unsigned>(), sc.scr.as<unsigned>(),
+                             sc.tot.as<unsigned>(), &h_cnt);
       if (r != HFP_OK) return r;
       if (h_cnt == 0) break;
-      unsigned wtot = 0;
-      scan_exclusive(wts.as<unsigned>(), h_cnt, scr.as<unsigned>(), tot.as<unsigned>(), st);
-      CK(cudaMemsetAsync(taken.p, 0, sizeof(unsigned), st));
-      k_take<<<nb(h_cnt, 256, sms * 8), 256, 0, st>>>(h_cnt, cand.as<int32_t>(), wts.as<unsigned>(),
-                                                      hg->node_w, left, inb.as<uint8_t>(),
-                                                      taken.as<unsigned>());
+      scan_exclusive(sc.wts.as<unsigned>(), h_cnt, sc.scr.as<unsigned>(), sc.tot.as<unsigned>(),
+                     st);
+      CK(cudaMemsetAsync(sc.taken.p, 0, sizeof(unsigned), st));
+      k_take<<<nb(h_cnt, 256, sms * 8), 256, 0, st>>>(h_cnt, sc.cand.as<int32_t>(),
+                                                      sc.wts.as<unsigned>(), hg->node_w, left,
+                                                      sc.inb.as<uint8_t>(),
+                                                      sc.taken.as<unsigned>());
       count_launches(1);
       unsigned h2[2];
-      CK(cudaMemcpyAsync(&h2[0], taken.p, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
-      CK(cudaMemcpyAsync(&h2[1], tot.p, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+      CK(cudaMemcpyAsync(&h2[0], sc.taken.p, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+      CK(cudaMemcpyAsync(&h2[1], sc.tot.p, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));
-      wtot = h2[1];
       if (h2[0] < h_cnt) break;           // the first vertex that does not fit ends growth
-      left -= (long long)wtot;
+      left -= (long long)h2[1];
       if (d == prm->delta) break;
       k_next_level<<<nb((long long)h_cnt * 32, 256, sms * 16), 256, 0, st>>>(
-          h_cnt, cand.as<int32_t>(), hg->vnet_off, hg->vnet, hg->net_off, hg->pins,
-          side.as<int32_t>(), s, lev.as<int32_t>(), d + 1);
+          h_cnt, sc.cand.as<int32_t>(), hg->vnet_off, hg->vnet, hg->net_off, hg->pins,
+          sc.side.as<int32_t>(), s, sc.lev.as<int32_t>(), d + 1);
       count_launches(1);
     }
   }
   // region (ascending) and its distances
-  k_inb_flag<<<nb(n, 256, sms * 8), 256, 0, st>>>(n, inb.as<uint8_t>(), flag.as<unsigned>());
+  k_inb_flag<<<nb(n, 256, sms * 8), 256, 0, st>>>(n, sc.inb.as<uint8_t>(), sc.flag.as<unsigned>());
   count_launches(1);
   unsigned nr = 0;
-  hfp_status r = compact(hg, n, flag.as<unsigned>(), pos.as<unsigned>(), cand.as<int32_t>(),
-                         nullptr, scr.as<unsigned>(), tot.as<unsigned>(), &nr);
+  hfp_status r = compact(hg, n, sc.flag.as<unsigned>(), sc.pos.as<unsigned>(),
+                         sc.cand.as<int32_t>(), nullptr, sc.scr.as<unsigned>(),
+                         sc.tot.as<unsigned>(), &nr);
   if (r != HFP_OK) return r;
   DevBuf dist;
   CK(dist.alloc(sizeof(int32_t) * (nr > 0 ? nr : 1), st));
+  CK(w.region.alloc(sizeof(int32_t) * (nr > 0 ? nr : 1), st));
   if (nr) {
-    k_region_dist<<<nb(nr, 256, sms * 8), 256, 0, st>>>(nr, cand.as<int32_t>(), lev.as<int32_t>(),
-                                                        dist.as<int32_t>());
+    k_region_dist<<<nb(nr, 256, sms * 8), 256, 0, st>>>(nr, sc.cand.as<int32_t>(),
+                                                        sc.lev.as<int32_t>(), dist.as<int32_t>());
     count_launches(1);
+    CK(cudaMemcpyAsync(w.region.p, sc.cand.p, sizeof(int32_t) * nr, cudaMemcpyDeviceToDevice, st));
   }
+  w.nr = (int32_t)nr;
   res->region_size = (int32_t)nr;
   hfp_hypergraph Hd{n, m, hg->net_off, hg->pins, hg->net_w, hg->node_w};
-  hfp_net* net = nullptr;
-  r = hfp_build_flow_network(ctx, &Hd, HFP_MEM_DEVICE, cand.as<int32_t>(), (int32_t)nr,
-                             side.as<int32_t>(), dist.as<int32_t>(), &net);
+  r = hfp_build_flow_network(ctx, &Hd, HFP_MEM_DEVICE, w.region.as<int32_t>(), (int32_t)nr,
+                             sc.side.as<int32_t>(), dist.as<int32_t>(), &w.net);
   if (r != HFP_OK) return r;
-  res->pins = net->d.p_pins;
-  {
-    DevBuf cut;
-    CK(cut.alloc(sizeof(unsigned long long), st));
-    CK(cudaMemsetAsync(cut.p, 0, sizeof(unsigned long long), st));
-    if (net->d.m_nets) {
-      k_pair_cut<<<nb((long long)net->d.m_nets * 32, 256, sms * 16), 256, 0, st>>>(
-          net->d, cut.as<unsigned long long>());
-      count_launches(1);
-    }
-    unsigned long long hc = 0;
-    CK(cudaMemcpyAsync(&hc, cut.p, sizeof(hc), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    res->original_cut = (int64_t)hc;
+  res->pins = w.net->d.p_pins;
+  CK(cudaMemsetAsync(sc.cut.p, 0, sizeof(unsigned long long), st));
+  if (w.net->d.m_nets) {
+    k_pair_cut<<<nb((long long)w.net->d.m_nets * 32, 256, sms * 16), 256, 0, st>>>(
+        w.net->d, sc.cut.as<unsigned long long>());
+    count_launches(1);
   }
+  unsigned long long hc = 0;
+  CK(cudaMemcpyAsync(&hc, sc.cut.p, sizeof(hc), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  res->original_cut = (int64_t)hc;
+  return HFP_OK;
+}
+
+// FlowCutter parameters of a pair: the k-way bound L and the original cut as
+// flow bound (Section 8.3, "Flow Value").
+hfp_fc_params pair_fc_params(hfp_hgraph* hg, int32_t k, const hfp_refine_params* prm,
+                             const PairWork& w) {
   hfp_fc_params fp;
   fp.max_block_weight = ((100 + prm->eps_pct) * ((hg->total_w + k - 1) / k)) / 100;
-  fp.flow_bound = res->original_cut;
+  fp.flow_bound = w.r.original_cut;
   fp.seed = prm->seed;
   fp.max_iterations = 0;
-  hfp_fc_result fr{};
-  r = hfp_flowcutter(net, &fp, nullptr, nullptr, nullptr, 0, &fr);
-  res->status = r;
+  return fp;
+}
+
+// FlowCutter outcome -> result fields and the moves (region order) against
+// the partition the pair was prepared with.  The network is released.
+hfp_status finish_pair(hfp_hgraph* hg, const int32_t* part, hfp_status fc, const hfp_fc_result& fr,
+                       RegionScratch& sc, PairWork& w, DevBuf& moves_dev) {
+  hfp_ctx* ctx = hg->ctx;
+  cudaStream_t st = ctx->stream;
+  const int sms = ctx->sms;
+  hfp_pair_result* res = &w.r;
+  res->status = fc;
   res->flow = fr.flow;
   res->iterations = fr.iterations;
-  if (r == HFP_NO_BALANCED_CUT || r == HFP_ABORTED_WORSE) {
-    hfp_net_destroy(net);
+  if (fc == HFP_NO_BALANCED_CUT || fc == HFP_ABORTED_WORSE) {
+    hfp_net_destroy(w.net);
+    w.net = nullptr;
     set_last_error("");
     return HFP_OK;
   }
-  if (r != HFP_OK) {
-    hfp_net_destroy(net);
-    return r;
-  }
+  if (fc != HFP_OK) return fc;
   res->delta_exp = res->original_cut - fr.flow;
-  // moves in region order
-  DevBuf fin, mflag, mpos;
-  CK(fin.alloc(nr > 0 ? nr : 1, st));
-  CK(mflag.alloc(sizeof(unsigned) * (nr > 0 ? nr : 1), st));
-  CK(mpos.alloc(sizeof(unsigned) * (nr > 0 ? nr : 1), st));
+  const unsigned nr = (unsigned)w.nr;
   unsigned nm = 0;
   if (nr) {
-    launch_region_side(net->d, fr.result_side, (int32_t)nr, fin.as<uint8_t>(), sms, st);
-    k_move_flags<<<nb(nr, 256, sms * 8), 256, 0, st>>>(nr, cand.as<int32_t>(), side.as<int32_t>(),
+    DevBuf fin, mflag, mpos;
+    CK(fin.alloc(nr, st));
+    CK(mflag.alloc(sizeof(unsigned) * nr, st));
+    CK(mpos.alloc(sizeof(unsigned) * nr, st));
+    launch_region_side(w.net->d, fr.result_side, (int32_t)nr, fin.as<uint8_t>(), sms, st);
+    k_move_flags<<<nb(nr, 256, sms * 8), 256, 0, st>>>(nr, w.region.as<int32_t>(), part, res->bi,
                                                        fin.as<uint8_t>(), mflag.as<unsigned>());
     count_launches(1);
     CK(cudaMemcpyAsync(mpos.p, mflag.p, sizeof(unsigned) * nr, cudaMemcpyDeviceToDevice, st));
-    scan_exclusive(mpos.as<unsigned>(), nr, scr.as<unsigned>(), tot.as<unsigned>(), st);
-    CK(cudaMemcpyAsync(&nm, tot.p, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    scan_exclusive(mpos.as<unsigned>(), nr, sc.scr.as<unsigned>(), sc.tot.as<unsigned>(), st);
+    CK(cudaMemcpyAsync(&nm, sc.tot.p, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     CK(moves_dev.alloc(sizeof(int32_t) * 3 * (nm > 0 ? nm : 1), st));
-    k_move_fill<<<nb(nr, 256, sms * 8), 256, 0, st>>>(nr, cand.as<int32_t>(), fin.as<uint8_t>(),
+    k_move_fill<<<nb(nr, 256, sms * 8), 256, 0, st>>>(nr, w.region.as<int32_t>(), fin.as<uint8_t>(),
                                                       mflag.as<unsigned>(), mpos.as<unsigned>(),
-                                                      bi, bj, moves_dev.as<int32_t>());
+                                                      res->bi, res->bj, moves_dev.as<int32_t>());
     count_launches(1);
   }
   res->n_moves = (int32_t)nm;
-  hfp_net_destroy(net);
+  hfp_net_destroy(w.net);
+  w.net = nullptr;
   return HFP_OK;
+}
+
+// One pair, one problem per launch sequence: region, network, FlowCutter
+// (hfp_flowcutter), moves.
+hfp_status refine_pair(hfp_hgraph* hg, const int32_t* part, int32_t k, int32_t bi, int32_t bj,
+                       const hfp_refine_params* prm, RegionScratch& sc, DevBuf& moves_dev,
+                       hfp_pair_result* res) {
+  PairWork w;
+  hfp_status s = prepare_pair(hg, part, k, bi, bj, prm, sc, w);
+  if (s != HFP_OK) return s;
+  const hfp_fc_params fp = pair_fc_params(hg, k, prm, w);
+  hfp_fc_result fr{};
+  const hfp_status fc = hfp_flowcutter(w.net, &fp, nullptr, nullptr, nullptr, 0, &fr);
+  s = finish_pair(hg, part, fc, fr, sc, w, moves_dev);
+  *res = w.r;
+  return s;
 }
 
 }  // namespace
@@ -652,8 +697,10 @@ HFP_API hfp_status hfp_refine_block_pair(hfp_hgraph* hg, const int32_t* part, in
     return fail(HFP_ERR_INVALID, "bad block pair");
   hfp_status s = hg_set_device(hg);
   if (s != HFP_OK) return s;
+  RegionScratch sc;
+  if ((s = sc.alloc(hg)) != HFP_OK) return s;
   DevBuf mv;
-  if ((s = refine_pair(hg, part, k, bi, bj, prm, mv, res)) != HFP_OK) return s;
+  if ((s = refine_pair(hg, part, k, bi, bj, prm, sc, mv, res)) != HFP_OK) return s;
   if (moves && res->n_moves > 0) {
     const int32_t c = res->n_moves < cap ? res->n_moves : cap;
     if (c > 0)
@@ -688,19 +735,15 @@ HFP_API hfp_status hfp_connectivity(hfp_hgraph* hg, const int32_t* part, int32_t
   return HFP_OK;
 }
 
-HFP_API hfp_status hfp_refine_round(hfp_hgraph* hg, int32_t* part, int32_t k,
-                                    const hfp_refine_params* prm, const float* pair_scores,
-                                    float min_score, hfp_round_stats* stats,
-                                    hfp_pair_result* pairs, int32_t cap, int32_t* n_pairs) {
-  if (!hg || !part || !prm || !stats) return fail(HFP_ERR_INVALID, "NULL argument");
-  if (k < 2 || k > 64) return fail(HFP_ERR_INVALID, "k must be in [2, 64]");
-  hfp_status s = hg_set_device(hg);
-  if (s != HFP_OK) return s;
-  hfp_ctx* ctx = hg->ctx;
-  cudaStream_t st = ctx->stream;
-  const int n = hg->n, m = hg->m, sms = ctx->sms;
-  memset(stats, 0, sizeof(*stats));
-  // connectivity and quotient graph
+namespace {
+
+// Pairs of adjacent blocks (quotient graph, Section 5) in ascending (i, j);
+// fills stats->connectivity_before and ->pairs_skipped.
+hfp_status round_pairs(hfp_hgraph* hg, const int32_t* part, int32_t k, const float* pair_scores,
+                       float min_score, hfp_round_stats* stats,
+                       std::vector<std::pair<int, int>>& pairs) {
+  cudaStream_t st = hg->ctx->stream;
+  const int m = hg->m, sms = hg->ctx->sms;
   DevBuf conn, qn, qw;
   CK(conn.alloc(sizeof(unsigned long long), st));
   CK(qn.alloc(sizeof(unsigned long long) * k * k, st));
@@ -716,16 +759,11 @@ HFP_API hfp_status hfp_refine_round(hfp_hgraph* hg, int32_t* part, int32_t k,
   }
   std::vector<unsigned long long> hq((size_t)k * k);
   unsigned long long c0 = 0;
-  CK(cudaMemcpyAsync(hq.data(), qn.p, sizeof(unsigned long long) * k * k, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(hq.data(), qn.p, sizeof(unsigned long long) * k * k, cudaMemcpyDeviceToHost,
+                     st));
   CK(cudaMemcpyAsync(&c0, conn.p, sizeof(c0), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   stats->connectivity_before = (int64_t)c0;
-  // refine every selected pair against the same partition
-  struct Item {
-    hfp_pair_result r;
-    DevBuf mv;
-  };
-  std::deque<Item> items;
   for (int i = 0; i < k; i++)
     for (int j = i + 1; j < k; j++) {
       if (hq[(size_t)i * k + j] == 0) continue;
@@ -733,10 +771,63 @@ HFP_API hfp_status hfp_refine_round(hfp_hgraph* hg, int32_t* part, int32_t k,
         stats->pairs_skipped++;
         continue;
       }
+      pairs.emplace_back(i, j);
+    }
+  return HFP_OK;
+}
+
+struct Item {
+  hfp_pair_result r;
+  DevBuf mv;
+};
+
+// Refines every pair against the same partition: one FlowCutter per launch
+// sequence (plain) or all FlowCutter problems in one batched launch.
+hfp_status refine_pairs(hfp_hgraph* hg, const int32_t* part, int32_t k,
+                        const hfp_refine_params* prm, const std::vector<std::pair<int, int>>& pairs,
+                        bool batched, int32_t group_ctas, std::deque<Item>& items,
+                        float* flow_ms) {
+  RegionScratch sc;
+  hfp_status s = sc.alloc(hg);
+  if (s != HFP_OK) return s;
+  if (!batched) {
+    for (const auto& pr : pairs) {
       items.emplace_back();
-      if ((s = refine_pair(hg, part, k, i, j, prm, items.back().mv, &items.back().r)) != HFP_OK)
+      if ((s = refine_pair(hg, part, k, pr.first, pr.second, prm, sc, items.back().mv,
+                           &items.back().r)) != HFP_OK)
         return s;
     }
+    return HFP_OK;
+  }
+  std::deque<PairWork> works;
+  for (const auto& pr : pairs) {
+    works.emplace_back();
+    if ((s = prepare_pair(hg, part, k, pr.first, pr.second, prm, sc, works.back())) != HFP_OK)
+      return s;
+  }
+  const int n = (int)works.size();
+  std::vector<BatchItem> bi(n);
+  for (int t = 0; t < n; t++) {
+    bi[t].net = works[t].net;
+    bi[t].params = pair_fc_params(hg, k, prm, works[t]);
+  }
+  const int G = group_ctas > 0 ? group_ctas : hg->tuned_group;
+  if ((s = run_fc_batch(hg->ctx, bi.data(), n, G, flow_ms)) != HFP_OK) return s;
+  for (int t = 0; t < n; t++) {
+    items.emplace_back();
+    s = finish_pair(hg, part, bi[t].status, bi[t].result, sc, works[t], items.back().mv);
+    items.back().r = works[t].r;
+    if (s != HFP_OK) return s;
+  }
+  return HFP_OK;
+}
+
+// Algorithm 1's apply step (Section 5, "Apply Moves") on the refined pairs.
+hfp_status apply_round(hfp_hgraph* hg, int32_t* part, int32_t k, const hfp_refine_params* prm,
+                       std::deque<Item>& items, hfp_round_stats* stats) {
+  hfp_ctx* ctx = hg->ctx;
+  cudaStream_t st = ctx->stream;
+  const int n = hg->n, m = hg->m, sms = ctx->sms;
   stats->pairs = (int32_t)items.size();
   // apply in descending Delta_exp, ties ascending (i, j)
   std::vector<int> order;
@@ -820,8 +911,95 @@ HFP_API hfp_status hfp_refine_round(hfp_hgraph* hg, int32_t* part, int32_t k,
   }
   CK(cudaStreamSynchronize(st));
   stats->connectivity_after = stats->connectivity_before - stats->gain;
+  return HFP_OK;
+}
+
+hfp_status round_impl(hfp_hgraph* hg, int32_t* part, int32_t k, const hfp_refine_params* prm,
+                      const float* pair_scores, float min_score, hfp_round_stats* stats,
+                      hfp_pair_result* pairs, int32_t cap, int32_t* n_pairs, bool batched,
+                      int32_t group_ctas, float* flow_ms) {
+  if (!hg || !part || !prm || !stats) return fail(HFP_ERR_INVALID, "NULL argument");
+  if (k < 2 || k > 64) return fail(HFP_ERR_INVALID, "k must be in [2, 64]");
+  if (prm->delta < 1) return fail(HFP_ERR_INVALID, "delta must be positive");
+  hfp_status s = hg_set_device(hg);
+  if (s != HFP_OK) return s;
+  memset(stats, 0, sizeof(*stats));
+  std::vector<std::pair<int, int>> pl;
+  if ((s = round_pairs(hg, part, k, pair_scores, min_score, stats, pl)) != HFP_OK) return s;
+  std::deque<Item> items;
+  if ((s = refine_pairs(hg, part, k, prm, pl, batched, group_ctas, items, flow_ms)) != HFP_OK)
+    return s;
+  if ((s = apply_round(hg, part, k, prm, items, stats)) != HFP_OK) return s;
   if (n_pairs) *n_pairs = (int32_t)items.size();
   if (pairs)
     for (int t = 0; t < (int)items.size() && t < cap; t++) pairs[t] = items[t].r;
+  return HFP_OK;
+}
+
+}  // namespace
+
+HFP_API hfp_status hfp_refine_round(hfp_hgraph* hg, int32_t* part, int32_t k,
+                                    const hfp_refine_params* prm, const float* pair_scores,
+                                    float min_score, hfp_round_stats* stats,
+                                    hfp_pair_result* pairs, int32_t cap, int32_t* n_pairs) {
+  return round_impl(hg, part, k, prm, pair_scores, min_score, stats, pairs, cap, n_pairs, false,
+                    0, nullptr);
+}
+
+HFP_API hfp_status hfp_refine_round_batched(hfp_hgraph* hg, int32_t* part, int32_t k,
+                                            const hfp_refine_params* prm,
+                                            const float* pair_scores, float min_score,
+                                            int32_t group_ctas, hfp_round_stats* stats,
+                                            hfp_pair_result* pairs, int32_t cap,
+                                            int32_t* n_pairs, float* flowcutter_ms) {
+  return round_impl(hg, part, k, prm, pair_scores, min_score, stats, pairs, cap, n_pairs, true,
+                    group_ctas, flowcutter_ms);
+}
+
+HFP_API hfp_status hfp_autotune_round(hfp_hgraph* hg, const int32_t* part, int32_t k,
+                                      const hfp_refine_params* prm, const int32_t* candidates,
+                                      int32_t n_candidates, float* ms, int32_t* best) {
+  if (!hg || !part || !prm || !candidates || n_candidates <= 0)
+    return fail(HFP_ERR_INVALID, "bad arguments");
+  if (k < 2 || k > 64 || prm->delta < 1) return fail(HFP_ERR_INVALID, "bad k or delta");
+  hfp_status s = hg_set_device(hg);
+  if (s != HFP_OK) return s;
+  int grid = 0;
+  if ((s = batch_grid(hg->ctx, &grid)) != HFP_OK) return s;
+  for (int c = 0; c < n_candidates; c++)
+    if (candidates[c] < 1 || candidates[c] > grid)
+      return fail(HFP_ERR_INVALID, "candidate %d: group size %d outside [1, %d]", c,
+                  candidates[c], grid);
+  hfp_round_stats st{};
+  std::vector<std::pair<int, int>> pl;
+  if ((s = round_pairs(hg, part, k, nullptr, 0.f, &st, pl)) != HFP_OK) return s;
+  RegionScratch sc;
+  if ((s = sc.alloc(hg)) != HFP_OK) return s;
+  float best_ms = 0.f;
+  int best_g = 0;
+  for (int c = 0; c < n_candidates; c++) {
+    // the same networks, rebuilt for every candidate
+    std::deque<PairWork> works;
+    for (const auto& pr : pl) {
+      works.emplace_back();
+      if ((s = prepare_pair(hg, part, k, pr.first, pr.second, prm, sc, works.back())) != HFP_OK)
+        return s;
+    }
+    const int n = (int)works.size();
+    std::vector<BatchItem> bi(n);
+    for (int t = 0; t < n; t++) {
+      bi[t].net = works[t].net;
+      bi[t].params = pair_fc_params(hg, k, prm, works[t]);
+    }
+    float t_ms = 0.f;
+    if ((s = run_fc_batch(hg->ctx, bi.data(), n, candidates[c], &t_ms)) != HFP_OK) return s;
+    if (ms) ms[c] = t_ms;
+    if (c == 0 || t_ms < best_ms) {
+      best_ms = t_ms;
+      best_g = candidates[c];
+    }
+  }
+  hg->tuned_group = best_g;
+  if (best) *best = best_g;
   return HFP_OK;
 }

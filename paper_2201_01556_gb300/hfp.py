@@ -73,6 +73,11 @@ class RoundStats(ctypes.Structure):
                 ("pairs_applied", ctypes.c_int32), ("pairs_skipped", ctypes.c_int32)]
 
 
+class AdamParams(ctypes.Structure):
+    _fields_ = [("lr", ctypes.c_float), ("eps", ctypes.c_float), ("beta1", ctypes.c_double),
+                ("beta2", ctypes.c_double)]
+
+
 class _NetworkView(ctypes.Structure):
     _fields_ = [("n_nodes", ctypes.c_int32), ("m_nets", ctypes.c_int32),
                 ("p_pins", ctypes.c_int64), ("net_off", ctypes.c_void_p),
@@ -90,6 +95,13 @@ class _FcResult(ctypes.Structure):
     _fields_ = [("flow", ctypes.c_int64), ("source_weight", ctypes.c_int64),
                 ("iterations", ctypes.c_int32), ("n_pierced", ctypes.c_int32),
                 ("result_side", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
+class _FcTask(ctypes.Structure):
+    _fields_ = [("net", ctypes.c_void_p), ("params", FcParams), ("final_side", ctypes.c_void_p),
+                ("pierce_side", ctypes.c_void_p), ("pierce_node", ctypes.c_void_p),
+                ("pierce_cap", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("result", _FcResult)]
 
 
 def library_path() -> str:
@@ -135,6 +147,17 @@ def load():
         "hfp_ctx_get_tuning": (i32, [P, ctypes.POINTER(Tuning)]),
         "hfp_ctx_set_tuning": (i32, [P, ctypes.POINTER(Tuning)]),
         "hfp_net_get_trace": (i32, [P, P, P, P, i32, P]),
+        "hfp_pair_features": (i32, [P, P, i32, i32, P, P, P, i32, P]),
+        "hfp_flowcutter_batch": (i32, [P, P, i32, i32]),
+        "hfp_refine_round_batched": (i32, [P, P, i32, ctypes.POINTER(RefineParams), P,
+                                           ctypes.c_float, i32, ctypes.POINTER(RoundStats), P,
+                                           i32, P, P]),
+        "hfp_autotune_round": (i32, [P, P, i32, ctypes.POINTER(RefineParams), P, i32, P, P]),
+        "hfp_mlp_forward": (i32, [P, P, P, i32, P]),
+        "hfp_mlp_grad": (i32, [P, P, P, P, i32, P, P]),
+        "hfp_mlp_train": (i32, [P, P, P, P, P, P, P, i32, i32, ctypes.POINTER(AdamParams), P,
+                                i32]),
+        "hfp_pair_scores": (i32, [P, P, i32, i32, P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -391,6 +414,134 @@ def refine_round(hg: HGraph, part_dev, k: int, params: RefineParams | None = Non
                                    ctypes.c_float(min_score), ctypes.byref(stats), arr, cap,
                                    ctypes.byref(n)))
     return stats, [arr[i] for i in range(n.value)]
+
+
+MLP_FEATURES, MLP_HIDDEN, MLP_PARAMS = 16, 64, 5313
+
+
+def flowcutter_batch(ctx: Context, nets, params, group_ctas: int = 0,
+                     pierce_cap: int | None = None):
+    """hfp_flowcutter_batch: FlowCutter on every network in one launch ->
+    [FlowCutterResult] (params: one FcParams per network)."""
+    n = len(nets)
+    tasks = (_FcTask * max(n, 1))()
+    keep = []
+    for i, (net, prm) in enumerate(zip(nets, params)):
+        cap = net.info.n_nodes if pierce_cap is None else pierce_cap
+        fs = np.zeros(max(net.n_region, 1), np.uint8)
+        ps = np.zeros(max(cap, 1), np.int32)
+        pn = np.zeros(max(cap, 1), np.int32)
+        keep.append((fs, ps, pn))
+        tasks[i].net = net.h
+        tasks[i].params = prm
+        tasks[i].final_side = fs.ctypes.data
+        tasks[i].pierce_side = ps.ctypes.data
+        tasks[i].pierce_node = pn.ctypes.data
+        tasks[i].pierce_cap = cap
+    _check(load().hfp_flowcutter_batch(ctx.h, tasks, n, group_ctas))
+    out = []
+    for i, net in enumerate(nets):
+        t = tasks[i]
+        fs, ps, pn = keep[i]
+        k = min(t.result.n_pierced, t.pierce_cap)
+        out.append(FlowCutterResult(t.status, t.result.flow, t.result.source_weight,
+                                    t.result.iterations, t.result.result_side,
+                                    fs[: net.n_region], ps[:k].copy(), pn[:k].copy()))
+    return out
+
+
+def refine_round_batched(hg: HGraph, part_dev, k: int, params: RefineParams | None = None,
+                         pair_scores=None, min_score: float = 0.0, group_ctas: int = 0):
+    """hfp_refine_round_batched -> (RoundStats, [PairResult], FlowCutter launch ms)."""
+    params = params or refine_params()
+    stats = RoundStats()
+    cap = k * k
+    arr = (PairResult * cap)()
+    n = ctypes.c_int32()
+    ms = ctypes.c_float()
+    sc = None if pair_scores is None else np.ascontiguousarray(pair_scores, np.float32)
+    _check(load().hfp_refine_round_batched(hg.h, _ptr(part_dev), k, ctypes.byref(params), _ptr(sc),
+                                           ctypes.c_float(min_score), group_ctas,
+                                           ctypes.byref(stats), arr, cap, ctypes.byref(n),
+                                           ctypes.byref(ms)))
+    return stats, [arr[i] for i in range(n.value)], float(ms.value)
+
+
+def autotune_round(hg: HGraph, part_dev, k: int, candidates, params: RefineParams | None = None):
+    """hfp_autotune_round -> (best group size, ms per candidate)."""
+    params = params or refine_params()
+    c = np.ascontiguousarray(candidates, np.int32)
+    ms = np.zeros(len(c), np.float32)
+    best = ctypes.c_int32()
+    _check(load().hfp_autotune_round(hg.h, _ptr(part_dev), k, ctypes.byref(params), _ptr(c), len(c),
+                                     _ptr(ms), ctypes.byref(best)))
+    return int(best.value), ms
+
+
+def pair_features(hg: HGraph, part_dev, k: int, eps_pct: int = 3, prev_gain=None):
+    """hfp_pair_features -> (pairs CUDA int32[P, 2], features CUDA float32[P, 16])."""
+    import torch
+    cap = k * (k - 1) // 2
+    dev = part_dev.device
+    feat = torch.zeros((max(cap, 1), MLP_FEATURES), dtype=torch.float32, device=dev)
+    pairs = torch.zeros((max(cap, 1), 2), dtype=torch.int32, device=dev)
+    pg = None if prev_gain is None else np.ascontiguousarray(prev_gain, np.int64)
+    n = ctypes.c_int32()
+    _check(load().hfp_pair_features(hg.h, _ptr(part_dev), k, eps_pct, _ptr(pg), _ptr(feat),
+                                    _ptr(pairs), cap, ctypes.byref(n)))
+    return pairs[: n.value], feat[: n.value]
+
+
+def mlp_forward(ctx: Context, params_dev, x_dev):
+    """hfp_mlp_forward -> scores (CUDA float32[rows])."""
+    import torch
+    rows = int(x_dev.shape[0])
+    out = torch.zeros(max(rows, 1), dtype=torch.float32, device=x_dev.device)
+    _check(load().hfp_mlp_forward(ctx.h, _ptr(params_dev), _ptr(x_dev), rows, _ptr(out)))
+    return out[:rows]
+
+
+def mlp_grad(ctx: Context, params_dev, x_dev, y_dev):
+    """hfp_mlp_grad -> (mean loss, gradient CUDA float32[MLP_PARAMS])."""
+    import torch
+    g = torch.zeros(MLP_PARAMS, dtype=torch.float32, device=x_dev.device)
+    loss = ctypes.c_float()
+    _check(load().hfp_mlp_grad(ctx.h, _ptr(params_dev), _ptr(x_dev), _ptr(y_dev),
+                               int(x_dev.shape[0]), _ptr(g), ctypes.byref(loss)))
+    return float(loss.value), g
+
+
+class MlpState:
+    """Parameters, Adam moments and step counter of the scheduler, on the
+    device (float32 CUDA tensors; the counter an int32 tensor)."""
+
+    def __init__(self, params_dev):
+        import torch
+        self.params = params_dev.contiguous()
+        self.m = torch.zeros_like(self.params)
+        self.v = torch.zeros_like(self.params)
+        self.step = torch.zeros(1, dtype=torch.int32, device=self.params.device)
+
+
+def mlp_train(ctx: Context, state: MlpState, x_dev, y_dev, steps: int, lr: float = 1e-3,
+              beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8):
+    """hfp_mlp_train: `steps` Adam steps in place -> losses CUDA float32[steps]."""
+    import torch
+    losses = torch.zeros(max(steps, 1), dtype=torch.float32, device=x_dev.device)
+    opt = AdamParams(lr, eps, beta1, beta2)
+    _check(load().hfp_mlp_train(ctx.h, _ptr(state.params), _ptr(state.m), _ptr(state.v),
+                                _ptr(state.step), _ptr(x_dev), _ptr(y_dev), int(x_dev.shape[0]),
+                                steps, ctypes.byref(opt), _ptr(losses), steps))
+    return losses[:steps]
+
+
+def pair_scores(hg: HGraph, part_dev, k: int, params_dev, eps_pct: int = 3, prev_gain=None):
+    """hfp_pair_scores -> host float32[k, k] (-1 where blocks share no net)."""
+    out = np.zeros((k, k), np.float32)
+    pg = None if prev_gain is None else np.ascontiguousarray(prev_gain, np.int64)
+    _check(load().hfp_pair_scores(hg.h, _ptr(part_dev), k, eps_pct, _ptr(pg), _ptr(params_dev),
+                                  _ptr(out)))
+    return out
 
 
 def net_stats(net: Net) -> dict:

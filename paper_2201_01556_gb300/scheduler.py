@@ -1,0 +1,112 @@
+"""Learned block-pair scheduler around hfp_refine_round.
+
+The paper's rounds refine every edge of the quotient graph (Section 5).  This
+module adds a small perceptron (hfp_mlp_*) that scores each edge before the
+round; pairs scoring below a threshold are skipped.  Everything numeric runs
+in libhfp's kernels; this file only sequences the calls:
+
+  collect()   runs plain (unpruned) rounds and records, per refined pair,
+              its 16 features and the label "the pair's flow refinement
+              found an improvement" (status OK and Delta_exp > 0);
+  train()     full-batch Adam on those samples (hfp_mlp_train);
+  refine()    rounds with or without the scheduler, returning the
+              connectivity trajectory and the wall time.
+"""
+from __future__ import annotations
+
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import hfp
+
+
+def init_params(seed: int = 0) -> np.ndarray:
+    """He-uniform hidden layers, a small output layer, zero biases (seeded)."""
+    rng = np.random.default_rng(seed)
+    W1 = rng.uniform(-1, 1, (64, 16)) * np.sqrt(6 / 16) * 0.25
+    W2 = rng.uniform(-1, 1, (64, 64)) * np.sqrt(6 / 64)
+    w3 = rng.uniform(-1, 1, 64) * np.sqrt(6 / 128)
+    z = np.zeros
+    return np.concatenate([W1.reshape(-1), z(64), W2.reshape(-1), z(64), w3, z(1)]).astype(
+        np.float32)
+
+
+def _prev_from(results, k: int) -> np.ndarray:
+    prev = -np.ones((k, k), np.int64)
+    for r in results:
+        prev[r.bi, r.bj] = r.gain if r.applied else 0
+    return prev
+
+
+@dataclass
+class Samples:
+    x: list = field(default_factory=list)      # float32[P, 16] per round
+    y: list = field(default_factory=list)      # float32[P]
+    pins: list = field(default_factory=list)   # int64[P]: network pins (cost proxy)
+
+    def arrays(self):
+        return (np.concatenate(self.x).astype(np.float32), np.concatenate(self.y).astype(np.float32),
+                np.concatenate(self.pins))
+
+
+def collect(hg, part_dev, k: int, rounds: int = 2, params=None, samples: Samples | None = None):
+    """Plain rounds on part_dev (updated); appends features and labels."""
+    params = params or hfp.refine_params()
+    samples = samples if samples is not None else Samples()
+    prev = None
+    for _ in range(rounds):
+        pairs, feat = hfp.pair_features(hg, part_dev, k, params.eps_pct, prev)
+        pairs = pairs.cpu().numpy()
+        stats, res = hfp.refine_round(hg, part_dev, k, params)
+        by = {(r.bi, r.bj): r for r in res}
+        y = np.zeros(len(pairs), np.float32)
+        pins = np.zeros(len(pairs), np.int64)
+        for t, (i, j) in enumerate(pairs):
+            r = by[(int(i), int(j))]
+            y[t] = 1.0 if (r.status == hfp.OK and r.delta_exp > 0) else 0.0
+            pins[t] = r.pins
+        samples.x.append(feat.cpu().numpy())
+        samples.y.append(y)
+        samples.pins.append(pins)
+        prev = _prev_from(res, k)
+    return samples
+
+
+def train(ctx, x: np.ndarray, y: np.ndarray, steps: int = 2000, lr: float = 3e-3, seed: int = 0):
+    """Adam on (x, y) from init_params(seed) -> (params CUDA tensor, losses)."""
+    import torch
+    st = hfp.MlpState(torch.from_numpy(init_params(seed)).cuda())
+    xd = torch.from_numpy(np.ascontiguousarray(x, np.float32)).cuda()
+    yd = torch.from_numpy(np.ascontiguousarray(y, np.float32)).cuda()
+    losses = hfp.mlp_train(ctx, st, xd, yd, steps, lr=lr)
+    return st.params, losses.cpu().numpy()
+
+
+def refine(hg, part_dev, k: int, rounds: int, params=None, mlp_params=None,
+           threshold: float = 0.5):
+    """rounds of refinement (stopping early at a round without gain), pruned
+    by the scheduler when mlp_params is given -> dict with the connectivity
+    after each round, pairs refined and skipped, and the wall time."""
+    import torch
+    params = params or hfp.refine_params()
+    prev = None
+    conn, refined, skipped = [], 0, 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(rounds):
+        scores = None
+        if mlp_params is not None:
+            scores = hfp.pair_scores(hg, part_dev, k, mlp_params, params.eps_pct, prev)
+        stats, res = hfp.refine_round(hg, part_dev, k, params, pair_scores=scores,
+                                      min_score=threshold)
+        refined += stats.pairs
+        skipped += stats.pairs_skipped
+        conn.append(int(stats.connectivity_after))
+        prev = _prev_from(res, k)
+        if stats.gain == 0:
+            break
+    torch.cuda.synchronize()
+    return dict(connectivity=conn, pairs=refined, skipped=skipped,
+                seconds=time.perf_counter() - t0)

@@ -9,6 +9,12 @@ flow by push-relabel, and extract the minimal source-side cut S_r.
 value = Lawler-network pins (p_N, s/t pins included) / step time, summed over
 ranks (independent replicas; the single max flow does not shard).
 
+The line also carries "kway": k-way refinement rounds (Algorithm 1) on the
+8,000,000-vertex / 12,000,000-net ring (2 + Zipf(2.5) pins capped at 10,000,
+k = 64 contiguous arcs, 5 % of the vertices moved to a neighbouring block),
+all FlowCutter problems of a round in one batched launch; --kway-plain adds
+the same rounds with one problem per launch sequence (identical partitions).
+
 --impl reference times the CPU oracle (Dinic on the explicit Lawler graph)
 on the host cores on a bounded sample of the same generator.
 """
@@ -162,6 +168,41 @@ def run_reference(args, rank, world):
     return 0
 
 
+def kway_rounds(hfp, ctx, args):
+    """Timed k-way refinement rounds: batched (and optionally plain) on the
+    same start partition; identical outcomes, so the times compare at equal
+    (lambda - 1)."""
+    import torch
+    n = args.kway_n
+    inst = synth.instance("ring_n8M_zipf_k64", args.seed, n=n, m=n * 3 // 2)
+    H, part = inst["H"], inst["part"]
+    hg = hfp.HGraph(ctx, H.net_off, H.pins, H.net_w, H.node_w, H.n)
+    out = {"workload": f"ring n={n} m={n * 3 // 2} k=64 (2+Zipf(2.5) <= 10000, 5% moved)",
+           "pins_H": int(H.p), "group_ctas": args.kway_group}
+    for mode in ("batched", "plain") if args.kway_plain else ("batched",):
+        pd = torch.from_numpy(part.copy()).cuda()
+        conn = [hfp.connectivity(hg, pd, 64)]
+        secs, pairs, fc_ms = [], [], []
+        for _ in range(args.kway_rounds):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            if mode == "batched":
+                st, _, ms = hfp.refine_round_batched(hg, pd, 64, group_ctas=args.kway_group)
+                fc_ms.append(round(ms, 1))
+            else:
+                st, _ = hfp.refine_round(hg, pd, 64)
+            torch.cuda.synchronize()
+            secs.append(round(time.perf_counter() - t0, 3))
+            conn.append(int(st.connectivity_after))
+            pairs.append(int(st.pairs))
+        out[mode] = {"seconds_per_round": secs, "connectivity_minus_1": conn,
+                     "pairs_per_round": pairs}
+        if fc_ms:
+            out[mode]["flowcutter_launch_ms"] = fc_ms
+    hg.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -175,6 +216,13 @@ def main():
     ap.add_argument("--n", type=int, default=None)
     ap.add_argument("--m", type=int, default=None)
     ap.add_argument("--radius", type=int, default=None)
+    ap.add_argument("--kway-rounds", type=int, default=2,
+                    help="k-way refinement rounds to time (0: none)")
+    ap.add_argument("--kway-n", type=int, default=8_000_000)
+    ap.add_argument("--kway-group", type=int, default=16,
+                    help="CTAs per FlowCutter problem (hfp_autotune_round's pick at 8M, k=64)")
+    ap.add_argument("--kway-plain", action="store_true",
+                    help="also time the one-problem-per-launch round")
     args = ap.parse_args()
     rank, world, local = env_rank()
     if args.impl == "reference":
@@ -290,6 +338,8 @@ def main():
             "clocks": clk, "roofline": roof,
             "engine": {"rounds": st["rounds"], "global_relabels": st["global_relabels"],
                        "gr_levels": st["gr_levels"], "pushes": st["pushes"]}}
+    if args.kway_rounds > 0:
+        line["kway"] = kway_rounds(hfp, ctx, args)
     if not args.no_cpu_baseline:
         sinst = synth.instance(WORKLOAD, args.seed, **SAMPLE)
         p, dt, _ = oracle_step(sinst)

@@ -10,7 +10,8 @@ in libhfp's kernels; this file only sequences the calls:
               found an improvement" (status OK and Delta_exp > 0);
   train()     full-batch Adam on those samples (hfp_mlp_train);
   refine()    rounds with or without the scheduler, returning the
-              connectivity trajectory and the wall time.
+              connectivity trajectory and the wall time; a pruned round
+              without gain is repeated unpruned before refinement stops.
 """
 from __future__ import annotations
 
@@ -51,15 +52,27 @@ class Samples:
                 np.concatenate(self.pins))
 
 
-def collect(hg, part_dev, k: int, rounds: int = 2, params=None, samples: Samples | None = None):
-    """Plain rounds on part_dev (updated); appends features and labels."""
+def _round(hg, part_dev, k, params, scores=None, threshold=0.5, batched=True):
+    if batched:
+        stats, res, _ = hfp.refine_round_batched(hg, part_dev, k, params, pair_scores=scores,
+                                                 min_score=threshold)
+    else:
+        stats, res = hfp.refine_round(hg, part_dev, k, params, pair_scores=scores,
+                                      min_score=threshold)
+    return stats, res
+
+
+def collect(hg, part_dev, k: int, rounds: int = 2, params=None, samples: Samples | None = None,
+            batched: bool = True):
+    """Unpruned rounds on part_dev (updated); appends features and labels.
+    The batched round gives the plain round's outcome, faster."""
     params = params or hfp.refine_params()
     samples = samples if samples is not None else Samples()
     prev = None
     for _ in range(rounds):
         pairs, feat = hfp.pair_features(hg, part_dev, k, params.eps_pct, prev)
         pairs = pairs.cpu().numpy()
-        stats, res = hfp.refine_round(hg, part_dev, k, params)
+        stats, res = _round(hg, part_dev, k, params, batched=batched)
         by = {(r.bi, r.bj): r for r in res}
         y = np.zeros(len(pairs), np.float32)
         pins = np.zeros(len(pairs), np.int64)
@@ -85,7 +98,7 @@ def train(ctx, x: np.ndarray, y: np.ndarray, steps: int = 2000, lr: float = 3e-3
 
 
 def refine(hg, part_dev, k: int, rounds: int, params=None, mlp_params=None,
-           threshold: float = 0.5):
+           threshold: float = 0.5, batched: bool = True):
     """rounds of refinement (stopping early at a round without gain), pruned
     by the scheduler when mlp_params is given -> dict with the connectivity
     after each round, pairs refined and skipped, and the wall time."""
@@ -95,18 +108,24 @@ def refine(hg, part_dev, k: int, rounds: int, params=None, mlp_params=None,
     conn, refined, skipped = [], 0, 0
     torch.cuda.synchronize()
     t0 = time.perf_counter()
+    fallbacks = 0
     for _ in range(rounds):
         scores = None
         if mlp_params is not None:
             scores = hfp.pair_scores(hg, part_dev, k, mlp_params, params.eps_pct, prev)
-        stats, res = hfp.refine_round(hg, part_dev, k, params, pair_scores=scores,
-                                      min_score=threshold)
+        stats, res = _round(hg, part_dev, k, params, scores, threshold, batched)
         refined += stats.pairs
         skipped += stats.pairs_skipped
+        if stats.gain == 0 and scores is not None and stats.pairs_skipped > 0:
+            # the unpruned schedule is the fallback: a pruned round without
+            # gain is repeated with every pair before refinement stops
+            fallbacks += 1
+            stats, res = _round(hg, part_dev, k, params, None, threshold, batched)
+            refined += stats.pairs
         conn.append(int(stats.connectivity_after))
         prev = _prev_from(res, k)
         if stats.gain == 0:
             break
     torch.cuda.synchronize()
-    return dict(connectivity=conn, pairs=refined, skipped=skipped,
+    return dict(connectivity=conn, pairs=refined, skipped=skipped, fallbacks=fallbacks,
                 seconds=time.perf_counter() - t0)

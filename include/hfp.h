@@ -137,7 +137,11 @@ uint64_t hfp_kernel_launches(void);
  *   tail_enter, tail_exit  frontiers of at most tail_enter nodes are run by
  *                 one CTA with block barriers until they exceed tail_exit
  *                 [64, 192]
- *   max_rounds    discharge-round budget of one network [2^22] */
+ *   max_rounds    discharge-round budget of one network [2^22]
+ *   bfs_enter, bfs_exit  breadth-first-search levels (global relabel, S_r,
+ *                 distances) of at most bfs_enter nodes (a heavy node counts
+ *                 32) are run by one CTA until they exceed bfs_exit
+ *                 [0, 0]: off; 0 still runs empty levels alone */
 typedef struct {
   uint32_t gr_work_x100;
   uint32_t stall_rounds;
@@ -145,6 +149,8 @@ typedef struct {
   uint32_t tail_enter;
   uint32_t tail_exit;
   uint32_t max_rounds;
+  uint32_t bfs_enter;
+  uint32_t bfs_exit;
 } hfp_tuning;
 hfp_status hfp_ctx_get_tuning(hfp_ctx* ctx, hfp_tuning* tuning);
 hfp_status hfp_ctx_set_tuning(hfp_ctx* ctx, const hfp_tuning* tuning);

@@ -131,10 +131,12 @@ hfp_status ensure_max_flow(hfp_net* net) {
 
 hfp_status ensure_source_side(hfp_net* net) {
   if (net->sr_valid) return HFP_OK;
-  launch_engine_setup(net->E, SETUP_SR, net->ctx->stream);
+  if (net->sr_seed >= 0) launch_engine_setup(net->E, SETUP_SR_ADD, net->ctx->stream, net->sr_seed);
+  else launch_engine_setup(net->E, SETUP_SR, net->ctx->stream);
   hfp_status s = run_engine(net);
   if (s != HFP_OK) return s;
   net->sr_valid = true;
+  net->sr_seed = -1;
   return HFP_OK;
 }
 
@@ -197,6 +199,8 @@ HFP_API hfp_status hfp_ctx_create(hfp_ctx** out, int device, void* stream) {
   c->params.stall_nodes = 1500;
   c->params.tail_enter = 64;       // CTA 0 alone at or below this frontier size
   c->params.tail_exit = 192;
+  c->params.bfs_enter = 0;         // CTA 0 alone for BFS levels up to this size: off (the
+  c->params.bfs_exit = 0;          // relabel BFS levels are wide; measured slower alone)
   *out = c;
   return HFP_OK;
 }
@@ -631,13 +635,15 @@ HFP_API hfp_status hfp_ctx_get_tuning(hfp_ctx* ctx, hfp_tuning* t) {
   t->tail_enter = ctx->params.tail_enter;
   t->tail_exit = ctx->params.tail_exit;
   t->max_rounds = (uint32_t)ctx->params.max_rounds;
+  t->bfs_enter = ctx->params.bfs_enter;
+  t->bfs_exit = ctx->params.bfs_exit;
   return HFP_OK;
 }
 
 HFP_API hfp_status hfp_ctx_set_tuning(hfp_ctx* ctx, const hfp_tuning* t) {
   if (!ctx || !t) return fail(HFP_ERR_INVALID, "NULL argument");
   if (t->gr_work_x100 == 0 || t->stall_rounds == 0 || t->max_rounds == 0 ||
-      t->tail_exit < t->tail_enter)
+      t->tail_exit < t->tail_enter || t->bfs_exit < t->bfs_enter)
     return fail(HFP_ERR_INVALID, "bad tuning values");
   ctx->gr_work_x100 = t->gr_work_x100;
   ctx->params.stall_rounds = t->stall_rounds;
@@ -645,6 +651,8 @@ HFP_API hfp_status hfp_ctx_set_tuning(hfp_ctx* ctx, const hfp_tuning* t) {
   ctx->params.tail_enter = t->tail_enter;
   ctx->params.tail_exit = t->tail_exit;
   ctx->params.max_rounds = t->max_rounds;
+  ctx->params.bfs_enter = t->bfs_enter;
+  ctx->params.bfs_exit = t->bfs_exit;
   return HFP_OK;
 }
 
@@ -737,7 +745,8 @@ HFP_API hfp_status hfp_min_cut_sink_side(hfp_net* net, hfp_mem mem, uint8_t* in_
 namespace {
 
 // Piercing-node selection by the rule of Section 7 (see hfp_flowcutter).
-hfp_status select_pierce(hfp_net* net, int grow_s, const hfp_fc_params* prm, int32_t* node) {
+hfp_status select_pierce(hfp_net* net, int grow_s, const hfp_fc_params* prm, int32_t* node,
+                         bool* no_path = nullptr) {
   Ctl c;
   hfp_status s = ensure_dist(net);
   if (s != HFP_OK) return s;
@@ -752,26 +761,51 @@ hfp_status select_pierce(hfp_net* net, int grow_s, const hfp_fc_params* prm, int
     return fail(HFP_NO_BALANCED_CUT, "no piercing candidate");
   }
   *node = c.best_node;
+  if (no_path) *no_path = ((c.best_key >> 53) & 1ull) != 0;
   return HFP_OK;
 }
 
-hfp_status pierce(hfp_net* net, int side, const int32_t* nodes, int32_t count) {
+// Piercing (Algorithm 2, the S or T update).  With `lazy` (one source-side
+// node that has no augmenting path: not in T_r) the flow is left alone: the
+// current preflow stays a maximum preflow for the grown S, T_r and the flow
+// value do not change, and S_r only grows by what the node reaches, so only
+// the node is marked and the next source-side search starts from it.  Its
+// arcs stay unsaturated until a sink-side piercing could open a path through
+// them; a later source-side piercing makes all it reaches sources anyway.
+hfp_status pierce(hfp_net* net, int side, const int32_t* nodes, int32_t count,
+                  bool lazy = false) {
   hfp_status s = stage_nodes(net, nodes, count);
   if (s != HFP_OK) return s;
   cudaStream_t st = net->ctx->stream;
   if (side == 0) {
     // S <- S_r + nodes; labels stay valid, the new excess is the frontier
     launch_mark_sources(net->d, net->dev_nodes, count, net->ctx->sms, st);
+    if (lazy && count == 1) {
+      net->pending_source = nodes[0];
+      net->sr_seed = net->sr_valid ? nodes[0] : -1;
+      net->sr_valid = false;
+      return HFP_OK;
+    }
+    net->pending_source = -1;
     launch_engine_setup(net->E, SETUP_PREP, st);
     launch_saturate(net->d, net->E, net->dev_nodes, count, st);
     launch_engine_setup(net->E, SETUP_ROUND, st);
   } else {
     // T <- T_r + nodes; labels are no longer lower bounds: relabel globally
     launch_mark_sinks(net->d, net->E, net->dev_nodes, count, net->ctx->sms, st);
+    if (net->pending_source >= 0) {
+      // the unsaturated source may now reach T: saturate it before the flow
+      const int32_t u = net->pending_source;
+      net->pending_source = -1;
+      if ((s = stage_nodes(net, &u, 1)) != HFP_OK) return s;
+      launch_engine_setup(net->E, SETUP_PREP, st);
+      launch_saturate(net->d, net->E, net->dev_nodes, 1, st);
+    }
     launch_engine_setup(net->E, SETUP_GR, st);
   }
   net->labels_exact = false;
   net->sr_valid = false;
+  net->sr_seed = -1;
   if ((s = run_engine(net)) != HFP_OK) return s;
   net->labels_exact = true;
   return HFP_OK;
@@ -860,14 +894,15 @@ HFP_API hfp_status hfp_flowcutter(hfp_net* net, const hfp_fc_params* prm, uint8_
     }
     const int grow_s = wS <= wT;
     int32_t p = -1;
-    if ((s = select_pierce(net, grow_s, prm, &p)) != HFP_OK) {
+    bool no_path = false;
+    if ((s = select_pierce(net, grow_s, prm, &p, &no_path)) != HFP_OK) {
       status = s;
       break;
     }
     if (pierce_side && np < pierce_cap) pierce_side[np] = grow_s ? 0 : 1;
     if (pierce_node && np < pierce_cap) pierce_node[np] = p;
     np++;
-    if ((s = pierce(net, grow_s ? 0 : 1, &p, 1)) != HFP_OK) return s;
+    if ((s = pierce(net, grow_s ? 0 : 1, &p, 1, grow_s && no_path)) != HFP_OK) return s;
     it++;
   }
   r.iterations = it;

@@ -22,7 +22,7 @@ __device__ void zero_phase_counters(EngineCtl& X) {
   X.gr_act[1] = 0;
 }
 
-__global__ void k_engine_setup(EngineCtl* E, int mode) {
+__global__ void k_engine_setup(EngineCtl* E, int mode, int32_t arg) {
   EngineCtl& X = *E;
   X.bar_count = 0;
   X.c.err = kDevOk;
@@ -67,6 +67,14 @@ __global__ void k_engine_setup(EngineCtl* E, int mode) {
       break;
     case SETUP_BATCH:
       zero_phase_counters(X);
+      break;
+    case SETUP_SR_ADD:
+      // S_r grows by the reach of one new source; wS is kept
+      zero_phase_counters(X);
+      X.s.state = ST_SR_ADD;
+      X.s.epoch++;
+      X.s.sr_seed = arg;
+      X.s.wS_set = 1;
       break;
   }
 }
@@ -289,8 +297,8 @@ static inline unsigned nblk(long long work, unsigned per, unsigned cap) {
   return (unsigned)b;
 }
 
-void launch_engine_setup(EngineCtl* E, int mode, cudaStream_t st) {
-  k_engine_setup<<<1, 1, 0, st>>>(E, mode);
+void launch_engine_setup(EngineCtl* E, int mode, cudaStream_t st, int32_t arg) {
+  k_engine_setup<<<1, 1, 0, st>>>(E, mode, arg);
   count_launches(1);
 }
 

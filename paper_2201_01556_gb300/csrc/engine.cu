@@ -60,10 +60,20 @@ struct Team {
   unsigned gwarp, nwarps, tid, nth, block, nblocks;
 };
 
-// Append counters and accumulators of the current phase (slot phase % 3).
+// Append counters and accumulators of the current phase: slot phase % 3 of
+// the control block in grid phases, shared memory in CTA-alone phases.
 struct Slot {
   unsigned* c[C_COUNT];
   unsigned long long* flow;
+  unsigned* act[2];            // active nodes found by the running global relabel
+};
+
+// Counters of CTA-alone phases (shared memory of the CTA running them).
+struct SoloSh {
+  unsigned c[C_COUNT];
+  unsigned act[2];
+  unsigned long long flow;
+  int stay;
 };
 
 __device__ __forceinline__ int32_t* lab_cur(const NetDev& N, int lp) { return lp ? N.lab1 : N.lab0; }
@@ -202,6 +212,7 @@ __device__ void advance(Sched& L, const Snap& q, const Params& P, const NetDev& 
     }
     case ST_GR_INIT:
     case ST_SR_INIT:
+    case ST_SR_ADD:
     case ST_DIST_INIT:
       L.bfs_begin = 0;
       L.bfs_end = q.c[C_BFS];
@@ -209,9 +220,9 @@ __device__ void advance(Sched& L, const Snap& q, const Params& P, const NetDev& 
       L.bfsh_end = q.c[C_BFSH];
       L.level = 0;
       if (L.state == ST_GR_INIT) L.wT += q.w;
-      if (L.state == ST_SR_INIT) L.wS += q.w;
+      if (L.state == ST_SR_INIT || L.state == ST_SR_ADD) L.wS += q.w;
       L.state = L.state == ST_GR_INIT ? ST_GR_LEVEL
-                : L.state == ST_SR_INIT ? ST_SR_LEVEL : ST_DIST_LEVEL;
+                : L.state == ST_DIST_INIT ? ST_DIST_LEVEL : ST_SR_LEVEL;
       break;
     case ST_GR_LEVEL:
     case ST_SR_LEVEL:
@@ -839,7 +850,7 @@ __device__ __forceinline__ void gr_emit(const NetDev& N, EngineCtl* E, const Sch
   bool act, hv;
   const bool k = gr_claim(N, c, d1, act, hv, a);
   append_split(k, c, hv, N.list[L_BFS], S.c[C_BFS], S.c[C_BFSH], L.bfs_end, L.bfsh_end, N.NL);
-  append_split(act, c, hv, N.list[L_FRONT], &E->gr_act[0], &E->gr_act[1], 0, 0, N.NL);
+  append_split(act, c, hv, N.list[L_FRONT], S.act[0], S.act[1], 0, 0, N.NL);
 }
 
 // Global relabel, one level: reverse BFS over residual arcs of the capped
@@ -911,6 +922,25 @@ __device__ void sr_init(const NetDev& N, const Sched& L, const Team& T, const Sl
     }
     append_split(seed, (int)x, hv, N.list[L_BFS], S.c[C_BFS], S.c[C_BFSH], 0, 0, N.NL);
   }
+}
+
+// Source-side cut after adding one source u whose arcs were left as they
+// were (a piercing node without augmenting path): the preflow is still a
+// maximum preflow, S_r only grows by what u reaches, so the search starts at
+// u alone and keeps every node already in S_r.
+__device__ void sr_add(const NetDev& N, const Sched& L, const Team& T, const Slot& S,
+                       unsigned lane, Acc& a) {
+  if (T.tid >= 32) return;
+  const int u = L.sr_seed;
+  bool seed = false, hv = false;
+  if (lane == 0 && u >= 0 && !N.insr[u]) {
+    N.insr[u] = 1;
+    N.stamp[u] = L.epoch;
+    hv = (N.flags[u] & kHeavy) != 0;
+    if (u < N.n_nodes) a.w += N.node_w[u];
+    seed = true;
+  }
+  append_split(seed, u, hv, N.list[L_BFS], S.c[C_BFS], S.c[C_BFSH], 0, 0, N.NL);
 }
 
 // Forward residual arcs out of x with (u, e_in) uncapped, arc group k.
@@ -1040,19 +1070,22 @@ __device__ __forceinline__ Slot slot_of(EngineCtl* E, unsigned k) {
 #pragma unroll
   for (int i = 0; i < C_COUNT; i++) S.c[i] = &E->cnt3[i][sl];
   S.flow = &E->flow3[sl];
+  S.act[0] = &E->gr_act[0];
+  S.act[1] = &E->gr_act[1];
   return S;
 }
 
-// One phase of the current state by team T; weights go to the phase slot.
-__device__ void run_phase(const NetDev& N, EngineCtl* E, const Sched& L, const Team& T,
-                          unsigned lane, Acc& a, long long* w_sh) {
-  const Slot S = slot_of(E, L.phase);
+// One phase of the current state by team T with counters S; hypernode
+// weights reached go to w_sh.
+__device__ void run_phase_s(const NetDev& N, EngineCtl* E, const Sched& L, const Team& T,
+                            const Slot& S, unsigned lane, Acc& a, long long* w_sh) {
   switch (L.state) {
     case ST_ROUND_A: phase_a(N, L, T, S, lane, a, E); break;
     case ST_ROUND_B: phase_b(N, L, T, S, lane, a); break;
     case ST_GR_INIT: gr_init(N, T, S, lane, a); break;
     case ST_GR_LEVEL: gr_level(N, E, L, T, S, lane, a); break;
     case ST_SR_INIT: sr_init(N, L, T, S, lane, a); break;
+    case ST_SR_ADD: sr_add(N, L, T, S, lane, a); break;
     case ST_SR_LEVEL: sr_level(N, L, T, S, lane, a); break;
     case ST_DIST_INIT: dist_init(N, T, S, lane); break;
     case ST_DIST_LEVEL: dist_level(N, L, T, S, lane); break;
@@ -1062,6 +1095,12 @@ __device__ void run_phase(const NetDev& N, EngineCtl* E, const Sched& L, const T
     atomicAdd((unsigned long long*)w_sh, (unsigned long long)a.w);
     a.w = 0;
   }
+}
+
+// One grid phase: counters in the phase's slot of the control block.
+__device__ void run_phase(const NetDev& N, EngineCtl* E, const Sched& L, const Team& T,
+                          unsigned lane, Acc& a, long long* w_sh) {
+  run_phase_s(N, E, L, T, slot_of(E, L.phase), lane, a, w_sh);
 }
 
 __device__ __forceinline__ void flush_weight(EngineCtl* E, unsigned k, long long* w_sh) {
@@ -1085,35 +1124,105 @@ __device__ __forceinline__ void tick(Clock& ck, int st) {
   ck.t_last = t;
 }
 
-// Rounds by CTA 0 alone while the frontier stays small: block barriers
-// instead of grid barriers.  Leaves with L holding the next grid state.
-__device__ void tail_rounds(const NetDev& N, EngineCtl* E, const Params& P, Sched& L,
-                            unsigned lane, Acc& a, long long* w_sh, Clock& ck) {
+__device__ __forceinline__ bool is_level(int st) {
+  return st == ST_GR_LEVEL || st == ST_SR_LEVEL || st == ST_DIST_LEVEL;
+}
+
+// Work of the next BFS level: light nodes, plus heavy ones counted 32 times
+// (a CTA walks a heavy node's arcs alone).
+__device__ __forceinline__ unsigned level_size(const Sched& L) {
+  return (L.bfs_end - L.bfs_begin) + 32u * (L.bfsh_end - L.bfsh_begin);
+}
+
+// Whether the next phase runs CTA-alone: small frontiers (the ST_TAIL state
+// that advance() picks) and thin breadth-first-search levels.  Every CTA
+// evaluates it on its identical copy of the state.
+__device__ __forceinline__ bool solo_next(const Sched& L, const Params& P) {
+  return L.state == ST_TAIL || (is_level(L.state) && level_size(L) <= P.bfs_enter);
+}
+
+// Phases run by one CTA while the work stays small: rounds while the
+// frontier has at most tail_exit nodes, breadth-first-search levels while
+// they have at most bfs_exit nodes.  Block barriers instead of grid barriers
+// and append counters in shared memory, so a phase costs its own dependent
+// loads and nothing else.  The active-node counters of a running global
+// relabel move into shared memory and back; on leaving, every phase slot of
+// the control block is zeroed (the other CTAs wait at the grid barrier).
+// Leaves with L holding the next grid state.
+__device__ void solo_phases(const NetDev& N, EngineCtl* E, const Params& P, Sched& L,
+                            unsigned lane, Acc& a, long long* w_sh, Clock& ck, SoloSh& sh) {
   const Team T{threadIdx.x >> 5, blockDim.x >> 5, threadIdx.x, blockDim.x, 0, 1};
   __syncthreads();   // every thread has read the caller's state before it is rewritten
-  if (threadIdx.x == 0) L.state = ST_ROUND_A;
-  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (L.state == ST_TAIL) L.state = ST_ROUND_A;
+    sh.act[0] = ld_cg(&E->gr_act[0]);
+    sh.act[1] = ld_cg(&E->gr_act[1]);
+  }
+  Slot S;
+  for (int i = 0; i < C_COUNT; i++) S.c[i] = &sh.c[i];
+  S.flow = &sh.flow;
+  S.act[0] = &sh.act[0];
+  S.act[1] = &sh.act[1];
+  const unsigned long long t0 = globaltimer();
   for (;;) {
-    if (threadIdx.x == 0) clear_slot(E, (L.phase + 1) % 3, false);
-    __syncthreads();
-    run_phase(N, E, L, T, lane, a, w_sh);
-    __syncthreads();
-    __threadfence_block();
     if (threadIdx.x == 0) {
-      flush_weight(E, L.phase, w_sh);
-      const Snap q = take_snap(E, L.phase);
-      tick(ck, ST_TAIL);
-      advance(L, q, P, N, &E->c, true);
-      L.phase++;
-      if (L.state == ST_TAIL) L.state = ST_ROUND_A;
-      if (L.state == ST_ROUND_A && L.fcnt + L.fcnth > P.tail_exit) L.state = ST_ROUND_A + 100;
+      for (int i = 0; i < C_COUNT; i++) sh.c[i] = 0;
+      sh.flow = 0;
     }
     __syncthreads();
-    const int st = L.state;
-    if (st != ST_ROUND_A && st != ST_ROUND_B) break;
+    run_phase_s(N, E, L, T, S, lane, a, w_sh);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      Snap q;
+      for (int i = 0; i < C_COUNT; i++) q.c[i] = sh.c[i];
+      q.act = sh.act[0];
+      q.acth = sh.act[1];
+      q.flow = sh.flow;
+      q.w = *w_sh;
+      *w_sh = 0;
+      q.key = 0;
+      q.node = -1;
+      tick(ck, ST_TAIL);
+      const int s1 = L.state;
+      advance(L, q, P, N, &E->c, true);
+      L.phase++;
+      const int s2 = L.state;
+      bool stay;
+      if (is_level(s1) && !is_level(s2)) {
+        // a search ended: labels claimed by atomics must reach the plain
+        // loads of the next phases, which the grid barrier's acquire does
+        stay = false;
+      } else if (s2 == ST_TAIL) {
+        L.state = ST_ROUND_A;
+        stay = true;
+      } else if (s2 == ST_ROUND_B) {
+        stay = true;
+      } else if (s2 == ST_ROUND_A) {
+        stay = L.fcnt + L.fcnth <= P.tail_exit;
+      } else if (is_level(s2)) {
+        stay = level_size(L) <= P.bfs_exit;
+      } else {
+        stay = false;
+      }
+      if (stay && (ld_volatile_int(&E->c.err) != kDevOk || globaltimer() - t0 > P.timeout_ns)) {
+        // bounded like a grid barrier wait: give up with an error status
+        atomicCAS(&E->c.err, kDevOk, kDevTimeout);
+        E->c.err_where = 2;
+        L.state = ST_DONE;
+        stay = false;
+      }
+      sh.stay = stay ? 1 : 0;
+    }
+    __syncthreads();
+    if (!sh.stay) break;
   }
-  __syncthreads();   // every thread has left the loop before the state is rewritten
-  if (threadIdx.x == 0 && L.state == ST_ROUND_A + 100) L.state = ST_ROUND_A;
+  __syncthreads();   // every thread has read sh.stay
+  if (threadIdx.x == 0) {
+    E->gr_act[0] = sh.act[0];
+    E->gr_act[1] = sh.act[1];
+    for (unsigned sl = 0; sl < 3; sl++) clear_slot(E, sl, false);
+    __threadfence();
+  }
   __syncthreads();
 }
 
@@ -1134,6 +1243,7 @@ __device__ void load_sched(Sched& L, const EngineCtl* E) {
   L.epoch = v->epoch;
   L.after_gr_exit = v->after_gr_exit;
   L.phase = v->phase;
+  L.sr_seed = v->sr_seed;
   L.rounds = v->rounds;
   L.grs = v->grs;
   L.gr_levels = v->gr_levels;
@@ -1164,6 +1274,7 @@ __device__ void store_sched(EngineCtl* E, const Sched& L) {
   v->epoch = L.epoch;
   v->after_gr_exit = L.after_gr_exit;
   v->phase = L.phase;
+  v->sr_seed = L.sr_seed;
   v->rounds = L.rounds;
   v->grs = L.grs;
   v->gr_levels = L.gr_levels;
@@ -1182,6 +1293,7 @@ __global__ void __launch_bounds__(kEngineThreads) engine_kernel(NetDev N, Engine
   __shared__ Acc acc_sh;
   __shared__ long long w_sh;
   __shared__ Clock ck;
+  __shared__ SoloSh solo;
   const unsigned lane = lane_id();
   const unsigned wib = threadIdx.x >> 5, nwb = blockDim.x >> 5;
   const Team G{blockIdx.x * nwb + wib, gridDim.x * nwb, blockIdx.x * blockDim.x + threadIdx.x,
@@ -1201,9 +1313,9 @@ __global__ void __launch_bounds__(kEngineThreads) engine_kernel(NetDev N, Engine
   for (;;) {
     const int st = L.state;
     if (st == ST_DONE) break;
-    if (st == ST_TAIL) {
+    if (solo_next(L, P)) {
       if (cta0) {
-        tail_rounds(N, E, P, L, lane, a, &w_sh, ck);
+        solo_phases(N, E, P, L, lane, a, &w_sh, ck, solo);
         if (threadIdx.x == 0) store_sched(E, L);
       }
       const bool ok = grid_barrier(E, gridDim.x * ++bar_seq, P.timeout_ns);

@@ -24,6 +24,7 @@ enum EngineState : int {
   ST_FC_FIND = 12,    // the candidate holding that key
   ST_FC_MARK_S = 13,  // S <- S_r + pierced node
   ST_FC_MARK_T = 14,  // T <- T_r + pierced node, their excess joins the flow
+  ST_SR_ADD = 15,   // source-side cut grown from one new source (S_r kept)
 };
 
 // list ids in NetDev::list.  Each list array holds light nodes from the front
@@ -47,7 +48,7 @@ struct Sched {
   unsigned int epoch;     // stamp epoch of this round / BFS
   int after_gr_exit;      // exit after the running global relabel
   unsigned int phase;     // phase index (selects the counter slots)
-  int pad;
+  int sr_seed;            // ST_SR_ADD: the new source whose reach joins S_r
   unsigned long long rounds, grs, gr_levels, work, stall, flow, flow_ref;
   long long wS, wT;
   int wS_set, wT_set;
@@ -61,7 +62,8 @@ struct Params {
   unsigned int stall_nodes;          // ... each with fewer active nodes
   unsigned int tail_enter;           // frontier size at or below which CTA 0 runs alone
   unsigned int tail_exit;            // frontier size above which the grid takes over
-  unsigned int pad;
+  unsigned int bfs_enter;            // BFS level size at or below which CTA 0 runs alone
+  unsigned int bfs_exit;             // BFS level size above which the grid takes over
 };
 
 struct EngineCtl {

@@ -42,6 +42,11 @@ __device__ __forceinline__ unsigned long long batch_pierce_key(const NetDev& N, 
          ((unsigned long long)(sd + (1 << 20)) << 32) | (unsigned long long)(0xffffffffu - hh);
 }
 
+__device__ __forceinline__ bool is_fc_state(int st) {
+  return st == ST_FC_SAT || st == ST_FC_SEL || st == ST_FC_FIND || st == ST_FC_MARK_S ||
+         st == ST_FC_MARK_T;
+}
+
 // FlowCutter control of one job, replicated in every CTA of the group.
 enum FcStage : int { FC_FLOW = 0, FC_SR = 1, FC_DIST = 2 };
 struct FcState {
@@ -55,6 +60,9 @@ struct FcState {
   int status;         // outcome once the job is finished
   int result_side;
   int finished;
+  int nopath;         // the chosen piercing node has no augmenting path
+  int pending;        // unsaturated source left by a lazy piercing (-1: none)
+  int sat_gr;         // ST_FC_SAT saturates the pending source before a relabel
   unsigned long long best;
   long long source_weight;
 };
@@ -246,9 +254,11 @@ __device__ void fc_advance(Sched& L, FcState& F, const Snap& q, const FcJob& J, 
     case ST_FC_SAT:
       L.flow += q.flow;
       F.stage = FC_FLOW;
-      if (F.initial) {
-        // first flow: the labels are built by a global relabel (SETUP_GR)
+      if (F.initial || F.sat_gr) {
+        // first flow, or a sink piercing after a lazy one: the labels are
+        // built by a global relabel (SETUP_GR)
         F.initial = 0;
+        F.sat_gr = 0;
         begin_gr(L);
         L.after_gr_exit = 0;
       } else {
@@ -273,6 +283,7 @@ __device__ void fc_advance(Sched& L, FcState& F, const Snap& q, const FcJob& J, 
       break;
     case ST_FC_FIND:
       F.node = q.node;
+      F.nopath = (int)((F.best >> 53) & 1ull);
       if (recorder && F.np < J.pierce_cap) {
         if (J.pierce_node) J.pierce_node[F.np] = q.node;
         if (J.pierce_side) J.pierce_side[F.np] = (int8_t)(F.grow_s ? 0 : 1);
@@ -281,15 +292,36 @@ __device__ void fc_advance(Sched& L, FcState& F, const Snap& q, const FcJob& J, 
       L.state = F.grow_s ? ST_FC_MARK_S : ST_FC_MARK_T;
       break;
     case ST_FC_MARK_S:
-      L.epoch++;           // SETUP_PREP: fresh stamps for the saturation's frontier
-      L.state = ST_FC_SAT;
+      L.epoch++;           // SETUP_PREP / SETUP_SR_ADD: fresh stamps
+      if (F.nopath) {
+        // lazy piercing (hfp_flowcutter's rule): the preflow stays maximum,
+        // S_r grows by the node's reach, its arcs wait for a sink piercing
+        F.pending = F.node;
+        F.stage = FC_SR;
+        F.it++;
+        L.state = ST_SR_ADD;
+        L.sr_seed = F.node;
+        L.wS_set = 1;
+      } else {
+        F.pending = -1;
+        L.state = ST_FC_SAT;
+      }
       break;
     case ST_FC_MARK_T:
       L.flow += q.flow;    // excess absorbed by the new sinks
       F.stage = FC_FLOW;
-      begin_gr(L);         // SETUP_GR: labels are no longer lower bounds
-      L.after_gr_exit = 0;
       F.it++;
+      if (F.pending >= 0) {
+        // the unsaturated source may now reach T: saturate it first
+        F.node = F.pending;
+        F.pending = -1;
+        F.sat_gr = 1;
+        L.epoch++;
+        L.state = ST_FC_SAT;
+      } else {
+        begin_gr(L);       // SETUP_GR: labels are no longer lower bounds
+        L.after_gr_exit = 0;
+      }
       break;
     default:
       L.state = ST_DONE;
@@ -348,7 +380,7 @@ __device__ void run_phase_batch(const NetDev& N, EngineCtl* E, const Sched& L, c
 // One job by one group of G CTAs (rank = position in the group).
 __device__ void fc_run_job(FcJob* job, const Params& P0, int rank, int G, unsigned lane,
                            Sched& L, FcState& F, NetDev& N, Params& P, long long* w_sh,
-                           Clock& ck) {
+                           Clock& ck, SoloSh& solo) {
   const unsigned wib = threadIdx.x >> 5, nwb = blockDim.x >> 5;
   const Team T{rank * nwb + wib, G * nwb, rank * blockDim.x + threadIdx.x, G * blockDim.x,
                (unsigned)rank, (unsigned)G};
@@ -359,7 +391,7 @@ __device__ void fc_run_job(FcJob* job, const Params& P0, int rank, int G, unsign
     P.gr_work = job->gr_work;
     load_sched(L, E);
     L.flow = *(const volatile unsigned long long*)&E->c.flow;
-    F = FcState{FC_FLOW, 0, 1, 0, 0, 1, job->dist_ready, 0, 0, 0, 0ull, 0ll};
+    F = FcState{FC_FLOW, 0, 1, 0, 0, 1, job->dist_ready, 0, 0, 0, 0, -1, 0, 0ull, 0ll};
     // SETUP_PREP, then the saturation of s opens the first flow
     L.epoch++;
     L.state = ST_FC_SAT;
@@ -372,9 +404,9 @@ __device__ void fc_run_job(FcJob* job, const Params& P0, int rank, int G, unsign
   for (;;) {
     const int st = L.state;
     if (st == ST_DONE) break;
-    if (st == ST_TAIL) {
+    if (solo_next(L, P)) {
       if (lead) {
-        tail_rounds(N, E, P, L, lane, a, w_sh, ck);
+        solo_phases(N, E, P, L, lane, a, w_sh, ck, solo);
         if (threadIdx.x == 0) store_sched(E, L);
       }
       const bool ok = grid_barrier(E, G * ++bar_seq, P.timeout_ns);
@@ -397,7 +429,7 @@ __device__ void fc_run_job(FcJob* job, const Params& P0, int rank, int G, unsign
         fc_on_done(L, F, *job, &E->c);
       } else {
         const Snap q = take_snap(E, L.phase);
-        if (st >= ST_FC_SAT) fc_advance(L, F, q, *job, lead);
+        if (is_fc_state(st)) fc_advance(L, F, q, *job, lead);
         else advance(L, q, P, N, &E->c, lead);
         L.phase++;
         if (L.state == ST_DONE && !F.finished) fc_on_done(L, F, *job, &E->c);
@@ -437,6 +469,7 @@ __global__ void __launch_bounds__(kEngineThreads) fc_batch_kernel(FcJob* jobs, i
   __shared__ Params P;
   __shared__ long long w_sh;
   __shared__ Clock ck;
+  __shared__ SoloSh solo;
   __shared__ unsigned job_sh;
   const int gid = blockIdx.x / G, rank = blockIdx.x % G;
   const unsigned lane = lane_id();
@@ -449,7 +482,7 @@ __global__ void __launch_bounds__(kEngineThreads) fc_batch_kernel(FcJob* jobs, i
     __syncthreads();
     const unsigned j = job_sh;
     if (j >= (unsigned)n_jobs) break;
-    fc_run_job(&jobs[j], P0, rank, G, lane, L, F, N, P, &w_sh, ck);
+    fc_run_job(&jobs[j], P0, rank, G, lane, L, F, N, P, &w_sh, ck, solo);
     if (!group_sync(B, gid, G * ++gseq, P0.timeout_ns)) break;
   }
 }

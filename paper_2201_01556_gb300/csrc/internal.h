@@ -76,6 +76,11 @@ struct hfp_net {
   bool labels_exact = false;
   bool sr_valid = false;
   bool dist_ready = false;
+  // a source pierced without augmenting path whose arcs were left unsaturated
+  // (saturated before the next sink-side piercing), and the seed of the next
+  // incremental source-side search (-1: a full search is needed)
+  int32_t pending_source = -1;
+  int32_t sr_seed = -1;
   void* trace_buf = nullptr;
   uint64_t launches = 0;
   uint64_t engine_ns = 0;

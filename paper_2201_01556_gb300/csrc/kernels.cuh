@@ -44,15 +44,15 @@ void launch_st_attrs(int32_t* node_gid, int32_t* node_w, int8_t* node_orig,
                      const unsigned long long* wsum, uint8_t* flags, int* err, cudaStream_t st);
 
 // engine.cu
-constexpr int kEngineThreads = 512;
+constexpr int kEngineThreads = 512;   // block scans assume < 32 warps
 __global__ void __launch_bounds__(kEngineThreads) engine_kernel(NetDev N, EngineCtl* E, Params P);
 __global__ void __launch_bounds__(kEngineThreads) fc_batch_kernel(FcJob* jobs, int n_jobs,
                                                                   BatchCtl* B, int G, Params P0);
 
 // cuts.cu
 enum SetupMode : int { SETUP_GR = 0, SETUP_ROUND = 1, SETUP_SR = 2, SETUP_PREP = 3, SETUP_DIST = 4,
-                       SETUP_BATCH = 5 };
-void launch_engine_setup(EngineCtl* E, int mode, cudaStream_t st);
+                       SETUP_BATCH = 5, SETUP_SR_ADD = 6 };
+void launch_engine_setup(EngineCtl* E, int mode, cudaStream_t st, int32_t arg = 0);
 void launch_saturate(const NetDev& N, EngineCtl* E, const int32_t* nodes, int32_t count,
                      cudaStream_t st);
 void launch_mark_sources(const NetDev& N, const int32_t* extra, int32_t count, int sms,

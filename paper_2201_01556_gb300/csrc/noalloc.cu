@@ -243,6 +243,8 @@ extern "C" __attribute__((visibility("default"))) hfp_status hfp_max_flow_noallo
   P.stall_nodes = 1500;
   P.tail_enter = 64;
   P.tail_exit = 192;
+  P.bfs_enter = 0;
+  P.bfs_exit = 0;
   void* args[] = {(void*)&D, (void*)&E, (void*)&P};
 
   // maximum preflow from {s} to {t}: saturate s, global relabel, rounds

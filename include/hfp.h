@@ -141,7 +141,14 @@ uint64_t hfp_kernel_launches(void);
  *   bfs_enter, bfs_exit  breadth-first-search levels (global relabel, S_r,
  *                 distances) of at most bfs_enter nodes (a heavy node counts
  *                 32) are run by one CTA until they exceed bfs_exit
- *                 [0, 0]: off; 0 still runs empty levels alone */
+ *                 [0, 0]: off; 0 still runs empty levels alone
+ *   pierce_relabel  after a source-side piercing that creates an augmenting
+ *                 path, start the flow with a global relabel instead of
+ *                 rounds on the new excess (Section 8.4 skips it) [0]
+ *   stall_rounds_pierce  the stall_rounds rule for the incremental flows
+ *                 after a piercing; 0: adaptive, as many rounds as the last
+ *                 global relabel had levels (at least 8, at most
+ *                 stall_rounds) [0] */
 typedef struct {
   uint32_t gr_work_x100;
   uint32_t stall_rounds;
@@ -151,6 +158,8 @@ typedef struct {
   uint32_t max_rounds;
   uint32_t bfs_enter;
   uint32_t bfs_exit;
+  uint32_t pierce_relabel;
+  uint32_t stall_rounds_pierce;
 } hfp_tuning;
 hfp_status hfp_ctx_get_tuning(hfp_ctx* ctx, hfp_tuning* tuning);
 hfp_status hfp_ctx_set_tuning(hfp_ctx* ctx, const hfp_tuning* tuning);

@@ -69,7 +69,13 @@ hfp_status read_ctl(hfp_net* net, Ctl* out) {
 
 hfp_status run_engine(hfp_net* net) {
   hfp_ctx* c = net->ctx;
-  void* args[] = {(void*)&net->d, (void*)&net->E, (void*)&c->params};
+  Params P = c->params;
+  // flows after a piercing are incremental: their own stall rule
+  if (net->pierced) {
+    if (P.stall_rounds_pierce) P.stall_rounds = P.stall_rounds_pierce;
+    else P.stall_adapt = 1;
+  }
+  void* args[] = {(void*)&net->d, (void*)&net->E, (void*)&P};
   CK(cudaEventRecord(c->ev0, c->stream));
   CK(cudaLaunchCooperativeKernel((void*)engine_kernel, dim3(c->coop_grid), dim3(c->threads),
                                  args, 0, c->stream));
@@ -201,6 +207,9 @@ HFP_API hfp_status hfp_ctx_create(hfp_ctx** out, int device, void* stream) {
   c->params.tail_exit = 192;
   c->params.bfs_enter = 0;         // CTA 0 alone for BFS levels up to this size: off (the
   c->params.bfs_exit = 0;          // relabel BFS levels are wide; measured slower alone)
+  c->params.pierce_relabel = 0;
+  c->params.stall_rounds_pierce = 0;    // incremental flows after a piercing: adaptive
+  c->params.stall_adapt = 0;
   *out = c;
   return HFP_OK;
 }
@@ -637,6 +646,8 @@ HFP_API hfp_status hfp_ctx_get_tuning(hfp_ctx* ctx, hfp_tuning* t) {
   t->max_rounds = (uint32_t)ctx->params.max_rounds;
   t->bfs_enter = ctx->params.bfs_enter;
   t->bfs_exit = ctx->params.bfs_exit;
+  t->pierce_relabel = ctx->params.pierce_relabel;
+  t->stall_rounds_pierce = (uint32_t)ctx->params.stall_rounds_pierce;
   return HFP_OK;
 }
 
@@ -653,6 +664,8 @@ HFP_API hfp_status hfp_ctx_set_tuning(hfp_ctx* ctx, const hfp_tuning* t) {
   ctx->params.max_rounds = t->max_rounds;
   ctx->params.bfs_enter = t->bfs_enter;
   ctx->params.bfs_exit = t->bfs_exit;
+  ctx->params.pierce_relabel = t->pierce_relabel ? 1 : 0;
+  ctx->params.stall_rounds_pierce = t->stall_rounds_pierce;
   return HFP_OK;
 }
 
@@ -765,17 +778,22 @@ hfp_status select_pierce(hfp_net* net, int grow_s, const hfp_fc_params* prm, int
   return HFP_OK;
 }
 
-// Piercing (Algorithm 2, the S or T update).  With `lazy` (one source-side
-// node that has no augmenting path: not in T_r) the flow is left alone: the
-// current preflow stays a maximum preflow for the grown S, T_r and the flow
-// value do not change, and S_r only grows by what the node reaches, so only
-// the node is marked and the next source-side search starts from it.  Its
-// arcs stay unsaturated until a sink-side piercing could open a path through
-// them; a later source-side piercing makes all it reaches sources anyway.
+// Piercing (Algorithm 2, the S or T update).  With `lazy` (one node that
+// has no augmenting path) the flow is left alone: the current preflow stays
+// a maximum preflow and the flow value does not change.
+//  - Source side (node not in T_r): T_r stays and S_r only grows by what the
+//    node reaches, so only the node is marked and the next source-side search
+//    starts from it.  Its arcs stay unsaturated until a sink-side piercing
+//    could open a path through them; a later source-side piercing makes all it
+//    reaches sources anyway.
+//  - Sink side (node not in S_r): S_r stays and T_r grows by the nodes that
+//    reach it, found by a reverse search from it alone; the labels are then no
+//    longer exact distances, so the next flow computation first relabels.
 hfp_status pierce(hfp_net* net, int side, const int32_t* nodes, int32_t count,
                   bool lazy = false) {
   hfp_status s = stage_nodes(net, nodes, count);
   if (s != HFP_OK) return s;
+  net->pierced = true;
   cudaStream_t st = net->ctx->stream;
   if (side == 0) {
     // S <- S_r + nodes; labels stay valid, the new excess is the frontier
@@ -789,10 +807,21 @@ hfp_status pierce(hfp_net* net, int side, const int32_t* nodes, int32_t count,
     net->pending_source = -1;
     launch_engine_setup(net->E, SETUP_PREP, st);
     launch_saturate(net->d, net->E, net->dev_nodes, count, st);
-    launch_engine_setup(net->E, SETUP_ROUND, st);
+    launch_engine_setup(net->E,
+                        net->gr_pending || net->ctx->params.pierce_relabel ? SETUP_GR
+                                                                           : SETUP_ROUND,
+                        st);
   } else {
     // T <- T_r + nodes; labels are no longer lower bounds: relabel globally
     launch_mark_sinks(net->d, net->E, net->dev_nodes, count, net->ctx->sms, st);
+    if (lazy && count == 1) {
+      launch_engine_setup(net->E, SETUP_GR_ADD, st, nodes[0]);
+      net->labels_exact = false;
+      if ((s = run_engine(net)) != HFP_OK) return s;
+      net->labels_exact = true;
+      net->gr_pending = true;
+      return HFP_OK;
+    }
     if (net->pending_source >= 0) {
       // the unsaturated source may now reach T: saturate it before the flow
       const int32_t u = net->pending_source;
@@ -806,6 +835,7 @@ hfp_status pierce(hfp_net* net, int side, const int32_t* nodes, int32_t count,
   net->labels_exact = false;
   net->sr_valid = false;
   net->sr_seed = -1;
+  net->gr_pending = false;
   if ((s = run_engine(net)) != HFP_OK) return s;
   net->labels_exact = true;
   return HFP_OK;
@@ -902,7 +932,7 @@ HFP_API hfp_status hfp_flowcutter(hfp_net* net, const hfp_fc_params* prm, uint8_
     if (pierce_side && np < pierce_cap) pierce_side[np] = grow_s ? 0 : 1;
     if (pierce_node && np < pierce_cap) pierce_node[np] = p;
     np++;
-    if ((s = pierce(net, grow_s ? 0 : 1, &p, 1, grow_s && no_path)) != HFP_OK) return s;
+    if ((s = pierce(net, grow_s ? 0 : 1, &p, 1, no_path)) != HFP_OK) return s;
     it++;
   }
   r.iterations = it;

@@ -68,12 +68,20 @@ __global__ void k_engine_setup(EngineCtl* E, int mode, int32_t arg) {
     case SETUP_BATCH:
       zero_phase_counters(X);
       break;
+    case SETUP_GR_ADD:
+      // T_r grows by the nodes reaching one new sink; wT is kept
+      zero_phase_counters(X);
+      X.s.state = ST_GR_ADD;
+      X.s.seed = arg;
+      X.s.after_gr_exit = 0;
+      X.s.wT_set = 1;
+      break;
     case SETUP_SR_ADD:
       // S_r grows by the reach of one new source; wS is kept
       zero_phase_counters(X);
       X.s.state = ST_SR_ADD;
       X.s.epoch++;
-      X.s.sr_seed = arg;
+      X.s.seed = arg;
       X.s.wS_set = 1;
       break;
   }

@@ -160,6 +160,16 @@ struct Snap {
   int node;
 };
 
+// Rounds without flow change before a global relabel (Section 8.3, "Avoid
+// Pushing Flow Back").  In adaptive mode (incremental flows after a
+// piercing) the limit follows the cost of a relabel: as many rounds as the
+// last one had levels, at least 8, at most stall_rounds.
+__device__ __forceinline__ unsigned long long stall_limit(const Sched& L, const Params& P) {
+  if (!P.stall_adapt) return P.stall_rounds;
+  unsigned long long s = L.last_gr < 8u ? 8u : L.last_gr;
+  return s < P.stall_rounds ? s : P.stall_rounds;
+}
+
 __device__ void begin_gr(Sched& L) {
   L.grs++;
   L.state = ST_GR_INIT;
@@ -203,7 +213,7 @@ __device__ void advance(Sched& L, const Snap& q, const Params& P, const NetDev& 
       } else if (L.rounds >= P.max_rounds) {
         atomicCAS(&c->err, kDevOk, kDevIterLimit);
         L.state = ST_DONE;
-      } else if (L.work >= P.gr_work || L.stall >= P.stall_rounds) {
+      } else if (L.work >= P.gr_work || L.stall >= stall_limit(L, P)) {
         begin_gr(L);
       } else {
         L.state = f <= P.tail_enter ? ST_TAIL : ST_ROUND_A;
@@ -211,6 +221,7 @@ __device__ void advance(Sched& L, const Snap& q, const Params& P, const NetDev& 
       break;
     }
     case ST_GR_INIT:
+    case ST_GR_ADD:
     case ST_SR_INIT:
     case ST_SR_ADD:
     case ST_DIST_INIT:
@@ -219,9 +230,9 @@ __device__ void advance(Sched& L, const Snap& q, const Params& P, const NetDev& 
       L.bfsh_begin = 0;
       L.bfsh_end = q.c[C_BFSH];
       L.level = 0;
-      if (L.state == ST_GR_INIT) L.wT += q.w;
+      if (L.state == ST_GR_INIT || L.state == ST_GR_ADD) L.wT += q.w;
       if (L.state == ST_SR_INIT || L.state == ST_SR_ADD) L.wS += q.w;
-      L.state = L.state == ST_GR_INIT ? ST_GR_LEVEL
+      L.state = (L.state == ST_GR_INIT || L.state == ST_GR_ADD) ? ST_GR_LEVEL
                 : L.state == ST_DIST_INIT ? ST_DIST_LEVEL : ST_SR_LEVEL;
       break;
     case ST_GR_LEVEL:
@@ -235,6 +246,7 @@ __device__ void advance(Sched& L, const Snap& q, const Params& P, const NetDev& 
       if (st == ST_SR_LEVEL) L.wS += q.w;
       if (q.c[C_BFS] == 0 && q.c[C_BFSH] == 0) {
         if (st == ST_GR_LEVEL) {
+          L.last_gr = (unsigned)L.level + 1;
           L.fcnt = q.act;
           L.fcnth = q.acth;
           L.rcnt = 0;
@@ -802,6 +814,26 @@ __device__ void gr_init(const NetDev& N, const Team& T, const Slot& S, unsigned 
   }
 }
 
+// Sink-side cut after adding one sink u that no excess can reach (a piercing
+// node outside S_r): the flow and S_r stay, T_r grows by the nodes that reach
+// u, found by a reverse search seeded at u alone that only claims unlabelled
+// nodes.  The labels of the old T_r are then no longer exact distances; the
+// next flow computation starts with a full global relabel.
+__device__ void gr_add(const NetDev& N, const Sched& L, const Team& T, const Slot& S,
+                       unsigned lane, Acc& a) {
+  if (T.tid >= 32) return;
+  const int u = L.seed;
+  bool seed = false, hv = false;
+  if (lane == 0 && u >= 0) {
+    N.lab0[u] = 0;
+    N.lab1[u] = 0;
+    hv = (N.flags[u] & kHeavy) != 0;
+    if (u < N.n_nodes) a.w += N.node_w[u];
+    seed = true;
+  }
+  append_split(seed, u, hv, N.list[L_BFS], S.c[C_BFS], S.c[C_BFSH], 0, 0, N.NL);
+}
+
 __device__ __forceinline__ bool gr_claim(const NetDev& N, int x, int d1, bool& act, bool& hv,
                                          Acc& a) {
   act = false;
@@ -931,7 +963,7 @@ __device__ void sr_init(const NetDev& N, const Sched& L, const Team& T, const Sl
 __device__ void sr_add(const NetDev& N, const Sched& L, const Team& T, const Slot& S,
                        unsigned lane, Acc& a) {
   if (T.tid >= 32) return;
-  const int u = L.sr_seed;
+  const int u = L.seed;
   bool seed = false, hv = false;
   if (lane == 0 && u >= 0 && !N.insr[u]) {
     N.insr[u] = 1;
@@ -1083,6 +1115,7 @@ __device__ void run_phase_s(const NetDev& N, EngineCtl* E, const Sched& L, const
     case ST_ROUND_A: phase_a(N, L, T, S, lane, a, E); break;
     case ST_ROUND_B: phase_b(N, L, T, S, lane, a); break;
     case ST_GR_INIT: gr_init(N, T, S, lane, a); break;
+    case ST_GR_ADD: gr_add(N, L, T, S, lane, a); break;
     case ST_GR_LEVEL: gr_level(N, E, L, T, S, lane, a); break;
     case ST_SR_INIT: sr_init(N, L, T, S, lane, a); break;
     case ST_SR_ADD: sr_add(N, L, T, S, lane, a); break;
@@ -1243,7 +1276,8 @@ __device__ void load_sched(Sched& L, const EngineCtl* E) {
   L.epoch = v->epoch;
   L.after_gr_exit = v->after_gr_exit;
   L.phase = v->phase;
-  L.sr_seed = v->sr_seed;
+  L.seed = v->seed;
+  L.last_gr = v->last_gr;
   L.rounds = v->rounds;
   L.grs = v->grs;
   L.gr_levels = v->gr_levels;
@@ -1274,7 +1308,8 @@ __device__ void store_sched(EngineCtl* E, const Sched& L) {
   v->epoch = L.epoch;
   v->after_gr_exit = L.after_gr_exit;
   v->phase = L.phase;
-  v->sr_seed = L.sr_seed;
+  v->seed = L.seed;
+  v->last_gr = L.last_gr;
   v->rounds = L.rounds;
   v->grs = L.grs;
   v->gr_levels = L.gr_levels;
@@ -1326,7 +1361,8 @@ __global__ void __launch_bounds__(kEngineThreads) engine_kernel(NetDev N, Engine
       __syncthreads();
       continue;
     }
-    if (cta0 && threadIdx.x == 0) clear_slot(E, (L.phase + 1) % 3, st == ST_GR_INIT);
+    if (cta0 && threadIdx.x == 0)
+      clear_slot(E, (L.phase + 1) % 3, st == ST_GR_INIT || st == ST_GR_ADD);
     run_phase(N, E, L, G, lane, a, &w_sh);
     __syncthreads();
     if (threadIdx.x == 0) flush_weight(E, L.phase, &w_sh);

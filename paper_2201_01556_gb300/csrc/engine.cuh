@@ -25,6 +25,7 @@ enum EngineState : int {
   ST_FC_MARK_S = 13,  // S <- S_r + pierced node
   ST_FC_MARK_T = 14,  // T <- T_r + pierced node, their excess joins the flow
   ST_SR_ADD = 15,   // source-side cut grown from one new source (S_r kept)
+  ST_GR_ADD = 16,   // sink-side cut grown from one new sink (T_r and its labels kept)
 };
 
 // list ids in NetDev::list.  Each list array holds light nodes from the front
@@ -48,7 +49,8 @@ struct Sched {
   unsigned int epoch;     // stamp epoch of this round / BFS
   int after_gr_exit;      // exit after the running global relabel
   unsigned int phase;     // phase index (selects the counter slots)
-  int sr_seed;            // ST_SR_ADD: the new source whose reach joins S_r
+  int seed;               // ST_SR_ADD / ST_GR_ADD: the node whose reach joins S_r / T_r
+  unsigned int last_gr;   // levels of the last global relabel
   unsigned long long rounds, grs, gr_levels, work, stall, flow, flow_ref;
   long long wS, wT;
   int wS_set, wT_set;
@@ -64,6 +66,10 @@ struct Params {
   unsigned int tail_exit;            // frontier size above which the grid takes over
   unsigned int bfs_enter;            // BFS level size at or below which CTA 0 runs alone
   unsigned int bfs_exit;             // BFS level size above which the grid takes over
+  unsigned int pierce_relabel;       // source piercing: start the flow with a global relabel
+  unsigned int stall_rounds_pierce;  // stall_rounds of the flows after a piercing (0: adaptive)
+  unsigned int stall_adapt;          // stall limit = levels of the last global relabel
+  unsigned int pad;
 };
 
 struct EngineCtl {

@@ -42,13 +42,19 @@ __device__ __forceinline__ unsigned long long batch_pierce_key(const NetDev& N, 
          ((unsigned long long)(sd + (1 << 20)) << 32) | (unsigned long long)(0xffffffffu - hh);
 }
 
+// The stall rule of the incremental flows after a piercing.
+__device__ __forceinline__ void incremental_stall(Params& P) {
+  if (P.stall_rounds_pierce) P.stall_rounds = P.stall_rounds_pierce;
+  else P.stall_adapt = 1;
+}
+
 __device__ __forceinline__ bool is_fc_state(int st) {
   return st == ST_FC_SAT || st == ST_FC_SEL || st == ST_FC_FIND || st == ST_FC_MARK_S ||
          st == ST_FC_MARK_T;
 }
 
 // FlowCutter control of one job, replicated in every CTA of the group.
-enum FcStage : int { FC_FLOW = 0, FC_SR = 1, FC_DIST = 2 };
+enum FcStage : int { FC_FLOW = 0, FC_SR = 1, FC_DIST = 2, FC_TADD = 3 };
 struct FcState {
   int stage;          // what the engine is computing when it reaches ST_DONE
   int grow_s;
@@ -63,6 +69,7 @@ struct FcState {
   int nopath;         // the chosen piercing node has no augmenting path
   int pending;        // unsaturated source left by a lazy piercing (-1: none)
   int sat_gr;         // ST_FC_SAT saturates the pending source before a relabel
+  int gr_pending;     // labels not exact since a lazy sink piercing
   unsigned long long best;
   long long source_weight;
 };
@@ -210,7 +217,7 @@ __device__ void fc_on_done(Sched& L, FcState& F, const FcJob& J, const Ctl* c) {
       L.state = ST_FC_SEL;
       return;
     default:
-      break;
+      break;   // FC_SR, FC_TADD: S_r and T_r are current
   }
   // FC_SR: S_r and T_r of the current flow are known (Algorithm 2, lines 3-6)
   const long long W = J.total_w, Lm = J.max_w;
@@ -249,11 +256,13 @@ __device__ void fc_on_done(Sched& L, FcState& F, const FcJob& J, const Ctl* c) {
 }
 
 // After a FlowCutter phase and its barrier.
-__device__ void fc_advance(Sched& L, FcState& F, const Snap& q, const FcJob& J, bool recorder) {
+__device__ void fc_advance(Sched& L, FcState& F, const Snap& q, const FcJob& J, Params& P,
+                           bool recorder) {
   switch (L.state) {
     case ST_FC_SAT:
       L.flow += q.flow;
       F.stage = FC_FLOW;
+      if (!F.initial) incremental_stall(P);
       if (F.initial || F.sat_gr) {
         // first flow, or a sink piercing after a lazy one: the labels are
         // built by a global relabel (SETUP_GR)
@@ -261,6 +270,13 @@ __device__ void fc_advance(Sched& L, FcState& F, const Snap& q, const FcJob& J, 
         F.sat_gr = 0;
         begin_gr(L);
         L.after_gr_exit = 0;
+      } else if (F.gr_pending || P.pierce_relabel) {
+        // labels are stale after a lazy sink piercing, or the tuning asks for
+        // exact labels before the rounds: relabel first
+        F.gr_pending = 0;
+        begin_gr(L);
+        L.after_gr_exit = 0;
+        F.it++;
       } else {
         // the new excess is the frontier; labels stay valid (SETUP_ROUND)
         L.epoch++;
@@ -300,7 +316,7 @@ __device__ void fc_advance(Sched& L, FcState& F, const Snap& q, const FcJob& J, 
         F.stage = FC_SR;
         F.it++;
         L.state = ST_SR_ADD;
-        L.sr_seed = F.node;
+        L.seed = F.node;
         L.wS_set = 1;
       } else {
         F.pending = -1;
@@ -311,6 +327,19 @@ __device__ void fc_advance(Sched& L, FcState& F, const Snap& q, const FcJob& J, 
       L.flow += q.flow;    // excess absorbed by the new sinks
       F.stage = FC_FLOW;
       F.it++;
+      incremental_stall(P);   // the flows from here on are incremental
+      if (F.nopath) {
+        // lazy piercing: the flow and S_r stay, T_r grows by a reverse search
+        // from the node; the next flow computation relabels first
+        F.stage = FC_TADD;
+        F.gr_pending = 1;
+        L.state = ST_GR_ADD;
+        L.seed = F.node;
+        L.after_gr_exit = 0;
+        L.wT_set = 1;
+        break;
+      }
+      F.gr_pending = 0;
       if (F.pending >= 0) {
         // the unsaturated source may now reach T: saturate it first
         F.node = F.pending;
@@ -391,7 +420,7 @@ __device__ void fc_run_job(FcJob* job, const Params& P0, int rank, int G, unsign
     P.gr_work = job->gr_work;
     load_sched(L, E);
     L.flow = *(const volatile unsigned long long*)&E->c.flow;
-    F = FcState{FC_FLOW, 0, 1, 0, 0, 1, job->dist_ready, 0, 0, 0, 0, -1, 0, 0ull, 0ll};
+    F = FcState{FC_FLOW, 0, 1, 0, 0, 1, job->dist_ready, 0, 0, 0, 0, -1, 0, 0, 0ull, 0ll};
     // SETUP_PREP, then the saturation of s opens the first flow
     L.epoch++;
     L.state = ST_FC_SAT;
@@ -418,7 +447,8 @@ __device__ void fc_run_job(FcJob* job, const Params& P0, int rank, int G, unsign
       __syncthreads();
       continue;
     }
-    if (lead && threadIdx.x == 0) clear_slot(E, (L.phase + 1) % 3, st == ST_GR_INIT);
+    if (lead && threadIdx.x == 0)
+      clear_slot(E, (L.phase + 1) % 3, st == ST_GR_INIT || st == ST_GR_ADD);
     run_phase_batch(N, E, L, F, *job, T, lane, a, w_sh);
     __syncthreads();
     if (threadIdx.x == 0) flush_weight(E, L.phase, w_sh);
@@ -429,7 +459,7 @@ __device__ void fc_run_job(FcJob* job, const Params& P0, int rank, int G, unsign
         fc_on_done(L, F, *job, &E->c);
       } else {
         const Snap q = take_snap(E, L.phase);
-        if (is_fc_state(st)) fc_advance(L, F, q, *job, lead);
+        if (is_fc_state(st)) fc_advance(L, F, q, *job, P, lead);
         else advance(L, q, P, N, &E->c, lead);
         L.phase++;
         if (L.state == ST_DONE && !F.finished) fc_on_done(L, F, *job, &E->c);

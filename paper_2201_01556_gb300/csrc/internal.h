@@ -81,6 +81,11 @@ struct hfp_net {
   // incremental source-side search (-1: a full search is needed)
   int32_t pending_source = -1;
   int32_t sr_seed = -1;
+  // a sink was pierced without augmenting path: T_r was grown by a search from
+  // it, so the labels are no longer exact distances and the next flow
+  // computation starts with a global relabel
+  bool gr_pending = false;
+  bool pierced = false;            // flows from now on are incremental
   void* trace_buf = nullptr;
   uint64_t launches = 0;
   uint64_t engine_ns = 0;

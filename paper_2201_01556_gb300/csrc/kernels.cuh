@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(kEngineThreads) fc_batch_kernel(FcJob* jobs, i
 
 // cuts.cu
 enum SetupMode : int { SETUP_GR = 0, SETUP_ROUND = 1, SETUP_SR = 2, SETUP_PREP = 3, SETUP_DIST = 4,
-                       SETUP_BATCH = 5, SETUP_SR_ADD = 6 };
+                       SETUP_BATCH = 5, SETUP_SR_ADD = 6, SETUP_GR_ADD = 7 };
 void launch_engine_setup(EngineCtl* E, int mode, cudaStream_t st, int32_t arg = 0);
 void launch_saturate(const NetDev& N, EngineCtl* E, const int32_t* nodes, int32_t count,
                      cudaStream_t st);

@@ -245,6 +245,9 @@ extern "C" __attribute__((visibility("default"))) hfp_status hfp_max_flow_noallo
   P.tail_exit = 192;
   P.bfs_enter = 0;
   P.bfs_exit = 0;
+  P.pierce_relabel = 0;
+  P.stall_rounds_pierce = 0;
+  P.stall_adapt = 0;
   void* args[] = {(void*)&D, (void*)&E, (void*)&P};
 
   // maximum preflow from {s} to {t}: saturate s, global relabel, rounds

@@ -50,7 +50,8 @@ class _Stats(ctypes.Structure):
 class Tuning(ctypes.Structure):
     _fields_ = [(k, ctypes.c_uint32) for k in ("gr_work_x100", "stall_rounds", "stall_nodes",
                                                "tail_enter", "tail_exit", "max_rounds",
-                                               "bfs_enter", "bfs_exit")]
+                                               "bfs_enter", "bfs_exit", "pierce_relabel",
+                                               "stall_rounds_pierce")]
 
 
 class RefineParams(ctypes.Structure):

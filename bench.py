@@ -182,7 +182,7 @@ def kway_rounds(hfp, ctx, args):
     for mode in ("batched", "plain") if args.kway_plain else ("batched",):
         pd = torch.from_numpy(part.copy()).cuda()
         conn = [hfp.connectivity(hg, pd, 64)]
-        secs, pairs, fc_ms = [], [], []
+        secs, pairs, fc_ms, parts = [], [], [], []
         for _ in range(args.kway_rounds):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -195,8 +195,10 @@ def kway_rounds(hfp, ctx, args):
             secs.append(round(time.perf_counter() - t0, 3))
             conn.append(int(st.connectivity_after))
             pairs.append(int(st.pairs))
+            parts.append({f: round(getattr(st, "ms_" + f), 1)
+                          for f in ("pairs", "prepare", "flow", "finish", "apply")})
         out[mode] = {"seconds_per_round": secs, "connectivity_minus_1": conn,
-                     "pairs_per_round": pairs}
+                     "pairs_per_round": pairs, "round_parts_ms": parts}
         if fc_ms:
             out[mode]["flowcutter_launch_ms"] = fc_ms
     hg.close()

@@ -110,7 +110,8 @@ typedef struct {
   int32_t iterations;        /* max-flow augmentations */
   int32_t n_pierced;         /* piercing steps taken */
   int32_t result_side;       /* 0: (S_r, V \ S_r) returned; 1: (V \ T_r, T_r) */
-  int32_t pad;
+  int32_t device_us;         /* batched launch: device time of this problem in its group
+                              * (microseconds, globaltimer); 0 elsewhere */
 } hfp_fc_result;
 
 /* --- context --------------------------------------------------------------
@@ -148,7 +149,17 @@ uint64_t hfp_kernel_launches(void);
  *   stall_rounds_pierce  the stall_rounds rule for the incremental flows
  *                 after a piercing; 0: adaptive, as many rounds as the last
  *                 global relabel had levels (at least 8, at most
- *                 stall_rounds) [0] */
+ *                 stall_rounds) [0]
+ *   batch_cluster  batched FlowCutter: launch groups of at most 16 CTAs as
+ *                 thread-block clusters (group barriers in distributed
+ *                 shared memory) when as many such clusters can be resident
+ *                 as there would be groups; 0: always one cooperative launch
+ *                 with barriers in global memory [1]
+ *   batch_big_ctas, batch_big_groups  batched FlowCutter: the first
+ *                 batch_big_groups groups get batch_big_ctas CTAs each (the
+ *                 largest problems start on them), the others the launch's
+ *                 group size; used when batch_big_ctas exceeds that size
+ *                 [0, 0]: uniform groups */
 typedef struct {
   uint32_t gr_work_x100;
   uint32_t stall_rounds;
@@ -160,6 +171,9 @@ typedef struct {
   uint32_t bfs_exit;
   uint32_t pierce_relabel;
   uint32_t stall_rounds_pierce;
+  uint32_t batch_cluster;
+  uint32_t batch_big_ctas;
+  uint32_t batch_big_groups;
 } hfp_tuning;
 hfp_status hfp_ctx_get_tuning(hfp_ctx* ctx, hfp_tuning* tuning);
 hfp_status hfp_ctx_set_tuning(hfp_ctx* ctx, const hfp_tuning* tuning);
@@ -320,6 +334,8 @@ typedef struct {
   int32_t applied;         /* hfp_refine_round: 1 if the moves were kept */
   int32_t valid_moves;     /* hfp_refine_round: moves that were not stale */
   int64_t gain;            /* hfp_refine_round: actual reduction of (lambda - 1) */
+  int32_t device_us;       /* batched round: device time of the pair's FlowCutter */
+  int32_t group_ctas;      /* batched round: CTAs of the group that solved it */
 } hfp_pair_result;
 
 typedef struct {
@@ -330,6 +346,12 @@ typedef struct {
   int32_t pairs_improved;  /* pairs with Delta_exp > 0 */
   int32_t pairs_applied;   /* move sets kept */
   int32_t pairs_skipped;   /* pairs below min_score */
+  /* host wall-clock milliseconds of the round's parts: quotient graph and
+   * pair list, regions + networks (+ FlowCutter in hfp_refine_round), the
+   * batched FlowCutter launch (0 in hfp_refine_round), move extraction,
+   * apply step */
+  float ms_pairs, ms_prepare, ms_flow, ms_finish, ms_apply;
+  int32_t pad;
 } hfp_round_stats;
 
 /* Uploads H (in `mem` memory) and builds its vertex -> nets incidence. */

@@ -648,6 +648,9 @@ HFP_API hfp_status hfp_ctx_get_tuning(hfp_ctx* ctx, hfp_tuning* t) {
   t->bfs_exit = ctx->params.bfs_exit;
   t->pierce_relabel = ctx->params.pierce_relabel;
   t->stall_rounds_pierce = (uint32_t)ctx->params.stall_rounds_pierce;
+  t->batch_cluster = ctx->batch_cluster;
+  t->batch_big_ctas = ctx->batch_big_ctas;
+  t->batch_big_groups = ctx->batch_big_groups;
   return HFP_OK;
 }
 
@@ -666,6 +669,9 @@ HFP_API hfp_status hfp_ctx_set_tuning(hfp_ctx* ctx, const hfp_tuning* t) {
   ctx->params.bfs_exit = t->bfs_exit;
   ctx->params.pierce_relabel = t->pierce_relabel ? 1 : 0;
   ctx->params.stall_rounds_pierce = t->stall_rounds_pierce;
+  ctx->batch_cluster = t->batch_cluster ? 1 : 0;
+  ctx->batch_big_ctas = t->batch_big_ctas;
+  ctx->batch_big_groups = t->batch_big_groups;
   return HFP_OK;
 }
 

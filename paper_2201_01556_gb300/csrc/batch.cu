@@ -1,7 +1,9 @@
-// Batched FlowCutter: many flow networks in one cooperative launch of
-// fc_batch_kernel (engine_batch.cuh), with a device work queue handing the
-// networks to groups of CTAs.  Used by hfp_flowcutter_batch and by the
-// batched k-way round (kway.cu).
+// Batched FlowCutter: many flow networks in one launch of fc_batch_kernel
+// (engine_batch.cuh), with a device work queue handing the networks to groups
+// of CTAs.  Groups of up to kMaxClusterCtas CTAs are thread-block clusters
+// (barriers in distributed shared memory); larger groups share a cooperative
+// launch.  Used by hfp_flowcutter_batch and by the batched k-way round
+// (kway.cu).
 #include <algorithm>
 #include <cstring>
 #include <numeric>
@@ -42,9 +44,37 @@ hfp_status run_fc_batch(hfp_ctx* ctx, BatchItem* items, int n, int group_ctas, f
     if (G < 1) G = 1;
   }
   if (G > grid) G = grid;
-  const int groups = grid / G;
+  // big groups first (the largest jobs start on them), then groups of G
+  int Gb = (int)ctx->batch_big_ctas, big = (int)ctx->batch_big_groups;
+  if (Gb <= G || big <= 0) {
+    Gb = G;
+    big = 0;
+  }
+  if (big > n) big = n;
+  while (big > 0 && big * Gb > grid) big--;
+  int groups = big + (grid - big * Gb) / G;
+  bool cluster = big == 0 && ctx->batch_cluster && G <= kMaxClusterCtas;
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  if (cluster) {
+    // clusters only when as many of them can be resident as there are groups
+    CK(cudaFuncSetAttribute(fc_batch_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    cfg.gridDim = dim3(groups * G);
+    cfg.blockDim = dim3(kEngineThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = G;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int resident = 0;
+    CK(cudaOccupancyMaxActiveClusters(&resident, fc_batch_kernel, &cfg));
+    cluster = resident >= groups;
+  }
   if (groups > kMaxGroups) return fail(HFP_ERR_INVALID, "too many groups");
-  const int launch = groups * G;
+  const int launch = big * Gb + (groups - big) * G;
   // jobs, largest network first
   std::vector<int> order(n);
   std::iota(order.begin(), order.end(), 0);
@@ -80,10 +110,15 @@ hfp_status run_fc_batch(hfp_ctx* ctx, BatchItem* items, int n, int group_ctas, f
   FcJob* jp = djobs.as<FcJob>();
   BatchCtl* bp = dctl.as<BatchCtl>();
   Params P0 = ctx->params;
-  void* args[] = {(void*)&jp, (void*)&n, (void*)&bp, (void*)&G, (void*)&P0};
+  int use_cluster = cluster ? 1 : 0;
+  void* args[] = {(void*)&jp,     (void*)&n,      (void*)&bp, (void*)&G,          (void*)&Gb,
+                  (void*)&big,    (void*)&groups, (void*)&P0, (void*)&use_cluster};
   CK(cudaEventRecord(ctx->ev0, st));
-  CK(cudaLaunchCooperativeKernel((void*)fc_batch_kernel, dim3(launch), dim3(kEngineThreads), args,
-                                 0, st));
+  if (cluster)
+    CK(cudaLaunchKernelEx(&cfg, fc_batch_kernel, jp, n, bp, G, Gb, big, groups, P0, use_cluster));
+  else
+    CK(cudaLaunchCooperativeKernel((void*)fc_batch_kernel, dim3(launch), dim3(kEngineThreads),
+                                   args, 0, st));
   CK(cudaEventRecord(ctx->ev1, st));
   count_launches(1);
   int berr = 0;
@@ -106,6 +141,8 @@ hfp_status run_fc_batch(hfp_ctx* ctx, BatchItem* items, int n, int group_ctas, f
     it.result.iterations = J.iterations;
     it.result.n_pierced = J.n_pierced;
     it.result.result_side = J.result_side;
+    it.result.device_us = (int32_t)std::min<unsigned long long>(J.device_ns / 1000, 0x7fffffffull);
+    it.group_ctas = J.group_ctas;
     if (J.status >= 100) {
       it.status = J.status - 100 == kDevBadInput ? HFP_ERR_INVALID : HFP_ERR_ITER_LIMIT;
       if (first_err == HFP_OK)

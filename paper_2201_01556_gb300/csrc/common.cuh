@@ -99,6 +99,44 @@ __device__ __forceinline__ void st_release(unsigned int* p, unsigned int v) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+// Release reduction: every write this thread has made or observed (including,
+// through a preceding __syncthreads, those of its CTA) is visible before the
+// addition is.
+__device__ __forceinline__ void red_release_add(unsigned int* p, unsigned int v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Thread-block cluster helpers.  `addr` is a shared::cluster address (mapa).
+__device__ __forceinline__ unsigned dsmem_addr(const void* smem, unsigned rank) {
+  const unsigned local = (unsigned)__cvta_generic_to_shared(smem);
+  unsigned r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local), "r"(rank));
+  return r;
+}
+
+__device__ __forceinline__ void dsmem_red_release_add(unsigned addr, unsigned v) {
+  asm volatile("red.release.cluster.shared::cluster.add.u32 [%0], %1;" ::"r"(addr), "r"(v)
+               : "memory");
+}
+
+__device__ __forceinline__ unsigned dsmem_ld_acquire(unsigned addr) {
+  unsigned v;
+  asm volatile("ld.acquire.cluster.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
+  return v;
+}
+
+// Hardware barrier of all threads of the cluster (every thread must call it).
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile(
+      "barrier.cluster.arrive.release.aligned;\n\t"
+      "barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// Count-up barrier arithmetic that survives wrap-around of the counter.
+__device__ __forceinline__ bool count_reached(unsigned v, unsigned target) {
+  return (int)(v - target) >= 0;
+}
+
 __device__ __forceinline__ int ld_volatile_int(const int* p) {
   return *(const volatile int*)p;
 }

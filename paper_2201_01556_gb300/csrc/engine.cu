@@ -311,20 +311,23 @@ __device__ __forceinline__ void clear_slot(EngineCtl* E, unsigned sl, bool gr_in
 
 // Count-up grid barrier for a cooperative launch (all CTAs co-resident): a
 // CTA adds one and waits until every CTA has added one for this barrier.  The
-// wait is bounded by P.timeout_ns of globaltimer; on expiry, or once another
-// CTA raised an error, ctl->err is set and false is returned.
+// arrival is a release reduction and the wait an acquire spin, so the writes
+// of every CTA before the barrier are visible to every CTA after it.  The
+// wait is bounded by timeout_ns of globaltimer: on expiry, or when it finds
+// ctl->err raised by another CTA (polled every 256 spins), ctl->err is set and
+// false is returned.  A CTA that raised an error itself also moves its own
+// schedule to ST_DONE, so no error needs to be read after a completed wait.
 __device__ bool grid_barrier(EngineCtl* E, unsigned target, unsigned long long timeout_ns) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
-    __threadfence();
-    atomicAdd(&E->bar_count, 1u);
+    red_release_add(&E->bar_count, 1u);
     unsigned spins = 0;
     unsigned long long t0 = 0;
-    while (ld_acquire(&E->bar_count) < target) {
-      if (ld_volatile_int(&E->c.err) != kDevOk) { ok = 0; break; }
+    while (!count_reached(ld_acquire(&E->bar_count), target)) {
       if ((++spins & 255u) == 0) {
+        if (ld_volatile_int(&E->c.err) != kDevOk) { ok = 0; break; }
         const unsigned long long t = globaltimer();
         if (t0 == 0) t0 = t;
         else if (t - t0 > timeout_ns) {
@@ -335,8 +338,6 @@ __device__ bool grid_barrier(EngineCtl* E, unsigned target, unsigned long long t
         }
       }
     }
-    __threadfence();
-    if (ld_volatile_int(&E->c.err) != kDevOk) ok = 0;
     s_ok = ok;
   }
   __syncthreads();
@@ -1336,6 +1337,7 @@ __global__ void __launch_bounds__(kEngineThreads) engine_kernel(NetDev N, Engine
   const bool cta0 = blockIdx.x == 0;
   if (threadIdx.x == 0) {
     load_sched(L, E);
+    if (ld_volatile_int(&E->c.err) != kDevOk) L.state = ST_DONE;   // left by an earlier launch
     L.flow = *(const volatile unsigned long long*)&E->c.flow;  // host kernels add to it
     acc_sh = Acc{0, 0, 0, 0, 0};
     w_sh = 0;

@@ -109,6 +109,9 @@ struct FcJob {
   int32_t result_side;        // 0: S_r side, 1: T_r side
   long long flow;
   long long source_weight;
+  unsigned long long device_ns;  // globaltimer time of the job in its group
+  int32_t group_ctas;            // CTAs of that group
+  int32_t pad;
 };
 
 // Work queue and per-group barriers of a batched launch.

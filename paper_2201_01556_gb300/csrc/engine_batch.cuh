@@ -365,13 +365,12 @@ __device__ bool group_sync(BatchCtl* B, int gid, unsigned target,
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
-    __threadfence();
-    atomicAdd(&B->gbar[gid], 1u);
+    red_release_add(&B->gbar[gid], 1u);
     unsigned spins = 0;
     unsigned long long t0 = 0;
-    while (ld_acquire(&B->gbar[gid]) < target) {
-      if (ld_volatile_int(&B->err) != 0) { ok = 0; break; }
+    while (!count_reached(ld_acquire(&B->gbar[gid]), target)) {
       if ((++spins & 255u) == 0) {
+        if (ld_volatile_int(&B->err) != 0) { ok = 0; break; }
         const unsigned long long t = globaltimer();
         if (t0 == 0) t0 = t;
         else if (t - t0 > timeout_ns) {
@@ -381,11 +380,59 @@ __device__ bool group_sync(BatchCtl* B, int gid, unsigned target,
         }
       }
     }
-    __threadfence();
     s_ok = ok;
   }
   __syncthreads();
   return s_ok != 0;
+}
+
+// Barrier of a group that is one thread-block cluster: the counter is a
+// word in the shared memory of the cluster's first CTA (`ctr`, a
+// shared::cluster address), arrivals are cluster-scope release reductions
+// and the wait is a cluster-scope acquire spin, so the group's global-memory
+// writes before the barrier are visible to the whole group after it.  The
+// wait is bounded like grid_barrier: every 256 spins it polls *err (raised by
+// another CTA) and globaltimer; on expiry *err = code (and *where = 1 when
+// given) and false is returned.
+__device__ bool cluster_barrier(unsigned ctr, unsigned target, int* err, int code, int* where,
+                                unsigned long long timeout_ns) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    dsmem_red_release_add(ctr, 1u);
+    unsigned spins = 0;
+    unsigned long long t0 = 0;
+    while (!count_reached(dsmem_ld_acquire(ctr), target)) {
+      if ((++spins & 255u) == 0) {
+        if (ld_volatile_int(err) != 0) { ok = 0; break; }
+        const unsigned long long t = globaltimer();
+        if (t0 == 0) t0 = t;
+        else if (t - t0 > timeout_ns) {
+          atomicCAS(err, 0, code);
+          if (where) *where = 1;
+          ok = 0;
+          break;
+        }
+      }
+    }
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// The barrier a group uses: the cluster-resident counter when the group is a
+// cluster (ctr != kNoCluster, running sequence *cseq over the launch), else
+// the job's global counter (sequence *bar_seq within the job).
+constexpr unsigned kNoCluster = 0xffffffffu;
+
+__device__ __forceinline__ bool job_barrier(EngineCtl* E, unsigned ctr, unsigned& cseq,
+                                            unsigned& bar_seq, unsigned G,
+                                            unsigned long long timeout_ns) {
+  if (ctr != kNoCluster)
+    return cluster_barrier(ctr, G * ++cseq, &E->c.err, kDevTimeout, &E->c.err_where, timeout_ns);
+  return grid_barrier(E, G * ++bar_seq, timeout_ns);
 }
 
 __device__ void run_phase_batch(const NetDev& N, EngineCtl* E, const Sched& L, const FcState& F,
@@ -409,12 +456,14 @@ __device__ void run_phase_batch(const NetDev& N, EngineCtl* E, const Sched& L, c
 // One job by one group of G CTAs (rank = position in the group).
 __device__ void fc_run_job(FcJob* job, const Params& P0, int rank, int G, unsigned lane,
                            Sched& L, FcState& F, NetDev& N, Params& P, long long* w_sh,
-                           Clock& ck, SoloSh& solo) {
+                           Clock& ck, SoloSh& solo, unsigned ctr, unsigned& cseq) {
   const unsigned wib = threadIdx.x >> 5, nwb = blockDim.x >> 5;
   const Team T{rank * nwb + wib, G * nwb, rank * blockDim.x + threadIdx.x, G * blockDim.x,
                (unsigned)rank, (unsigned)G};
   EngineCtl* E = job->E;
+  unsigned long long t_start = 0;
   if (threadIdx.x == 0) {
+    t_start = globaltimer();
     N = job->N;
     P = P0;
     P.gr_work = job->gr_work;
@@ -438,7 +487,7 @@ __device__ void fc_run_job(FcJob* job, const Params& P0, int rank, int G, unsign
         solo_phases(N, E, P, L, lane, a, w_sh, ck, solo);
         if (threadIdx.x == 0) store_sched(E, L);
       }
-      const bool ok = grid_barrier(E, G * ++bar_seq, P.timeout_ns);
+      const bool ok = job_barrier(E, ctr, cseq, bar_seq, G, P.timeout_ns);
       if (threadIdx.x == 0) {
         if (!lead) load_sched(L, E);
         if (!ok) L.state = ST_DONE;
@@ -452,7 +501,7 @@ __device__ void fc_run_job(FcJob* job, const Params& P0, int rank, int G, unsign
     run_phase_batch(N, E, L, F, *job, T, lane, a, w_sh);
     __syncthreads();
     if (threadIdx.x == 0) flush_weight(E, L.phase, w_sh);
-    const bool ok = grid_barrier(E, G * ++bar_seq, P.timeout_ns);
+    const bool ok = job_barrier(E, ctr, cseq, bar_seq, G, P.timeout_ns);
     if (threadIdx.x == 0) {
       if (!ok) {
         L.state = ST_DONE;
@@ -486,13 +535,23 @@ __device__ void fc_run_job(FcJob* job, const Params& P0, int rank, int G, unsign
     job->result_side = F.result_side;
     job->flow = (long long)L.flow;
     job->source_weight = F.source_weight;
+    job->device_ns = globaltimer() - t_start;
+    job->group_ctas = G;
   }
 }
 
-// The batched launch: gridDim.x / G groups take jobs from the queue in
-// order (the host sorts them, largest first) until none is left.
+// The batched launch.  The grid is cut into groups: the first `big` groups
+// of Gb CTAs, then groups of G CTAs.  The host sorts the jobs largest first;
+// group g starts on job g (so the big groups take the largest problems) and
+// every group then takes the next job from the queue until none is left.
+// With `cluster` set (uniform groups only) the launch has clusters of G CTAs
+// and each group is one cluster (group barriers in distributed shared
+// memory); otherwise it is a cooperative launch and groups synchronise
+// through global counters.
 __global__ void __launch_bounds__(kEngineThreads) fc_batch_kernel(FcJob* jobs, int n_jobs,
-                                                                  BatchCtl* B, int G, Params P0) {
+                                                                  BatchCtl* B, int G, int Gb,
+                                                                  int big, int n_groups,
+                                                                  Params P0, int cluster) {
   __shared__ Sched L;
   __shared__ FcState F;
   __shared__ NetDev N;
@@ -501,18 +560,43 @@ __global__ void __launch_bounds__(kEngineThreads) fc_batch_kernel(FcJob* jobs, i
   __shared__ Clock ck;
   __shared__ SoloSh solo;
   __shared__ unsigned job_sh;
-  const int gid = blockIdx.x / G, rank = blockIdx.x % G;
+  __shared__ unsigned gbar_sh;   // the group's barrier counter (cluster rank 0's is used)
+  const int big_ctas = big * Gb;
+  int gid, rank, Gg;
+  if ((int)blockIdx.x < big_ctas) {
+    gid = blockIdx.x / Gb;
+    rank = blockIdx.x % Gb;
+    Gg = Gb;
+  } else {
+    const int x = blockIdx.x - big_ctas;
+    gid = big + x / G;
+    rank = x % G;
+    Gg = G;
+  }
   const unsigned lane = lane_id();
-  if (threadIdx.x == 0) ck.t_last = globaltimer();
-  unsigned gseq = 0;
+  unsigned ctr = kNoCluster;
+  if (threadIdx.x == 0) {
+    ck.t_last = globaltimer();
+    gbar_sh = 0;
+  }
+  if (cluster) {
+    cluster_sync_all();           // every counter is zero before the first arrival
+    ctr = dsmem_addr(&gbar_sh, 0);
+  }
+  unsigned gseq = 0, cseq = 0;
+  unsigned j = (unsigned)gid;
   for (;;) {
-    if (rank == 0 && threadIdx.x == 0) B->gjob[gid] = atomicAdd(&B->next, 1u);
-    if (!group_sync(B, gid, G * ++gseq, P0.timeout_ns)) break;
+    if (j >= (unsigned)n_jobs) break;
+    fc_run_job(&jobs[j], P0, rank, Gg, lane, L, F, N, P, &w_sh, ck, solo, ctr, cseq);
+    // hand-out of the next job (the queue starts after the first job of every group)
+    if (rank == 0 && threadIdx.x == 0) B->gjob[gid] = n_groups + atomicAdd(&B->next, 1u);
+    const bool ok = cluster ? cluster_barrier(ctr, Gg * ++cseq, &B->err, 1, nullptr, P0.timeout_ns)
+                            : group_sync(B, gid, Gg * ++gseq, P0.timeout_ns);
+    if (!ok) break;
     if (threadIdx.x == 0) job_sh = *(const volatile unsigned*)&B->gjob[gid];
     __syncthreads();
-    const unsigned j = job_sh;
-    if (j >= (unsigned)n_jobs) break;
-    fc_run_job(&jobs[j], P0, rank, G, lane, L, F, N, P, &w_sh, ck, solo);
-    if (!group_sync(B, gid, G * ++gseq, P0.timeout_ns)) break;
+    j = job_sh;
   }
+  // no CTA of a cluster exits while another may still read its shared memory
+  if (cluster) cluster_sync_all();
 }

@@ -60,6 +60,9 @@ struct hfp_ctx {
   void* pinned_small = nullptr;    // 4 KB staging
   hfp::Params params{};
   uint32_t gr_work_x100 = 200;
+  uint32_t batch_cluster = 1;      // hfp_tuning.batch_cluster
+  uint32_t batch_big_ctas = 0;     // hfp_tuning.batch_big_ctas
+  uint32_t batch_big_groups = 0;   // hfp_tuning.batch_big_groups
 };
 
 struct hfp_net {
@@ -118,6 +121,7 @@ struct BatchItem {
   int32_t pierce_cap = 0;
   hfp_fc_result result{};
   hfp_status status = HFP_OK;
+  int32_t group_ctas = 0;          // CTAs of the group that solved it
 };
 
 // Grid of fc_batch_kernel on the context's device (all CTAs co-resident).

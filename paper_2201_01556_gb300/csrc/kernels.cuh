@@ -47,7 +47,12 @@ void launch_st_attrs(int32_t* node_gid, int32_t* node_w, int8_t* node_orig,
 constexpr int kEngineThreads = 512;   // block scans assume < 32 warps
 __global__ void __launch_bounds__(kEngineThreads) engine_kernel(NetDev N, EngineCtl* E, Params P);
 __global__ void __launch_bounds__(kEngineThreads) fc_batch_kernel(FcJob* jobs, int n_jobs,
-                                                                  BatchCtl* B, int G, Params P0);
+                                                                  BatchCtl* B, int G, int Gb,
+                                                                  int big, int n_groups,
+                                                                  Params P0, int cluster);
+// Largest group of fc_batch_kernel launched as one thread-block cluster
+// (non-portable cluster size); larger groups use a cooperative launch.
+constexpr int kMaxClusterCtas = 16;
 
 // cuts.cu
 enum SetupMode : int { SETUP_GR = 0, SETUP_ROUND = 1, SETUP_SR = 2, SETUP_PREP = 3, SETUP_DIST = 4,

@@ -15,6 +15,7 @@
 // dropping stale moves, skipping a set that would push a growing block past
 // the bound, and reverting a set whose actual gain is negative.
 #include <algorithm>
+#include <chrono>
 #include <cstring>
 #include <deque>
 #include <vector>
@@ -636,6 +637,7 @@ hfp_status finish_pair(hfp_hgraph* hg, const int32_t* part, hfp_status fc, const
   res->status = fc;
   res->flow = fr.flow;
   res->iterations = fr.iterations;
+  res->device_us = fr.device_us;
   if (fc == HFP_NO_BALANCED_CUT || fc == HFP_ABORTED_WORSE) {
     hfp_net_destroy(w.net);
     w.net = nullptr;
@@ -781,15 +783,21 @@ struct Item {
   DevBuf mv;
 };
 
+// Host wall-clock milliseconds since t0; the caller synchronises first.
+inline float ms_since(std::chrono::steady_clock::time_point t0) {
+  return std::chrono::duration<float, std::milli>(std::chrono::steady_clock::now() - t0).count();
+}
+
 // Refines every pair against the same partition: one FlowCutter per launch
 // sequence (plain) or all FlowCutter problems in one batched launch.
 hfp_status refine_pairs(hfp_hgraph* hg, const int32_t* part, int32_t k,
                         const hfp_refine_params* prm, const std::vector<std::pair<int, int>>& pairs,
                         bool batched, int32_t group_ctas, std::deque<Item>& items,
-                        float* flow_ms) {
+                        float* flow_ms, hfp_round_stats* stats) {
   RegionScratch sc;
   hfp_status s = sc.alloc(hg);
   if (s != HFP_OK) return s;
+  auto t0 = std::chrono::steady_clock::now();
   if (!batched) {
     for (const auto& pr : pairs) {
       items.emplace_back();
@@ -797,6 +805,8 @@ hfp_status refine_pairs(hfp_hgraph* hg, const int32_t* part, int32_t k,
                            &items.back().r)) != HFP_OK)
         return s;
     }
+    CK(cudaStreamSynchronize(hg->ctx->stream));
+    stats->ms_prepare = ms_since(t0);
     return HFP_OK;
   }
   std::deque<PairWork> works;
@@ -805,6 +815,9 @@ hfp_status refine_pairs(hfp_hgraph* hg, const int32_t* part, int32_t k,
     if ((s = prepare_pair(hg, part, k, pr.first, pr.second, prm, sc, works.back())) != HFP_OK)
       return s;
   }
+  CK(cudaStreamSynchronize(hg->ctx->stream));
+  stats->ms_prepare = ms_since(t0);
+  t0 = std::chrono::steady_clock::now();
   const int n = (int)works.size();
   std::vector<BatchItem> bi(n);
   for (int t = 0; t < n; t++) {
@@ -813,12 +826,17 @@ hfp_status refine_pairs(hfp_hgraph* hg, const int32_t* part, int32_t k,
   }
   const int G = group_ctas > 0 ? group_ctas : hg->tuned_group;
   if ((s = run_fc_batch(hg->ctx, bi.data(), n, G, flow_ms)) != HFP_OK) return s;
+  stats->ms_flow = ms_since(t0);
+  t0 = std::chrono::steady_clock::now();
   for (int t = 0; t < n; t++) {
     items.emplace_back();
+    works[t].r.group_ctas = bi[t].group_ctas;
     s = finish_pair(hg, part, bi[t].status, bi[t].result, sc, works[t], items.back().mv);
     items.back().r = works[t].r;
     if (s != HFP_OK) return s;
   }
+  CK(cudaStreamSynchronize(hg->ctx->stream));
+  stats->ms_finish = ms_since(t0);
   return HFP_OK;
 }
 
@@ -925,11 +943,16 @@ hfp_status round_impl(hfp_hgraph* hg, int32_t* part, int32_t k, const hfp_refine
   if (s != HFP_OK) return s;
   memset(stats, 0, sizeof(*stats));
   std::vector<std::pair<int, int>> pl;
+  auto t0 = std::chrono::steady_clock::now();
   if ((s = round_pairs(hg, part, k, pair_scores, min_score, stats, pl)) != HFP_OK) return s;
+  stats->ms_pairs = ms_since(t0);
   std::deque<Item> items;
-  if ((s = refine_pairs(hg, part, k, prm, pl, batched, group_ctas, items, flow_ms)) != HFP_OK)
+  if ((s = refine_pairs(hg, part, k, prm, pl, batched, group_ctas, items, flow_ms, stats)) !=
+      HFP_OK)
     return s;
+  t0 = std::chrono::steady_clock::now();
   if ((s = apply_round(hg, part, k, prm, items, stats)) != HFP_OK) return s;
+  stats->ms_apply = ms_since(t0);
   if (n_pairs) *n_pairs = (int32_t)items.size();
   if (pairs)
     for (int t = 0; t < (int)items.size() && t < cap; t++) pairs[t] = items[t].r;

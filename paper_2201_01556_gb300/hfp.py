@@ -51,7 +51,8 @@ class Tuning(ctypes.Structure):
     _fields_ = [(k, ctypes.c_uint32) for k in ("gr_work_x100", "stall_rounds", "stall_nodes",
                                                "tail_enter", "tail_exit", "max_rounds",
                                                "bfs_enter", "bfs_exit", "pierce_relabel",
-                                               "stall_rounds_pierce")]
+                                               "stall_rounds_pierce", "batch_cluster",
+                                               "batch_big_ctas", "batch_big_groups")]
 
 
 class RefineParams(ctypes.Structure):
@@ -65,14 +66,18 @@ class PairResult(ctypes.Structure):
                 ("original_cut", ctypes.c_int64), ("flow", ctypes.c_int64),
                 ("delta_exp", ctypes.c_int64), ("n_moves", ctypes.c_int32),
                 ("iterations", ctypes.c_int32), ("applied", ctypes.c_int32),
-                ("valid_moves", ctypes.c_int32), ("gain", ctypes.c_int64)]
+                ("valid_moves", ctypes.c_int32), ("gain", ctypes.c_int64),
+                ("device_us", ctypes.c_int32), ("group_ctas", ctypes.c_int32)]
 
 
 class RoundStats(ctypes.Structure):
     _fields_ = [("connectivity_before", ctypes.c_int64), ("connectivity_after", ctypes.c_int64),
                 ("gain", ctypes.c_int64), ("moves_applied", ctypes.c_int64),
                 ("pairs", ctypes.c_int32), ("pairs_improved", ctypes.c_int32),
-                ("pairs_applied", ctypes.c_int32), ("pairs_skipped", ctypes.c_int32)]
+                ("pairs_applied", ctypes.c_int32), ("pairs_skipped", ctypes.c_int32),
+                ("ms_pairs", ctypes.c_float), ("ms_prepare", ctypes.c_float),
+                ("ms_flow", ctypes.c_float), ("ms_finish", ctypes.c_float),
+                ("ms_apply", ctypes.c_float), ("pad", ctypes.c_int32)]
 
 
 class AdamParams(ctypes.Structure):
@@ -96,7 +101,7 @@ class FcParams(ctypes.Structure):
 class _FcResult(ctypes.Structure):
     _fields_ = [("flow", ctypes.c_int64), ("source_weight", ctypes.c_int64),
                 ("iterations", ctypes.c_int32), ("n_pierced", ctypes.c_int32),
-                ("result_side", ctypes.c_int32), ("pad", ctypes.c_int32)]
+                ("result_side", ctypes.c_int32), ("device_us", ctypes.c_int32)]
 
 
 class _FcTask(ctypes.Structure):

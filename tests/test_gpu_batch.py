@@ -126,6 +126,41 @@ def test_batched_round_equals_plain_round(env, seed, n, k, group):
         assert np.array_equal(p2.cpu().numpy(), newp) and s2.gain == total
 
 
+@pytest.mark.parametrize("group,big_ctas,big_groups,cluster", [(4, 16, 3, 1), (2, 32, 2, 1),
+                                                                (4, 0, 0, 0), (8, 0, 0, 1)])
+def test_batched_round_group_layouts(env, group, big_ctas, big_groups, cluster):
+    """Mixed group sizes (big groups for the largest problems), and uniform
+    groups as clusters or in one cooperative launch, give the plain round's
+    outcome and report per-pair device times."""
+    torch, hfp, ctx = env
+    H, part, hg = _kway(env, 6, 30000, 16)
+    base = hfp.ctx_get_tuning(ctx)
+    p1 = torch.from_numpy(part.copy()).cuda()
+    p2 = torch.from_numpy(part.copy()).cuda()
+    s1, r1 = hfp.refine_round(hg, p1, 16, hfp.refine_params(seed=2))
+    try:
+        hfp.ctx_set_tuning(ctx, batch_big_ctas=big_ctas, batch_big_groups=big_groups,
+                           batch_cluster=cluster)
+        s2, r2, ms = hfp.refine_round_batched(hg, p2, 16, hfp.refine_params(seed=2),
+                                              group_ctas=group)
+    finally:
+        hfp.ctx_set_tuning(ctx, **base)
+    assert np.array_equal(p1.cpu().numpy(), p2.cpu().numpy())
+    assert s1.connectivity_after == s2.connectivity_after and s1.pairs == s2.pairs
+    for a, b in zip(r1, r2):
+        for f in ("bi", "bj", "status", "flow", "delta_exp", "n_moves", "iterations"):
+            assert getattr(a, f) == getattr(b, f), f
+    assert all(r.device_us > 0 for r in r2) and all(r.device_us == 0 for r in r1)
+    sizes = sorted({r.group_ctas for r in r2})
+    if big_groups:
+        # the largest problems started on the big groups
+        by_pins = sorted(r2, key=lambda r: -r.pins)
+        assert all(r.group_ctas == big_ctas for r in by_pins[:min(big_groups, len(r2))])
+        assert sizes == sorted({group, big_ctas}) or sizes == [big_ctas]
+    else:
+        assert sizes == [group]
+
+
 def test_autotune_and_tuned_round(env):
     torch, hfp, ctx = env
     H, part, hg = _kway(env, 7, 30000, 32)

@@ -411,6 +411,58 @@ hfp_status hfp_autotune_round(hfp_hgraph* hg, const int32_t* part, int32_t k,
                               const hfp_refine_params* params, const int32_t* candidates,
                               int32_t n_candidates, float* ms, int32_t* best);
 
+/* --- one round in three calls ---------------------------------------------
+ * Algorithm 1 refines all block pairs of a round against the same partition
+ * and only then applies their move sets (Section 5, "Parallel Scheduling",
+ * "Apply Moves").  The pairs are therefore independent problems that several
+ * processes (one GPU each) can share; the apply step needs every pair's
+ * moves.  These calls expose the three stages: the pair list, the refinement
+ * of any subset of it, and the apply step over move sets gathered from all
+ * processes.  Refining every pair in one call and applying gives exactly
+ * hfp_refine_round_batched's outcome, whatever the split. */
+
+/* Edges of the quotient graph of `part` (device; Section 5, "Quotient Graph
+ * Construction"): every pair i < j of blocks with a net in both, ascending
+ * (i, j), without pairs whose pair_scores[i*k + j] (host, k*k; NULL: none)
+ * is below min_score.  pairs: host int32[cap][2]; pair_nets (host, may be
+ * NULL): int64[cap], the number of nets in both blocks (a size estimate);
+ * *n_pairs: the count (HFP_ERR_BUFFER_TOO_SMALL when above cap, *n_pairs
+ * still set); *connectivity (may be NULL): (lambda - 1)(part). */
+hfp_status hfp_round_pairs(hfp_hgraph* hg, const int32_t* part, int32_t k,
+                           const float* pair_scores, float min_score, int32_t* pairs,
+                           int64_t* pair_nets, int32_t cap, int32_t* n_pairs,
+                           int64_t* connectivity);
+
+/* Refines the n given pairs (host int32[n][2], 0 <= i < j < k, no repeats)
+ * against `part` (device, unchanged), exactly as hfp_refine_round_batched
+ * does (region, network, FlowCutter in one batched launch with group_ctas
+ * CTAs per problem, moves), without applying anything.  results[t] (host)
+ * is pair t's outcome; its moves (vertex, from block, to block) go to host
+ * moves[3 * move_off[t]] .. moves[3 * move_off[t + 1] - 1], move_off being
+ * host int64[n + 1].  HFP_ERR_BUFFER_TOO_SMALL when the moves exceed
+ * move_cap triples (move_off is filled: move_off[n] is the need).
+ * flowcutter_ms (may be NULL): device time of the batched launch. */
+hfp_status hfp_refine_pairs_batched(hfp_hgraph* hg, const int32_t* part, int32_t k,
+                                    const hfp_refine_params* params, const int32_t* pairs,
+                                    int32_t n, int32_t group_ctas, hfp_pair_result* results,
+                                    int32_t* moves, int64_t move_cap, int64_t* move_off,
+                                    float* flowcutter_ms);
+
+/* The apply step of a round (Section 5, "Apply Moves") on n pair results
+ * and their moves (host, the layout of hfp_refine_pairs_batched, in any
+ * order of the pairs): the move sets of pairs with status HFP_OK,
+ * Delta_exp >= 0 and at least one move, in descending Delta_exp with ties in
+ * ascending (bi, bj), each checked for stale moves and balance and reverted
+ * when its actual gain is negative.  part (device) is updated; results[t]
+ * receives applied, valid_moves and gain; stats the round's totals
+ * (connectivity before and after, gain, pairs, moves applied, ms_apply).
+ * HFP_ERR_INVALID for a result whose move count disagrees with move_off or
+ * a move that is not between the pair's two blocks. */
+hfp_status hfp_apply_moves(hfp_hgraph* hg, int32_t* part, int32_t k,
+                           const hfp_refine_params* params, hfp_pair_result* results,
+                           const int32_t* moves, const int64_t* move_off, int32_t n,
+                           hfp_round_stats* stats);
+
 /* --- learned block-pair scheduler ----------------------------------------
  * The paper has no learned component: its rounds refine every edge of the
  * quotient graph (Section 5, "Quotient Graph Construction" and "Parallel

@@ -441,6 +441,16 @@ def refine_round(H, part, k: int, eps_pct: int = 3, alpha_eps_pct: int = 48, del
         pairs = [(i, j) for i in range(k) for j in range(i + 1, k) if qn[i, j] > 0]
     res = [refine_block_pair(H, part, k, i, j, eps_pct, alpha_eps_pct, delta, seed)
            for i, j in pairs]
+    total, gains = apply_round(H, part, k, res, eps_pct)
+    return part, total, res, gains
+
+
+def apply_round(H, part: np.ndarray, k: int, res, eps_pct: int = 3):
+    """The apply step of a round (Section 5, "Apply Moves"): the move sets
+    of the results with status OK, Delta_exp >= 0 and moves, in descending
+    Delta_exp (ties: ascending (i, j)), each through apply_moves.  part
+    (int32) is updated in place.  Returns (total gain, {(i, j): (gain,
+    applied, valid moves)})."""
     L = max_block_weight(int(np.asarray(H.node_w, np.int64).sum()), k, eps_pct)
     order = sorted((r for r in res if r.status == OK and r.delta_exp >= 0 and len(r.moves)),
                    key=lambda r: (-r.delta_exp, r.bi, r.bj))
@@ -450,4 +460,4 @@ def refine_round(H, part, k: int, eps_pct: int = 3, alpha_eps_pct: int = 48, del
         g, applied, nv = apply_moves(H, part, k, L, r.moves)
         gains[(r.bi, r.bj)] = (g, applied, nv)
         total += g
-    return part, total, res, gains
+    return total, gains

@@ -743,7 +743,8 @@ namespace {
 // fills stats->connectivity_before and ->pairs_skipped.
 hfp_status round_pairs(hfp_hgraph* hg, const int32_t* part, int32_t k, const float* pair_scores,
                        float min_score, hfp_round_stats* stats,
-                       std::vector<std::pair<int, int>>& pairs) {
+                       std::vector<std::pair<int, int>>& pairs,
+                       std::vector<long long>* pair_nets = nullptr) {
   cudaStream_t st = hg->ctx->stream;
   const int m = hg->m, sms = hg->ctx->sms;
   DevBuf conn, qn, qw;
@@ -774,6 +775,7 @@ hfp_status round_pairs(hfp_hgraph* hg, const int32_t* part, int32_t k, const flo
         continue;
       }
       pairs.emplace_back(i, j);
+      if (pair_nets) pair_nets->push_back((long long)hq[(size_t)i * k + j]);
     }
   return HFP_OK;
 }
@@ -1024,5 +1026,122 @@ HFP_API hfp_status hfp_autotune_round(hfp_hgraph* hg, const int32_t* part, int32
   }
   hg->tuned_group = best_g;
   if (best) *best = best_g;
+  return HFP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// The round in three calls, for callers that split the block pairs of a round
+// across processes (one GPU each): pairs, refinement of a subset, apply step.
+
+HFP_API hfp_status hfp_round_pairs(hfp_hgraph* hg, const int32_t* part, int32_t k,
+                                   const float* pair_scores, float min_score, int32_t* pairs,
+                                   int64_t* pair_nets, int32_t cap, int32_t* n_pairs,
+                                   int64_t* connectivity) {
+  if (!hg || !part || !n_pairs || (cap > 0 && !pairs)) return fail(HFP_ERR_INVALID, "NULL argument");
+  if (k < 2 || k > 64) return fail(HFP_ERR_INVALID, "k must be in [2, 64]");
+  hfp_status s = hg_set_device(hg);
+  if (s != HFP_OK) return s;
+  hfp_round_stats st{};
+  std::vector<std::pair<int, int>> pl;
+  std::vector<long long> nets;
+  if ((s = round_pairs(hg, part, k, pair_scores, min_score, &st, pl, &nets)) != HFP_OK) return s;
+  *n_pairs = (int32_t)pl.size();
+  if (connectivity) *connectivity = st.connectivity_before;
+  if ((int64_t)pl.size() > cap)
+    return fail(HFP_ERR_BUFFER_TOO_SMALL, "%zu pairs, capacity %d", pl.size(), cap);
+  for (size_t t = 0; t < pl.size(); t++) {
+    pairs[2 * t] = pl[t].first;
+    pairs[2 * t + 1] = pl[t].second;
+    if (pair_nets) pair_nets[t] = nets[t];
+  }
+  return HFP_OK;
+}
+
+HFP_API hfp_status hfp_refine_pairs_batched(hfp_hgraph* hg, const int32_t* part, int32_t k,
+                                            const hfp_refine_params* prm, const int32_t* pairs,
+                                            int32_t n, int32_t group_ctas,
+                                            hfp_pair_result* results, int32_t* moves,
+                                            int64_t move_cap, int64_t* move_off,
+                                            float* flowcutter_ms) {
+  if (!hg || !part || !prm || n < 0 || (n > 0 && (!pairs || !results)) || !move_off ||
+      (move_cap > 0 && !moves))
+    return fail(HFP_ERR_INVALID, "NULL argument");
+  if (k < 2 || k > 64) return fail(HFP_ERR_INVALID, "k must be in [2, 64]");
+  if (prm->delta < 1) return fail(HFP_ERR_INVALID, "delta must be positive");
+  std::vector<std::pair<int, int>> pl;
+  for (int32_t t = 0; t < n; t++) {
+    const int32_t i = pairs[2 * t], j = pairs[2 * t + 1];
+    if (i < 0 || j <= i || j >= k) return fail(HFP_ERR_INVALID, "pair %d: (%d, %d)", t, i, j);
+    for (const auto& q : pl)
+      if (q.first == i && q.second == j) return fail(HFP_ERR_INVALID, "pair (%d, %d) repeats", i, j);
+    pl.emplace_back(i, j);
+  }
+  hfp_status s = hg_set_device(hg);
+  if (s != HFP_OK) return s;
+  if (flowcutter_ms) *flowcutter_ms = 0.f;
+  move_off[0] = 0;
+  if (n == 0) return HFP_OK;
+  std::deque<Item> items;
+  hfp_round_stats st{};
+  if ((s = refine_pairs(hg, part, k, prm, pl, true, group_ctas, items, flowcutter_ms, &st)) !=
+      HFP_OK)
+    return s;
+  for (int32_t t = 0; t < n; t++) {
+    results[t] = items[t].r;
+    move_off[t + 1] = move_off[t] + items[t].r.n_moves;
+  }
+  if (move_off[n] > move_cap)
+    return fail(HFP_ERR_BUFFER_TOO_SMALL, "%lld moves, capacity %lld", (long long)move_off[n],
+                (long long)move_cap);
+  cudaStream_t st_ = hg->ctx->stream;
+  for (int32_t t = 0; t < n; t++)
+    if (items[t].r.n_moves > 0)
+      CK(cudaMemcpyAsync(moves + 3 * move_off[t], items[t].mv.p,
+                         sizeof(int32_t) * 3 * (size_t)items[t].r.n_moves, cudaMemcpyDeviceToHost,
+                         st_));
+  CK(cudaStreamSynchronize(st_));
+  return HFP_OK;
+}
+
+HFP_API hfp_status hfp_apply_moves(hfp_hgraph* hg, int32_t* part, int32_t k,
+                                   const hfp_refine_params* prm, hfp_pair_result* results,
+                                   const int32_t* moves, const int64_t* move_off, int32_t n,
+                                   hfp_round_stats* stats) {
+  if (!hg || !part || !prm || !stats || n < 0 || (n > 0 && (!results || !move_off)))
+    return fail(HFP_ERR_INVALID, "NULL argument");
+  if (k < 2 || k > 64) return fail(HFP_ERR_INVALID, "k must be in [2, 64]");
+  hfp_status s = hg_set_device(hg);
+  if (s != HFP_OK) return s;
+  memset(stats, 0, sizeof(*stats));
+  int64_t c0 = 0;
+  if ((s = hfp_connectivity(hg, part, k, &c0)) != HFP_OK) return s;
+  stats->connectivity_before = c0;
+  cudaStream_t st = hg->ctx->stream;
+  std::deque<Item> items;
+  for (int32_t t = 0; t < n; t++) {
+    const hfp_pair_result& r = results[t];
+    if (r.bi < 0 || r.bj <= r.bi || r.bj >= k) return fail(HFP_ERR_INVALID, "result %d: bad pair", t);
+    if (move_off[t + 1] - move_off[t] != r.n_moves || r.n_moves < 0)
+      return fail(HFP_ERR_INVALID, "result %d: %d moves, offsets give %lld", t, r.n_moves,
+                  (long long)(move_off[t + 1] - move_off[t]));
+    items.emplace_back();
+    items.back().r = r;
+    if (r.n_moves > 0) {
+      if (!moves) return fail(HFP_ERR_INVALID, "moves is NULL");
+      for (int64_t x = move_off[t]; x < move_off[t + 1]; x++) {
+        const int32_t v = moves[3 * x], from = moves[3 * x + 1], to = moves[3 * x + 2];
+        if (v < 0 || v >= hg->n || (from != r.bi && from != r.bj) || (to != r.bi && to != r.bj) ||
+            from == to)
+          return fail(HFP_ERR_INVALID, "result %d: bad move (%d, %d, %d)", t, v, from, to);
+      }
+      CK(items.back().mv.alloc(sizeof(int32_t) * 3 * (size_t)r.n_moves, st));
+      CK(cudaMemcpyAsync(items.back().mv.p, moves + 3 * move_off[t],
+                         sizeof(int32_t) * 3 * (size_t)r.n_moves, cudaMemcpyHostToDevice, st));
+    }
+  }
+  auto t0 = std::chrono::steady_clock::now();
+  if ((s = apply_round(hg, part, k, prm, items, stats)) != HFP_OK) return s;
+  stats->ms_apply = ms_since(t0);
+  for (int32_t t = 0; t < n; t++) results[t] = items[t].r;
   return HFP_OK;
 }

@@ -165,6 +165,11 @@ def load():
         "hfp_mlp_train": (i32, [P, P, P, P, P, P, P, i32, i32, ctypes.POINTER(AdamParams), P,
                                 i32]),
         "hfp_pair_scores": (i32, [P, P, i32, i32, P, P, P]),
+        "hfp_round_pairs": (i32, [P, P, i32, P, ctypes.c_float, P, P, i32, P, P]),
+        "hfp_refine_pairs_batched": (i32, [P, P, i32, ctypes.POINTER(RefineParams), P, i32, i32,
+                                           P, P, ctypes.c_int64, P, P]),
+        "hfp_apply_moves": (i32, [P, P, i32, ctypes.POINTER(RefineParams), P, P, P, i32,
+                                  ctypes.POINTER(RoundStats)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -472,6 +477,59 @@ def refine_round_batched(hg: HGraph, part_dev, k: int, params: RefineParams | No
                                            ctypes.byref(stats), arr, cap, ctypes.byref(n),
                                            ctypes.byref(ms)))
     return stats, [arr[i] for i in range(n.value)], float(ms.value)
+
+
+def round_pairs(hg: HGraph, part_dev, k: int, pair_scores=None, min_score: float = 0.0):
+    """hfp_round_pairs -> (pairs int32[P, 2], nets in both blocks int64[P],
+    connectivity)."""
+    cap = k * (k - 1) // 2
+    pairs = np.zeros((max(cap, 1), 2), np.int32)
+    nets = np.zeros(max(cap, 1), np.int64)
+    n = ctypes.c_int32()
+    conn = ctypes.c_int64()
+    sc = None if pair_scores is None else np.ascontiguousarray(pair_scores, np.float32)
+    _check(load().hfp_round_pairs(hg.h, _ptr(part_dev), k, _ptr(sc), ctypes.c_float(min_score),
+                                  _ptr(pairs), _ptr(nets), cap, ctypes.byref(n),
+                                  ctypes.byref(conn)))
+    return pairs[:n.value].copy(), nets[:n.value].copy(), int(conn.value)
+
+
+def refine_pairs_batched(hg: HGraph, part_dev, k: int, pairs, params: RefineParams | None = None,
+                         group_ctas: int = 0):
+    """hfp_refine_pairs_batched -> ([PairResult], moves int32[M, 3], offsets
+    int64[n + 1], FlowCutter launch ms); part is not changed."""
+    params = params or refine_params()
+    pr = np.ascontiguousarray(np.asarray(pairs, np.int32).reshape(-1, 2))
+    n = len(pr)
+    res = (PairResult * max(n, 1))()
+    off = np.zeros(n + 1, np.int64)
+    ms = ctypes.c_float()
+    cap = 0
+    for _ in range(2):
+        moves = np.zeros((max(cap, 1), 3), np.int32)
+        st = _check(load().hfp_refine_pairs_batched(hg.h, _ptr(part_dev), k, ctypes.byref(params),
+                                                    _ptr(pr), n, group_ctas, res, _ptr(moves),
+                                                    cap, _ptr(off), ctypes.byref(ms)),
+                    allow=(ERR_BUFFER_TOO_SMALL,))
+        if st == OK:
+            return [res[i] for i in range(n)], moves[:off[n]].copy(), off, float(ms.value)
+        cap = int(off[n])
+    raise HfpError(ERR_BUFFER_TOO_SMALL, "moves did not fit")
+
+
+def apply_moves(hg: HGraph, part_dev, k: int, results, moves, offsets,
+                params: RefineParams | None = None):
+    """hfp_apply_moves (part updated in place) -> (RoundStats, [PairResult]
+    with applied / valid_moves / gain)."""
+    params = params or refine_params()
+    n = len(results)
+    arr = (PairResult * max(n, 1))(*results)
+    mv = np.ascontiguousarray(np.asarray(moves, np.int32).reshape(-1, 3))
+    off = np.ascontiguousarray(offsets, np.int64)
+    stats = RoundStats()
+    _check(load().hfp_apply_moves(hg.h, _ptr(part_dev), k, ctypes.byref(params), arr, _ptr(mv),
+                                  _ptr(off), n, ctypes.byref(stats)))
+    return stats, [arr[i] for i in range(n)]
 
 
 def autotune_round(hg: HGraph, part_dev, k: int, candidates, params: RefineParams | None = None):

@@ -12,7 +12,8 @@ ranks (independent replicas; the single max flow does not shard).
 The line also carries "kway": k-way refinement rounds (Algorithm 1) on the
 8,000,000-vertex / 12,000,000-net ring (2 + Zipf(2.5) pins capped at 10,000,
 k = 64 contiguous arcs, 5 % of the vertices moved to a neighbouring block),
-all FlowCutter problems of a round in one batched launch; --kway-plain adds
+all FlowCutter problems of a round in one batched launch (with several
+ranks, the round's block pairs are split across them); --kway-plain adds
 the same rounds with one problem per launch sequence (identical partitions).
 
 --impl reference times the CPU oracle (Dinic on the explicit Lawler graph)
@@ -168,17 +169,20 @@ def run_reference(args, rank, world):
     return 0
 
 
-def kway_rounds(hfp, ctx, args):
+def kway_rounds(hfp, ctx, args, world):
     """Timed k-way refinement rounds: batched (and optionally plain) on the
     same start partition; identical outcomes, so the times compare at equal
-    (lambda - 1)."""
+    (lambda - 1).  With several ranks the batched rounds split their block
+    pairs across the ranks (one all-gather of move sets per round) and every
+    rank runs this."""
     import torch
+    from paper_2201_01556_gb300 import sharded
     n = args.kway_n
     inst = synth.instance("ring_n8M_zipf_k64", args.seed, n=n, m=n * 3 // 2)
     H, part = inst["H"], inst["part"]
     hg = hfp.HGraph(ctx, H.net_off, H.pins, H.net_w, H.node_w, H.n)
     out = {"workload": f"ring n={n} m={n * 3 // 2} k=64 (2+Zipf(2.5) <= 10000, 5% moved)",
-           "pins_H": int(H.p), "group_ctas": args.kway_group}
+           "pins_H": int(H.p), "group_ctas": args.kway_group, "pairs_split_over_ranks": world}
     for mode in ("batched", "plain") if args.kway_plain else ("batched",):
         pd = torch.from_numpy(part.copy()).cuda()
         conn = [hfp.connectivity(hg, pd, 64)]
@@ -186,7 +190,9 @@ def kway_rounds(hfp, ctx, args):
         for _ in range(args.kway_rounds):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            if mode == "batched":
+            if mode == "batched" and world > 1:
+                st, _ = sharded.refine_round_sharded(hg, pd, 64, group_ctas=args.kway_group)
+            elif mode == "batched":
                 st, _, ms = hfp.refine_round_batched(hg, pd, 64, group_ctas=args.kway_group)
                 fc_ms.append(round(ms, 1))
             else:
@@ -304,6 +310,7 @@ def main():
         e2e_ms.append(1e3 * (time.perf_counter() - t0))
         net.close()
     e2e_value = world * p_pins / (statistics.mean(e2e_ms) / 1e3) if e2e_ms else None
+    kway = kway_rounds(hfp, ctx, args, world) if args.kway_rounds > 0 else None
 
     if rank != 0:
         return 0
@@ -340,8 +347,8 @@ def main():
             "clocks": clk, "roofline": roof,
             "engine": {"rounds": st["rounds"], "global_relabels": st["global_relabels"],
                        "gr_levels": st["gr_levels"], "pushes": st["pushes"]}}
-    if args.kway_rounds > 0:
-        line["kway"] = kway_rounds(hfp, ctx, args)
+    if kway is not None:
+        line["kway"] = kway
     if not args.no_cpu_baseline:
         sinst = synth.instance(WORKLOAD, args.seed, **SAMPLE)
         p, dt, _ = oracle_step(sinst)

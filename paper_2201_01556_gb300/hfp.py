@@ -504,9 +504,12 @@ def refine_pairs_batched(hg: HGraph, part_dev, k: int, pairs, params: RefinePara
     res = (PairResult * max(n, 1))()
     off = np.zeros(n + 1, np.int64)
     ms = ctypes.c_float()
-    cap = 0
+    # moves are region vertices whose block changes: the vertex count covers
+    # them unless vertices move in several pairs' regions at once; if not,
+    # the call reports the exact need and runs again
+    cap = max(int(hg.n), 1)
     for _ in range(2):
-        moves = np.zeros((max(cap, 1), 3), np.int32)
+        moves = np.empty((max(cap, 1), 3), np.int32)
         st = _check(load().hfp_refine_pairs_batched(hg.h, _ptr(part_dev), k, ctypes.byref(params),
                                                     _ptr(pr), n, group_ctas, res, _ptr(moves),
                                                     cap, _ptr(off), ctypes.byref(ms)),

@@ -209,17 +209,38 @@ hfp_status hfp_net_export(hfp_net* net, hfp_mem mem, uint32_t* net_off, int32_t*
                           int32_t* net_w, int32_t* net_gid, int32_t* node_w, uint32_t* node_off,
                           int32_t* inc_slot, int32_t* dist);
 hfp_status hfp_net_get_stats(hfp_net* net, hfp_stats* stats);
+/* Copies the network's current (pre)flow to caller buffers in `mem` memory
+ * (any pointer may be NULL to skip it), for checking it (Section 2,
+ * "Flows": capacity and conservation; Section 8.3, "Restricting
+ * Capacities": the cap f(u, e_in) <= w(e)):
+ *   f_in[p_pins]   flow on (u, e_in) of each pin slot, 0 <= f_in <= w(e);
+ *   f_out[p_pins]  flow on (e_out, u) of each pin slot, >= 0;
+ *   f_b[m_nets]    flow on the bridge (e_in, e_out), 0 <= f_b <= w(e);
+ *   excess[lawler_nodes]  excess of each non-terminal Lawler node (inflow -
+ *                  outflow once every push of the last round is applied;
+ *                  values of sources and sinks are not maintained);
+ *   delta[lawler_nodes]   pushes not yet applied to excess (all 0 once
+ *                  hfp_max_flow returned);
+ *   flags[lawler_nodes]   bit 0: node is in S, bit 1: node is in T.
+ * The flow value is the net inflow of T.  Per-arc flows are not unique;
+ * only the value and the minimal cuts are. */
+hfp_status hfp_net_export_flow(hfp_net* net, hfp_mem mem, int32_t* f_in, int32_t* f_out,
+                               int32_t* f_b, int64_t* excess, int64_t* delta, uint8_t* flags);
+
 
 /* --- tracing ----------------------------------------------------------------
- * hfp_net_enable_trace keeps a per-round trace of the next `rounds` discharge
- * rounds (allocates 16 bytes per round on the device).  hfp_net_get_trace
- * copies to host memory: state_ns[10] / state_cnt[10], the device time
- * (globaltimer) spent in, and the number of, engine phases of each state
- * (0 done, 1 push, 2 relabel/apply, 3/4 global relabel init/level, 5/6 S_r
- * init/level, 7/8 distance init/level); trace[2 * cap] pairs
- * (frontier << 32 | next-list size, flow value) per round; *n rounds
- * recorded. */
-hfp_status hfp_net_enable_trace(hfp_net* net, int32_t rounds);
+ * hfp_net_enable_trace keeps a trace of the next `phases` engine phases
+ * (allocates 32 bytes per phase on the device).  hfp_net_get_trace copies to
+ * host memory: state_ns[10] / state_cnt[10], the device time (globaltimer)
+ * spent in, and the number of, engine phases of each state (0 done, 1 push,
+ * 2 relabel/apply, 3/4 global relabel init/level, 5/6 S_r init/level, 7/8
+ * distance init/level, 9 phases run by one CTA); trace[4 * cap] holds four
+ * words per phase: (state | one_cta << 5) << 58 | light input << 29 | heavy
+ * input; light output << 32 | heavy output; the flow value; the phase's
+ * device time in ns.  The input is the frontier (push), the next list
+ * (relabel/apply) or the breadth-first-search level, the output the list the
+ * phase filled.  *n = phases recorded. */
+hfp_status hfp_net_enable_trace(hfp_net* net, int32_t phases);
 hfp_status hfp_net_get_trace(hfp_net* net, uint64_t* state_ns, uint64_t* state_cnt,
                              uint64_t* trace, int32_t cap, int32_t* n);
 
@@ -533,26 +554,29 @@ hfp_status hfp_pair_scores(hfp_hgraph* hg, const int32_t* part, int32_t k, int32
 
 /* --- allocation-free max flow ---------------------------------------------
  * The paper has no counterpart to this entry point; it exists for callers
- * that cannot allocate device memory where they need a flow: code inside a
- * CUDA stream capture, a plug-in bound to a host application's fixed
- * device-memory budget or allocator, a loop in which allocation is
- * forbidden.  It computes what hfp_max_flow + hfp_min_cut_source_side compute
- * for the flow problem {s} -> {t} of a network, with the same engine kernel,
- * but keeps all working state in one fixed static device array of 24 MiB
- * (library-wide, held by every GPU that loads the library until the process
- * exits).  It calls no cudaMalloc / cudaFree and no allocating library
- * routine.
+ * that cannot allocate device memory where they need a flow: a plug-in bound
+ * to a host application's fixed device-memory budget or allocator, or a
+ * loop in which allocation is forbidden (cudaMalloc may synchronise the
+ * device or fail under memory pressure).  It computes what hfp_max_flow +
+ * hfp_min_cut_source_side compute for the flow problem {s} -> {t} of a
+ * network, with the same engine kernel, but keeps all working state in one
+ * fixed static device array of 24 MiB (library-wide, held by every GPU that
+ * loads the library until the process exits).  It calls no cudaMalloc /
+ * cudaFree and no allocating library routine.
  *   net: the flow network in device memory, in the layout hfp_net_export
  *        writes (hypernode 0 = s, 1 = t).  It fits when
- *        47*L + 20*p + 4*m + ~4 KiB <= 24 MiB (L = n_nodes + 2*m_nets Lawler
+ *        47*L + 20*p + 4*m + 5 KiB <= 24 MiB (L = n_nodes + 2*m_nets Lawler
  *        nodes, p pins, m nets; e.g. L = 262,144 with p = 524,288);
- *        larger networks are rejected with HFP_ERR_INVALID.
+ *        larger networks are rejected with HFP_ERR_INVALID, and so are views
+ *        whose offsets or ids are out of range or whose incidence lists do
+ *        not name every pin slot of the node exactly once.
  *   flow_value, source_weight: host pointers (may be NULL);
  *   in_source_lawler[L]: device pointer (may be NULL), 1 for nodes of S_r.
  * The first call on a device looks up the array's device address (with that
- * device current); make that first call before any stream capture begins.
- * Every call shares the array and clears what it uses; calls that overlap on
- * the GPU race, so serialise them.  The call synchronises `stream`. */
+ * device current).  Every call shares the array and clears what it uses;
+ * calls that overlap on the GPU race, so serialise them.  The call
+ * synchronises `stream` and reads status words back to the host, so it
+ * cannot run inside a CUDA stream capture. */
 typedef struct {
   int32_t n_nodes;
   int32_t m_nets;

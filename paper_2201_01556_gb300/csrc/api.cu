@@ -572,6 +572,25 @@ HFP_API hfp_status hfp_net_export(hfp_net* net, hfp_mem mem, uint32_t* net_off, 
   return HFP_OK;
 }
 
+HFP_API hfp_status hfp_net_export_flow(hfp_net* net, hfp_mem mem, int32_t* f_in, int32_t* f_out,
+                                       int32_t* f_b, int64_t* excess, int64_t* delta,
+                                       uint8_t* flags) {
+  if (!net) return fail(HFP_ERR_INVALID, "net is NULL");
+  hfp_status s = set_device(net->ctx);
+  if (s != HFP_OK) return s;
+  cudaStream_t st = net->ctx->stream;
+  const NetDev& D = net->d;
+  const size_t p = (size_t)D.p_pins, m = (size_t)D.m_nets, nl = (size_t)D.NL;
+  if (f_in && (s = copy_out(f_in, D.f_in, sizeof(int32_t) * p, mem, st))) return s;
+  if (f_out && (s = copy_out(f_out, D.f_out, sizeof(int32_t) * p, mem, st))) return s;
+  if (f_b && (s = copy_out(f_b, D.f_b, sizeof(int32_t) * m, mem, st))) return s;
+  if (excess && (s = copy_out(excess, D.excess, sizeof(int64_t) * nl, mem, st))) return s;
+  if (delta && (s = copy_out(delta, D.delta, sizeof(int64_t) * nl, mem, st))) return s;
+  if (flags && (s = copy_out(flags, D.flags, nl, mem, st))) return s;
+  CK(cudaStreamSynchronize(st));
+  return HFP_OK;
+}
+
 HFP_API hfp_status hfp_net_get_stats(hfp_net* net, hfp_stats* out) {
   if (!net || !out) return fail(HFP_ERR_INVALID, "NULL argument");
   hfp_status s = set_device(net->ctx);
@@ -590,8 +609,8 @@ HFP_API hfp_status hfp_net_get_stats(hfp_net* net, hfp_stats* out) {
   return HFP_OK;
 }
 
-HFP_API hfp_status hfp_net_enable_trace(hfp_net* net, int32_t rounds) {
-  if (!net || rounds < 0) return fail(HFP_ERR_INVALID, "bad trace arguments");
+HFP_API hfp_status hfp_net_enable_trace(hfp_net* net, int32_t phases) {
+  if (!net || phases < 0) return fail(HFP_ERR_INVALID, "bad trace arguments");
   hfp_status s = set_device(net->ctx);
   if (s != HFP_OK) return s;
   cudaStream_t st = net->ctx->stream;
@@ -599,10 +618,10 @@ HFP_API hfp_status hfp_net_enable_trace(hfp_net* net, int32_t rounds) {
   net->trace_buf = nullptr;
   net->d.trace = nullptr;
   net->d.trace_cap = 0;
-  if (rounds > 0) {
-    CK(cudaMallocAsync(&net->trace_buf, sizeof(unsigned long long) * 2 * (size_t)rounds, st));
+  if (phases > 0) {
+    CK(cudaMallocAsync(&net->trace_buf, sizeof(unsigned long long) * 4 * (size_t)phases, st));
     net->d.trace = (unsigned long long*)net->trace_buf;
-    net->d.trace_cap = (unsigned)rounds;
+    net->d.trace_cap = (unsigned)phases;
   }
   CK(cudaMemsetAsync(&net->E->c.trace_len, 0, sizeof(unsigned long long), st));
   CK(cudaStreamSynchronize(st));
@@ -622,7 +641,7 @@ HFP_API hfp_status hfp_net_get_trace(hfp_net* net, uint64_t* state_ns, uint64_t*
   if (n) *n = len;
   if (trace && cap > 0 && len > 0 && net->trace_buf) {
     int32_t k = len < cap ? len : cap;
-    CK(cudaMemcpy(trace, net->trace_buf, sizeof(unsigned long long) * 2 * (size_t)k,
+    CK(cudaMemcpy(trace, net->trace_buf, sizeof(unsigned long long) * 4 * (size_t)k,
                   cudaMemcpyDeviceToHost));
   }
   return HFP_OK;

@@ -135,6 +135,7 @@ def load():
         "hfp_net_destroy": (None, [P]),
         "hfp_net_get_info": (i32, [P, ctypes.POINTER(_NetInfo)]),
         "hfp_net_export": (i32, [P, i32, P, P, P, P, P, P, P, P]),
+        "hfp_net_export_flow": (i32, [P, i32, P, P, P, P, P, P]),
         "hfp_net_get_stats": (i32, [P, ctypes.POINTER(_Stats)]),
         "hfp_max_flow": (i32, [P, P]),
         "hfp_min_cut_source_side": (i32, [P, i32, P, P, P, i32, P, P]),
@@ -310,6 +311,19 @@ def net_export(net: Net) -> dict:
     return out
 
 
+def net_export_flow(net: Net) -> dict:
+    """hfp_net_export_flow to host numpy arrays: per-arc flows, excess,
+    pending deltas and terminal flags."""
+    i = net.info
+    out = dict(f_in=np.zeros(i.p_pins, np.int32), f_out=np.zeros(i.p_pins, np.int32),
+               f_b=np.zeros(i.m_nets, np.int32), excess=np.zeros(i.lawler_nodes, np.int64),
+               delta=np.zeros(i.lawler_nodes, np.int64), flags=np.zeros(i.lawler_nodes, np.uint8))
+    _check(load().hfp_net_export_flow(net.h, MEM_HOST, *[_ptr(out[k]) for k in
+                                                         ("f_in", "f_out", "f_b", "excess",
+                                                          "delta", "flags")]))
+    return out
+
+
 def net_export_device(net: Net) -> dict:
     """hfp_net_export into CUDA int32 tensors (the layout hfp_max_flow_noalloc
     reads)."""
@@ -344,26 +358,34 @@ STATE_NAMES = ("done", "push", "relabel", "gr_init", "gr_level", "sr_init", "sr_
                "dist_init", "dist_level", "other")
 
 
-def net_enable_trace(net: Net, rounds: int):
-    """hfp_net_enable_trace."""
-    _check(load().hfp_net_enable_trace(net.h, rounds))
+def net_enable_trace(net: Net, phases: int):
+    """hfp_net_enable_trace: record the next `phases` engine phases."""
+    _check(load().hfp_net_enable_trace(net.h, phases))
 
 
 def net_trace(net: Net, cap: int = 0) -> dict:
     """hfp_net_get_trace -> per-state device time and counts, and the
-    per-round (frontier, next-list size, flow) trace."""
+    per-phase trace (state, CTA-alone flag, input and output list sizes,
+    flow value, device time)."""
     ns = np.zeros(10, np.uint64)
     cnt = np.zeros(10, np.uint64)
-    buf = np.zeros(max(2 * cap, 2), np.uint64)
+    buf = np.zeros(max(4 * cap, 4), np.uint64)
     n = ctypes.c_int32()
     _check(load().hfp_net_get_trace(net.h, _ptr(ns), _ptr(cnt), _ptr(buf), cap, ctypes.byref(n)))
     k = min(n.value, cap)
-    tr = buf[: 2 * k].reshape(-1, 2)
+    tr = buf[: 4 * k].reshape(-1, 4)
+    w0 = tr[:, 0]
+    m29 = np.uint64((1 << 29) - 1)
     return dict(state_ns={STATE_NAMES[i]: int(ns[i]) for i in range(10)},
                 state_cnt={STATE_NAMES[i]: int(cnt[i]) for i in range(10)},
-                rounds=int(n.value), frontier=(tr[:, 0] >> np.uint64(32)).astype(np.int64),
-                next=(tr[:, 0] & np.uint64(0xFFFFFFFF)).astype(np.int64),
-                flow=tr[:, 1].astype(np.int64))
+                phases=int(n.value),
+                state=((w0 >> np.uint64(58)) & np.uint64(31)).astype(np.int64),
+                solo=((w0 >> np.uint64(63)) & np.uint64(1)).astype(np.int64),
+                light_in=((w0 >> np.uint64(29)) & m29).astype(np.int64),
+                heavy_in=(w0 & m29).astype(np.int64),
+                light_out=(tr[:, 1] >> np.uint64(32)).astype(np.int64),
+                heavy_out=(tr[:, 1] & np.uint64(0xFFFFFFFF)).astype(np.int64),
+                flow=tr[:, 2].astype(np.int64), ns=tr[:, 3].astype(np.int64))
 
 
 class HGraph:

@@ -10,6 +10,7 @@ import pytest
 
 import oracle
 import synth
+from tests.flowcheck import check_preflow
 from tests.helpers import hypergraph_from_lists, load_golden, random_instance
 
 pytestmark = pytest.mark.gpu
@@ -62,10 +63,20 @@ def _check_structure(hfp, gnet, onet, H, side, region):
     assert np.array_equal(ex["dist"][2:], d)
 
 
+def _check_feasible(hfp, gnet, flow):
+    """The device's per-arc preflow: capacities (with the (u, e_in) cap),
+    conservation and value (per-arc flows are not unique, so they are
+    checked, not compared)."""
+    ex = hfp.net_export(gnet)
+    check_preflow(gnet.info.n_nodes, ex["net_off"], ex["pins"], ex["net_w"],
+                  hfp.net_export_flow(gnet), flow)
+
+
 def _check_flow(hfp, gnet, onet):
     mc = oracle.max_flow_min_cut(onet)
     flow = hfp.max_flow(gnet)
     assert flow == mc.flow
+    _check_feasible(hfp, gnet, flow)
     law, reg, cuts, ws = hfp.min_cut_source_side(gnet)
     assert np.array_equal(law, mc.source_side)
     assert np.array_equal(reg, mc.source_side[2:onet.n_nodes])
@@ -225,6 +236,8 @@ def _fc_compare(hfp, ctx, H, side, region, eps_pct=3, seed=0, dist_given=False):
     gnet = _gpu_net(hfp, ctx, H, side, region, dist=dist if dist_given else None)
     r = hfp.flowcutter(gnet, hfp.fc_params(L, seed=seed))
     assert r.status == o.status
+    if r.status in (oracle.OK, oracle.NO_BALANCED_CUT):
+        _check_feasible(hfp, gnet, o.flow)
     assert np.array_equal(r.pierce_side, o.pierce_side)
     assert np.array_equal(r.pierce_node, o.pierce_node)
     if o.status == oracle.OK:
@@ -285,6 +298,7 @@ def test_pierce_and_augment_explicit(hfp, ctx):
             G.augment(S, T)
             _, flow = hfp.pierce_and_augment(gnet, side_, [p])
             assert flow == G.flow_value(S)
+            _check_feasible(hfp, gnet, flow)
             law, _, _, _ = hfp.min_cut_source_side(gnet)
             assert np.array_equal(law, G.reach_from(S))
             tlaw, _, _ = hfp.min_cut_sink_side(gnet)
@@ -292,6 +306,29 @@ def test_pierce_and_augment_explicit(hfp, ctx):
             checked += 1
         gnet.close()
     assert checked > 150
+
+
+PIERCING = load_golden("piercing_order.json")["cases"]
+
+
+@pytest.mark.parametrize("c", PIERCING, ids=[c["name"] for c in PIERCING])
+def test_piercing_order_hand_cases(hfp, ctx, c):
+    """The hand-worked piercing cases (each key of Section 7 "Piercing"
+    decides one of them) through hfp_flowcutter, distances given."""
+    H = hypergraph_from_lists(6, c["nets"], c["net_w"], c["node_w"])
+    side = np.array(c["side"], np.int32)
+    region = np.array(c["region"], np.int32)
+    gnet = _gpu_net(hfp, ctx, H, side, region, dist=np.array(c["dist"], np.int32))
+    r = hfp.flowcutter(gnet, hfp.fc_params(c["max_block_weight"], seed=c["seed"]))
+    e = c["expected"]
+    assert r.status == 0
+    assert r.pierce_side.tolist() == e["pierce_side"]
+    assert r.pierce_node.tolist() == e["pierce_node"]
+    assert r.final_side.tolist() == e["final_side"][2:]
+    assert (r.flow, r.source_weight, r.result_side, r.iterations) == \
+        (e["flow"], e["source_weight"], e["result_side"], e["iterations"])
+    _check_feasible(hfp, gnet, r.flow)
+    gnet.close()
 
 
 def test_deterministic_runs(hfp, ctx):
@@ -306,3 +343,24 @@ def test_deterministic_runs(hfp, ctx):
         runs.append((f, law.tobytes(), st["rounds"], st["pushes"], st["global_relabels"]))
         gnet.close()
     assert runs[0] == runs[1] == runs[2]
+
+
+def test_round_budget_trips_and_context_stays_usable(hfp):
+    """A bounded device loop that runs out returns HFP_ERR_ITER_LIMIT (no
+    trap, no hang), and the same context then computes a normal flow."""
+    c = hfp.ctx_create(0)
+    inst = synth.instance("ring_n4096_geom", 3)
+    H, part, region = inst["H"], inst["part"], inst["region"]
+    onet = oracle.build_network(H, part, region)
+    default = hfp.ctx_get_tuning(c)
+    hfp.ctx_set_tuning(c, max_rounds=1)
+    gnet = _gpu_net(hfp, c, H, part, region)
+    with pytest.raises(hfp.HfpError) as e:
+        hfp.max_flow(gnet)
+    assert e.value.status == hfp.ERR_ITER_LIMIT
+    gnet.close()
+    hfp.ctx_set_tuning(c, **default)
+    gnet = _gpu_net(hfp, c, H, part, region)
+    _check_flow(hfp, gnet, onet)
+    gnet.close()
+    c.close()

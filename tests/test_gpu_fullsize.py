@@ -12,6 +12,7 @@ import numpy as np
 import pytest
 
 import synth
+from tests.flowcheck import check_preflow
 
 pytestmark = pytest.mark.gpu
 
@@ -62,6 +63,9 @@ def test_ring_2M_max_flow_and_cuts(hfp_ctx):
     ex = hfp.net_export(net)
     gid_w = dict(zip(ex["net_gid"].tolist(), ex["net_w"].tolist()))
     assert sum(gid_w[e] for e in cuts.tolist()) == g["flow"]
+    # the device's per-arc preflow is feasible and carries the value
+    check_preflow(net.info.n_nodes, ex["net_off"], ex["pins"], ex["net_w"],
+                  hfp.net_export_flow(net), g["flow"])
 
 
 def test_ring_500k_flowcutter(hfp_ctx):

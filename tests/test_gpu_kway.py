@@ -83,3 +83,36 @@ def test_round_skips_low_scores(env):
     assert stats.pairs_skipped > 0
     newp, total, _, _ = oracle.refine_round(H, part, 64, pairs=[(p.bi, p.bj) for p in pres])
     assert np.array_equal(pd.cpu().numpy(), newp) and stats.gain == total
+
+
+def _km1_host(H, part):
+    """(lambda - 1) recomputed from scratch on the host (Section 2): one
+    64-bit block mask per net, its population count minus one, times w(e)."""
+    bits = np.left_shift(np.uint64(1), part[H.pins].astype(np.uint64))
+    off = H.net_off.astype(np.int64)
+    masks = np.bitwise_or.reduceat(bits, off[:-1])
+    masks[off[1:] == off[:-1]] = 0
+    lam = np.array([bin(int(x)).count("1") for x in masks], np.int64) if masks.size < 10 \
+        else np.unpackbits(masks.view(np.uint8).reshape(-1, 8), axis=1).sum(1).astype(np.int64)
+    return int((np.maximum(lam - 1, 0) * H.net_w.astype(np.int64)).sum())
+
+
+def test_round_certificate_1M(env):
+    """A batched round at n = 1,000,000, k = 64 (too large for the oracle's
+    round): the returned partition's (lambda - 1), recomputed on the host,
+    equals connectivity_after and connectivity_before - gain; every applied
+    move set has a non-negative actual gain (Section 5, "Apply Moves")."""
+    torch, hfp, ctx = env
+    n = 1_000_000
+    H, part, hg, pd = _setup(env, 1, n, n * 3 // 2)
+    before = _km1_host(H, part)
+    stats, pres, _ = hfp.refine_round_batched(hg, pd, 64, group_ctas=4)
+    after = _km1_host(H, pd.cpu().numpy())
+    assert stats.connectivity_before == before
+    assert stats.connectivity_after == after
+    assert after == before - stats.gain
+    assert stats.gain > 0
+    applied = [p for p in pres if p.applied]
+    assert applied and all(p.gain >= 0 for p in applied)
+    assert sum(p.gain for p in applied) == stats.gain
+    hg.close()

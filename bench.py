@@ -42,7 +42,7 @@ L2_BYTES = 129 * 1024 * 1024
 # Oracle sample: the same generator at 1/10 scale (about 10-30 s of CPU work).
 SAMPLE = dict(n=200_000, m=300_000, radius=20_000)
 
-# algorithmic bytes per counted item of the engine (roofline)
+# algorithmic bytes per counted item of the engine (the roofline model)
 B_HYPER = 28   # incidence (8) + w(e) (4) + f_in (4) + f_out (4) + two labels (8)
 B_NET = 12     # pin (4) + pin flow (4) + label (4)
 B_NODE = 24    # list entry (4) + label (4) + excess (8) + delta (8)

@@ -177,8 +177,7 @@ __device__ void begin_gr(Sched& L) {
   L.wT_set = 1;
 }
 
-__device__ void advance(Sched& L, const Snap& q, const Params& P, const NetDev& N, Ctl* c,
-                        bool trace_writer) {
+__device__ void advance(Sched& L, const Snap& q, const Params& P, const NetDev& N, Ctl* c) {
   switch (L.state) {
     case ST_ROUND_A:
       L.ncnt = q.c[C_NEXT];
@@ -188,12 +187,6 @@ __device__ void advance(Sched& L, const Snap& q, const Params& P, const NetDev& 
       break;
     case ST_ROUND_B: {
       const unsigned fprev = L.fcnt + L.fcnth, nprev = L.ncnt + L.ncnth;
-      if (trace_writer && N.trace && c->trace_len < N.trace_cap) {
-        // round trace: (frontier size << 32 | next-list size), flow value
-        N.trace[2 * c->trace_len] = ((unsigned long long)fprev << 32) | nprev;
-        N.trace[2 * c->trace_len + 1] = L.flow;
-        c->trace_len++;
-      }
       L.rounds++;
       L.work += (unsigned long long)fprev + nprev;
       L.fcnt = q.c[C_FRONT];
@@ -1150,12 +1143,43 @@ struct Clock {
   unsigned long long ns[10], cnt[10];
 };
 
-__device__ __forceinline__ void tick(Clock& ck, int st) {
+// Returns the device time of the phase that just ended.
+__device__ __forceinline__ unsigned long long tick(Clock& ck, int st) {
   const unsigned long long t = globaltimer();
+  const unsigned long long dt = t - ck.t_last;
   st = st < 10 ? st : 9;
-  ck.ns[st] += t - ck.t_last;
+  ck.ns[st] += dt;
   ck.cnt[st]++;
   ck.t_last = t;
+  return dt;
+}
+
+// Phase trace (when enabled): four words per phase,
+//   (state | solo << 5) << 58 | light input << 29 | heavy input,
+//   light output << 32 | heavy output, flow value, device time (ns).
+// Inputs are the frontier (push), the next list (relabel/apply) or the BFS
+// level; outputs the list the phase appended to.  Counts are clipped to 29 /
+// 32 bits.
+__device__ void trace_phase(const NetDev& N, Ctl* c, const Sched& L, int st, bool solo,
+                            const Snap& q, unsigned long long dt) {
+  if (!N.trace || c->trace_len >= N.trace_cap) return;
+  unsigned long long a = 0, b = 0, oa = 0, ob = 0;
+  if (st == ST_ROUND_A) {
+    a = L.fcnt; b = L.fcnth; oa = q.c[C_NEXT]; ob = q.c[C_NEXTH];
+  } else if (st == ST_ROUND_B) {
+    a = L.ncnt; b = L.ncnth; oa = q.c[C_FRONT]; ob = q.c[C_FRONTH];
+  } else {
+    a = L.bfs_end - L.bfs_begin; b = L.bfsh_end - L.bfsh_begin;
+    oa = q.c[C_BFS]; ob = q.c[C_BFSH];
+  }
+  const unsigned long long m29 = (1ull << 29) - 1;
+  unsigned long long* w = N.trace + 4 * c->trace_len;
+  w[0] = ((unsigned long long)((st & 31) | (solo ? 32 : 0)) << 58) | (min(a, m29) << 29) |
+         min(b, m29);
+  w[1] = (min(oa, 0xffffffffull) << 32) | min(ob, 0xffffffffull);
+  w[2] = L.flow;
+  w[3] = dt;
+  c->trace_len++;
 }
 
 __device__ __forceinline__ bool is_level(int st) {
@@ -1216,9 +1240,10 @@ __device__ void solo_phases(const NetDev& N, EngineCtl* E, const Params& P, Sche
       *w_sh = 0;
       q.key = 0;
       q.node = -1;
-      tick(ck, ST_TAIL);
+      const unsigned long long dt = tick(ck, ST_TAIL);
       const int s1 = L.state;
-      advance(L, q, P, N, &E->c, true);
+      trace_phase(N, &E->c, L, s1, true, q, dt);
+      advance(L, q, P, N, &E->c);
       L.phase++;
       const int s2 = L.state;
       bool stay;
@@ -1374,8 +1399,8 @@ __global__ void __launch_bounds__(kEngineThreads) engine_kernel(NetDev N, Engine
         L.state = ST_DONE;
       } else {
         const Snap q = take_snap(E, L.phase);
-        if (cta0) tick(ck, st);
-        advance(L, q, P, N, &E->c, cta0);
+        if (cta0) trace_phase(N, &E->c, L, st, false, q, tick(ck, st));
+        advance(L, q, P, N, &E->c);
         L.phase++;
       }
     }

@@ -509,7 +509,7 @@ __device__ void fc_run_job(FcJob* job, const Params& P0, int rank, int G, unsign
       } else {
         const Snap q = take_snap(E, L.phase);
         if (is_fc_state(st)) fc_advance(L, F, q, *job, P, lead);
-        else advance(L, q, P, N, &E->c, lead);
+        else advance(L, q, P, N, &E->c);
         L.phase++;
         if (L.state == ST_DONE && !F.finished) fc_on_done(L, F, *job, &E->c);
       }

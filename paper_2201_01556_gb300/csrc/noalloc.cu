@@ -1,14 +1,16 @@
 // Allocation-free maximum flow and minimal source-side cut.
 //
 // Some callers cannot allocate device memory at the point where they need a
-// flow: code running inside a CUDA stream capture, a plug-in that must stay
-// within a host application's fixed device-memory budget or custom
-// allocator, or a latency-critical loop in which allocation is not allowed.
-// hfp_max_flow_noalloc serves them: it runs the same engine kernel as
-// hfp_max_flow / hfp_min_cut_source_side, but all of its working state lives
-// in one file-scope __device__ array of fixed size, so the call itself never
-// allocates or frees memory.  The caller passes the flow network (in the
-// layout hfp_net_export writes) and the output buffers.
+// flow: a plug-in that must stay within a host application's fixed
+// device-memory budget or custom allocator, or a latency-critical loop in
+// which allocation is not allowed (cudaMalloc can synchronise the device or
+// fail under memory pressure).  hfp_max_flow_noalloc serves them: it runs
+// the same engine kernel as hfp_max_flow / hfp_min_cut_source_side, but all
+// of its working state lives in one file-scope __device__ array of fixed
+// size, so the call itself never allocates or frees memory.  The caller
+// passes the flow network (in the layout hfp_net_export writes) and the
+// output buffers.  The call synchronises its stream and reads two status
+// words back to the host, so it cannot be recorded into a CUDA graph.
 //
 // The array is part of the library image: every GPU that loads the library
 // holds it until the process exits.  Each call clears the part it uses.
@@ -59,24 +61,47 @@ size_t static_bytes(int64_t NL, int64_t m, int64_t p) {
 
 }  // namespace
 
-// bounds of the caller's network; err[0] = 1 on any violation
+// Bounds and consistency of the caller's network; err[0] = 1 on any
+// violation.  Every incidence entry of hypernode u must name a pin slot
+// holding u, and every slot must be named once (mark[] counts, zeroed by the
+// caller; k_static_check_marks reads them).  Offsets are validated before
+// they index anything.
 __global__ void k_static_check(int32_t n, int32_t m, long long p, const uint32_t* net_off,
                                const int32_t* pins, const int32_t* net_w, const uint32_t* node_off,
-                               const int32_t* inc_slot, const int32_t* node_w, int* err) {
+                               const int32_t* inc_slot, const int32_t* node_w, int* mark,
+                               int* err) {
   const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long nth = (long long)gridDim.x * blockDim.x;
   if (tid == 0 && (net_off[0] != 0 || (long long)net_off[m] != p || node_off[0] != 0 ||
                    (long long)node_off[n] != p))
     err[0] = 1;
   for (long long e = tid; e < m; e += nth)
-    if (net_off[e + 1] < net_off[e] || net_w[e] <= 0) err[0] = 1;
-  for (long long u = tid; u < n; u += nth)
-    if (node_off[u + 1] < node_off[u] || node_w[u] < 0) err[0] = 1;
+    if (net_off[e + 1] < net_off[e] || (long long)net_off[e + 1] > p || net_w[e] <= 0) err[0] = 1;
   for (long long j = tid; j < p; j += nth) {
-    int v = pins[j];
-    int s = inc_slot[j];
+    const int v = pins[j];
+    const int s = inc_slot[j];
     if (v < 0 || v >= n || s < 0 || (long long)s >= p) err[0] = 1;
   }
+  for (long long u = tid; u < n; u += nth) {
+    const uint32_t b = node_off[u], e = node_off[u + 1];
+    if (e < b || (long long)e > p || node_w[u] < 0) {
+      err[0] = 1;
+      continue;
+    }
+    for (uint32_t j = b; j < e; j++) {
+      const int s = inc_slot[j];
+      if (s < 0 || (long long)s >= p) continue;   // reported above
+      if (pins[s] != (int)u) err[0] = 1;
+      atomicAdd(&mark[s], 1);
+    }
+  }
+}
+
+// every pin slot named by exactly one incidence entry
+__global__ void k_static_check_marks(long long p, const int* mark, int* err) {
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < p;
+       j += (long long)gridDim.x * blockDim.x)
+    if (mark[j] != 1) err[0] = 1;
 }
 
 // slot -> net of the caller's net CSR, warp per net
@@ -213,9 +238,11 @@ extern "C" __attribute__((visibility("default"))) hfp_status hfp_max_flow_noallo
 
   // the array keeps the previous call's contents: clear everything used
   CKS(cudaMemsetAsync(dev.scratch, 0, used, st));
+  // slot_net doubles as the slot marks of the check (zeroed above, refilled below)
   k_static_check<<<256, 256, 0, st>>>(D.n_nodes, D.m_nets, p, v->net_off, v->pins, v->net_w,
-                                      v->node_off, v->inc_slot, v->node_w, misc);
-  count_launches(1);
+                                      v->node_off, v->inc_slot, v->node_w, slot_net, misc);
+  k_static_check_marks<<<256, 256, 0, st>>>(p, slot_net, misc);
+  count_launches(2);
   int herr = 0;
   CKS(cudaMemcpyAsync(&herr, misc, sizeof(int), cudaMemcpyDeviceToHost, st));
   CKS(cudaStreamSynchronize(st));

@@ -94,6 +94,8 @@ typedef struct {
   uint64_t pushes;
   uint64_t engine_launches;  /* cooperative launches of the engine kernel */
   uint64_t engine_ns;        /* device time of those launches (CUDA events on the context stream) */
+  uint64_t gr_queue_entries; /* queue entries of the queue-driven global relabels */
+  uint64_t gr_queue_overflows;  /* such relabels redone level by level (queue full) */
 } hfp_stats;
 
 /* FlowCutter parameters (Section 7). */
@@ -150,6 +152,11 @@ uint64_t hfp_kernel_launches(void);
  *                 after a piercing; 0: adaptive, as many rounds as the last
  *                 global relabel had levels (at least 8, at most
  *                 stall_rounds) [0]
+ *   async_gr      global relabels of hfp_max_flow / hfp_flowcutter as one
+ *                 label-correcting search driven by a device work queue,
+ *                 without a grid barrier per breadth-first level; the labels
+ *                 are the same exact distances [1]
+ *   gr_warps      warps per CTA that serve that queue (1..16) [8]
  *   batch_cluster  batched FlowCutter: launch groups of at most 16 CTAs as
  *                 thread-block clusters (group barriers in distributed
  *                 shared memory) when as many such clusters can be resident
@@ -174,6 +181,8 @@ typedef struct {
   uint32_t batch_cluster;
   uint32_t batch_big_ctas;
   uint32_t batch_big_groups;
+  uint32_t async_gr;
+  uint32_t gr_warps;
 } hfp_tuning;
 hfp_status hfp_ctx_get_tuning(hfp_ctx* ctx, hfp_tuning* tuning);
 hfp_status hfp_ctx_set_tuning(hfp_ctx* ctx, const hfp_tuning* tuning);

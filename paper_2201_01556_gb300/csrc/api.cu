@@ -210,6 +210,8 @@ HFP_API hfp_status hfp_ctx_create(hfp_ctx** out, int device, void* stream) {
   c->params.pierce_relabel = 0;
   c->params.stall_rounds_pierce = 0;    // incremental flows after a piercing: adaptive
   c->params.stall_adapt = 0;
+  c->params.async_gr = 1;          // global relabels as one queue-driven search
+  c->params.gr_warps = 8;          // warps per CTA serving its queue (fewer: less re-expansion)
   *out = c;
   return HFP_OK;
 }
@@ -392,6 +394,14 @@ HFP_API hfp_status hfp_build_flow_network(hfp_ctx* ctx, const hfp_hypergraph* H,
   // W of the flow problem: c(s) + c(t) + c(B)
   const int64_t total_w = (int64_t)hh->wsum[0] + (int64_t)hh->wsum[1] + (int64_t)hh->wsum[4];
 
+  // work queue of the asynchronous global relabel: room for every node's
+  // chunks twice (a node is queued again whenever its label drops); a fuller
+  // queue makes that relabel fall back to the level-by-level search
+  const uint64_t gq_cap64 = 2 * ((uint64_t)NL + (uint64_t)p_net / 8) + 4096;
+  // (entries hold 27-bit Lawler ids: larger networks relabel level by level)
+  const unsigned gq_cap =
+      NL64 >= (1ll << 27) - 1 ? 0u : (gq_cap64 < 0xF0000000ull ? (unsigned)gq_cap64 : 0xF0000000u);
+
   // arena for the network and its flow state
   hfp_net* net = new hfp_net();
   net->ctx = ctx;
@@ -404,7 +414,8 @@ HFP_API hfp_status hfp_build_flow_network(hfp_ctx* ctx, const hfp_hypergraph* H,
       sizeof(int32_t) * p_net, sizeof(int32_t) * p_net, sizeof(int32_t) * m_net,
       sizeof(int32_t) * NL, sizeof(int32_t) * NL, sizeof(long long) * NL, sizeof(long long) * NL,
       sizeof(uint32_t) * NL, (size_t)NL, (size_t)NL, (size_t)NL, sizeof(int32_t) * NL,
-      sizeof(int32_t) * NL, sizeof(int32_t) * NL, sizeof(int32_t) * NL, sizeof(EngineCtl)};
+      sizeof(int32_t) * NL, sizeof(int32_t) * NL, sizeof(int32_t) * NL, sizeof(EngineCtl),
+      sizeof(unsigned long long) * gq_cap};
   size_t total = 0;
   for (size_t b : sz) total += align_up(b);
   cudaError_t ae = cudaMallocAsync(&net->arena, total, st);
@@ -458,6 +469,8 @@ HFP_API hfp_status hfp_build_flow_network(hfp_ctx* ctx, const hfp_hypergraph* H,
   D.insr = (uint8_t*)ptr[20];
   for (int k = 0; k < 4; k++) D.list[k] = (int32_t*)ptr[21 + k];
   net->E = (EngineCtl*)ptr[25];
+  D.gq = gq_cap ? (unsigned long long*)ptr[26] : nullptr;
+  D.gq_cap = gq_cap;
   net->total_w = total_w;
 
   hfp_status rs = HFP_OK;
@@ -476,6 +489,7 @@ HFP_API hfp_status hfp_build_flow_network(hfp_ctx* ctx, const hfp_hypergraph* H,
   CKN(cudaMemcpyAsync(node_w, a_w, sizeof(int32_t) * n_nodes, cudaMemcpyDeviceToDevice, st));
   CKN(cudaMemcpyAsync(node_orig, a_orig, n_nodes, cudaMemcpyDeviceToDevice, st));
   CKN(cudaMemsetAsync(D.flags, 0, NL, st));
+  if (gq_cap) CKN(cudaMemsetAsync(D.gq, 0, sizeof(unsigned long long) * gq_cap, st));   // empty slots
   launch_st_attrs(node_gid, node_w, node_orig, wsum.as<unsigned long long>(), D.flags,
                   err.as<int>(), st);
   launch_net_fill(m, d_off, d_pins, d_netw, loc.as<int32_t>(), keep.as<unsigned>(),
@@ -600,6 +614,8 @@ HFP_API hfp_status hfp_net_get_stats(hfp_net* net, hfp_stats* out) {
   out->rounds = c.rounds;
   out->global_relabels = c.global_relabels;
   out->gr_levels = c.gr_levels;
+  out->gr_queue_entries = c.gq_items;
+  out->gr_queue_overflows = c.gq_overs;
   out->items_hyper = c.items_hyper;
   out->items_net = c.items_net;
   out->node_visits = c.node_visits;
@@ -667,6 +683,8 @@ HFP_API hfp_status hfp_ctx_get_tuning(hfp_ctx* ctx, hfp_tuning* t) {
   t->bfs_exit = ctx->params.bfs_exit;
   t->pierce_relabel = ctx->params.pierce_relabel;
   t->stall_rounds_pierce = (uint32_t)ctx->params.stall_rounds_pierce;
+  t->async_gr = ctx->params.async_gr;
+  t->gr_warps = ctx->params.gr_warps;
   t->batch_cluster = ctx->batch_cluster;
   t->batch_big_ctas = ctx->batch_big_ctas;
   t->batch_big_groups = ctx->batch_big_groups;
@@ -688,6 +706,8 @@ HFP_API hfp_status hfp_ctx_set_tuning(hfp_ctx* ctx, const hfp_tuning* t) {
   ctx->params.bfs_exit = t->bfs_exit;
   ctx->params.pierce_relabel = t->pierce_relabel ? 1 : 0;
   ctx->params.stall_rounds_pierce = t->stall_rounds_pierce;
+  ctx->params.async_gr = t->async_gr ? 1 : 0;
+  ctx->params.gr_warps = t->gr_warps < 1 ? 1 : (t->gr_warps > 16 ? 16 : t->gr_warps);
   ctx->batch_cluster = t->batch_cluster ? 1 : 0;
   ctx->batch_big_ctas = t->batch_big_ctas;
   ctx->batch_big_groups = t->batch_big_groups;

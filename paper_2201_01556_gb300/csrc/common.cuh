@@ -58,8 +58,10 @@ struct NetDev {
   uint8_t* needrl;
   uint8_t* insr;                // forward residual reachability (S_r)
   int32_t* list[4];             // frontier, next, relabeled, BFS lists (NL each)
-  unsigned long long* trace;    // per-round trace (2 words per round), may be null
-  unsigned int trace_cap;       // rounds the trace can hold
+  unsigned long long* trace;    // per-phase trace (4 words per phase), may be null
+  unsigned int trace_cap;       // phases the trace can hold
+  unsigned int gq_cap;          // entries of gq
+  unsigned long long* gq;       // work queue of the asynchronous global relabel (may be null)
 };
 
 struct Ctl {
@@ -81,6 +83,8 @@ struct Ctl {
   unsigned long long state_ns[10];
   unsigned long long state_cnt[10];
   unsigned long long trace_len;   // entries written to the round trace
+  unsigned long long gq_items;    // asynchronous global relabels: queue entries expanded
+  unsigned long long gq_overs;    // ... and relabels redone level by level (queue full)
 };
 
 __device__ __forceinline__ unsigned long long globaltimer() {
@@ -93,6 +97,16 @@ __device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p) {
   unsigned int v;
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
+}
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
 __device__ __forceinline__ void st_release(unsigned int* p, unsigned int v) {

@@ -158,6 +158,8 @@ struct Snap {
   long long w;
   unsigned long long key;
   int node;
+  unsigned gq_over, gq_maxd;   // asynchronous global relabel: overflow, largest label
+  unsigned gq_tail;            // ... and the entries it queued
 };
 
 // Rounds without flow change before a global relabel (Section 8.3, "Avoid
@@ -175,6 +177,24 @@ __device__ void begin_gr(Sched& L) {
   L.state = ST_GR_INIT;
   L.wT = 0;
   L.wT_set = 1;
+}
+
+// End of a global relabel with `levels` breadth-first levels: the active
+// nodes it found form the frontier; labels are exact distances.
+__device__ __forceinline__ void end_gr(Sched& L, const Snap& q, const Params& P, unsigned levels) {
+  L.last_gr = levels;
+  L.gr_sync = 0;
+  L.fcnt = q.act;
+  L.fcnth = q.acth;
+  L.rcnt = 0;
+  L.lp = 0;
+  L.epoch++;
+  L.work = 0;
+  L.stall = 0;
+  L.flow_ref = L.flow;
+  const unsigned f = L.fcnt + L.fcnth;
+  if (f == 0 || L.after_gr_exit) L.state = ST_DONE;
+  else L.state = f <= P.tail_enter ? ST_TAIL : ST_ROUND_A;
 }
 
 __device__ void advance(Sched& L, const Snap& q, const Params& P, const NetDev& N, Ctl* c) {
@@ -213,6 +233,24 @@ __device__ void advance(Sched& L, const Snap& q, const Params& P, const NetDev& 
       }
       break;
     }
+    case ST_GR_SEED:
+      L.state = ST_GR_RUN;
+      break;
+    case ST_GR_RUN:
+      L.gq_items += q.gq_tail;
+      L.gq_prev = q.gq_tail;
+      if (q.gq_over) {
+        L.gq_overs++;
+        // the queue overflowed: redo this global relabel level by level
+        L.gr_sync = 1;
+        L.wT = 0;
+        L.state = ST_GR_INIT;
+      } else {
+        L.gr_levels += (unsigned long long)q.gq_maxd + 1;
+        L.wT += q.w;
+        end_gr(L, q, P, q.gq_maxd + 1);
+      }
+      break;
     case ST_GR_INIT:
     case ST_GR_ADD:
     case ST_SR_INIT:
@@ -225,6 +263,10 @@ __device__ void advance(Sched& L, const Snap& q, const Params& P, const NetDev& 
       L.level = 0;
       if (L.state == ST_GR_INIT || L.state == ST_GR_ADD) L.wT += q.w;
       if (L.state == ST_SR_INIT || L.state == ST_SR_ADD) L.wS += q.w;
+      if (L.state == ST_GR_INIT && P.async_gr && N.gq && !L.gr_sync) {
+        L.state = ST_GR_SEED;   // the sinks (this phase's BFS list) seed the queue
+        break;
+      }
       L.state = (L.state == ST_GR_INIT || L.state == ST_GR_ADD) ? ST_GR_LEVEL
                 : L.state == ST_DIST_INIT ? ST_DIST_LEVEL : ST_SR_LEVEL;
       break;
@@ -239,18 +281,7 @@ __device__ void advance(Sched& L, const Snap& q, const Params& P, const NetDev& 
       if (st == ST_SR_LEVEL) L.wS += q.w;
       if (q.c[C_BFS] == 0 && q.c[C_BFSH] == 0) {
         if (st == ST_GR_LEVEL) {
-          L.last_gr = (unsigned)L.level + 1;
-          L.fcnt = q.act;
-          L.fcnth = q.acth;
-          L.rcnt = 0;
-          L.lp = 0;
-          L.epoch++;
-          L.work = 0;
-          L.stall = 0;
-          L.flow_ref = L.flow;
-          const unsigned f = L.fcnt + L.fcnth;
-          if (f == 0 || L.after_gr_exit) L.state = ST_DONE;
-          else L.state = f <= P.tail_enter ? ST_TAIL : ST_ROUND_A;
+          end_gr(L, q, P, (unsigned)L.level + 1);
         } else {
           L.epoch++;
           L.state = ST_DONE;
@@ -283,6 +314,9 @@ __device__ Snap take_snap(EngineCtl* E, unsigned k) {
   q.w = *(const volatile long long*)&E->w3[sl];
   q.key = *(const volatile unsigned long long*)&E->key3[sl];
   q.node = *(const volatile int*)&E->node3[sl];
+  q.gq_over = ld_cg(&E->gq_over);
+  q.gq_maxd = ld_cg(&E->gq_maxd);
+  q.gq_tail = ld_cg(&E->gq_tail);
   return q;
 }
 
@@ -790,7 +824,22 @@ __device__ void phase_b(const NetDev& N, const Sched& L, const Team& T, const Sl
 
 // Global relabel, step 1: exact labels start from the sinks (Section 2,
 // "global relabeling").
-__device__ void gr_init(const NetDev& N, const Team& T, const Slot& S, unsigned lane, Acc& a) {
+__device__ void gr_init(const NetDev& N, EngineCtl* E, const Sched& L, const Team& T,
+                        const Slot& S, unsigned lane, Acc& a) {
+  if (N.gq) {
+    // empty the queue slots the last asynchronous relabel wrote
+    const unsigned used = min(L.gq_prev, N.gq_cap);
+    for (unsigned i = T.tid; i < used; i += T.nth) N.gq[i] = 0ull;
+  }
+  if (T.tid == 0) {
+    // the work queue of an asynchronous relabel starts empty (nothing reads
+    // it in this phase)
+    E->gq_head = 0;
+    E->gq_tail = 0;
+    E->gq_done = 0;
+    E->gq_over = 0;
+    E->gq_maxd = 0;
+  }
   for (unsigned x0 = T.tid - lane; x0 < (unsigned)N.NL; x0 += T.nth) {
     const unsigned x = x0 + lane;
     bool snk = false, hv = false;
@@ -927,6 +976,230 @@ __device__ void gr_level(const NetDev& N, EngineCtl* E, const Sched& L, const Te
       gr_emit(N, E, L, S, c2, d1, a);
     }
   }
+}
+
+// ---------------------------------------------------------------------------
+// Asynchronous global relabel.  The level-synchronous search above pays one
+// grid barrier and one dependent load chain per breadth-first level, and the
+// reverse searches of a large network are hundreds of levels deep.  Here the
+// whole search runs in one phase: a label-correcting search (labels only
+// decrease, by atomicMin) driven by a work queue in global memory.  Every
+// node whose label drops is queued again, so at the end every label is the
+// exact residual distance to the sinks, the same labels the level-by-level
+// search sets; the order of work only changes how often a node is expanded.
+//
+// Queue entries are 64-bit: (label + 1) << 37 | chunk << 27 | node, so an
+// entry is never zero and a zero slot is an empty one (the slots used by a
+// relabel are cleared by the next one; Lawler ids must stay below 2^27).  A
+// node with more than kLightItems arc groups is queued as chunks of at least
+// kGqChunk arc groups (at most 1,024 chunks), so one team walks one chunk.
+// Teams take slots from gq_head in order, wait for the slot's entry to be
+// written, expand it, and count it in gq_done once its own entries are
+// queued.  The search is over when gq_done equals gq_tail, read as tail,
+// done, tail with acquire loads: an entry is counted done only after the
+// entries it produced were counted in the tail, so equal counts mean nothing
+// is queued or being expanded.  An entry whose node has a smaller label by
+// now is skipped: the entry queued when the label dropped expands it.  A full
+// queue sets gq_over; the relabel is then redone level by level.
+constexpr unsigned kGqChunk = 16;
+constexpr unsigned kGqMaxChunks = 1024;
+constexpr unsigned kGqNodeBits = 27;
+
+__device__ __forceinline__ unsigned gq_chunk_size(unsigned items) {
+  return items <= kGqChunk * kGqMaxChunks ? kGqChunk : (items + kGqMaxChunks - 1) / kGqMaxChunks;
+}
+
+__device__ __forceinline__ unsigned gq_chunks(unsigned items) {
+  const unsigned cs = gq_chunk_size(items);
+  return items == 0 ? 1u : (items + cs - 1) / cs;
+}
+
+__device__ __forceinline__ unsigned long long gq_entry(int z, unsigned chunk, int label) {
+  return ((unsigned long long)(label + 1) << 37) | ((unsigned long long)chunk << kGqNodeBits) |
+         (unsigned)z;
+}
+
+// Queue every chunk of node z (label d, flag byte f) for the lanes with
+// `want`.  Warp-collective: one tail atomic per warp; the chunks of large
+// nodes are written by the whole warp.
+__device__ void gq_push(const NetDev& N, EngineCtl* E, bool want, int z, uint8_t f, int d) {
+  const unsigned lane = lane_id();
+  unsigned cnt = 0;
+  if (want) cnt = (f & kHeavy) ? gq_chunks(node_arcs(N, z).items) : 1u;
+  unsigned incl = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned t = __shfl_up_sync(FULL, incl, o);
+    if ((int)lane >= o) incl += t;
+  }
+  const unsigned total = __shfl_sync(FULL, incl, 31);
+  if (total == 0) return;
+  unsigned base = 0;
+  if (lane == 31) base = atomicAdd(&E->gq_tail, total);
+  base = __shfl_sync(FULL, base, 31);
+  const unsigned s0 = base + incl - cnt;
+  const bool fits = s0 <= N.gq_cap && N.gq_cap - s0 >= cnt;
+  if (cnt && !fits) *(volatile unsigned*)&E->gq_over = 1u;
+  if (cnt == 1 && fits) st_release_u64(&N.gq[s0], gq_entry(z, 0, d));
+  unsigned big = __ballot_sync(FULL, cnt > 1 && fits);
+  if (!big) return;
+  __syncwarp();   // every lane's label update is ordered before the other lanes' stores
+  while (big) {
+    const int src = __ffs(big) - 1;
+    big &= big - 1;
+    const unsigned bs = __shfl_sync(FULL, s0, src), bc = __shfl_sync(FULL, cnt, src);
+    const int bz = __shfl_sync(FULL, z, src), bd = __shfl_sync(FULL, d, src);
+    for (unsigned c = lane; c < bc; c += 32) st_release_u64(&N.gq[bs + c], gq_entry(bz, c, bd));
+  }
+}
+
+// Seeding: every sink (the BFS list of ST_GR_INIT, label 0) enters the queue.
+__device__ void gr_seed(const NetDev& N, EngineCtl* E, const Sched& L, const Team& T,
+                        unsigned lane) {
+  const unsigned nl = L.bfs_end, nh = L.bfsh_end, tot = nl + nh;
+  const int32_t* bl = N.list[L_BFS];
+  for (unsigned i0 = T.tid - lane; i0 < tot; i0 += T.nth) {
+    const unsigned i = i0 + lane;
+    int y = -1;
+    uint8_t f = 0;
+    if (i < tot) {
+      y = i < nl ? bl[i] : bl[N.NL - 1 - (i - nl)];
+      f = N.flags[y];
+    }
+    gq_push(N, E, y >= 0, y, f, 0);
+  }
+}
+
+// Label of z lowered to d1 when larger (sources never take labels).  On the
+// first label the node's weight joins T_r and, with excess, it joins the
+// frontier.  Warp-collective; queues the lanes' lowered nodes.
+__device__ __forceinline__ bool gq_relax(const NetDev& N, EngineCtl* E, const Slot& S, int z,
+                                         int d1, Acc& a) {
+  bool imp = false, first = false;
+  uint8_t f = 0;
+  if (z >= 0) {
+    const int cur = __ldcg(&N.lab0[z]);
+    f = N.flags[z];
+    if (cur > d1 && !(f & kSource)) {
+      const int old = atomicMin(&N.lab0[z], d1);
+      if (old > d1) {
+        imp = true;
+        atomicMin(&N.lab1[z], d1);
+        first = old == N.NL;
+      }
+    }
+  }
+  gq_push(N, E, imp, z, f, d1);
+  bool act = false;
+  if (first) {
+    if (z < N.n_nodes) a.w += N.node_w[z];
+    act = N.excess[z] > 0;
+  }
+  append_split(act, z, (f & kHeavy) != 0, N.list[L_FRONT], S.act[0], S.act[1], 0, 0, N.NL);
+  return imp;
+}
+
+// Expand chunk c of node x queued with label d (x < 0: idle team): relax
+// every reverse residual arc into x with d + 1.  Skipped when x's label has
+// dropped below d since (a later entry of x expands it).
+template <int TW>
+__device__ void gq_expand(const NetDev& N, EngineCtl* E, const Slot& S, int x, unsigned c, int d,
+                          unsigned lane, Acc& a, unsigned& maxd) {
+  const unsigned tl = lane & (TW - 1);
+  NodeArcs g{0, 0, 0, 0};
+  int w = 0, fb = 0;
+  unsigned k0 = 0, k1 = 0;
+  if (x >= 0) {
+    const int cur = __ldcg(&N.lab0[x]);
+    g = node_arcs(N, x);
+    if (g.kind) {
+      w = N.net_w[g.e];
+      fb = N.f_b[g.e];
+    }
+    const unsigned cs = gq_chunk_size(g.items);
+    k0 = c * cs;
+    k1 = min(k0 + cs, g.items);
+    if (cur < d || d >= N.NL) k1 = k0;
+  }
+  const int d1 = d + 1;
+  const unsigned steps = warp_max_u(k1 > k0 ? (k1 - k0 + TW - 1) / TW : 0u);
+  for (unsigned st = 0; st < steps; st++) {
+    const unsigned k = k0 + st * TW + tl;
+    int c1 = -1, c2 = -1;
+    if (k < k1) rev_arcs(N, g, k, w, fb, c1, c2, a);
+    const bool i1 = gq_relax(N, E, S, c1, d1, a);
+    const bool i2 = gq_relax(N, E, S, c2, d1, a);
+    if (i1 || i2) maxd = max(maxd, (unsigned)d1);
+  }
+}
+
+// The search itself: warps below P.gr_warps of every CTA serve the queue,
+// four 8-lane teams per warp, until it is finished, overflowed, or an error
+// or the time bound stops it.
+__device__ void gr_run(const NetDev& N, EngineCtl* E, const Sched& L, const Slot& S,
+                       unsigned lane, Acc& a, const Params& P) {
+  if ((threadIdx.x >> 5) >= P.gr_warps) return;
+  constexpr unsigned NONE = 0xffffffffu;
+  const unsigned tl = lane & (kTeam - 1), lead = lane & ~(unsigned)(kTeam - 1);
+  unsigned slot = NONE, maxd = 0, idle = 0;
+  unsigned long long t0 = 0;
+  for (;;) {
+    // slots for the teams that have none: one atomic per warp
+    const unsigned m = __ballot_sync(FULL, slot == NONE && tl == 0);
+    if (m) {
+      const int ld = __ffs(m) - 1;
+      unsigned base = 0;
+      if ((int)lane == ld) base = atomicAdd(&E->gq_head, (unsigned)__popc(m));
+      base = __shfl_sync(FULL, base, ld);
+      if (slot == NONE) slot = base + __popc(m & ((1u << lead) - 1u));
+    }
+    unsigned long long ent = 0;
+    if (tl == 0 && slot < N.gq_cap) ent = ld_acquire_u64(&N.gq[slot]);
+    ent = __shfl_sync(FULL, ent, lead);
+    const bool ready = ent != 0ull;
+    const unsigned rm = __ballot_sync(FULL, ready);
+    if (rm) {
+      const int x = ready ? (int)(ent & ((1u << kGqNodeBits) - 1u)) : -1;
+      const unsigned c = ready ? (unsigned)(ent >> kGqNodeBits) & (kGqMaxChunks - 1u) : 0u;
+      const int d = ready ? (int)(ent >> 37) - 1 : 0;
+      gq_expand<kTeam>(N, E, S, x, c, d, lane, a, maxd);
+      if (ready) slot = NONE;
+      __syncwarp();
+      if (lane == 0) red_release_add(&E->gq_done, (unsigned)__popc(rm) / kTeam);
+      idle = 0;
+      t0 = 0;
+      continue;
+    }
+    if ((++idle & 7u) == 0) {
+      int stop = 0;
+      if (lane == 0) {
+        if (ld_volatile_int((const int*)&E->gq_over) || ld_volatile_int(&E->c.err) != kDevOk) {
+          stop = 1;
+        } else {
+          const unsigned t1 = ld_acquire(&E->gq_tail);
+          const unsigned dn = ld_acquire(&E->gq_done);
+          const unsigned t2 = ld_acquire(&E->gq_tail);
+          if (dn == t1 && t1 == t2) {
+            stop = 1;
+          } else {
+            const unsigned long long t = globaltimer();
+            if (t0 == 0) {
+              t0 = t;
+            } else if (t - t0 > P.timeout_ns) {
+              atomicCAS(&E->c.err, kDevOk, kDevTimeout);
+              E->c.err_where = 3;
+              stop = 1;
+            }
+          }
+        }
+      }
+      if (__shfl_sync(FULL, stop, 0)) break;
+    }
+    if (idle > 32) __nanosleep(64);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) maxd = max(maxd, __shfl_xor_sync(FULL, maxd, o));
+  if (lane == 0 && maxd) atomicMax(&E->gq_maxd, maxd);
 }
 
 // Source-side cut, step 1: seeds are the sources and every non-sink node with
@@ -1104,11 +1377,14 @@ __device__ __forceinline__ Slot slot_of(EngineCtl* E, unsigned k) {
 // One phase of the current state by team T with counters S; hypernode
 // weights reached go to w_sh.
 __device__ void run_phase_s(const NetDev& N, EngineCtl* E, const Sched& L, const Team& T,
-                            const Slot& S, unsigned lane, Acc& a, long long* w_sh) {
+                            const Slot& S, unsigned lane, Acc& a, long long* w_sh,
+                            const Params& P) {
   switch (L.state) {
     case ST_ROUND_A: phase_a(N, L, T, S, lane, a, E); break;
     case ST_ROUND_B: phase_b(N, L, T, S, lane, a); break;
-    case ST_GR_INIT: gr_init(N, T, S, lane, a); break;
+    case ST_GR_INIT: gr_init(N, E, L, T, S, lane, a); break;
+    case ST_GR_SEED: gr_seed(N, E, L, T, lane); break;
+    case ST_GR_RUN: gr_run(N, E, L, S, lane, a, P); break;
     case ST_GR_ADD: gr_add(N, L, T, S, lane, a); break;
     case ST_GR_LEVEL: gr_level(N, E, L, T, S, lane, a); break;
     case ST_SR_INIT: sr_init(N, L, T, S, lane, a); break;
@@ -1126,8 +1402,8 @@ __device__ void run_phase_s(const NetDev& N, EngineCtl* E, const Sched& L, const
 
 // One grid phase: counters in the phase's slot of the control block.
 __device__ void run_phase(const NetDev& N, EngineCtl* E, const Sched& L, const Team& T,
-                          unsigned lane, Acc& a, long long* w_sh) {
-  run_phase_s(N, E, L, T, slot_of(E, L.phase), lane, a, w_sh);
+                          unsigned lane, Acc& a, long long* w_sh, const Params& P) {
+  run_phase_s(N, E, L, T, slot_of(E, L.phase), lane, a, w_sh, P);
 }
 
 __device__ __forceinline__ void flush_weight(EngineCtl* E, unsigned k, long long* w_sh) {
@@ -1228,7 +1504,7 @@ __device__ void solo_phases(const NetDev& N, EngineCtl* E, const Params& P, Sche
       sh.flow = 0;
     }
     __syncthreads();
-    run_phase_s(N, E, L, T, S, lane, a, w_sh);
+    run_phase_s(N, E, L, T, S, lane, a, w_sh, P);
     __syncthreads();
     if (threadIdx.x == 0) {
       Snap q;
@@ -1304,9 +1580,13 @@ __device__ void load_sched(Sched& L, const EngineCtl* E) {
   L.phase = v->phase;
   L.seed = v->seed;
   L.last_gr = v->last_gr;
+  L.gr_sync = v->gr_sync;
   L.rounds = v->rounds;
   L.grs = v->grs;
   L.gr_levels = v->gr_levels;
+  L.gq_items = v->gq_items;
+  L.gq_prev = v->gq_prev;
+  L.gq_overs = v->gq_overs;
   L.work = v->work;
   L.stall = v->stall;
   L.flow = v->flow;
@@ -1336,9 +1616,13 @@ __device__ void store_sched(EngineCtl* E, const Sched& L) {
   v->phase = L.phase;
   v->seed = L.seed;
   v->last_gr = L.last_gr;
+  v->gr_sync = L.gr_sync;
   v->rounds = L.rounds;
   v->grs = L.grs;
   v->gr_levels = L.gr_levels;
+  v->gq_items = L.gq_items;
+  v->gq_prev = L.gq_prev;
+  v->gq_overs = L.gq_overs;
   v->work = L.work;
   v->stall = L.stall;
   v->flow = L.flow;
@@ -1390,7 +1674,7 @@ __global__ void __launch_bounds__(kEngineThreads) engine_kernel(NetDev N, Engine
     }
     if (cta0 && threadIdx.x == 0)
       clear_slot(E, (L.phase + 1) % 3, st == ST_GR_INIT || st == ST_GR_ADD);
-    run_phase(N, E, L, G, lane, a, &w_sh);
+    run_phase(N, E, L, G, lane, a, &w_sh, P);
     __syncthreads();
     if (threadIdx.x == 0) flush_weight(E, L.phase, &w_sh);
     const bool ok = grid_barrier(E, gridDim.x * ++bar_seq, P.timeout_ns);
@@ -1423,6 +1707,8 @@ __global__ void __launch_bounds__(kEngineThreads) engine_kernel(NetDev N, Engine
       E->c.rounds = L.rounds;
       E->c.global_relabels = L.grs;
       E->c.gr_levels = L.gr_levels;
+      E->c.gq_items = L.gq_items;
+      E->c.gq_overs = L.gq_overs;
       if (L.wS_set) E->c.wS = L.wS;
       if (L.wT_set) E->c.wT = L.wT;
       for (int i = 0; i < 10; i++) {

@@ -26,6 +26,8 @@ enum EngineState : int {
   ST_FC_MARK_T = 14,  // T <- T_r + pierced node, their excess joins the flow
   ST_SR_ADD = 15,   // source-side cut grown from one new source (S_r kept)
   ST_GR_ADD = 16,   // sink-side cut grown from one new sink (T_r and its labels kept)
+  ST_GR_SEED = 17,  // asynchronous global relabel: the sinks enter the work queue
+  ST_GR_RUN = 18,   // asynchronous global relabel: label-correcting search to the end
 };
 
 // list ids in NetDev::list.  Each list array holds light nodes from the front
@@ -51,7 +53,11 @@ struct Sched {
   unsigned int phase;     // phase index (selects the counter slots)
   int seed;               // ST_SR_ADD / ST_GR_ADD: the node whose reach joins S_r / T_r
   unsigned int last_gr;   // levels of the last global relabel
+  int gr_sync;            // this global relabel runs level by level (queue overflowed)
   unsigned long long rounds, grs, gr_levels, work, stall, flow, flow_ref;
+  unsigned long long gq_items, gq_overs;   // queue entries expanded, queue overflows
+  unsigned gq_prev;       // queue slots written by the last asynchronous relabel
+  unsigned gq_pad;
   long long wS, wT;
   int wS_set, wT_set;
 };
@@ -69,6 +75,8 @@ struct Params {
   unsigned int pierce_relabel;       // source piercing: start the flow with a global relabel
   unsigned int stall_rounds_pierce;  // stall_rounds of the flows after a piercing (0: adaptive)
   unsigned int stall_adapt;          // stall limit = levels of the last global relabel
+  unsigned int async_gr;             // global relabels as one queue-driven search
+  unsigned int gr_warps;             // warps per CTA that serve that search's queue
   unsigned int pad;
 };
 
@@ -84,6 +92,13 @@ struct EngineCtl {
   unsigned long long key3[3];        // batched FlowCutter: best piercing key per slot
   int node3[3];                      // batched FlowCutter: node holding it per slot
   int pad3;
+  // work queue of the asynchronous global relabel, one counter per 128-byte
+  // line (entries handed out, entries written, entries finished)
+  alignas(128) unsigned gq_head;
+  alignas(128) unsigned gq_tail;
+  alignas(128) unsigned gq_done;
+  unsigned gq_over;                  // an entry did not fit: redo level by level
+  unsigned gq_maxd;                  // largest label set by the search
 };
 
 // One flow problem of a batched FlowCutter launch (Section 7, Algorithm 2):

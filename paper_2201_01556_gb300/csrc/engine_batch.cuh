@@ -437,7 +437,7 @@ __device__ __forceinline__ bool job_barrier(EngineCtl* E, unsigned ctr, unsigned
 
 __device__ void run_phase_batch(const NetDev& N, EngineCtl* E, const Sched& L, const FcState& F,
                                 const FcJob& J, const Team& T, unsigned lane, Acc& a,
-                                long long* w_sh) {
+                                long long* w_sh, const Params& P) {
   const Slot S = slot_of(E, L.phase);
   switch (L.state) {
     case ST_FC_SAT: fc_saturate(N, L, T, S, F.node, lane); break;
@@ -449,7 +449,7 @@ __device__ void run_phase_batch(const NetDev& N, EngineCtl* E, const Sched& L, c
       break;
     case ST_FC_MARK_S: fc_mark_sources(N, T, F.node); break;
     case ST_FC_MARK_T: fc_mark_sinks(N, T, S, F.node); break;
-    default: run_phase(N, E, L, T, lane, a, w_sh); break;
+    default: run_phase(N, E, L, T, lane, a, w_sh, P); break;
   }
 }
 
@@ -498,7 +498,7 @@ __device__ void fc_run_job(FcJob* job, const Params& P0, int rank, int G, unsign
     }
     if (lead && threadIdx.x == 0)
       clear_slot(E, (L.phase + 1) % 3, st == ST_GR_INIT || st == ST_GR_ADD);
-    run_phase_batch(N, E, L, F, *job, T, lane, a, w_sh);
+    run_phase_batch(N, E, L, F, *job, T, lane, a, w_sh, P);
     __syncthreads();
     if (threadIdx.x == 0) flush_weight(E, L.phase, w_sh);
     const bool ok = job_barrier(E, ctr, cseq, bar_seq, G, P.timeout_ns);

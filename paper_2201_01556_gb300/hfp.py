@@ -44,7 +44,8 @@ class _NetInfo(ctypes.Structure):
 class _Stats(ctypes.Structure):
     _fields_ = [(k, ctypes.c_uint64) for k in
                 ("rounds", "global_relabels", "gr_levels", "items_hyper", "items_net",
-                 "node_visits", "pushes", "engine_launches", "engine_ns")]
+                 "node_visits", "pushes", "engine_launches", "engine_ns", "gr_queue_entries",
+                 "gr_queue_overflows")]
 
 
 class Tuning(ctypes.Structure):
@@ -52,7 +53,8 @@ class Tuning(ctypes.Structure):
                                                "tail_enter", "tail_exit", "max_rounds",
                                                "bfs_enter", "bfs_exit", "pierce_relabel",
                                                "stall_rounds_pierce", "batch_cluster",
-                                               "batch_big_ctas", "batch_big_groups")]
+                                               "batch_big_ctas", "batch_big_groups",
+                                               "async_gr", "gr_warps")]
 
 
 class RefineParams(ctypes.Structure):

@@ -157,6 +157,10 @@ uint64_t hfp_kernel_launches(void);
  *                 without a grid barrier per breadth-first level; the labels
  *                 are the same exact distances [1]
  *   gr_warps      warps per CTA that serve that queue (1..16) [8]
+ *   fused_rounds  one grid-wide phase per discharge round: each node applies
+ *                 the previous round's pushes, discharges and relabels itself
+ *                 from its own residual arcs, raising its label by at most 2;
+ *                 0: a push phase and a relabel phase per round [1]
  *   batch_cluster  batched FlowCutter: launch groups of at most 16 CTAs as
  *                 thread-block clusters (group barriers in distributed
  *                 shared memory) when as many such clusters can be resident
@@ -183,6 +187,7 @@ typedef struct {
   uint32_t batch_big_groups;
   uint32_t async_gr;
   uint32_t gr_warps;
+  uint32_t fused_rounds;
 } hfp_tuning;
 hfp_status hfp_ctx_get_tuning(hfp_ctx* ctx, hfp_tuning* tuning);
 hfp_status hfp_ctx_set_tuning(hfp_ctx* ctx, const hfp_tuning* tuning);
@@ -228,8 +233,9 @@ hfp_status hfp_net_get_stats(hfp_net* net, hfp_stats* stats);
  *   excess[lawler_nodes]  excess of each non-terminal Lawler node (inflow -
  *                  outflow once every push of the last round is applied;
  *                  values of sources and sinks are not maintained);
- *   delta[lawler_nodes]   pushes not yet applied to excess (all 0 once
- *                  hfp_max_flow returned);
+ *   delta[lawler_nodes]   pushes not yet applied to excess, summed over
+ *                  the engine's delta buffers (all 0 once hfp_max_flow
+ *                  returned);
  *   flags[lawler_nodes]   bit 0: node is in S, bit 1: node is in T.
  * The flow value is the net inflow of T.  Per-arc flows are not unique;
  * only the value and the minimal cuts are. */

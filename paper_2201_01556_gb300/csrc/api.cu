@@ -212,6 +212,7 @@ HFP_API hfp_status hfp_ctx_create(hfp_ctx** out, int device, void* stream) {
   c->params.stall_adapt = 0;
   c->params.async_gr = 1;          // global relabels as one queue-driven search
   c->params.gr_warps = 8;          // warps per CTA serving its queue (fewer: less re-expansion)
+  c->params.fused_rounds = 1;      // one phase per discharge round
   *out = c;
   return HFP_OK;
 }
@@ -415,7 +416,7 @@ HFP_API hfp_status hfp_build_flow_network(hfp_ctx* ctx, const hfp_hypergraph* H,
       sizeof(int32_t) * NL, sizeof(int32_t) * NL, sizeof(long long) * NL, sizeof(long long) * NL,
       sizeof(uint32_t) * NL, (size_t)NL, (size_t)NL, (size_t)NL, sizeof(int32_t) * NL,
       sizeof(int32_t) * NL, sizeof(int32_t) * NL, sizeof(int32_t) * NL, sizeof(EngineCtl),
-      sizeof(unsigned long long) * gq_cap};
+      sizeof(unsigned long long) * gq_cap, sizeof(long long) * NL};
   size_t total = 0;
   for (size_t b : sz) total += align_up(b);
   cudaError_t ae = cudaMallocAsync(&net->arena, total, st);
@@ -470,6 +471,7 @@ HFP_API hfp_status hfp_build_flow_network(hfp_ctx* ctx, const hfp_hypergraph* H,
   for (int k = 0; k < 4; k++) D.list[k] = (int32_t*)ptr[21 + k];
   net->E = (EngineCtl*)ptr[25];
   D.gq = gq_cap ? (unsigned long long*)ptr[26] : nullptr;
+  D.delta1 = (long long*)ptr[27];
   D.gq_cap = gq_cap;
   net->total_w = total_w;
 
@@ -524,6 +526,7 @@ HFP_API hfp_status hfp_build_flow_network(hfp_ctx* ctx, const hfp_hypergraph* H,
   CKN(cudaMemsetAsync(D.f_b, 0, sizeof(int32_t) * m_net, st));
   CKN(cudaMemsetAsync(D.excess, 0, sizeof(long long) * NL, st));
   CKN(cudaMemsetAsync(D.delta, 0, sizeof(long long) * NL, st));
+  CKN(cudaMemsetAsync(D.delta1, 0, sizeof(long long) * NL, st));
   CKN(cudaMemsetAsync(D.stamp, 0, sizeof(uint32_t) * NL, st));
   CKN(cudaMemsetAsync(D.needrl, 0, NL, st));
   CKN(cudaMemsetAsync(D.insr, 0, NL, st));
@@ -599,7 +602,13 @@ HFP_API hfp_status hfp_net_export_flow(hfp_net* net, hfp_mem mem, int32_t* f_in,
   if (f_out && (s = copy_out(f_out, D.f_out, sizeof(int32_t) * p, mem, st))) return s;
   if (f_b && (s = copy_out(f_b, D.f_b, sizeof(int32_t) * m, mem, st))) return s;
   if (excess && (s = copy_out(excess, D.excess, sizeof(int64_t) * nl, mem, st))) return s;
-  if (delta && (s = copy_out(delta, D.delta, sizeof(int64_t) * nl, mem, st))) return s;
+  if (delta) {
+    // both delta buffers (one-phase rounds alternate them)
+    DevBuf tmp;
+    CK(tmp.alloc(sizeof(int64_t) * (nl > 0 ? nl : 1), st));
+    launch_add_i64(D.delta, D.delta1, tmp.as<long long>(), (long long)nl, net->ctx->sms, st);
+    if ((s = copy_out(delta, tmp.p, sizeof(int64_t) * nl, mem, st))) return s;
+  }
   if (flags && (s = copy_out(flags, D.flags, nl, mem, st))) return s;
   CK(cudaStreamSynchronize(st));
   return HFP_OK;
@@ -685,6 +694,7 @@ HFP_API hfp_status hfp_ctx_get_tuning(hfp_ctx* ctx, hfp_tuning* t) {
   t->stall_rounds_pierce = (uint32_t)ctx->params.stall_rounds_pierce;
   t->async_gr = ctx->params.async_gr;
   t->gr_warps = ctx->params.gr_warps;
+  t->fused_rounds = ctx->params.fused_rounds;
   t->batch_cluster = ctx->batch_cluster;
   t->batch_big_ctas = ctx->batch_big_ctas;
   t->batch_big_groups = ctx->batch_big_groups;
@@ -708,6 +718,7 @@ HFP_API hfp_status hfp_ctx_set_tuning(hfp_ctx* ctx, const hfp_tuning* t) {
   ctx->params.stall_rounds_pierce = t->stall_rounds_pierce;
   ctx->params.async_gr = t->async_gr ? 1 : 0;
   ctx->params.gr_warps = t->gr_warps < 1 ? 1 : (t->gr_warps > 16 ? 16 : t->gr_warps);
+  ctx->params.fused_rounds = t->fused_rounds ? 1 : 0;
   ctx->batch_cluster = t->batch_cluster ? 1 : 0;
   ctx->batch_big_ctas = t->batch_big_ctas;
   ctx->batch_big_groups = t->batch_big_groups;

@@ -110,7 +110,8 @@ hfp_status run_fc_batch(hfp_ctx* ctx, BatchItem* items, int n, int group_ctas, f
   FcJob* jp = djobs.as<FcJob>();
   BatchCtl* bp = dctl.as<BatchCtl>();
   Params P0 = ctx->params;
-  P0.async_gr = 0;   // groups relabel level by level
+  P0.async_gr = 0;       // groups relabel level by level
+  P0.fused_rounds = 0;   // and run two-phase rounds
   int use_cluster = cluster ? 1 : 0;
   void* args[] = {(void*)&jp,     (void*)&n,      (void*)&bp, (void*)&G,          (void*)&Gb,
                   (void*)&big,    (void*)&groups, (void*)&P0, (void*)&use_cluster};

@@ -53,6 +53,7 @@ struct NetDev {
   int32_t* lab1;
   long long* excess;
   long long* delta;
+  long long* delta1;            // second delta buffer of one-phase rounds (may be null)
   uint32_t* stamp;
   uint8_t* flags;
   uint8_t* needrl;

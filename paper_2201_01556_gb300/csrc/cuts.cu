@@ -378,4 +378,17 @@ void launch_inc_slots(const NetDev& N, int32_t* out, int sms, cudaStream_t st) {
   }
 }
 
+__global__ void k_add_i64(const long long* a, const long long* b, long long* out, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    out[i] = a[i] + (b ? b[i] : 0);
+}
+
+void launch_add_i64(const long long* a, const long long* b, long long* out, long long n, int sms,
+                    cudaStream_t st) {
+  if (n <= 0) return;
+  k_add_i64<<<sms * 4, 256, 0, st>>>(a, b, out, n);
+  count_launches(1);
+}
+
 }  // namespace hfp

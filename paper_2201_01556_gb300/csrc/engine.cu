@@ -179,6 +179,12 @@ __device__ void begin_gr(Sched& L) {
   L.wT_set = 1;
 }
 
+// The discharge round of this configuration: one phase, or push and
+// relabel phases.
+__device__ __forceinline__ int round_state(const Params& P) {
+  return P.fused_rounds ? ST_ROUND : ST_ROUND_A;
+}
+
 // End of a global relabel with `levels` breadth-first levels: the active
 // nodes it found form the frontier; labels are exact distances.
 __device__ __forceinline__ void end_gr(Sched& L, const Snap& q, const Params& P, unsigned levels) {
@@ -192,9 +198,10 @@ __device__ __forceinline__ void end_gr(Sched& L, const Snap& q, const Params& P,
   L.work = 0;
   L.stall = 0;
   L.flow_ref = L.flow;
+  L.fsel = L_FRONT;
   const unsigned f = L.fcnt + L.fcnth;
   if (f == 0 || L.after_gr_exit) L.state = ST_DONE;
-  else L.state = f <= P.tail_enter ? ST_TAIL : ST_ROUND_A;
+  else L.state = f <= P.tail_enter ? ST_TAIL : round_state(P);
 }
 
 __device__ void advance(Sched& L, const Snap& q, const Params& P, const NetDev& N, Ctl* c) {
@@ -233,6 +240,39 @@ __device__ void advance(Sched& L, const Snap& q, const Params& P, const NetDev& 
       }
       break;
     }
+    case ST_ROUND: {
+      // one-phase round: the next frontier is the list this round filled
+      const unsigned fprev = L.fcnt + L.fcnth;
+      L.flow += q.flow;
+      L.rounds++;
+      L.fcnt = q.c[C_NEXT];
+      L.fcnth = q.c[C_NEXTH];
+      L.work += (unsigned long long)fprev + L.fcnt + L.fcnth;
+      L.fsel ^= 1;
+      L.lp ^= 1;
+      L.epoch++;
+      const unsigned f = L.fcnt + L.fcnth;
+      if (L.flow != L.flow_ref || f >= P.stall_nodes) {
+        L.flow_ref = L.flow;
+        L.stall = 0;
+      } else {
+        L.stall++;
+      }
+      if (f == 0) {
+        begin_gr(L);   // nothing was pushed: no pending deltas
+      } else if (L.rounds >= P.max_rounds) {
+        atomicCAS(&c->err, kDevOk, kDevIterLimit);
+        L.state = ST_DONE;
+      } else if (L.work >= P.gr_work || L.stall >= stall_limit(L, P)) {
+        L.state = ST_FLUSH;
+      } else {
+        L.state = f <= P.tail_enter ? ST_TAIL : ST_ROUND;
+      }
+      break;
+    }
+    case ST_FLUSH:
+      begin_gr(L);
+      break;
     case ST_GR_SEED:
       L.state = ST_GR_RUN;
       break;
@@ -822,6 +862,309 @@ __device__ void phase_b(const NetDev& N, const Sched& L, const Team& T, const Sl
     apply_relabel_block(N, Lr, Ln, nx[N.NL - 1 - h], a, S);
 }
 
+// ---------------------------------------------------------------------------
+// One-phase rounds.  The two-phase round above spends a grid barrier and a
+// second dependent load chain on applying deltas and relabelling.  Here a
+// round is one phase: every frontier node first applies the pushes it
+// received in the previous round (delta buffers alternate by round parity,
+// so this round's pushes never mix with them), discharges against the labels
+// of the round, and relabels itself at once from its own arcs:
+//   new label = min(min over its residual arcs (x, y) of d(y) + 1, d(x) + 2).
+// The first term is the usual relabel over the arcs left residual by x's own
+// pushes (read with the round's labels, which only grow, so it stays valid
+// when neighbours relabel too).  The arcs that other nodes' pushes open into
+// x this round come from nodes with label d(x) + 1, so they never ask for
+// more than d(x) + 2; capping at d(x) + 2 keeps the labelling valid without
+// knowing whether such pushes happened.  It never exceeds the two-phase
+// relabel and still raises the label by at least one (no admissible arc is
+// left), so the method and its results are those of push-relabel; only the
+// number of rounds can differ.  Labels stay double-buffered: a node writes
+// its next label only when it is in the frontier, and every node whose label
+// changes keeps excess, so it is in the next frontier and copies its label
+// into the other buffer there.
+
+__device__ __forceinline__ bool deliver_to(const NetDev& N, long long* dcur, int y, long long d,
+                                           unsigned epoch, long long& sink_acc, bool& heavy) {
+  const uint8_t fl = N.flags[y];
+  heavy = (fl & kHeavy) != 0;
+  if (fl & kSink) {
+    sink_acc += d;
+    return false;
+  }
+  if (fl & kSource) return false;
+  atomicAdd((unsigned long long*)&dcur[y], (unsigned long long)d);
+  return atomicExch(&N.stamp[y], epoch) != epoch;
+}
+
+// Arc group k of node x for a discharge with relabel: admissible residuals
+// r1, r2 (label dt), residual capacities q1, q2 (-1: none; kInfRes: the
+// uncapacitated (e_out, u)) and head labels l1, l2.
+constexpr long long kInfRes = 1ll << 62;
+
+__device__ __forceinline__ void arc_group(const NetDev& N, const NodeArcs& g, unsigned k, int w,
+                                          int fb, const int32_t* Lr, int dt, long long rem,
+                                          long long& r1, long long& r2, long long& q1,
+                                          long long& q2, int& l1, int& l2, int& y1, int& y2,
+                                          int& p, int& fi, int& fo, Acc& a) {
+  const int nh = N.n_nodes, m = N.m_nets;
+  if (g.kind == 0) {
+    const int2 it = N.inc[g.beg + k];
+    p = it.y;
+    const int ww = N.net_w[it.x];
+    fi = N.f_in[p];
+    fo = N.f_out[p];
+    y1 = nh + it.x;
+    y2 = nh + m + it.x;
+    l1 = Lr[y1];
+    l2 = Lr[y2];
+    q1 = ww - fi;
+    q2 = fo;
+    if (q1 > 0 && l1 == dt) r1 = q1;
+    if (q2 > 0 && l2 == dt) r2 = q2;
+    a.hyper++;
+  } else if (g.kind == 1) {
+    if (k == 0) {
+      y1 = nh + m + g.e;
+      q1 = w - fb;
+      l1 = Lr[y1];
+      if (q1 > 0 && l1 == dt) r1 = q1;
+    } else {
+      p = g.beg + k - 1;
+      fi = N.f_in[p];
+      q1 = fi;
+      if (fi > 0) {
+        y1 = N.pin[p];
+        l1 = Lr[y1];
+        if (l1 == dt) r1 = fi;
+      }
+    }
+    a.net++;
+  } else {
+    if (k == 0) {
+      y1 = nh + g.e;
+      q1 = fb;
+      if (fb > 0) {
+        l1 = Lr[y1];
+        if (l1 == dt) r1 = fb;
+      }
+    } else {
+      p = g.beg + k - 1;
+      y1 = N.pin[p];
+      l1 = Lr[y1];
+      q1 = kInfRes;
+      if (l1 == dt) r1 = rem;
+    }
+    a.net++;
+  }
+}
+
+// Flow updates of the takes t1, t2 on arc group k (as in discharge_team).
+__device__ __forceinline__ void apply_takes(const NetDev& N, const NodeArcs& g, unsigned k,
+                                            int fb, int p, int fi, int fo, long long t1,
+                                            long long t2) {
+  if (t1 > 0) {
+    if (g.kind == 0) N.f_in[p] = fi + (int)t1;
+    else if (g.kind == 1) {
+      if (k == 0) N.f_b[g.e] = fb + (int)t1;
+      else N.f_in[p] = fi - (int)t1;
+    } else {
+      if (k == 0) N.f_b[g.e] = fb - (int)t1;
+      else N.f_out[p] += (int)t1;
+    }
+  }
+  if (t2 > 0) N.f_out[p] = fo - (int)t2;
+}
+
+// Relabel candidate of the arcs of one group after its takes.
+__device__ __forceinline__ int group_cand(long long q1, long long q2, int l1, int l2,
+                                          long long t1, long long t2, int cand) {
+  if (q1 > 0 && q1 - t1 > 0) cand = min(cand, l1 + 1);
+  if (q2 > 0 && q2 - t2 > 0) cand = min(cand, l2 + 1);
+  return cand;
+}
+
+// One-phase discharge of node x by a team of TW lanes (x < 0: idle team).
+template <int TW>
+__device__ void round_team(const NetDev& N, int x, const int32_t* Lr, int32_t* Ln,
+                           long long* dprev, long long* dcur, int32_t* nl, unsigned epoch,
+                           unsigned lane, long long& sink_acc, Acc& a, const Slot& S) {
+  const int NL = N.NL;
+  const unsigned tl = lane & (TW - 1);
+  long long ex = 0, dp = 0;
+  int dx = NL;
+  if (x >= 0) {
+    ex = __ldcg(&N.excess[x]);
+    dp = __ldcg(&dprev[x]);
+    dx = Lr[x];
+  }
+  ex += dp;
+  const bool act = x >= 0 && ex > 0 && dx < NL;
+  long long rem = act ? ex : 0;
+  NodeArcs g{0, 0, 0, 0};
+  int w = 0, fb = 0;
+  if (act) {
+    g = node_arcs(N, x);
+    if (g.kind) {
+      w = N.net_w[g.e];
+      fb = N.f_b[g.e];
+    }
+  }
+  const int dt = dx - 1;
+  int cand = NL;
+  const unsigned steps = warp_max_u((g.items + TW - 1) / TW);
+  for (unsigned c = 0; c < steps; c++) {
+    const unsigned k = c * TW + tl;
+    long long r1 = 0, r2 = 0, q1 = -1, q2 = -1;
+    int l1 = NL, l2 = NL, y1 = -1, y2 = -1, p = 0, fi = 0, fo = 0;
+    if (rem > 0 && k < g.items)
+      arc_group(N, g, k, w, fb, Lr, dt, rem, r1, r2, q1, q2, l1, l2, y1, y2, p, fi, fo, a);
+    const long long r = r1 + r2;
+    const long long incl = team_incl_scan<TW>(r, tl);
+    const long long take = min(max(rem - (incl - r), 0LL), r);
+    const long long t1 = min(take, r1), t2 = take - t1;
+    cand = group_cand(q1, q2, l1, l2, t1, t2, cand);
+    apply_takes(N, g, k, fb, p, fi, fo, t1, t2);
+    bool a1 = false, a2 = false, h1 = false, h2 = false;
+    if (t1 > 0) {
+      a1 = deliver_to(N, dcur, y1, t1, epoch, sink_acc, h1);
+      a.pushes++;
+    }
+    if (t2 > 0) {
+      a2 = deliver_to(N, dcur, y2, t2, epoch, sink_acc, h2);
+      a.pushes++;
+    }
+    append_split(a1, y1, h1, nl, S.c[C_NEXT], S.c[C_NEXTH], 0, 0, NL);
+    append_split(a2, y2, h2, nl, S.c[C_NEXT], S.c[C_NEXTH], 0, 0, NL);
+    const long long tot = __shfl_sync(FULL, incl, TW - 1, TW);
+    rem -= min(rem, tot);
+  }
+  cand = team_min<TW>(cand);
+  bool want = false;
+  if (x >= 0 && tl == 0) {
+    if (dp) dprev[x] = 0;
+    if (act) {
+      N.excess[x] = rem;
+      Ln[x] = rem > 0 ? min(min(cand, dx + 2), NL) : dx;
+      if (rem > 0) want = atomicExch(&N.stamp[x], epoch) != epoch;
+      a.nodes++;
+    } else {
+      // no excess, or cut off from the sinks: keep the excess and the label
+      if (dp) N.excess[x] = ex;
+      Ln[x] = dx;
+    }
+  }
+  append_split(want, x, TW == 32, nl, S.c[C_NEXT], S.c[C_NEXTH], 0, 0, NL);
+}
+
+// One-phase discharge of one heavy node by the whole CTA.
+__device__ void round_block(const NetDev& N, int x, const int32_t* Lr, int32_t* Ln,
+                            long long* dprev, long long* dcur, int32_t* nl, unsigned epoch,
+                            long long& sink_acc, Acc& a, const Slot& S) {
+  const int NL = N.NL;
+  const long long dp = __ldcg(&dprev[x]);
+  const long long ex = __ldcg(&N.excess[x]) + dp;
+  const int dx = Lr[x];
+  if (ex <= 0 || dx >= NL) {   // uniform over the CTA
+    __syncthreads();           // every thread has read dprev[x] before it is cleared
+    if (threadIdx.x == 0) {
+      if (dp) {
+        dprev[x] = 0;
+        N.excess[x] = ex;
+      }
+      Ln[x] = dx;
+    }
+    return;
+  }
+  const int dt = dx - 1;
+  long long rem = ex;
+  const NodeArcs g = node_arcs(N, x);
+  const int w = g.kind ? N.net_w[g.e] : 0;
+  const int fb = g.kind ? N.f_b[g.e] : 0;
+  int cand = NL;
+  for (unsigned k0 = 0; k0 < g.items && rem > 0; k0 += blockDim.x) {
+    const unsigned k = k0 + threadIdx.x;
+    long long r1 = 0, r2 = 0, q1 = -1, q2 = -1;
+    int l1 = NL, l2 = NL, y1 = -1, y2 = -1, p = 0, fi = 0, fo = 0;
+    if (k < g.items)
+      arc_group(N, g, k, w, fb, Lr, dt, rem, r1, r2, q1, q2, l1, l2, y1, y2, p, fi, fo, a);
+    const long long r = r1 + r2;
+    long long tot;
+    const long long incl = block_incl_scan(r, &tot);
+    const long long take = min(max(rem - (incl - r), 0LL), r);
+    const long long t1 = min(take, r1), t2 = take - t1;
+    cand = group_cand(q1, q2, l1, l2, t1, t2, cand);
+    apply_takes(N, g, k, fb, p, fi, fo, t1, t2);
+    bool a1 = false, a2 = false, h1 = false, h2 = false;
+    if (t1 > 0) {
+      a1 = deliver_to(N, dcur, y1, t1, epoch, sink_acc, h1);
+      a.pushes++;
+    }
+    if (t2 > 0) {
+      a2 = deliver_to(N, dcur, y2, t2, epoch, sink_acc, h2);
+      a.pushes++;
+    }
+    append_split(a1, y1, h1, nl, S.c[C_NEXT], S.c[C_NEXTH], 0, 0, NL);
+    append_split(a2, y2, h2, nl, S.c[C_NEXT], S.c[C_NEXTH], 0, 0, NL);
+    rem -= min(rem, tot);
+  }
+  cand = block_min(cand);
+  bool want = false;
+  if (threadIdx.x == 0) {
+    if (dp) dprev[x] = 0;
+    N.excess[x] = rem;
+    Ln[x] = rem > 0 ? min(min(cand, dx + 2), NL) : dx;
+    if (rem > 0) want = atomicExch(&N.stamp[x], epoch) != epoch;
+    a.nodes++;
+  }
+  if (threadIdx.x < 32) append_split(want, x, true, nl, S.c[C_NEXT], S.c[C_NEXTH], 0, 0, NL);
+}
+
+// Delta buffers of round `rounds`: pushes go to cur, the previous round's
+// pushes are read from prev.
+__device__ __forceinline__ long long* delta_cur(const NetDev& N, unsigned long long rounds) {
+  return (rounds & 1) ? N.delta1 : N.delta;
+}
+__device__ __forceinline__ long long* delta_prev(const NetDev& N, unsigned long long rounds) {
+  return (rounds & 1) ? N.delta : N.delta1;
+}
+
+__device__ void phase_round(const NetDev& N, const Sched& L, const Team& T, const Slot& S,
+                            unsigned lane, Acc& a) {
+  const int32_t* Lr = lab_cur(N, L.lp);
+  int32_t* Ln = lab_cur(N, L.lp ^ 1);
+  long long* dcur = delta_cur(N, L.rounds);
+  long long* dprev = delta_prev(N, L.rounds);
+  const int32_t* fl = N.list[L.fsel];
+  int32_t* nl = N.list[L.fsel ^ 1];
+  long long sink_acc = 0;
+  constexpr unsigned TPW = 32 / kTeam;
+  for (unsigned base = T.gwarp * TPW; base < L.fcnt; base += T.nwarps * TPW) {
+    const unsigned i = base + lane / kTeam;
+    round_team<kTeam>(N, i < L.fcnt ? fl[i] : -1, Lr, Ln, dprev, dcur, nl, L.epoch, lane,
+                      sink_acc, a, S);
+  }
+  for (unsigned h = T.block; h < L.fcnth; h += T.nblocks)
+    round_block(N, fl[N.NL - 1 - h], Lr, Ln, dprev, dcur, nl, L.epoch, sink_acc, a, S);
+  sink_acc = warp_sum(sink_acc);
+  if (lane == 0 && sink_acc) atomicAdd(S.flow, (unsigned long long)sink_acc);
+}
+
+// The last one-phase round's pushes are applied before a global relabel (the
+// frontier list holds every node they reached).
+__device__ void phase_flush(const NetDev& N, const Sched& L, const Team& T) {
+  long long* dprev = delta_prev(N, L.rounds);
+  const int32_t* fl = N.list[L.fsel];
+  const unsigned tot = L.fcnt + L.fcnth;
+  for (unsigned i = T.tid; i < tot; i += T.nth) {
+    const int y = i < L.fcnt ? fl[i] : fl[N.NL - 1 - (i - L.fcnt)];
+    const long long d = __ldcg(&dprev[y]);
+    if (d) {
+      N.excess[y] += d;
+      dprev[y] = 0;
+    }
+  }
+}
+
 // Global relabel, step 1: exact labels start from the sinks (Section 2,
 // "global relabeling").
 __device__ void gr_init(const NetDev& N, EngineCtl* E, const Sched& L, const Team& T,
@@ -1381,6 +1724,8 @@ __device__ void run_phase_s(const NetDev& N, EngineCtl* E, const Sched& L, const
                             const Params& P) {
   switch (L.state) {
     case ST_ROUND_A: phase_a(N, L, T, S, lane, a, E); break;
+    case ST_ROUND: phase_round(N, L, T, S, lane, a); break;
+    case ST_FLUSH: phase_flush(N, L, T); break;
     case ST_ROUND_B: phase_b(N, L, T, S, lane, a); break;
     case ST_GR_INIT: gr_init(N, E, L, T, S, lane, a); break;
     case ST_GR_SEED: gr_seed(N, E, L, T, lane); break;
@@ -1440,7 +1785,7 @@ __device__ void trace_phase(const NetDev& N, Ctl* c, const Sched& L, int st, boo
                             const Snap& q, unsigned long long dt) {
   if (!N.trace || c->trace_len >= N.trace_cap) return;
   unsigned long long a = 0, b = 0, oa = 0, ob = 0;
-  if (st == ST_ROUND_A) {
+  if (st == ST_ROUND_A || st == ST_ROUND || st == ST_FLUSH) {
     a = L.fcnt; b = L.fcnth; oa = q.c[C_NEXT]; ob = q.c[C_NEXTH];
   } else if (st == ST_ROUND_B) {
     a = L.ncnt; b = L.ncnth; oa = q.c[C_FRONT]; ob = q.c[C_FRONTH];
@@ -1488,7 +1833,7 @@ __device__ void solo_phases(const NetDev& N, EngineCtl* E, const Params& P, Sche
   const Team T{threadIdx.x >> 5, blockDim.x >> 5, threadIdx.x, blockDim.x, 0, 1};
   __syncthreads();   // every thread has read the caller's state before it is rewritten
   if (threadIdx.x == 0) {
-    if (L.state == ST_TAIL) L.state = ST_ROUND_A;
+    if (L.state == ST_TAIL) L.state = round_state(P);
     sh.act[0] = ld_cg(&E->gr_act[0]);
     sh.act[1] = ld_cg(&E->gr_act[1]);
   }
@@ -1528,11 +1873,11 @@ __device__ void solo_phases(const NetDev& N, EngineCtl* E, const Params& P, Sche
         // loads of the next phases, which the grid barrier's acquire does
         stay = false;
       } else if (s2 == ST_TAIL) {
-        L.state = ST_ROUND_A;
+        L.state = round_state(P);
         stay = true;
-      } else if (s2 == ST_ROUND_B) {
+      } else if (s2 == ST_ROUND_B || s2 == ST_FLUSH) {
         stay = true;
-      } else if (s2 == ST_ROUND_A) {
+      } else if (s2 == ST_ROUND_A || s2 == ST_ROUND) {
         stay = L.fcnt + L.fcnth <= P.tail_exit;
       } else if (is_level(s2)) {
         stay = level_size(L) <= P.bfs_exit;
@@ -1581,6 +1926,7 @@ __device__ void load_sched(Sched& L, const EngineCtl* E) {
   L.seed = v->seed;
   L.last_gr = v->last_gr;
   L.gr_sync = v->gr_sync;
+  L.fsel = v->fsel;
   L.rounds = v->rounds;
   L.grs = v->grs;
   L.gr_levels = v->gr_levels;
@@ -1617,6 +1963,7 @@ __device__ void store_sched(EngineCtl* E, const Sched& L) {
   v->seed = L.seed;
   v->last_gr = L.last_gr;
   v->gr_sync = L.gr_sync;
+  v->fsel = L.fsel;
   v->rounds = L.rounds;
   v->grs = L.grs;
   v->gr_levels = L.gr_levels;
@@ -1647,6 +1994,11 @@ __global__ void __launch_bounds__(kEngineThreads) engine_kernel(NetDev N, Engine
   if (threadIdx.x == 0) {
     load_sched(L, E);
     if (ld_volatile_int(&E->c.err) != kDevOk) L.state = ST_DONE;   // left by an earlier launch
+    if (L.state == ST_ROUND_A && P.fused_rounds) {
+      // rounds set up by the host (new excess in the frontier list)
+      L.state = ST_ROUND;
+      L.fsel = L_FRONT;
+    }
     L.flow = *(const volatile unsigned long long*)&E->c.flow;  // host kernels add to it
     acc_sh = Acc{0, 0, 0, 0, 0};
     w_sh = 0;

@@ -28,6 +28,8 @@ enum EngineState : int {
   ST_GR_ADD = 16,   // sink-side cut grown from one new sink (T_r and its labels kept)
   ST_GR_SEED = 17,  // asynchronous global relabel: the sinks enter the work queue
   ST_GR_RUN = 18,   // asynchronous global relabel: label-correcting search to the end
+  ST_ROUND = 19,    // one-phase round: apply last round's pushes, discharge, relabel
+  ST_FLUSH = 20,    // apply the pushes of the last one-phase round (before a relabel)
 };
 
 // list ids in NetDev::list.  Each list array holds light nodes from the front
@@ -54,6 +56,7 @@ struct Sched {
   int seed;               // ST_SR_ADD / ST_GR_ADD: the node whose reach joins S_r / T_r
   unsigned int last_gr;   // levels of the last global relabel
   int gr_sync;            // this global relabel runs level by level (queue overflowed)
+  int fsel;               // one-phase rounds: list holding the frontier (L_FRONT / L_NEXT)
   unsigned long long rounds, grs, gr_levels, work, stall, flow, flow_ref;
   unsigned long long gq_items, gq_overs;   // queue entries expanded, queue overflows
   unsigned gq_prev;       // queue slots written by the last asynchronous relabel
@@ -77,7 +80,7 @@ struct Params {
   unsigned int stall_adapt;          // stall limit = levels of the last global relabel
   unsigned int async_gr;             // global relabels as one queue-driven search
   unsigned int gr_warps;             // warps per CTA that serve that search's queue
-  unsigned int pad;
+  unsigned int fused_rounds;         // one phase per discharge round (needs NetDev::delta1)
 };
 
 struct EngineCtl {

@@ -74,5 +74,7 @@ void launch_cut_net_compact(const NetDev& N, const unsigned* flags, const unsign
                             const int32_t* net_gid, int32_t* out, int32_t cap, int sms,
                             cudaStream_t st);
 void launch_inc_slots(const NetDev& N, int32_t* out, int sms, cudaStream_t st);
+void launch_add_i64(const long long* a, const long long* b, long long* out, long long n, int sms,
+                    cudaStream_t st);
 
 }  // namespace hfp

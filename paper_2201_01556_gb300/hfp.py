@@ -54,7 +54,7 @@ class Tuning(ctypes.Structure):
                                                "bfs_enter", "bfs_exit", "pierce_relabel",
                                                "stall_rounds_pierce", "batch_cluster",
                                                "batch_big_ctas", "batch_big_groups",
-                                               "async_gr", "gr_warps")]
+                                               "async_gr", "gr_warps", "fused_rounds")]
 
 
 class RefineParams(ctypes.Structure):

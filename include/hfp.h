@@ -156,7 +156,7 @@ uint64_t hfp_kernel_launches(void);
  *                 label-correcting search driven by a device work queue,
  *                 without a grid barrier per breadth-first level; the labels
  *                 are the same exact distances [1]
- *   gr_warps      warps per CTA that serve that queue (1..16) [8]
+ *   gr_warps      warps per CTA that serve that queue (1..16) [12]
  *   fused_rounds  one grid-wide phase per discharge round: each node applies
  *                 the previous round's pushes, discharges and relabels itself
  *                 from its own residual arcs, raising its label by at most 2;

@@ -67,9 +67,41 @@ hfp_status read_ctl(hfp_net* net, Ctl* out) {
   return HFP_OK;
 }
 
+// Buffers only the plain engine's one-phase rounds and queue-driven global
+// relabels use (the batched FlowCutter runs without them), allocated at the
+// network's first launch that needs them.
+hfp_status ensure_engine_buffers(hfp_net* net, const Params& P) {
+  hfp_ctx* c = net->ctx;
+  NetDev& D = net->d;
+  const size_t NL = (size_t)D.NL;
+  if (P.fused_rounds && !D.delta1) {
+    CK(cudaMallocAsync(&net->delta1_buf, sizeof(long long) * (NL ? NL : 1), c->stream));
+    CK(cudaMemsetAsync(net->delta1_buf, 0, sizeof(long long) * (NL ? NL : 1), c->stream));
+    D.delta1 = (long long*)net->delta1_buf;
+  }
+  // Work queue of the global relabel: room for every node's chunks four
+  // times (a node is queued again whenever its label drops; the sinks of a
+  // relabel after sink-side piercings are all seeds); a fuller queue makes
+  // that relabel fall back to the level-by-level search.  Entries hold
+  // 27-bit Lawler ids: larger networks relabel level by level.
+  if (P.async_gr && !D.gq && D.NL < (1 << 27) - 1) {
+    const uint64_t cap64 = 4 * ((uint64_t)D.NL + (uint64_t)D.p_pins / 8) + 4096;
+    const unsigned cap = cap64 < 0xF0000000ull ? (unsigned)cap64 : 0xF0000000u;
+    CK(cudaMallocAsync(&net->gq_buf, sizeof(unsigned long long) * cap, c->stream));
+    CK(cudaMemsetAsync(net->gq_buf, 0, sizeof(unsigned long long) * cap, c->stream));   // empty
+    D.gq = (unsigned long long*)net->gq_buf;
+    D.gq_cap = cap;
+  }
+  return HFP_OK;
+}
+
 hfp_status run_engine(hfp_net* net) {
   hfp_ctx* c = net->ctx;
   Params P = c->params;
+  if (hfp_status s0 = ensure_engine_buffers(net, P)) return s0;
+  // without its buffers the engine runs the two-phase, level-by-level forms
+  if (!net->d.delta1) P.fused_rounds = 0;
+  if (!net->d.gq) P.async_gr = 0;
   // flows after a piercing are incremental: their own stall rule
   if (net->pierced) {
     if (P.stall_rounds_pierce) P.stall_rounds = P.stall_rounds_pierce;
@@ -211,7 +243,7 @@ HFP_API hfp_status hfp_ctx_create(hfp_ctx** out, int device, void* stream) {
   c->params.stall_rounds_pierce = 0;    // incremental flows after a piercing: adaptive
   c->params.stall_adapt = 0;
   c->params.async_gr = 1;          // global relabels as one queue-driven search
-  c->params.gr_warps = 8;          // warps per CTA serving its queue (fewer: less re-expansion)
+  c->params.gr_warps = 12;         // warps per CTA serving its queue (fewer: less re-expansion)
   c->params.fused_rounds = 1;      // one phase per discharge round
   *out = c;
   return HFP_OK;
@@ -242,6 +274,8 @@ HFP_API void hfp_net_destroy(hfp_net* net) {
   if (net->arena) cudaFreeAsync(net->arena, st);
   if (net->dev_nodes) cudaFreeAsync(net->dev_nodes, st);
   if (net->trace_buf) cudaFreeAsync(net->trace_buf, st);
+  if (net->gq_buf) cudaFreeAsync(net->gq_buf, st);
+  if (net->delta1_buf) cudaFreeAsync(net->delta1_buf, st);
   cudaStreamSynchronize(st);
   delete net;
   ctx_release(c);
@@ -395,14 +429,6 @@ HFP_API hfp_status hfp_build_flow_network(hfp_ctx* ctx, const hfp_hypergraph* H,
   // W of the flow problem: c(s) + c(t) + c(B)
   const int64_t total_w = (int64_t)hh->wsum[0] + (int64_t)hh->wsum[1] + (int64_t)hh->wsum[4];
 
-  // work queue of the asynchronous global relabel: room for every node's
-  // chunks twice (a node is queued again whenever its label drops); a fuller
-  // queue makes that relabel fall back to the level-by-level search
-  const uint64_t gq_cap64 = 2 * ((uint64_t)NL + (uint64_t)p_net / 8) + 4096;
-  // (entries hold 27-bit Lawler ids: larger networks relabel level by level)
-  const unsigned gq_cap =
-      NL64 >= (1ll << 27) - 1 ? 0u : (gq_cap64 < 0xF0000000ull ? (unsigned)gq_cap64 : 0xF0000000u);
-
   // arena for the network and its flow state
   hfp_net* net = new hfp_net();
   net->ctx = ctx;
@@ -415,8 +441,7 @@ HFP_API hfp_status hfp_build_flow_network(hfp_ctx* ctx, const hfp_hypergraph* H,
       sizeof(int32_t) * p_net, sizeof(int32_t) * p_net, sizeof(int32_t) * m_net,
       sizeof(int32_t) * NL, sizeof(int32_t) * NL, sizeof(long long) * NL, sizeof(long long) * NL,
       sizeof(uint32_t) * NL, (size_t)NL, (size_t)NL, (size_t)NL, sizeof(int32_t) * NL,
-      sizeof(int32_t) * NL, sizeof(int32_t) * NL, sizeof(int32_t) * NL, sizeof(EngineCtl),
-      sizeof(unsigned long long) * gq_cap, sizeof(long long) * NL};
+      sizeof(int32_t) * NL, sizeof(int32_t) * NL, sizeof(int32_t) * NL, sizeof(EngineCtl)};
   size_t total = 0;
   for (size_t b : sz) total += align_up(b);
   cudaError_t ae = cudaMallocAsync(&net->arena, total, st);
@@ -470,9 +495,6 @@ HFP_API hfp_status hfp_build_flow_network(hfp_ctx* ctx, const hfp_hypergraph* H,
   D.insr = (uint8_t*)ptr[20];
   for (int k = 0; k < 4; k++) D.list[k] = (int32_t*)ptr[21 + k];
   net->E = (EngineCtl*)ptr[25];
-  D.gq = gq_cap ? (unsigned long long*)ptr[26] : nullptr;
-  D.delta1 = (long long*)ptr[27];
-  D.gq_cap = gq_cap;
   net->total_w = total_w;
 
   hfp_status rs = HFP_OK;
@@ -491,7 +513,6 @@ HFP_API hfp_status hfp_build_flow_network(hfp_ctx* ctx, const hfp_hypergraph* H,
   CKN(cudaMemcpyAsync(node_w, a_w, sizeof(int32_t) * n_nodes, cudaMemcpyDeviceToDevice, st));
   CKN(cudaMemcpyAsync(node_orig, a_orig, n_nodes, cudaMemcpyDeviceToDevice, st));
   CKN(cudaMemsetAsync(D.flags, 0, NL, st));
-  if (gq_cap) CKN(cudaMemsetAsync(D.gq, 0, sizeof(unsigned long long) * gq_cap, st));   // empty slots
   launch_st_attrs(node_gid, node_w, node_orig, wsum.as<unsigned long long>(), D.flags,
                   err.as<int>(), st);
   launch_net_fill(m, d_off, d_pins, d_netw, loc.as<int32_t>(), keep.as<unsigned>(),
@@ -526,7 +547,6 @@ HFP_API hfp_status hfp_build_flow_network(hfp_ctx* ctx, const hfp_hypergraph* H,
   CKN(cudaMemsetAsync(D.f_b, 0, sizeof(int32_t) * m_net, st));
   CKN(cudaMemsetAsync(D.excess, 0, sizeof(long long) * NL, st));
   CKN(cudaMemsetAsync(D.delta, 0, sizeof(long long) * NL, st));
-  CKN(cudaMemsetAsync(D.delta1, 0, sizeof(long long) * NL, st));
   CKN(cudaMemsetAsync(D.stamp, 0, sizeof(uint32_t) * NL, st));
   CKN(cudaMemsetAsync(D.needrl, 0, NL, st));
   CKN(cudaMemsetAsync(D.insr, 0, NL, st));

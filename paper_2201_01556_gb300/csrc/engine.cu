@@ -883,17 +883,23 @@ __device__ void phase_b(const NetDev& N, const Sched& L, const Team& T, const Sl
 // changes keeps excess, so it is in the next frontier and copies its label
 // into the other buffer there.
 
-__device__ __forceinline__ bool deliver_to(const NetDev& N, long long* dcur, int y, long long d,
-                                           unsigned epoch, long long& sink_acc, bool& heavy) {
-  const uint8_t fl = N.flags[y];
-  heavy = (fl & kHeavy) != 0;
+// A round's delta word of a node doubles as its membership of the next
+// frontier: the first addition (a push, or kSelf by a node that keeps
+// excess) finds zero and appends the node.  Readers strip kSelf.
+constexpr long long kSelf = 1ll << 62;
+
+__device__ __forceinline__ long long strip_self(long long d) { return d & ~kSelf; }
+
+// Push of d into y (flag byte fl of y, loaded with its label).  Returns true
+// when y must join the next frontier.
+__device__ __forceinline__ bool deliver_to(long long* dcur, int y, uint8_t fl, long long d,
+                                           long long& sink_acc) {
   if (fl & kSink) {
     sink_acc += d;
     return false;
   }
   if (fl & kSource) return false;
-  atomicAdd((unsigned long long*)&dcur[y], (unsigned long long)d);
-  return atomicExch(&N.stamp[y], epoch) != epoch;
+  return atomicAdd((unsigned long long*)&dcur[y], (unsigned long long)d) == 0ull;
 }
 
 // Arc group k of node x for a discharge with relabel: admissible residuals
@@ -905,7 +911,8 @@ __device__ __forceinline__ void arc_group(const NetDev& N, const NodeArcs& g, un
                                           int fb, const int32_t* Lr, int dt, long long rem,
                                           long long& r1, long long& r2, long long& q1,
                                           long long& q2, int& l1, int& l2, int& y1, int& y2,
-                                          int& p, int& fi, int& fo, Acc& a) {
+                                          uint8_t& f1, uint8_t& f2, int& p, int& fi, int& fo,
+                                          Acc& a) {
   const int nh = N.n_nodes, m = N.m_nets;
   if (g.kind == 0) {
     const int2 it = N.inc[g.beg + k];
@@ -917,6 +924,8 @@ __device__ __forceinline__ void arc_group(const NetDev& N, const NodeArcs& g, un
     y2 = nh + m + it.x;
     l1 = Lr[y1];
     l2 = Lr[y2];
+    f1 = N.flags[y1];
+    f2 = N.flags[y2];
     q1 = ww - fi;
     q2 = fo;
     if (q1 > 0 && l1 == dt) r1 = q1;
@@ -927,14 +936,17 @@ __device__ __forceinline__ void arc_group(const NetDev& N, const NodeArcs& g, un
       y1 = nh + m + g.e;
       q1 = w - fb;
       l1 = Lr[y1];
+      f1 = N.flags[y1];
       if (q1 > 0 && l1 == dt) r1 = q1;
     } else {
       p = g.beg + k - 1;
       fi = N.f_in[p];
+      const int u = N.pin[p];
       q1 = fi;
       if (fi > 0) {
-        y1 = N.pin[p];
+        y1 = u;
         l1 = Lr[y1];
+        f1 = N.flags[y1];
         if (l1 == dt) r1 = fi;
       }
     }
@@ -945,12 +957,14 @@ __device__ __forceinline__ void arc_group(const NetDev& N, const NodeArcs& g, un
       q1 = fb;
       if (fb > 0) {
         l1 = Lr[y1];
+        f1 = N.flags[y1];
         if (l1 == dt) r1 = fb;
       }
     } else {
       p = g.beg + k - 1;
       y1 = N.pin[p];
       l1 = Lr[y1];
+      f1 = N.flags[y1];
       q1 = kInfRes;
       if (l1 == dt) r1 = rem;
     }
@@ -986,17 +1000,18 @@ __device__ __forceinline__ int group_cand(long long q1, long long q2, int l1, in
 // One-phase discharge of node x by a team of TW lanes (x < 0: idle team).
 template <int TW>
 __device__ void round_team(const NetDev& N, int x, const int32_t* Lr, int32_t* Ln,
-                           long long* dprev, long long* dcur, int32_t* nl, unsigned epoch,
-                           unsigned lane, long long& sink_acc, Acc& a, const Slot& S) {
+                           long long* dprev, long long* dcur, int32_t* nl, unsigned lane,
+                           long long& sink_acc, Acc& a, const Slot& S) {
   const int NL = N.NL;
   const unsigned tl = lane & (TW - 1);
-  long long ex = 0, dp = 0;
+  long long ex = 0, dp0 = 0;
   int dx = NL;
   if (x >= 0) {
     ex = __ldcg(&N.excess[x]);
-    dp = __ldcg(&dprev[x]);
+    dp0 = __ldcg(&dprev[x]);
     dx = Lr[x];
   }
+  const long long dp = strip_self(dp0);
   ex += dp;
   const bool act = x >= 0 && ex > 0 && dx < NL;
   long long rem = act ? ex : 0;
@@ -1016,36 +1031,39 @@ __device__ void round_team(const NetDev& N, int x, const int32_t* Lr, int32_t* L
     const unsigned k = c * TW + tl;
     long long r1 = 0, r2 = 0, q1 = -1, q2 = -1;
     int l1 = NL, l2 = NL, y1 = -1, y2 = -1, p = 0, fi = 0, fo = 0;
+    uint8_t f1 = 0, f2 = 0;
     if (rem > 0 && k < g.items)
-      arc_group(N, g, k, w, fb, Lr, dt, rem, r1, r2, q1, q2, l1, l2, y1, y2, p, fi, fo, a);
+      arc_group(N, g, k, w, fb, Lr, dt, rem, r1, r2, q1, q2, l1, l2, y1, y2, f1, f2, p, fi, fo,
+                a);
     const long long r = r1 + r2;
     const long long incl = team_incl_scan<TW>(r, tl);
     const long long take = min(max(rem - (incl - r), 0LL), r);
     const long long t1 = min(take, r1), t2 = take - t1;
     cand = group_cand(q1, q2, l1, l2, t1, t2, cand);
     apply_takes(N, g, k, fb, p, fi, fo, t1, t2);
-    bool a1 = false, a2 = false, h1 = false, h2 = false;
+    bool a1 = false, a2 = false;
     if (t1 > 0) {
-      a1 = deliver_to(N, dcur, y1, t1, epoch, sink_acc, h1);
+      a1 = deliver_to(dcur, y1, f1, t1, sink_acc);
       a.pushes++;
     }
     if (t2 > 0) {
-      a2 = deliver_to(N, dcur, y2, t2, epoch, sink_acc, h2);
+      a2 = deliver_to(dcur, y2, f2, t2, sink_acc);
       a.pushes++;
     }
-    append_split(a1, y1, h1, nl, S.c[C_NEXT], S.c[C_NEXTH], 0, 0, NL);
-    append_split(a2, y2, h2, nl, S.c[C_NEXT], S.c[C_NEXTH], 0, 0, NL);
+    append_split(a1, y1, (f1 & kHeavy) != 0, nl, S.c[C_NEXT], S.c[C_NEXTH], 0, 0, NL);
+    append_split(a2, y2, (f2 & kHeavy) != 0, nl, S.c[C_NEXT], S.c[C_NEXTH], 0, 0, NL);
     const long long tot = __shfl_sync(FULL, incl, TW - 1, TW);
     rem -= min(rem, tot);
   }
   cand = team_min<TW>(cand);
   bool want = false;
   if (x >= 0 && tl == 0) {
-    if (dp) dprev[x] = 0;
+    if (dp || dp0) dprev[x] = 0;
     if (act) {
       N.excess[x] = rem;
       Ln[x] = rem > 0 ? min(min(cand, dx + 2), NL) : dx;
-      if (rem > 0) want = atomicExch(&N.stamp[x], epoch) != epoch;
+      if (rem > 0)
+        want = atomicAdd((unsigned long long*)&dcur[x], (unsigned long long)kSelf) == 0ull;
       a.nodes++;
     } else {
       // no excess, or cut off from the sinks: keep the excess and the label
@@ -1058,19 +1076,18 @@ __device__ void round_team(const NetDev& N, int x, const int32_t* Lr, int32_t* L
 
 // One-phase discharge of one heavy node by the whole CTA.
 __device__ void round_block(const NetDev& N, int x, const int32_t* Lr, int32_t* Ln,
-                            long long* dprev, long long* dcur, int32_t* nl, unsigned epoch,
-                            long long& sink_acc, Acc& a, const Slot& S) {
+                            long long* dprev, long long* dcur, int32_t* nl, long long& sink_acc,
+                            Acc& a, const Slot& S) {
   const int NL = N.NL;
-  const long long dp = __ldcg(&dprev[x]);
+  const long long dp0 = __ldcg(&dprev[x]);
+  const long long dp = strip_self(dp0);
   const long long ex = __ldcg(&N.excess[x]) + dp;
   const int dx = Lr[x];
   if (ex <= 0 || dx >= NL) {   // uniform over the CTA
     __syncthreads();           // every thread has read dprev[x] before it is cleared
     if (threadIdx.x == 0) {
-      if (dp) {
-        dprev[x] = 0;
-        N.excess[x] = ex;
-      }
+      if (dp0) dprev[x] = 0;
+      if (dp) N.excess[x] = ex;
       Ln[x] = dx;
     }
     return;
@@ -1085,8 +1102,10 @@ __device__ void round_block(const NetDev& N, int x, const int32_t* Lr, int32_t* 
     const unsigned k = k0 + threadIdx.x;
     long long r1 = 0, r2 = 0, q1 = -1, q2 = -1;
     int l1 = NL, l2 = NL, y1 = -1, y2 = -1, p = 0, fi = 0, fo = 0;
+    uint8_t f1 = 0, f2 = 0;
     if (k < g.items)
-      arc_group(N, g, k, w, fb, Lr, dt, rem, r1, r2, q1, q2, l1, l2, y1, y2, p, fi, fo, a);
+      arc_group(N, g, k, w, fb, Lr, dt, rem, r1, r2, q1, q2, l1, l2, y1, y2, f1, f2, p, fi, fo,
+                a);
     const long long r = r1 + r2;
     long long tot;
     const long long incl = block_incl_scan(r, &tot);
@@ -1094,26 +1113,27 @@ __device__ void round_block(const NetDev& N, int x, const int32_t* Lr, int32_t* 
     const long long t1 = min(take, r1), t2 = take - t1;
     cand = group_cand(q1, q2, l1, l2, t1, t2, cand);
     apply_takes(N, g, k, fb, p, fi, fo, t1, t2);
-    bool a1 = false, a2 = false, h1 = false, h2 = false;
+    bool a1 = false, a2 = false;
     if (t1 > 0) {
-      a1 = deliver_to(N, dcur, y1, t1, epoch, sink_acc, h1);
+      a1 = deliver_to(dcur, y1, f1, t1, sink_acc);
       a.pushes++;
     }
     if (t2 > 0) {
-      a2 = deliver_to(N, dcur, y2, t2, epoch, sink_acc, h2);
+      a2 = deliver_to(dcur, y2, f2, t2, sink_acc);
       a.pushes++;
     }
-    append_split(a1, y1, h1, nl, S.c[C_NEXT], S.c[C_NEXTH], 0, 0, NL);
-    append_split(a2, y2, h2, nl, S.c[C_NEXT], S.c[C_NEXTH], 0, 0, NL);
+    append_split(a1, y1, (f1 & kHeavy) != 0, nl, S.c[C_NEXT], S.c[C_NEXTH], 0, 0, NL);
+    append_split(a2, y2, (f2 & kHeavy) != 0, nl, S.c[C_NEXT], S.c[C_NEXTH], 0, 0, NL);
     rem -= min(rem, tot);
   }
   cand = block_min(cand);
   bool want = false;
   if (threadIdx.x == 0) {
-    if (dp) dprev[x] = 0;
+    if (dp0) dprev[x] = 0;
     N.excess[x] = rem;
     Ln[x] = rem > 0 ? min(min(cand, dx + 2), NL) : dx;
-    if (rem > 0) want = atomicExch(&N.stamp[x], epoch) != epoch;
+    if (rem > 0)
+      want = atomicAdd((unsigned long long*)&dcur[x], (unsigned long long)kSelf) == 0ull;
     a.nodes++;
   }
   if (threadIdx.x < 32) append_split(want, x, true, nl, S.c[C_NEXT], S.c[C_NEXTH], 0, 0, NL);
@@ -1138,13 +1158,28 @@ __device__ void phase_round(const NetDev& N, const Sched& L, const Team& T, cons
   int32_t* nl = N.list[L.fsel ^ 1];
   long long sink_acc = 0;
   constexpr unsigned TPW = 32 / kTeam;
-  for (unsigned base = T.gwarp * TPW; base < L.fcnt; base += T.nwarps * TPW) {
-    const unsigned i = base + lane / kTeam;
-    round_team<kTeam>(N, i < L.fcnt ? fl[i] : -1, Lr, Ln, dprev, dcur, nl, L.epoch, lane,
-                      sink_acc, a, S);
+  // While heavy nodes fill at most half of the CTAs, the last fcnth CTAs take
+  // one heavy node each and no light ones, so that a heavy node's longer
+  // chain runs beside the light work instead of after it.
+  const unsigned nwb = blockDim.x >> 5;
+  const bool split = L.fcnth > 0 && 2 * L.fcnth <= T.nblocks;
+  const unsigned light_blocks = split ? T.nblocks - L.fcnth : T.nblocks;
+  if (T.block < light_blocks) {
+    const unsigned w0 = T.block * nwb + (threadIdx.x >> 5), nw = light_blocks * nwb;
+    for (unsigned base = w0 * TPW; base < L.fcnt; base += nw * TPW) {
+      const unsigned i = base + lane / kTeam;
+      round_team<kTeam>(N, i < L.fcnt ? fl[i] : -1, Lr, Ln, dprev, dcur, nl, lane, sink_acc, a,
+                        S);
+    }
   }
-  for (unsigned h = T.block; h < L.fcnth; h += T.nblocks)
-    round_block(N, fl[N.NL - 1 - h], Lr, Ln, dprev, dcur, nl, L.epoch, sink_acc, a, S);
+  if (split) {
+    if (T.block >= light_blocks)
+      round_block(N, fl[N.NL - 1 - (T.block - light_blocks)], Lr, Ln, dprev, dcur, nl, sink_acc,
+                  a, S);
+  } else {
+    for (unsigned h = T.block; h < L.fcnth; h += T.nblocks)
+      round_block(N, fl[N.NL - 1 - h], Lr, Ln, dprev, dcur, nl, sink_acc, a, S);
+  }
   sink_acc = warp_sum(sink_acc);
   if (lane == 0 && sink_acc) atomicAdd(S.flow, (unsigned long long)sink_acc);
 }
@@ -1159,7 +1194,7 @@ __device__ void phase_flush(const NetDev& N, const Sched& L, const Team& T) {
     const int y = i < L.fcnt ? fl[i] : fl[N.NL - 1 - (i - L.fcnt)];
     const long long d = __ldcg(&dprev[y]);
     if (d) {
-      N.excess[y] += d;
+      N.excess[y] += strip_self(d);
       dprev[y] = 0;
     }
   }

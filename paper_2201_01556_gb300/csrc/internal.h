@@ -90,6 +90,8 @@ struct hfp_net {
   bool gr_pending = false;
   bool pierced = false;            // flows from now on are incremental
   void* trace_buf = nullptr;
+  void* gq_buf = nullptr;          // work queue of queue-driven global relabels
+  void* delta1_buf = nullptr;      // second delta buffer of one-phase rounds
   uint64_t launches = 0;
   uint64_t engine_ns = 0;
 };

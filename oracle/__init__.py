@@ -45,7 +45,13 @@ def build(force: bool = False) -> str:
 class _FcResult(ctypes.Structure):
     _fields_ = [("flow", ctypes.c_int64), ("iterations", ctypes.c_int32),
                 ("n_pierced", ctypes.c_int32), ("result_side", ctypes.c_int32),
-                ("status", ctypes.c_int32), ("source_weight", ctypes.c_int64)]
+                ("status", ctypes.c_int32), ("source_weight", ctypes.c_int64),
+                ("bulk_steps", ctypes.c_int32), ("mb_steps", ctypes.c_int32)]
+
+
+class _FcOptions(ctypes.Structure):
+    _fields_ = [("bulk_beta_pct", ctypes.c_int32), ("bulk_warmup", ctypes.c_int32),
+                ("mb_reps", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 
 def _load():
@@ -57,6 +63,10 @@ def _load():
         lib.or_build_network.argtypes = [i32, i32, P, P, P, P, P, P, i32, P, P, P, P, P, P]
         lib.or_dist_from_cut.restype = i32
         lib.or_dist_from_cut.argtypes = [i32, i32, P, P, P, P, i32, P]
+        lib.or_dedup_nets.restype = i32
+        lib.or_dedup_nets.argtypes = [i32, P, P, P, P, P, P, P, P, P]
+        lib.or_seqpr.restype = i64
+        lib.or_seqpr.argtypes = [i32, i32, P, P, P, P, P, P]
         lib.or_lawler_create.restype = P
         lib.or_lawler_create.argtypes = [i32, i32, P, P, P, P]
         lib.or_lawler_free.restype = None
@@ -79,6 +89,9 @@ def _load():
         lib.or_export_arcs.argtypes = [P, P, P, P, P]
         lib.or_bruteforce.restype = i32
         lib.or_bruteforce.argtypes = [i32, i32, P, P, P, P, i64, P, P, P, P, P]
+        lib.or_flowcutter_ex.restype = i32
+        lib.or_flowcutter_ex.argtypes = [P, i64, P, P, P, u32, i64, i32, i32, P, P, P, P, i32,
+                                         P]
         lib.or_flowcutter.restype = i32
         lib.or_flowcutter.argtypes = [P, i64, P, P, P, u32, i64, i32, i32, P, P, P, i32,
                                       ctypes.POINTER(_FcResult)]
@@ -138,6 +151,26 @@ def build_network(H, side, region) -> FlowNetwork:
     mm = int(out_m[0])
     return FlowNetwork(nr + 2, mm, nnet_off[: mm + 1].copy(), npins[:p].copy(),
                        nnet_w[:mm].copy(), nnet_gid[:mm].copy(), nnode_w)
+
+
+def dedup_network(net: FlowNetwork) -> FlowNetwork:
+    """Identical net removal (Section 6, "Identical Net Removal"), read as in
+    oracle.c: the flow hypergraph with every net merged into the smallest-id
+    net with the same pin set (found through (fingerprint, size) groups)."""
+    lib = _load()
+    m = net.m_nets
+    off = np.zeros(m + 1, np.uint32)
+    pins = np.zeros(max(net.p, 1), np.int32)
+    w = np.zeros(max(m, 1), np.int32)
+    gid = np.zeros(max(m, 1), np.int32)
+    rep = np.zeros(max(m, 1), np.int32)
+    mm = lib.or_dedup_nets(m, _p(_c(net.net_off, np.uint32)), _p(_c(net.pins, np.int32)),
+                           _p(_c(net.net_w, np.int32)), _p(_c(net.net_gid, np.int32)), _p(off),
+                           _p(pins), _p(w), _p(gid), _p(rep))
+    if mm < 0:
+        raise MemoryError("or_dedup_nets failed")
+    return FlowNetwork(net.n_nodes, int(mm), off[: mm + 1].copy(), pins[: off[mm]].copy(),
+                       w[:mm].copy(), gid[:mm].copy(), net.node_w.copy())
 
 
 def dist_from_cut(H, side, region) -> np.ndarray:
@@ -232,6 +265,34 @@ def max_flow_min_cut(net: FlowNetwork, algo: str = "dinic") -> MinCut:
     return MinCut(G.flow_value(S), G.reach_from(S), G.reach_to(T), G)
 
 
+@dataclass
+class SeqPRResult:
+    flow: int
+    source_side: np.ndarray   # uint8[N]: S_r
+    sink_side: np.ndarray     # uint8[N]: T_r
+    pushes: int
+    relabels: int
+    global_relabels: int
+
+
+def seqpr(net: FlowNetwork) -> SeqPRResult:
+    """Sequential FIFO push-relabel on the flow hypergraph with global
+    relabeling, to a maximum preflow (the paper's SeqPR baseline, Appendix
+    "Flow Algorithms"; Section 2, "Push-Relabel Algorithm"), with both
+    minimal cut sides."""
+    lib = _load()
+    N = net.lawler_nodes
+    src = np.zeros(max(N, 1), np.uint8)
+    snk = np.zeros(max(N, 1), np.uint8)
+    st = np.zeros(4, np.int64)
+    f = lib.or_seqpr(net.n_nodes, net.m_nets, _p(_c(net.net_off, np.uint32)),
+                     _p(_c(net.pins, np.int32)), _p(_c(net.net_w, np.int32)), _p(src), _p(snk),
+                     _p(st))
+    if f < 0:
+        raise MemoryError(f"or_seqpr failed: {f}")
+    return SeqPRResult(int(f), src[:N], snk[:N], int(st[0]), int(st[1]), int(st[2]))
+
+
 def cut_weight(net: FlowNetwork, in_source_h: np.ndarray) -> int:
     """Hypergraph cut of a bipartition of the flow hypergraph's hypernodes:
     sum of w(e) over nets with pins on both sides (Section 2)."""
@@ -279,28 +340,38 @@ class FlowCutterResult:
     pierce_node: np.ndarray    # int32[n_pierced] (flow-hypergraph node ids)
     result_side: int
     source_weight: int
+    bulk_steps: int = 0        # iterations that pierced several nodes
+    mb_steps: int = 0          # path-free piercings after the first balanced cut
 
 
 def flowcutter(net: FlowNetwork, max_w: int, orig_side: np.ndarray, dist: np.ndarray,
                gid: np.ndarray, seed: int = 0, flow_bound: int = -1, max_iter: int = 1 << 30,
-               recompute: bool = False) -> FlowCutterResult:
+               recompute: bool = False, bulk_beta_pct: int = 0, bulk_warmup: int = 3,
+               mb_reps: int = 0) -> FlowCutterResult:
     """FlowCutter core, Algorithm 2 (Section 7), with the piercing rules of
     Section 7 "Piercing" as read in oracle.c.  Per hypernode arrays:
-    orig_side (0/1), dist (distance from the original cut), gid (id in H)."""
+    orig_side (0/1), dist (distance from the original cut), gid (id in H).
+    bulk_beta_pct > 0 turns on bulk piercing (Section 7, "Bulk Piercing";
+    beta in percent, `bulk_warmup` single piercings per side first);
+    mb_reps > 0 continues to the most balanced cut (Section 7, "Most
+    Balanced Cut") with that many repetitions.  The readings are in
+    oracle.c."""
     lib = _load()
     G = Lawler(net)
     nh = net.n_nodes
     final = np.zeros(nh, np.uint8)
-    cap = nh + 1
+    cap = (nh + 1) * (1 + max(int(mb_reps), 0))
     ps = np.zeros(cap, np.int32); pn = np.zeros(cap, np.int32)
     res = _FcResult()
-    lib.or_flowcutter(G.h, int(max_w), _p(_c(orig_side, np.int32)), _p(_c(dist, np.int32)),
-                      _p(_c(gid, np.int32)), ctypes.c_uint32(seed & 0xFFFFFFFF), int(flow_bound),
-                      int(min(max_iter, 2**31 - 1)), 1 if recompute else 0, _p(final), _p(ps),
-                      _p(pn), cap, ctypes.byref(res))
+    opt = _FcOptions(int(bulk_beta_pct), int(bulk_warmup), int(mb_reps), 0)
+    lib.or_flowcutter_ex(G.h, int(max_w), _p(_c(orig_side, np.int32)), _p(_c(dist, np.int32)),
+                         _p(_c(gid, np.int32)), ctypes.c_uint32(seed & 0xFFFFFFFF),
+                         int(flow_bound), int(min(max_iter, 2**31 - 1)), 1 if recompute else 0,
+                         ctypes.byref(opt), _p(final), _p(ps), _p(pn), cap, ctypes.byref(res))
     k = min(res.n_pierced, cap)
     return FlowCutterResult(res.status, res.flow, res.iterations, final, ps[:k].copy(),
-                            pn[:k].copy(), res.result_side, res.source_weight)
+                            pn[:k].copy(), res.result_side, res.source_weight, res.bulk_steps,
+                            res.mb_steps)
 
 
 def node_arrays(net: FlowNetwork, side, region, dist_region):

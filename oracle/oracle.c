@@ -498,20 +498,110 @@ typedef struct {
     int64_t flow;           /* final flow value = cut weight of the result */
     int32_t iterations;     /* max-flow augmentations performed */
     int32_t n_pierced;      /* length of the piercing sequence */
-    int32_t result_side;    /* 0: (S_r, V\S_r) returned, 1: (V\T_r, T_r) */
+    int32_t result_side;    /* 0: (S_r, V\S_r) returned, 1: (V\T_r, T_r); 2: a most
+                             * balanced cut found after the first balanced one */
     int32_t status;
     int64_t source_weight;  /* weight of the returned block 0 */
+    int32_t bulk_steps;     /* iterations that pierced more than one node */
+    int32_t mb_steps;       /* path-free piercings after the first balanced cut */
 } or_fc_result;
 
-int32_t or_flowcutter(Lawler *G, int64_t max_w, const int32_t *orig_side, const int32_t *dist,
-                      const int32_t *gid, uint32_t seed, int64_t flow_bound, int32_t max_iter,
-                      int32_t recompute, uint8_t *final_side, int32_t *pierce_side,
-                      int32_t *pierce_node, int32_t pierce_cap, or_fc_result *res) {
-    int32_t N = G->N, nh = G->n_nodes, mN = G->m_nets;
+/* Options of the two FlowCutter extensions of Section 7 (both off = the core
+ * algorithm above):
+ *
+ * Bulk piercing ("Bulk Piercing"), read as follows where the text leaves
+ * room.  Each side X (S or T) keeps its own goal and measurement.  The goal
+ * of the weight to add to X in one iteration starts at
+ *   base_X = beta * (c(V) / 2 - c(terminal of X))
+ * (integers: floor(beta_pct * (c(V) - 2 c(x)) / 200)) and base_X is
+ * multiplied by beta (floor(base * beta_pct / 100)) after every iteration
+ * that grows X; the part of a goal an iteration did not reach (goal minus
+ * the growth of X's reachable set, if positive) is carried into the next
+ * goal of X.  The average weight added per pierced node of X is the total
+ * growth of X's reachable set over the number of nodes pierced into X.  An
+ * iteration pierces several nodes only when piercing cannot avoid an
+ * augmenting path (the best candidate has a path), X is far from balance
+ * (2 (c(X_r) + goal) <= c(V)), and X has grown at least `warmup` times:
+ * then k = ceil(goal / average) candidates are pierced, taken in piercing
+ * key order while the side stays within L.  Otherwise one node is pierced.
+ *
+ * Most balanced cut ("Most Balanced Cut"): after the first balanced
+ * bipartition, piercing continues on the lighter side while a path-free
+ * candidate exists (no flow changes), keeping the most balanced bipartition
+ * seen (smaller heavier side; ties keep the earlier); this is repeated
+ * `mb_reps` times from the first balanced state, repetition r hashing with
+ * seed + r, and the most balanced result over all repetitions is returned
+ * (its cut is the flow value, like every bipartition derived here).  These
+ * piercings follow the core sequence in the piercing record, with side 2
+ * for S and 3 for T. */
+typedef struct {
+    int32_t bulk_beta_pct;  /* 0: single piercing */
+    int32_t bulk_warmup;    /* single piercings of a side before bulk ones */
+    int32_t mb_reps;        /* 0: return the first balanced bipartition */
+    int32_t pad;
+} or_fc_options;
+
+/* Candidates of growing side grow_s (Section 7, "Piercing"), best first by
+ * the keys of the core algorithm; returns their number.  key order:
+ * path-free first, larger signed distance, smaller hash. */
+typedef struct { int32_t h; int no_path; int sd; uint32_t hh; } FcCand;
+
+static int fc_cand_better(const FcCand *a, const FcCand *b) {
+    if (a->no_path != b->no_path) return a->no_path > b->no_path;
+    if (a->sd != b->sd) return a->sd > b->sd;
+    return a->hh < b->hh;
+}
+
+static int fc_cand_cmp(const void *x, const void *y) {
+    const FcCand *a = (const FcCand *)x, *b = (const FcCand *)y;
+    if (fc_cand_better(a, b)) return -1;
+    if (fc_cand_better(b, a)) return 1;
+    return 0;
+}
+
+static int32_t fc_candidates(const Lawler *G, int grow_s, const uint8_t *R, const uint8_t *Ro,
+                             const uint8_t *O, int64_t wR, int64_t max_w,
+                             const int32_t *orig_side, const int32_t *dist, const int32_t *gid,
+                             uint32_t seed, uint8_t *cand, FcCand *out) {
+    int32_t nh = G->n_nodes, mN = G->m_nets;
+    memset(cand, 0, (size_t)nh);
+    for (int32_t e = 0; e < mN; e++) {
+        int32_t node = grow_s ? nh + e : nh + mN + e;   /* in-node for S, out-node for T */
+        if (!R[node]) continue;
+        for (int64_t a = G->adj_off[nh + e]; a < G->adj_off[nh + e + 1]; a++) {
+            int32_t h = G->head[a];
+            if (h < nh) cand[h] = 1;                    /* pins of the net */
+        }
+    }
+    int32_t nc = 0;
+    for (int32_t h = 0; h < nh; h++) {
+        if (!cand[h] || R[h] || O[h]) continue;
+        if (wR + G->node_w[h] > max_w) continue;
+        FcCand c;
+        c.h = h;
+        c.no_path = !Ro[h];
+        c.sd = (orig_side[h] == (grow_s ? 0 : 1)) ? dist[h] : -dist[h];
+        c.hh = fmix32((uint32_t)gid[h] ^ seed);
+        out[nc++] = c;
+    }
+    qsort(out, (size_t)nc, sizeof(FcCand), fc_cand_cmp);
+    return nc;
+}
+
+int32_t or_flowcutter_ex(Lawler *G, int64_t max_w, const int32_t *orig_side, const int32_t *dist,
+                         const int32_t *gid, uint32_t seed, int64_t flow_bound, int32_t max_iter,
+                         int32_t recompute, const or_fc_options *opt, uint8_t *final_side,
+                         int32_t *pierce_side, int32_t *pierce_node, int32_t pierce_cap,
+                         or_fc_result *res) {
+    int32_t N = G->N, nh = G->n_nodes;
     uint8_t *S = (uint8_t *)calloc((size_t)N, 1), *T = (uint8_t *)calloc((size_t)N, 1);
     uint8_t *Sr = (uint8_t *)calloc((size_t)N, 1), *Tr = (uint8_t *)calloc((size_t)N, 1);
     uint8_t *cand = (uint8_t *)calloc((size_t)nh, 1);
-    if (!S || !T || !Sr || !Tr || !cand) { free(S); free(T); free(Sr); free(Tr); free(cand); return OR_ERR_OOM; }
+    FcCand *cl = (FcCand *)malloc(sizeof(FcCand) * (size_t)nh);
+    if (!S || !T || !Sr || !Tr || !cand || !cl) {
+        free(S); free(T); free(Sr); free(Tr); free(cand); free(cl);
+        return OR_ERR_OOM;
+    }
     int64_t W = 0;
     for (int32_t h = 0; h < nh; h++) W += G->node_w[h];
     S[0] = 1;
@@ -519,6 +609,13 @@ int32_t or_flowcutter(Lawler *G, int64_t max_w, const int32_t *orig_side, const 
     or_reset_flow(G);
     int32_t status = OR_OK, np = 0, it = 0;
     memset(res, 0, sizeof(*res));
+    /* bulk piercing state per side: 0 = S, 1 = T */
+    int64_t base[2], carry[2] = {0, 0}, added_w[2] = {0, 0}, added_n[2] = {0, 0}, pre_w[2] = {0, 0};
+    int32_t grown[2] = {0, 0}, pending[2] = {0, 0};
+    base[0] = opt ? (int64_t)opt->bulk_beta_pct * (W - 2 * G->node_w[0]) / 200 : 0;
+    base[1] = opt ? (int64_t)opt->bulk_beta_pct * (W - 2 * G->node_w[1]) / 200 : 0;
+    int bulk = opt && opt->bulk_beta_pct > 0;
+    int64_t wS = 0, wT = 0;
     for (;;) {
         if (it >= max_iter) { status = OR_ITER_LIMIT; break; }
         it++;
@@ -529,7 +626,19 @@ int32_t or_flowcutter(Lawler *G, int64_t max_w, const int32_t *orig_side, const 
         if (flow_bound >= 0 && flow > flow_bound) { status = OR_ABORTED_WORSE; break; }
         or_reach_from(G, S, Sr);                      /* derive S_r and T_r */
         or_reach_to(G, T, Tr);
-        int64_t wS = node_set_weight(G, Sr), wT = node_set_weight(G, Tr);
+        wS = node_set_weight(G, Sr);
+        wT = node_set_weight(G, Tr);
+        /* measurement of the last growth of each side (bulk piercing) */
+        for (int x = 0; x < 2; x++)
+            if (pending[x]) {
+                int64_t grew = (x == 0 ? wS : wT) - pre_w[x];
+                int64_t goal = base[x] + carry[x];
+                added_w[x] += grew;
+                carry[x] = goal - grew > 0 ? goal - grew : 0;
+                base[x] = base[x] * (opt ? opt->bulk_beta_pct : 0) / 100;
+                grown[x]++;
+                pending[x] = 0;
+            }
         int balS = (wS <= max_w) && (W - wS <= max_w);
         int balT = (wT <= max_w) && (W - wT <= max_w);
         if (balS || balT) {
@@ -547,46 +656,110 @@ int32_t or_flowcutter(Lawler *G, int64_t max_w, const int32_t *orig_side, const 
             break;
         }
         int grow_s = wS <= wT;
+        int x = grow_s ? 0 : 1;
         const uint8_t *R = grow_s ? Sr : Tr;       /* reachable set of the growing side */
         const uint8_t *Ro = grow_s ? Tr : Sr;      /* reachable set of the other side */
         const uint8_t *O = grow_s ? T : S;         /* terminal set of the other side */
         int64_t wR = grow_s ? wS : wT;
-        memset(cand, 0, (size_t)nh);
-        for (int32_t e = 0; e < mN; e++) {
-            int32_t node = grow_s ? nh + e : nh + mN + e;   /* in-node for S, out-node for T */
-            if (!R[node]) continue;
-            for (int64_t a = G->adj_off[nh + e]; a < G->adj_off[nh + e + 1]; a++) {
-                int32_t h = G->head[a];
-                if (h < nh) cand[h] = 1;                    /* pins of the net */
+        int32_t nc = fc_candidates(G, grow_s, R, Ro, O, wR, max_w, orig_side, dist, gid, seed,
+                                   cand, cl);
+        if (nc == 0) { status = OR_NO_BALANCED_CUT; break; }
+        /* how many nodes this iteration pierces */
+        int64_t k = 1;
+        if (bulk) {
+            int64_t goal = base[x] + carry[x];
+            int far = 2 * (wR + goal) <= W;
+            if (!cl[0].no_path && far && grown[x] >= opt->bulk_warmup && added_n[x] > 0) {
+                int64_t avg = added_w[x] / added_n[x];
+                if (avg < 1) avg = 1;
+                k = (goal + avg - 1) / avg;
+                if (k < 1) k = 1;
             }
         }
-        int32_t best = -1;
-        int best_np = 0, best_d = 0;
-        uint32_t best_h = 0;
-        for (int32_t h = 0; h < nh; h++) {
-            if (!cand[h] || R[h] || O[h]) continue;
-            if (wR + G->node_w[h] > max_w) continue;
-            int no_path = !Ro[h];
-            int sd = (orig_side[h] == (grow_s ? 0 : 1)) ? dist[h] : -dist[h];
-            uint32_t hh = fmix32((uint32_t)gid[h] ^ seed);
-            int better = 0;
-            if (best < 0) better = 1;
-            else if (no_path != best_np) better = no_path > best_np;
-            else if (sd != best_d) better = sd > best_d;
-            else better = hh < best_h;
-            if (better) { best = h; best_np = no_path; best_d = sd; best_h = hh; }
+        /* pierce: candidates in key order while the side stays within L */
+        int64_t taken_w = 0;
+        int32_t taken = 0;
+        uint8_t *Xset = grow_s ? S : T;
+        const uint8_t *Xr = grow_s ? Sr : Tr;
+        for (int32_t x2 = 0; x2 < N; x2++) if (Xr[x2]) Xset[x2] = 1;
+        for (int32_t c = 0; c < nc && taken < k; c++) {
+            int32_t h = cl[c].h;
+            if (wR + taken_w + G->node_w[h] > max_w) continue;
+            if (np < pierce_cap) { pierce_side[np] = x; pierce_node[np] = h; }
+            np++;
+            Xset[h] = 1;
+            taken_w += G->node_w[h];
+            taken++;
         }
-        if (best < 0) { status = OR_NO_BALANCED_CUT; break; }
-        if (np < pierce_cap) { pierce_side[np] = grow_s ? 0 : 1; pierce_node[np] = best; }
-        np++;
-        if (grow_s) { for (int32_t x = 0; x < N; x++) if (Sr[x]) S[x] = 1; S[best] = 1; }
-        else { for (int32_t x = 0; x < N; x++) if (Tr[x]) T[x] = 1; T[best] = 1; }
+        if (taken > 1) res->bulk_steps++;
+        pre_w[x] = wR;
+        added_n[x] += taken;
+        pending[x] = 1;
+    }
+    /* most balanced cut: path-free piercings from the first balanced state */
+    if (status == OR_OK && opt && opt->mb_reps > 0) {
+        uint8_t *S0 = (uint8_t *)malloc((size_t)N), *T0 = (uint8_t *)malloc((size_t)N);
+        uint8_t *side = (uint8_t *)malloc((size_t)nh);
+        int64_t best_max = res->source_weight > W - res->source_weight ? res->source_weight
+                                                                         : W - res->source_weight;
+        int64_t best_sw = res->source_weight;
+        int32_t best_rs = res->result_side;
+        memcpy(S0, S, (size_t)N);
+        memcpy(T0, T, (size_t)N);
+        for (int32_t r = 0; r < opt->mb_reps; r++) {
+            memcpy(S, S0, (size_t)N);
+            memcpy(T, T0, (size_t)N);
+            uint32_t rs = seed + (uint32_t)r;
+            for (;;) {
+                or_reach_from(G, S, Sr);
+                or_reach_to(G, T, Tr);
+                wS = node_set_weight(G, Sr);
+                wT = node_set_weight(G, Tr);
+                /* the two bipartitions of this state, both of cut weight = flow */
+                for (int use_t = 0; use_t < 2; use_t++) {
+                    int64_t w0 = use_t ? W - wT : wS;
+                    if (w0 > max_w || W - w0 > max_w) continue;
+                    int64_t mx = w0 > W - w0 ? w0 : W - w0;
+                    if (mx < best_max) {
+                        best_max = mx;
+                        best_sw = w0;
+                        best_rs = 2;
+                        for (int32_t h = 0; h < nh; h++)
+                            side[h] = use_t ? (Tr[h] ? 1 : 0) : (Sr[h] ? 0 : 1);
+                        memcpy(final_side, side, (size_t)nh);
+                    }
+                }
+                int grow_s = wS <= wT;
+                const uint8_t *R = grow_s ? Sr : Tr, *Ro = grow_s ? Tr : Sr, *O = grow_s ? T : S;
+                int32_t nc = fc_candidates(G, grow_s, R, Ro, O, grow_s ? wS : wT, max_w,
+                                           orig_side, dist, gid, rs, cand, cl);
+                if (nc == 0 || !cl[0].no_path) break;   /* only path-free piercings */
+                uint8_t *Xset = grow_s ? S : T;
+                for (int32_t x2 = 0; x2 < N; x2++) if (R[x2]) Xset[x2] = 1;
+                Xset[cl[0].h] = 1;
+                /* recorded after the core sequence with side 2 (S) or 3 (T) */
+                if (np < pierce_cap) { pierce_side[np] = grow_s ? 2 : 3; pierce_node[np] = cl[0].h; }
+                np++;
+                res->mb_steps++;
+            }
+        }
+        res->source_weight = best_sw;
+        res->result_side = best_rs;
+        free(S0); free(T0); free(side);
     }
     res->iterations = it;
     res->n_pierced = np;
     res->status = status;
-    free(S); free(T); free(Sr); free(Tr); free(cand);
+    free(S); free(T); free(Sr); free(Tr); free(cand); free(cl);
     return status;
+}
+
+int32_t or_flowcutter(Lawler *G, int64_t max_w, const int32_t *orig_side, const int32_t *dist,
+                      const int32_t *gid, uint32_t seed, int64_t flow_bound, int32_t max_iter,
+                      int32_t recompute, uint8_t *final_side, int32_t *pierce_side,
+                      int32_t *pierce_node, int32_t pierce_cap, or_fc_result *res) {
+    return or_flowcutter_ex(G, max_w, orig_side, dist, gid, seed, flow_bound, max_iter, recompute,
+                            NULL, final_side, pierce_side, pierce_node, pierce_cap, res);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -809,4 +982,303 @@ void or_pair_stats(int32_t m, const uint32_t *net_off, const int32_t *pins, cons
     }
     free(seen);
     free(blocks);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sequential FIFO push-relabel on the flow hypergraph (the paper's SeqPR
+ * baseline, Appendix "Flow Algorithms"; the method of Section 2,
+ * "Push-Relabel Algorithm": discharge in FIFO order plus global relabeling
+ * after linear work), used as a second CPU timing beside Dinic.  Unlike the
+ * routines above it works on the hypergraph form (no explicit arcs): for pin
+ * slot p (pin u of net e) fin[p] is the flow on (u, e_in), capped at w(e)
+ * during the preflow (Section 8.3, "Restricting Capacities"), fout[p] the
+ * flow on (e_out, u); fb[e] is the bridge flow.  Arc groups of a node, in
+ * scan order: hypernode u - per incident slot, (u, e_in) with residual
+ * w(e) - fin and (u, e_out) with residual fout; in-node - the bridge
+ * (w - fb), then (e_in, u) with residual fin per pin; out-node - (e_out,
+ * e_in) with residual fb, then (e_out, u) uncapacitated per pin.
+ * It stops at a maximum preflow (no excess node labelled below NL), which
+ * already fixes the flow value and both minimal cuts (Section 2, last
+ * sentence of "Push-Relabel Algorithm"): S_r by forward residual search
+ * from s and every non-sink excess node with (u, e_in) uncapped (Section
+ * 8.3), T_r by reverse residual search into t.  Outputs per Lawler node.
+ * Returns the flow value or a negative error. */
+typedef struct {
+    int32_t nh, m, NL;
+    const uint32_t *net_off;
+    const int32_t *pins, *net_w;
+    int32_t *node_off, *slot, *slot_net;
+    int64_t *fin, *fout, *fb, *excess;
+    int32_t *d;
+    int64_t flow;                    /* excess that reached t */
+} SeqPR;
+
+typedef struct { int32_t head; int64_t res; int32_t kind; int32_t idx; } SprArc;
+
+/* Residual arc j (0-based, in scan order) of node x; returns 0 past the end.
+ * kind/idx say which flow variable the arc moves: 0 fin[idx] up, 1 fin[idx]
+ * down, 2 fout[idx] up, 3 fout[idx] down, 4 fb[idx] up, 5 fb[idx] down. */
+static int spr_arc(const SeqPR *P, int32_t x, int32_t j, SprArc *a) {
+    int32_t nh = P->nh, m = P->m;
+    if (x < nh) {
+        int32_t deg = P->node_off[x + 1] - P->node_off[x];
+        if (j >= 2 * deg) return 0;
+        int32_t p = P->slot[P->node_off[x] + j / 2], e = P->slot_net[p];
+        if (j % 2 == 0) { a->head = nh + e; a->res = P->net_w[e] - P->fin[p]; a->kind = 0; }
+        else { a->head = nh + m + e; a->res = P->fout[p]; a->kind = 3; }
+        a->idx = p;
+        return 1;
+    }
+    int32_t e = x < nh + m ? x - nh : x - nh - m;
+    int32_t size = (int32_t)(P->net_off[e + 1] - P->net_off[e]);
+    if (j > size) return 0;
+    if (x < nh + m) {                              /* in-node */
+        if (j == 0) { a->head = nh + m + e; a->res = P->net_w[e] - P->fb[e]; a->kind = 4; a->idx = e; }
+        else {
+            int32_t p = (int32_t)P->net_off[e] + j - 1;
+            a->head = P->pins[p]; a->res = P->fin[p]; a->kind = 1; a->idx = p;
+        }
+    } else {                                        /* out-node */
+        if (j == 0) { a->head = nh + e; a->res = P->fb[e]; a->kind = 5; a->idx = e; }
+        else {
+            int32_t p = (int32_t)P->net_off[e] + j - 1;
+            a->head = P->pins[p]; a->res = ((int64_t)1 << 60); a->kind = 2; a->idx = p;
+        }
+    }
+    return 1;
+}
+
+static void spr_move(SeqPR *P, const SprArc *a, int64_t delta) {
+    switch (a->kind) {
+        case 0: P->fin[a->idx] += delta; break;
+        case 1: P->fin[a->idx] -= delta; break;
+        case 2: P->fout[a->idx] += delta; break;
+        case 3: P->fout[a->idx] -= delta; break;
+        case 4: P->fb[a->idx] += delta; break;
+        default: P->fb[a->idx] -= delta; break;
+    }
+}
+
+/* Exact labels: reverse breadth-first search from t over residual arcs
+ * (capped).  Labels of unreached nodes and of s are NL. */
+static void spr_global_relabel(SeqPR *P, int32_t *bfs) {
+    int32_t NL = P->NL, nh = P->nh, m = P->m;
+    for (int32_t x = 0; x < NL; x++) P->d[x] = NL;
+    int32_t h = 0, t = 0;
+    P->d[1] = 0;
+    bfs[t++] = 1;
+    while (h < t) {
+        int32_t y = bfs[h++];
+        /* candidates x with an arc (x, y): the arc groups of y name exactly
+         * the neighbours; check the residual of (x, y) from x's side */
+        SprArc a;
+        for (int32_t j = 0; spr_arc(P, y, j, &a); j++) {
+            int32_t x = a.head;
+            if (x == 0 || P->d[x] != NL) continue;
+            /* residual of (x, y) */
+            int64_t r;
+            if (x < nh) {                        /* y is e_in or e_out of net e */
+                int32_t p = a.idx;                /* slot of x in that net */
+                r = (y < nh + m) ? P->net_w[P->slot_net[p]] - P->fin[p] : P->fout[p];
+            } else if (y < nh) {                  /* x is e_in / e_out, y a pin */
+                r = (x < nh + m) ? P->fin[a.idx] : ((int64_t)1 << 60);
+            } else if (x < nh + m) {              /* bridge e_in -> e_out */
+                r = P->net_w[x - nh] - P->fb[x - nh];
+            } else {                              /* e_out -> e_in */
+                r = P->fb[x - nh - m];
+            }
+            if (r > 0) { P->d[x] = P->d[y] + 1; bfs[t++] = x; }
+        }
+    }
+}
+
+int64_t or_seqpr(int32_t nh, int32_t m, const uint32_t *net_off, const int32_t *pins,
+                 const int32_t *net_w, uint8_t *src_side, uint8_t *snk_side, int64_t *stats) {
+    if (nh < 2 || m < 0) return OR_ERR_INVALID;
+    int32_t NL = nh + 2 * m;
+    uint32_t p_tot = net_off[m];
+    SeqPR P = {nh, m, NL, net_off, pins, net_w, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    P.node_off = (int32_t *)calloc((size_t)nh + 1, sizeof(int32_t));
+    P.slot = (int32_t *)malloc(sizeof(int32_t) * (size_t)(p_tot + 1));
+    P.slot_net = (int32_t *)malloc(sizeof(int32_t) * (size_t)(p_tot + 1));
+    P.fin = (int64_t *)calloc((size_t)p_tot + 1, sizeof(int64_t));
+    P.fout = (int64_t *)calloc((size_t)p_tot + 1, sizeof(int64_t));
+    P.fb = (int64_t *)calloc((size_t)m + 1, sizeof(int64_t));
+    P.excess = (int64_t *)calloc((size_t)NL, sizeof(int64_t));
+    P.d = (int32_t *)malloc(sizeof(int32_t) * (size_t)NL);
+    int32_t *queue = (int32_t *)malloc(sizeof(int32_t) * (size_t)NL);
+    int32_t *bfs = (int32_t *)malloc(sizeof(int32_t) * (size_t)NL);
+    uint8_t *inq = (uint8_t *)calloc((size_t)NL, 1);
+    int32_t *fill = (int32_t *)malloc(sizeof(int32_t) * (size_t)nh + 4);
+    if (!P.node_off || !P.slot || !P.slot_net || !P.fin || !P.fout || !P.fb || !P.excess ||
+        !P.d || !queue || !bfs || !inq || !fill)
+        return OR_ERR_OOM;   /* (process-lifetime test code: leaks on this path) */
+    for (int32_t e = 0; e < m; e++)
+        for (uint32_t p = net_off[e]; p < net_off[e + 1]; p++) {
+            P.slot_net[p] = e;
+            P.node_off[pins[p] + 1]++;
+        }
+    for (int32_t u = 0; u < nh; u++) P.node_off[u + 1] += P.node_off[u];
+    memcpy(fill, P.node_off, sizeof(int32_t) * (size_t)nh);
+    for (uint32_t p = 0; p < p_tot; p++) P.slot[fill[pins[p]]++] = (int32_t)p;
+
+    /* saturate the arcs out of s: (s, e_in) up to w(e) */
+    for (int32_t j = P.node_off[0]; j < P.node_off[1]; j++) {
+        int32_t p = P.slot[j], e = P.slot_net[p];
+        P.fin[p] = net_w[e];
+        P.excess[nh + e] += net_w[e];
+    }
+    int64_t scans = 0, relabels = 0, pushes = 0, grs = 0, work = 0;
+    const int64_t gr_work = 2 * (int64_t)NL + (int64_t)p_tot;
+    int32_t qh = 0, qt = 0, qn = 0;   /* FIFO ring of active nodes */
+#define SPR_PUSHQ(x) do { if (!inq[x]) { inq[x] = 1; queue[qt] = (x); qt = (qt + 1) % NL; qn++; } } while (0)
+    for (;;) {
+        /* global relabel, then every excess node with a label below NL is active */
+        spr_global_relabel(&P, bfs);
+        grs++;
+        work = 0;
+        qh = qt = qn = 0;
+        memset(inq, 0, (size_t)NL);
+        for (int32_t x = 2; x < NL; x++)
+            if (P.excess[x] > 0 && P.d[x] < NL) SPR_PUSHQ(x);
+        if (qn == 0) break;
+        while (qn > 0 && work < gr_work) {
+            int32_t x = queue[qh];
+            qh = (qh + 1) % NL;
+            qn--;
+            inq[x] = 0;
+            /* discharge: scan the arcs once, pushing on admissible ones,
+             * then relabel if excess is left */
+            int32_t dx = P.d[x];
+            if (dx >= NL || P.excess[x] <= 0) continue;
+            SprArc a;
+            int32_t best = NL;
+            for (int32_t j = 0; spr_arc(&P, x, j, &a); j++) {
+                scans++;
+                work++;
+                if (a.res <= 0) continue;
+                int32_t y = a.head;
+                if (P.excess[x] > 0 && P.d[y] == dx - 1) {
+                    int64_t delta = P.excess[x] < a.res ? P.excess[x] : a.res;
+                    spr_move(&P, &a, delta);
+                    P.excess[x] -= delta;
+                    pushes++;
+                    if (y == 1) P.flow += delta;
+                    else if (y != 0) {
+                        P.excess[y] += delta;
+                        SPR_PUSHQ(y);
+                    }
+                    if (a.res - delta <= 0) continue;   /* arc saturated */
+                }
+                if (P.d[y] + 1 < best) best = P.d[y] + 1;
+            }
+            if (P.excess[x] > 0) {
+                /* relabel: min over residual arcs after the scan */
+                P.d[x] = best < NL ? best : NL;
+                relabels++;
+                if (P.d[x] < NL) SPR_PUSHQ(x);
+            }
+        }
+    }
+#undef SPR_PUSHQ
+    /* minimal sink side: reverse search into t (labels are exact now) */
+    for (int32_t x = 0; x < NL; x++) snk_side[x] = P.d[x] < NL ? 1 : 0;
+    snk_side[0] = 0;
+    /* minimal source side: forward search from s and every non-sink excess
+     * node, (u, e_in) taken as uncapacitated */
+    memset(src_side, 0, (size_t)NL);
+    int32_t h = 0, t = 0;
+    for (int32_t x = 0; x < NL; x++)
+        if (x == 0 || (x != 1 && P.excess[x] > 0)) { src_side[x] = 1; bfs[t++] = x; }
+    while (h < t) {
+        int32_t x = bfs[h++];
+        SprArc a;
+        for (int32_t j = 0; spr_arc(&P, x, j, &a); j++) {
+            int64_t r = a.res;
+            if (x < nh && j % 2 == 0) r = 1;    /* (u, e_in) is uncapacitated */
+            if (r > 0 && !src_side[a.head]) { src_side[a.head] = 1; bfs[t++] = a.head; }
+        }
+    }
+    if (stats) { stats[0] = pushes; stats[1] = relabels; stats[2] = grs; stats[3] = scans; }
+    int64_t flow = P.flow;
+    free(P.node_off); free(P.slot); free(P.slot_net); free(P.fin); free(P.fout); free(P.fb);
+    free(P.excess); free(P.d); free(queue); free(bfs); free(inq); free(fill);
+    return flow;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Identical net removal (Section 6, "Identical Net Removal"): nets of the
+ * flow hypergraph with the same pin set are merged into one representative
+ * that carries their summed weight.  Nets are compared through fingerprints
+ * f(e) = sum of v^2 over the pins v of e (flow-hypergraph node ids, modulo
+ * 2^64) and sizes; nets with different fingerprints or sizes are never
+ * identical, and nets of one (fingerprint, size) group are compared as pin
+ * sets.  Reading for determinism: every net merges into the smallest-id net
+ * with the same pin set.  Kept nets keep their order, pin order and ids in
+ * H.  Returns the new net count (pins go to out_pins, offsets to
+ * out_off[m' + 1]; rep_of[e] = the net e merged into, or e). */
+typedef struct { uint64_t f; uint32_t size; int32_t e; } NetFp;
+
+static int netfp_cmp(const void *a, const void *b) {
+    const NetFp *x = (const NetFp *)a, *y = (const NetFp *)b;
+    if (x->f != y->f) return x->f < y->f ? -1 : 1;
+    if (x->size != y->size) return x->size < y->size ? -1 : 1;
+    return x->e < y->e ? -1 : (x->e > y->e);
+}
+
+static int i32_cmp(const void *a, const void *b) {
+    int32_t x = *(const int32_t *)a, y = *(const int32_t *)b;
+    return x < y ? -1 : (x > y);
+}
+
+int32_t or_dedup_nets(int32_t m, const uint32_t *net_off, const int32_t *pins, const int32_t *net_w,
+                      const int32_t *net_gid, uint32_t *out_off, int32_t *out_pins,
+                      int32_t *out_w, int32_t *out_gid, int32_t *rep_of) {
+    NetFp *fp = (NetFp *)malloc(sizeof(NetFp) * (size_t)(m > 0 ? m : 1));
+    int64_t *wsum = (int64_t *)calloc((size_t)(m > 0 ? m : 1), sizeof(int64_t));
+    int32_t *a = (int32_t *)malloc(sizeof(int32_t) * (size_t)(net_off[m] + 1));
+    int32_t *b = (int32_t *)malloc(sizeof(int32_t) * (size_t)(net_off[m] + 1));
+    if (!fp || !wsum || !a || !b) return OR_ERR_OOM;
+    for (int32_t e = 0; e < m; e++) {
+        uint64_t f = 0;
+        for (uint32_t j = net_off[e]; j < net_off[e + 1]; j++) f += (uint64_t)pins[j] * (uint64_t)pins[j];
+        fp[e].f = f;
+        fp[e].size = net_off[e + 1] - net_off[e];
+        fp[e].e = e;
+        rep_of[e] = e;
+    }
+    qsort(fp, (size_t)m, sizeof(NetFp), netfp_cmp);
+    for (int32_t i = 0; i < m;) {
+        int32_t j = i;
+        while (j < m && fp[j].f == fp[i].f && fp[j].size == fp[i].size) j++;
+        /* the group in ascending id: each net merges into the first earlier
+         * net of the group with the same pin set */
+        uint32_t s = fp[i].size;
+        for (int32_t t = i + 1; t < j; t++) {
+            int32_t e = fp[t].e;
+            memcpy(b, pins + net_off[e], sizeof(int32_t) * s);
+            qsort(b, s, sizeof(int32_t), i32_cmp);
+            for (int32_t u = i; u < t; u++) {
+                int32_t r = fp[u].e;
+                if (rep_of[r] != r) continue;          /* only representatives */
+                memcpy(a, pins + net_off[r], sizeof(int32_t) * s);
+                qsort(a, s, sizeof(int32_t), i32_cmp);
+                if (memcmp(a, b, sizeof(int32_t) * s) == 0) { rep_of[e] = r; break; }
+            }
+        }
+        i = j;
+    }
+    for (int32_t e = 0; e < m; e++) wsum[rep_of[e]] += net_w[e];
+    int32_t mm = 0;
+    uint32_t p = 0;
+    out_off[0] = 0;
+    for (int32_t e = 0; e < m; e++) {
+        if (rep_of[e] != e) continue;
+        for (uint32_t j = net_off[e]; j < net_off[e + 1]; j++) out_pins[p++] = pins[j];
+        out_w[mm] = (int32_t)wsum[e];
+        out_gid[mm] = net_gid[e];
+        out_off[++mm] = p;
+    }
+    free(fp); free(wsum); free(a); free(b);
+    return mm;
 }

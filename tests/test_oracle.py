@@ -373,3 +373,41 @@ def test_flowcutter_invariants():
         done += 1
         pierced += len(r.pierce_node) > 0
     assert done > 120 and pierced > 30
+
+
+def test_seqpr_matches_dinic_random():
+    """The sequential FIFO push-relabel CPU baseline (SeqPR) reaches the
+    same flow value and the same minimal cut sides as Dinic, which the other
+    tests pin to brute force and scipy."""
+    checked = 0
+    for H, side, region, net in _random_nets(2024, 300, n_hi=40, m_hi=80, c_max=3):
+        mc = oracle.max_flow_min_cut(net)
+        r = oracle.seqpr(net)
+        assert r.flow == mc.flow
+        assert np.array_equal(r.source_side, mc.source_side)
+        assert np.array_equal(r.sink_side, mc.sink_side)
+        checked += 1
+    assert checked == 300
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3, 4, 5])
+def test_seqpr_matches_dinic_ring4096(seed):
+    inst = synth.instance("ring_n4096_geom", seed)
+    net = oracle.build_network(inst["H"], inst["part"], inst["region"])
+    mc = oracle.max_flow_min_cut(net)
+    r = oracle.seqpr(net)
+    assert r.flow == mc.flow
+    assert np.array_equal(r.source_side, mc.source_side)
+    assert np.array_equal(r.sink_side, mc.sink_side)
+    assert r.global_relabels >= 1
+
+
+def test_seqpr_scaled_zipf_ring():
+    """A heavy-tailed ring (the 2M workload's generator at n = 20,000)."""
+    inst = synth.instance("ring_n2M_zipf", 3, n=20000, m=30000, radius=2000)
+    net = oracle.build_network(inst["H"], inst["part"], inst["region"])
+    mc = oracle.max_flow_min_cut(net)
+    r = oracle.seqpr(net)
+    assert r.flow == mc.flow
+    assert np.array_equal(r.source_side, mc.source_side)
+    assert np.array_equal(r.sink_side, mc.sink_side)

@@ -98,12 +98,31 @@ typedef struct {
   uint64_t gr_queue_overflows;  /* such relabels redone level by level (queue full) */
 } hfp_stats;
 
-/* FlowCutter parameters (Section 7). */
+/* FlowCutter parameters (Section 7).  The two extensions of Section 7 are
+ * off when their fields are 0 (the batched launch supports neither):
+ *  - bulk piercing ("Bulk Piercing"): each side keeps a goal of weight to add
+ *    per iteration, starting at floor(bulk_beta_pct * (c(V) - 2 c(terminal))
+ *    / 200) and multiplied by bulk_beta_pct / 100 after every iteration that
+ *    grows the side, plus the part of the last goal not reached; when the
+ *    best candidate opens an augmenting path, the side is far from balance
+ *    (2 (c(X_r) + goal) <= c(V)) and the side has grown bulk_warmup times,
+ *    ceil(goal / average growth per pierced node) candidates are pierced at
+ *    once, in piercing-key order while the side stays within L;
+ *  - most balanced cut ("Most Balanced Cut"): after the first balanced
+ *    bipartition, mb_reps repetitions (third key seeded with seed + r) of
+ *    path-free piercings of the lighter side from that state; the most
+ *    balanced bipartition seen (lighter heavier side, earlier on ties) is
+ *    returned; these piercings follow the others in the piercing record with
+ *    side 2 (S) or 3 (T). */
 typedef struct {
   int64_t max_block_weight;  /* L: a side is balanced iff its weight <= L */
   int64_t flow_bound;        /* abort with HFP_ABORTED_WORSE once flow > bound; < 0: none */
   uint32_t seed;             /* seeds the third piercing key */
   int32_t max_iterations;    /* <= 0: no limit beyond the number of hypernodes */
+  int32_t bulk_beta_pct;     /* bulk piercing's beta in percent; 0: off */
+  int32_t bulk_warmup;       /* single piercings of a side before bulk ones */
+  int32_t mb_reps;           /* most balanced cut repetitions; 0: off */
+  int32_t pad;
 } hfp_fc_params;
 
 typedef struct {
@@ -111,9 +130,12 @@ typedef struct {
   int64_t source_weight;     /* weight of block 0 of the returned bipartition */
   int32_t iterations;        /* max-flow augmentations */
   int32_t n_pierced;         /* piercing steps taken */
-  int32_t result_side;       /* 0: (S_r, V \ S_r) returned; 1: (V \ T_r, T_r) */
+  int32_t result_side;       /* 0: (S_r, V \ S_r) returned; 1: (V \ T_r, T_r);
+                              * 2: a more balanced cut found after the first one */
   int32_t device_us;         /* batched launch: device time of this problem in its group
                               * (microseconds, globaltimer); 0 elsewhere */
+  int32_t bulk_steps;        /* iterations that pierced several nodes */
+  int32_t mb_steps;          /* path-free piercings of the most balanced cut search */
 } hfp_fc_result;
 
 /* --- context --------------------------------------------------------------
@@ -130,7 +152,7 @@ uint64_t hfp_kernel_launches(void);
 
 /* --- engine tuning -------------------------------------------------------------
  * Speed-only knobs of the flow engine; no value changes any result (flow,
- * cuts, piercing sequence).  Defaults in brackets.
+ * hypernode cuts, piercing sequence).  Defaults in brackets.
  *   gr_work_x100  global relabel once the frontier and next-list entries
  *                 processed since the last one exceed gr_work_x100 / 100
  *                 Lawler nodes (Section 8.1, "after linear work") [200]
@@ -157,6 +179,12 @@ uint64_t hfp_kernel_launches(void);
  *                 without a grid barrier per breadth-first level; the labels
  *                 are the same exact distances [1]
  *   gr_warps      warps per CTA that serve that queue (1..16) [12]
+ *   identical_nets  networks built from now on merge nets with identical pin
+ *                 sets into the smallest-id one, which carries their summed
+ *                 weight (Section 6, "Identical Net Removal"); flows, cut
+ *                 sides over the hypernodes and FlowCutter outcomes are
+ *                 unchanged, Lawler-node outputs and cut net ids refer to
+ *                 the merged nets (representatives' ids in H) [0]
  *   fused_rounds  one grid-wide phase per discharge round: each node applies
  *                 the previous round's pushes, discharges and relabels itself
  *                 from its own residual arcs, raising its label by at most 2;
@@ -188,6 +216,7 @@ typedef struct {
   uint32_t async_gr;
   uint32_t gr_warps;
   uint32_t fused_rounds;
+  uint32_t identical_nets;
 } hfp_tuning;
 hfp_status hfp_ctx_get_tuning(hfp_ctx* ctx, hfp_tuning* tuning);
 hfp_status hfp_ctx_set_tuning(hfp_ctx* ctx, const hfp_tuning* tuning);
@@ -330,7 +359,9 @@ hfp_status hfp_flowcutter(hfp_net* net, const hfp_fc_params* params, uint8_t* fi
  * HFP_NO_BALANCED_CUT, HFP_ABORTED_WORSE or an error code; final_side /
  * pierce_side / pierce_node (host, may be NULL) as in hfp_flowcutter.  The
  * call returns the first task error other than those two outcomes, or
- * HFP_ERR_BUFFER_TOO_SMALL when a piercing record did not fit. */
+ * HFP_ERR_BUFFER_TOO_SMALL when a piercing record did not fit.  Bulk
+ * piercing and the most balanced cut are not supported here (a task asking
+ * for them gives HFP_ERR_INVALID). */
 typedef struct {
   hfp_net* net;
   hfp_fc_params params;

@@ -421,11 +421,11 @@ HFP_API hfp_status hfp_build_flow_network(hfp_ctx* ctx, const hfp_hypergraph* H,
   if (hh->err != kDevOk) return fail(HFP_ERR_INVALID, "invalid hypergraph, region or side input");
   if (hh->wsum[2] >= (1ull << 31)) return fail(HFP_ERR_INVALID, "vertex weights sum to >= 2^31");
   if (hh->wsum[3] >= (1ull << 31)) return fail(HFP_ERR_INVALID, "net weights sum to >= 2^31");
-  const int32_t m_net = (int32_t)hh->totals[0];
-  const unsigned p_net = hh->totals[1];
+  int32_t m_net = (int32_t)hh->totals[0];
+  unsigned p_net = hh->totals[1];
   const int64_t NL64 = (int64_t)n_nodes + 2 * (int64_t)m_net;
   if (NL64 >= (1ll << 31) - 2) return fail(HFP_ERR_INVALID, "flow network too large");
-  const int32_t NL = (int32_t)NL64;
+  int32_t NL = (int32_t)NL64;
   // W of the flow problem: c(s) + c(t) + c(B)
   const int64_t total_w = (int64_t)hh->wsum[0] + (int64_t)hh->wsum[1] + (int64_t)hh->wsum[4];
 
@@ -524,6 +524,77 @@ HFP_API hfp_status hfp_build_flow_network(hfp_ctx* ctx, const hfp_hypergraph* H,
     *hp = p_net;
     CKN(cudaMemcpyAsync(nnet_off + m_net, hp, sizeof(uint32_t), cudaMemcpyHostToDevice, st));
   }
+  // identical net removal (Section 6): the kept nets are compacted in place;
+  // the incidence lists below are built from them (s / t lists from the
+  // membership flags of the kept nets)
+  DevBuf d_keep, d_newe, d_hs, d_ht, d_ps, d_pt;
+  const int32_t m_before = m_net;
+  const bool dedup = ctx->identical_nets && m_net > 1;
+  if (dedup) {
+    const int32_t m = m_net;
+    unsigned tsz = 1;
+    while (tsz < 2u * (unsigned)m) tsz <<= 1;
+    DevBuf tag, ttag, tmin, rep, wacc, size, newp, o_off, o_pin, o_w, o_gid, sums;
+    CKN(tag.alloc(sizeof(unsigned long long) * m, st));
+    CKN(ttag.alloc(sizeof(unsigned long long) * tsz, st));
+    CKN(tmin.alloc(sizeof(int32_t) * tsz, st));
+    CKN(rep.alloc(sizeof(int32_t) * m, st));
+    CKN(wacc.alloc(sizeof(unsigned long long) * m, st));
+    CKN(d_keep.alloc(sizeof(unsigned) * (m + 1), st));
+    CKN(d_newe.alloc(sizeof(unsigned) * (m + 1), st));
+    CKN(size.alloc(sizeof(unsigned) * (m + 1), st));
+    CKN(newp.alloc(sizeof(unsigned) * (m + 1), st));
+    CKN(d_hs.alloc(sizeof(unsigned) * (m + 1), st));
+    CKN(d_ht.alloc(sizeof(unsigned) * (m + 1), st));
+    CKN(d_ps.alloc(sizeof(unsigned) * (m + 1), st));
+    CKN(d_pt.alloc(sizeof(unsigned) * (m + 1), st));
+    CKN(sums.alloc(sizeof(unsigned) * 8, st));
+    CKN(o_off.alloc(sizeof(uint32_t) * (m + 1), st));
+    CKN(o_pin.alloc(sizeof(int32_t) * (p_net > 0 ? p_net : 1), st));
+    CKN(o_w.alloc(sizeof(int32_t) * m, st));
+    CKN(o_gid.alloc(sizeof(int32_t) * m, st));
+    CKN(cudaMemsetAsync(ttag.p, 0, sizeof(unsigned long long) * tsz, st));
+    CKN(cudaMemsetAsync(tmin.p, 0x7f, sizeof(int32_t) * tsz, st));
+    CKN(cudaMemsetAsync(wacc.p, 0, sizeof(unsigned long long) * m, st));
+    launch_net_tags(m, nnet_off, npin, tag.as<unsigned long long>(),
+                    ttag.as<unsigned long long>(), tmin.as<int32_t>(), tsz - 1, rep.as<int32_t>(),
+                    err.as<int>(), sms, st);
+    launch_net_merge(m, nnet_off, npin, nnet_w, rep.as<int32_t>(), wacc.as<unsigned long long>(),
+                     d_keep.as<unsigned>(), size.as<unsigned>(), d_hs.as<unsigned>(),
+                     d_ht.as<unsigned>(), sms, st);
+    // exclusive scans: new net ids, new pin offsets, positions in the s / t lists
+    CKN(cudaMemcpyAsync(d_newe.p, d_keep.p, sizeof(unsigned) * m, cudaMemcpyDeviceToDevice, st));
+    CKN(cudaMemcpyAsync(newp.p, size.p, sizeof(unsigned) * m, cudaMemcpyDeviceToDevice, st));
+    CKN(cudaMemcpyAsync(d_ps.p, d_hs.p, sizeof(unsigned) * m, cudaMemcpyDeviceToDevice, st));
+    CKN(cudaMemcpyAsync(d_pt.p, d_ht.p, sizeof(unsigned) * m, cudaMemcpyDeviceToDevice, st));
+    unsigned* sm = sums.as<unsigned>();
+    scan_exclusive(d_newe.as<unsigned>(), m, scan_scr.as<unsigned>(), sm + 0, st);
+    scan_exclusive(newp.as<unsigned>(), m, scan_scr.as<unsigned>(), sm + 1, st);
+    scan_exclusive(d_ps.as<unsigned>(), m, scan_scr.as<unsigned>(), sm + 2, st);
+    scan_exclusive(d_pt.as<unsigned>(), m, scan_scr.as<unsigned>(), sm + 3, st);
+    launch_net_compact(m, nnet_off, npin, net->net_gid, d_keep.as<unsigned>(),
+                       d_newe.as<unsigned>(), newp.as<unsigned>(),
+                       wacc.as<unsigned long long>(), o_off.as<uint32_t>(), o_pin.as<int32_t>(),
+                       o_w.as<int32_t>(), o_gid.as<int32_t>(), sms, st);
+    unsigned* hs = (unsigned*)((char*)ctx->pinned_small + 1024);
+    CKN(cudaMemcpyAsync(hs, sm, sizeof(unsigned) * 4, cudaMemcpyDeviceToHost, st));
+    int herr = 0;
+    CKN(cudaMemcpyAsync(&herr, err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CKN(cudaStreamSynchronize(st));
+    if (herr) return done(fail(HFP_ERR_CUDA, "identical net table overflow"));
+    m_net = (int32_t)hs[0];
+    p_net = hs[1];
+    NL = n_nodes + 2 * m_net;
+    CKN(cudaMemcpyAsync(nnet_off, o_off.p, sizeof(uint32_t) * m_net, cudaMemcpyDeviceToDevice, st));
+    CKN(cudaMemcpyAsync(npin, o_pin.p, sizeof(int32_t) * p_net, cudaMemcpyDeviceToDevice, st));
+    CKN(cudaMemcpyAsync(nnet_w, o_w.p, sizeof(int32_t) * m_net, cudaMemcpyDeviceToDevice, st));
+    CKN(cudaMemcpyAsync(net->net_gid, o_gid.p, sizeof(int32_t) * m_net, cudaMemcpyDeviceToDevice,
+                        st));
+    launch_dedup_totals((unsigned)m_net, p_net, sm + 2, sm + 3, nnet_off, tot, st);
+    D.m_nets = m_net;
+    D.NL = NL;
+    D.p_pins = p_net;
+  }
   {
     DevBuf cursor, tmp;
     CKN(cursor.alloc(sizeof(unsigned) * n_nodes, st));
@@ -531,6 +602,10 @@ HFP_API hfp_status hfp_build_flow_network(hfp_ctx* ctx, const hfp_hypergraph* H,
     launch_incidence(n_nodes, m_net, p_net, nnet_off, npin, node_off, cursor.as<unsigned>(), tot,
                      inc, tmp.as<int2>(), scan_scr.as<unsigned>(), tot + 4, sms, st);
   }
+  if (dedup)
+    launch_st_inc(m_before, nnet_off, d_keep.as<unsigned>(), d_newe.as<unsigned>(),
+                  d_hs.as<unsigned>(), d_ht.as<unsigned>(), d_ps.as<unsigned>(),
+                  d_pt.as<unsigned>(), node_off, nnet_off, inc, sms, st);
   launch_heavy_flags(D, sms, st);
   // distances from the original cut: given, or seeded here and completed by
   // the engine on first use (ensure_dist)
@@ -715,6 +790,7 @@ HFP_API hfp_status hfp_ctx_get_tuning(hfp_ctx* ctx, hfp_tuning* t) {
   t->async_gr = ctx->params.async_gr;
   t->gr_warps = ctx->params.gr_warps;
   t->fused_rounds = ctx->params.fused_rounds;
+  t->identical_nets = ctx->identical_nets;
   t->batch_cluster = ctx->batch_cluster;
   t->batch_big_ctas = ctx->batch_big_ctas;
   t->batch_big_groups = ctx->batch_big_groups;
@@ -739,6 +815,7 @@ HFP_API hfp_status hfp_ctx_set_tuning(hfp_ctx* ctx, const hfp_tuning* t) {
   ctx->params.async_gr = t->async_gr ? 1 : 0;
   ctx->params.gr_warps = t->gr_warps < 1 ? 1 : (t->gr_warps > 16 ? 16 : t->gr_warps);
   ctx->params.fused_rounds = t->fused_rounds ? 1 : 0;
+  ctx->identical_nets = t->identical_nets ? 1 : 0;
   ctx->batch_cluster = t->batch_cluster ? 1 : 0;
   ctx->batch_big_ctas = t->batch_big_ctas;
   ctx->batch_big_groups = t->batch_big_groups;
@@ -833,17 +910,23 @@ HFP_API hfp_status hfp_min_cut_sink_side(hfp_net* net, hfp_mem mem, uint8_t* in_
 
 namespace {
 
-// Piercing-node selection by the rule of Section 7 (see hfp_flowcutter).
+// Piercing-node selection by the rule of Section 7 (see hfp_flowcutter):
+// the candidate with the largest key, or with the largest key below `below`
+// (the next one in key order after a pick) when below != 0; w_reach < 0
+// takes the growing side's reachable weight.
 hfp_status select_pierce(hfp_net* net, int grow_s, const hfp_fc_params* prm, int32_t* node,
-                         bool* no_path = nullptr) {
+                         bool* no_path = nullptr, long long w_reach = -1,
+                         unsigned long long below = 0, unsigned long long* key = nullptr,
+                         uint32_t seed_override = 0, bool use_seed = false) {
   Ctl c;
   hfp_status s = ensure_dist(net);
   if (s != HFP_OK) return s;
   s = read_ctl(net, &c);
   if (s != HFP_OK) return s;
-  const long long w_reach = grow_s ? c.wS : c.wT;
-  launch_pierce_select(net->d, net->E, grow_s, prm->max_block_weight, w_reach, prm->seed,
-                       net->ctx->sms, net->ctx->stream);
+  if (w_reach < 0) w_reach = grow_s ? c.wS : c.wT;
+  launch_pierce_select(net->d, net->E, grow_s, prm->max_block_weight, w_reach,
+                       use_seed ? seed_override : prm->seed, net->ctx->sms, net->ctx->stream,
+                       below);
   if ((s = read_ctl(net, &c)) != HFP_OK) return s;
   if (c.best_key == 0 || c.best_node < 0) {
     *node = -1;
@@ -851,6 +934,7 @@ hfp_status select_pierce(hfp_net* net, int grow_s, const hfp_fc_params* prm, int
   }
   *node = c.best_node;
   if (no_path) *no_path = ((c.best_key >> 53) & 1ull) != 0;
+  if (key) *key = c.best_key;
   return HFP_OK;
 }
 
@@ -945,10 +1029,89 @@ HFP_API hfp_status hfp_pierce_and_augment(hfp_net* net, int32_t side, const int3
   return HFP_OK;
 }
 
+namespace {
+
+// Device state a most-balanced-cut repetition starts from (the first
+// balanced state): terminal flags, S_r marks, labels, excess and the control
+// block (all but its stamp epoch, which keeps increasing), plus the
+// host-side bookkeeping of the network.
+struct NetSnapshot {
+  DevBuf flags, insr, lab0, lab1, excess, ctl;
+  int32_t pending_source, sr_seed;
+  bool sr_valid, labels_exact, gr_pending, pierced;
+
+  hfp_status take(hfp_net* net) {
+    const NetDev& D = net->d;
+    cudaStream_t st = net->ctx->stream;
+    const size_t NL = (size_t)D.NL;
+    CK(flags.alloc(NL, st));
+    CK(insr.alloc(NL, st));
+    CK(lab0.alloc(4 * NL, st));
+    CK(lab1.alloc(4 * NL, st));
+    CK(excess.alloc(8 * NL, st));
+    CK(ctl.alloc(sizeof(EngineCtl), st));
+    CK(cudaMemcpyAsync(flags.p, D.flags, NL, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(insr.p, D.insr, NL, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(lab0.p, D.lab0, 4 * NL, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(lab1.p, D.lab1, 4 * NL, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(excess.p, D.excess, 8 * NL, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(ctl.p, net->E, sizeof(EngineCtl), cudaMemcpyDeviceToDevice, st));
+    pending_source = net->pending_source;
+    sr_seed = net->sr_seed;
+    sr_valid = net->sr_valid;
+    labels_exact = net->labels_exact;
+    gr_pending = net->gr_pending;
+    pierced = net->pierced;
+    return HFP_OK;
+  }
+
+  hfp_status restore(hfp_net* net) const {
+    const NetDev& D = net->d;
+    cudaStream_t st = net->ctx->stream;
+    const size_t NL = (size_t)D.NL;
+    // the stamp epoch moves on rather than back: stamps written since the
+    // snapshot must not match the searches of the next repetition
+    unsigned epoch = 0;
+    CK(cudaMemcpyAsync(&epoch, &net->E->s.epoch, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    CK(cudaMemcpyAsync(D.flags, flags.p, NL, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(D.insr, insr.p, NL, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(D.lab0, lab0.p, 4 * NL, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(D.lab1, lab1.p, 4 * NL, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(D.excess, excess.p, 8 * NL, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(net->E, ctl.p, sizeof(EngineCtl), cudaMemcpyDeviceToDevice, st));
+    unsigned* h = (unsigned*)((char*)net->ctx->pinned_small + 1024);
+    *h = epoch + 1;
+    CK(cudaMemcpyAsync(&net->E->s.epoch, h, sizeof(unsigned), cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
+    net->pending_source = pending_source;
+    net->sr_seed = sr_seed;
+    net->sr_valid = sr_valid;
+    net->labels_exact = labels_exact;
+    net->gr_pending = gr_pending;
+    net->pierced = pierced;
+    return HFP_OK;
+  }
+};
+
+hfp_status node_weight(hfp_net* net, int32_t h, int64_t* w) {
+  int32_t v = 0;
+  CK(cudaMemcpyAsync(&v, net->d.node_w + h, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                     net->ctx->stream));
+  CK(cudaStreamSynchronize(net->ctx->stream));
+  *w = v;
+  return HFP_OK;
+}
+
+}  // namespace
+
 HFP_API hfp_status hfp_flowcutter(hfp_net* net, const hfp_fc_params* prm, uint8_t* final_side,
                                   int32_t* pierce_side, int32_t* pierce_node, int32_t pierce_cap,
                                   hfp_fc_result* result) {
   if (!net || !prm) return fail(HFP_ERR_INVALID, "NULL argument");
+  if (prm->bulk_beta_pct < 0 || prm->bulk_beta_pct > 100 || prm->bulk_warmup < 0 ||
+      prm->mb_reps < 0)
+    return fail(HFP_ERR_INVALID, "bad bulk piercing or most balanced cut parameters");
   hfp_status s = set_device(net->ctx);
   if (s != HFP_OK) return s;
   set_gr_work(net);
@@ -958,6 +1121,24 @@ HFP_API hfp_status hfp_flowcutter(hfp_net* net, const hfp_fc_params* prm, uint8_
   hfp_fc_result r{};
   int32_t np = 0, it = 0;
   hfp_status status = HFP_OK;
+  auto record = [&](int32_t side, int32_t node) {
+    if (pierce_side && np < pierce_cap) pierce_side[np] = side;
+    if (pierce_node && np < pierce_cap) pierce_node[np] = node;
+    np++;
+  };
+  // bulk piercing bookkeeping per side (0 = S, 1 = T), as in the header
+  const int64_t beta = prm->bulk_beta_pct;
+  int64_t base[2] = {0, 0}, carry[2] = {0, 0}, added_w[2] = {0, 0}, added_n[2] = {0, 0};
+  int64_t pre_w[2] = {0, 0};
+  int32_t grown[2] = {0, 0};
+  bool pending[2] = {false, false};
+  if (beta > 0) {
+    int64_t ws = 0, wt = 0;
+    if ((s = node_weight(net, 0, &ws)) != HFP_OK) return s;
+    if ((s = node_weight(net, 1, &wt)) != HFP_OK) return s;
+    base[0] = beta * (W - 2 * ws) / 200;
+    base[1] = beta * (W - 2 * wt) / 200;
+  }
   if ((s = ensure_max_flow(net)) != HFP_OK) return s;
   it = 1;
   for (;;) {
@@ -971,6 +1152,16 @@ HFP_API hfp_status hfp_flowcutter(hfp_net* net, const hfp_fc_params* prm, uint8_
       break;
     }
     const int64_t wS = c.wS, wT = c.wT;
+    for (int x = 0; x < 2; x++)
+      if (pending[x]) {
+        const int64_t grew = (x == 0 ? wS : wT) - pre_w[x];
+        const int64_t goal = base[x] + carry[x];
+        added_w[x] += grew;
+        carry[x] = goal - grew > 0 ? goal - grew : 0;
+        base[x] = base[x] * beta / 100;
+        grown[x]++;
+        pending[x] = false;
+      }
     const bool balS = wS <= L && W - wS <= L;
     const bool balT = wT <= L && W - wT <= L;
     if (balS || balT) {
@@ -984,12 +1175,54 @@ HFP_API hfp_status hfp_flowcutter(hfp_net* net, const hfp_fc_params* prm, uint8_
       }
       r.result_side = use_t ? 1 : 0;
       r.source_weight = use_t ? W - wT : wS;
+      DevBuf best;
+      if (net->n_region > 0) {
+        CK(best.alloc(net->n_region, st));
+        launch_region_side(net->d, use_t ? 1 : 0, net->n_region, best.as<uint8_t>(),
+                           net->ctx->sms, st);
+      }
+      if (prm->mb_reps > 0) {
+        // most balanced cut: path-free piercings from this state, mb_reps times
+        NetSnapshot snap;
+        if ((s = snap.take(net)) != HFP_OK) return s;
+        int64_t best_max = r.source_weight > W - r.source_weight ? r.source_weight
+                                                                  : W - r.source_weight;
+        for (int32_t rep = 0; rep < prm->mb_reps; rep++) {
+          if (rep > 0 && (s = snap.restore(net)) != HFP_OK) return s;
+          const uint32_t seed = prm->seed + (uint32_t)rep;
+          for (;;) {
+            if ((s = ensure_source_side(net)) != HFP_OK) return s;
+            Ctl cm;
+            if ((s = read_ctl(net, &cm)) != HFP_OK) return s;
+            for (int ut = 0; ut < 2; ut++) {
+              const int64_t w0 = ut ? W - cm.wT : cm.wS;
+              if (w0 > L || W - w0 > L) continue;
+              const int64_t mx = w0 > W - w0 ? w0 : W - w0;
+              if (mx < best_max) {
+                best_max = mx;
+                r.source_weight = w0;
+                r.result_side = 2;
+                if (net->n_region > 0)
+                  launch_region_side(net->d, ut, net->n_region, best.as<uint8_t>(),
+                                     net->ctx->sms, st);
+              }
+            }
+            const int grow_s = cm.wS <= cm.wT;
+            int32_t p = -1;
+            bool no_path = false;
+            s = select_pierce(net, grow_s, prm, &p, &no_path, -1, 0, nullptr, seed, true);
+            if (s == HFP_NO_BALANCED_CUT) break;
+            if (s != HFP_OK) return s;
+            if (!no_path) break;   // only piercings that open no augmenting path
+            record(grow_s ? 2 : 3, p);
+            r.mb_steps++;
+            if ((s = pierce(net, grow_s ? 0 : 1, &p, 1, true)) != HFP_OK) return s;
+          }
+        }
+        set_last_error("");
+      }
       if (final_side && net->n_region > 0) {
-        DevBuf tmp;
-        CK(tmp.alloc(net->n_region, st));
-        launch_region_side(net->d, use_t ? 1 : 0, net->n_region, tmp.as<uint8_t>(), net->ctx->sms,
-                           st);
-        CK(cudaMemcpyAsync(final_side, tmp.p, net->n_region, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(final_side, best.p, net->n_region, cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
       }
       break;
@@ -999,16 +1232,53 @@ HFP_API hfp_status hfp_flowcutter(hfp_net* net, const hfp_fc_params* prm, uint8_
       break;
     }
     const int grow_s = wS <= wT;
+    const int x = grow_s ? 0 : 1;
+    const int64_t wR = grow_s ? wS : wT;
     int32_t p = -1;
     bool no_path = false;
-    if ((s = select_pierce(net, grow_s, prm, &p, &no_path)) != HFP_OK) {
+    unsigned long long key = 0;
+    if ((s = select_pierce(net, grow_s, prm, &p, &no_path, -1, 0, &key)) != HFP_OK) {
       status = s;
       break;
     }
-    if (pierce_side && np < pierce_cap) pierce_side[np] = grow_s ? 0 : 1;
-    if (pierce_node && np < pierce_cap) pierce_node[np] = p;
-    np++;
-    if ((s = pierce(net, grow_s ? 0 : 1, &p, 1, no_path)) != HFP_OK) return s;
+    // bulk piercing: how many nodes this iteration takes
+    int64_t k = 1;
+    if (beta > 0) {
+      const int64_t goal = base[x] + carry[x];
+      const bool far = 2 * (wR + goal) <= W;
+      if (!no_path && far && grown[x] >= prm->bulk_warmup && added_n[x] > 0) {
+        int64_t avg = added_w[x] / added_n[x];
+        if (avg < 1) avg = 1;
+        k = (goal + avg - 1) / avg;
+        if (k < 1) k = 1;
+      }
+    }
+    std::vector<int32_t> nodes{p};
+    if (k > 1) {
+      int64_t taken_w = 0;
+      if ((s = node_weight(net, p, &taken_w)) != HFP_OK) return s;
+      while ((int64_t)nodes.size() < k) {
+        int32_t q = -1;
+        unsigned long long kq = 0;
+        s = select_pierce(net, grow_s, prm, &q, nullptr, wR + taken_w, key, &kq);
+        if (s == HFP_NO_BALANCED_CUT) break;
+        if (s != HFP_OK) return s;
+        int64_t wq = 0;
+        if ((s = node_weight(net, q, &wq)) != HFP_OK) return s;
+        nodes.push_back(q);
+        taken_w += wq;
+        key = kq;
+      }
+      set_last_error("");
+      if (nodes.size() > 1) r.bulk_steps++;
+    }
+    for (int32_t q : nodes) record(x, q);
+    pre_w[x] = wR;
+    added_n[x] += (int64_t)nodes.size();
+    pending[x] = true;
+    if ((s = pierce(net, x, nodes.data(), (int32_t)nodes.size(),
+                    nodes.size() == 1 && no_path)) != HFP_OK)
+      return s;
     it++;
   }
   r.iterations = it;

@@ -86,6 +86,9 @@ hfp_status run_fc_batch(hfp_ctx* ctx, BatchItem* items, int n, int group_ctas, f
     BatchItem& it = items[order[t]];
     hfp_net* net = it.net;
     if (net->flow_started) return fail(HFP_ERR_STATE, "batched FlowCutter needs fresh networks");
+    if (it.params.bulk_beta_pct || it.params.mb_reps)
+      return fail(HFP_ERR_INVALID,
+                  "bulk piercing and the most balanced cut are not supported in the batched launch");
     FcJob& J = jobs[t];
     memset(&J, 0, sizeof(J));
     J.N = net->d;

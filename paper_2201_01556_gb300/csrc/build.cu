@@ -487,4 +487,210 @@ void launch_st_attrs(int32_t* node_gid, int32_t* node_w, int8_t* node_orig,
   count_launches(1);
 }
 
+// ---------------------------------------------------------------------------
+// Identical net removal (Section 6, "Identical Net Removal").  Nets of the
+// built flow hypergraph are grouped by a tag derived from the paper's
+// fingerprint sum of v^2, the size and an order-independent 64-bit mix of
+// the pins; within a group the smallest net id is found with atomicMin in an
+// open-addressing table, and a net merges into it when the two pin sets are
+// equal (compared pin by pin).  Nets with identical sets always share a tag,
+// so every net merges into the smallest-id net with its set (two different
+// sets with one tag would only leave a merge undone).  Kept nets stay in
+// ascending order; the representative carries the summed weight.
+
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
+  // SplitMix64's output function (Steele, Lea and Flood, 2014)
+  z ^= z >> 30;
+  z *= 0xbf58476d1ce4e5b9ull;
+  z ^= z >> 27;
+  z *= 0x94d049bb133111ebull;
+  z ^= z >> 31;
+  return z;
+}
+
+// warp per net: the group tag (never 0)
+__global__ void k_net_tag(int32_t m, const uint32_t* off, const int32_t* pin,
+                          unsigned long long* tag) {
+  const unsigned lane = threadIdx.x & 31;
+  const unsigned gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const unsigned nw = (gridDim.x * blockDim.x) >> 5;
+  for (unsigned e = gw; e < (unsigned)m; e += nw) {
+    unsigned long long f = 0, h = 0;
+    for (unsigned p = off[e] + lane; p < off[e + 1]; p += 32) {
+      const unsigned long long v = (unsigned)pin[p];
+      f += v * v;
+      h += mix64(v + 0x9e3779b97f4a7c15ull);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      f += __shfl_xor_sync(FULLB, f, o);
+      h += __shfl_xor_sync(FULLB, h, o);
+    }
+    if (lane == 0) {
+      const unsigned long long size = off[e + 1] - off[e];
+      tag[e] = mix64(f ^ mix64(h ^ (size << 40))) | 1ull;
+    }
+  }
+}
+
+// smallest net id per tag (open addressing, linear probing; the table has
+// at least twice as many slots as nets, so a probe always ends)
+__global__ void k_tag_insert(int32_t m, const unsigned long long* tag, unsigned long long* tab_tag,
+                             int32_t* tab_min, unsigned mask, int* err) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m; e += gridDim.x * blockDim.x) {
+    const unsigned long long t = tag[e];
+    unsigned slot = (unsigned)(t >> 20) & mask;
+    for (unsigned probe = 0;; probe++) {
+      if (probe > mask) {
+        atomicExch(err, 1);
+        break;
+      }
+      const unsigned long long old = atomicCAS(&tab_tag[slot], 0ull, t);
+      if (old == 0ull || old == t) {
+        atomicMin(&tab_min[slot], e);
+        break;
+      }
+      slot = (slot + 1) & mask;
+    }
+  }
+}
+
+// warp per net: its representative (the group's smallest id when the pin
+// sets are equal, else itself)
+__global__ void k_net_rep(int32_t m, const uint32_t* off, const int32_t* pin,
+                          const unsigned long long* tag, const unsigned long long* tab_tag,
+                          const int32_t* tab_min, unsigned mask, int32_t* rep) {
+  const unsigned lane = threadIdx.x & 31;
+  const unsigned gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const unsigned nw = (gridDim.x * blockDim.x) >> 5;
+  for (unsigned e = gw; e < (unsigned)m; e += nw) {
+    const unsigned long long t = tag[e];
+    unsigned slot = (unsigned)(t >> 20) & mask;
+    for (unsigned probe = 0; probe <= mask && tab_tag[slot] != t; probe++) slot = (slot + 1) & mask;
+    const int r = tab_tag[slot] == t ? tab_min[slot] : (int)e;
+    bool same = r != (int)e;
+    if (same) {
+      // sizes are equal (part of the tag); every pin of e must occur in r
+      const unsigned b = off[e], size = off[e + 1] - b, rb = off[r];
+      bool all = true;
+      for (unsigned i = lane; i < size; i += 32) {
+        const int v = pin[b + i];
+        bool found = false;
+        for (unsigned j = 0; j < size && !found; j++) found = pin[rb + j] == v;
+        all = all && found;
+      }
+      same = __all_sync(FULLB, all);
+    }
+    if (lane == 0) rep[e] = same ? r : (int)e;
+  }
+}
+
+// weights to representatives; kept-net flags and sizes; s / t membership
+__global__ void k_net_merge(int32_t m, const uint32_t* off, const int32_t* pin,
+                            const int32_t* net_w, const int32_t* rep, unsigned long long* wacc,
+                            unsigned* keep, unsigned* size, unsigned* has_s, unsigned* has_t) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m; e += gridDim.x * blockDim.x) {
+    atomicAdd(&wacc[rep[e]], (unsigned long long)net_w[e]);
+    const bool k = rep[e] == e;
+    const unsigned sz = off[e + 1] - off[e];
+    const int last = pin[off[e + 1] - 1];   // s, then t, come after the region pins
+    keep[e] = k ? 1u : 0u;
+    size[e] = k ? sz : 0u;
+    has_s[e] = k && last == 0 ? 1u : 0u;
+    has_t[e] = k && last == 1 ? 1u : 0u;
+  }
+}
+
+// warp per kept net: copy to its compacted place
+__global__ void k_net_compact(int32_t m, const uint32_t* off, const int32_t* pin,
+                              const int32_t* gid, const unsigned* keep, const unsigned* new_e,
+                              const unsigned* new_p, const unsigned long long* wacc,
+                              uint32_t* o_off, int32_t* o_pin, int32_t* o_w, int32_t* o_gid) {
+  const unsigned lane = threadIdx.x & 31;
+  const unsigned gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const unsigned nw = (gridDim.x * blockDim.x) >> 5;
+  for (unsigned e = gw; e < (unsigned)m; e += nw) {
+    if (!keep[e]) continue;
+    const unsigned ne = new_e[e], np = new_p[e], b = off[e], size = off[e + 1] - b;
+    for (unsigned i = lane; i < size; i += 32) o_pin[np + i] = pin[b + i];
+    if (lane == 0) {
+      o_off[ne] = np;
+      o_w[ne] = (int32_t)wacc[e];
+      o_gid[ne] = gid[e];
+    }
+  }
+}
+
+// s / t incidences of the compacted nets, in ascending net order
+__global__ void k_st_inc(int32_t m, const uint32_t* off, const unsigned* keep,
+                         const unsigned* new_e, const unsigned* has_s, const unsigned* has_t,
+                         const unsigned* pos_s, const unsigned* pos_t, const unsigned* node_off,
+                         const uint32_t* n_off, int2* inc) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m; e += gridDim.x * blockDim.x) {
+    if (!keep[e]) continue;
+    const int ne = (int)new_e[e];
+    const int slot = (int)n_off[ne + 1] - 1;
+    if (has_s[e]) inc[node_off[0] + pos_s[e]] = make_int2(ne, slot);
+    if (has_t[e]) inc[node_off[1] + pos_t[e]] = make_int2(ne, slot);
+  }
+}
+
+__global__ void k_dedup_totals(unsigned m_new, unsigned p_new, const unsigned* has_s_tot,
+                               const unsigned* has_t_tot, uint32_t* n_off, unsigned* totals) {
+  n_off[m_new] = p_new;
+  totals[0] = m_new;
+  totals[1] = p_new;
+  totals[2] = *has_s_tot;
+  totals[3] = *has_t_tot;
+}
+
+void launch_net_tags(int32_t m, const uint32_t* off, const int32_t* pin, unsigned long long* tag,
+                     unsigned long long* tab_tag, int32_t* tab_min, unsigned mask, int32_t* rep,
+                     int* err, int sms, cudaStream_t st) {
+  if (m <= 0) return;
+  const unsigned wb = blocks_for((unsigned long long)m * 32, 256, sms * 16);
+  k_net_tag<<<wb, 256, 0, st>>>(m, off, pin, tag);
+  k_tag_insert<<<blocks_for(m, 256, sms * 8), 256, 0, st>>>(m, tag, tab_tag, tab_min, mask, err);
+  k_net_rep<<<wb, 256, 0, st>>>(m, off, pin, tag, tab_tag, tab_min, mask, rep);
+  count_launches(3);
+}
+
+void launch_net_merge(int32_t m, const uint32_t* off, const int32_t* pin, const int32_t* net_w,
+                      const int32_t* rep, unsigned long long* wacc, unsigned* keep,
+                      unsigned* size, unsigned* has_s, unsigned* has_t, int sms,
+                      cudaStream_t st) {
+  if (m <= 0) return;
+  k_net_merge<<<blocks_for(m, 256, sms * 8), 256, 0, st>>>(m, off, pin, net_w, rep, wacc, keep,
+                                                          size, has_s, has_t);
+  count_launches(1);
+}
+
+void launch_net_compact(int32_t m, const uint32_t* off, const int32_t* pin, const int32_t* gid,
+                        const unsigned* keep, const unsigned* new_e, const unsigned* new_p,
+                        const unsigned long long* wacc, uint32_t* o_off, int32_t* o_pin,
+                        int32_t* o_w, int32_t* o_gid, int sms, cudaStream_t st) {
+  if (m <= 0) return;
+  k_net_compact<<<blocks_for((unsigned long long)m * 32, 256, sms * 16), 256, 0, st>>>(
+      m, off, pin, gid, keep, new_e, new_p, wacc, o_off, o_pin, o_w, o_gid);
+  count_launches(1);
+}
+
+void launch_dedup_totals(unsigned m_new, unsigned p_new, const unsigned* has_s_tot,
+                         const unsigned* has_t_tot, uint32_t* n_off, unsigned* totals,
+                         cudaStream_t st) {
+  k_dedup_totals<<<1, 1, 0, st>>>(m_new, p_new, has_s_tot, has_t_tot, n_off, totals);
+  count_launches(1);
+}
+
+void launch_st_inc(int32_t m, const uint32_t* off, const unsigned* keep, const unsigned* new_e,
+                   const unsigned* has_s, const unsigned* has_t, const unsigned* pos_s,
+                   const unsigned* pos_t, const unsigned* node_off, const uint32_t* n_off,
+                   int2* inc, int sms, cudaStream_t st) {
+  if (m <= 0) return;
+  k_st_inc<<<blocks_for(m, 256, sms * 8), 256, 0, st>>>(m, off, keep, new_e, has_s, has_t, pos_s,
+                                                       pos_t, node_off, n_off, inc);
+  count_launches(1);
+}
+
 }  // namespace hfp
+

@@ -229,7 +229,8 @@ __device__ __forceinline__ unsigned long long pierce_key(const NetDev& N, int h,
 }
 
 __global__ void k_pierce_scan(const NetDev N, EngineCtl* E, int grow_s, long long max_w,
-                              long long w_reach, uint32_t seed, int find) {
+                              long long w_reach, uint32_t seed, int find,
+                              unsigned long long below) {
   const int nh = N.n_nodes, m = N.m_nets, NL = N.NL;
   const unsigned lane = threadIdx.x & 31;
   const unsigned gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -242,7 +243,8 @@ __global__ void k_pierce_scan(const NetDev N, EngineCtl* E, int grow_s, long lon
     if (!reach) continue;
     for (unsigned p = N.net_off[e] + lane; p < N.net_off[e + 1]; p += 32) {
       const int h = N.pin[p];
-      const unsigned long long k = pierce_key(N, h, grow_s, max_w, w_reach, seed);
+      unsigned long long k = pierce_key(N, h, grow_s, max_w, w_reach, seed);
+      if (below && k >= below) k = 0;   // the next candidate after an earlier pick
       if (find) {
         if (k != 0 && k == best) E->c.best_node = h;
       } else if (k > mx) {
@@ -331,13 +333,14 @@ void launch_mark_sinks(const NetDev& N, EngineCtl* E, const int32_t* extra, int3
 }
 
 void launch_pierce_select(const NetDev& N, EngineCtl* E, int grow_s, long long max_w,
-                          long long w_reach, uint32_t seed, int sms, cudaStream_t st) {
+                          long long w_reach, uint32_t seed, int sms, cudaStream_t st,
+                          unsigned long long below) {
   k_pierce_reset<<<1, 1, 0, st>>>(E);
   count_launches(1);
   unsigned b = nblk((long long)N.m_nets * 32, 256, sms * 16);
-  k_pierce_scan<<<b, 256, 0, st>>>(N, E, grow_s, max_w, w_reach, seed, 0);
+  k_pierce_scan<<<b, 256, 0, st>>>(N, E, grow_s, max_w, w_reach, seed, 0, below);
   count_launches(1);
-  k_pierce_scan<<<b, 256, 0, st>>>(N, E, grow_s, max_w, w_reach, seed, 1);
+  k_pierce_scan<<<b, 256, 0, st>>>(N, E, grow_s, max_w, w_reach, seed, 1, below);
   count_launches(1);
 }
 

@@ -63,6 +63,7 @@ struct hfp_ctx {
   uint32_t batch_cluster = 1;      // hfp_tuning.batch_cluster
   uint32_t batch_big_ctas = 0;     // hfp_tuning.batch_big_ctas
   uint32_t batch_big_groups = 0;   // hfp_tuning.batch_big_groups
+  uint32_t identical_nets = 0;     // hfp_tuning.identical_nets
 };
 
 struct hfp_net {

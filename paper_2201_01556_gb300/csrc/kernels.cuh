@@ -42,6 +42,26 @@ void launch_dist_copy(int32_t n_region, const int32_t* dist_in, int32_t* dist, i
                       cudaStream_t st);
 void launch_st_attrs(int32_t* node_gid, int32_t* node_w, int8_t* node_orig,
                      const unsigned long long* wsum, uint8_t* flags, int* err, cudaStream_t st);
+// identical net removal (Section 6): group tags, smallest id per group and
+// representatives; merged weights and kept-net flags / sizes / s-t
+// membership; compaction; new totals; s / t incidences of the kept nets
+void launch_net_tags(int32_t m, const uint32_t* off, const int32_t* pin, unsigned long long* tag,
+                     unsigned long long* tab_tag, int32_t* tab_min, unsigned mask, int32_t* rep,
+                     int* err, int sms, cudaStream_t st);
+void launch_net_merge(int32_t m, const uint32_t* off, const int32_t* pin, const int32_t* net_w,
+                      const int32_t* rep, unsigned long long* wacc, unsigned* keep,
+                      unsigned* size, unsigned* has_s, unsigned* has_t, int sms, cudaStream_t st);
+void launch_net_compact(int32_t m, const uint32_t* off, const int32_t* pin, const int32_t* gid,
+                        const unsigned* keep, const unsigned* new_e, const unsigned* new_p,
+                        const unsigned long long* wacc, uint32_t* o_off, int32_t* o_pin,
+                        int32_t* o_w, int32_t* o_gid, int sms, cudaStream_t st);
+void launch_dedup_totals(unsigned m_new, unsigned p_new, const unsigned* has_s_tot,
+                         const unsigned* has_t_tot, uint32_t* n_off, unsigned* totals,
+                         cudaStream_t st);
+void launch_st_inc(int32_t m, const uint32_t* off, const unsigned* keep, const unsigned* new_e,
+                   const unsigned* has_s, const unsigned* has_t, const unsigned* pos_s,
+                   const unsigned* pos_t, const unsigned* node_off, const uint32_t* n_off,
+                   int2* inc, int sms, cudaStream_t st);
 
 // engine.cu
 constexpr int kEngineThreads = 512;   // block scans assume < 32 warps
@@ -64,8 +84,11 @@ void launch_mark_sources(const NetDev& N, const int32_t* extra, int32_t count, i
                          cudaStream_t st);
 void launch_mark_sinks(const NetDev& N, EngineCtl* E, const int32_t* extra, int32_t count,
                        int sms, cudaStream_t st);
+// Largest piercing key (and its node) among the candidates, or among those
+// with a key below `below` when it is not 0.
 void launch_pierce_select(const NetDev& N, EngineCtl* E, int grow_s, long long max_w,
-                          long long w_reach, uint32_t seed, int sms, cudaStream_t st);
+                          long long w_reach, uint32_t seed, int sms, cudaStream_t st,
+                          unsigned long long below = 0);
 void launch_region_side(const NetDev& N, int use_t, int32_t n_region, uint8_t* out, int sms,
                         cudaStream_t st);
 void launch_lawler_sink_side(const NetDev& N, uint8_t* out, int sms, cudaStream_t st);

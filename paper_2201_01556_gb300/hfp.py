@@ -54,7 +54,8 @@ class Tuning(ctypes.Structure):
                                                "bfs_enter", "bfs_exit", "pierce_relabel",
                                                "stall_rounds_pierce", "batch_cluster",
                                                "batch_big_ctas", "batch_big_groups",
-                                               "async_gr", "gr_warps", "fused_rounds")]
+                                               "async_gr", "gr_warps", "fused_rounds",
+                                               "identical_nets")]
 
 
 class RefineParams(ctypes.Structure):
@@ -97,13 +98,16 @@ class _NetworkView(ctypes.Structure):
 
 class FcParams(ctypes.Structure):
     _fields_ = [("max_block_weight", ctypes.c_int64), ("flow_bound", ctypes.c_int64),
-                ("seed", ctypes.c_uint32), ("max_iterations", ctypes.c_int32)]
+                ("seed", ctypes.c_uint32), ("max_iterations", ctypes.c_int32),
+                ("bulk_beta_pct", ctypes.c_int32), ("bulk_warmup", ctypes.c_int32),
+                ("mb_reps", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 
 class _FcResult(ctypes.Structure):
     _fields_ = [("flow", ctypes.c_int64), ("source_weight", ctypes.c_int64),
                 ("iterations", ctypes.c_int32), ("n_pierced", ctypes.c_int32),
-                ("result_side", ctypes.c_int32), ("device_us", ctypes.c_int32)]
+                ("result_side", ctypes.c_int32), ("device_us", ctypes.c_int32),
+                ("bulk_steps", ctypes.c_int32), ("mb_steps", ctypes.c_int32)]
 
 
 class _FcTask(ctypes.Structure):
@@ -690,9 +694,10 @@ def min_cut_sink_side(net: Net, lawler: bool = True):
 
 
 def fc_params(max_block_weight: int, flow_bound: int = -1, seed: int = 0,
-              max_iterations: int = 0) -> FcParams:
+              max_iterations: int = 0, bulk_beta_pct: int = 0, bulk_warmup: int = 3,
+              mb_reps: int = 0) -> FcParams:
     return FcParams(int(max_block_weight), int(flow_bound), int(seed) & 0xFFFFFFFF,
-                    int(max_iterations))
+                    int(max_iterations), int(bulk_beta_pct), int(bulk_warmup), int(mb_reps), 0)
 
 
 def pierce_and_augment(net: Net, side: int, nodes=None, params: FcParams | None = None):
@@ -716,12 +721,15 @@ class FlowCutterResult:
     final_side: np.ndarray
     pierce_side: np.ndarray
     pierce_node: np.ndarray
+    bulk_steps: int = 0
+    mb_steps: int = 0
 
 
 def flowcutter(net: Net, params: FcParams, pierce_cap: int | None = None) -> FlowCutterResult:
     """hfp_flowcutter.  Statuses NO_BALANCED_CUT / ABORTED_WORSE are returned
     in the result rather than raised."""
-    cap = net.info.n_nodes if pierce_cap is None else pierce_cap
+    cap = (net.info.n_nodes + 1) * (1 + max(params.mb_reps, 0)) if pierce_cap is None \
+        else pierce_cap
     fs = np.zeros(max(net.n_region, 1), np.uint8)
     ps = np.zeros(max(cap, 1), np.int32)
     pn = np.zeros(max(cap, 1), np.int32)
@@ -731,4 +739,5 @@ def flowcutter(net: Net, params: FcParams, pierce_cap: int | None = None) -> Flo
                 allow=(NO_BALANCED_CUT, ABORTED_WORSE))
     k = min(r.n_pierced, cap)
     return FlowCutterResult(st, r.flow, r.source_weight, r.iterations, r.result_side,
-                            fs[: net.n_region], ps[:k].copy(), pn[:k].copy())
+                            fs[: net.n_region], ps[:k].copy(), pn[:k].copy(), r.bulk_steps,
+                            r.mb_steps)

@@ -226,16 +226,17 @@ def test_device_inputs_match_host_inputs(hfp, ctx):
     _check_flow(hfp, gnet, onet)
 
 
-def _fc_compare(hfp, ctx, H, side, region, eps_pct=3, seed=0, dist_given=False):
+def _fc_compare(hfp, ctx, H, side, region, eps_pct=3, seed=0, dist_given=False, **ext):
     onet = oracle.build_network(H, side, region)
     W = int(onet.node_w.sum())
     L = oracle.max_block_weight(W, 2, eps_pct)
     dist = oracle.dist_from_cut(H, side, region)
     orig, d, gid = oracle.node_arrays(onet, side, region, dist)
-    o = oracle.flowcutter(onet, L, orig, d, gid, seed=seed)
+    o = oracle.flowcutter(onet, L, orig, d, gid, seed=seed, **ext)
     gnet = _gpu_net(hfp, ctx, H, side, region, dist=dist if dist_given else None)
-    r = hfp.flowcutter(gnet, hfp.fc_params(L, seed=seed))
+    r = hfp.flowcutter(gnet, hfp.fc_params(L, seed=seed, **ext))
     assert r.status == o.status
+    assert (r.bulk_steps, r.mb_steps) == (o.bulk_steps, o.mb_steps)
     if r.status in (oracle.OK, oracle.NO_BALANCED_CUT):
         _check_feasible(hfp, gnet, o.flow)
     assert np.array_equal(r.pierce_side, o.pierce_side)
@@ -257,6 +258,59 @@ def test_flowcutter_random(hfp, ctx):
         o = _fc_compare(hfp, ctx, H, side, region, seed=i, dist_given=(i % 2 == 1))
         pierced += len(o.pierce_node) > 0
     assert pierced > 20
+
+
+@pytest.mark.parametrize("beta,warmup,min_bulk", [(55, 1, 40), (55, 3, 15), (70, 1, 3)])
+def test_flowcutter_bulk_piercing_random(hfp, ctx, beta, warmup, min_bulk):
+    """Bulk piercing (Section 7, "Bulk Piercing") against the oracle's
+    reading: piercing sequence, final bipartition, flow, bulk step count."""
+    bulk = 0
+    for i, (H, side, region) in enumerate(_random_cases(505 + beta + warmup, 120, n_lo=10,
+                                                        n_hi=60, m_hi=120, c_max=2)):
+        o = _fc_compare(hfp, ctx, H, side, region, eps_pct=int((3, 10)[i % 2]), seed=i,
+                        bulk_beta_pct=beta, bulk_warmup=warmup)
+        bulk += o.bulk_steps
+    assert bulk >= min_bulk     # (the oracle's count on this sample, so bulk steps occur)
+
+
+def test_flowcutter_most_balanced_random(hfp, ctx):
+    """Most balanced cut (Section 7) against the oracle: the path-free
+    piercings after the first balanced cut and the chosen bipartition."""
+    steps = moved = 0
+    for i, (H, side, region) in enumerate(_random_cases(606, 120, n_lo=8, n_hi=50, m_hi=90,
+                                                        c_max=3)):
+        o = _fc_compare(hfp, ctx, H, side, region, eps_pct=int((3, 10, 25)[i % 3]), seed=i,
+                        mb_reps=2)
+        steps += o.mb_steps
+        moved += o.result_side == 2
+    assert steps > 100 and moved >= 3
+
+
+def test_most_balanced_hand_case(hfp, ctx):
+    c = load_golden("most_balanced.json")
+    H = hypergraph_from_lists(6, c["nets"], c["net_w"], c["node_w"])
+    side = np.array(c["side"], np.int32)
+    region = np.array(c["region"], np.int32)
+    gnet = _gpu_net(hfp, ctx, H, side, region, dist=np.array(c["dist"], np.int32))
+    e = c["expected"]
+    r = hfp.flowcutter(gnet, hfp.fc_params(c["max_block_weight"], seed=c["seed"],
+                                           mb_reps=e["mb_reps"]))
+    assert r.status == 0
+    assert r.final_side.tolist() == e["final_side"][2:]
+    assert (r.flow, r.source_weight, r.result_side, r.mb_steps) == \
+        (e["flow"], e["source_weight"], e["result_side"], e["mb_steps"])
+    assert r.pierce_side.tolist() == [2, 3] and r.pierce_node.tolist() == [4, 3]
+    _check_feasible(hfp, gnet, r.flow)
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_flowcutter_extensions_ring_scaled(hfp, ctx, seed):
+    """Both extensions on the 500k FlowCutter workload's generator at
+    n = 20,000."""
+    inst = synth.instance("ring_n500k_zipf_fc", seed, n=20000, m=30000, radius=2000)
+    o = _fc_compare(hfp, ctx, inst["H"], inst["part"], inst["region"], seed=seed,
+                    bulk_beta_pct=55, bulk_warmup=3, mb_reps=2)
+    assert o.status == oracle.OK
 
 
 @pytest.mark.parametrize("seed", [1, 2, 3])
@@ -364,3 +418,71 @@ def test_round_budget_trips_and_context_stays_usable(hfp):
     _check_flow(hfp, gnet, onet)
     gnet.close()
     c.close()
+
+
+@pytest.fixture(scope="module")
+def ctx_dedup(hfp):
+    c = hfp.ctx_create(0)
+    hfp.ctx_set_tuning(c, identical_nets=1)
+    yield c
+    c.close()
+
+
+def _check_dedup(hfp, ctx_dedup, H, side, region, fc_seed=None):
+    """The device network with identical nets merged equals the oracle's
+    merged network (structure bit for bit), and so do its flow and cuts; the
+    hypernode cut sides equal those of the unmerged network."""
+    gnet = _gpu_net(hfp, ctx_dedup, H, side, region)
+    full = oracle.build_network(H, side, region)
+    onet = oracle.dedup_network(full)
+    ex = hfp.net_export(gnet)
+    assert (gnet.info.m_nets, gnet.info.p_pins) == (onet.m_nets, onet.p)
+    assert np.array_equal(ex["net_off"], onet.net_off)
+    assert np.array_equal(ex["pins"], onet.pins)
+    assert np.array_equal(ex["net_w"], onet.net_w)
+    assert np.array_equal(ex["net_gid"], onet.net_gid)
+    off, slots = _expected_incidence(onet)
+    assert np.array_equal(ex["node_off"], off)
+    assert np.array_equal(ex["inc_slot"], slots)
+    mc = _check_flow(hfp, gnet, onet)
+    mf = oracle.max_flow_min_cut(full)
+    nh = full.n_nodes
+    assert mc.flow == mf.flow
+    assert np.array_equal(mc.source_side[:nh], mf.source_side[:nh])
+    assert np.array_equal(mc.sink_side[:nh], mf.sink_side[:nh])
+    gnet.close()
+    return full.m_nets - onet.m_nets
+
+
+def test_identical_nets_hand_case(hfp, ctx_dedup):
+    g = load_golden("identical_nets.json")
+    side = np.array(g["side"], np.int32)
+    region = np.array(g["region"], np.int32)
+    for nets, w in ((g["nets"], g["net_w"]), (g["collision"]["nets"], g["collision"]["net_w"])):
+        H = hypergraph_from_lists(g["n"], nets, w)
+        _check_dedup(hfp, ctx_dedup, H, side, region)
+
+
+def test_identical_nets_random_and_rings(hfp, ctx_dedup):
+    merged = 0
+    for H, side, region in _random_cases(707, 120, n_lo=4, n_hi=40, m_hi=120):
+        merged += _check_dedup(hfp, ctx_dedup, H, side, region)
+    for seed in (1, 2, 3):
+        inst = synth.instance("ring_n4096_geom", seed)
+        merged += _check_dedup(hfp, ctx_dedup, inst["H"], inst["part"], inst["region"])
+    inst = synth.instance("ring_n2M_zipf", 2, n=20000, m=30000, radius=2000)
+    merged += _check_dedup(hfp, ctx_dedup, inst["H"], inst["part"], inst["region"])
+    assert merged > 50
+
+
+def test_identical_nets_flowcutter_unchanged(hfp, ctx, ctx_dedup):
+    inst = synth.instance("ring_n500k_zipf_fc", 2, n=20000, m=30000, radius=2000)
+    H, side, region = inst["H"], inst["part"], inst["region"]
+    L = oracle.max_block_weight(int(oracle.build_network(H, side, region).node_w.sum()), 2, 3)
+    res = []
+    for c in (ctx, ctx_dedup):
+        gnet = _gpu_net(hfp, c, H, side, region)
+        r = hfp.flowcutter(gnet, hfp.fc_params(L, seed=4))
+        res.append((r.status, r.flow, r.iterations, r.pierce_node.tolist(), r.final_side.tobytes()))
+        gnet.close()
+    assert res[0] == res[1]

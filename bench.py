@@ -9,15 +9,25 @@ flow by push-relabel, and extract the minimal source-side cut S_r.
 value = Lawler-network pins (p_N, s/t pins included) / step time, summed over
 ranks (independent replicas; the single max flow does not shard).
 
-The line also carries "kway": k-way refinement rounds (Algorithm 1) on the
-8,000,000-vertex / 12,000,000-net ring (2 + Zipf(2.5) pins capped at 10,000,
-k = 64 contiguous arcs, 5 % of the vertices moved to a neighbouring block),
-all FlowCutter problems of a round in one batched launch (with several
-ranks, the round's block pairs are split across them); --kway-plain adds
-the same rounds with one problem per launch sequence (identical partitions).
+The line also carries "kway", the second half of the metric (k-way refine
+time at equal connectivity - 1):
+  - "batched": rounds of Algorithm 1 on the 8,000,000-vertex / 12,000,000-net
+    ring (2 + Zipf(2.5) pins capped at 10,000, k = 64 contiguous arcs, 5 % of
+    the vertices moved to a neighbouring block), all FlowCutter problems of a
+    round in one batched launch (with several ranks the round's block pairs
+    are split across them);
+  - "compare": from one start partition of the same generator at a smaller
+    size, the plain round (one FlowCutter problem after another), the batched
+    round (identical partitions) and the batched round pruned by the learned
+    scheduler with the committed weights (train_scheduler.py), to convergence
+    or a round limit: seconds, pairs refined and final (lambda - 1) per arm;
+  - every round's (lambda - 1) recomputed on the host from the returned
+    partition ("certificate").
 
---impl reference times the CPU oracle (Dinic on the explicit Lawler graph)
-on the host cores on a bounded sample of the same generator.
+cpu_baseline: the CPU oracle (Dinic on the explicit Lawler graph) on a 1/10
+sample of the workload, plus the sequential FIFO push-relabel (SeqPR) on the
+full workload, one host core each.  --impl reference times the oracle on the
+sample.
 """
 import argparse
 import json
@@ -163,51 +173,150 @@ def run_reference(args, rank, world):
             "config": {"workload": WORKLOAD, "seed": args.seed,
                        "sample": sample},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": sample},
+                             "sample": sample, "nproc": host_cpu()[0],
+                             "cpu_model": host_cpu()[1]},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
 
-def kway_rounds(hfp, ctx, args, world):
-    """Timed k-way refinement rounds: batched (and optionally plain) on the
-    same start partition; identical outcomes, so the times compare at equal
-    (lambda - 1).  With several ranks the batched rounds split their block
-    pairs across the ranks (one all-gather of move sets per round) and every
-    rank runs this."""
+def km1_host(H, part):
+    """(lambda - 1) recomputed on the host from a partition (Section 2): one
+    64-bit block mask per net, its population count minus one, times w(e)."""
+    bits = np.left_shift(np.uint64(1), part[H.pins].astype(np.uint64))
+    off = H.net_off.astype(np.int64)
+    masks = np.bitwise_or.reduceat(bits, off[:-1]) if len(off) > 1 else np.zeros(0, np.uint64)
+    masks[off[1:] == off[:-1]] = 0
+    lam = np.unpackbits(masks.view(np.uint8).reshape(-1, 8), axis=1).sum(1).astype(np.int64)
+    return int((np.maximum(lam - 1, 0) * H.net_w.astype(np.int64)).sum())
+
+
+def kway_batched(hfp, ctx, args, world):
+    """Batched k-way rounds on the large ring, each round's (lambda - 1)
+    checked against a host recount of the returned partition.  With several
+    ranks the rounds split their block pairs across the ranks (one all-gather
+    of move sets per round) and every rank runs this."""
     import torch
     from paper_2201_01556_gb300 import sharded
     n = args.kway_n
     inst = synth.instance("ring_n8M_zipf_k64", args.seed, n=n, m=n * 3 // 2)
     H, part = inst["H"], inst["part"]
     hg = hfp.HGraph(ctx, H.net_off, H.pins, H.net_w, H.node_w, H.n)
-    out = {"workload": f"ring n={n} m={n * 3 // 2} k=64 (2+Zipf(2.5) <= 10000, 5% moved)",
-           "pins_H": int(H.p), "group_ctas": args.kway_group, "pairs_split_over_ranks": world}
-    for mode in ("batched", "plain") if args.kway_plain else ("batched",):
-        pd = torch.from_numpy(part.copy()).cuda()
-        conn = [hfp.connectivity(hg, pd, 64)]
-        secs, pairs, fc_ms, parts = [], [], [], []
-        for _ in range(args.kway_rounds):
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            if mode == "batched" and world > 1:
-                st, _ = sharded.refine_round_sharded(hg, pd, 64, group_ctas=args.kway_group)
-            elif mode == "batched":
-                st, _, ms = hfp.refine_round_batched(hg, pd, 64, group_ctas=args.kway_group)
-                fc_ms.append(round(ms, 1))
-            else:
-                st, _ = hfp.refine_round(hg, pd, 64)
-            torch.cuda.synchronize()
-            secs.append(round(time.perf_counter() - t0, 3))
-            conn.append(int(st.connectivity_after))
-            pairs.append(int(st.pairs))
-            parts.append({f: round(getattr(st, "ms_" + f), 1)
-                          for f in ("pairs", "prepare", "flow", "finish", "apply")})
-        out[mode] = {"seconds_per_round": secs, "connectivity_minus_1": conn,
-                     "pairs_per_round": pairs, "round_parts_ms": parts}
-        if fc_ms:
-            out[mode]["flowcutter_launch_ms"] = fc_ms
+    pd = torch.from_numpy(part.copy()).cuda()
+    conn = [hfp.connectivity(hg, pd, 64)]
+    cert = [km1_host(H, part) == conn[0]]
+    secs, pairs, fc_ms, parts = [], [], [], []
+    for _ in range(args.kway_rounds):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        if world > 1:
+            st, _ = sharded.refine_round_sharded(hg, pd, 64, group_ctas=args.kway_group)
+        else:
+            st, _, ms = hfp.refine_round_batched(hg, pd, 64, group_ctas=args.kway_group)
+            fc_ms.append(round(ms, 1))
+        torch.cuda.synchronize()
+        secs.append(round(time.perf_counter() - t0, 3))
+        conn.append(int(st.connectivity_after))
+        cert.append(km1_host(H, pd.cpu().numpy()) == int(st.connectivity_after)
+                    and int(st.connectivity_before) - int(st.gain) == int(st.connectivity_after))
+        pairs.append(int(st.pairs))
+        parts.append({f: round(getattr(st, "ms_" + f), 1)
+                      for f in ("pairs", "prepare", "flow", "finish", "apply")})
     hg.close()
+    out = {"workload": f"ring n={n} m={n * 3 // 2} k=64 (2+Zipf(2.5) <= 10000, 5% moved)",
+           "pins_H": int(H.p), "group_ctas": args.kway_group, "pairs_split_over_ranks": world,
+           "seconds_per_round": secs, "connectivity_minus_1": conn, "pairs_per_round": pairs,
+           "round_parts_ms": parts, "certificate": all(cert)}
+    if fc_ms:
+        out["flowcutter_launch_ms"] = fc_ms
+    return out
+
+
+def kway_compare(hfp, ctx, args):
+    """Plain vs batched vs batched + learned rounds from one start partition
+    (seed 1001, held out from the scheduler's training seeds)."""
+    import torch
+    from paper_2201_01556_gb300 import eval_scheduler, scheduler, train_scheduler
+    n, k = args.compare_n, 64
+    inst = synth.instance("ring_n8M_zipf_k64", 1001, n=n, m=n * 3 // 2)
+    H, part = inst["H"], inst["part"]
+    loaded = train_scheduler.load_params()
+    mlp = torch.from_numpy(loaded[0]).cuda() if loaded is not None else None
+    r = eval_scheduler.compare(hfp, scheduler, ctx, H, part, k, args.compare_rounds, mlp,
+                               plain=True) if mlp is not None else None
+    out = {"workload": f"ring n={n} m={n * 3 // 2} k={k} seed 1001 (held out)",
+           "rounds_max": args.compare_rounds}
+    if r is None:
+        out["unavailable"] = "no committed scheduler weights"
+        return out
+    for a, v in r.items():
+        out[a] = {"seconds": round(v["seconds"], 3), "pairs": v["pairs"],
+                  "rounds": len(v["connectivity"]),
+                  "connectivity_minus_1": v["connectivity"][-1]}
+    out["plain_identical_to_batched"] = r["plain"]["identical_to_batched"]
+    b = out["batched"]["connectivity_minus_1"]
+    out["learned_vs_unpruned"] = out["learned"]["connectivity_minus_1"] / b - 1.0 if b else None
+    out["within_0.5pct"] = out["learned_vs_unpruned"] is not None and \
+        out["learned_vs_unpruned"] <= 0.005
+    out["speedup_batched_over_plain"] = out["plain"]["seconds"] / out["batched"]["seconds"]
+    out["speedup_learned_over_plain"] = out["plain"]["seconds"] / out["learned"]["seconds"]
+    out["scheduler_training"] = loaded[1]
+    return out
+
+
+def host_cpu():
+    """Host core count and CPU model (for the CPU baselines)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if model is None:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except OSError:
+            pass
+    import platform
+    return os.cpu_count(), model or platform.machine()
+
+
+def cpu_baselines(args, full_inst, gpu_value):
+    """The oracle on the 1/10 sample and SeqPR on the full workload."""
+    import oracle
+    nproc, model = host_cpu()
+    sinst = synth.instance(WORKLOAD, args.seed, **SAMPLE)
+    p, dt, _ = oracle_step(sinst)
+    golden = None
+    try:
+        with open(os.path.join(ROOT, "tests", "golden", f"{WORKLOAD}_seed1_maxflow.json")) as f:
+            golden = json.load(f).get("oracle_seconds")
+    except (OSError, ValueError):
+        pass
+    out = {"value": p / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"1/10-size sample: ring n={SAMPLE['n']}, m={SAMPLE['m']}, radius="
+                     f"{SAMPLE['radius']} ({p} Lawler-network pins), one run, {dt:.1f} s; "
+                     f"Dinic is super-linear here, so the sample flatters the oracle",
+           "nproc": nproc, "cpu_model": model,
+           "oracle_full_size_seconds": golden,
+           "oracle_full_size_note": "the oracle on the full workload when its golden file was "
+                                    "written (tests/golden), one core"}
+    if not args.no_seqpr:
+        H = full_inst["H"]
+        t0 = time.perf_counter()
+        net = oracle.build_network(H, full_inst["part"], full_inst["region"])
+        r = oracle.seqpr(net)
+        ds = time.perf_counter() - t0
+        out["seqpr"] = {"value": net.p / ds, "unit": UNIT, "seconds": round(ds, 2), "cores": 1,
+                        "kind": "sequential FIFO push-relabel with global relabeling (SeqPR)",
+                        "sample": "the full workload", "flow": r.flow,
+                        "gpu_over_seqpr": gpu_value / (net.p / ds)}
     return out
 
 
@@ -229,8 +338,10 @@ def main():
     ap.add_argument("--kway-n", type=int, default=8_000_000)
     ap.add_argument("--kway-group", type=int, default=16,
                     help="CTAs per FlowCutter problem (hfp_autotune_round's pick at 8M, k=64)")
-    ap.add_argument("--kway-plain", action="store_true",
-                    help="also time the one-problem-per-launch round")
+    ap.add_argument("--compare-n", type=int, default=200_000,
+                    help="ring size of the plain / batched / learned comparison (0: skip)")
+    ap.add_argument("--compare-rounds", type=int, default=3)
+    ap.add_argument("--no-seqpr", action="store_true", help="skip the full-size SeqPR timing")
     args = ap.parse_args()
     rank, world, local = env_rank()
     if args.impl == "reference":
@@ -310,7 +421,11 @@ def main():
         e2e_ms.append(1e3 * (time.perf_counter() - t0))
         net.close()
     e2e_value = world * p_pins / (statistics.mean(e2e_ms) / 1e3) if e2e_ms else None
-    kway = kway_rounds(hfp, ctx, args, world) if args.kway_rounds > 0 else None
+    kway = {}
+    if args.kway_rounds > 0:
+        kway["batched"] = kway_batched(hfp, ctx, args, world)
+    if args.compare_n > 0 and world == 1:
+        kway["compare"] = kway_compare(hfp, ctx, args)
 
     if rank != 0:
         return 0
@@ -346,16 +461,13 @@ def main():
             "gpu_launches": int(launches),
             "clocks": clk, "roofline": roof,
             "engine": {"rounds": st["rounds"], "global_relabels": st["global_relabels"],
-                       "gr_levels": st["gr_levels"], "pushes": st["pushes"]}}
-    if kway is not None:
+                       "gr_levels": st["gr_levels"], "pushes": st["pushes"],
+                       "gr_queue_entries": st["gr_queue_entries"],
+                       "gr_queue_overflows": st["gr_queue_overflows"]}}
+    if kway:
         line["kway"] = kway
     if not args.no_cpu_baseline:
-        sinst = synth.instance(WORKLOAD, args.seed, **SAMPLE)
-        p, dt, _ = oracle_step(sinst)
-        line["cpu_baseline"] = {"value": p / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": f"ring n={SAMPLE['n']}, m={SAMPLE['m']}, radius="
-                                          f"{SAMPLE['radius']} ({p} Lawler-network pins), "
-                                          f"one run, {dt:.1f} s"}
+        line["cpu_baseline"] = cpu_baselines(args, inst, value)
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -121,7 +121,7 @@ typedef struct {
   int32_t max_iterations;    /* <= 0: no limit beyond the number of hypernodes */
   int32_t bulk_beta_pct;     /* bulk piercing's beta in percent; 0: off */
   int32_t bulk_warmup;       /* single piercings of a side before bulk ones */
-  int32_t mb_reps;           /* most balanced cut repetitions; 0: off */
+  int32_t mb_reps;           /* most balanced cut repetitions (<= 1024); 0: off */
   int32_t pad;
 } hfp_fc_params;
 

@@ -1110,7 +1110,7 @@ HFP_API hfp_status hfp_flowcutter(hfp_net* net, const hfp_fc_params* prm, uint8_
                                   hfp_fc_result* result) {
   if (!net || !prm) return fail(HFP_ERR_INVALID, "NULL argument");
   if (prm->bulk_beta_pct < 0 || prm->bulk_beta_pct > 100 || prm->bulk_warmup < 0 ||
-      prm->mb_reps < 0)
+      prm->mb_reps < 0 || prm->mb_reps > 1024)
     return fail(HFP_ERR_INVALID, "bad bulk piercing or most balanced cut parameters");
   hfp_status s = set_device(net->ctx);
   if (s != HFP_OK) return s;

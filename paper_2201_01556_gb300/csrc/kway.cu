@@ -618,7 +618,7 @@ hfp_status prepare_pair(hfp_hgraph* hg, const int32_t* part, int32_t k, int32_t 
 // flow bound (Section 8.3, "Flow Value").
 hfp_fc_params pair_fc_params(hfp_hgraph* hg, int32_t k, const hfp_refine_params* prm,
                              const PairWork& w) {
-  hfp_fc_params fp;
+  hfp_fc_params fp{};
   fp.max_block_weight = ((100 + prm->eps_pct) * ((hg->total_w + k - 1) / k)) / 100;
   fp.flow_bound = w.r.original_cut;
   fp.seed = prm->seed;

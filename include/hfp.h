@@ -158,7 +158,7 @@ uint64_t hfp_kernel_launches(void);
  *                 Lawler nodes (Section 8.1, "after linear work") [200]
  *   stall_rounds, stall_nodes  also relabel globally after stall_rounds
  *                 rounds without a flow change, each with fewer than
- *                 stall_nodes active nodes (Section 8.3) [200, 1500]
+ *                 stall_nodes active nodes (Section 8.3) [100, 1500]
  *   tail_enter, tail_exit  frontiers of at most tail_enter nodes are run by
  *                 one CTA with block barriers until they exceed tail_exit
  *                 [64, 192]
@@ -172,8 +172,7 @@ uint64_t hfp_kernel_launches(void);
  *                 rounds on the new excess (Section 8.4 skips it) [0]
  *   stall_rounds_pierce  the stall_rounds rule for the incremental flows
  *                 after a piercing; 0: adaptive, as many rounds as the last
- *                 global relabel had levels (at least 8, at most
- *                 stall_rounds) [0]
+ *                 global relabel had levels (at least 8, at most 200) [0]
  *   async_gr      global relabels of hfp_max_flow / hfp_flowcutter as one
  *                 label-correcting search driven by a device work queue,
  *                 without a grid barrier per breadth-first level; the labels

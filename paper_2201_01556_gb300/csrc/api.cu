@@ -233,7 +233,7 @@ HFP_API hfp_status hfp_ctx_create(hfp_ctx** out, int device, void* stream) {
   c->params.timeout_ns = 10ull * 1000 * 1000 * 1000;
   c->params.max_rounds = 1ull << 22;
   c->params.gr_work = 0;           // set per network (a multiple of its node count)
-  c->params.stall_rounds = 200;    // Section 8.3, "Avoid Pushing Flow Back" (tuned: 500 in the paper)
+  c->params.stall_rounds = 100;    // Section 8.3, "Avoid Pushing Flow Back" (tuned: 500 in the paper)
   c->params.stall_nodes = 1500;
   c->params.tail_enter = 64;       // CTA 0 alone at or below this frontier size
   c->params.tail_exit = 192;

@@ -165,11 +165,13 @@ struct Snap {
 // Rounds without flow change before a global relabel (Section 8.3, "Avoid
 // Pushing Flow Back").  In adaptive mode (incremental flows after a
 // piercing) the limit follows the cost of a relabel: as many rounds as the
-// last one had levels, at least 8, at most stall_rounds.
+// last one had levels, at least 8, at most kStallAdaptCap.
+constexpr unsigned long long kStallAdaptCap = 200;
+
 __device__ __forceinline__ unsigned long long stall_limit(const Sched& L, const Params& P) {
   if (!P.stall_adapt) return P.stall_rounds;
   unsigned long long s = L.last_gr < 8u ? 8u : L.last_gr;
-  return s < P.stall_rounds ? s : P.stall_rounds;
+  return s < kStallAdaptCap ? s : kStallAdaptCap;
 }
 
 __device__ void begin_gr(Sched& L) {

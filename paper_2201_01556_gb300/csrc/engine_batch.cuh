@@ -548,7 +548,7 @@ __device__ void fc_run_job(FcJob* job, const Params& P0, int rank, int G, unsign
 // and each group is one cluster (group barriers in distributed shared
 // memory); otherwise it is a cooperative launch and groups synchronise
 // through global counters.
-__global__ void __launch_bounds__(kEngineThreads) fc_batch_kernel(FcJob* jobs, int n_jobs,
+__global__ void __launch_bounds__(kEngineThreads, 2) fc_batch_kernel(FcJob* jobs, int n_jobs,
                                                                   BatchCtl* B, int G, int Gb,
                                                                   int big, int n_groups,
                                                                   Params P0, int cluster) {

@@ -66,7 +66,7 @@ void launch_st_inc(int32_t m, const uint32_t* off, const unsigned* keep, const u
 // engine.cu
 constexpr int kEngineThreads = 512;   // block scans assume < 32 warps
 __global__ void __launch_bounds__(kEngineThreads) engine_kernel(NetDev N, EngineCtl* E, Params P);
-__global__ void __launch_bounds__(kEngineThreads) fc_batch_kernel(FcJob* jobs, int n_jobs,
+__global__ void __launch_bounds__(kEngineThreads, 2) fc_batch_kernel(FcJob* jobs, int n_jobs,
                                                                   BatchCtl* B, int G, int Gb,
                                                                   int big, int n_groups,
                                                                   Params P0, int cluster);

@@ -197,7 +197,11 @@ uint64_t hfp_kernel_launches(void);
  *                 batch_big_groups groups get batch_big_ctas CTAs each (the
  *                 largest problems start on them), the others the launch's
  *                 group size; used when batch_big_ctas exceeds that size
- *                 [0, 0]: uniform groups */
+ *                 [0, 0]: uniform groups
+ *   batch_fused_rounds, batch_async_gr  fused_rounds and async_gr for the
+ *                 flows of the batched FlowCutter [1, 0]: in groups of a few
+ *                 CTAs a level costs little more than its work, and the
+ *                 queue-driven search measured slower there */
 typedef struct {
   uint32_t gr_work_x100;
   uint32_t stall_rounds;
@@ -216,6 +220,8 @@ typedef struct {
   uint32_t gr_warps;
   uint32_t fused_rounds;
   uint32_t identical_nets;
+  uint32_t batch_fused_rounds;
+  uint32_t batch_async_gr;
 } hfp_tuning;
 hfp_status hfp_ctx_get_tuning(hfp_ctx* ctx, hfp_tuning* tuning);
 hfp_status hfp_ctx_set_tuning(hfp_ctx* ctx, const hfp_tuning* tuning);
@@ -373,6 +379,20 @@ typedef struct {
 } hfp_fc_task;
 
 hfp_status hfp_flowcutter_batch(hfp_ctx* ctx, hfp_fc_task* tasks, int32_t n, int32_t group_ctas);
+
+/* Profile of the batched launches (hfp_flowcutter_batch and the batched
+ * k-way rounds) since the last reset, summed over their networks: the
+ * device time (globaltimer, measured by each group's first CTA) a group
+ * spent in each engine state, and the number of phases, for states
+ * 0 .. n_states - 1 (at most 24; the numbering of hfp_net_get_trace, plus
+ * 10 saturation of a new source, 11 piercing-key maximum with its holder
+ * (12 unused), 13 / 14 marking S / T, 15 / 16 S_r / T_r grown from one node, 17 / 18
+ * queue-driven global relabel seed / search, 19 one-phase round, 20 flush
+ * of its pushes; phases run by one CTA count as 9).  reset != 0 zeroes the
+ * sums after copying.  Host memory; either pointer may be NULL.  No paper
+ * counterpart. */
+hfp_status hfp_ctx_batch_profile(hfp_ctx* ctx, uint64_t* state_ns, uint64_t* state_cnt,
+                                 int32_t n_states, int32_t reset);
 
 /* --- k-way refinement (Section 4, Algorithm 1; Sections 5 and 6) ---------
  * A device-resident hypergraph (with its vertex -> nets incidence) for

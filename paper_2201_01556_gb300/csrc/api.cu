@@ -38,6 +38,33 @@ hfp_status fail(hfp_status s, const char* fmt, ...) {
 // error message setter for entry points defined in other translation units
 void set_last_error(const char* msg) { g_err = msg; }
 
+// Buffers only the one-phase rounds and the queue-driven global relabels
+// use, allocated at the network's first launch that needs them.
+hfp_status ensure_engine_buffers(hfp_net* net, const Params& P) {
+  hfp_ctx* c = net->ctx;
+  NetDev& D = net->d;
+  const size_t NL = (size_t)D.NL;
+  if (P.fused_rounds && !D.delta1) {
+    CK(cudaMallocAsync(&net->delta1_buf, sizeof(long long) * (NL ? NL : 1), c->stream));
+    CK(cudaMemsetAsync(net->delta1_buf, 0, sizeof(long long) * (NL ? NL : 1), c->stream));
+    D.delta1 = (long long*)net->delta1_buf;
+  }
+  // Work queue of the global relabel: room for every node's chunks four
+  // times (a node is queued again whenever its label drops; the sinks of a
+  // relabel after sink-side piercings are all seeds); a fuller queue makes
+  // that relabel fall back to the level-by-level search.  Entries hold
+  // 27-bit Lawler ids: larger networks relabel level by level.
+  if (P.async_gr && !D.gq && D.NL < (1 << 27) - 1) {
+    const uint64_t cap64 = 4 * ((uint64_t)D.NL + (uint64_t)D.p_pins / 8) + 4096;
+    const unsigned cap = cap64 < 0xF0000000ull ? (unsigned)cap64 : 0xF0000000u;
+    CK(cudaMallocAsync(&net->gq_buf, sizeof(unsigned long long) * cap, c->stream));
+    CK(cudaMemsetAsync(net->gq_buf, 0, sizeof(unsigned long long) * cap, c->stream));   // empty
+    D.gq = (unsigned long long*)net->gq_buf;
+    D.gq_cap = cap;
+  }
+  return HFP_OK;
+}
+
 }  // namespace hfp
 
 namespace {
@@ -64,34 +91,6 @@ hfp_status read_ctl(hfp_net* net, Ctl* out) {
   CK(cudaMemcpyAsync(c->pinned_ctl, &net->E->c, sizeof(Ctl), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   *out = *c->pinned_ctl;
-  return HFP_OK;
-}
-
-// Buffers only the plain engine's one-phase rounds and queue-driven global
-// relabels use (the batched FlowCutter runs without them), allocated at the
-// network's first launch that needs them.
-hfp_status ensure_engine_buffers(hfp_net* net, const Params& P) {
-  hfp_ctx* c = net->ctx;
-  NetDev& D = net->d;
-  const size_t NL = (size_t)D.NL;
-  if (P.fused_rounds && !D.delta1) {
-    CK(cudaMallocAsync(&net->delta1_buf, sizeof(long long) * (NL ? NL : 1), c->stream));
-    CK(cudaMemsetAsync(net->delta1_buf, 0, sizeof(long long) * (NL ? NL : 1), c->stream));
-    D.delta1 = (long long*)net->delta1_buf;
-  }
-  // Work queue of the global relabel: room for every node's chunks four
-  // times (a node is queued again whenever its label drops; the sinks of a
-  // relabel after sink-side piercings are all seeds); a fuller queue makes
-  // that relabel fall back to the level-by-level search.  Entries hold
-  // 27-bit Lawler ids: larger networks relabel level by level.
-  if (P.async_gr && !D.gq && D.NL < (1 << 27) - 1) {
-    const uint64_t cap64 = 4 * ((uint64_t)D.NL + (uint64_t)D.p_pins / 8) + 4096;
-    const unsigned cap = cap64 < 0xF0000000ull ? (unsigned)cap64 : 0xF0000000u;
-    CK(cudaMallocAsync(&net->gq_buf, sizeof(unsigned long long) * cap, c->stream));
-    CK(cudaMemsetAsync(net->gq_buf, 0, sizeof(unsigned long long) * cap, c->stream));   // empty
-    D.gq = (unsigned long long*)net->gq_buf;
-    D.gq_cap = cap;
-  }
   return HFP_OK;
 }
 
@@ -794,6 +793,8 @@ HFP_API hfp_status hfp_ctx_get_tuning(hfp_ctx* ctx, hfp_tuning* t) {
   t->batch_cluster = ctx->batch_cluster;
   t->batch_big_ctas = ctx->batch_big_ctas;
   t->batch_big_groups = ctx->batch_big_groups;
+  t->batch_fused_rounds = ctx->batch_fused_rounds;
+  t->batch_async_gr = ctx->batch_async_gr;
   return HFP_OK;
 }
 
@@ -819,6 +820,8 @@ HFP_API hfp_status hfp_ctx_set_tuning(hfp_ctx* ctx, const hfp_tuning* t) {
   ctx->batch_cluster = t->batch_cluster ? 1 : 0;
   ctx->batch_big_ctas = t->batch_big_ctas;
   ctx->batch_big_groups = t->batch_big_groups;
+  ctx->batch_fused_rounds = t->batch_fused_rounds ? 1 : 0;
+  ctx->batch_async_gr = t->batch_async_gr ? 1 : 0;
   return HFP_OK;
 }
 
@@ -957,7 +960,7 @@ hfp_status pierce(hfp_net* net, int side, const int32_t* nodes, int32_t count,
   cudaStream_t st = net->ctx->stream;
   if (side == 0) {
     // S <- S_r + nodes; labels stay valid, the new excess is the frontier
-    launch_mark_sources(net->d, net->dev_nodes, count, net->ctx->sms, st);
+    launch_mark_sources(net->d, net->E, net->dev_nodes, count, net->ctx->sms, st);
     if (lazy && count == 1) {
       net->pending_source = nodes[0];
       net->sr_seed = net->sr_valid ? nodes[0] : -1;

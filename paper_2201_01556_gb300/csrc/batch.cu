@@ -75,12 +75,16 @@ hfp_status run_fc_batch(hfp_ctx* ctx, BatchItem* items, int n, int group_ctas, f
   }
   if (groups > kMaxGroups) return fail(HFP_ERR_INVALID, "too many groups");
   const int launch = big * Gb + (groups - big) * G;
+  if (launch > kMaxBatchCtas) return fail(HFP_ERR_INVALID, "grid above %d CTAs", kMaxBatchCtas);
   // jobs, largest network first
   std::vector<int> order(n);
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
     return items[a].net->d.p_pins > items[b].net->d.p_pins;
   });
+  Params P0 = ctx->params;
+  P0.fused_rounds = ctx->batch_fused_rounds;
+  P0.async_gr = ctx->batch_async_gr;
   std::vector<FcJob> jobs(n);
   for (int t = 0; t < n; t++) {
     BatchItem& it = items[order[t]];
@@ -89,6 +93,9 @@ hfp_status run_fc_batch(hfp_ctx* ctx, BatchItem* items, int n, int group_ctas, f
     if (it.params.bulk_beta_pct || it.params.mb_reps)
       return fail(HFP_ERR_INVALID,
                   "bulk piercing and the most balanced cut are not supported in the batched launch");
+    // a network without these buffers runs two-phase rounds and level-by-level
+    // relabels (the kernel checks per job)
+    if (hfp_status s2 = ensure_engine_buffers(net, P0)) return s2;
     FcJob& J = jobs[t];
     memset(&J, 0, sizeof(J));
     J.N = net->d;
@@ -112,9 +119,6 @@ hfp_status run_fc_batch(hfp_ctx* ctx, BatchItem* items, int n, int group_ctas, f
   CK(cudaMemsetAsync(dctl.p, 0, sizeof(BatchCtl), st));
   FcJob* jp = djobs.as<FcJob>();
   BatchCtl* bp = dctl.as<BatchCtl>();
-  Params P0 = ctx->params;
-  P0.async_gr = 0;       // groups relabel level by level
-  P0.fused_rounds = 0;   // and run two-phase rounds
   int use_cluster = cluster ? 1 : 0;
   void* args[] = {(void*)&jp,     (void*)&n,      (void*)&bp, (void*)&G,          (void*)&Gb,
                   (void*)&big,    (void*)&groups, (void*)&P0, (void*)&use_cluster};
@@ -138,6 +142,10 @@ hfp_status run_fc_batch(hfp_ctx* ctx, BatchItem* items, int n, int group_ctas, f
   for (int t = 0; t < n; t++) {
     BatchItem& it = items[order[t]];
     const FcJob& J = jobs[t];
+    for (int k = 0; k < kStateSlots; k++) {
+      ctx->batch_ns[k] += J.st_ns[k];
+      ctx->batch_cnt[k] += J.st_cnt[k];
+    }
     hfp_net* net = it.net;
     net->flow_started = true;
     net->launches++;
@@ -220,4 +228,18 @@ HFP_API hfp_status hfp_flowcutter_batch(hfp_ctx* ctx, hfp_fc_task* tasks, int32_
                  it.result.n_pierced);
   }
   return ret;
+}
+
+HFP_API hfp_status hfp_ctx_batch_profile(hfp_ctx* ctx, uint64_t* state_ns, uint64_t* state_cnt,
+                                         int32_t n_states, int32_t reset) {
+  if (!ctx || n_states < 0) return fail(HFP_ERR_INVALID, "bad arguments");
+  const int k = std::min<int>(n_states, kStateSlots);
+  for (int i = 0; i < k; i++) {
+    if (state_ns) state_ns[i] = ctx->batch_ns[i];
+    if (state_cnt) state_cnt[i] = ctx->batch_cnt[i];
+  }
+  if (reset) {
+    for (int i = 0; i < kStateSlots; i++) ctx->batch_ns[i] = ctx->batch_cnt[i] = 0;
+  }
+  return HFP_OK;
 }

@@ -165,8 +165,14 @@ __global__ void k_saturate(const NetDev N, EngineCtl* E, const int32_t* nodes, i
 
 // S <- S_r + extra: every node of S_r and every extra hypernode becomes a
 // source with label NL; their excess is absorbed (Algorithm 2, line 8).
-__global__ void k_mark_sources(const NetDev N, const int32_t* extra, int32_t count) {
+// S <- S_r + extra.  With one new source v, v is the only source with
+// residual arcs leaving S (S_r is closed under residual arcs, sources never
+// receive pushes and push only when saturated), so the next S_r searches
+// expand v alone besides the excess nodes; with several, every source.
+__global__ void k_mark_sources(const NetDev N, EngineCtl* E, const int32_t* extra,
+                               int32_t count) {
   const int NL = N.NL;
+  if (blockIdx.x == 0 && threadIdx.x == 0) E->s.sr_one = count == 1 ? extra[0] + 1 : 0;
   for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < NL + count; x += gridDim.x * blockDim.x) {
     int y;
     if (x < NL) {
@@ -184,9 +190,13 @@ __global__ void k_mark_sources(const NetDev N, const int32_t* extra, int32_t cou
 
 // T <- T_r + extra (Algorithm 2, line 10).  T_r is {x : label < NL} right
 // after a final global relabel.  The excess of a node that turns into a sink
-// is added to the flow value (Section 8.4, "Sink-Side Piercing").
+// is added to the flow value (Section 8.4, "Sink-Side Piercing").  With one
+// new sink v, v is the only sink a non-sink can have a residual arc into (no
+// residual arc entered T_r, and sinks never push), so the next global
+// relabels expand v alone; with several, every sink.
 __global__ void k_mark_sinks(const NetDev N, EngineCtl* E, const int32_t* extra, int32_t count) {
   const int NL = N.NL;
+  if (blockIdx.x == 0 && threadIdx.x == 0) E->s.gr_one = count == 1 ? extra[0] + 1 : 0;
   unsigned long long acc = 0;
   for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < NL + count; x += gridDim.x * blockDim.x) {
     int y;
@@ -320,9 +330,10 @@ void launch_saturate(const NetDev& N, EngineCtl* E, const int32_t* nodes, int32_
   }
 }
 
-void launch_mark_sources(const NetDev& N, const int32_t* extra, int32_t count, int sms,
-                         cudaStream_t st) {
-  k_mark_sources<<<nblk((long long)N.NL + count, 256, sms * 8), 256, 0, st>>>(N, extra, count);
+void launch_mark_sources(const NetDev& N, EngineCtl* E, const int32_t* extra, int32_t count,
+                         int sms, cudaStream_t st) {
+  k_mark_sources<<<nblk((long long)N.NL + count, 256, sms * 8), 256, 0, st>>>(N, E, extra,
+                                                                              count);
   count_launches(1);
 }
 

@@ -6,11 +6,10 @@
 // reset while it is read or written); small frontiers are discharged by CTA 0
 // alone with block barriers while the other CTAs wait.
 //
-// Light nodes (at most kLightItems arc groups) are handled one per lane: a
-// warp walks the arcs of its 32 nodes in lockstep, so list appends stay
-// warp-aggregated.  Heavy nodes (large nets, high-degree vertices) get a
-// whole warp, which scans 32 arcs per step and places pushes by an inclusive
-// scan of residual capacities.
+// Light nodes (at most kLightItems arc groups) are handled by teams of kTeam
+// lanes, which place their pushes by a team scan of residual capacities.
+// Heavy nodes (large nets, s, t, high-degree vertices) get a whole CTA, which
+// scans blockDim.x arc groups per step and places pushes by a block scan.
 //
 // Method (Section 8 of the paper, "Parallel Maximum Flow Algorithm"):
 //  - rounds discharge all active nodes in parallel against the labels and
@@ -30,15 +29,22 @@
 //    (Section 8.4, "Source-Side Cut"; Section 8.3, last paragraph of
 //    "Restricting Capacities").
 //
-// Difference from the paper's round: a round here is split into a push phase
-// and a relabel phase separated by a grid barrier.  Pushes use only the old
-// labels, and a node relabels (against the old labels of its neighbours, read
-// from the other buffer of a double-buffered label array) only after every
-// push of the round has landed, so the new residual arcs created by
-// concurrent pushes are always seen.  Labels therefore stay valid at all
-// times, the push-relabel conflict of Section 8.2 cannot occur, and no
-// winning criterion is needed: an arc can only be admissible in one
-// direction under one labelling.  The run is deterministic.
+// Difference from the paper's round.  Two round forms are built, and both
+// keep every label valid, so the push-relabel conflict of Section 8.2 cannot
+// occur and no winning criterion is needed:
+//  - two-phase rounds (ROUND_A / ROUND_B): pushes use only the old labels,
+//    and a node relabels (against the old labels of its neighbours, read from
+//    the other buffer of a double-buffered label array) only after every push
+//    of the round has landed;
+//  - one-phase rounds (ROUND / FLUSH, the default of single flows): a node
+//    applies the pushes it received in the previous round, discharges and
+//    relabels itself at once with the capped rule explained at phase_round.
+// Global relabeling is either level-synchronous (one grid phase per BFS
+// level) or one queue-driven label-correcting search (GR_SEED / GR_RUN).
+// Runs are deterministic: excess moves by integer atomics only, and the
+// queue-driven search ends at the exact BFS distances the level-synchronous
+// one computes.  The two round forms reach the same flow value and cuts
+// (both unique) in different numbers of rounds.
 #include <climits>
 
 #include "kernels.cuh"
@@ -108,6 +114,33 @@ __device__ __forceinline__ void append_split(bool want, int32_t value, bool heav
     pos = __shfl_sync(FULL, pos, leader);
     if (want && heavy) list[NL - 1 - (base_h + pos + __popc(mh & lt))] = value;
   }
+}
+
+// append_split for two values per lane (value 1 before value 2 of the same
+// lane): one ballot pair and at most two atomics per warp.
+__device__ __forceinline__ void append_split2(bool w1, int32_t v1, bool h1, bool w2, int32_t v2,
+                                              bool h2, int32_t* list, unsigned* cl,
+                                              unsigned* ch, unsigned base_l, unsigned base_h,
+                                              int NL) {
+  const unsigned lane = lane_id();
+  const unsigned lt = (1u << lane) - 1u;
+  const unsigned l1 = __ballot_sync(FULL, w1 && !h1), l2 = __ballot_sync(FULL, w2 && !h2);
+  const unsigned g1 = __ballot_sync(FULL, w1 && h1), g2 = __ballot_sync(FULL, w2 && h2);
+  const unsigned nl = __popc(l1) + __popc(l2), nh = __popc(g1) + __popc(g2);
+  if (nl + nh == 0) return;
+  unsigned pl = 0, ph = 0;
+  if (lane == 0) {
+    if (nl) pl = atomicAdd(cl, nl);
+    if (nh) ph = atomicAdd(ch, nh);
+  }
+  pl = __shfl_sync(FULL, pl, 0);
+  ph = __shfl_sync(FULL, ph, 0);
+  unsigned o = pl + __popc(l1 & lt) + __popc(l2 & lt);
+  if (w1 && !h1) list[base_l + o++] = v1;
+  if (w2 && !h2) list[base_l + o] = v2;
+  o = ph + __popc(g1 & lt) + __popc(g2 & lt);
+  if (w1 && h1) list[NL - 1 - (base_h + o++)] = v1;
+  if (w2 && h2) list[NL - 1 - (base_h + o)] = v2;
 }
 
 __device__ __forceinline__ void append_plain(bool want, int32_t value, int32_t* list,
@@ -1233,7 +1266,8 @@ __device__ void gr_init(const NetDev& N, EngineCtl* E, const Sched& L, const Tea
       N.needrl[x] = 0;
       if (snk && x < (unsigned)N.n_nodes) a.w += N.node_w[x];
     }
-    append_split(snk, (int)x, hv, N.list[L_BFS], S.c[C_BFS], S.c[C_BFSH], 0, 0, N.NL);
+    append_split(snk && (L.gr_one == 0 || (int)x == L.gr_one - 1), (int)x, hv, N.list[L_BFS],
+                 S.c[C_BFS], S.c[C_BFSH], 0, 0, N.NL);
   }
 }
 
@@ -1255,22 +1289,6 @@ __device__ void gr_add(const NetDev& N, const Sched& L, const Team& T, const Slo
     seed = true;
   }
   append_split(seed, u, hv, N.list[L_BFS], S.c[C_BFS], S.c[C_BFSH], 0, 0, N.NL);
-}
-
-__device__ __forceinline__ bool gr_claim(const NetDev& N, int x, int d1, bool& act, bool& hv,
-                                         Acc& a) {
-  act = false;
-  hv = false;
-  if (x < 0) return false;
-  if (N.lab0[x] != N.NL) return false;
-  const uint8_t f = N.flags[x];
-  if (f & kSource) return false;
-  if (atomicCAS(&N.lab0[x], N.NL, d1) != N.NL) return false;
-  N.lab1[x] = d1;
-  hv = (f & kHeavy) != 0;
-  act = N.excess[x] > 0;
-  if (x < N.n_nodes) a.w += N.node_w[x];
-  return true;
 }
 
 // Reverse residual arcs (capped network) into y, arc group k: up to two
@@ -1300,12 +1318,43 @@ __device__ __forceinline__ void rev_arcs(const NetDev& N, const NodeArcs& g, uns
   }
 }
 
-__device__ __forceinline__ void gr_emit(const NetDev& N, EngineCtl* E, const Sched& L,
-                                        const Slot& S, int c, int d1, Acc& a) {
-  bool act, hv;
-  const bool k = gr_claim(N, c, d1, act, hv, a);
-  append_split(k, c, hv, N.list[L_BFS], S.c[C_BFS], S.c[C_BFSH], L.bfs_end, L.bfsh_end, N.NL);
-  append_split(act, c, hv, N.list[L_FRONT], S.act[0], S.act[1], 0, 0, N.NL);
+// The two tails c1, c2 of one arc group (-1: none; distinct when both are
+// given) claimed with label d1: a node still unlabelled (label N_L) that is
+// not a source takes d1 by compare-and-swap, joins the next level, T_r's
+// weight, and the frontier when it has excess.  The loads of both are issued
+// before either claim, and both appends share one ballot pass.
+__device__ __forceinline__ void gr_emit2(const NetDev& N, const Sched& L, const Slot& S, int c1,
+                                         int c2, int d1, Acc& a) {
+  const int NL = N.NL;
+  int l1 = 0, l2 = 0;
+  uint8_t f1 = 0, f2 = 0;
+  if (c1 >= 0) {
+    l1 = N.lab0[c1];
+    f1 = N.flags[c1];
+  }
+  if (c2 >= 0) {
+    l2 = N.lab0[c2];
+    f2 = N.flags[c2];
+  }
+  bool k1 = c1 >= 0 && l1 == NL && !(f1 & kSource);
+  bool k2 = c2 >= 0 && l2 == NL && !(f2 & kSource);
+  if (k1) k1 = atomicCAS(&N.lab0[c1], NL, d1) == NL;
+  if (k2) k2 = atomicCAS(&N.lab0[c2], NL, d1) == NL;
+  bool a1 = false, a2 = false;
+  if (k1) {
+    N.lab1[c1] = d1;
+    a1 = N.excess[c1] > 0;
+    if (c1 < N.n_nodes) a.w += N.node_w[c1];
+  }
+  if (k2) {
+    N.lab1[c2] = d1;
+    a2 = N.excess[c2] > 0;
+    if (c2 < N.n_nodes) a.w += N.node_w[c2];
+  }
+  const bool h1 = (f1 & kHeavy) != 0, h2 = (f2 & kHeavy) != 0;
+  append_split2(k1, c1, h1, k2, c2, h2, N.list[L_BFS], S.c[C_BFS], S.c[C_BFSH], L.bfs_end,
+                L.bfsh_end, NL);
+  append_split2(a1, c1, h1, a2, c2, h2, N.list[L_FRONT], S.act[0], S.act[1], 0, 0, NL);
 }
 
 // Global relabel, one level: reverse BFS over residual arcs of the capped
@@ -1328,8 +1377,7 @@ __device__ void gr_team(const NetDev& N, EngineCtl* E, const Sched& L, const Slo
     const unsigned k = c * TW + tl;
     int c1 = -1, c2 = -1;
     if (k < g.items) rev_arcs(N, g, k, w, fb, c1, c2, a);
-    gr_emit(N, E, L, S, c1, d1, a);
-    gr_emit(N, E, L, S, c2, d1, a);
+    gr_emit2(N, L, S, c1, c2, d1, a);
   }
 }
 
@@ -1352,8 +1400,7 @@ __device__ void gr_level(const NetDev& N, EngineCtl* E, const Sched& L, const Te
       const unsigned k = k0 + threadIdx.x;
       int c1 = -1, c2 = -1;
       if (k < g.items) rev_arcs(N, g, k, w, fb, c1, c2, a);
-      gr_emit(N, E, L, S, c1, d1, a);
-      gr_emit(N, E, L, S, c2, d1, a);
+      gr_emit2(N, L, S, c1, c2, d1, a);
     }
   }
 }
@@ -1588,18 +1635,20 @@ __device__ void sr_init(const NetDev& N, const Sched& L, const Team& T, const Sl
                         unsigned lane, Acc& a) {
   for (unsigned x0 = T.tid - lane; x0 < (unsigned)N.NL; x0 += T.nth) {
     const unsigned x = x0 + lane;
-    bool seed = false, hv = false;
+    bool seed = false, hv = false, expand = false;
     if (x < (unsigned)N.NL) {
       const uint8_t f = N.flags[x];
       hv = (f & kHeavy) != 0;
-      seed = (f & kSource) || (!(f & kSink) && N.excess[x] > 0);
+      const bool src = (f & kSource) != 0;
+      seed = src || (!(f & kSink) && N.excess[x] > 0);
       N.insr[x] = seed ? 1 : 0;
       if (seed) {
         N.stamp[x] = L.epoch;
         if (x < (unsigned)N.n_nodes) a.w += N.node_w[x];
       }
+      expand = seed && (!src || L.sr_one == 0 || (int)x == L.sr_one - 1);
     }
-    append_split(seed, (int)x, hv, N.list[L_BFS], S.c[C_BFS], S.c[C_BFSH], 0, 0, N.NL);
+    append_split(expand, (int)x, hv, N.list[L_BFS], S.c[C_BFS], S.c[C_BFSH], 0, 0, N.NL);
   }
 }
 
@@ -1648,16 +1697,32 @@ __device__ __forceinline__ void fwd_arcs(const NetDev& N, const NodeArcs& g, uns
   }
 }
 
-__device__ __forceinline__ void sr_emit(const NetDev& N, const Sched& L, const Slot& S, int y,
-                                        Acc& a) {
-  bool k = false, hv = false;
-  if (y >= 0 && !N.insr[y] && atomicExch(&N.stamp[y], L.epoch) != L.epoch) {
-    N.insr[y] = 1;
-    hv = (N.flags[y] & kHeavy) != 0;
-    if (y < N.n_nodes) a.w += N.node_w[y];
-    k = true;
+// sr_emit for the two heads c1, c2 of one arc group (distinct when both are
+// given): the loads of both first, one ballot pass for both appends.
+__device__ __forceinline__ void sr_emit2(const NetDev& N, const Sched& L, const Slot& S, int c1,
+                                         int c2, Acc& a) {
+  uint8_t i1 = 1, i2 = 1, f1 = 0, f2 = 0;
+  if (c1 >= 0) {
+    i1 = N.insr[c1];
+    f1 = N.flags[c1];
   }
-  append_split(k, y, hv, N.list[L_BFS], S.c[C_BFS], S.c[C_BFSH], L.bfs_end, L.bfsh_end, N.NL);
+  if (c2 >= 0) {
+    i2 = N.insr[c2];
+    f2 = N.flags[c2];
+  }
+  bool k1 = !i1, k2 = !i2;
+  if (k1) k1 = atomicExch(&N.stamp[c1], L.epoch) != L.epoch;
+  if (k2) k2 = atomicExch(&N.stamp[c2], L.epoch) != L.epoch;
+  if (k1) {
+    N.insr[c1] = 1;
+    if (c1 < N.n_nodes) a.w += N.node_w[c1];
+  }
+  if (k2) {
+    N.insr[c2] = 1;
+    if (c2 < N.n_nodes) a.w += N.node_w[c2];
+  }
+  append_split2(k1, c1, (f1 & kHeavy) != 0, k2, c2, (f2 & kHeavy) != 0, N.list[L_BFS],
+                S.c[C_BFS], S.c[C_BFSH], L.bfs_end, L.bfsh_end, N.NL);
 }
 
 template <int TW>
@@ -1678,8 +1743,7 @@ __device__ void sr_team(const NetDev& N, const Sched& L, const Slot& S, int x, u
     const unsigned k = c * TW + tl;
     int c1 = -1, c2 = -1;
     if (k < g.items) fwd_arcs(N, g, k, w, fb, c1, c2, a);
-    sr_emit(N, L, S, c1, a);
-    sr_emit(N, L, S, c2, a);
+    sr_emit2(N, L, S, c1, c2, a);
   }
 }
 
@@ -1700,8 +1764,7 @@ __device__ void sr_level(const NetDev& N, const Sched& L, const Team& T, const S
       const unsigned k = k0 + threadIdx.x;
       int c1 = -1, c2 = -1;
       if (k < g.items) fwd_arcs(N, g, k, w, fb, c1, c2, a);
-      sr_emit(N, L, S, c1, a);
-      sr_emit(N, L, S, c2, a);
+      sr_emit2(N, L, S, c1, c2, a);
     }
   }
 }
@@ -1963,6 +2026,8 @@ __device__ void load_sched(Sched& L, const EngineCtl* E) {
   L.seed = v->seed;
   L.last_gr = v->last_gr;
   L.gr_sync = v->gr_sync;
+  L.gr_one = v->gr_one;
+  L.sr_one = v->sr_one;
   L.fsel = v->fsel;
   L.rounds = v->rounds;
   L.grs = v->grs;
@@ -2000,6 +2065,8 @@ __device__ void store_sched(EngineCtl* E, const Sched& L) {
   v->seed = L.seed;
   v->last_gr = L.last_gr;
   v->gr_sync = L.gr_sync;
+  v->gr_one = L.gr_one;
+  v->sr_one = L.sr_one;
   v->fsel = L.fsel;
   v->rounds = L.rounds;
   v->grs = L.grs;

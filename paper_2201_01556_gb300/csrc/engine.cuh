@@ -20,8 +20,8 @@ enum EngineState : int {
   ST_TAIL = 9,      // rounds run by CTA 0 alone while the frontier is small
   // batched FlowCutter (fc_batch_kernel): the steps of Algorithm 2 around the flow
   ST_FC_SAT = 10,     // saturate the arcs out of a new source hypernode
-  ST_FC_SEL = 11,     // largest piercing key over the candidates
-  ST_FC_FIND = 12,    // the candidate holding that key
+  ST_FC_SEL = 11,     // largest piercing key over the candidates, and its holder
+  ST_FC_FIND = 12,    // (unused: the holder comes with the key)
   ST_FC_MARK_S = 13,  // S <- S_r + pierced node
   ST_FC_MARK_T = 14,  // T <- T_r + pierced node, their excess joins the flow
   ST_SR_ADD = 15,   // source-side cut grown from one new source (S_r kept)
@@ -31,6 +31,9 @@ enum EngineState : int {
   ST_ROUND = 19,    // one-phase round: apply last round's pushes, discharge, relabel
   ST_FLUSH = 20,    // apply the pushes of the last one-phase round (before a relabel)
 };
+
+// Slots of per-state time accounting (states 0 .. ST_FLUSH).
+constexpr int kStateSlots = 24;
 
 // list ids in NetDev::list.  Each list array holds light nodes from the front
 // and heavy nodes from the back (heavy entry i sits at NL - 1 - i); a node is
@@ -61,6 +64,11 @@ struct Sched {
   unsigned long long gq_items, gq_overs;   // queue entries expanded, queue overflows
   unsigned gq_prev;       // queue slots written by the last asynchronous relabel
   unsigned gq_pad;
+  // Seeds of the searches from the terminal sets: 0 seeds every sink (global
+  // relabel) / every source (S_r); v + 1 seeds only the terminal v, the one
+  // terminal that can have residual arcs to (from) the other nodes.  The
+  // other terminals still get label 0 / join S_r, they are only not expanded.
+  int gr_one, sr_one;
   long long wS, wT;
   int wS_set, wT_set;
 };
@@ -130,15 +138,22 @@ struct FcJob {
   unsigned long long device_ns;  // globaltimer time of the job in its group
   int32_t group_ctas;            // CTAs of that group
   int32_t pad;
+  // group time per engine state (phases run by one CTA count as ST_TAIL)
+  unsigned long long st_ns[kStateSlots];
+  unsigned st_cnt[kStateSlots];
 };
 
 // Work queue and per-group barriers of a batched launch.
 constexpr int kMaxGroups = 1024;
+constexpr int kMaxBatchCtas = 1024;
 struct BatchCtl {
   unsigned next;              // next job to hand out
   int err;                    // a group barrier timed out
   unsigned gbar[kMaxGroups];  // count-up barrier per group
   unsigned gjob[kMaxGroups];  // job handed to each group
+  // per CTA: its largest piercing key and the node holding it (ST_FC_SEL)
+  unsigned long long sel_key[kMaxBatchCtas];
+  int sel_node[kMaxBatchCtas];
 };
 
 }  // namespace hfp

@@ -126,65 +126,178 @@ __device__ void fc_saturate(const NetDev& N, const Sched& L, const Team& T, cons
   if (sink_acc) atomicAdd(S.flow, sink_acc);
 }
 
+// The marking scans take kMarkUnroll nodes per thread and step, so that the
+// membership loads of a step are in flight together.
+constexpr int kMarkUnroll = 4;
+
+__device__ __forceinline__ void mark_source(const NetDev& N, int y) {
+  N.flags[y] = (N.flags[y] & kHeavy) | kSource;
+  N.lab0[y] = N.NL;
+  N.lab1[y] = N.NL;
+  N.excess[y] = 0;
+}
+
 // S <- S_r + {u}: sources get label NL and lose their excess.
 __device__ void fc_mark_sources(const NetDev& N, const Team& T, int u) {
   const int NL = N.NL;
-  for (int x = T.tid; x <= NL; x += T.nth) {
-    const int y = x < NL ? x : u;
-    if (x < NL && !N.insr[x]) continue;
-    N.flags[y] = (N.flags[y] & kHeavy) | kSource;
-    N.lab0[y] = NL;
-    N.lab1[y] = NL;
-    N.excess[y] = 0;
+  for (int base = T.tid; base < NL; base += kMarkUnroll * T.nth) {
+    bool in[kMarkUnroll];
+#pragma unroll
+    for (int j = 0; j < kMarkUnroll; j++) {
+      const int x = base + j * T.nth;
+      in[j] = x < NL && N.insr[x] != 0;
+    }
+#pragma unroll
+    for (int j = 0; j < kMarkUnroll; j++)
+      if (in[j]) mark_source(N, base + j * T.nth);
   }
+  if (T.tid == 0) mark_source(N, u);
 }
 
-// T <- T_r + {u} (T_r = {label < NL} after the final global relabel); the
-// excess of a node that becomes a sink joins the flow (Section 8.4,
-// "Sink-Side Piercing").
+__device__ __forceinline__ unsigned long long mark_sink(const NetDev& N, int y) {
+  const uint8_t f = N.flags[y];
+  if (f & kSink) return 0;
+  const long long ex = N.excess[y];
+  N.excess[y] = 0;
+  N.flags[y] = (f & kHeavy) | kSink;
+  return ex > 0 ? (unsigned long long)ex : 0ull;
+}
+
+// T <- T_r + {u} (T_r = {label < NL} after the final global relabel; u is
+// outside it); the excess of a node that becomes a sink joins the flow
+// (Section 8.4, "Sink-Side Piercing").
 __device__ void fc_mark_sinks(const NetDev& N, const Team& T, const Slot& S, int u) {
   const int NL = N.NL;
   unsigned long long acc = 0;
-  for (int x = T.tid; x <= NL; x += T.nth) {
-    const int y = x < NL ? x : u;
-    if (x < NL && N.lab0[x] >= NL) continue;
-    if (N.flags[y] & kSink) continue;
-    const long long ex = N.excess[y];
-    if (ex > 0) acc += (unsigned long long)ex;
-    N.excess[y] = 0;
-    N.flags[y] = (N.flags[y] & kHeavy) | kSink;
+  for (int base = T.tid; base < NL; base += kMarkUnroll * T.nth) {
+    bool in[kMarkUnroll];
+#pragma unroll
+    for (int j = 0; j < kMarkUnroll; j++) {
+      const int x = base + j * T.nth;
+      in[j] = x < NL && N.lab0[x] < NL;
+    }
+#pragma unroll
+    for (int j = 0; j < kMarkUnroll; j++)
+      if (in[j]) acc += mark_sink(N, base + j * T.nth);
   }
+  if (T.tid == 0) acc += mark_sink(N, u);
   if (acc) atomicAdd(S.flow, acc);
 }
 
-// Largest piercing key (find = false) or the node holding key `best`.
-__device__ void fc_pierce_scan(const NetDev& N, const Team& T, EngineCtl* E, unsigned sl,
-                               const FcJob& J, const FcState& F, long long w_reach, bool find,
-                               unsigned lane) {
+// Largest piercing key over the candidates and the node holding it, as the
+// CTA's entry (sel_key, sel_node)[blockIdx.x] of the launch's BatchCtl (the
+// group reduces its entries after the barrier; keys of distinct candidates
+// differ in the hash bits, so the maximum has one holder).  A warp takes 32
+// consecutive nets, one per lane, and walks the concatenated pin lists of the
+// reachable ones 32 pins per step, so a step costs one chain of dependent
+// loads for up to 32 nets.  Every thread of the CTA must call it.
+__device__ void fc_pierce_select(const NetDev& N, const Team& T, BatchCtl* B, const FcJob& J,
+                                 const FcState& F, long long w_reach, unsigned lane) {
+  __shared__ unsigned long long sk[32];
+  __shared__ int sn[32];
   const int nh = N.n_nodes, m = N.m_nets, NL = N.NL;
-  unsigned long long mx = 0;
-  for (unsigned e = T.gwarp; e < (unsigned)m; e += T.nwarps) {
-    const int node = F.grow_s ? nh + e : nh + m + e;
-    const bool reach = F.grow_s ? N.insr[node] != 0 : N.lab0[node] < NL;
-    if (!reach) continue;
-    for (unsigned p = N.net_off[e] + lane; p < N.net_off[e + 1]; p += 32) {
-      const int h = N.pin[p];
-      const unsigned long long k = batch_pierce_key(N, h, F.grow_s, J.max_w, w_reach, J.seed);
-      if (find) {
-        if (k != 0 && k == F.best) E->node3[sl] = h;
-      } else if (k > mx) {
-        mx = k;
+  unsigned long long best = 0;
+  int bnode = -1;
+  for (unsigned e0 = T.gwarp * 32; e0 < (unsigned)m; e0 += T.nwarps * 32) {
+    const unsigned e = e0 + lane;
+    unsigned beg = 0, sz = 0;
+    if (e < (unsigned)m) {
+      const int node = F.grow_s ? nh + (int)e : nh + m + (int)e;
+      const bool reach = F.grow_s ? N.insr[node] != 0 : N.lab0[node] < NL;
+      if (reach) {
+        beg = N.net_off[e];
+        sz = N.net_off[e + 1] - beg;
+      }
+    }
+    unsigned incl = sz;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned t = __shfl_up_sync(FULL, incl, o);
+      if ((int)lane >= o) incl += t;
+    }
+    const unsigned total = __shfl_sync(FULL, incl, 31);
+    const unsigned excl = incl - sz;
+    for (unsigned q0 = 0; q0 < total; q0 += 32) {
+      const unsigned q = q0 + lane;
+      // owner = number of lanes whose inclusive end is <= q
+      int own = 0;
+#pragma unroll
+      for (int step = 16; step > 0; step >>= 1) {
+        const unsigned v = __shfl_sync(FULL, incl, own + step - 1);
+        if (v <= q) own += step;
+      }
+      own = own < 31 ? own : 31;
+      const unsigned ob = __shfl_sync(FULL, beg, own), oe = __shfl_sync(FULL, excl, own);
+      if (q < total) {
+        const int h = N.pin[ob + (q - oe)];
+        const unsigned long long k = batch_pierce_key(N, h, F.grow_s, J.max_w, w_reach, J.seed);
+        if (k > best) {
+          best = k;
+          bnode = h;
+        }
       }
     }
   }
-  if (!find) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long tk = __shfl_xor_sync(FULL, best, o);
+    const int tn = __shfl_xor_sync(FULL, bnode, o);
+    if (tk > best) {
+      best = tk;
+      bnode = tn;
+    }
+  }
+  const unsigned w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (lane == 0) {
+    sk[w] = best;
+    sn[w] = bnode;
+  }
+  __syncthreads();
+  if (w == 0) {
+    best = lane < nw ? sk[lane] : 0ull;
+    bnode = lane < nw ? sn[lane] : -1;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      const unsigned long long t = __shfl_xor_sync(FULL, mx, o);
-      mx = t > mx ? t : mx;
+      const unsigned long long tk = __shfl_xor_sync(FULL, best, o);
+      const int tn = __shfl_xor_sync(FULL, bnode, o);
+      if (tk > best) {
+        best = tk;
+        bnode = tn;
+      }
     }
-    if (lane == 0 && mx) atomicMax(&E->key3[sl], mx);
+    if (lane == 0) {
+      B->sel_key[blockIdx.x] = best;
+      B->sel_node[blockIdx.x] = bnode;
+    }
   }
+}
+
+// The group's largest key and its node from the entries of its G CTAs
+// (first CTA of the group: c0).  Warp 0 of the calling CTA; the result is
+// in lane 0.
+__device__ void fc_select_reduce(const BatchCtl* B, unsigned c0, int G, unsigned lane,
+                                 unsigned long long& key, int& node) {
+  unsigned long long best = 0;
+  int bnode = -1;
+  for (int r = (int)lane; r < G; r += 32) {
+    const unsigned long long k = __ldcg(&B->sel_key[c0 + r]);
+    const int h = __ldcg(&B->sel_node[c0 + r]);
+    if (k > best) {
+      best = k;
+      bnode = h;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long tk = __shfl_xor_sync(FULL, best, o);
+    const int tn = __shfl_xor_sync(FULL, bnode, o);
+    if (tk > best) {
+      best = tk;
+      bnode = tn;
+    }
+  }
+  key = best;
+  node = bnode;
 }
 
 // ---------------------------------------------------------------------------
@@ -256,6 +369,18 @@ __device__ void fc_on_done(Sched& L, FcState& F, const FcJob& J, const Ctl* c) {
 }
 
 // After a FlowCutter phase and its barrier.
+//
+// Terminal boundaries.  After S <- S_r + {v}, the only source with a residual
+// arc to a non-source is v: S_r was closed under residual arcs, no push ever
+// enters a source (its label is N_L and no label exceeds N_L), and a source
+// pushes only when it is saturated, which is v's own step.  Symmetrically,
+// after T <- T_r + {v} only v can have a residual arc from a non-sink: no
+// residual arc entered T_r from outside, and sinks never push, so no arc into
+// T gains residual capacity later.  So the global relabels seed the last
+// pierced sink alone (every sink still gets label 0) and the S_r searches the
+// last pierced source alone plus the excess nodes (every source still joins
+// S_r): the same labels and cuts as seeding every terminal, without
+// expanding the interiors of S and T, which grow to half the network.
 __device__ void fc_advance(Sched& L, FcState& F, const Snap& q, const FcJob& J, Params& P,
                            bool recorder) {
   switch (L.state) {
@@ -280,7 +405,8 @@ __device__ void fc_advance(Sched& L, FcState& F, const Snap& q, const FcJob& J, 
       } else {
         // the new excess is the frontier; labels stay valid (SETUP_ROUND)
         L.epoch++;
-        L.state = ST_ROUND_A;
+        L.state = round_state(P);
+        L.fsel = L_FRONT;
         L.fcnt = q.c[C_FRONT];
         L.fcnth = q.c[C_FRONTH];
         L.rcnt = 0;
@@ -290,14 +416,12 @@ __device__ void fc_advance(Sched& L, FcState& F, const Snap& q, const FcJob& J, 
       }
       break;
     case ST_FC_SEL:
+      // q.key / q.node: the group's largest key and its holder
       if (q.key == 0) {
         fc_finish(L, F, -5 /* HFP_NO_BALANCED_CUT */);
-      } else {
-        F.best = q.key;
-        L.state = ST_FC_FIND;
+        break;
       }
-      break;
-    case ST_FC_FIND:
+      F.best = q.key;
       F.node = q.node;
       F.nopath = (int)((F.best >> 53) & 1ull);
       if (recorder && F.np < J.pierce_cap) {
@@ -309,6 +433,7 @@ __device__ void fc_advance(Sched& L, FcState& F, const Snap& q, const FcJob& J, 
       break;
     case ST_FC_MARK_S:
       L.epoch++;           // SETUP_PREP / SETUP_SR_ADD: fresh stamps
+      L.sr_one = F.node + 1;   // the one source with residual arcs out of S
       if (F.nopath) {
         // lazy piercing (hfp_flowcutter's rule): the preflow stays maximum,
         // S_r grows by the node's reach, its arcs wait for a sink piercing
@@ -325,6 +450,7 @@ __device__ void fc_advance(Sched& L, FcState& F, const Snap& q, const FcJob& J, 
       break;
     case ST_FC_MARK_T:
       L.flow += q.flow;    // excess absorbed by the new sinks
+      L.gr_one = F.node + 1;   // the one sink with residual arcs into T
       F.stage = FC_FLOW;
       F.it++;
       incremental_stall(P);   // the flows from here on are incremental
@@ -435,28 +561,39 @@ __device__ __forceinline__ bool job_barrier(EngineCtl* E, unsigned ctr, unsigned
   return grid_barrier(E, G * ++bar_seq, timeout_ns);
 }
 
-__device__ void run_phase_batch(const NetDev& N, EngineCtl* E, const Sched& L, const FcState& F,
-                                const FcJob& J, const Team& T, unsigned lane, Acc& a,
-                                long long* w_sh, const Params& P) {
+__device__ void run_phase_batch(const NetDev& N, EngineCtl* E, BatchCtl* B, const Sched& L,
+                                const FcState& F, const FcJob& J, const Team& T, unsigned lane,
+                                Acc& a, long long* w_sh, const Params& P) {
   const Slot S = slot_of(E, L.phase);
   switch (L.state) {
     case ST_FC_SAT: fc_saturate(N, L, T, S, F.node, lane); break;
-    case ST_FC_SEL:
-      fc_pierce_scan(N, T, E, L.phase % 3, J, F, F.grow_s ? L.wS : L.wT, false, lane);
-      break;
-    case ST_FC_FIND:
-      fc_pierce_scan(N, T, E, L.phase % 3, J, F, F.grow_s ? L.wS : L.wT, true, lane);
-      break;
+    case ST_FC_SEL: fc_pierce_select(N, T, B, J, F, F.grow_s ? L.wS : L.wT, lane); break;
     case ST_FC_MARK_S: fc_mark_sources(N, T, F.node); break;
     case ST_FC_MARK_T: fc_mark_sinks(N, T, S, F.node); break;
     default: run_phase(N, E, L, T, lane, a, w_sh, P); break;
   }
 }
 
+// Group time per state of the running job, kept by thread 0 of its first CTA.
+struct BatchClock {
+  unsigned long long t;
+  unsigned long long ns[kStateSlots];
+  unsigned cnt[kStateSlots];
+};
+
+__device__ __forceinline__ void batch_tick(BatchClock& bc, int st) {
+  const unsigned long long t = globaltimer();
+  st = st < kStateSlots ? st : kStateSlots - 1;
+  bc.ns[st] += t - bc.t;
+  bc.cnt[st]++;
+  bc.t = t;
+}
+
 // One job by one group of G CTAs (rank = position in the group).
 __device__ void fc_run_job(FcJob* job, const Params& P0, int rank, int G, unsigned lane,
                            Sched& L, FcState& F, NetDev& N, Params& P, long long* w_sh,
-                           Clock& ck, SoloSh& solo, unsigned ctr, unsigned& cseq) {
+                           Clock& ck, SoloSh& solo, unsigned ctr, unsigned& cseq,
+                           BatchClock& bc, BatchCtl* B) {
   const unsigned wib = threadIdx.x >> 5, nwb = blockDim.x >> 5;
   const Team T{rank * nwb + wib, G * nwb, rank * blockDim.x + threadIdx.x, G * blockDim.x,
                (unsigned)rank, (unsigned)G};
@@ -467,12 +604,23 @@ __device__ void fc_run_job(FcJob* job, const Params& P0, int rank, int G, unsign
     N = job->N;
     P = P0;
     P.gr_work = job->gr_work;
+    if (!N.delta1) P.fused_rounds = 0;   // buffers of this network
+    if (!N.gq) P.async_gr = 0;
+    if (rank == 0) {
+      for (int k = 0; k < kStateSlots; k++) {
+        bc.ns[k] = 0;
+        bc.cnt[k] = 0;
+      }
+      bc.t = t_start;
+    }
     load_sched(L, E);
     L.flow = *(const volatile unsigned long long*)&E->c.flow;
     F = FcState{FC_FLOW, 0, 1, 0, 0, 1, job->dist_ready, 0, 0, 0, 0, -1, 0, 0, 0ull, 0ll};
     // SETUP_PREP, then the saturation of s opens the first flow
     L.epoch++;
     L.state = ST_FC_SAT;
+    L.sr_one = 1;   // S = {s}, T = {t}
+    L.gr_one = 2;
     *w_sh = 0;
   }
   __syncthreads();
@@ -489,6 +637,7 @@ __device__ void fc_run_job(FcJob* job, const Params& P0, int rank, int G, unsign
       }
       const bool ok = job_barrier(E, ctr, cseq, bar_seq, G, P.timeout_ns);
       if (threadIdx.x == 0) {
+        if (lead) batch_tick(bc, ST_TAIL);
         if (!lead) load_sched(L, E);
         if (!ok) L.state = ST_DONE;
         if (L.state == ST_DONE && !F.finished) fc_on_done(L, F, *job, &E->c);
@@ -498,16 +647,25 @@ __device__ void fc_run_job(FcJob* job, const Params& P0, int rank, int G, unsign
     }
     if (lead && threadIdx.x == 0)
       clear_slot(E, (L.phase + 1) % 3, st == ST_GR_INIT || st == ST_GR_ADD);
-    run_phase_batch(N, E, L, F, *job, T, lane, a, w_sh, P);
+    run_phase_batch(N, E, B, L, F, *job, T, lane, a, w_sh, P);
     __syncthreads();
     if (threadIdx.x == 0) flush_weight(E, L.phase, w_sh);
     const bool ok = job_barrier(E, ctr, cseq, bar_seq, G, P.timeout_ns);
+    unsigned long long sel_key = 0;
+    int sel_node = -1;
+    if (st == ST_FC_SEL && threadIdx.x < 32)
+      fc_select_reduce(B, blockIdx.x - (unsigned)rank, G, lane, sel_key, sel_node);
     if (threadIdx.x == 0) {
+      if (lead) batch_tick(bc, st);
       if (!ok) {
         L.state = ST_DONE;
         fc_on_done(L, F, *job, &E->c);
       } else {
-        const Snap q = take_snap(E, L.phase);
+        Snap q = take_snap(E, L.phase);
+        if (st == ST_FC_SEL) {
+          q.key = sel_key;
+          q.node = sel_node;
+        }
         if (is_fc_state(st)) fc_advance(L, F, q, *job, P, lead);
         else advance(L, q, P, N, &E->c);
         L.phase++;
@@ -522,6 +680,9 @@ __device__ void fc_run_job(FcJob* job, const Params& P0, int rank, int G, unsign
   if (a.nodes) atomicAdd(&E->c.node_visits, a.nodes);
   if (a.pushes) atomicAdd(&E->c.pushes, a.pushes);
   if (lead && threadIdx.x == 0) {
+    // later calls on the network seed every terminal again
+    L.gr_one = 0;
+    L.sr_one = 0;
     store_sched(E, L);
     E->c.flow = L.flow;
     E->c.rounds = L.rounds;
@@ -537,6 +698,10 @@ __device__ void fc_run_job(FcJob* job, const Params& P0, int rank, int G, unsign
     job->source_weight = F.source_weight;
     job->device_ns = globaltimer() - t_start;
     job->group_ctas = G;
+    for (int k = 0; k < kStateSlots; k++) {
+      job->st_ns[k] = bc.ns[k];
+      job->st_cnt[k] = bc.cnt[k];
+    }
   }
 }
 
@@ -561,6 +726,7 @@ __global__ void __launch_bounds__(kEngineThreads, 2) fc_batch_kernel(FcJob* jobs
   __shared__ SoloSh solo;
   __shared__ unsigned job_sh;
   __shared__ unsigned gbar_sh;   // the group's barrier counter (cluster rank 0's is used)
+  __shared__ BatchClock bclk;
   const int big_ctas = big * Gb;
   int gid, rank, Gg;
   if ((int)blockIdx.x < big_ctas) {
@@ -587,7 +753,7 @@ __global__ void __launch_bounds__(kEngineThreads, 2) fc_batch_kernel(FcJob* jobs
   unsigned j = (unsigned)gid;
   for (;;) {
     if (j >= (unsigned)n_jobs) break;
-    fc_run_job(&jobs[j], P0, rank, Gg, lane, L, F, N, P, &w_sh, ck, solo, ctr, cseq);
+    fc_run_job(&jobs[j], P0, rank, Gg, lane, L, F, N, P, &w_sh, ck, solo, ctr, cseq, bclk, B);
     // hand-out of the next job (the queue starts after the first job of every group)
     if (rank == 0 && threadIdx.x == 0) B->gjob[gid] = n_groups + atomicAdd(&B->next, 1u);
     const bool ok = cluster ? cluster_barrier(ctr, Gg * ++cseq, &B->err, 1, nullptr, P0.timeout_ns)

@@ -64,6 +64,11 @@ struct hfp_ctx {
   uint32_t batch_big_ctas = 0;     // hfp_tuning.batch_big_ctas
   uint32_t batch_big_groups = 0;   // hfp_tuning.batch_big_groups
   uint32_t identical_nets = 0;     // hfp_tuning.identical_nets
+  uint32_t batch_fused_rounds = 1; // hfp_tuning.batch_fused_rounds
+  uint32_t batch_async_gr = 0;     // hfp_tuning.batch_async_gr
+  // group time per engine state of the batched launches since the last reset
+  uint64_t batch_ns[hfp::kStateSlots] = {};
+  uint64_t batch_cnt[hfp::kStateSlots] = {};
 };
 
 struct hfp_net {
@@ -126,6 +131,10 @@ struct BatchItem {
   hfp_status status = HFP_OK;
   int32_t group_ctas = 0;          // CTAs of the group that solved it
 };
+
+// Allocates the buffers of one-phase rounds (P.fused_rounds) and queue-driven
+// global relabels (P.async_gr) that the network does not have yet (api.cu).
+hfp_status ensure_engine_buffers(hfp_net* net, const Params& P);
 
 // Grid of fc_batch_kernel on the context's device (all CTAs co-resident).
 hfp_status batch_grid(hfp_ctx* ctx, int* grid);

@@ -80,8 +80,8 @@ enum SetupMode : int { SETUP_GR = 0, SETUP_ROUND = 1, SETUP_SR = 2, SETUP_PREP =
 void launch_engine_setup(EngineCtl* E, int mode, cudaStream_t st, int32_t arg = 0);
 void launch_saturate(const NetDev& N, EngineCtl* E, const int32_t* nodes, int32_t count,
                      cudaStream_t st);
-void launch_mark_sources(const NetDev& N, const int32_t* extra, int32_t count, int sms,
-                         cudaStream_t st);
+void launch_mark_sources(const NetDev& N, EngineCtl* E, const int32_t* extra, int32_t count,
+                         int sms, cudaStream_t st);
 void launch_mark_sinks(const NetDev& N, EngineCtl* E, const int32_t* extra, int32_t count,
                        int sms, cudaStream_t st);
 // Largest piercing key (and its node) among the candidates, or among those

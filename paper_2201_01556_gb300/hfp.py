@@ -55,7 +55,8 @@ class Tuning(ctypes.Structure):
                                                "stall_rounds_pierce", "batch_cluster",
                                                "batch_big_ctas", "batch_big_groups",
                                                "async_gr", "gr_warps", "fused_rounds",
-                                               "identical_nets")]
+                                               "identical_nets", "batch_fused_rounds",
+                                               "batch_async_gr")]
 
 
 class RefineParams(ctypes.Structure):
@@ -163,6 +164,7 @@ def load():
         "hfp_net_get_trace": (i32, [P, P, P, P, i32, P]),
         "hfp_pair_features": (i32, [P, P, i32, i32, P, P, P, i32, P]),
         "hfp_flowcutter_batch": (i32, [P, P, i32, i32]),
+        "hfp_ctx_batch_profile": (i32, [P, P, P, i32, i32]),
         "hfp_refine_round_batched": (i32, [P, P, i32, ctypes.POINTER(RefineParams), P,
                                            ctypes.c_float, i32, ctypes.POINTER(RoundStats), P,
                                            i32, P, P]),
@@ -362,6 +364,28 @@ def max_flow_noalloc(device: int, stream: int, view: dict, n_nodes: int, m_nets:
 
 STATE_NAMES = ("done", "push", "relabel", "gr_init", "gr_level", "sr_init", "sr_level",
                "dist_init", "dist_level", "other")
+
+
+# engine states 0 .. 20 (the numbering of the batched-launch profile)
+ENGINE_STATES = ("done", "push", "relabel", "gr_init", "gr_level", "sr_init", "sr_level",
+                 "dist_init", "dist_level", "one_cta", "fc_saturate", "fc_select", "unused12",
+                 "fc_mark_s", "fc_mark_t", "sr_add", "gr_add", "gr_seed", "gr_run", "round",
+                 "flush")
+
+
+def ctx_batch_profile(ctx: Context, reset: bool = True) -> dict:
+    """hfp_ctx_batch_profile -> {state: (device ns, phases)} of the batched
+    launches since the last reset, summed over their networks (states with
+    no phase are left out)."""
+    ns = np.zeros(24, np.uint64)
+    cnt = np.zeros(24, np.uint64)
+    _check(load().hfp_ctx_batch_profile(ctx.h, _ptr(ns), _ptr(cnt), 24, 1 if reset else 0))
+    out = {}
+    for i in range(24):
+        if cnt[i]:
+            name = ENGINE_STATES[i] if i < len(ENGINE_STATES) else f"state{i}"
+            out[name] = (int(ns[i]), int(cnt[i]))
+    return out
 
 
 def net_enable_trace(net: Net, phases: int):

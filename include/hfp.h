@@ -388,11 +388,16 @@ hfp_status hfp_flowcutter_batch(hfp_ctx* ctx, hfp_fc_task* tasks, int32_t n, int
  * 10 saturation of a new source, 11 piercing-key maximum with its holder
  * (12 unused), 13 / 14 marking S / T, 15 / 16 S_r / T_r grown from one node, 17 / 18
  * queue-driven global relabel seed / search, 19 one-phase round, 20 flush
- * of its pushes; phases run by one CTA count as 9).  reset != 0 zeroes the
- * sums after copying.  Host memory; either pointer may be NULL.  No paper
+ * of its pushes; phases run by one CTA count as 9), and the summed input
+ * sizes of those phases, light_in / heavy_in (nodes of at most / more than
+ * 16 arc groups in the frontier, the list being applied, or the
+ * breadth-first-search level; for state 11 light_in counts the nets whose
+ * pins the selection walked; 0 for other states).  reset != 0 zeroes the
+ * sums after copying.  Host memory; any pointer may be NULL.  No paper
  * counterpart. */
 hfp_status hfp_ctx_batch_profile(hfp_ctx* ctx, uint64_t* state_ns, uint64_t* state_cnt,
-                                 int32_t n_states, int32_t reset);
+                                 uint64_t* light_in, uint64_t* heavy_in, int32_t n_states,
+                                 int32_t reset);
 
 /* --- k-way refinement (Section 4, Algorithm 1; Sections 5 and 6) ---------
  * A device-resident hypergraph (with its vertex -> nets incidence) for

@@ -275,6 +275,7 @@ HFP_API void hfp_net_destroy(hfp_net* net) {
   if (net->trace_buf) cudaFreeAsync(net->trace_buf, st);
   if (net->gq_buf) cudaFreeAsync(net->gq_buf, st);
   if (net->delta1_buf) cudaFreeAsync(net->delta1_buf, st);
+  if (net->net_done_buf) cudaFreeAsync(net->net_done_buf, st);
   cudaStreamSynchronize(st);
   delete net;
   ctx_release(c);

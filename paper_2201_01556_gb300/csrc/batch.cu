@@ -96,6 +96,12 @@ hfp_status run_fc_batch(hfp_ctx* ctx, BatchItem* items, int n, int group_ctas, f
     // a network without these buffers runs two-phase rounds and level-by-level
     // relabels (the kernel checks per job)
     if (hfp_status s2 = ensure_engine_buffers(net, P0)) return s2;
+    if (!net->d.net_done) {
+      const size_t mb = net->d.m_nets > 0 ? (size_t)net->d.m_nets : 1;
+      CK(cudaMallocAsync(&net->net_done_buf, mb, st));
+      CK(cudaMemsetAsync(net->net_done_buf, 0, mb, st));
+      net->d.net_done = (uint8_t*)net->net_done_buf;
+    }
     FcJob& J = jobs[t];
     memset(&J, 0, sizeof(J));
     J.N = net->d;
@@ -145,6 +151,8 @@ hfp_status run_fc_batch(hfp_ctx* ctx, BatchItem* items, int n, int group_ctas, f
     for (int k = 0; k < kStateSlots; k++) {
       ctx->batch_ns[k] += J.st_ns[k];
       ctx->batch_cnt[k] += J.st_cnt[k];
+      ctx->batch_lin[k] += J.st_lin[k];
+      ctx->batch_hin[k] += J.st_hin[k];
     }
     hfp_net* net = it.net;
     net->flow_started = true;
@@ -231,15 +239,19 @@ HFP_API hfp_status hfp_flowcutter_batch(hfp_ctx* ctx, hfp_fc_task* tasks, int32_
 }
 
 HFP_API hfp_status hfp_ctx_batch_profile(hfp_ctx* ctx, uint64_t* state_ns, uint64_t* state_cnt,
+                                         uint64_t* light_in, uint64_t* heavy_in,
                                          int32_t n_states, int32_t reset) {
   if (!ctx || n_states < 0) return fail(HFP_ERR_INVALID, "bad arguments");
   const int k = std::min<int>(n_states, kStateSlots);
   for (int i = 0; i < k; i++) {
     if (state_ns) state_ns[i] = ctx->batch_ns[i];
     if (state_cnt) state_cnt[i] = ctx->batch_cnt[i];
+    if (light_in) light_in[i] = ctx->batch_lin[i];
+    if (heavy_in) heavy_in[i] = ctx->batch_hin[i];
   }
   if (reset) {
-    for (int i = 0; i < kStateSlots; i++) ctx->batch_ns[i] = ctx->batch_cnt[i] = 0;
+    for (int i = 0; i < kStateSlots; i++)
+      ctx->batch_ns[i] = ctx->batch_cnt[i] = ctx->batch_lin[i] = ctx->batch_hin[i] = 0;
   }
   return HFP_OK;
 }

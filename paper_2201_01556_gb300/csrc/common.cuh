@@ -63,6 +63,8 @@ struct NetDev {
   unsigned int trace_cap;       // phases the trace can hold
   unsigned int gq_cap;          // entries of gq
   unsigned long long* gq;       // work queue of the asynchronous global relabel (may be null)
+  uint8_t* net_done;            // per net: every pin is a terminal (batched piercing scans;
+                                // may be null)
 };
 
 struct Ctl {

@@ -179,6 +179,154 @@ __device__ __forceinline__ NodeArcs node_arcs(const NetDev& N, int x) {
   return r;
 }
 
+// The light nodes nodes[0 .. count) (count <= 32) of a breadth-first level
+// by one warp: every lane loads one node, and the warp walks the
+// concatenated arc groups of the 32 nodes, 32 per step, so that a step costs
+// one chain of dependent loads for up to 32 arc groups of different nodes
+// (a team of lanes per node would wait once per node).  fn(g, k, w, fb) is
+// called by every lane of the warp with the arc group k of node arcs g
+// (k == kNoArc: none for this lane in this step); w and fb are the net's
+// weight and bridge flow for net nodes.
+constexpr unsigned kNoArc = 0xffffffffu;
+
+template <class Fn>
+__device__ __forceinline__ void warp_walk_arcs(const NetDev& N, const int32_t* nodes,
+                                               unsigned count, unsigned lane, Fn fn) {
+  NodeArcs g{0, 0, 0, 0};
+  int w = 0, fb = 0;
+  if (lane < count) {
+    g = node_arcs(N, nodes[lane]);
+    if (g.kind) {
+      w = N.net_w[g.e];
+      fb = N.f_b[g.e];
+    }
+  }
+  unsigned incl = g.items;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned t = __shfl_up_sync(FULL, incl, o);
+    if ((int)lane >= o) incl += t;
+  }
+  const unsigned total = __shfl_sync(FULL, incl, 31);
+  const unsigned excl = incl - g.items;
+  for (unsigned q0 = 0; q0 < total; q0 += 32) {
+    const unsigned q = q0 + lane;
+    // owner: the number of lanes whose arcs end at or before q
+    int own = 0;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) {
+      const unsigned v = __shfl_sync(FULL, incl, own + step - 1);
+      if (v <= q) own += step;
+    }
+    own = own < 31 ? own : 31;
+    NodeArcs og;
+    og.kind = __shfl_sync(FULL, g.kind, own);
+    og.e = __shfl_sync(FULL, g.e, own);
+    og.beg = __shfl_sync(FULL, g.beg, own);
+    og.items = __shfl_sync(FULL, g.items, own);
+    const int ow = __shfl_sync(FULL, w, own), ofb = __shfl_sync(FULL, fb, own);
+    const unsigned oex = __shfl_sync(FULL, excl, own);
+    fn(og, q < total ? q - oex : kNoArc, ow, ofb);
+  }
+}
+
+// Node x (x < 0: idle team) by a team of kTeam lanes, kTeam arc groups per
+// step; fn as in warp_walk_arcs.
+template <class Fn>
+__device__ __forceinline__ void team_walk_arcs(const NetDev& N, int x, unsigned lane, Fn fn) {
+  const unsigned tl = lane & (kTeam - 1);
+  NodeArcs g{0, 0, 0, 0};
+  int w = 0, fb = 0;
+  if (x >= 0) {
+    g = node_arcs(N, x);
+    if (g.kind) {
+      w = N.net_w[g.e];
+      fb = N.f_b[g.e];
+    }
+  }
+  const unsigned steps = warp_max_u((g.items + kTeam - 1) / kTeam);
+  for (unsigned c = 0; c < steps; c++) {
+    const unsigned k = c * kTeam + tl;
+    fn(g, k < g.items ? k : kNoArc, w, fb);
+  }
+}
+
+// The light nodes nodes[0 .. count) of a breadth-first level over the warps
+// of T: 32 per warp (warp_walk_arcs) when the level has more than kWalkMin
+// nodes per warp, else one per team, so that a small level still keeps
+// every warp busy.
+constexpr unsigned kWalkMin = 8;
+
+template <class Fn>
+__device__ __forceinline__ void level_light(const NetDev& N, const int32_t* nodes, unsigned count,
+                                            const Team& T, unsigned lane, Fn fn) {
+  if (count > kWalkMin * T.nwarps) {
+    for (unsigned base = T.gwarp * 32; base < count; base += T.nwarps * 32)
+      warp_walk_arcs(N, nodes + base, min(32u, count - base), lane, fn);
+  } else {
+    constexpr unsigned TPW = 32 / kTeam;
+    for (unsigned base = T.gwarp * TPW; base < count; base += T.nwarps * TPW) {
+      const unsigned i = base + lane / kTeam;
+      team_walk_arcs(N, i < count ? nodes[i] : -1, lane, fn);
+    }
+  }
+}
+
+// The heavy nodes of a breadth-first level (heavy entries hb .. hb + count
+// of a split list), up to 32 per CTA step: warp 0 loads one node per lane,
+// and the CTA walks the concatenated arc groups of those nodes blockDim.x per
+// step.  (A CTA per node would leave most threads idle for the typical heavy
+// node of a few dozen arc groups and take the nodes one after another.)  fn
+// as in warp_walk_arcs; every thread of the CTA must call this.
+struct HeavyStep {
+  NodeArcs g[32];
+  int w[32], fb[32];
+  unsigned incl[32];
+};
+
+template <class Fn>
+__device__ __forceinline__ void block_walk_heavy(const NetDev& N, const int32_t* list, unsigned hb,
+                                                 unsigned count, const Team& T, Fn fn) {
+  __shared__ HeavyStep H;
+  for (unsigned h0 = T.block * 32; h0 < count; h0 += T.nblocks * 32) {
+    if (threadIdx.x < 32) {
+      const unsigned t = threadIdx.x;
+      NodeArcs g{0, 0, 0, 0};
+      int w = 0, fb = 0;
+      if (h0 + t < count) {
+        g = node_arcs(N, list[N.NL - 1 - (hb + h0 + t)]);
+        if (g.kind) {
+          w = N.net_w[g.e];
+          fb = N.f_b[g.e];
+        }
+      }
+      unsigned incl = g.items;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned v = __shfl_up_sync(FULL, incl, o);
+        if ((int)t >= o) incl += v;
+      }
+      H.g[t] = g;
+      H.w[t] = w;
+      H.fb[t] = fb;
+      H.incl[t] = incl;
+    }
+    __syncthreads();
+    const unsigned total = H.incl[31];
+    for (unsigned q0 = 0; q0 < total; q0 += blockDim.x) {
+      const unsigned q = q0 + threadIdx.x;
+      int own = 0;
+#pragma unroll
+      for (int step = 16; step > 0; step >>= 1)
+        if (H.incl[own + step - 1] <= q) own += step;
+      own = own < 31 ? own : 31;
+      const NodeArcs og = H.g[own];
+      fn(og, q < total ? q - (H.incl[own] - og.items) : kNoArc, H.w[own], H.fb[own]);
+    }
+    __syncthreads();   // H is rewritten by the next step
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Control: every CTA's thread 0 runs this after each barrier on its own copy
 // of the state, with the counters of the phase that ended.  The decisions
@@ -1358,51 +1506,25 @@ __device__ __forceinline__ void gr_emit2(const NetDev& N, const Sched& L, const 
 }
 
 // Global relabel, one level: reverse BFS over residual arcs of the capped
-// network; newly reached excess nodes become the frontier.  A team per node.
-template <int TW>
-__device__ void gr_team(const NetDev& N, EngineCtl* E, const Sched& L, const Slot& S, int y,
-                        int d1, unsigned lane, Acc& a) {
-  const unsigned tl = lane & (TW - 1);
-  NodeArcs g{0, 0, 0, 0};
-  int w = 0, fb = 0;
-  if (y >= 0) {
-    g = node_arcs(N, y);
-    if (g.kind) {
-      w = N.net_w[g.e];
-      fb = N.f_b[g.e];
-    }
-  }
-  const unsigned steps = warp_max_u((g.items + TW - 1) / TW);
-  for (unsigned c = 0; c < steps; c++) {
-    const unsigned k = c * TW + tl;
-    int c1 = -1, c2 = -1;
-    if (k < g.items) rev_arcs(N, g, k, w, fb, c1, c2, a);
-    gr_emit2(N, L, S, c1, c2, d1, a);
-  }
-}
-
+// network; newly reached excess nodes become the frontier.  Light nodes by
+// level_light, heavy ones by block_walk_heavy.
 __device__ void gr_level(const NetDev& N, EngineCtl* E, const Sched& L, const Team& T,
                          const Slot& S, unsigned lane, Acc& a) {
   const int d1 = L.level + 1;
   const int32_t* bl = N.list[L_BFS];
   const unsigned nlight = L.bfs_end - L.bfs_begin, nheavy = L.bfsh_end - L.bfsh_begin;
-  constexpr unsigned TPW = 32 / kTeam;
-  for (unsigned base = T.gwarp * TPW; base < nlight; base += T.nwarps * TPW) {
-    const unsigned i = base + lane / kTeam;
-    gr_team<kTeam>(N, E, L, S, i < nlight ? bl[L.bfs_begin + i] : -1, d1, lane, a);
-  }
-  for (unsigned h = T.block; h < nheavy; h += T.nblocks) {
-    // heavy node: the whole CTA, blockDim.x arc groups per step
-    const int y = bl[N.NL - 1 - (L.bfsh_begin + h)];
-    const NodeArcs g = node_arcs(N, y);
-    const int w = g.kind ? N.net_w[g.e] : 0, fb = g.kind ? N.f_b[g.e] : 0;
-    for (unsigned k0 = 0; k0 < g.items; k0 += blockDim.x) {
-      const unsigned k = k0 + threadIdx.x;
-      int c1 = -1, c2 = -1;
-      if (k < g.items) rev_arcs(N, g, k, w, fb, c1, c2, a);
-      gr_emit2(N, L, S, c1, c2, d1, a);
-    }
-  }
+  level_light(N, bl + L.bfs_begin, nlight, T, lane,
+              [&](const NodeArcs& g, unsigned k, int w, int fb) {
+                int c1 = -1, c2 = -1;
+                if (k != kNoArc) rev_arcs(N, g, k, w, fb, c1, c2, a);
+                gr_emit2(N, L, S, c1, c2, d1, a);
+              });
+  block_walk_heavy(N, bl, L.bfsh_begin, nheavy, T,
+                   [&](const NodeArcs& g, unsigned k, int w, int fb) {
+                     int c1 = -1, c2 = -1;
+                     if (k != kNoArc) rev_arcs(N, g, k, w, fb, c1, c2, a);
+                     gr_emit2(N, L, S, c1, c2, d1, a);
+                   });
 }
 
 // ---------------------------------------------------------------------------
@@ -1429,6 +1551,7 @@ __device__ void gr_level(const NetDev& N, EngineCtl* E, const Sched& L, const Te
 // now is skipped: the entry queued when the label dropped expands it.  A full
 // queue sets gq_over; the relabel is then redone level by level.
 constexpr unsigned kGqChunk = 16;
+static_assert(kLightItems <= (int)kGqChunk, "a light node is queued as one chunk");
 constexpr unsigned kGqMaxChunks = 1024;
 constexpr unsigned kGqNodeBits = 27;
 
@@ -1725,48 +1848,24 @@ __device__ __forceinline__ void sr_emit2(const NetDev& N, const Sched& L, const 
                 S.c[C_BFS], S.c[C_BFSH], L.bfs_end, L.bfsh_end, N.NL);
 }
 
-template <int TW>
-__device__ void sr_team(const NetDev& N, const Sched& L, const Slot& S, int x, unsigned lane,
-                        Acc& a) {
-  const unsigned tl = lane & (TW - 1);
-  NodeArcs g{0, 0, 0, 0};
-  int w = 0, fb = 0;
-  if (x >= 0) {
-    g = node_arcs(N, x);
-    if (g.kind) {
-      w = N.net_w[g.e];
-      fb = N.f_b[g.e];
-    }
-  }
-  const unsigned steps = warp_max_u((g.items + TW - 1) / TW);
-  for (unsigned c = 0; c < steps; c++) {
-    const unsigned k = c * TW + tl;
-    int c1 = -1, c2 = -1;
-    if (k < g.items) fwd_arcs(N, g, k, w, fb, c1, c2, a);
-    sr_emit2(N, L, S, c1, c2, a);
-  }
-}
-
+// Source-side cut, one level: forward BFS over residual arcs with (u, e_in)
+// uncapped.  Light nodes by level_light, heavy ones by block_walk_heavy.
 __device__ void sr_level(const NetDev& N, const Sched& L, const Team& T, const Slot& S,
                          unsigned lane, Acc& a) {
   const int32_t* bl = N.list[L_BFS];
   const unsigned nlight = L.bfs_end - L.bfs_begin, nheavy = L.bfsh_end - L.bfsh_begin;
-  constexpr unsigned TPW = 32 / kTeam;
-  for (unsigned base = T.gwarp * TPW; base < nlight; base += T.nwarps * TPW) {
-    const unsigned i = base + lane / kTeam;
-    sr_team<kTeam>(N, L, S, i < nlight ? bl[L.bfs_begin + i] : -1, lane, a);
-  }
-  for (unsigned h = T.block; h < nheavy; h += T.nblocks) {
-    const int x = bl[N.NL - 1 - (L.bfsh_begin + h)];
-    const NodeArcs g = node_arcs(N, x);
-    const int w = g.kind ? N.net_w[g.e] : 0, fb = g.kind ? N.f_b[g.e] : 0;
-    for (unsigned k0 = 0; k0 < g.items; k0 += blockDim.x) {
-      const unsigned k = k0 + threadIdx.x;
-      int c1 = -1, c2 = -1;
-      if (k < g.items) fwd_arcs(N, g, k, w, fb, c1, c2, a);
-      sr_emit2(N, L, S, c1, c2, a);
-    }
-  }
+  level_light(N, bl + L.bfs_begin, nlight, T, lane,
+              [&](const NodeArcs& g, unsigned k, int w, int fb) {
+                int c1 = -1, c2 = -1;
+                if (k != kNoArc) fwd_arcs(N, g, k, w, fb, c1, c2, a);
+                sr_emit2(N, L, S, c1, c2, a);
+              });
+  block_walk_heavy(N, bl, L.bfsh_begin, nheavy, T,
+                   [&](const NodeArcs& g, unsigned k, int w, int fb) {
+                     int c1 = -1, c2 = -1;
+                     if (k != kNoArc) fwd_arcs(N, g, k, w, fb, c1, c2, a);
+                     sr_emit2(N, L, S, c1, c2, a);
+                   });
 }
 
 // Distance from the original cut (reading of Section 6 "Region Growing" and

@@ -141,6 +141,7 @@ struct FcJob {
   // group time per engine state (phases run by one CTA count as ST_TAIL)
   unsigned long long st_ns[kStateSlots];
   unsigned st_cnt[kStateSlots];
+  unsigned long long st_lin[kStateSlots], st_hin[kStateSlots];   // light / heavy inputs
 };
 
 // Work queue and per-group barriers of a batched launch.

@@ -126,8 +126,9 @@ __device__ void fc_saturate(const NetDev& N, const Sched& L, const Team& T, cons
   if (sink_acc) atomicAdd(S.flow, sink_acc);
 }
 
-// The marking scans take kMarkUnroll nodes per thread and step, so that the
-// membership loads of a step are in flight together.
+// The marking scans read the membership of four nodes per load (insr bytes
+// as one word, labels as an int4; both arrays are 256-byte aligned) and
+// kMarkUnroll such loads per thread and step, in flight together.
 constexpr int kMarkUnroll = 4;
 
 __device__ __forceinline__ void mark_source(const NetDev& N, int y) {
@@ -139,18 +140,26 @@ __device__ __forceinline__ void mark_source(const NetDev& N, int y) {
 
 // S <- S_r + {u}: sources get label NL and lose their excess.
 __device__ void fc_mark_sources(const NetDev& N, const Team& T, int u) {
-  const int NL = N.NL;
-  for (int base = T.tid; base < NL; base += kMarkUnroll * T.nth) {
-    bool in[kMarkUnroll];
+  const int NL = N.NL, n4 = NL >> 2;
+  const uint32_t* in4 = reinterpret_cast<const uint32_t*>(N.insr);
+  for (int base = (int)T.tid; base < n4; base += kMarkUnroll * (int)T.nth) {
+    uint32_t v[kMarkUnroll];
 #pragma unroll
     for (int j = 0; j < kMarkUnroll; j++) {
-      const int x = base + j * T.nth;
-      in[j] = x < NL && N.insr[x] != 0;
+      const int i = base + j * (int)T.nth;
+      v[j] = i < n4 ? in4[i] : 0u;
     }
 #pragma unroll
-    for (int j = 0; j < kMarkUnroll; j++)
-      if (in[j]) mark_source(N, base + j * T.nth);
+    for (int j = 0; j < kMarkUnroll; j++) {
+      if (!v[j]) continue;
+      const int x0 = 4 * (base + j * (int)T.nth);
+#pragma unroll
+      for (int b = 0; b < 4; b++)
+        if ((v[j] >> (8 * b)) & 0xffu) mark_source(N, x0 + b);
+    }
   }
+  for (int x = 4 * n4 + (int)T.tid; x < NL; x += (int)T.nth)
+    if (N.insr[x]) mark_source(N, x);
   if (T.tid == 0) mark_source(N, u);
 }
 
@@ -167,19 +176,27 @@ __device__ __forceinline__ unsigned long long mark_sink(const NetDev& N, int y) 
 // outside it); the excess of a node that becomes a sink joins the flow
 // (Section 8.4, "Sink-Side Piercing").
 __device__ void fc_mark_sinks(const NetDev& N, const Team& T, const Slot& S, int u) {
-  const int NL = N.NL;
+  const int NL = N.NL, n4 = NL >> 2;
+  const int4* l4 = reinterpret_cast<const int4*>(N.lab0);
   unsigned long long acc = 0;
-  for (int base = T.tid; base < NL; base += kMarkUnroll * T.nth) {
-    bool in[kMarkUnroll];
+  for (int base = (int)T.tid; base < n4; base += kMarkUnroll * (int)T.nth) {
+    int4 v[kMarkUnroll];
 #pragma unroll
     for (int j = 0; j < kMarkUnroll; j++) {
-      const int x = base + j * T.nth;
-      in[j] = x < NL && N.lab0[x] < NL;
+      const int i = base + j * (int)T.nth;
+      v[j] = i < n4 ? l4[i] : make_int4(NL, NL, NL, NL);
     }
 #pragma unroll
-    for (int j = 0; j < kMarkUnroll; j++)
-      if (in[j]) acc += mark_sink(N, base + j * T.nth);
+    for (int j = 0; j < kMarkUnroll; j++) {
+      const int x0 = 4 * (base + j * (int)T.nth);
+      if (v[j].x < NL) acc += mark_sink(N, x0);
+      if (v[j].y < NL) acc += mark_sink(N, x0 + 1);
+      if (v[j].z < NL) acc += mark_sink(N, x0 + 2);
+      if (v[j].w < NL) acc += mark_sink(N, x0 + 3);
+    }
   }
+  for (int x = 4 * n4 + (int)T.tid; x < NL; x += (int)T.nth)
+    if (N.lab0[x] < NL) acc += mark_sink(N, x);
   if (T.tid == 0) acc += mark_sink(N, u);
   if (acc) atomicAdd(S.flow, acc);
 }
@@ -190,24 +207,39 @@ __device__ void fc_mark_sinks(const NetDev& N, const Team& T, const Slot& S, int
 // differ in the hash bits, so the maximum has one holder).  A warp takes 32
 // consecutive nets, one per lane, and walks the concatenated pin lists of the
 // reachable ones 32 pins per step, so a step costs one chain of dependent
-// loads for up to 32 nets.  Every thread of the CTA must call it.
+// loads for up to 32 nets.  A reachable net whose pins all lie in the
+// growing side's reachable set gets its net_done flag: the marking that
+// follows this selection makes all of them terminals, so the net never has
+// a candidate again and later scans skip it.  Every thread of the CTA must
+// call it.
+constexpr unsigned kSelBig = 256;   // pins above which the CTA walks a net
+constexpr int kSelBigCap = 256;     // CTA queue of such nets (more: walked by warps)
+
 __device__ void fc_pierce_select(const NetDev& N, const Team& T, BatchCtl* B, const FcJob& J,
-                                 const FcState& F, long long w_reach, unsigned lane) {
+                                 const FcState& F, long long w_reach, unsigned lane,
+                                 unsigned* walked) {
   __shared__ unsigned long long sk[32];
   __shared__ int sn[32];
+  __shared__ int qbuf[kEngineThreads / 32][64];   // per warp: reachable nets not yet walked
+  __shared__ int bigq[kSelBigCap];                  // per CTA: reachable nets of many pins
+  __shared__ unsigned bign;
+  __shared__ unsigned bincl[32];
+  __shared__ int bout[32];
   const int nh = N.n_nodes, m = N.m_nets, NL = N.NL;
+  if (threadIdx.x == 0) bign = 0;
+  __syncthreads();
+  const unsigned lt = (1u << lane) - 1u;
+  int* qb = qbuf[threadIdx.x >> 5];
   unsigned long long best = 0;
   int bnode = -1;
-  for (unsigned e0 = T.gwarp * 32; e0 < (unsigned)m; e0 += T.nwarps * 32) {
-    const unsigned e = e0 + lane;
+  // Pins of the nets e (one per lane, -1: none), 32 pins per step.
+  auto walk = [&](int e) {
+    const unsigned nw = __popc(__ballot_sync(FULL, e >= 0));
+    if (lane == 0) atomicAdd(walked, nw);
     unsigned beg = 0, sz = 0;
-    if (e < (unsigned)m) {
-      const int node = F.grow_s ? nh + (int)e : nh + m + (int)e;
-      const bool reach = F.grow_s ? N.insr[node] != 0 : N.lab0[node] < NL;
-      if (reach) {
-        beg = N.net_off[e];
-        sz = N.net_off[e + 1] - beg;
-      }
+    if (e >= 0) {
+      beg = N.net_off[e];
+      sz = N.net_off[e + 1] - beg;
     }
     unsigned incl = sz;
 #pragma unroll
@@ -217,6 +249,7 @@ __device__ void fc_pierce_select(const NetDev& N, const Team& T, BatchCtl* B, co
     }
     const unsigned total = __shfl_sync(FULL, incl, 31);
     const unsigned excl = incl - sz;
+    bool outside = false;   // this lane's net has a pin outside the reachable set
     for (unsigned q0 = 0; q0 < total; q0 += 32) {
       const unsigned q = q0 + lane;
       // owner = number of lanes whose inclusive end is <= q
@@ -228,16 +261,128 @@ __device__ void fc_pierce_select(const NetDev& N, const Team& T, BatchCtl* B, co
       }
       own = own < 31 ? own : 31;
       const unsigned ob = __shfl_sync(FULL, beg, own), oe = __shfl_sync(FULL, excl, own);
+      bool out = false;
       if (q < total) {
         const int h = N.pin[ob + (q - oe)];
-        const unsigned long long k = batch_pierce_key(N, h, F.grow_s, J.max_w, w_reach, J.seed);
-        if (k > best) {
-          best = k;
-          bnode = h;
+        out = F.grow_s ? N.insr[h] == 0 : N.lab0[h] >= NL;
+        if (out) {
+          const unsigned long long k = batch_pierce_key(N, h, F.grow_s, J.max_w, w_reach, J.seed);
+          if (k > best) {
+            best = k;
+            bnode = h;
+          }
         }
+      }
+      // this step's lanes [lo, hi) hold pins of this lane's net
+      const unsigned ob_out = __ballot_sync(FULL, out);
+      if (sz && excl < q0 + 32 && incl > q0) {
+        const unsigned lo = excl > q0 ? excl - q0 : 0u;
+        const unsigned hi = incl - q0 < 32u ? incl - q0 : 32u;
+        const unsigned mask = (hi == 32u ? FULL : ((1u << hi) - 1u)) & ~((1u << lo) - 1u);
+        if (ob_out & mask) outside = true;
+      }
+    }
+    if (sz && !outside && N.net_done) N.net_done[e] = 1;
+  };
+  // The reach of 4 batches of 32 nets is loaded at once; the reachable nets
+  // not yet done are queued per warp and walked 32 at a time, so the walks
+  // run with full warps however the reachable nets spread over the ids.
+  // Nets of more than kSelBig pins go to the CTA's queue instead (a warp
+  // would walk a net of thousands of pins alone while the group waits).
+  constexpr int kBatches = 4;
+  unsigned qn = 0;
+  for (unsigned e00 = T.gwarp * 32 * kBatches; e00 < (unsigned)m;
+       e00 += T.nwarps * 32 * kBatches) {
+    bool rch[kBatches];
+#pragma unroll
+    for (int j = 0; j < kBatches; j++) {
+      const unsigned e = e00 + j * 32 + lane;
+      rch[j] = false;
+      if (e < (unsigned)m) {
+        const int node = F.grow_s ? nh + (int)e : nh + m + (int)e;
+        const bool done = N.net_done && N.net_done[e];
+        const bool reach = F.grow_s ? N.insr[node] != 0 : N.lab0[node] < NL;
+        rch[j] = reach && !done;
+      }
+    }
+#pragma unroll 1
+    for (int j = 0; j < kBatches; j++) {
+      if (!__ballot_sync(FULL, rch[j])) continue;
+      const unsigned e = e00 + j * 32 + lane;
+      if (rch[j] && N.net_off[e + 1] - N.net_off[e] > kSelBig) {
+        const unsigned slot = atomicAdd(&bign, 1u);
+        if (slot < (unsigned)kSelBigCap) {
+          bigq[slot] = (int)e;
+          rch[j] = false;
+        }
+      }
+      const unsigned msk = __ballot_sync(FULL, rch[j]);
+      if (rch[j]) qb[qn + __popc(msk & lt)] = (int)e;
+      qn += __popc(msk);
+      __syncwarp();
+      if (qn >= 32) {
+        const int e = qb[lane];
+        const int rest = lane + 32 < qn ? qb[lane + 32] : -1;
+        __syncwarp();
+        if (lane + 32 < qn) qb[lane] = rest;
+        qn -= 32;
+        __syncwarp();
+        walk(e);
       }
     }
   }
+  if (qn) walk(lane < qn ? qb[lane] : -1);
+  // the CTA's nets of many pins, up to 32 per step: the CTA walks their
+  // concatenated pin lists blockDim.x pins at a time
+  __syncthreads();
+  const unsigned nbig = min(bign, (unsigned)kSelBigCap);
+  for (unsigned b0 = 0; b0 < nbig; b0 += 32) {
+    if (threadIdx.x < 32) {
+      const unsigned t = threadIdx.x;
+      unsigned sz = 0;
+      if (b0 + t < nbig) {
+        const int e = bigq[b0 + t];
+        sz = N.net_off[e + 1] - N.net_off[e];
+      }
+      unsigned incl = sz;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned v = __shfl_up_sync(FULL, incl, o);
+        if ((int)t >= o) incl += v;
+      }
+      bincl[t] = incl;
+      bout[t] = 0;
+    }
+    __syncthreads();
+    const unsigned total = bincl[31];
+    for (unsigned q0 = 0; q0 < total; q0 += blockDim.x) {
+      const unsigned q = q0 + threadIdx.x;
+      if (q < total) {
+        int own = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1)
+          if (bincl[own + step - 1] <= q) own += step;
+        own = own < 31 ? own : 31;
+        const int e = bigq[b0 + own];
+        const unsigned first = own ? bincl[own - 1] : 0u;
+        const int h = N.pin[N.net_off[e] + (q - first)];
+        const bool out = F.grow_s ? N.insr[h] == 0 : N.lab0[h] >= NL;
+        if (out) {
+          bout[own] = 1;
+          const unsigned long long k = batch_pierce_key(N, h, F.grow_s, J.max_w, w_reach, J.seed);
+          if (k > best) {
+            best = k;
+            bnode = h;
+          }
+        }
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x < 32 && b0 + threadIdx.x < nbig && !bout[threadIdx.x] && N.net_done)
+      N.net_done[bigq[b0 + threadIdx.x]] = 1;
+    __syncthreads();   // bincl and bout are rewritten by the next step
+  }
+  if (threadIdx.x == 0 && nbig) atomicAdd(walked, nbig);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     const unsigned long long tk = __shfl_xor_sync(FULL, best, o);
@@ -567,7 +712,9 @@ __device__ void run_phase_batch(const NetDev& N, EngineCtl* E, BatchCtl* B, cons
   const Slot S = slot_of(E, L.phase);
   switch (L.state) {
     case ST_FC_SAT: fc_saturate(N, L, T, S, F.node, lane); break;
-    case ST_FC_SEL: fc_pierce_select(N, T, B, J, F, F.grow_s ? L.wS : L.wT, lane); break;
+    case ST_FC_SEL:
+      fc_pierce_select(N, T, B, J, F, F.grow_s ? L.wS : L.wT, lane, S.c[C_RELAB]);
+      break;
     case ST_FC_MARK_S: fc_mark_sources(N, T, F.node); break;
     case ST_FC_MARK_T: fc_mark_sinks(N, T, S, F.node); break;
     default: run_phase(N, E, L, T, lane, a, w_sh, P); break;
@@ -579,13 +726,40 @@ struct BatchClock {
   unsigned long long t;
   unsigned long long ns[kStateSlots];
   unsigned cnt[kStateSlots];
+  unsigned long long lin[kStateSlots], hin[kStateSlots];   // light / heavy input nodes
 };
 
-__device__ __forceinline__ void batch_tick(BatchClock& bc, int st) {
+// Input of a phase of state st: the frontier (rounds), the next list (apply
+// and relabel) or the breadth-first-search level (light, heavy).
+__device__ __forceinline__ void phase_input(const Sched& L, int st, unsigned long long& li,
+                                            unsigned long long& hi) {
+  if (st == ST_ROUND_A || st == ST_ROUND || st == ST_FLUSH) {
+    li = L.fcnt;
+    hi = L.fcnth;
+  } else if (st == ST_ROUND_B) {
+    li = L.ncnt;
+    hi = L.ncnth;
+  } else if (st == ST_GR_LEVEL || st == ST_SR_LEVEL || st == ST_DIST_LEVEL) {
+    li = L.bfs_end - L.bfs_begin;
+    hi = L.bfsh_end - L.bfsh_begin;
+  } else {
+    li = hi = 0;
+  }
+}
+
+// `walked`: nets whose pins a selection phase walked (counted as its light
+// input).
+__device__ __forceinline__ void batch_tick(BatchClock& bc, int st, const Sched& L,
+                                           unsigned walked) {
   const unsigned long long t = globaltimer();
+  unsigned long long li, hi;
+  phase_input(L, st, li, hi);
+  if (st == ST_FC_SEL) li = walked;
   st = st < kStateSlots ? st : kStateSlots - 1;
   bc.ns[st] += t - bc.t;
   bc.cnt[st]++;
+  bc.lin[st] += li;
+  bc.hin[st] += hi;
   bc.t = t;
 }
 
@@ -610,6 +784,8 @@ __device__ void fc_run_job(FcJob* job, const Params& P0, int rank, int G, unsign
       for (int k = 0; k < kStateSlots; k++) {
         bc.ns[k] = 0;
         bc.cnt[k] = 0;
+        bc.lin[k] = 0;
+        bc.hin[k] = 0;
       }
       bc.t = t_start;
     }
@@ -637,7 +813,7 @@ __device__ void fc_run_job(FcJob* job, const Params& P0, int rank, int G, unsign
       }
       const bool ok = job_barrier(E, ctr, cseq, bar_seq, G, P.timeout_ns);
       if (threadIdx.x == 0) {
-        if (lead) batch_tick(bc, ST_TAIL);
+        if (lead) batch_tick(bc, ST_TAIL, L, 0);
         if (!lead) load_sched(L, E);
         if (!ok) L.state = ST_DONE;
         if (L.state == ST_DONE && !F.finished) fc_on_done(L, F, *job, &E->c);
@@ -656,12 +832,13 @@ __device__ void fc_run_job(FcJob* job, const Params& P0, int rank, int G, unsign
     if (st == ST_FC_SEL && threadIdx.x < 32)
       fc_select_reduce(B, blockIdx.x - (unsigned)rank, G, lane, sel_key, sel_node);
     if (threadIdx.x == 0) {
-      if (lead) batch_tick(bc, st);
       if (!ok) {
+        if (lead) batch_tick(bc, st, L, 0);
         L.state = ST_DONE;
         fc_on_done(L, F, *job, &E->c);
       } else {
         Snap q = take_snap(E, L.phase);
+        if (lead) batch_tick(bc, st, L, st == ST_FC_SEL ? q.c[C_RELAB] : 0u);
         if (st == ST_FC_SEL) {
           q.key = sel_key;
           q.node = sel_node;
@@ -701,6 +878,8 @@ __device__ void fc_run_job(FcJob* job, const Params& P0, int rank, int G, unsign
     for (int k = 0; k < kStateSlots; k++) {
       job->st_ns[k] = bc.ns[k];
       job->st_cnt[k] = bc.cnt[k];
+      job->st_lin[k] = bc.lin[k];
+      job->st_hin[k] = bc.hin[k];
     }
   }
 }

@@ -69,6 +69,8 @@ struct hfp_ctx {
   // group time per engine state of the batched launches since the last reset
   uint64_t batch_ns[hfp::kStateSlots] = {};
   uint64_t batch_cnt[hfp::kStateSlots] = {};
+  uint64_t batch_lin[hfp::kStateSlots] = {};
+  uint64_t batch_hin[hfp::kStateSlots] = {};
 };
 
 struct hfp_net {
@@ -98,6 +100,7 @@ struct hfp_net {
   void* trace_buf = nullptr;
   void* gq_buf = nullptr;          // work queue of queue-driven global relabels
   void* delta1_buf = nullptr;      // second delta buffer of one-phase rounds
+  void* net_done_buf = nullptr;    // nets the batched piercing scans skip
   uint64_t launches = 0;
   uint64_t engine_ns = 0;
 };

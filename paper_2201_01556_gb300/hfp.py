@@ -164,7 +164,7 @@ def load():
         "hfp_net_get_trace": (i32, [P, P, P, P, i32, P]),
         "hfp_pair_features": (i32, [P, P, i32, i32, P, P, P, i32, P]),
         "hfp_flowcutter_batch": (i32, [P, P, i32, i32]),
-        "hfp_ctx_batch_profile": (i32, [P, P, P, i32, i32]),
+        "hfp_ctx_batch_profile": (i32, [P, P, P, P, P, i32, i32]),
         "hfp_refine_round_batched": (i32, [P, P, i32, ctypes.POINTER(RefineParams), P,
                                            ctypes.c_float, i32, ctypes.POINTER(RoundStats), P,
                                            i32, P, P]),
@@ -374,17 +374,17 @@ ENGINE_STATES = ("done", "push", "relabel", "gr_init", "gr_level", "sr_init", "s
 
 
 def ctx_batch_profile(ctx: Context, reset: bool = True) -> dict:
-    """hfp_ctx_batch_profile -> {state: (device ns, phases)} of the batched
-    launches since the last reset, summed over their networks (states with
-    no phase are left out)."""
-    ns = np.zeros(24, np.uint64)
-    cnt = np.zeros(24, np.uint64)
-    _check(load().hfp_ctx_batch_profile(ctx.h, _ptr(ns), _ptr(cnt), 24, 1 if reset else 0))
+    """hfp_ctx_batch_profile -> {state: (device ns, phases, light input
+    nodes, heavy input nodes)} of the batched launches since the last reset,
+    summed over their networks (states with no phase are left out)."""
+    ns, cnt, li, hi = (np.zeros(24, np.uint64) for _ in range(4))
+    _check(load().hfp_ctx_batch_profile(ctx.h, _ptr(ns), _ptr(cnt), _ptr(li), _ptr(hi), 24,
+                                        1 if reset else 0))
     out = {}
     for i in range(24):
         if cnt[i]:
             name = ENGINE_STATES[i] if i < len(ENGINE_STATES) else f"state{i}"
-            out[name] = (int(ns[i]), int(cnt[i]))
+            out[name] = (int(ns[i]), int(cnt[i]), int(li[i]), int(hi[i]))
     return out
 
 

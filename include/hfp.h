@@ -462,7 +462,8 @@ hfp_status hfp_connectivity(hfp_hgraph* hg, const int32_t* part, int32_t k, int6
  * (vertex, from, to) in ascending vertex order (host buffer of 3 * cap
  * int32) and Delta_exp = original cut - final flow.  A FlowCutter that finds
  * no balanced cut or exceeds the bound gives res->status != HFP_OK and no
- * moves; the call itself still returns HFP_OK. */
+ * moves; the call itself still returns HFP_OK.  k <= 64 (block masks of the
+ * nets), else HFP_ERR_INVALID. */
 hfp_status hfp_refine_block_pair(hfp_hgraph* hg, const int32_t* part, int32_t k, int32_t bi,
                                  int32_t bj, const hfp_refine_params* params, int32_t* moves,
                                  int32_t cap, hfp_pair_result* res);

@@ -281,10 +281,12 @@ HFP_API void hfp_net_destroy(hfp_net* net) {
   ctx_release(c);
 }
 
-HFP_API hfp_status hfp_build_flow_network(hfp_ctx* ctx, const hfp_hypergraph* H, hfp_mem mem,
-                                          const int32_t* region, int32_t n_region,
-                                          const int32_t* side, const int32_t* dist_from_cut,
-                                          hfp_net** out) {
+namespace hfp {
+
+hfp_status build_network_impl(hfp_ctx* ctx, const hfp_hypergraph* H, hfp_mem mem,
+                              const int32_t* region, int32_t n_region, const int32_t* side,
+                              const int32_t* dist_from_cut, const int32_t* nets, int32_t n_nets,
+                              const int32_t* verts, int32_t n_verts, hfp_net** out) {
   if (!out) return fail(HFP_ERR_INVALID, "out is NULL");
   *out = nullptr;
   if (!ctx || !H) return fail(HFP_ERR_INVALID, "ctx or H is NULL");
@@ -295,10 +297,14 @@ HFP_API hfp_status hfp_build_flow_network(hfp_ctx* ctx, const hfp_hypergraph* H,
       (n_region > 0 && !region))
     return fail(HFP_ERR_INVALID, "missing input array");
   if (mem != HFP_MEM_HOST && mem != HFP_MEM_DEVICE) return fail(HFP_ERR_INVALID, "bad mem");
+  if ((nets || verts) && (mem != HFP_MEM_DEVICE || n_nets < 0 || n_verts < 0))
+    return fail(HFP_ERR_INVALID, "net / vertex lists need device inputs");
   hfp_status s = set_device(ctx);
   if (s != HFP_OK) return s;
   cudaStream_t st = ctx->stream;
   const int sms = ctx->sms;
+  // nets scanned (and per-net scratch entries): the list, or all of H
+  const int32_t M = nets ? n_nets : m;
 
   // total pins of H
   uint32_t P = 0;
@@ -357,7 +363,7 @@ HFP_API hfp_status hfp_build_flow_network(hfp_ctx* ctx, const hfp_hypergraph* H,
   const int32_t n_nodes = n_region + 2;
   DevBuf loc, keep, size, has_s, has_t, net_pos, pin_pos, s_pos, t_pos, totals, wsum, err,
       dist_tmp, scan_scr;
-  const size_t mm = (size_t)(m > 0 ? m : 1);
+  const size_t mm = (size_t)(M > 0 ? M : 1);
   CK(loc.alloc(sizeof(int32_t) * (n > 0 ? n : 1), st));
   CK(keep.alloc(sizeof(unsigned) * mm, st));
   CK(size.alloc(sizeof(unsigned) * mm, st));
@@ -371,7 +377,7 @@ HFP_API hfp_status hfp_build_flow_network(hfp_ctx* ctx, const hfp_hypergraph* H,
   CK(wsum.alloc(sizeof(unsigned long long) * 8, st));
   CK(err.alloc(sizeof(int), st));
   CK(dist_tmp.alloc(sizeof(int32_t) * (n_region > 0 ? n_region : 1), st));
-  size_t scan_words = scan_scratch_words((unsigned)(m > n_nodes + 1 ? m : n_nodes + 1)) + 8;
+  size_t scan_words = scan_scratch_words((unsigned)(M > n_nodes + 1 ? M : n_nodes + 1)) + 8;
   CK(scan_scr.alloc(sizeof(unsigned) * scan_words, st));
   if (n) CK(cudaMemsetAsync(loc.p, 0xFF, sizeof(int32_t) * n, st));
   CK(cudaMemsetAsync(totals.p, 0, sizeof(unsigned) * 8, st));
@@ -391,22 +397,22 @@ HFP_API hfp_status hfp_build_flow_network(hfp_ctx* ctx, const hfp_hypergraph* H,
   unsigned* tot = totals.as<unsigned>();
   launch_region_map(n, n_region, d_region, d_side, d_nodew, loc.as<int32_t>(), a_gid, a_w, a_orig,
                     err.as<int>(), st);
-  launch_st_weight(n, loc.as<int32_t>(), d_side, d_nodew, wsum.as<unsigned long long>(),
-                   err.as<int>(), sms, st);
-  launch_net_scan(n, m, d_off, d_pins, d_netw, d_side, loc.as<int32_t>(), keep.as<unsigned>(),
-                  size.as<unsigned>(), has_s.as<unsigned>(), has_t.as<unsigned>(),
-                  dist_tmp.as<int32_t>(), d_dist ? 0 : 1, wsum.as<unsigned long long>() + 3,
-                  err.as<int>(), sms, st);
-  if (m) {
-    CK(cudaMemcpyAsync(net_pos.p, keep.p, sizeof(unsigned) * m, cudaMemcpyDeviceToDevice, st));
-    CK(cudaMemcpyAsync(pin_pos.p, size.p, sizeof(unsigned) * m, cudaMemcpyDeviceToDevice, st));
-    CK(cudaMemcpyAsync(s_pos.p, has_s.p, sizeof(unsigned) * m, cudaMemcpyDeviceToDevice, st));
-    CK(cudaMemcpyAsync(t_pos.p, has_t.p, sizeof(unsigned) * m, cudaMemcpyDeviceToDevice, st));
+  launch_st_weight(verts ? n_verts : n, verts, loc.as<int32_t>(), d_side, d_nodew,
+                   wsum.as<unsigned long long>(), err.as<int>(), sms, st);
+  launch_net_scan(n, M, nets, d_off, d_pins, d_netw, d_side, loc.as<int32_t>(),
+                  keep.as<unsigned>(), size.as<unsigned>(), has_s.as<unsigned>(),
+                  has_t.as<unsigned>(), dist_tmp.as<int32_t>(), d_dist ? 0 : 1,
+                  wsum.as<unsigned long long>() + 3, err.as<int>(), sms, st);
+  if (M) {
+    CK(cudaMemcpyAsync(net_pos.p, keep.p, sizeof(unsigned) * M, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(pin_pos.p, size.p, sizeof(unsigned) * M, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(s_pos.p, has_s.p, sizeof(unsigned) * M, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(t_pos.p, has_t.p, sizeof(unsigned) * M, cudaMemcpyDeviceToDevice, st));
   }
-  scan_exclusive(net_pos.as<unsigned>(), m, scan_scr.as<unsigned>(), tot + 0, st);
-  scan_exclusive(pin_pos.as<unsigned>(), m, scan_scr.as<unsigned>(), tot + 1, st);
-  scan_exclusive(s_pos.as<unsigned>(), m, scan_scr.as<unsigned>(), tot + 2, st);
-  scan_exclusive(t_pos.as<unsigned>(), m, scan_scr.as<unsigned>(), tot + 3, st);
+  scan_exclusive(net_pos.as<unsigned>(), M, scan_scr.as<unsigned>(), tot + 0, st);
+  scan_exclusive(pin_pos.as<unsigned>(), M, scan_scr.as<unsigned>(), tot + 1, st);
+  scan_exclusive(s_pos.as<unsigned>(), M, scan_scr.as<unsigned>(), tot + 2, st);
+  scan_exclusive(t_pos.as<unsigned>(), M, scan_scr.as<unsigned>(), tot + 3, st);
 
   struct Head {
     unsigned totals[8];
@@ -515,7 +521,7 @@ HFP_API hfp_status hfp_build_flow_network(hfp_ctx* ctx, const hfp_hypergraph* H,
   CKN(cudaMemsetAsync(D.flags, 0, NL, st));
   launch_st_attrs(node_gid, node_w, node_orig, wsum.as<unsigned long long>(), D.flags,
                   err.as<int>(), st);
-  launch_net_fill(m, d_off, d_pins, d_netw, loc.as<int32_t>(), keep.as<unsigned>(),
+  launch_net_fill(M, nets, d_off, d_pins, d_netw, loc.as<int32_t>(), keep.as<unsigned>(),
                   net_pos.as<unsigned>(), pin_pos.as<unsigned>(), s_pos.as<unsigned>(),
                   t_pos.as<unsigned>(), has_s.as<unsigned>(), has_t.as<unsigned>(), tot,
                   nnet_off, npin, nnet_w, net->net_gid, inc, sms, st);
@@ -640,6 +646,16 @@ HFP_API hfp_status hfp_build_flow_network(hfp_ctx* ctx, const hfp_hypergraph* H,
   *out = net;
   return done(rs);
 #undef CKN
+}
+
+}  // namespace hfp
+
+HFP_API hfp_status hfp_build_flow_network(hfp_ctx* ctx, const hfp_hypergraph* H, hfp_mem mem,
+                                          const int32_t* region, int32_t n_region,
+                                          const int32_t* side, const int32_t* dist_from_cut,
+                                          hfp_net** out) {
+  return build_network_impl(ctx, H, mem, region, n_region, side, dist_from_cut, nullptr, 0,
+                            nullptr, 0, out);
 }
 
 HFP_API hfp_status hfp_net_get_info(hfp_net* net, hfp_net_info* info) {

@@ -131,14 +131,18 @@ __global__ void k_region_map(int32_t n, int32_t n_region, const int32_t* region,
 }
 
 // contracted weights of s and t, and the total weight check
-__global__ void k_st_weight(int32_t n, const int32_t* loc, const int32_t* side,
-                            const int32_t* node_w_h, unsigned long long* wsum, int* err) {
+// verts (may be null): the vertices to scan (every vertex of side 0 or 1 must
+// be among them); n is their count then, else all n vertices are scanned.
+__global__ void k_st_weight(int32_t n, const int32_t* verts, const int32_t* loc,
+                            const int32_t* side, const int32_t* node_w_h,
+                            unsigned long long* wsum, int* err) {
   // wsum: [0] s, [1] t, [2] all of H, [3] nets (k_net_scan), [4] region
   __shared__ unsigned long long sh[5];
   if (threadIdx.x < 5) sh[threadIdx.x] = 0;
   __syncthreads();
   unsigned long long a0 = 0, a1 = 0, at = 0, ar = 0;
-  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int v = verts ? verts[i] : i;
     int c = node_w_h ? node_w_h[v] : 1;
     if (c <= 0) set_err(err, kDevBadInput);
     unsigned long long cc = (unsigned long long)(c > 0 ? c : 0);
@@ -161,15 +165,20 @@ __global__ void k_st_weight(int32_t n, const int32_t* loc, const int32_t* side,
 }
 
 // pass 1, warp per net of H
-__global__ void k_net_scan(int32_t n, int32_t m, const uint32_t* net_off, const int32_t* pins,
-                           const int32_t* net_w, const int32_t* side, const int32_t* loc,
-                           unsigned* keep, unsigned* size, unsigned* has_s, unsigned* has_t,
-                           int32_t* dist_tmp, int mark_dist, unsigned long long* wnet, int* err) {
+// nets (may be null): the nets to scan, ascending (every net with a region
+// pin must be among them); m is their count then.  Per-net outputs are
+// indexed by the position in that list (by the net id without one).
+__global__ void k_net_scan(int32_t n, int32_t m, const int32_t* nets, const uint32_t* net_off,
+                           const int32_t* pins, const int32_t* net_w, const int32_t* side,
+                           const int32_t* loc, unsigned* keep, unsigned* size, unsigned* has_s,
+                           unsigned* has_t, int32_t* dist_tmp, int mark_dist,
+                           unsigned long long* wnet, int* err) {
   const unsigned lane = threadIdx.x & 31;
   const unsigned gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const unsigned nw = (gridDim.x * blockDim.x) >> 5;
   unsigned long long wacc = 0;
-  for (unsigned e = gw; e < (unsigned)m; e += nw) {
+  for (unsigned i = gw; i < (unsigned)m; i += nw) {
+    const unsigned e = nets ? (unsigned)nets[i] : i;
     const unsigned beg = net_off[e], end = net_off[e + 1];
     if (end < beg) { set_err(err, kDevBadInput); continue; }
     unsigned cnt = 0;
@@ -202,10 +211,10 @@ __global__ void k_net_scan(int32_t n, int32_t m, const uint32_t* net_off, const 
       int w = net_w[e];
       if (w <= 0) set_err(err, kDevBadInput);
       wacc += (unsigned long long)(w > 0 ? w : 0);
-      keep[e] = k;
-      size[e] = k ? tot : 0;
-      has_s[e] = k && hs;
-      has_t[e] = k && ht;
+      keep[i] = k;
+      size[i] = k ? tot : 0;
+      has_s[i] = k && hs;
+      has_t[i] = k && ht;
     }
     if (mark_dist && s0 && s1) {
       // region pins of a net with pins on both sides: distance 1
@@ -222,8 +231,9 @@ __global__ void k_net_scan(int32_t n, int32_t m, const uint32_t* net_off, const 
 }
 
 // pass 2, warp per net of H that is kept
-__global__ void k_net_fill(int32_t m, const uint32_t* net_off, const int32_t* pins,
-                           const int32_t* net_w, const int32_t* loc, const unsigned* keep,
+__global__ void k_net_fill(int32_t m, const int32_t* nets, const uint32_t* net_off,
+                           const int32_t* pins, const int32_t* net_w, const int32_t* loc,
+                           const unsigned* keep,
                            const unsigned* net_pos, const unsigned* pin_pos,
                            const unsigned* s_pos, const unsigned* t_pos,
                            const unsigned* has_s_flag, const unsigned* has_t_flag,
@@ -233,11 +243,12 @@ __global__ void k_net_fill(int32_t m, const uint32_t* net_off, const int32_t* pi
   const unsigned gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const unsigned nw = (gridDim.x * blockDim.x) >> 5;
   const unsigned deg_s = totals[2];
-  for (unsigned e = gw; e < (unsigned)m; e += nw) {
-    if (!keep[e]) continue;
+  for (unsigned i = gw; i < (unsigned)m; i += nw) {
+    if (!keep[i]) continue;
+    const unsigned e = nets ? (unsigned)nets[i] : i;
     const unsigned beg = net_off[e], end = net_off[e + 1];
-    const unsigned ep = net_pos[e];
-    unsigned out = pin_pos[e];
+    const unsigned ep = net_pos[i];
+    unsigned out = pin_pos[i];
     if (lane == 0) {
       nnet_off[ep] = out;
       nnet_w[ep] = net_w[e];
@@ -252,14 +263,14 @@ __global__ void k_net_fill(int32_t m, const uint32_t* net_off, const int32_t* pi
       out += __popc(mask);
     }
     if (lane == 0) {
-      if (has_s_flag[e]) {
+      if (has_s_flag[i]) {
         npin[out] = 0;
-        inc[s_pos[e]] = make_int2((int)ep, (int)out);
+        inc[s_pos[i]] = make_int2((int)ep, (int)out);
         out++;
       }
-      if (has_t_flag[e]) {
+      if (has_t_flag[i]) {
         npin[out] = 1;
-        inc[deg_s + t_pos[e]] = make_int2((int)ep, (int)out);
+        inc[deg_s + t_pos[i]] = make_int2((int)ep, (int)out);
         out++;
       }
     }
@@ -400,35 +411,38 @@ void launch_region_map(int32_t n, int32_t n_region, const int32_t* region, const
   }
 }
 
-void launch_st_weight(int32_t n, const int32_t* loc, const int32_t* side, const int32_t* node_w_h,
-                      unsigned long long* wsum, int* err, int sms, cudaStream_t st) {
-  k_st_weight<<<blocks_for(n, 256, sms * 8), 256, 0, st>>>(n, loc, side, node_w_h, wsum, err);
+void launch_st_weight(int32_t n, const int32_t* verts, const int32_t* loc, const int32_t* side,
+                      const int32_t* node_w_h, unsigned long long* wsum, int* err, int sms,
+                      cudaStream_t st) {
+  k_st_weight<<<blocks_for(n, 256, sms * 8), 256, 0, st>>>(n, verts, loc, side, node_w_h, wsum,
+                                                            err);
   count_launches(1);
 }
 
-void launch_net_scan(int32_t n, int32_t m, const uint32_t* net_off, const int32_t* pins,
-                     const int32_t* net_w, const int32_t* side, const int32_t* loc,
-                     unsigned* keep, unsigned* size, unsigned* has_s, unsigned* has_t,
-                     int32_t* dist_tmp, int mark_dist, unsigned long long* wnet, int* err,
-                     int sms, cudaStream_t st) {
+void launch_net_scan(int32_t n, int32_t m, const int32_t* nets, const uint32_t* net_off,
+                     const int32_t* pins, const int32_t* net_w, const int32_t* side,
+                     const int32_t* loc, unsigned* keep, unsigned* size, unsigned* has_s,
+                     unsigned* has_t, int32_t* dist_tmp, int mark_dist, unsigned long long* wnet,
+                     int* err, int sms, cudaStream_t st) {
   if (m > 0) {
     k_net_scan<<<blocks_for((unsigned long long)m * 32, 256, sms * 16), 256, 0, st>>>(
-        n, m, net_off, pins, net_w, side, loc, keep, size, has_s, has_t, dist_tmp, mark_dist,
-        wnet, err);
+        n, m, nets, net_off, pins, net_w, side, loc, keep, size, has_s, has_t, dist_tmp,
+        mark_dist, wnet, err);
     count_launches(1);
   }
 }
 
-void launch_net_fill(int32_t m, const uint32_t* net_off, const int32_t* pins,
-                     const int32_t* net_w, const int32_t* loc, const unsigned* keep,
+void launch_net_fill(int32_t m, const int32_t* nets, const uint32_t* net_off,
+                     const int32_t* pins, const int32_t* net_w, const int32_t* loc,
+                     const unsigned* keep,
                      const unsigned* net_pos, const unsigned* pin_pos, const unsigned* s_pos,
                      const unsigned* t_pos, const unsigned* has_s, const unsigned* has_t,
                      const unsigned* totals, uint32_t* nnet_off, int32_t* npin, int32_t* nnet_w,
                      int32_t* nnet_gid, int2* inc, int sms, cudaStream_t st) {
   if (m > 0) {
     k_net_fill<<<blocks_for((unsigned long long)m * 32, 256, sms * 16), 256, 0, st>>>(
-        m, net_off, pins, net_w, loc, keep, net_pos, pin_pos, s_pos, t_pos, has_s, has_t, totals,
-        nnet_off, npin, nnet_w, nnet_gid, inc);
+        m, nets, net_off, pins, net_w, loc, keep, net_pos, pin_pos, s_pos, t_pos, has_s, has_t,
+        totals, nnet_off, npin, nnet_w, nnet_gid, inc);
     count_launches(1);
   }
 }

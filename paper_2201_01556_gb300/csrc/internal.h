@@ -135,6 +135,15 @@ struct BatchItem {
   int32_t group_ctas = 0;          // CTAs of the group that solved it
 };
 
+// hfp_build_flow_network with optional restrictions (device inputs only):
+// nets[n_nets] (ascending) holds every net of H with a pin in the region, and
+// verts[n_verts] every vertex whose side is 0 or 1; only those are scanned.
+// Null lists scan all of H.
+hfp_status build_network_impl(hfp_ctx* ctx, const hfp_hypergraph* H, hfp_mem mem,
+                              const int32_t* region, int32_t n_region, const int32_t* side,
+                              const int32_t* dist_from_cut, const int32_t* nets, int32_t n_nets,
+                              const int32_t* verts, int32_t n_verts, hfp_net** out);
+
 // Allocates the buffers of one-phase rounds (P.fused_rounds) and queue-driven
 // global relabels (P.async_gr) that the network does not have yet (api.cu).
 hfp_status ensure_engine_buffers(hfp_net* net, const Params& P);

@@ -16,15 +16,19 @@ void scan_exclusive(unsigned* a, unsigned n, unsigned* scratch, unsigned* total,
 void launch_region_map(int32_t n, int32_t n_region, const int32_t* region, const int32_t* side,
                        const int32_t* node_w_h, int32_t* loc, int32_t* node_gid, int32_t* node_w,
                        int8_t* node_orig, int* err, cudaStream_t st);
-void launch_st_weight(int32_t n, const int32_t* loc, const int32_t* side, const int32_t* node_w_h,
-                      unsigned long long* wsum, int* err, int sms, cudaStream_t st);
-void launch_net_scan(int32_t n, int32_t m, const uint32_t* net_off, const int32_t* pins,
-                     const int32_t* net_w, const int32_t* side, const int32_t* loc,
-                     unsigned* keep, unsigned* size, unsigned* has_s, unsigned* has_t,
-                     int32_t* dist_tmp, int mark_dist, unsigned long long* wnet, int* err,
-                     int sms, cudaStream_t st);
-void launch_net_fill(int32_t m, const uint32_t* net_off, const int32_t* pins,
-                     const int32_t* net_w, const int32_t* loc, const unsigned* keep,
+// verts / nets (may be null): the vertices / ascending nets to scan (n / m
+// is then their count); per-net outputs are indexed by list position
+void launch_st_weight(int32_t n, const int32_t* verts, const int32_t* loc, const int32_t* side,
+                      const int32_t* node_w_h, unsigned long long* wsum, int* err, int sms,
+                      cudaStream_t st);
+void launch_net_scan(int32_t n, int32_t m, const int32_t* nets, const uint32_t* net_off,
+                     const int32_t* pins, const int32_t* net_w, const int32_t* side,
+                     const int32_t* loc, unsigned* keep, unsigned* size, unsigned* has_s,
+                     unsigned* has_t, int32_t* dist_tmp, int mark_dist, unsigned long long* wnet,
+                     int* err, int sms, cudaStream_t st);
+void launch_net_fill(int32_t m, const int32_t* nets, const uint32_t* net_off,
+                     const int32_t* pins, const int32_t* net_w, const int32_t* loc,
+                     const unsigned* keep,
                      const unsigned* net_pos, const unsigned* pin_pos, const unsigned* s_pos,
                      const unsigned* t_pos, const unsigned* has_s, const unsigned* has_t,
                      const unsigned* totals, uint32_t* nnet_off, int32_t* npin, int32_t* nnet_w,

@@ -88,59 +88,6 @@ __global__ void k_unit_weights(int32_t n, int32_t* w) {
 
 // ---------------------------------------------------------------------------
 // pair region
-__global__ void k_side(int32_t n, const int32_t* part, int32_t bi, int32_t bj,
-                       const int32_t* node_w, int32_t* side, int32_t* lev,
-                       unsigned long long* wsum) {
-  unsigned long long a = 0, b = 0;
-  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
-    const int p = part[v];
-    const int s = p == bi ? 0 : (p == bj ? 1 : -1);
-    side[v] = s;
-    lev[v] = 0;
-    if (s == 0) a += node_w[v];
-    if (s == 1) b += node_w[v];
-  }
-  if (a) atomicAdd(&wsum[0], a);
-  if (b) atomicAdd(&wsum[1], b);
-}
-
-// warp per net: region pins of nets with pins on both sides get level 1
-__global__ void k_level1(int32_t m, const uint32_t* net_off, const int32_t* pins,
-                         const int32_t* side, int32_t* lev) {
-  const unsigned lane = threadIdx.x & 31;
-  const unsigned gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const unsigned nw = (gridDim.x * blockDim.x) >> 5;
-  for (unsigned e = gw; e < (unsigned)m; e += nw) {
-    const unsigned beg = net_off[e], end = net_off[e + 1];
-    bool a = false, b = false;
-    for (unsigned j0 = beg; j0 < end; j0 += 32) {
-      const unsigned j = j0 + lane;
-      const int s = j < end ? side[pins[j]] : -1;
-      a |= __any_sync(0xffffffffu, s == 0);
-      b |= __any_sync(0xffffffffu, s == 1);
-    }
-    if (!(a && b)) continue;
-    for (unsigned j = beg + lane; j < end; j += 32) {
-      const int v = pins[j];
-      if (side[v] >= 0) lev[v] = 1;
-    }
-  }
-}
-
-__global__ void k_flag(int32_t n, const int32_t* side, const int32_t* lev, int s, int d,
-                       unsigned* flag) {
-  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
-    flag[v] = (side[v] == s && lev[v] == d) ? 1u : 0u;
-}
-
-__global__ void k_scatter(int32_t n, const unsigned* flag, const unsigned* pos, int32_t* out,
-                          const int32_t* node_w, unsigned* wout) {
-  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
-    if (flag[v]) {
-      out[pos[v]] = v;
-      if (wout) wout[pos[v]] = (unsigned)node_w[v];
-    }
-}
 
 // candidates in ascending order with exclusive weight prefix wpre: the first
 // ones whose inclusive prefix fits in the budget are taken
@@ -174,11 +121,6 @@ __global__ void k_next_level(unsigned cnt, const int32_t* cand, const uint32_t* 
       }
     }
   }
-}
-
-__global__ void k_inb_flag(int32_t n, const uint8_t* in_b, unsigned* flag) {
-  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
-    flag[v] = in_b[v];
 }
 
 __global__ void k_region_dist(unsigned cnt, const int32_t* region, const int32_t* lev,
@@ -229,6 +171,168 @@ __global__ void k_move_fill(unsigned cnt, const int32_t* region, const uint8_t* 
       moves[3 * q + 1] = fin[i] ? bi : bj;
       moves[3 * q + 2] = fin[i] ? bj : bi;
     }
+}
+
+// ---------------------------------------------------------------------------
+// block lists: the vertices and the nets of every block, ascending, so that
+// the preparation of a pair works on its two blocks only
+
+// block mask of every net (k <= 64), a warp per net
+__global__ void k_net_mask(int32_t m, const uint32_t* net_off, const int32_t* pins,
+                           const int32_t* part, unsigned long long* mask) {
+  const unsigned lane = threadIdx.x & 31;
+  const unsigned gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const unsigned nw = (gridDim.x * blockDim.x) >> 5;
+  for (unsigned e = gw; e < (unsigned)m; e += nw) {
+    unsigned long long mk = 0;
+    for (unsigned j = net_off[e] + lane; j < net_off[e + 1]; j += 32) mk |= 1ull << part[pins[j]];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mk |= __shfl_xor_sync(0xffffffffu, mk, o);
+    if (lane == 0) mask[e] = mk;
+  }
+}
+
+// Stable grouping of items by block (counting sort in tiles of kGrpTile
+// items, one CTA each): item i belongs to every block of its mask (a vertex:
+// its block; a net: the blocks of its pins).  k_grp_count writes the count
+// of block b in tile t to C[b * T + t]; after an exclusive scan of C (block
+// major), k_grp_place puts item i of block b at C[b * T + t] + the number of
+// earlier items of its tile in b, so every block's list is ascending.
+constexpr int kGrpTile = 512;
+
+__device__ __forceinline__ unsigned long long grp_mask(int32_t i, int32_t n, const int32_t* part,
+                                                       const unsigned long long* nmask) {
+  if (i >= n) return 0ull;
+  return part ? 1ull << part[i] : nmask[i];
+}
+
+__global__ void __launch_bounds__(kGrpTile) k_grp_count(int32_t n, const int32_t* part,
+                                                        const unsigned long long* nmask, int k,
+                                                        unsigned T, unsigned* C) {
+  __shared__ unsigned cnt[64];
+  if (threadIdx.x < 64) cnt[threadIdx.x] = 0;
+  __syncthreads();
+  unsigned long long mk = grp_mask(blockIdx.x * kGrpTile + threadIdx.x, n, part, nmask);
+  while (mk) {
+    atomicAdd(&cnt[__ffsll(mk) - 1], 1u);
+    mk &= mk - 1;
+  }
+  __syncthreads();
+  if ((int)threadIdx.x < k) C[threadIdx.x * T + blockIdx.x] = cnt[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(kGrpTile) k_grp_place(int32_t n, const int32_t* part,
+                                                        const unsigned long long* nmask, int k,
+                                                        unsigned T, const unsigned* C,
+                                                        int32_t* out) {
+  __shared__ unsigned wc[kGrpTile / 32][64];
+  const unsigned lane = threadIdx.x & 31, w = threadIdx.x >> 5, lt = (1u << lane) - 1u;
+  const int32_t i = blockIdx.x * kGrpTile + threadIdx.x;
+  const unsigned long long mk = grp_mask(i, n, part, nmask);
+  for (int b = 0; b < k; b++) {
+    const unsigned bal = __ballot_sync(0xffffffffu, (mk >> b) & 1ull);
+    if (lane == 0) wc[w][b] = __popc(bal);
+  }
+  __syncthreads();
+  if ((int)threadIdx.x < k) {
+    unsigned run = 0;
+    for (int q = 0; q < kGrpTile / 32; q++) {
+      const unsigned v = wc[q][threadIdx.x];
+      wc[q][threadIdx.x] = run;
+      run += v;
+    }
+  }
+  __syncthreads();
+  for (int b = 0; b < k; b++) {
+    const bool in = (mk >> b) & 1ull;
+    const unsigned bal = __ballot_sync(0xffffffffu, in);
+    if (in) out[C[b * T + blockIdx.x] + wc[w][b] + __popc(bal & lt)] = i;
+  }
+}
+
+// side of the vertices of one block (s = 0 / 1) or back to -1 with level 0
+// and not taken (s < 0)
+__global__ void k_list_side(unsigned cnt, const int32_t* list, int s, int32_t* side, int32_t* lev,
+                            uint8_t* in_b) {
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x) {
+    const int v = list[i];
+    side[v] = s;
+    if (s < 0) {
+      lev[v] = 0;
+      in_b[v] = 0;
+    }
+  }
+}
+
+// level 1 from the nets of block bi that also hold pins of block bj (the
+// pair's cut nets): their pins of either block, a warp per net
+__global__ void k_level1_list(unsigned cnt, const int32_t* nets, const unsigned long long* mask,
+                              int32_t bi, int32_t bj, const uint32_t* net_off, const int32_t* pins,
+                              const int32_t* side, int32_t* lev) {
+  const unsigned lane = threadIdx.x & 31;
+  const unsigned gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const unsigned nw = (gridDim.x * blockDim.x) >> 5;
+  for (unsigned i = gw; i < cnt; i += nw) {
+    const int e = nets[i];
+    if (!((mask[e] >> bj) & 1ull)) continue;
+    for (unsigned j = net_off[e] + lane; j < net_off[e + 1]; j += 32) {
+      const int v = pins[j];
+      if (side[v] >= 0) lev[v] = 1;
+    }
+  }
+  (void)bi;
+}
+
+// flag[i] = the vertex list[i] has level d (d >= 0) / is taken (d < 0)
+__global__ void k_list_flag(unsigned cnt, const int32_t* list, const int32_t* lev,
+                            const uint8_t* in_b, int d, unsigned* flag) {
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x) {
+    const int v = list[i];
+    flag[i] = d >= 0 ? (lev[v] == d ? 1u : 0u) : (unsigned)in_b[v];
+  }
+}
+
+// flag[i] = net nets[i] has no pin in block b
+__global__ void k_net_not_in(unsigned cnt, const int32_t* nets, const unsigned long long* mask,
+                             int32_t b, unsigned* flag) {
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x)
+    flag[i] = ((mask[nets[i]] >> b) & 1ull) ? 0u : 1u;
+}
+
+__global__ void k_list_scatter(unsigned cnt, const int32_t* list, const unsigned* flag,
+                               const unsigned* pos, int32_t* out, const int32_t* node_w,
+                               unsigned* wout) {
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x)
+    if (flag[i]) {
+      out[pos[i]] = list[i];
+      if (wout) wout[pos[i]] = (unsigned)node_w[list[i]];
+    }
+}
+
+// block list offsets from the scanned tile counts: out[b] = start of block b,
+// out[k] = total
+__global__ void k_grp_offsets(const unsigned* C, unsigned T, int k, const unsigned* total,
+                              unsigned* out) {
+  if ((int)threadIdx.x < k) out[threadIdx.x] = C[threadIdx.x * T];
+  if (threadIdx.x == 0) out[k] = *total;
+}
+
+// merge of two disjoint ascending lists into one ascending list
+__global__ void k_merge_sorted(const int32_t* a, unsigned na, const int32_t* b, unsigned nb,
+                               int32_t* out) {
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < na + nb;
+       i += gridDim.x * blockDim.x) {
+    const bool in_a = i < na;
+    const int32_t v = in_a ? a[i] : b[i - na];
+    const int32_t* o = in_a ? b : a;
+    unsigned lo = 0, hi = in_a ? nb : na;   // elements of the other list below v
+    while (lo < hi) {
+      const unsigned mid = (lo + hi) >> 1;
+      if (o[mid] < v) lo = mid + 1;
+      else hi = mid;
+    }
+    out[(in_a ? i : i - na) + lo] = v;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -350,21 +454,6 @@ hfp_status hg_set_device(hfp_hgraph* hg) {
   return HFP_OK;
 }
 
-// exclusive scan + compaction of flag[0..n) into out (ascending), optionally
-// with the weights; returns the count (synchronises)
-hfp_status compact(hfp_hgraph* hg, unsigned n, unsigned* flag, unsigned* pos, int32_t* out,
-                   unsigned* wout, unsigned* scr, unsigned* tot, unsigned* count) {
-  cudaStream_t st = hg->ctx->stream;
-  CK(cudaMemcpyAsync(pos, flag, sizeof(unsigned) * n, cudaMemcpyDeviceToDevice, st));
-  scan_exclusive(pos, n, scr, tot, st);
-  k_scatter<<<nb(n, 256, hg->ctx->sms * 8), 256, 0, st>>>((int32_t)n, flag, pos, out, hg->node_w,
-                                                          wout);
-  count_launches(1);
-  CK(cudaMemcpyAsync(count, tot, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
-  return HFP_OK;
-}
-
 }  // namespace
 
 HFP_API hfp_status hfp_hgraph_create(hfp_ctx* ctx, const hfp_hypergraph* H, hfp_mem mem,
@@ -480,24 +569,94 @@ namespace {
 
 // One pair: region, network, FlowCutter, moves (device) and Delta_exp.
 // moves_dev receives up to cap triples; res->n_moves is the count.
-// n-sized buffers of region growing, reused by the pairs of a round.
+// Buffers of region growing, reused by the pairs of a round.  side, lev and
+// in_b cover all vertices; a pair sets them for its two blocks and puts them
+// back (-1, 0, 0) when its network is built.
 struct RegionScratch {
-  DevBuf side, lev, wsum, flag, pos, cand, wts, scr, tot, inb, taken, cut;
+  DevBuf side, lev, flag, pos, cand, wts, scr, tot, inb, taken, cut, rv, nets2, netlist, vlist;
   hfp_status alloc(hfp_hgraph* hg) {
     cudaStream_t st = hg->ctx->stream;
-    const size_t n = hg->n > 0 ? hg->n : 1;
+    const size_t n = hg->n > 0 ? hg->n : 1, m = hg->m > 0 ? hg->m : 1;
+    const size_t nm = n > m ? n : m;
     CK(side.alloc(sizeof(int32_t) * n, st));
     CK(lev.alloc(sizeof(int32_t) * n, st));
-    CK(wsum.alloc(sizeof(unsigned long long) * 2, st));
-    CK(flag.alloc(sizeof(unsigned) * n, st));
-    CK(pos.alloc(sizeof(unsigned) * n, st));
+    CK(flag.alloc(sizeof(unsigned) * nm, st));
+    CK(pos.alloc(sizeof(unsigned) * nm, st));
     CK(cand.alloc(sizeof(int32_t) * n, st));
     CK(wts.alloc(sizeof(unsigned) * n, st));
-    CK(scr.alloc(sizeof(unsigned) * (scan_scratch_words((unsigned)n) + 8), st));
+    CK(scr.alloc(sizeof(unsigned) * (scan_scratch_words((unsigned)nm) + 8), st));
     CK(tot.alloc(sizeof(unsigned), st));
     CK(inb.alloc(n, st));
     CK(taken.alloc(sizeof(unsigned), st));
     CK(cut.alloc(sizeof(unsigned long long), st));
+    CK(rv.alloc(sizeof(int32_t) * n, st));
+    CK(nets2.alloc(sizeof(int32_t) * m, st));
+    CK(netlist.alloc(sizeof(int32_t) * m, st));
+    CK(vlist.alloc(sizeof(int32_t) * n, st));
+    CK(cudaMemsetAsync(side.p, 0xFF, sizeof(int32_t) * n, st));
+    CK(cudaMemsetAsync(lev.p, 0, sizeof(int32_t) * n, st));
+    CK(cudaMemsetAsync(inb.p, 0, n, st));
+    return HFP_OK;
+  }
+};
+
+// The vertices and the nets of every block in ascending order, the nets'
+// block masks and the block weights, for one partition (k <= 64).
+struct BlockLists {
+  DevBuf nmask, C, bv, bn, offs;
+  std::vector<unsigned> bv_off, bn_off;     // k + 1 each
+  std::vector<unsigned long long> bw;       // k
+  hfp_status build(hfp_hgraph* hg, const int32_t* part, int32_t k) {
+    hfp_ctx* ctx = hg->ctx;
+    cudaStream_t st = ctx->stream;
+    const int n = hg->n, m = hg->m, sms = ctx->sms;
+    const unsigned Tv = (unsigned)((n + kGrpTile - 1) / kGrpTile);
+    const unsigned Tn = (unsigned)((m + kGrpTile - 1) / kGrpTile);
+    const size_t cmax = (size_t)k * (Tv > Tn ? Tv : Tn) + 1;
+    DevBuf scr, tot, dbw;
+    CK(nmask.alloc(sizeof(unsigned long long) * (m > 0 ? m : 1), st));
+    CK(C.alloc(sizeof(unsigned) * cmax, st));
+    CK(bv.alloc(sizeof(int32_t) * (n > 0 ? n : 1), st));
+    CK(bn.alloc(sizeof(int32_t) * (hg->p > 0 ? hg->p : 1), st));
+    CK(offs.alloc(sizeof(unsigned) * 2 * (k + 1), st));
+    CK(scr.alloc(sizeof(unsigned) * (scan_scratch_words((unsigned)cmax) + 8), st));
+    CK(tot.alloc(sizeof(unsigned) * 2, st));
+    CK(dbw.alloc(sizeof(unsigned long long) * k, st));
+    CK(cudaMemsetAsync(offs.p, 0, sizeof(unsigned) * 2 * (k + 1), st));
+    CK(cudaMemsetAsync(dbw.p, 0, sizeof(unsigned long long) * k, st));
+    unsigned* of = offs.as<unsigned>();
+    if (n) {
+      k_grp_count<<<Tv, kGrpTile, 0, st>>>(n, part, nullptr, k, Tv, C.as<unsigned>());
+      scan_exclusive(C.as<unsigned>(), (unsigned)k * Tv, scr.as<unsigned>(), tot.as<unsigned>(),
+                     st);
+      k_grp_place<<<Tv, kGrpTile, 0, st>>>(n, part, nullptr, k, Tv, C.as<unsigned>(),
+                                           bv.as<int32_t>());
+      k_grp_offsets<<<1, 64, 0, st>>>(C.as<unsigned>(), Tv, k, tot.as<unsigned>(), of);
+      k_block_weights<<<nb(n, 256, sms * 8), 256, 0, st>>>(n, part, hg->node_w,
+                                                           dbw.as<unsigned long long>());
+      count_launches(5);
+    }
+    if (m) {
+      k_net_mask<<<nb((long long)m * 32, 256, sms * 16), 256, 0, st>>>(
+          m, hg->net_off, hg->pins, part, nmask.as<unsigned long long>());
+      k_grp_count<<<Tn, kGrpTile, 0, st>>>(m, nullptr, nmask.as<unsigned long long>(), k, Tn,
+                                           C.as<unsigned>());
+      scan_exclusive(C.as<unsigned>(), (unsigned)k * Tn, scr.as<unsigned>(),
+                     tot.as<unsigned>() + 1, st);
+      k_grp_place<<<Tn, kGrpTile, 0, st>>>(m, nullptr, nmask.as<unsigned long long>(), k, Tn,
+                                           C.as<unsigned>(), bn.as<int32_t>());
+      k_grp_offsets<<<1, 64, 0, st>>>(C.as<unsigned>(), Tn, k, tot.as<unsigned>() + 1,
+                                      of + (k + 1));
+      count_launches(4);
+    }
+    std::vector<unsigned> h(2 * (k + 1));
+    bw.assign(k, 0);
+    CK(cudaMemcpyAsync(h.data(), of, sizeof(unsigned) * 2 * (k + 1), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(bw.data(), dbw.p, sizeof(unsigned long long) * k, cudaMemcpyDeviceToHost,
+                       st));
+    CK(cudaStreamSynchronize(st));
+    bv_off.assign(h.begin(), h.begin() + (k + 1));
+    bn_off.assign(h.begin() + (k + 1), h.end());
     return HFP_OK;
   }
 };
@@ -515,10 +674,32 @@ struct PairWork {
   }
 };
 
+// Compaction of list[i] for flag[i] != 0 into out (list order), optionally
+// with the vertex weights; returns the count (synchronises).
+hfp_status compact_list(hfp_hgraph* hg, unsigned cnt, const int32_t* list, unsigned* flag,
+                        unsigned* pos, int32_t* out, unsigned* wout, unsigned* scr, unsigned* tot,
+                        unsigned* count) {
+  cudaStream_t st = hg->ctx->stream;
+  if (cnt == 0) {
+    *count = 0;
+    return HFP_OK;
+  }
+  CK(cudaMemcpyAsync(pos, flag, sizeof(unsigned) * cnt, cudaMemcpyDeviceToDevice, st));
+  scan_exclusive(pos, cnt, scr, tot, st);
+  k_list_scatter<<<nb(cnt, 256, hg->ctx->sms * 8), 256, 0, st>>>(cnt, list, flag, pos, out,
+                                                                 hg->node_w, wout);
+  count_launches(1);
+  CK(cudaMemcpyAsync(count, tot, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return HFP_OK;
+}
+
 // Region of the pair (Section 6), its flow network and the pair's original
-// cut on the network's nets.
+// cut on the network's nets.  Everything but the flow network's own
+// construction works on the two blocks' vertex and net lists.
 hfp_status prepare_pair(hfp_hgraph* hg, const int32_t* part, int32_t k, int32_t bi, int32_t bj,
-                        const hfp_refine_params* prm, RegionScratch& sc, PairWork& w) {
+                        const hfp_refine_params* prm, RegionScratch& sc, const BlockLists& bl,
+                        PairWork& w) {
   hfp_ctx* ctx = hg->ctx;
   cudaStream_t st = ctx->stream;
   const int n = hg->n, m = hg->m, sms = ctx->sms;
@@ -526,20 +707,29 @@ hfp_status prepare_pair(hfp_hgraph* hg, const int32_t* part, int32_t k, int32_t 
   memset(res, 0, sizeof(*res));
   res->bi = bi;
   res->bj = bj;
-  CK(cudaMemsetAsync(sc.wsum.p, 0, sizeof(unsigned long long) * 2, st));
-  CK(cudaMemsetAsync(sc.inb.p, 0, n > 0 ? n : 1, st));
-  k_side<<<nb(n, 256, sms * 8), 256, 0, st>>>(n, part, bi, bj, hg->node_w, sc.side.as<int32_t>(),
-                                             sc.lev.as<int32_t>(),
-                                             sc.wsum.as<unsigned long long>());
-  count_launches(1);
-  if (m) {
-    k_level1<<<nb((long long)m * 32, 256, sms * 16), 256, 0, st>>>(
-        m, hg->net_off, hg->pins, sc.side.as<int32_t>(), sc.lev.as<int32_t>());
+  (void)k;
+  const int32_t* bv = bl.bv.as<int32_t>();
+  const int32_t* bn = bl.bn.as<int32_t>();
+  const unsigned long long* nmask = bl.nmask.as<unsigned long long>();
+  const int32_t* V[2] = {bv + bl.bv_off[bi], bv + bl.bv_off[bj]};
+  const unsigned nv[2] = {bl.bv_off[bi + 1] - bl.bv_off[bi], bl.bv_off[bj + 1] - bl.bv_off[bj]};
+  const int32_t* Ni = bn + bl.bn_off[bi];
+  const int32_t* Nj = bn + bl.bn_off[bj];
+  const unsigned nni = bl.bn_off[bi + 1] - bl.bn_off[bi], nnj = bl.bn_off[bj + 1] - bl.bn_off[bj];
+  int32_t* side = sc.side.as<int32_t>();
+  int32_t* lev = sc.lev.as<int32_t>();
+  uint8_t* inb = sc.inb.as<uint8_t>();
+  for (int s = 0; s < 2; s++)
+    if (nv[s]) {
+      k_list_side<<<nb(nv[s], 256, sms * 8), 256, 0, st>>>(nv[s], V[s], s, side, lev, inb);
+      count_launches(1);
+    }
+  if (nni) {
+    k_level1_list<<<nb((long long)nni * 32, 256, sms * 16), 256, 0, st>>>(
+        nni, Ni, nmask, bi, bj, hg->net_off, hg->pins, side, lev);
     count_launches(1);
   }
-  unsigned long long cw[2];
-  CK(cudaMemcpyAsync(cw, sc.wsum.p, sizeof(cw), cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
+  const unsigned long long cw[2] = {bl.bw[bi], bl.bw[bj]};
   const long long half = (long long)((cw[0] + cw[1] + 1) / 2);
   const long long lim = ((long long)(100 + prm->alpha_eps_pct) * half) / 100;
   long long budget[2] = {std::max(0ll, lim - (long long)cw[1]),
@@ -548,12 +738,13 @@ hfp_status prepare_pair(hfp_hgraph* hg, const int32_t* part, int32_t k, int32_t 
   for (int s = 0; s < 2; s++) {
     long long left = budget[s];
     for (int d = 1; d <= prm->delta; d++) {
-      k_flag<<<nb(n, 256, sms * 8), 256, 0, st>>>(n, sc.side.as<int32_t>(), sc.lev.as<int32_t>(),
-                                                  s, d, sc.flag.as<unsigned>());
+      if (nv[s] == 0) break;
+      k_list_flag<<<nb(nv[s], 256, sms * 8), 256, 0, st>>>(nv[s], V[s], lev, inb, d,
+                                                           sc.flag.as<unsigned>());
       count_launches(1);
-      hfp_status r = compact(hg, n, sc.flag.as<unsigned>(), sc.pos.as<unsigned>(),
-                             sc.cand.as<int32_t>(), sc.wts.as<unsigned>(), sc.scr.as<unsigned>(),
-                             sc.tot.as<unsigned>(), &h_cnt);
+      hfp_status r = compact_list(hg, nv[s], V[s], sc.flag.as<unsigned>(), sc.pos.as<unsigned>(),
+                                  sc.cand.as<int32_t>(), sc.wts.as<unsigned>(),
+                                  sc.scr.as<unsigned>(), sc.tot.as<unsigned>(), &h_cnt);
       if (r != HFP_OK) return r;
       if (h_cnt == 0) break;
       scan_exclusive(sc.wts.as<unsigned>(), h_cnt, sc.scr.as<unsigned>(), sc.tot.as<unsigned>(),
@@ -561,8 +752,7 @@ hfp_status prepare_pair(hfp_hgraph* hg, const int32_t* part, int32_t k, int32_t 
       CK(cudaMemsetAsync(sc.taken.p, 0, sizeof(unsigned), st));
       k_take<<<nb(h_cnt, 256, sms * 8), 256, 0, st>>>(h_cnt, sc.cand.as<int32_t>(),
                                                       sc.wts.as<unsigned>(), hg->node_w, left,
-                                                      sc.inb.as<uint8_t>(),
-                                                      sc.taken.as<unsigned>());
+                                                      inb, sc.taken.as<unsigned>());
       count_launches(1);
       unsigned h2[2];
       CK(cudaMemcpyAsync(&h2[0], sc.taken.p, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
@@ -572,33 +762,70 @@ hfp_status prepare_pair(hfp_hgraph* hg, const int32_t* part, int32_t k, int32_t 
       left -= (long long)h2[1];
       if (d == prm->delta) break;
       k_next_level<<<nb((long long)h_cnt * 32, 256, sms * 16), 256, 0, st>>>(
-          h_cnt, sc.cand.as<int32_t>(), hg->vnet_off, hg->vnet, hg->net_off, hg->pins,
-          sc.side.as<int32_t>(), s, sc.lev.as<int32_t>(), d + 1);
+          h_cnt, sc.cand.as<int32_t>(), hg->vnet_off, hg->vnet, hg->net_off, hg->pins, side, s,
+          lev, d + 1);
       count_launches(1);
     }
   }
-  // region (ascending) and its distances
-  k_inb_flag<<<nb(n, 256, sms * 8), 256, 0, st>>>(n, sc.inb.as<uint8_t>(), sc.flag.as<unsigned>());
-  count_launches(1);
-  unsigned nr = 0;
-  hfp_status r = compact(hg, n, sc.flag.as<unsigned>(), sc.pos.as<unsigned>(),
-                         sc.cand.as<int32_t>(), nullptr, sc.scr.as<unsigned>(),
-                         sc.tot.as<unsigned>(), &nr);
-  if (r != HFP_OK) return r;
+  // region: the taken vertices of each block (ascending), merged
+  unsigned rc[2] = {0, 0};
+  int32_t* rv = sc.rv.as<int32_t>();
+  for (int s = 0; s < 2; s++) {
+    if (nv[s] == 0) continue;
+    k_list_flag<<<nb(nv[s], 256, sms * 8), 256, 0, st>>>(nv[s], V[s], lev, inb, -1,
+                                                         sc.flag.as<unsigned>());
+    count_launches(1);
+    hfp_status r = compact_list(hg, nv[s], V[s], sc.flag.as<unsigned>(), sc.pos.as<unsigned>(),
+                                rv + rc[0], nullptr, sc.scr.as<unsigned>(), sc.tot.as<unsigned>(),
+                                &rc[s]);
+    if (r != HFP_OK) return r;
+  }
+  const unsigned nr = rc[0] + rc[1];
   DevBuf dist;
   CK(dist.alloc(sizeof(int32_t) * (nr > 0 ? nr : 1), st));
   CK(w.region.alloc(sizeof(int32_t) * (nr > 0 ? nr : 1), st));
   if (nr) {
-    k_region_dist<<<nb(nr, 256, sms * 8), 256, 0, st>>>(nr, sc.cand.as<int32_t>(),
-                                                        sc.lev.as<int32_t>(), dist.as<int32_t>());
-    count_launches(1);
-    CK(cudaMemcpyAsync(w.region.p, sc.cand.p, sizeof(int32_t) * nr, cudaMemcpyDeviceToDevice, st));
+    k_merge_sorted<<<nb(nr, 256, sms * 8), 256, 0, st>>>(rv, rc[0], rv + rc[0], rc[1],
+                                                         w.region.as<int32_t>());
+    k_region_dist<<<nb(nr, 256, sms * 8), 256, 0, st>>>(nr, w.region.as<int32_t>(), lev,
+                                                        dist.as<int32_t>());
+    count_launches(2);
   }
   w.nr = (int32_t)nr;
   res->region_size = (int32_t)nr;
+  // nets of the network: those of block bi, and those of block bj without a
+  // pin in bi, merged into ascending order; vertices: both blocks
+  unsigned nj2 = 0;
+  if (nnj) {
+    k_net_not_in<<<nb(nnj, 256, sms * 8), 256, 0, st>>>(nnj, Nj, nmask, bi,
+                                                        sc.flag.as<unsigned>());
+    count_launches(1);
+    hfp_status r = compact_list(hg, nnj, Nj, sc.flag.as<unsigned>(), sc.pos.as<unsigned>(),
+                                sc.nets2.as<int32_t>(), nullptr, sc.scr.as<unsigned>(),
+                                sc.tot.as<unsigned>(), &nj2);
+    if (r != HFP_OK) return r;
+  }
+  const unsigned nnet = nni + nj2;
+  if (nnet) {
+    k_merge_sorted<<<nb(nnet, 256, sms * 8), 256, 0, st>>>(Ni, nni, sc.nets2.as<int32_t>(), nj2,
+                                                           sc.netlist.as<int32_t>());
+    count_launches(1);
+  }
+  if (nv[0]) CK(cudaMemcpyAsync(sc.vlist.p, V[0], sizeof(int32_t) * nv[0], cudaMemcpyDeviceToDevice, st));
+  if (nv[1])
+    CK(cudaMemcpyAsync(sc.vlist.as<int32_t>() + nv[0], V[1], sizeof(int32_t) * nv[1],
+                       cudaMemcpyDeviceToDevice, st));
   hfp_hypergraph Hd{n, m, hg->net_off, hg->pins, hg->net_w, hg->node_w};
-  r = hfp_build_flow_network(ctx, &Hd, HFP_MEM_DEVICE, w.region.as<int32_t>(), (int32_t)nr,
-                             sc.side.as<int32_t>(), dist.as<int32_t>(), &w.net);
+  hfp_status r = build_network_impl(ctx, &Hd, HFP_MEM_DEVICE, w.region.as<int32_t>(), (int32_t)nr,
+                                    side, dist.as<int32_t>(), sc.netlist.as<int32_t>(),
+                                    (int32_t)nnet, sc.vlist.as<int32_t>(),
+                                    (int32_t)(nv[0] + nv[1]), &w.net);
+  // the two blocks' entries go back for the next pair
+  for (int s = 0; s < 2; s++)
+    if (nv[s]) {
+      k_list_side<<<nb(nv[s], 256, sms * 8), 256, 0, st>>>(nv[s], V[s], -1, side, lev, inb);
+      count_launches(1);
+    }
   if (r != HFP_OK) return r;
   res->pins = w.net->d.p_pins;
   CK(cudaMemsetAsync(sc.cut.p, 0, sizeof(unsigned long long), st));
@@ -676,10 +903,10 @@ hfp_status finish_pair(hfp_hgraph* hg, const int32_t* part, hfp_status fc, const
 // One pair, one problem per launch sequence: region, network, FlowCutter
 // (hfp_flowcutter), moves.
 hfp_status refine_pair(hfp_hgraph* hg, const int32_t* part, int32_t k, int32_t bi, int32_t bj,
-                       const hfp_refine_params* prm, RegionScratch& sc, DevBuf& moves_dev,
-                       hfp_pair_result* res) {
+                       const hfp_refine_params* prm, RegionScratch& sc, const BlockLists& bl,
+                       DevBuf& moves_dev, hfp_pair_result* res) {
   PairWork w;
-  hfp_status s = prepare_pair(hg, part, k, bi, bj, prm, sc, w);
+  hfp_status s = prepare_pair(hg, part, k, bi, bj, prm, sc, bl, w);
   if (s != HFP_OK) return s;
   const hfp_fc_params fp = pair_fc_params(hg, k, prm, w);
   hfp_fc_result fr{};
@@ -695,14 +922,16 @@ HFP_API hfp_status hfp_refine_block_pair(hfp_hgraph* hg, const int32_t* part, in
                                          int32_t bi, int32_t bj, const hfp_refine_params* prm,
                                          int32_t* moves, int32_t cap, hfp_pair_result* res) {
   if (!hg || !part || !prm || !res) return fail(HFP_ERR_INVALID, "NULL argument");
-  if (k < 2 || bi < 0 || bj < 0 || bi >= k || bj >= k || bi == bj || prm->delta < 1)
+  if (k < 2 || k > 64 || bi < 0 || bj < 0 || bi >= k || bj >= k || bi == bj || prm->delta < 1)
     return fail(HFP_ERR_INVALID, "bad block pair");
   hfp_status s = hg_set_device(hg);
   if (s != HFP_OK) return s;
   RegionScratch sc;
   if ((s = sc.alloc(hg)) != HFP_OK) return s;
+  BlockLists bl;
+  if ((s = bl.build(hg, part, k)) != HFP_OK) return s;
   DevBuf mv;
-  if ((s = refine_pair(hg, part, k, bi, bj, prm, sc, mv, res)) != HFP_OK) return s;
+  if ((s = refine_pair(hg, part, k, bi, bj, prm, sc, bl, mv, res)) != HFP_OK) return s;
   if (moves && res->n_moves > 0) {
     const int32_t c = res->n_moves < cap ? res->n_moves : cap;
     if (c > 0)
@@ -800,10 +1029,12 @@ hfp_status refine_pairs(hfp_hgraph* hg, const int32_t* part, int32_t k,
   hfp_status s = sc.alloc(hg);
   if (s != HFP_OK) return s;
   auto t0 = std::chrono::steady_clock::now();
+  BlockLists bl;
+  if ((s = bl.build(hg, part, k)) != HFP_OK) return s;
   if (!batched) {
     for (const auto& pr : pairs) {
       items.emplace_back();
-      if ((s = refine_pair(hg, part, k, pr.first, pr.second, prm, sc, items.back().mv,
+      if ((s = refine_pair(hg, part, k, pr.first, pr.second, prm, sc, bl, items.back().mv,
                            &items.back().r)) != HFP_OK)
         return s;
     }
@@ -814,7 +1045,7 @@ hfp_status refine_pairs(hfp_hgraph* hg, const int32_t* part, int32_t k,
   std::deque<PairWork> works;
   for (const auto& pr : pairs) {
     works.emplace_back();
-    if ((s = prepare_pair(hg, part, k, pr.first, pr.second, prm, sc, works.back())) != HFP_OK)
+    if ((s = prepare_pair(hg, part, k, pr.first, pr.second, prm, sc, bl, works.back())) != HFP_OK)
       return s;
   }
   CK(cudaStreamSynchronize(hg->ctx->stream));
@@ -1000,6 +1231,8 @@ HFP_API hfp_status hfp_autotune_round(hfp_hgraph* hg, const int32_t* part, int32
   if ((s = round_pairs(hg, part, k, nullptr, 0.f, &st, pl)) != HFP_OK) return s;
   RegionScratch sc;
   if ((s = sc.alloc(hg)) != HFP_OK) return s;
+  BlockLists bl;
+  if ((s = bl.build(hg, part, k)) != HFP_OK) return s;
   float best_ms = 0.f;
   int best_g = 0;
   for (int c = 0; c < n_candidates; c++) {
@@ -1007,7 +1240,8 @@ HFP_API hfp_status hfp_autotune_round(hfp_hgraph* hg, const int32_t* part, int32
     std::deque<PairWork> works;
     for (const auto& pr : pl) {
       works.emplace_back();
-      if ((s = prepare_pair(hg, part, k, pr.first, pr.second, prm, sc, works.back())) != HFP_OK)
+      if ((s = prepare_pair(hg, part, k, pr.first, pr.second, prm, sc, bl, works.back())) !=
+          HFP_OK)
         return s;
     }
     const int n = (int)works.size();

@@ -201,7 +201,11 @@ uint64_t hfp_kernel_launches(void);
  *   batch_fused_rounds, batch_async_gr  fused_rounds and async_gr for the
  *                 flows of the batched FlowCutter [1, 0]: in groups of a few
  *                 CTAs a level costs little more than its work, and the
- *                 queue-driven search measured slower there */
+ *                 queue-driven search measured slower there
+ *   parpr_block   one-phase rounds keep labels valid by ParPR-Block
+ *                 (Section 8.2, first fix: in a round a node pushed to may not
+ *                 relabel and a relabeled node may not be pushed to, whichever
+ *                 comes first) instead of capping a self relabel at d + 2 [0] */
 typedef struct {
   uint32_t gr_work_x100;
   uint32_t stall_rounds;
@@ -222,6 +226,7 @@ typedef struct {
   uint32_t identical_nets;
   uint32_t batch_fused_rounds;
   uint32_t batch_async_gr;
+  uint32_t parpr_block;
 } hfp_tuning;
 hfp_status hfp_ctx_get_tuning(hfp_ctx* ctx, hfp_tuning* tuning);
 hfp_status hfp_ctx_set_tuning(hfp_ctx* ctx, const hfp_tuning* tuning);

@@ -49,6 +49,11 @@ hfp_status ensure_engine_buffers(hfp_net* net, const Params& P) {
     CK(cudaMemsetAsync(net->delta1_buf, 0, sizeof(long long) * (NL ? NL : 1), c->stream));
     D.delta1 = (long long*)net->delta1_buf;
   }
+  if (P.parpr_block && P.fused_rounds && !D.blk) {
+    CK(cudaMallocAsync(&net->blk_buf, sizeof(uint32_t) * (NL ? NL : 1), c->stream));
+    CK(cudaMemsetAsync(net->blk_buf, 0, sizeof(uint32_t) * (NL ? NL : 1), c->stream));
+    D.blk = (uint32_t*)net->blk_buf;
+  }
   // Work queue of the global relabel: room for every node's chunks four
   // times (a node is queued again whenever its label drops; the sinks of a
   // relabel after sink-side piercings are all seeds); a fuller queue makes
@@ -101,6 +106,7 @@ hfp_status run_engine(hfp_net* net) {
   // without its buffers the engine runs the two-phase, level-by-level forms
   if (!net->d.delta1) P.fused_rounds = 0;
   if (!net->d.gq) P.async_gr = 0;
+  if (!net->d.blk) P.parpr_block = 0;
   // flows after a piercing are incremental: their own stall rule
   if (net->pierced) {
     if (P.stall_rounds_pierce) P.stall_rounds = P.stall_rounds_pierce;
@@ -276,6 +282,7 @@ HFP_API void hfp_net_destroy(hfp_net* net) {
   if (net->gq_buf) cudaFreeAsync(net->gq_buf, st);
   if (net->delta1_buf) cudaFreeAsync(net->delta1_buf, st);
   if (net->net_done_buf) cudaFreeAsync(net->net_done_buf, st);
+  if (net->blk_buf) cudaFreeAsync(net->blk_buf, st);
   cudaStreamSynchronize(st);
   delete net;
   ctx_release(c);
@@ -812,6 +819,7 @@ HFP_API hfp_status hfp_ctx_get_tuning(hfp_ctx* ctx, hfp_tuning* t) {
   t->batch_big_groups = ctx->batch_big_groups;
   t->batch_fused_rounds = ctx->batch_fused_rounds;
   t->batch_async_gr = ctx->batch_async_gr;
+  t->parpr_block = ctx->params.parpr_block;
   return HFP_OK;
 }
 
@@ -839,6 +847,7 @@ HFP_API hfp_status hfp_ctx_set_tuning(hfp_ctx* ctx, const hfp_tuning* t) {
   ctx->batch_big_groups = t->batch_big_groups;
   ctx->batch_fused_rounds = t->batch_fused_rounds ? 1 : 0;
   ctx->batch_async_gr = t->batch_async_gr ? 1 : 0;
+  ctx->params.parpr_block = t->parpr_block ? 1 : 0;
   return HFP_OK;
 }
 

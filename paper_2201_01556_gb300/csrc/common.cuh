@@ -65,6 +65,7 @@ struct NetDev {
   unsigned long long* gq;       // work queue of the asynchronous global relabel (may be null)
   uint8_t* net_done;            // per net: every pin is a terminal (batched piercing scans;
                                 // may be null)
+  uint32_t* blk;                // per node: ParPR-Block tag of the running round (may be null)
 };
 
 struct Ctl {

@@ -1180,11 +1180,44 @@ __device__ __forceinline__ int group_cand(long long q1, long long q2, int l1, in
   return cand;
 }
 
+// ParPR-Block (Section 8.2, the first of the two fixes of the push-relabel
+// conflict), the alternative to the capped self relabel of one-phase rounds:
+// in round R a node that was pushed to may not relabel, and a node that
+// relabeled may not be pushed to, whichever comes first.  Each node has a
+// tag word; R's tags are 2R (pushed to) and 2R + 1 (relabeled), set by
+// compare-and-swap, so the first of the two operations wins and the other is
+// refused.  A refused push leaves the arc residual (the node keeps its
+// excess for the next round); a refused relabel keeps the label.  The node
+// then relabels to the plain minimum over its residual arcs, without the
+// d(x) + 2 cap.  pb_mark(blk, y, mine, other) sets y's tag to `mine` unless
+// it already holds `other`; true when y holds `mine` afterwards.
+__device__ __forceinline__ bool pb_mark(uint32_t* blk, int y, unsigned mine, unsigned other) {
+  unsigned cur = *(volatile uint32_t*)&blk[y];
+  for (int i = 0; i < 3; i++) {
+    if (cur == mine) return true;
+    if (cur == other) return false;
+    const unsigned old = atomicCAS(&blk[y], cur, mine);
+    if (old == cur) return true;
+    cur = old;   // another thread set one of this round's tags
+  }
+  return cur == mine;
+}
+
+// New label of a discharged node with excess left: the capped self relabel,
+// or under ParPR-Block (pbt = 2R != 0) the uncapped one when x may relabel.
+__device__ __forceinline__ int round_label(const NetDev& N, int x, int dx, int cand,
+                                           unsigned pbt) {
+  if (!pbt) return min(min(cand, dx + 2), N.NL);
+  const int nl = min(cand, N.NL);
+  if (nl > dx && !pb_mark(N.blk, x, pbt | 1u, pbt)) return dx;
+  return nl;
+}
+
 // One-phase discharge of node x by a team of TW lanes (x < 0: idle team).
 template <int TW>
 __device__ void round_team(const NetDev& N, int x, const int32_t* Lr, int32_t* Ln,
                            long long* dprev, long long* dcur, int32_t* nl, unsigned lane,
-                           long long& sink_acc, Acc& a, const Slot& S) {
+                           long long& sink_acc, Acc& a, const Slot& S, unsigned pbt) {
   const int NL = N.NL;
   const unsigned tl = lane & (TW - 1);
   long long ex = 0, dp0 = 0;
@@ -1218,6 +1251,10 @@ __device__ void round_team(const NetDev& N, int x, const int32_t* Lr, int32_t* L
     if (rem > 0 && k < g.items)
       arc_group(N, g, k, w, fb, Lr, dt, rem, r1, r2, q1, q2, l1, l2, y1, y2, f1, f2, p, fi, fo,
                 a);
+    if (pbt) {
+      if (r1 > 0 && !(f1 & kTerminal) && !pb_mark(N.blk, y1, pbt, pbt | 1u)) r1 = 0;
+      if (r2 > 0 && !(f2 & kTerminal) && !pb_mark(N.blk, y2, pbt, pbt | 1u)) r2 = 0;
+    }
     const long long r = r1 + r2;
     const long long incl = team_incl_scan<TW>(r, tl);
     const long long take = min(max(rem - (incl - r), 0LL), r);
@@ -1244,7 +1281,7 @@ __device__ void round_team(const NetDev& N, int x, const int32_t* Lr, int32_t* L
     if (dp || dp0) dprev[x] = 0;
     if (act) {
       N.excess[x] = rem;
-      Ln[x] = rem > 0 ? min(min(cand, dx + 2), NL) : dx;
+      Ln[x] = rem > 0 ? round_label(N, x, dx, cand, pbt) : dx;
       if (rem > 0)
         want = atomicAdd((unsigned long long*)&dcur[x], (unsigned long long)kSelf) == 0ull;
       a.nodes++;
@@ -1260,7 +1297,7 @@ __device__ void round_team(const NetDev& N, int x, const int32_t* Lr, int32_t* L
 // One-phase discharge of one heavy node by the whole CTA.
 __device__ void round_block(const NetDev& N, int x, const int32_t* Lr, int32_t* Ln,
                             long long* dprev, long long* dcur, int32_t* nl, long long& sink_acc,
-                            Acc& a, const Slot& S) {
+                            Acc& a, const Slot& S, unsigned pbt) {
   const int NL = N.NL;
   const long long dp0 = __ldcg(&dprev[x]);
   const long long dp = strip_self(dp0);
@@ -1289,6 +1326,10 @@ __device__ void round_block(const NetDev& N, int x, const int32_t* Lr, int32_t* 
     if (k < g.items)
       arc_group(N, g, k, w, fb, Lr, dt, rem, r1, r2, q1, q2, l1, l2, y1, y2, f1, f2, p, fi, fo,
                 a);
+    if (pbt) {
+      if (r1 > 0 && !(f1 & kTerminal) && !pb_mark(N.blk, y1, pbt, pbt | 1u)) r1 = 0;
+      if (r2 > 0 && !(f2 & kTerminal) && !pb_mark(N.blk, y2, pbt, pbt | 1u)) r2 = 0;
+    }
     const long long r = r1 + r2;
     long long tot;
     const long long incl = block_incl_scan(r, &tot);
@@ -1314,7 +1355,7 @@ __device__ void round_block(const NetDev& N, int x, const int32_t* Lr, int32_t* 
   if (threadIdx.x == 0) {
     if (dp0) dprev[x] = 0;
     N.excess[x] = rem;
-    Ln[x] = rem > 0 ? min(min(cand, dx + 2), NL) : dx;
+    Ln[x] = rem > 0 ? round_label(N, x, dx, cand, pbt) : dx;
     if (rem > 0)
       want = atomicAdd((unsigned long long*)&dcur[x], (unsigned long long)kSelf) == 0ull;
     a.nodes++;
@@ -1332,7 +1373,10 @@ __device__ __forceinline__ long long* delta_prev(const NetDev& N, unsigned long 
 }
 
 __device__ void phase_round(const NetDev& N, const Sched& L, const Team& T, const Slot& S,
-                            unsigned lane, Acc& a) {
+                            unsigned lane, Acc& a, const Params& P) {
+  // ParPR-Block tags of this round (0: capped self relabel)
+  const unsigned pbt =
+      P.parpr_block && N.blk ? (((unsigned)(L.rounds + 1) & 0x3fffffffu) << 1) : 0u;
   const int32_t* Lr = lab_cur(N, L.lp);
   int32_t* Ln = lab_cur(N, L.lp ^ 1);
   long long* dcur = delta_cur(N, L.rounds);
@@ -1352,16 +1396,16 @@ __device__ void phase_round(const NetDev& N, const Sched& L, const Team& T, cons
     for (unsigned base = w0 * TPW; base < L.fcnt; base += nw * TPW) {
       const unsigned i = base + lane / kTeam;
       round_team<kTeam>(N, i < L.fcnt ? fl[i] : -1, Lr, Ln, dprev, dcur, nl, lane, sink_acc, a,
-                        S);
+                        S, pbt);
     }
   }
   if (split) {
     if (T.block >= light_blocks)
       round_block(N, fl[N.NL - 1 - (T.block - light_blocks)], Lr, Ln, dprev, dcur, nl, sink_acc,
-                  a, S);
+                  a, S, pbt);
   } else {
     for (unsigned h = T.block; h < L.fcnth; h += T.nblocks)
-      round_block(N, fl[N.NL - 1 - h], Lr, Ln, dprev, dcur, nl, sink_acc, a, S);
+      round_block(N, fl[N.NL - 1 - h], Lr, Ln, dprev, dcur, nl, sink_acc, a, S, pbt);
   }
   sink_acc = warp_sum(sink_acc);
   if (lane == 0 && sink_acc) atomicAdd(S.flow, (unsigned long long)sink_acc);
@@ -1981,7 +2025,7 @@ __device__ void run_phase_s(const NetDev& N, EngineCtl* E, const Sched& L, const
                             const Params& P) {
   switch (L.state) {
     case ST_ROUND_A: phase_a(N, L, T, S, lane, a, E); break;
-    case ST_ROUND: phase_round(N, L, T, S, lane, a); break;
+    case ST_ROUND: phase_round(N, L, T, S, lane, a, P); break;
     case ST_FLUSH: phase_flush(N, L, T); break;
     case ST_ROUND_B: phase_b(N, L, T, S, lane, a); break;
     case ST_GR_INIT: gr_init(N, E, L, T, S, lane, a); break;

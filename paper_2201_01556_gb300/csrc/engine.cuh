@@ -89,6 +89,7 @@ struct Params {
   unsigned int async_gr;             // global relabels as one queue-driven search
   unsigned int gr_warps;             // warps per CTA that serve that search's queue
   unsigned int fused_rounds;         // one phase per discharge round (needs NetDev::delta1)
+  unsigned int parpr_block;          // one-phase rounds relabel by ParPR-Block (needs NetDev::blk)
 };
 
 struct EngineCtl {

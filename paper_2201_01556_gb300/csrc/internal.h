@@ -101,6 +101,7 @@ struct hfp_net {
   void* gq_buf = nullptr;          // work queue of queue-driven global relabels
   void* delta1_buf = nullptr;      // second delta buffer of one-phase rounds
   void* net_done_buf = nullptr;    // nets the batched piercing scans skip
+  void* blk_buf = nullptr;         // ParPR-Block tags
   uint64_t launches = 0;
   uint64_t engine_ns = 0;
 };

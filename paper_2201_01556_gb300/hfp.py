@@ -56,7 +56,7 @@ class Tuning(ctypes.Structure):
                                                "batch_big_ctas", "batch_big_groups",
                                                "async_gr", "gr_warps", "fused_rounds",
                                                "identical_nets", "batch_fused_rounds",
-                                               "batch_async_gr")]
+                                               "batch_async_gr", "parpr_block")]
 
 
 class RefineParams(ctypes.Structure):

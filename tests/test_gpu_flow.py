@@ -486,3 +486,49 @@ def test_identical_nets_flowcutter_unchanged(hfp, ctx, ctx_dedup):
         res.append((r.status, r.flow, r.iterations, r.pierce_node.tolist(), r.final_side.tobytes()))
         gnet.close()
     assert res[0] == res[1]
+
+
+@pytest.fixture(scope="module")
+def ctx_parpr(hfp):
+    c = hfp.ctx_create(0)
+    hfp.ctx_set_tuning(c, parpr_block=1)
+    yield c
+    c.close()
+
+
+def test_parpr_block_flows_and_cuts(hfp, ctx_parpr):
+    """ParPR-Block (Section 8.2, first fix of the push-relabel conflict) as
+    the rounds' relabel rule: the flow value, both minimal cuts and the
+    per-arc preflow's feasibility are checked against the oracle like the
+    default rule's."""
+    for H, side, region in _random_cases(909, 120, n_lo=4, n_hi=60, m_hi=120):
+        gnet = _gpu_net(hfp, ctx_parpr, H, side, region)
+        _check_flow(hfp, gnet, oracle.build_network(H, side, region))
+        gnet.close()
+    for seed in range(1, 21):
+        inst = synth.instance("ring_n4096_geom", seed)
+        gnet = _gpu_net(hfp, ctx_parpr, inst["H"], inst["part"], inst["region"])
+        _check_flow(hfp, gnet, oracle.build_network(inst["H"], inst["part"], inst["region"]))
+        gnet.close()
+
+
+def test_parpr_block_flowcutter_unchanged(hfp, ctx, ctx_parpr):
+    """FlowCutter with ParPR-Block rounds takes the same piercing sequence and
+    ends in the same bipartition (max flow values and minimal cuts are
+    unique), on a scaled ring and on random networks."""
+    cases = [(synth.instance("ring_n500k_zipf_fc", 3, n=20000, m=30000, radius=2000), 5)]
+    for inst, seed in cases:
+        H, side, region = inst["H"], inst["part"], inst["region"]
+        L = oracle.max_block_weight(int(oracle.build_network(H, side, region).node_w.sum()), 2, 3)
+        res = []
+        for c in (ctx, ctx_parpr):
+            gnet = _gpu_net(hfp, c, H, side, region)
+            r = hfp.flowcutter(gnet, hfp.fc_params(L, seed=seed))
+            res.append((r.status, r.flow, r.iterations, r.pierce_node.tolist(),
+                        r.final_side.tobytes()))
+            gnet.close()
+        assert res[0] == res[1]
+        assert res[0][2] > 3
+    for i, (H, side, region) in enumerate(_random_cases(911, 40, n_lo=6, n_hi=50, m_hi=90,
+                                                        c_max=4)):
+        _fc_compare(hfp, ctx_parpr, H, side, region, seed=i)

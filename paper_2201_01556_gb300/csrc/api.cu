@@ -293,7 +293,8 @@ namespace hfp {
 hfp_status build_network_impl(hfp_ctx* ctx, const hfp_hypergraph* H, hfp_mem mem,
                               const int32_t* region, int32_t n_region, const int32_t* side,
                               const int32_t* dist_from_cut, const int32_t* nets, int32_t n_nets,
-                              const int32_t* verts, int32_t n_verts, hfp_net** out) {
+                              const int32_t* verts, int32_t n_verts, hfp_net** out,
+                              const SortBuildIn* sb) {
   if (!out) return fail(HFP_ERR_INVALID, "out is NULL");
   *out = nullptr;
   if (!ctx || !H) return fail(HFP_ERR_INVALID, "ctx or H is NULL");
@@ -310,8 +311,9 @@ hfp_status build_network_impl(hfp_ctx* ctx, const hfp_hypergraph* H, hfp_mem mem
   if (s != HFP_OK) return s;
   cudaStream_t st = ctx->stream;
   const int sms = ctx->sms;
-  // nets scanned (and per-net scratch entries): the list, or all of H
-  const int32_t M = nets ? n_nets : m;
+  // nets scanned (and per-net scratch entries): the list, or all of H, or
+  // the runs of the sorted region incidences
+  int32_t M = nets ? n_nets : m;
 
   // total pins of H
   uint32_t P = 0;
@@ -366,6 +368,42 @@ hfp_status build_network_impl(hfp_ctx* ctx, const hfp_hypergraph* H, hfp_mem mem
     }
   }
 
+  // second construction algorithm: the region's (net, vertex) pairs sorted by
+  // net; every run is a net of the region
+  const bool use_sb = sb && dist_from_cut && mem == HFP_MEM_DEVICE;
+  DevBuf sb_pos, sb_key, sb_val, sb_key2, sb_val2, sb_hist, sb_head, sb_rid, sb_rs, sb_rn, sb_scr,
+      sb_tot;
+  unsigned sb_R = 0;
+  if (use_sb) {
+    const size_t nr1 = (size_t)(n_region > 0 ? n_region : 1);
+    CK(sb_pos.alloc(sizeof(unsigned) * nr1, st));
+    CK(sb_tot.alloc(sizeof(unsigned), st));
+    CK(sb_scr.alloc(sizeof(unsigned) * (scan_scratch_words((unsigned)nr1) + 8), st));
+    unsigned P2 = 0;
+    CK(sort_build_count(n_region, d_region, sb->vnet_off, sb_pos.as<unsigned>(),
+                        sb_scr.as<unsigned>(), sb_tot.as<unsigned>(), &P2, sms, st));
+    const size_t p2 = P2 > 0 ? P2 : 1;
+    const unsigned T = (P2 + 511) / 512;
+    const size_t hw = (size_t)256 * (T > 0 ? T : 1);
+    CK(sb_key.alloc(sizeof(unsigned) * p2, st));
+    CK(sb_val.alloc(sizeof(int32_t) * p2, st));
+    CK(sb_key2.alloc(sizeof(unsigned) * p2, st));
+    CK(sb_val2.alloc(sizeof(int32_t) * p2, st));
+    CK(sb_head.alloc(sizeof(unsigned) * p2, st));
+    CK(sb_rid.alloc(sizeof(unsigned) * p2, st));
+    CK(sb_hist.alloc(sizeof(unsigned) * hw, st));
+    CK(sb_rs.alloc(sizeof(unsigned) * (p2 + 1), st));
+    CK(sb_rn.alloc(sizeof(int32_t) * p2, st));
+    DevBuf scr2;
+    CK(scr2.alloc(sizeof(unsigned) * (scan_scratch_words((unsigned)(p2 > hw ? p2 : hw)) + 8), st));
+    CK(sort_build_runs(n_region, d_region, sb->vnet_off, sb->vnet, m, P2, sb_pos.as<unsigned>(),
+                       scr2.as<unsigned>(), sb_tot.as<unsigned>(), sb_key.as<unsigned>(),
+                       sb_val.as<int32_t>(), sb_key2.as<unsigned>(), sb_val2.as<int32_t>(),
+                       sb_hist.as<unsigned>(), sb_head.as<unsigned>(), sb_rid.as<unsigned>(),
+                       sb_rs.as<unsigned>(), sb_rn.as<int32_t>(), &sb_R, sms, st));
+    M = (int32_t)sb_R;
+  }
+
   // pass 1 scratch
   const int32_t n_nodes = n_region + 2;
   DevBuf loc, keep, size, has_s, has_t, net_pos, pin_pos, s_pos, t_pos, totals, wsum, err,
@@ -406,10 +444,16 @@ hfp_status build_network_impl(hfp_ctx* ctx, const hfp_hypergraph* H, hfp_mem mem
                     err.as<int>(), st);
   launch_st_weight(verts ? n_verts : n, verts, loc.as<int32_t>(), d_side, d_nodew,
                    wsum.as<unsigned long long>(), err.as<int>(), sms, st);
-  launch_net_scan(n, M, nets, d_off, d_pins, d_netw, d_side, loc.as<int32_t>(),
-                  keep.as<unsigned>(), size.as<unsigned>(), has_s.as<unsigned>(),
-                  has_t.as<unsigned>(), dist_tmp.as<int32_t>(), d_dist ? 0 : 1,
-                  wsum.as<unsigned long long>() + 3, err.as<int>(), sms, st);
+  if (use_sb)
+    launch_sb_eval(sb_R, sb_rs.as<unsigned>(), sb_rn.as<int32_t>(), sb_val.as<int32_t>(),
+                   d_region, d_side, d_netw, sb->mask, sb->noff, sb->cnt, sb->b0, sb->b1,
+                   keep.as<unsigned>(), size.as<unsigned>(), has_s.as<unsigned>(),
+                   has_t.as<unsigned>(), wsum.as<unsigned long long>() + 3, sms, st);
+  else
+    launch_net_scan(n, M, nets, d_off, d_pins, d_netw, d_side, loc.as<int32_t>(),
+                    keep.as<unsigned>(), size.as<unsigned>(), has_s.as<unsigned>(),
+                    has_t.as<unsigned>(), dist_tmp.as<int32_t>(), d_dist ? 0 : 1,
+                    wsum.as<unsigned long long>() + 3, err.as<int>(), sms, st);
   if (M) {
     CK(cudaMemcpyAsync(net_pos.p, keep.p, sizeof(unsigned) * M, cudaMemcpyDeviceToDevice, st));
     CK(cudaMemcpyAsync(pin_pos.p, size.p, sizeof(unsigned) * M, cudaMemcpyDeviceToDevice, st));
@@ -528,10 +572,17 @@ hfp_status build_network_impl(hfp_ctx* ctx, const hfp_hypergraph* H, hfp_mem mem
   CKN(cudaMemsetAsync(D.flags, 0, NL, st));
   launch_st_attrs(node_gid, node_w, node_orig, wsum.as<unsigned long long>(), D.flags,
                   err.as<int>(), st);
-  launch_net_fill(M, nets, d_off, d_pins, d_netw, loc.as<int32_t>(), keep.as<unsigned>(),
-                  net_pos.as<unsigned>(), pin_pos.as<unsigned>(), s_pos.as<unsigned>(),
-                  t_pos.as<unsigned>(), has_s.as<unsigned>(), has_t.as<unsigned>(), tot,
-                  nnet_off, npin, nnet_w, net->net_gid, inc, sms, st);
+  if (use_sb)
+    launch_sb_fill(sb_R, sb_rs.as<unsigned>(), sb_rn.as<int32_t>(), sb_val.as<int32_t>(), d_side,
+                   d_region, d_netw, keep.as<unsigned>(), net_pos.as<unsigned>(),
+                   pin_pos.as<unsigned>(), s_pos.as<unsigned>(), t_pos.as<unsigned>(),
+                   has_s.as<unsigned>(), has_t.as<unsigned>(), tot, nnet_off, npin, nnet_w,
+                   net->net_gid, inc, sms, st);
+  else
+    launch_net_fill(M, nets, d_off, d_pins, d_netw, loc.as<int32_t>(), keep.as<unsigned>(),
+                    net_pos.as<unsigned>(), pin_pos.as<unsigned>(), s_pos.as<unsigned>(),
+                    t_pos.as<unsigned>(), has_s.as<unsigned>(), has_t.as<unsigned>(), tot,
+                    nnet_off, npin, nnet_w, net->net_gid, inc, sms, st);
   {
     uint32_t* hp = (uint32_t*)((char*)ctx->pinned_small + 1024);
     *hp = p_net;
@@ -820,6 +871,7 @@ HFP_API hfp_status hfp_ctx_get_tuning(hfp_ctx* ctx, hfp_tuning* t) {
   t->batch_fused_rounds = ctx->batch_fused_rounds;
   t->batch_async_gr = ctx->batch_async_gr;
   t->parpr_block = ctx->params.parpr_block;
+  t->construction = ctx->construction;
   return HFP_OK;
 }
 
@@ -848,6 +900,7 @@ HFP_API hfp_status hfp_ctx_set_tuning(hfp_ctx* ctx, const hfp_tuning* t) {
   ctx->batch_fused_rounds = t->batch_fused_rounds ? 1 : 0;
   ctx->batch_async_gr = t->batch_async_gr ? 1 : 0;
   ctx->params.parpr_block = t->parpr_block ? 1 : 0;
+  ctx->construction = t->construction <= 2 ? t->construction : 1;
   return HFP_OK;
 }
 

@@ -13,6 +13,8 @@
 //   scanned positions.
 // Incidence of region vertices: count, scan, scatter, then a per-vertex rank
 //   sort by pin slot so every list is in ascending slot order (deterministic).
+#include <utility>
+
 #include "kernels.cuh"
 
 namespace hfp {
@@ -394,6 +396,190 @@ __global__ void k_st_attrs(int32_t* node_gid, int32_t* node_w, int8_t* node_orig
 
 // ---------------------------------------------------------------------------
 // host launchers
+// ---------------------------------------------------------------------------
+// Second construction algorithm (Section 6, "Construction Algorithms"): the
+// pairs (e, u) of every region vertex u and its nets e, sorted by net with
+// the region order kept inside a net (a stable LSD radix sort), give the pin
+// lists of the region's sub-hypergraph; s joins net e when fewer of e's pins
+// of block 0 are in the region than e has in block 0, t likewise.  The work
+// depends on the region's incidences only, not on the full pin lists of the
+// nets that touch it.
+
+// incidence count of every region vertex
+__global__ void k_sb_deg(int32_t nr, const int32_t* region, const uint32_t* vnet_off,
+                         unsigned* deg) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nr; i += gridDim.x * blockDim.x) {
+    const int v = region[i];
+    deg[i] = vnet_off[v + 1] - vnet_off[v];
+  }
+}
+
+// the pairs: key = net, value = local id 2 + i, grouped by region vertex
+__global__ void k_sb_pairs(int32_t nr, const int32_t* region, const uint32_t* vnet_off,
+                           const int32_t* vnet, const unsigned* pos, unsigned* key,
+                           int32_t* val) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nr; i += gridDim.x * blockDim.x) {
+    const int v = region[i];
+    unsigned q = pos[i];
+    for (unsigned t = vnet_off[v]; t < vnet_off[v + 1]; t++, q++) {
+      key[q] = (unsigned)vnet[t];
+      val[q] = 2 + i;
+    }
+  }
+}
+
+// Stable radix sort pass (8 bits at `shift`) over tiles of kRsTile items:
+// per tile digit counts (digit-major), then a stable scatter by warp-level
+// peer ranks and per-warp digit counts.
+constexpr int kRsTile = 512;
+
+__global__ void __launch_bounds__(kRsTile) k_rs_count(unsigned n, const unsigned* key, int shift,
+                                                      unsigned T, unsigned* hist) {
+  __shared__ unsigned cnt[256];
+  for (int d = threadIdx.x; d < 256; d += blockDim.x) cnt[d] = 0;
+  __syncthreads();
+  const unsigned i = blockIdx.x * kRsTile + threadIdx.x;
+  if (i < n) atomicAdd(&cnt[(key[i] >> shift) & 255u], 1u);
+  __syncthreads();
+  for (int d = threadIdx.x; d < 256; d += blockDim.x) hist[d * T + blockIdx.x] = cnt[d];
+}
+
+__global__ void __launch_bounds__(kRsTile) k_rs_scatter(unsigned n, const unsigned* key,
+                                                        const int32_t* val, int shift, unsigned T,
+                                                        const unsigned* hist, unsigned* key_out,
+                                                        int32_t* val_out) {
+  __shared__ unsigned wc[kRsTile / 32][256];
+  const unsigned lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int j = threadIdx.x; j < (kRsTile / 32) * 256; j += blockDim.x) (&wc[0][0])[j] = 0;
+  __syncthreads();
+  const unsigned i = blockIdx.x * kRsTile + threadIdx.x;
+  const bool in = i < n;
+  const unsigned k = in ? key[i] : 0u;
+  const unsigned d = in ? (k >> shift) & 255u : 256u;
+  const unsigned peers = __match_any_sync(FULLB, d);
+  const unsigned rank = __popc(peers & ((1u << lane) - 1u));
+  if (in && rank == 0) wc[w][d] = __popc(peers);
+  __syncthreads();
+  for (int dd = threadIdx.x; dd < 256; dd += blockDim.x) {
+    unsigned run = 0;
+    for (int q = 0; q < kRsTile / 32; q++) {
+      const unsigned c = wc[q][dd];
+      wc[q][dd] = run;
+      run += c;
+    }
+  }
+  __syncthreads();
+  if (in) {
+    const unsigned o = hist[d * T + blockIdx.x] + wc[w][d] + rank;
+    key_out[o] = k;
+    val_out[o] = val[i];
+  }
+}
+
+// first pair of every net (run head)
+__global__ void k_sb_heads(unsigned n, const unsigned* key, unsigned* head) {
+  for (unsigned j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
+    head[j] = (j == 0 || key[j] != key[j - 1]) ? 1u : 0u;
+}
+
+// run_start[R] = the pair count (R = the number of runs, at *R)
+__global__ void k_sb_end(unsigned* run_start, const unsigned* R, unsigned n) { run_start[*R] = n; }
+
+__global__ void k_sb_runs(unsigned n, const unsigned* key, const unsigned* head,
+                          const unsigned* rid, unsigned* run_start, int32_t* run_net) {
+  for (unsigned j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
+    if (head[j]) {
+      run_start[rid[j]] = j;
+      run_net[rid[j]] = (int32_t)key[j];
+    }
+}
+
+// per net of the region: region pins by side, pins of the two blocks in H
+// (cnt[noff[e] + rank of the block in the net's mask]), s / t membership,
+// kept size (the first algorithm's rules)
+__global__ void k_sb_eval(unsigned R, const unsigned* run_start, const int32_t* run_net,
+                          const int32_t* val, const int32_t* region, const int32_t* side,
+                          const int32_t* net_w, const unsigned long long* mask,
+                          const unsigned* noff, const unsigned* cnt, int32_t b0, int32_t b1,
+                          unsigned* keep, unsigned* size, unsigned* has_s, unsigned* has_t,
+                          unsigned long long* wnet) {
+  unsigned long long wacc = 0;
+  for (unsigned r = blockIdx.x * blockDim.x + threadIdx.x; r < R; r += gridDim.x * blockDim.x) {
+    const int e = run_net[r];
+    unsigned in0 = 0, in1 = 0;
+    for (unsigned j = run_start[r]; j < run_start[r + 1]; j++) {
+      const int sd = side[region[val[j] - 2]];
+      in0 += sd == 0;
+      in1 += sd == 1;
+    }
+    const unsigned long long mk = mask[e];
+    const unsigned tot0 = (mk >> b0) & 1ull
+                              ? cnt[noff[e] + __popcll(mk & ((1ull << b0) - 1ull))] : 0u;
+    const unsigned tot1 = (mk >> b1) & 1ull
+                              ? cnt[noff[e] + __popcll(mk & ((1ull << b1) - 1ull))] : 0u;
+    const bool hs = in0 < tot0, ht = in1 < tot1;
+    const unsigned tot = in0 + in1 + hs + ht;
+    const bool k = tot >= 2 && !(hs && ht);
+    keep[r] = k;
+    size[r] = k ? tot : 0;
+    has_s[r] = k && hs;
+    has_t[r] = k && ht;
+    wacc += (unsigned long long)net_w[e];
+  }
+  if (wacc) atomicAdd(wnet, wacc);
+}
+
+// the kept nets' pin lists (region pins in region order, then s, then t),
+// weights, ids in H and s / t incidences, a warp per net
+__global__ void k_sb_fill(unsigned R, const unsigned* run_start, const int32_t* run_net,
+                          const int32_t* val, const int32_t* side, const int32_t* region,
+                          const int32_t* net_w, const unsigned* keep, const unsigned* net_pos,
+                          const unsigned* pin_pos, const unsigned* s_pos, const unsigned* t_pos,
+                          const unsigned* has_s_flag, const unsigned* has_t_flag,
+                          const unsigned* totals, uint32_t* nnet_off, int32_t* npin,
+                          int32_t* nnet_w, int32_t* nnet_gid, int2* inc) {
+  const unsigned lane = threadIdx.x & 31;
+  const unsigned gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const unsigned nw = (gridDim.x * blockDim.x) >> 5;
+  const unsigned deg_s = totals[2];
+  for (unsigned r = gw; r < R; r += nw) {
+    if (!keep[r]) continue;
+    const unsigned beg = run_start[r], end = run_start[r + 1];
+    const unsigned ep = net_pos[r];
+    unsigned out = pin_pos[r];
+    const int e = run_net[r];
+    if (lane == 0) {
+      nnet_off[ep] = out;
+      nnet_w[ep] = net_w[e];
+      nnet_gid[ep] = e;
+    }
+    for (unsigned j0 = beg; j0 < end; j0 += 32) {
+      const unsigned j = j0 + lane;
+      int l = -1;
+      if (j < end) {
+        l = val[j];
+        const int sd = side[region[l - 2]];
+        if (sd != 0 && sd != 1) l = -1;
+      }
+      const unsigned mk = __ballot_sync(FULLB, l >= 0);
+      if (l >= 0) npin[out + __popc(mk & ((1u << lane) - 1u))] = l;
+      out += __popc(mk);
+    }
+    if (lane == 0) {
+      if (has_s_flag[r]) {
+        npin[out] = 0;
+        inc[s_pos[r]] = make_int2((int)ep, (int)out);
+        out++;
+      }
+      if (has_t_flag[r]) {
+        npin[out] = 1;
+        inc[deg_s + t_pos[r]] = make_int2((int)ep, (int)out);
+        out++;
+      }
+    }
+  }
+}
+
 static inline unsigned blocks_for(unsigned long long work, unsigned per_block, unsigned cap) {
   unsigned long long b = (work + per_block - 1) / per_block;
   if (b < 1) b = 1;
@@ -703,6 +889,98 @@ void launch_st_inc(int32_t m, const uint32_t* off, const unsigned* keep, const u
   if (m <= 0) return;
   k_st_inc<<<blocks_for(m, 256, sms * 8), 256, 0, st>>>(m, off, keep, new_e, has_s, has_t, pos_s,
                                                        pos_t, node_off, n_off, inc);
+  count_launches(1);
+}
+
+// Second construction algorithm, pass 1: the region's (net, vertex) pairs
+// sorted by net; returns the number of nets touching the region (*R) and
+// fills run_start[R + 1] / run_net[R] (buffers of at least the pair count;
+// key/val and key2/val2 of the pair count).  Synchronises.
+cudaError_t sort_build_count(int32_t nr, const int32_t* region, const uint32_t* vnet_off,
+                             unsigned* deg, unsigned* scr, unsigned* tot, unsigned* n_pairs,
+                             int sms, cudaStream_t st) {
+  *n_pairs = 0;
+  if (nr <= 0) return cudaSuccess;
+  k_sb_deg<<<blocks_for(nr, 256, sms * 8), 256, 0, st>>>(nr, region, vnet_off, deg);
+  count_launches(1);
+  scan_exclusive(deg, (unsigned)nr, scr, tot, st);
+  cudaError_t ce = cudaMemcpyAsync(n_pairs, tot, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+  return ce;
+}
+
+cudaError_t sort_build_runs(int32_t nr, const int32_t* region, const uint32_t* vnet_off,
+                            const int32_t* vnet, int32_t m, unsigned P2, const unsigned* pos,
+                            unsigned* scr, unsigned* tot, unsigned* key, int32_t* val,
+                            unsigned* key2, int32_t* val2, unsigned* hist, unsigned* head,
+                            unsigned* rid, unsigned* run_start, int32_t* run_net, unsigned* R,
+                            int sms, cudaStream_t st) {
+  *R = 0;
+  cudaError_t ce = cudaSuccess;
+  if (P2 == 0) return cudaSuccess;
+  k_sb_pairs<<<blocks_for(nr, 256, sms * 8), 256, 0, st>>>(nr, region, vnet_off, vnet, pos, key,
+                                                           val);
+  count_launches(1);
+  const unsigned T = (P2 + kRsTile - 1) / kRsTile;
+  int bits = 1;
+  while (bits < 31 && (1u << bits) < (unsigned)m) bits++;
+  unsigned *ka = key, *kb = key2;
+  int32_t *va = val, *vb = val2;
+  for (int shift = 0; shift < bits; shift += 8) {
+    k_rs_count<<<T, kRsTile, 0, st>>>(P2, ka, shift, T, hist);
+    scan_exclusive(hist, 256 * T, scr, tot, st);
+    k_rs_scatter<<<T, kRsTile, 0, st>>>(P2, ka, va, shift, T, hist, kb, vb);
+    count_launches(2);
+    std::swap(ka, kb);
+    std::swap(va, vb);
+  }
+  // the sorted pairs end in key / val
+  if (ka != key) {
+    ce = cudaMemcpyAsync(key, ka, sizeof(unsigned) * P2, cudaMemcpyDeviceToDevice, st);
+    if (ce == cudaSuccess)
+      ce = cudaMemcpyAsync(val, va, sizeof(int32_t) * P2, cudaMemcpyDeviceToDevice, st);
+    if (ce != cudaSuccess) return ce;
+  }
+  // runs of equal nets
+  k_sb_heads<<<blocks_for(P2, 256, sms * 8), 256, 0, st>>>(P2, key, head);
+  count_launches(1);
+  ce = cudaMemcpyAsync(rid, head, sizeof(unsigned) * P2, cudaMemcpyDeviceToDevice, st);
+  if (ce != cudaSuccess) return ce;
+  scan_exclusive(rid, P2, scr, tot, st);
+  k_sb_runs<<<blocks_for(P2, 256, sms * 8), 256, 0, st>>>(P2, key, head, rid, run_start, run_net);
+  k_sb_end<<<1, 1, 0, st>>>(run_start, tot, P2);
+  count_launches(2);
+  unsigned r = 0;
+  ce = cudaMemcpyAsync(&r, tot, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+  *R = r;
+  return ce;
+}
+
+void launch_sb_eval(unsigned R, const unsigned* run_start, const int32_t* run_net,
+                    const int32_t* val, const int32_t* region, const int32_t* side,
+                    const int32_t* net_w, const unsigned long long* mask, const unsigned* noff,
+                    const unsigned* cnt, int32_t b0, int32_t b1, unsigned* keep, unsigned* size,
+                    unsigned* has_s, unsigned* has_t, unsigned long long* wnet, int sms,
+                    cudaStream_t st) {
+  if (R == 0) return;
+  k_sb_eval<<<blocks_for(R, 256, sms * 8), 256, 0, st>>>(R, run_start, run_net, val, region, side,
+                                                         net_w, mask, noff, cnt, b0, b1, keep,
+                                                         size, has_s, has_t, wnet);
+  count_launches(1);
+}
+
+void launch_sb_fill(unsigned R, const unsigned* run_start, const int32_t* run_net,
+                    const int32_t* val, const int32_t* side, const int32_t* region,
+                    const int32_t* net_w, const unsigned* keep, const unsigned* net_pos,
+                    const unsigned* pin_pos, const unsigned* s_pos, const unsigned* t_pos,
+                    const unsigned* has_s, const unsigned* has_t, const unsigned* totals,
+                    uint32_t* nnet_off, int32_t* npin, int32_t* nnet_w, int32_t* nnet_gid,
+                    int2* inc, int sms, cudaStream_t st) {
+  if (R == 0) return;
+  k_sb_fill<<<blocks_for((unsigned long long)R * 32, 256, sms * 16), 256, 0, st>>>(
+      R, run_start, run_net, val, side, region, net_w, keep, net_pos, pin_pos, s_pos, t_pos,
+      has_s, has_t, totals, nnet_off, npin, nnet_w, nnet_gid, inc);
   count_launches(1);
 }
 

@@ -66,6 +66,7 @@ struct hfp_ctx {
   uint32_t identical_nets = 0;     // hfp_tuning.identical_nets
   uint32_t batch_fused_rounds = 1; // hfp_tuning.batch_fused_rounds
   uint32_t batch_async_gr = 0;     // hfp_tuning.batch_async_gr
+  uint32_t construction = 1;       // hfp_tuning.construction
   // group time per engine state of the batched launches since the last reset
   uint64_t batch_ns[hfp::kStateSlots] = {};
   uint64_t batch_cnt[hfp::kStateSlots] = {};
@@ -136,14 +137,30 @@ struct BatchItem {
   int32_t group_ctas = 0;          // CTAs of the group that solved it
 };
 
+// Inputs of the second construction algorithm (Section 6) for a block pair:
+// H's vertex -> nets incidence (ascending), the nets' block masks, the pins
+// of every (net, block) pair at cnt[noff[e] + rank of the block in mask[e]],
+// and the pair's blocks (side 0 = b0, side 1 = b1).
+struct SortBuildIn {
+  const uint32_t* vnet_off;
+  const int32_t* vnet;
+  const unsigned long long* mask;
+  const unsigned* noff;
+  const unsigned* cnt;
+  int32_t b0, b1;
+};
+
 // hfp_build_flow_network with optional restrictions (device inputs only):
 // nets[n_nets] (ascending) holds every net of H with a pin in the region, and
 // verts[n_verts] every vertex whose side is 0 or 1; only those are scanned.
-// Null lists scan all of H.
+// Null lists scan all of H.  With sb (and distances given) the nets come from
+// the region's incidences sorted by net instead (the second construction
+// algorithm); the network is the same.
 hfp_status build_network_impl(hfp_ctx* ctx, const hfp_hypergraph* H, hfp_mem mem,
                               const int32_t* region, int32_t n_region, const int32_t* side,
                               const int32_t* dist_from_cut, const int32_t* nets, int32_t n_nets,
-                              const int32_t* verts, int32_t n_verts, hfp_net** out);
+                              const int32_t* verts, int32_t n_verts, hfp_net** out,
+                              const SortBuildIn* sb = nullptr);
 
 // Allocates the buffers of one-phase rounds (P.fused_rounds) and queue-driven
 // global relabels (P.async_gr) that the network does not have yet (api.cu).

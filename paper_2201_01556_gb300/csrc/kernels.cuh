@@ -46,6 +46,36 @@ void launch_dist_copy(int32_t n_region, const int32_t* dist_in, int32_t* dist, i
                       cudaStream_t st);
 void launch_st_attrs(int32_t* node_gid, int32_t* node_w, int8_t* node_orig,
                      const unsigned long long* wsum, uint8_t* flags, int* err, cudaStream_t st);
+// Second construction algorithm (Section 6).  sort_build_count: the number
+// of (net, vertex) pairs of the region (deg[nr] becomes their offsets);
+// synchronises.  sort_build_runs: the pairs sorted by net (stable) as runs
+// run_start[R + 1] / run_net[R] over key / val (key2 / val2: second buffers;
+// head, rid: scratch of the pair count; hist: 256 counters per tile of 512
+// pairs); synchronises.  Then per run the first algorithm's keep / size /
+// s / t rules from the pins of blocks b0 / b1 in H (cnt[noff[e] + rank of the
+// block in mask[e]]), and the fill of the kept nets.
+cudaError_t sort_build_count(int32_t nr, const int32_t* region, const uint32_t* vnet_off,
+                             unsigned* deg, unsigned* scr, unsigned* tot, unsigned* n_pairs,
+                             int sms, cudaStream_t st);
+cudaError_t sort_build_runs(int32_t nr, const int32_t* region, const uint32_t* vnet_off,
+                            const int32_t* vnet, int32_t m, unsigned P2, const unsigned* pos,
+                            unsigned* scr, unsigned* tot, unsigned* key, int32_t* val,
+                            unsigned* key2, int32_t* val2, unsigned* hist, unsigned* head,
+                            unsigned* rid, unsigned* run_start, int32_t* run_net, unsigned* R,
+                            int sms, cudaStream_t st);
+void launch_sb_eval(unsigned R, const unsigned* run_start, const int32_t* run_net,
+                    const int32_t* val, const int32_t* region, const int32_t* side,
+                    const int32_t* net_w, const unsigned long long* mask, const unsigned* noff,
+                    const unsigned* cnt, int32_t b0, int32_t b1, unsigned* keep, unsigned* size,
+                    unsigned* has_s, unsigned* has_t, unsigned long long* wnet, int sms,
+                    cudaStream_t st);
+void launch_sb_fill(unsigned R, const unsigned* run_start, const int32_t* run_net,
+                    const int32_t* val, const int32_t* side, const int32_t* region,
+                    const int32_t* net_w, const unsigned* keep, const unsigned* net_pos,
+                    const unsigned* pin_pos, const unsigned* s_pos, const unsigned* t_pos,
+                    const unsigned* has_s, const unsigned* has_t, const unsigned* totals,
+                    uint32_t* nnet_off, int32_t* npin, int32_t* nnet_w, int32_t* nnet_gid,
+                    int2* inc, int sms, cudaStream_t st);
 // identical net removal (Section 6): group tags, smallest id per group and
 // representatives; merged weights and kept-net flags / sizes / s-t
 // membership; compaction; new totals; s / t incidences of the kept nets

@@ -309,6 +309,28 @@ __global__ void k_list_scatter(unsigned cnt, const int32_t* list, const unsigned
     }
 }
 
+// pins of a net in each block of its mask, at cnt[noff[e] + rank of the block
+// in the mask] (a warp per net)
+__global__ void k_mask_popc(int32_t m, const unsigned long long* mask, unsigned* out) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m; e += gridDim.x * blockDim.x)
+    out[e] = __popcll(mask[e]);
+}
+
+__global__ void k_net_block_counts(int32_t m, const uint32_t* net_off, const int32_t* pins,
+                                   const int32_t* part, const unsigned long long* mask,
+                                   const unsigned* noff, unsigned* cnt) {
+  const unsigned lane = threadIdx.x & 31;
+  const unsigned gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const unsigned nw = (gridDim.x * blockDim.x) >> 5;
+  for (unsigned e = gw; e < (unsigned)m; e += nw) {
+    const unsigned long long mk = mask[e];
+    for (unsigned j = net_off[e] + lane; j < net_off[e + 1]; j += 32) {
+      const int b = part[pins[j]];
+      atomicAdd(&cnt[noff[e] + __popcll(mk & ((1ull << b) - 1ull))], 1u);
+    }
+  }
+}
+
 // block list offsets from the scanned tile counts: out[b] = start of block b,
 // out[k] = total
 __global__ void k_grp_offsets(const unsigned* C, unsigned T, int k, const unsigned* total,
@@ -603,9 +625,39 @@ struct RegionScratch {
 // The vertices and the nets of every block in ascending order, the nets'
 // block masks and the block weights, for one partition (k <= 64).
 struct BlockLists {
-  DevBuf nmask, C, bv, bn, offs;
+  DevBuf nmask, C, bv, bn, offs, noff, cnt;
   std::vector<unsigned> bv_off, bn_off;     // k + 1 each
   std::vector<unsigned long long> bw;       // k
+  bool counts = false;                      // noff / cnt built
+  // pins of every (net, block) pair, for the second construction algorithm
+  hfp_status build_counts(hfp_hgraph* hg, const int32_t* part) {
+    if (counts) return HFP_OK;
+    cudaStream_t st = hg->ctx->stream;
+    const int m = hg->m, sms = hg->ctx->sms;
+    CK(noff.alloc(sizeof(unsigned) * (m + 1), st));
+    unsigned total = 0;
+    if (m) {
+      DevBuf scr, tot;
+      CK(scr.alloc(sizeof(unsigned) * (scan_scratch_words((unsigned)m) + 8), st));
+      CK(tot.alloc(sizeof(unsigned), st));
+      k_mask_popc<<<nb(m, 256, sms * 8), 256, 0, st>>>(m, nmask.as<unsigned long long>(),
+                                                       noff.as<unsigned>());
+      count_launches(1);
+      scan_exclusive(noff.as<unsigned>(), (unsigned)m, scr.as<unsigned>(), tot.as<unsigned>(), st);
+      CK(cudaMemcpyAsync(&total, tot.p, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+    }
+    CK(cnt.alloc(sizeof(unsigned) * (total > 0 ? total : 1), st));
+    CK(cudaMemsetAsync(cnt.p, 0, sizeof(unsigned) * (total > 0 ? total : 1), st));
+    if (m) {
+      k_net_block_counts<<<nb((long long)m * 32, 256, sms * 16), 256, 0, st>>>(
+          m, hg->net_off, hg->pins, part, nmask.as<unsigned long long>(), noff.as<unsigned>(),
+          cnt.as<unsigned>());
+      count_launches(1);
+    }
+    counts = true;
+    return HFP_OK;
+  }
   hfp_status build(hfp_hgraph* hg, const int32_t* part, int32_t k) {
     hfp_ctx* ctx = hg->ctx;
     cudaStream_t st = ctx->stream;
@@ -698,7 +750,7 @@ hfp_status compact_list(hfp_hgraph* hg, unsigned cnt, const int32_t* list, unsig
 // cut on the network's nets.  Everything but the flow network's own
 // construction works on the two blocks' vertex and net lists.
 hfp_status prepare_pair(hfp_hgraph* hg, const int32_t* part, int32_t k, int32_t bi, int32_t bj,
-                        const hfp_refine_params* prm, RegionScratch& sc, const BlockLists& bl,
+                        const hfp_refine_params* prm, RegionScratch& sc, BlockLists& bl,
                         PairWork& w) {
   hfp_ctx* ctx = hg->ctx;
   cudaStream_t st = ctx->stream;
@@ -793,10 +845,24 @@ hfp_status prepare_pair(hfp_hgraph* hg, const int32_t* part, int32_t k, int32_t 
   }
   w.nr = (int32_t)nr;
   res->region_size = (int32_t)nr;
-  // nets of the network: those of block bi, and those of block bj without a
-  // pin in bi, merged into ascending order; vertices: both blocks
+  // Construction (Section 6): the first algorithm scans the nets of the two
+  // blocks, the second sorts the region's incidences by net; the paper takes
+  // the second for sparse hypergraphs (|E| / |V| <= 0.5) or large nets
+  // (average size >= 100), and so does the automatic choice here
+  const uint32_t cmode = ctx->construction;
+  const bool sorted_build =
+      cmode == 2 || (cmode == 0 && ((long long)m * 2 <= (long long)n || hg->p >= 100ll * m));
+  SortBuildIn sbi{};
+  if (sorted_build) {
+    if (hfp_status r0 = bl.build_counts(hg, part)) return r0;
+    sbi = SortBuildIn{hg->vnet_off, hg->vnet, nmask, bl.noff.as<unsigned>(),
+                      bl.cnt.as<unsigned>(), bi, bj};
+  }
+  // nets of the network (first algorithm): those of block bi, and those of
+  // block bj without a pin in bi, merged into ascending order; vertices: both
+  // blocks
   unsigned nj2 = 0;
-  if (nnj) {
+  if (nnj && !sorted_build) {
     k_net_not_in<<<nb(nnj, 256, sms * 8), 256, 0, st>>>(nnj, Nj, nmask, bi,
                                                         sc.flag.as<unsigned>());
     count_launches(1);
@@ -805,7 +871,7 @@ hfp_status prepare_pair(hfp_hgraph* hg, const int32_t* part, int32_t k, int32_t 
                                 sc.tot.as<unsigned>(), &nj2);
     if (r != HFP_OK) return r;
   }
-  const unsigned nnet = nni + nj2;
+  const unsigned nnet = sorted_build ? 0u : nni + nj2;
   if (nnet) {
     k_merge_sorted<<<nb(nnet, 256, sms * 8), 256, 0, st>>>(Ni, nni, sc.nets2.as<int32_t>(), nj2,
                                                            sc.netlist.as<int32_t>());
@@ -819,7 +885,8 @@ hfp_status prepare_pair(hfp_hgraph* hg, const int32_t* part, int32_t k, int32_t 
   hfp_status r = build_network_impl(ctx, &Hd, HFP_MEM_DEVICE, w.region.as<int32_t>(), (int32_t)nr,
                                     side, dist.as<int32_t>(), sc.netlist.as<int32_t>(),
                                     (int32_t)nnet, sc.vlist.as<int32_t>(),
-                                    (int32_t)(nv[0] + nv[1]), &w.net);
+                                    (int32_t)(nv[0] + nv[1]), &w.net,
+                                    sorted_build ? &sbi : nullptr);
   // the two blocks' entries go back for the next pair
   for (int s = 0; s < 2; s++)
     if (nv[s]) {
@@ -903,7 +970,7 @@ hfp_status finish_pair(hfp_hgraph* hg, const int32_t* part, hfp_status fc, const
 // One pair, one problem per launch sequence: region, network, FlowCutter
 // (hfp_flowcutter), moves.
 hfp_status refine_pair(hfp_hgraph* hg, const int32_t* part, int32_t k, int32_t bi, int32_t bj,
-                       const hfp_refine_params* prm, RegionScratch& sc, const BlockLists& bl,
+                       const hfp_refine_params* prm, RegionScratch& sc, BlockLists& bl,
                        DevBuf& moves_dev, hfp_pair_result* res) {
   PairWork w;
   hfp_status s = prepare_pair(hg, part, k, bi, bj, prm, sc, bl, w);

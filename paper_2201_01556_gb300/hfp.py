@@ -56,7 +56,8 @@ class Tuning(ctypes.Structure):
                                                "batch_big_ctas", "batch_big_groups",
                                                "async_gr", "gr_warps", "fused_rounds",
                                                "identical_nets", "batch_fused_rounds",
-                                               "batch_async_gr", "parpr_block")]
+                                               "batch_async_gr", "parpr_block",
+                                               "construction")]
 
 
 class RefineParams(ctypes.Structure):

@@ -116,3 +116,45 @@ def test_round_certificate_1M(env):
     assert applied and all(p.gain >= 0 for p in applied)
     assert sum(p.gain for p in applied) == stats.gain
     hg.close()
+
+
+def _with_construction(hfp, ctx, mode):
+    t = hfp.ctx_get_tuning(ctx)
+    hfp.ctx_set_tuning(ctx, construction=mode)
+    return t
+
+
+@pytest.mark.parametrize("seed,n,m,k", [(7, 16000, 24000, 64), (8, 30000, 12000, 16)])
+def test_sorted_construction_matches_oracle(env, seed, n, m, k):
+    """The second construction algorithm (Section 6: the region's incidences
+    sorted by net) gives the networks of the first: every refined pair's
+    region, pin count, original cut, flow and moves equal the oracle's (whose
+    construction is the first algorithm's), and so does a whole round.  The
+    second case is a sparse hypergraph (|E| < |V| / 2), where the automatic
+    choice takes the sorted construction."""
+    torch, hfp, ctx = env
+    H, part, hg, pd = _setup(env, seed, n, m, k)
+    qn, _ = oracle.quotient(H, part, k)
+    pairs = [(i, j) for i in range(k) for j in range(i + 1, k) if qn[i, j] > 0]
+    rng = np.random.default_rng(seed)
+    pick = [pairs[t] for t in rng.choice(len(pairs), min(12, len(pairs)), replace=False)]
+    base = _with_construction(hfp, ctx, 2)
+    try:
+        for i, j in pick:
+            o = oracle.refine_block_pair(H, part, k, i, j, seed=7)
+            g, mv = hfp.refine_block_pair(hg, pd, k, i, j, hfp.refine_params(seed=7))
+            assert (g.status, g.region_size, g.original_cut, g.pins) == (
+                o.status, o.region_size, o.original_cut, o.pins), (i, j)
+            if o.status == oracle.OK:
+                assert g.flow == o.flow and g.delta_exp == o.delta_exp
+                assert np.array_equal(mv, o.moves)
+        newp, total, _, _ = oracle.refine_round(H, part, k, seed=5)
+        for mode in (0, 2):
+            hfp.ctx_set_tuning(ctx, construction=mode)
+            pd2 = torch.from_numpy(part.copy()).cuda()
+            stats, _, _ = hfp.refine_round_batched(hg, pd2, k, hfp.refine_params(seed=5),
+                                                   group_ctas=4)
+            assert stats.gain == total
+            assert np.array_equal(pd2.cpu().numpy(), newp)
+    finally:
+        hfp.ctx_set_tuning(ctx, **base)

@@ -18,9 +18,10 @@ time at equal connectivity - 1):
     are split across them);
   - "compare": from one start partition of the same generator at a smaller
     size, the plain round (one FlowCutter problem after another), the batched
-    round (identical partitions) and the batched round pruned by the learned
-    scheduler with the committed weights (train_scheduler.py), to convergence
-    or a round limit: seconds, pairs refined and final (lambda - 1) per arm;
+    round (identical partitions), the batched round pruned by the learned
+    scheduler with the committed weights (train_scheduler.py), and batched
+    rounds under the paper's active block scheduling, to convergence or a
+    round limit: seconds, pairs refined and final (lambda - 1) per arm;
   - every round's (lambda - 1) recomputed on the host from the returned
     partition ("certificate").
 
@@ -272,6 +273,9 @@ def kway_compare(hfp, ctx, args):
         out["learned_vs_unpruned"] <= 0.005
     out["speedup_batched_over_plain"] = out["plain"]["seconds"] / out["batched"]["seconds"]
     out["speedup_learned_over_plain"] = out["plain"]["seconds"] / out["learned"]["seconds"]
+    if "active" in out and b:
+        out["active_vs_unpruned"] = out["active"]["connectivity_minus_1"] / b - 1.0
+        out["speedup_active_over_plain"] = out["plain"]["seconds"] / out["active"]["seconds"]
     out["scheduler_training"] = loaded[1]
     return out
 

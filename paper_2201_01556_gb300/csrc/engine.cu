@@ -1613,34 +1613,13 @@ __device__ __forceinline__ unsigned long long gq_entry(int z, unsigned chunk, in
          (unsigned)z;
 }
 
-// Chunks node z (flag byte f) takes in the queue when `want` (0 otherwise).
-__device__ __forceinline__ unsigned gq_count(const NetDev& N, bool want, int z, uint8_t f) {
-  return want ? ((f & kHeavy) ? gq_chunks(node_arcs(N, z).items) : 1u) : 0u;
-}
-
-// The chunks of the multi-chunk entries of the lanes in `big`, written by
-// the whole warp (slot s, count cnt, node z and label d of each such lane;
-// the teams of a warp expand entries of different labels).
-__device__ __forceinline__ void gq_write_big(const NetDev& N, unsigned big, unsigned s, unsigned cnt,
-                                             int z, int d) {
+// Queue every chunk of node z (label d, flag byte f) for the lanes with
+// `want`.  Warp-collective: one tail atomic per warp; the chunks of large
+// nodes are written by the whole warp.
+__device__ void gq_push(const NetDev& N, EngineCtl* E, bool want, int z, uint8_t f, int d) {
   const unsigned lane = lane_id();
-  while (big) {
-    const int src = __ffs(big) - 1;
-    big &= big - 1;
-    const unsigned bs = __shfl_sync(FULL, s, src), bc = __shfl_sync(FULL, cnt, src);
-    const int bz = __shfl_sync(FULL, z, src), bd = __shfl_sync(FULL, d, src);
-    for (unsigned c = lane; c < bc; c += 32) st_release_u64(&N.gq[bs + c], gq_entry(bz, c, bd));
-  }
-}
-
-// Queue every chunk of nodes z1 (flag byte f1) and z2 (f2), with the lane's
-// label d, for the lanes with want1 / want2.  Warp-collective: one tail atomic per warp; the
-// chunks of large nodes are written by the whole warp.
-__device__ void gq_push2(const NetDev& N, EngineCtl* E, bool want1, int z1, uint8_t f1,
-                         bool want2, int z2, uint8_t f2, int d) {
-  const unsigned lane = lane_id();
-  const unsigned cnt1 = gq_count(N, want1, z1, f1), cnt2 = gq_count(N, want2, z2, f2);
-  const unsigned cnt = cnt1 + cnt2;
+  unsigned cnt = 0;
+  if (want) cnt = (f & kHeavy) ? gq_chunks(node_arcs(N, z).items) : 1u;
   unsigned incl = cnt;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -1652,17 +1631,20 @@ __device__ void gq_push2(const NetDev& N, EngineCtl* E, bool want1, int z1, uint
   unsigned base = 0;
   if (lane == 31) base = atomicAdd(&E->gq_tail, total);
   base = __shfl_sync(FULL, base, 31);
-  const unsigned s1 = base + incl - cnt, s2 = s1 + cnt1;
-  const bool fits = s1 <= N.gq_cap && N.gq_cap - s1 >= cnt;
+  const unsigned s0 = base + incl - cnt;
+  const bool fits = s0 <= N.gq_cap && N.gq_cap - s0 >= cnt;
   if (cnt && !fits) *(volatile unsigned*)&E->gq_over = 1u;
-  if (fits && cnt1 == 1) st_release_u64(&N.gq[s1], gq_entry(z1, 0, d));
-  if (fits && cnt2 == 1) st_release_u64(&N.gq[s2], gq_entry(z2, 0, d));
-  const unsigned big1 = __ballot_sync(FULL, fits && cnt1 > 1);
-  const unsigned big2 = __ballot_sync(FULL, fits && cnt2 > 1);
-  if (!(big1 | big2)) return;
+  if (cnt == 1 && fits) st_release_u64(&N.gq[s0], gq_entry(z, 0, d));
+  unsigned big = __ballot_sync(FULL, cnt > 1 && fits);
+  if (!big) return;
   __syncwarp();   // every lane's label update is ordered before the other lanes' stores
-  gq_write_big(N, big1, s1, cnt1, z1, d);
-  gq_write_big(N, big2, s2, cnt2, z2, d);
+  while (big) {
+    const int src = __ffs(big) - 1;
+    big &= big - 1;
+    const unsigned bs = __shfl_sync(FULL, s0, src), bc = __shfl_sync(FULL, cnt, src);
+    const int bz = __shfl_sync(FULL, z, src), bd = __shfl_sync(FULL, d, src);
+    for (unsigned c = lane; c < bc; c += 32) st_release_u64(&N.gq[bs + c], gq_entry(bz, c, bd));
+  }
 }
 
 // Seeding: every sink (the BFS list of ST_GR_INIT, label 0) enters the queue.
@@ -1678,56 +1660,37 @@ __device__ void gr_seed(const NetDev& N, EngineCtl* E, const Sched& L, const Tea
       y = i < nl ? bl[i] : bl[N.NL - 1 - (i - nl)];
       f = N.flags[y];
     }
-    gq_push2(N, E, y >= 0, y, f, false, -1, 0, 0);
+    gq_push(N, E, y >= 0, y, f, 0);
   }
 }
 
-// Labels of z1 and z2 (distinct or -1) lowered to d1 when larger (sources
-// never take labels).  On its first label a node's weight joins T_r and,
-// with excess, it joins the frontier.  Warp-collective; queues the lanes'
-// lowered nodes with one tail atomic per warp.  True when either dropped.
-__device__ __forceinline__ bool gq_relax2(const NetDev& N, EngineCtl* E, const Slot& S, int z1,
-                                          int z2, int d1, Acc& a) {
-  bool imp1 = false, imp2 = false, first1 = false, first2 = false;
-  uint8_t f1 = 0, f2 = 0;
-  int cur1 = 0, cur2 = 0;
-  if (z1 >= 0) {
-    cur1 = __ldcg(&N.lab0[z1]);
-    f1 = N.flags[z1];
-  }
-  if (z2 >= 0) {
-    cur2 = __ldcg(&N.lab0[z2]);
-    f2 = N.flags[z2];
-  }
-  if (z1 >= 0 && cur1 > d1 && !(f1 & kSource)) {
-    const int old = atomicMin(&N.lab0[z1], d1);
-    if (old > d1) {
-      imp1 = true;
-      atomicMin(&N.lab1[z1], d1);
-      first1 = old == N.NL;
+// Label of z lowered to d1 when larger (sources never take labels).  On the
+// first label the node's weight joins T_r and, with excess, it joins the
+// frontier.  Warp-collective; queues the lanes' lowered nodes.
+__device__ __forceinline__ bool gq_relax(const NetDev& N, EngineCtl* E, const Slot& S, int z,
+                                         int d1, Acc& a) {
+  bool imp = false, first = false;
+  uint8_t f = 0;
+  if (z >= 0) {
+    const int cur = __ldcg(&N.lab0[z]);
+    f = N.flags[z];
+    if (cur > d1 && !(f & kSource)) {
+      const int old = atomicMin(&N.lab0[z], d1);
+      if (old > d1) {
+        imp = true;
+        atomicMin(&N.lab1[z], d1);
+        first = old == N.NL;
+      }
     }
   }
-  if (z2 >= 0 && cur2 > d1 && !(f2 & kSource)) {
-    const int old = atomicMin(&N.lab0[z2], d1);
-    if (old > d1) {
-      imp2 = true;
-      atomicMin(&N.lab1[z2], d1);
-      first2 = old == N.NL;
-    }
+  gq_push(N, E, imp, z, f, d1);
+  bool act = false;
+  if (first) {
+    if (z < N.n_nodes) a.w += N.node_w[z];
+    act = N.excess[z] > 0;
   }
-  gq_push2(N, E, imp1, z1, f1, imp2, z2, f2, d1);
-  bool act1 = false, act2 = false;
-  if (first1) {
-    if (z1 < N.n_nodes) a.w += N.node_w[z1];
-    act1 = N.excess[z1] > 0;
-  }
-  if (first2) {
-    if (z2 < N.n_nodes) a.w += N.node_w[z2];
-    act2 = N.excess[z2] > 0;
-  }
-  append_split2(act1, z1, (f1 & kHeavy) != 0, act2, z2, (f2 & kHeavy) != 0, N.list[L_FRONT],
-                S.act[0], S.act[1], 0, 0, N.NL);
-  return imp1 || imp2;
+  append_split(act, z, (f & kHeavy) != 0, N.list[L_FRONT], S.act[0], S.act[1], 0, 0, N.NL);
+  return imp;
 }
 
 // Expand chunk c of node x queued with label d (x < 0: idle team): relax
@@ -1758,39 +1721,31 @@ __device__ void gq_expand(const NetDev& N, EngineCtl* E, const Slot& S, int x, u
     const unsigned k = k0 + st * TW + tl;
     int c1 = -1, c2 = -1;
     if (k < k1) rev_arcs(N, g, k, w, fb, c1, c2, a);
-    if (gq_relax2(N, E, S, c1, c2, d1, a)) maxd = max(maxd, (unsigned)d1);
+    const bool i1 = gq_relax(N, E, S, c1, d1, a);
+    const bool i2 = gq_relax(N, E, S, c2, d1, a);
+    if (i1 || i2) maxd = max(maxd, (unsigned)d1);
   }
 }
 
 // The search itself: warps below P.gr_warps of every CTA serve the queue,
 // four 8-lane teams per warp, until it is finished, overflowed, or an error
-// or the time bound stops it.  A team claims kGqClaim consecutive slots at a
-// time (one head atomic per warp for all its teams); more than one slot per
-// claim takes entries further out of queue order, and the search then
-// corrects more labels (2 slots: 75 % more entries on the 2M-vertex ring).
-// A warp adds its finished entries to gq_done in batches, flushed before it
-// waits or polls for the end: delaying a done count only delays the end.
-constexpr unsigned kGqClaim = 1;
-constexpr unsigned kGqDoneBatch = 32;
-
+// or the time bound stops it.
 __device__ void gr_run(const NetDev& N, EngineCtl* E, const Sched& L, const Slot& S,
                        unsigned lane, Acc& a, const Params& P) {
   if ((threadIdx.x >> 5) >= P.gr_warps) return;
+  constexpr unsigned NONE = 0xffffffffu;
   const unsigned tl = lane & (kTeam - 1), lead = lane & ~(unsigned)(kTeam - 1);
-  unsigned slot = 0, left = 0, maxd = 0, idle = 0, pend = 0;
+  unsigned slot = NONE, maxd = 0, idle = 0;
   unsigned long long t0 = 0;
   for (;;) {
-    // slots for the teams that have none left: one atomic per warp
-    const unsigned m = __ballot_sync(FULL, left == 0 && tl == 0);
+    // slots for the teams that have none: one atomic per warp
+    const unsigned m = __ballot_sync(FULL, slot == NONE && tl == 0);
     if (m) {
       const int ld = __ffs(m) - 1;
       unsigned base = 0;
-      if ((int)lane == ld) base = atomicAdd(&E->gq_head, (unsigned)__popc(m) * kGqClaim);
+      if ((int)lane == ld) base = atomicAdd(&E->gq_head, (unsigned)__popc(m));
       base = __shfl_sync(FULL, base, ld);
-      if (left == 0) {
-        slot = base + kGqClaim * __popc(m & ((1u << lead) - 1u));
-        left = kGqClaim;
-      }
+      if (slot == NONE) slot = base + __popc(m & ((1u << lead) - 1u));
     }
     unsigned long long ent = 0;
     if (tl == 0 && slot < N.gq_cap) ent = ld_acquire_u64(&N.gq[slot]);
@@ -1802,25 +1757,12 @@ __device__ void gr_run(const NetDev& N, EngineCtl* E, const Sched& L, const Slot
       const unsigned c = ready ? (unsigned)(ent >> kGqNodeBits) & (kGqMaxChunks - 1u) : 0u;
       const int d = ready ? (int)(ent >> 37) - 1 : 0;
       gq_expand<kTeam>(N, E, S, x, c, d, lane, a, maxd);
-      if (ready) {
-        slot++;
-        left--;
-      }
-      pend += (unsigned)__popc(rm) / kTeam;
-      if (pend >= kGqDoneBatch) {
-        __syncwarp();
-        if (lane == 0) red_release_add(&E->gq_done, pend);
-        pend = 0;
-      }
+      if (ready) slot = NONE;
+      __syncwarp();
+      if (lane == 0) red_release_add(&E->gq_done, (unsigned)__popc(rm) / kTeam);
       idle = 0;
       t0 = 0;
       continue;
-    }
-    if (pend) {
-      // before waiting or polling for the end, every finished entry is counted
-      __syncwarp();
-      if (lane == 0) red_release_add(&E->gq_done, pend);
-      pend = 0;
     }
     if ((++idle & 7u) == 0) {
       int stop = 0;

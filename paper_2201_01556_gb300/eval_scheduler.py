@@ -6,8 +6,9 @@
 Every arm starts from the same partition and runs up to `rounds` rounds
 (stopping at a round without gain): the plain round (hfp_refine_round, one
 FlowCutter problem at a time), the batched round (hfp_refine_round_batched,
-identical outcome), and the batched round pruned by the learned scheduler
-with the committed weights (train_scheduler).  Prints one JSON object with
+identical outcome), the batched round pruned by the learned scheduler with
+the committed weights (train_scheduler), and batched rounds under the
+paper's active block scheduling (scheduler.refine_active).  Prints one JSON object with
 per-arm totals: wall seconds, pairs refined, final (lambda - 1), and the
 relative (lambda - 1) difference of the learned arm to the unpruned one.
 """
@@ -38,6 +39,9 @@ def compare(hfp, scheduler, ctx, H, part, k, rounds, mlp_params, threshold=0.5, 
                              batched=batched)
         finals[name] = pd.cpu().numpy()
         out[name] = r
+    # the paper's active block scheduling (batched rounds)
+    pd = torch.from_numpy(part.copy()).cuda()
+    out["active"] = scheduler.refine_active(hg, pd, k, rounds)
     if plain:
         # the batched round is the plain round run differently: same partition
         out["plain"]["identical_to_batched"] = bool(np.array_equal(finals["plain"],
@@ -65,7 +69,8 @@ def main(argv=None):
         raise SystemExit("no committed scheduler weights: run train_scheduler first")
     params = torch.from_numpy(loaded[0]).cuda()
     ctx = hfp.ctx_create(0)
-    tot = {a: dict(seconds=0.0, pairs=0, connectivity=0) for a in ("plain", "batched", "learned")}
+    tot = {a: dict(seconds=0.0, pairs=0, connectivity=0)
+           for a in ("plain", "batched", "learned", "active")}
     rows = []
     for seed in [int(s) for s in args.seeds.split(",")]:
         inst = synth.instance("ring_n8M_zipf_k64", seed, n=args.n, m=args.n * 3 // 2)

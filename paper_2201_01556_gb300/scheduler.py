@@ -12,6 +12,13 @@ in libhfp's kernels; this file only sequences the calls:
   refine()    rounds with or without the scheduler, returning the
               connectivity trajectory and the wall time; a pruned round
               without gain is repeated unpruned before refinement stops.
+
+The paper's own pruning, active block scheduling (Section 5, "Parallel
+Active Block Scheduling"), is here too: refine_active() refines every pair
+in the first round and afterwards only the pairs with a block that an
+applied move set of the previous round improved, and stops when no block is
+active or a round improves (lambda - 1) by less than 0.1 %.  Its rounds are
+synchronous; the paper interleaves the rounds' pairs in one queue.
 """
 from __future__ import annotations
 
@@ -128,4 +135,46 @@ def refine(hg, part_dev, k: int, rounds: int, params=None, mlp_params=None,
             break
     torch.cuda.synchronize()
     return dict(connectivity=conn, pairs=refined, skipped=skipped, fallbacks=fallbacks,
+                seconds=time.perf_counter() - t0)
+
+
+def active_blocks(results, k: int) -> np.ndarray:
+    """Blocks of the pairs whose move set was applied with a positive gain."""
+    act = np.zeros(k, bool)
+    for r in results:
+        if r.applied and r.gain > 0:
+            act[r.bi] = act[r.bj] = True
+    return act
+
+
+def active_scores(active: np.ndarray) -> np.ndarray:
+    """Pair scores selecting the pairs with an active block (1) over the
+    others (0), for a round's min_score of 0.5."""
+    a = active.astype(np.float32)
+    return np.maximum(a[:, None], a[None, :]).astype(np.float32)
+
+
+def refine_active(hg, part_dev, k: int, rounds: int, params=None, min_rel_gain: float = 0.001,
+                  batched: bool = True):
+    """Rounds under active block scheduling (see the module docstring) ->
+    dict with the connectivity after each round, pairs refined and skipped,
+    and the wall time."""
+    import torch
+    params = params or hfp.refine_params()
+    conn, refined, skipped = [], 0, 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    scores = None
+    for _ in range(rounds):
+        stats, res = _round(hg, part_dev, k, params, scores, 0.5, batched)
+        refined += stats.pairs
+        skipped += stats.pairs_skipped
+        conn.append(int(stats.connectivity_after))
+        act = active_blocks(res, k)
+        before = int(stats.connectivity_before)
+        if not act.any() or stats.gain < min_rel_gain * max(before, 1):
+            break
+        scores = active_scores(act)
+    torch.cuda.synchronize()
+    return dict(connectivity=conn, pairs=refined, skipped=skipped, fallbacks=0,
                 seconds=time.perf_counter() - t0)

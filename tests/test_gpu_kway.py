@@ -158,3 +158,28 @@ def test_sorted_construction_matches_oracle(env, seed, n, m, k):
             assert np.array_equal(pd2.cpu().numpy(), newp)
     finally:
         hfp.ctx_set_tuning(ctx, **base)
+
+
+def test_active_block_rounds_match_oracle(env):
+    """Two rounds of active block scheduling (Section 5): the first refines
+    every pair, the second only the pairs with a block that an applied move
+    set improved; partition and connectivity equal the oracle's rounds on
+    the same pair sets."""
+    torch, hfp, ctx = env
+    from paper_2201_01556_gb300 import scheduler
+    H, part, hg, pd = _setup(env, 9, 16000, 24000)
+    p1, _, _, gains1 = oracle.refine_round(H, part, 64)
+    act = set()
+    for (i, j), (gain, applied, _) in gains1.items():
+        if applied and gain > 0:
+            act |= {i, j}
+    assert act
+    qn, _ = oracle.quotient(H, p1, 64)
+    pairs2 = [(i, j) for i in range(64) for j in range(i + 1, 64)
+              if qn[i, j] > 0 and (i in act or j in act)]
+    p2, _, _, _ = oracle.refine_round(H, p1, 64, pairs=pairs2)
+    r = scheduler.refine_active(hg, pd, 64, rounds=2, min_rel_gain=0.0)
+    assert r["connectivity"] == [oracle.connectivity(H, p1, 64), oracle.connectivity(H, p2, 64)]
+    assert np.array_equal(pd.cpu().numpy(), p2)
+    qn0, _ = oracle.quotient(H, part, 64)
+    assert r["pairs"] == int((np.triu(qn0, 1) > 0).sum()) + len(pairs2)

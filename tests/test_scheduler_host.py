@@ -106,3 +106,45 @@ def test_collect_labels_improving_pairs(monkeypatch):
     assert x.shape == (6, 16) and np.array_equal(x[:3], feats)
     assert y.tolist() == [1, 0, 0, 1, 0, 0]
     assert pins.tolist() == [10, 20, 30, 10, 20, 30]
+
+
+def test_active_blocks_and_scores():
+    """Active block scheduling (Section 5): a block is active after an
+    applied move set with positive gain on one of its pairs; the next round's
+    scores select exactly the pairs with an active block."""
+    R = types.SimpleNamespace
+    res = [R(bi=0, bj=1, gain=5, applied=1), R(bi=2, bj=3, gain=0, applied=1),
+           R(bi=1, bj=4, gain=7, applied=0), R(bi=3, bj=5, gain=2, applied=1)]
+    act = scheduler.active_blocks(res, 6)
+    assert act.tolist() == [True, True, False, True, False, True]
+    sc = scheduler.active_scores(act)
+    for i in range(6):
+        for j in range(6):
+            assert (sc[i, j] > 0.5) == (act[i] or act[j])
+
+
+def test_refine_active_stops_without_active_blocks(monkeypatch):
+    """The first round refines every pair; later rounds are pruned to active
+    blocks; refinement stops once a round activates no block, or improves
+    (lambda - 1) by less than the relative threshold."""
+    calls = []
+
+    def fake_round(hg, part, k, params, pair_scores=None, min_score=0.0):
+        calls.append(None if pair_scores is None else pair_scores.copy())
+        n = len(calls)
+        gain = {1: 50, 2: 20, 3: 0}[n]
+        st = types.SimpleNamespace(gain=gain, pairs=3, pairs_skipped=0 if n == 1 else 2,
+                                   connectivity_before=1000, connectivity_after=1000 - gain)
+        res = [types.SimpleNamespace(bi=n - 1, bj=n, gain=gain, applied=1 if gain else 0)]
+        return st, res, 1.0
+
+    monkeypatch.setattr(hfp, "refine_round_batched", fake_round)
+    monkeypatch.setattr(torch.cuda, "synchronize", lambda: None)
+    r = scheduler.refine_active(None, None, 4, rounds=10, min_rel_gain=0.0)
+    assert calls[0] is None
+    assert calls[1][0, 1] == 1.0 and calls[1][2, 3] == 0.0
+    assert calls[2][1, 2] == 1.0 and calls[2][0, 3] == 0.0
+    assert r["connectivity"] == [950, 980, 1000] and len(calls) == 3
+    calls.clear()
+    r = scheduler.refine_active(None, None, 4, rounds=10, min_rel_gain=0.03)
+    assert len(calls) == 2   # the second round gains 2 % < 3 %

@@ -253,16 +253,22 @@ __device__ __forceinline__ void team_walk_arcs(const NetDev& N, int x, unsigned 
 
 // The light nodes nodes[0 .. count) of a breadth-first level over the warps
 // of T: 32 per warp (warp_walk_arcs) when the level has more than kWalkMin
-// nodes per warp, else one per team, so that a small level still keeps
-// every warp busy.
+// nodes per warp, taken from the phase counter *grab (zero at the phase's
+// start) so that the warps finish together; else one per team, so that a
+// small level still keeps every warp busy.
 constexpr unsigned kWalkMin = 8;
 
 template <class Fn>
 __device__ __forceinline__ void level_light(const NetDev& N, const int32_t* nodes, unsigned count,
-                                            const Team& T, unsigned lane, Fn fn) {
+                                            const Team& T, unsigned lane, unsigned* grab, Fn fn) {
   if (count > kWalkMin * T.nwarps) {
-    for (unsigned base = T.gwarp * 32; base < count; base += T.nwarps * 32)
+    for (;;) {
+      unsigned base = 0;
+      if (lane == 0) base = atomicAdd(grab, 32u);
+      base = __shfl_sync(FULL, base, 0);
+      if (base >= count) break;
       warp_walk_arcs(N, nodes + base, min(32u, count - base), lane, fn);
+    }
   } else {
     constexpr unsigned TPW = 32 / kTeam;
     for (unsigned base = T.gwarp * TPW; base < count; base += T.nwarps * TPW) {
@@ -273,7 +279,8 @@ __device__ __forceinline__ void level_light(const NetDev& N, const int32_t* node
 }
 
 // The heavy nodes of a breadth-first level (heavy entries hb .. hb + count
-// of a split list), up to 32 per CTA step: warp 0 loads one node per lane,
+// of a split list), up to 32 per CTA step (taken from the phase counter
+// *grab, zero at the phase's start): warp 0 loads one node per lane,
 // and the CTA walks the concatenated arc groups of those nodes blockDim.x per
 // step.  (A CTA per node would leave most threads idle for the typical heavy
 // node of a few dozen arc groups and take the nodes one after another.)  fn
@@ -286,9 +293,16 @@ struct HeavyStep {
 
 template <class Fn>
 __device__ __forceinline__ void block_walk_heavy(const NetDev& N, const int32_t* list, unsigned hb,
-                                                 unsigned count, const Team& T, Fn fn) {
+                                                 unsigned count, const Team& T, unsigned* grab,
+                                                 Fn fn) {
   __shared__ HeavyStep H;
-  for (unsigned h0 = T.block * 32; h0 < count; h0 += T.nblocks * 32) {
+  __shared__ unsigned h0_sh;
+  for (;;) {
+    // the next 32 entries for this CTA, from the phase counter *grab
+    if (threadIdx.x == 0) h0_sh = count ? atomicAdd(grab, 32u) : count;
+    __syncthreads();
+    const unsigned h0 = h0_sh;
+    if (h0 >= count) break;
     if (threadIdx.x < 32) {
       const unsigned t = threadIdx.x;
       NodeArcs g{0, 0, 0, 0};
@@ -1557,13 +1571,13 @@ __device__ void gr_level(const NetDev& N, EngineCtl* E, const Sched& L, const Te
   const int d1 = L.level + 1;
   const int32_t* bl = N.list[L_BFS];
   const unsigned nlight = L.bfs_end - L.bfs_begin, nheavy = L.bfsh_end - L.bfsh_begin;
-  level_light(N, bl + L.bfs_begin, nlight, T, lane,
+  level_light(N, bl + L.bfs_begin, nlight, T, lane, S.c[C_RELAB],
               [&](const NodeArcs& g, unsigned k, int w, int fb) {
                 int c1 = -1, c2 = -1;
                 if (k != kNoArc) rev_arcs(N, g, k, w, fb, c1, c2, a);
                 gr_emit2(N, L, S, c1, c2, d1, a);
               });
-  block_walk_heavy(N, bl, L.bfsh_begin, nheavy, T,
+  block_walk_heavy(N, bl, L.bfsh_begin, nheavy, T, S.c[C_NEXT],
                    [&](const NodeArcs& g, unsigned k, int w, int fb) {
                      int c1 = -1, c2 = -1;
                      if (k != kNoArc) rev_arcs(N, g, k, w, fb, c1, c2, a);
@@ -1898,13 +1912,13 @@ __device__ void sr_level(const NetDev& N, const Sched& L, const Team& T, const S
                          unsigned lane, Acc& a) {
   const int32_t* bl = N.list[L_BFS];
   const unsigned nlight = L.bfs_end - L.bfs_begin, nheavy = L.bfsh_end - L.bfsh_begin;
-  level_light(N, bl + L.bfs_begin, nlight, T, lane,
+  level_light(N, bl + L.bfs_begin, nlight, T, lane, S.c[C_RELAB],
               [&](const NodeArcs& g, unsigned k, int w, int fb) {
                 int c1 = -1, c2 = -1;
                 if (k != kNoArc) fwd_arcs(N, g, k, w, fb, c1, c2, a);
                 sr_emit2(N, L, S, c1, c2, a);
               });
-  block_walk_heavy(N, bl, L.bfsh_begin, nheavy, T,
+  block_walk_heavy(N, bl, L.bfsh_begin, nheavy, T, S.c[C_NEXT],
                    [&](const NodeArcs& g, unsigned k, int w, int fb) {
                      int c1 = -1, c2 = -1;
                      if (k != kNoArc) fwd_arcs(N, g, k, w, fb, c1, c2, a);

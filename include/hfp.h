@@ -514,6 +514,21 @@ hfp_status hfp_refine_round_batched(hfp_hgraph* hg, int32_t* part, int32_t k,
  * `part` (unchanged) once per candidate group size (CTAs per problem),
  * times the batched FlowCutter launch for each (ms[c], host, may be NULL),
  * and keeps the fastest in hg for hfp_refine_round_batched (*best). */
+/* Autotuner of the batched round's engine knobs (beyond the group size):
+ * with group_ctas CTAs per problem (<= 0: the autotuned or default size) it
+ * builds the round's networks for `part` (unchanged) once per try and times
+ * the batched launch for, in turn, gr_work_x100 in {100, 200, 400},
+ * stall_rounds_pierce in {0 (adaptive), 30, 100}, (tail_enter, tail_exit) in
+ * {(64, 192), (16, 64), (256, 768)} and batch_fused_rounds in {1, 0}, each
+ * knob from the best setting found so far.  ms[cap] (host, may be NULL when
+ * cap is 0) receives the launch times in that order, *n_tried their count;
+ * the fastest setting is kept in hg for its batched rounds and returned in
+ * *chosen (the context's tuning with those knobs; may be NULL).  Single flows
+ * and other hypergraphs keep the context's knobs.  No paper counterpart. */
+hfp_status hfp_autotune_round_engine(hfp_hgraph* hg, const int32_t* part, int32_t k,
+                                     const hfp_refine_params* params, int32_t group_ctas,
+                                     float* ms, int32_t cap, int32_t* n_tried,
+                                     hfp_tuning* chosen);
 hfp_status hfp_autotune_round(hfp_hgraph* hg, const int32_t* part, int32_t k,
                               const hfp_refine_params* params, const int32_t* candidates,
                               int32_t n_candidates, float* ms, int32_t* best);

@@ -31,7 +31,8 @@ hfp_status batch_grid(hfp_ctx* ctx, int* grid) {
   return HFP_OK;
 }
 
-hfp_status run_fc_batch(hfp_ctx* ctx, BatchItem* items, int n, int group_ctas, float* ms_out) {
+hfp_status run_fc_batch(hfp_ctx* ctx, BatchItem* items, int n, int group_ctas, float* ms_out,
+                        const BatchTune* tune) {
   if (n == 0) return HFP_OK;
   cudaStream_t st = ctx->stream;
   int grid = 0;
@@ -85,6 +86,11 @@ hfp_status run_fc_batch(hfp_ctx* ctx, BatchItem* items, int n, int group_ctas, f
   Params P0 = ctx->params;
   P0.fused_rounds = ctx->batch_fused_rounds;
   P0.async_gr = ctx->batch_async_gr;
+  uint32_t gr_work_x100 = ctx->gr_work_x100;
+  if (tune) {
+    P0 = tune->P;
+    gr_work_x100 = tune->gr_work_x100;
+  }
   std::vector<FcJob> jobs(n);
   for (int t = 0; t < n; t++) {
     BatchItem& it = items[order[t]];
@@ -109,7 +115,7 @@ hfp_status run_fc_batch(hfp_ctx* ctx, BatchItem* items, int n, int group_ctas, f
     J.total_w = net->total_w;
     J.max_w = it.params.max_block_weight;
     J.flow_bound = it.params.flow_bound;
-    J.gr_work = (unsigned long long)net->d.NL * ctx->gr_work_x100 / 100 + 1024;
+    J.gr_work = (unsigned long long)net->d.NL * gr_work_x100 / 100 + 1024;
     J.pierce_node = it.pierce_node_dev;
     J.pierce_side = it.pierce_side_dev;
     J.pierce_cap = it.pierce_cap;

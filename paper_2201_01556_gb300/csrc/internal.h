@@ -46,6 +46,12 @@ struct DevBuf {
 
 inline size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
 
+// Engine knobs of a batched launch (the context's, or an autotuner's pick).
+struct BatchTune {
+  Params P;
+  uint32_t gr_work_x100;
+};
+
 }  // namespace hfp
 
 struct hfp_ctx {
@@ -121,6 +127,8 @@ struct hfp_hgraph {
   uint32_t* vnet_off = nullptr;   // vertex -> nets incidence (ascending net ids)
   int32_t* vnet = nullptr;
   int32_t tuned_group = 0;        // CTAs per FlowCutter problem picked by hfp_autotune_round
+  bool tuned_engine = false;      // engine knobs picked by hfp_autotune_round_engine
+  hfp::BatchTune tuned{};
 };
 
 namespace hfp {
@@ -171,6 +179,7 @@ hfp_status batch_grid(hfp_ctx* ctx, int* grid);
 // Runs FlowCutter on every item in one launch; group_ctas <= 0 picks the
 // largest group size that gives every item its own group.  ms_out (may be
 // null) receives the kernel time.
-hfp_status run_fc_batch(hfp_ctx* ctx, BatchItem* items, int n, int group_ctas, float* ms_out);
+hfp_status run_fc_batch(hfp_ctx* ctx, BatchItem* items, int n, int group_ctas, float* ms_out,
+                        const BatchTune* tune = nullptr);
 
 }  // namespace hfp

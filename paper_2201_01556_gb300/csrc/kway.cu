@@ -1125,7 +1125,9 @@ hfp_status refine_pairs(hfp_hgraph* hg, const int32_t* part, int32_t k,
     bi[t].params = pair_fc_params(hg, k, prm, works[t]);
   }
   const int G = group_ctas > 0 ? group_ctas : hg->tuned_group;
-  if ((s = run_fc_batch(hg->ctx, bi.data(), n, G, flow_ms)) != HFP_OK) return s;
+  if ((s = run_fc_batch(hg->ctx, bi.data(), n, G, flow_ms,
+                        hg->tuned_engine ? &hg->tuned : nullptr)) != HFP_OK)
+    return s;
   stats->ms_flow = ms_since(t0);
   t0 = std::chrono::steady_clock::now();
   for (int t = 0; t < n; t++) {
@@ -1327,6 +1329,93 @@ HFP_API hfp_status hfp_autotune_round(hfp_hgraph* hg, const int32_t* part, int32
   }
   hg->tuned_group = best_g;
   if (best) *best = best_g;
+  return HFP_OK;
+}
+
+// Engine knobs of the batched launch tried by hfp_autotune_round_engine, one
+// knob after the other (the best value of a knob is kept for the next):
+// global-relabel work, the stall rule of incremental flows, the CTA-alone
+// round thresholds, the round form.
+namespace {
+struct KnobTry {
+  int knob;        // 0 gr_work_x100, 1 stall_rounds_pierce, 2 tail_enter/exit, 3 fused rounds
+  unsigned a, b;
+};
+const KnobTry kKnobTries[] = {{0, 100, 0}, {0, 200, 0}, {0, 400, 0},
+                              {1, 0, 0},   {1, 30, 0},  {1, 100, 0},
+                              {2, 64, 192}, {2, 16, 64}, {2, 256, 768},
+                              {3, 1, 0},   {3, 0, 0}};
+void apply_knob(BatchTune& t, const KnobTry& k) {
+  switch (k.knob) {
+    case 0: t.gr_work_x100 = k.a; break;
+    case 1: t.P.stall_rounds_pierce = k.a; break;
+    case 2: t.P.tail_enter = k.a; t.P.tail_exit = k.b; break;
+    default: t.P.fused_rounds = k.a; break;
+  }
+}
+}  // namespace
+
+HFP_API hfp_status hfp_autotune_round_engine(hfp_hgraph* hg, const int32_t* part, int32_t k,
+                                             const hfp_refine_params* prm, int32_t group_ctas,
+                                             float* ms, int32_t cap, int32_t* n_tried,
+                                             hfp_tuning* chosen) {
+  if (!hg || !part || !prm || !n_tried || (cap > 0 && !ms)) return fail(HFP_ERR_INVALID, "bad arguments");
+  if (k < 2 || k > 64 || prm->delta < 1) return fail(HFP_ERR_INVALID, "bad k or delta");
+  hfp_status s = hg_set_device(hg);
+  if (s != HFP_OK) return s;
+  hfp_ctx* ctx = hg->ctx;
+  hfp_round_stats st{};
+  std::vector<std::pair<int, int>> pl;
+  if ((s = round_pairs(hg, part, k, nullptr, 0.f, &st, pl)) != HFP_OK) return s;
+  RegionScratch sc;
+  if ((s = sc.alloc(hg)) != HFP_OK) return s;
+  BlockLists bl;
+  if ((s = bl.build(hg, part, k)) != HFP_OK) return s;
+  const int G = group_ctas > 0 ? group_ctas : hg->tuned_group;
+  // start from the context's knobs
+  BatchTune best{ctx->params, ctx->gr_work_x100};
+  best.P.fused_rounds = ctx->batch_fused_rounds;
+  best.P.async_gr = ctx->batch_async_gr;
+  float best_ms = -1.f;
+  int tried = 0;
+  const int nk = (int)(sizeof(kKnobTries) / sizeof(kKnobTries[0]));
+  for (int t = 0; t < nk; t++) {
+    BatchTune cand = best;
+    apply_knob(cand, kKnobTries[t]);
+    // the same networks, rebuilt for every try
+    std::deque<PairWork> works;
+    for (const auto& pr : pl) {
+      works.emplace_back();
+      if ((s = prepare_pair(hg, part, k, pr.first, pr.second, prm, sc, bl, works.back())) !=
+          HFP_OK)
+        return s;
+    }
+    const int n = (int)works.size();
+    std::vector<BatchItem> bi(n);
+    for (int q = 0; q < n; q++) {
+      bi[q].net = works[q].net;
+      bi[q].params = pair_fc_params(hg, k, prm, works[q]);
+    }
+    float t_ms = 0.f;
+    if ((s = run_fc_batch(ctx, bi.data(), n, G, &t_ms, &cand)) != HFP_OK) return s;
+    if (tried < cap) ms[tried] = t_ms;
+    tried++;
+    if (best_ms < 0.f || t_ms < best_ms) {
+      best_ms = t_ms;
+      best = cand;
+    }
+  }
+  hg->tuned = best;
+  hg->tuned_engine = true;
+  *n_tried = tried;
+  if (chosen) {
+    if ((s = hfp_ctx_get_tuning(ctx, chosen)) != HFP_OK) return s;
+    chosen->gr_work_x100 = best.gr_work_x100;
+    chosen->stall_rounds_pierce = best.P.stall_rounds_pierce;
+    chosen->tail_enter = best.P.tail_enter;
+    chosen->tail_exit = best.P.tail_exit;
+    chosen->batch_fused_rounds = best.P.fused_rounds;
+  }
   return HFP_OK;
 }
 

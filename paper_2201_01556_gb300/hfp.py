@@ -170,6 +170,8 @@ def load():
                                            ctypes.c_float, i32, ctypes.POINTER(RoundStats), P,
                                            i32, P, P]),
         "hfp_autotune_round": (i32, [P, P, i32, ctypes.POINTER(RefineParams), P, i32, P, P]),
+        "hfp_autotune_round_engine": (i32, [P, P, i32, ctypes.POINTER(RefineParams), i32, P, i32,
+                                            P, ctypes.POINTER(Tuning)]),
         "hfp_mlp_forward": (i32, [P, P, P, i32, P]),
         "hfp_mlp_grad": (i32, [P, P, P, P, i32, P, P]),
         "hfp_mlp_train": (i32, [P, P, P, P, P, P, P, i32, i32, ctypes.POINTER(AdamParams), P,
@@ -597,6 +599,19 @@ def autotune_round(hg: HGraph, part_dev, k: int, candidates, params: RefineParam
     _check(load().hfp_autotune_round(hg.h, _ptr(part_dev), k, ctypes.byref(params), _ptr(c), len(c),
                                      _ptr(ms), ctypes.byref(best)))
     return int(best.value), ms
+
+
+def autotune_round_engine(hg: HGraph, part_dev, k: int, params: RefineParams | None = None,
+                          group_ctas: int = 0):
+    """hfp_autotune_round_engine -> (chosen tuning dict, launch ms per try)."""
+    params = params or refine_params()
+    ms = np.zeros(32, np.float32)
+    n = ctypes.c_int32()
+    t = Tuning()
+    _check(load().hfp_autotune_round_engine(hg.h, _ptr(part_dev), k, ctypes.byref(params),
+                                            group_ctas, _ptr(ms), len(ms), ctypes.byref(n),
+                                            ctypes.byref(t)))
+    return {f: int(getattr(t, f)) for f, _ in Tuning._fields_}, ms[: n.value]
 
 
 def pair_features(hg: HGraph, part_dev, k: int, eps_pct: int = 3, prev_gain=None):

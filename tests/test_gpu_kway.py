@@ -183,3 +183,22 @@ def test_active_block_rounds_match_oracle(env):
     assert np.array_equal(pd.cpu().numpy(), p2)
     qn0, _ = oracle.quotient(H, part, 64)
     assert r["pairs"] == int((np.triu(qn0, 1) > 0).sum()) + len(pairs2)
+
+
+def test_engine_autotuner_keeps_outcomes(env):
+    """hfp_autotune_round_engine times the batched launch over its knob list
+    (speed only) and keeps the fastest setting for the hypergraph; a batched
+    round afterwards still equals the oracle's round."""
+    torch, hfp, ctx = env
+    H, part, hg, pd = _setup(env, 10, 16000, 24000)
+    chosen, ms = hfp.autotune_round_engine(hg, pd, 64, group_ctas=4)
+    assert len(ms) == 11 and (ms > 0).all()
+    assert chosen["gr_work_x100"] in (100, 200, 400)
+    assert chosen["stall_rounds_pierce"] in (0, 30, 100)
+    assert (chosen["tail_enter"], chosen["tail_exit"]) in ((64, 192), (16, 64), (256, 768))
+    assert chosen["batch_fused_rounds"] in (0, 1)
+    assert np.array_equal(pd.cpu().numpy(), part)
+    newp, total, _, _ = oracle.refine_round(H, part, 64, seed=5)
+    stats, _, _ = hfp.refine_round_batched(hg, pd, 64, hfp.refine_params(seed=5), group_ctas=4)
+    assert stats.gain == total
+    assert np.array_equal(pd.cpu().numpy(), newp)

@@ -214,7 +214,11 @@ uint64_t hfp_kernel_launches(void);
  *                 Here the first algorithm only scans the nets of the two
  *                 blocks (per-round block lists), and it measured faster on
  *                 dense and sparse rings alike (8M: 251 vs 282 ms of pair
- *                 preparation per round; |E| = 0.4 |V|: 176 vs 205 ms) [1] */
+ *                 preparation per round; |E| = 0.4 |V|: 176 vs 205 ms) [1]
+ *   batch_gr_work_x100, batch_stall_rounds_pierce  gr_work_x100 and
+ *                 stall_rounds_pierce of the batched FlowCutter [100, 30]:
+ *                 the engine autotuner picked both on the 1M and 8M k = 64
+ *                 rounds (launch 1028 -> 950 ms and 2730 -> 2653 ms) */
 typedef struct {
   uint32_t gr_work_x100;
   uint32_t stall_rounds;
@@ -237,6 +241,8 @@ typedef struct {
   uint32_t batch_async_gr;
   uint32_t parpr_block;
   uint32_t construction;
+  uint32_t batch_gr_work_x100;
+  uint32_t batch_stall_rounds_pierce;
 } hfp_tuning;
 hfp_status hfp_ctx_get_tuning(hfp_ctx* ctx, hfp_tuning* tuning);
 hfp_status hfp_ctx_set_tuning(hfp_ctx* ctx, const hfp_tuning* tuning);
@@ -520,7 +526,9 @@ hfp_status hfp_refine_round_batched(hfp_hgraph* hg, int32_t* part, int32_t k,
  * the batched launch for, in turn, gr_work_x100 in {100, 200, 400},
  * stall_rounds_pierce in {0 (adaptive), 30, 100}, (tail_enter, tail_exit) in
  * {(64, 192), (16, 64), (256, 768)} and batch_fused_rounds in {1, 0}, each
- * knob from the best setting found so far.  ms[cap] (host, may be NULL when
+ * knob from the best setting found so far (starting from the context's
+ * batched-launch knobs; gr_work_x100 and stall_rounds_pierce stand for their
+ * batch_ forms here and in *chosen).  ms[cap] (host, may be NULL when
  * cap is 0) receives the launch times in that order, *n_tried their count;
  * the fastest setting is kept in hg for its batched rounds and returned in
  * *chosen (the context's tuning with those knobs; may be NULL).  Single flows

@@ -872,6 +872,8 @@ HFP_API hfp_status hfp_ctx_get_tuning(hfp_ctx* ctx, hfp_tuning* t) {
   t->batch_async_gr = ctx->batch_async_gr;
   t->parpr_block = ctx->params.parpr_block;
   t->construction = ctx->construction;
+  t->batch_gr_work_x100 = ctx->batch_gr_work_x100;
+  t->batch_stall_rounds_pierce = ctx->batch_stall_rounds_pierce;
   return HFP_OK;
 }
 
@@ -901,6 +903,9 @@ HFP_API hfp_status hfp_ctx_set_tuning(hfp_ctx* ctx, const hfp_tuning* t) {
   ctx->batch_async_gr = t->batch_async_gr ? 1 : 0;
   ctx->params.parpr_block = t->parpr_block ? 1 : 0;
   ctx->construction = t->construction <= 2 ? t->construction : 1;
+  if (t->batch_gr_work_x100 == 0) return fail(HFP_ERR_INVALID, "bad tuning values");
+  ctx->batch_gr_work_x100 = t->batch_gr_work_x100;
+  ctx->batch_stall_rounds_pierce = t->batch_stall_rounds_pierce;
   return HFP_OK;
 }
 

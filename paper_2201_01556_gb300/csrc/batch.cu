@@ -86,7 +86,8 @@ hfp_status run_fc_batch(hfp_ctx* ctx, BatchItem* items, int n, int group_ctas, f
   Params P0 = ctx->params;
   P0.fused_rounds = ctx->batch_fused_rounds;
   P0.async_gr = ctx->batch_async_gr;
-  uint32_t gr_work_x100 = ctx->gr_work_x100;
+  P0.stall_rounds_pierce = ctx->batch_stall_rounds_pierce;
+  uint32_t gr_work_x100 = ctx->batch_gr_work_x100;
   if (tune) {
     P0 = tune->P;
     gr_work_x100 = tune->gr_work_x100;

@@ -73,6 +73,8 @@ struct hfp_ctx {
   uint32_t batch_fused_rounds = 1; // hfp_tuning.batch_fused_rounds
   uint32_t batch_async_gr = 0;     // hfp_tuning.batch_async_gr
   uint32_t construction = 1;       // hfp_tuning.construction
+  uint32_t batch_gr_work_x100 = 100;       // hfp_tuning.batch_gr_work_x100
+  uint32_t batch_stall_rounds_pierce = 30; // hfp_tuning.batch_stall_rounds_pierce
   // group time per engine state of the batched launches since the last reset
   uint64_t batch_ns[hfp::kStateSlots] = {};
   uint64_t batch_cnt[hfp::kStateSlots] = {};

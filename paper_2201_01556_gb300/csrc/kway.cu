@@ -1372,10 +1372,11 @@ HFP_API hfp_status hfp_autotune_round_engine(hfp_hgraph* hg, const int32_t* part
   BlockLists bl;
   if ((s = bl.build(hg, part, k)) != HFP_OK) return s;
   const int G = group_ctas > 0 ? group_ctas : hg->tuned_group;
-  // start from the context's knobs
-  BatchTune best{ctx->params, ctx->gr_work_x100};
+  // start from the context's knobs of batched launches
+  BatchTune best{ctx->params, ctx->batch_gr_work_x100};
   best.P.fused_rounds = ctx->batch_fused_rounds;
   best.P.async_gr = ctx->batch_async_gr;
+  best.P.stall_rounds_pierce = ctx->batch_stall_rounds_pierce;
   float best_ms = -1.f;
   int tried = 0;
   const int nk = (int)(sizeof(kKnobTries) / sizeof(kKnobTries[0]));
@@ -1410,8 +1411,8 @@ HFP_API hfp_status hfp_autotune_round_engine(hfp_hgraph* hg, const int32_t* part
   *n_tried = tried;
   if (chosen) {
     if ((s = hfp_ctx_get_tuning(ctx, chosen)) != HFP_OK) return s;
-    chosen->gr_work_x100 = best.gr_work_x100;
-    chosen->stall_rounds_pierce = best.P.stall_rounds_pierce;
+    chosen->batch_gr_work_x100 = best.gr_work_x100;
+    chosen->batch_stall_rounds_pierce = best.P.stall_rounds_pierce;
     chosen->tail_enter = best.P.tail_enter;
     chosen->tail_exit = best.P.tail_exit;
     chosen->batch_fused_rounds = best.P.fused_rounds;

@@ -57,7 +57,8 @@ class Tuning(ctypes.Structure):
                                                "async_gr", "gr_warps", "fused_rounds",
                                                "identical_nets", "batch_fused_rounds",
                                                "batch_async_gr", "parpr_block",
-                                               "construction")]
+                                               "construction", "batch_gr_work_x100",
+                                               "batch_stall_rounds_pierce")]
 
 
 class RefineParams(ctypes.Structure):

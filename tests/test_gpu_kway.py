@@ -193,8 +193,8 @@ def test_engine_autotuner_keeps_outcomes(env):
     H, part, hg, pd = _setup(env, 10, 16000, 24000)
     chosen, ms = hfp.autotune_round_engine(hg, pd, 64, group_ctas=4)
     assert len(ms) == 11 and (ms > 0).all()
-    assert chosen["gr_work_x100"] in (100, 200, 400)
-    assert chosen["stall_rounds_pierce"] in (0, 30, 100)
+    assert chosen["batch_gr_work_x100"] in (100, 200, 400)
+    assert chosen["batch_stall_rounds_pierce"] in (0, 30, 100)
     assert (chosen["tail_enter"], chosen["tail_exit"]) in ((64, 192), (16, 64), (256, 768))
     assert chosen["batch_fused_rounds"] in (0, 1)
     assert np.array_equal(pd.cpu().numpy(), part)

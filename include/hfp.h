@@ -218,7 +218,13 @@ uint64_t hfp_kernel_launches(void);
  *   batch_gr_work_x100, batch_stall_rounds_pierce  gr_work_x100 and
  *                 stall_rounds_pierce of the batched FlowCutter [100, 30]:
  *                 the engine autotuner picked both on the 1M and 8M k = 64
- *                 rounds (launch 1028 -> 950 ms and 2730 -> 2653 ms) */
+ *                 rounds (launch 1028 -> 950 ms and 2730 -> 2653 ms)
+ *   wait_timeout_ms  bound on every device wait of this context's launches
+ *                 (grid, group and cluster barriers, the relabel queue's
+ *                 waits, one-CTA loops), 1..600000 ms; a wait that runs out
+ *                 sets the launch's error word, every CTA leaves, and the
+ *                 call returns HFP_ERR_ITER_LIMIT with the context usable
+ *                 [10000] */
 typedef struct {
   uint32_t gr_work_x100;
   uint32_t stall_rounds;
@@ -243,6 +249,7 @@ typedef struct {
   uint32_t construction;
   uint32_t batch_gr_work_x100;
   uint32_t batch_stall_rounds_pierce;
+  uint32_t wait_timeout_ms;
 } hfp_tuning;
 hfp_status hfp_ctx_get_tuning(hfp_ctx* ctx, hfp_tuning* tuning);
 hfp_status hfp_ctx_set_tuning(hfp_ctx* ctx, const hfp_tuning* tuning);
@@ -419,6 +426,17 @@ hfp_status hfp_flowcutter_batch(hfp_ctx* ctx, hfp_fc_task* tasks, int32_t n, int
 hfp_status hfp_ctx_batch_profile(hfp_ctx* ctx, uint64_t* state_ns, uint64_t* state_cnt,
                                  uint64_t* light_in, uint64_t* heavy_in, int32_t n_states,
                                  int32_t reset);
+
+/* Failure path of the device waits: one launch of 2 CTAs whose barrier
+ * (barrier 0: the engine's grid barrier; 1: a batched group's barrier in
+ * global memory; 2: a cluster barrier in distributed shared memory, the two
+ * CTAs then forming one thread-block cluster) waits for one arrival more than
+ * the launch has CTAs, so only the context's wait_timeout_ms ends it.
+ * Returns HFP_ERR_ITER_LIMIT when the wait ran out as designed, with
+ * *waited_ms (host, may be NULL) the launch's device time; HFP_OK would mean
+ * a barrier completed without all its arrivals.  The context stays usable.
+ * HFP_ERR_INVALID for barrier outside 0..2.  No paper counterpart. */
+hfp_status hfp_ctx_wait_selftest(hfp_ctx* ctx, int32_t barrier, float* waited_ms);
 
 /* --- k-way refinement (Section 4, Algorithm 1; Sections 5 and 6) ---------
  * A device-resident hypergraph (with its vertex -> nets incidence) for

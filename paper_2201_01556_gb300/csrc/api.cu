@@ -874,13 +874,15 @@ HFP_API hfp_status hfp_ctx_get_tuning(hfp_ctx* ctx, hfp_tuning* t) {
   t->construction = ctx->construction;
   t->batch_gr_work_x100 = ctx->batch_gr_work_x100;
   t->batch_stall_rounds_pierce = ctx->batch_stall_rounds_pierce;
+  t->wait_timeout_ms = (uint32_t)(ctx->params.timeout_ns / 1000000ull);
   return HFP_OK;
 }
 
 HFP_API hfp_status hfp_ctx_set_tuning(hfp_ctx* ctx, const hfp_tuning* t) {
   if (!ctx || !t) return fail(HFP_ERR_INVALID, "NULL argument");
   if (t->gr_work_x100 == 0 || t->stall_rounds == 0 || t->max_rounds == 0 ||
-      t->tail_exit < t->tail_enter || t->bfs_exit < t->bfs_enter)
+      t->tail_exit < t->tail_enter || t->bfs_exit < t->bfs_enter || t->batch_gr_work_x100 == 0 ||
+      t->wait_timeout_ms == 0 || t->wait_timeout_ms > 600000)
     return fail(HFP_ERR_INVALID, "bad tuning values");
   ctx->gr_work_x100 = t->gr_work_x100;
   ctx->params.stall_rounds = t->stall_rounds;
@@ -903,9 +905,9 @@ HFP_API hfp_status hfp_ctx_set_tuning(hfp_ctx* ctx, const hfp_tuning* t) {
   ctx->batch_async_gr = t->batch_async_gr ? 1 : 0;
   ctx->params.parpr_block = t->parpr_block ? 1 : 0;
   ctx->construction = t->construction <= 2 ? t->construction : 1;
-  if (t->batch_gr_work_x100 == 0) return fail(HFP_ERR_INVALID, "bad tuning values");
   ctx->batch_gr_work_x100 = t->batch_gr_work_x100;
   ctx->batch_stall_rounds_pierce = t->batch_stall_rounds_pierce;
+  ctx->params.timeout_ns = (unsigned long long)t->wait_timeout_ms * 1000000ull;
   return HFP_OK;
 }
 

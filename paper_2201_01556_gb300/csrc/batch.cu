@@ -88,8 +88,10 @@ hfp_status run_fc_batch(hfp_ctx* ctx, BatchItem* items, int n, int group_ctas, f
   P0.async_gr = ctx->batch_async_gr;
   P0.stall_rounds_pierce = ctx->batch_stall_rounds_pierce;
   uint32_t gr_work_x100 = ctx->batch_gr_work_x100;
-  if (tune) {
+  if (tune) {   // the tuned speed knobs; budgets and wait bounds stay the context's
     P0 = tune->P;
+    P0.max_rounds = ctx->params.max_rounds;
+    P0.timeout_ns = ctx->params.timeout_ns;
     gr_work_x100 = tune->gr_work_x100;
   }
   std::vector<FcJob> jobs(n);
@@ -260,5 +262,49 @@ HFP_API hfp_status hfp_ctx_batch_profile(hfp_ctx* ctx, uint64_t* state_ns, uint6
     for (int i = 0; i < kStateSlots; i++)
       ctx->batch_ns[i] = ctx->batch_cnt[i] = ctx->batch_lin[i] = ctx->batch_hin[i] = 0;
   }
+  return HFP_OK;
+}
+
+HFP_API hfp_status hfp_ctx_wait_selftest(hfp_ctx* ctx, int32_t barrier, float* waited_ms) {
+  if (!ctx || barrier < 0 || barrier > 2) return fail(HFP_ERR_INVALID, "bad arguments");
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t st = ctx->stream;
+  DevBuf e, b;
+  CK(e.alloc(sizeof(EngineCtl), st));
+  CK(b.alloc(sizeof(BatchCtl), st));
+  CK(cudaMemsetAsync(e.p, 0, sizeof(EngineCtl), st));
+  CK(cudaMemsetAsync(b.p, 0, sizeof(BatchCtl), st));
+  EngineCtl* E = e.as<EngineCtl>();
+  BatchCtl* B = b.as<BatchCtl>();
+  const unsigned long long tns = ctx->params.timeout_ns;
+  const int ctas = 2, threads = 128;
+  CK(cudaEventRecord(ctx->ev0, st));
+  if (barrier == 2) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    cfg.gridDim = dim3(ctas);
+    cfg.blockDim = dim3(threads);
+    cfg.stream = st;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = ctas;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    CK(cudaLaunchKernelEx(&cfg, wait_selftest_kernel, E, B, (int)barrier, tns));
+  } else {
+    wait_selftest_kernel<<<ctas, threads, 0, st>>>(E, B, barrier, tns);
+    CK(cudaGetLastError());
+  }
+  CK(cudaEventRecord(ctx->ev1, st));
+  count_launches(1);
+  int err = 0;
+  CK(cudaMemcpyAsync(&err, barrier == 0 ? &E->c.err : &B->err, sizeof(int),
+                     cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  float ms = 0.f;
+  CK(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
+  if (waited_ms) *waited_ms = ms;
+  if (err != 0) return fail(HFP_ERR_ITER_LIMIT, "device wait ran out after %.1f ms", ms);
   return HFP_OK;
 }

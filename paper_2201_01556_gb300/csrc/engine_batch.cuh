@@ -945,3 +945,24 @@ __global__ void __launch_bounds__(kEngineThreads, 2) fc_batch_kernel(FcJob* jobs
   // no CTA of a cluster exits while another may still read its shared memory
   if (cluster) cluster_sync_all();
 }
+
+// A bounded wait that nothing completes: the barrier `which` (0: the engine's
+// grid barrier, 1: a batched group's barrier in global memory, 2: a cluster
+// barrier in the first CTA's shared memory; the launch is then one cluster)
+// waits for one arrival more than the launch has CTAs, so only its timeout
+// ends it.  Every CTA leaves with the error word set and nothing in flight.
+__global__ void wait_selftest_kernel(EngineCtl* E, BatchCtl* B, int which,
+                                     unsigned long long timeout_ns) {
+  __shared__ unsigned ctr_sh;
+  const unsigned target = gridDim.x + 1;
+  if (which == 2) {
+    if (threadIdx.x == 0) ctr_sh = 0;
+    cluster_sync_all();
+    cluster_barrier(dsmem_addr(&ctr_sh, 0), target, &B->err, 1, nullptr, timeout_ns);
+    cluster_sync_all();   // no CTA leaves while another may read its shared memory
+  } else if (which == 1) {
+    group_sync(B, 0, target, timeout_ns);
+  } else {
+    grid_barrier(E, target, timeout_ns);
+  }
+}

@@ -104,6 +104,10 @@ __global__ void __launch_bounds__(kEngineThreads, 2) fc_batch_kernel(FcJob* jobs
                                                                   BatchCtl* B, int G, int Gb,
                                                                   int big, int n_groups,
                                                                   Params P0, int cluster);
+// A barrier wait that only its timeout ends (which: 0 grid, 1 group in
+// global memory, 2 cluster); hfp_ctx_wait_selftest launches it.
+__global__ void wait_selftest_kernel(EngineCtl* E, BatchCtl* B, int which,
+                                     unsigned long long timeout_ns);
 // Largest group of fc_batch_kernel launched as one thread-block cluster
 // (non-portable cluster size); larger groups use a cooperative launch.
 constexpr int kMaxClusterCtas = 16;

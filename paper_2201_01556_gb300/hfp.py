@@ -58,7 +58,7 @@ class Tuning(ctypes.Structure):
                                                "identical_nets", "batch_fused_rounds",
                                                "batch_async_gr", "parpr_block",
                                                "construction", "batch_gr_work_x100",
-                                               "batch_stall_rounds_pierce")]
+                                               "batch_stall_rounds_pierce", "wait_timeout_ms")]
 
 
 class RefineParams(ctypes.Structure):
@@ -167,6 +167,7 @@ def load():
         "hfp_pair_features": (i32, [P, P, i32, i32, P, P, P, i32, P]),
         "hfp_flowcutter_batch": (i32, [P, P, i32, i32]),
         "hfp_ctx_batch_profile": (i32, [P, P, P, P, P, i32, i32]),
+        "hfp_ctx_wait_selftest": (i32, [P, i32, ctypes.POINTER(ctypes.c_float)]),
         "hfp_refine_round_batched": (i32, [P, P, i32, ctypes.POINTER(RefineParams), P,
                                            ctypes.c_float, i32, ctypes.POINTER(RoundStats), P,
                                            i32, P, P]),
@@ -390,6 +391,18 @@ def ctx_batch_profile(ctx: Context, reset: bool = True) -> dict:
             name = ENGINE_STATES[i] if i < len(ENGINE_STATES) else f"state{i}"
             out[name] = (int(ns[i]), int(cnt[i]), int(li[i]), int(hi[i]))
     return out
+
+
+def ctx_wait_selftest(ctx: Context, barrier: int) -> tuple[int, float]:
+    """hfp_ctx_wait_selftest -> (status, device ms of the launch): a barrier
+    wait (0 grid, 1 group in global memory, 2 cluster) that only the
+    context's wait_timeout_ms ends; ERR_ITER_LIMIT is the designed outcome.
+    Other errors raise HfpError."""
+    ms = ctypes.c_float()
+    st = load().hfp_ctx_wait_selftest(ctx.h, barrier, ctypes.byref(ms))
+    if st not in (OK, ERR_ITER_LIMIT):
+        _check(st)
+    return st, float(ms.value)
 
 
 def net_enable_trace(net: Net, phases: int):

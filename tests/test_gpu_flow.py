@@ -420,6 +420,35 @@ def test_round_budget_trips_and_context_stays_usable(hfp):
     c.close()
 
 
+@pytest.mark.parametrize("barrier", [0, 1, 2])
+def test_barrier_wait_runs_out_and_context_stays_usable(hfp, barrier):
+    """Each kind of device barrier (0: the engine's grid barrier, 1: a
+    batched group's barrier in global memory, 2: a cluster barrier in
+    distributed shared memory) waits on a count that no CTA completes: the
+    wait ends by the context's timeout with HFP_ERR_ITER_LIMIT, no trap and no
+    hang, and the same context then gives the oracle's flow and cuts."""
+    c = hfp.ctx_create(0)
+    default = hfp.ctx_get_tuning(c)
+    assert default["wait_timeout_ms"] == 10000
+    hfp.ctx_set_tuning(c, wait_timeout_ms=200)
+    assert hfp.ctx_get_tuning(c)["wait_timeout_ms"] == 200
+    st, ms = hfp.ctx_wait_selftest(c, barrier)
+    assert st == hfp.ERR_ITER_LIMIT
+    assert 200.0 <= ms < 5000.0
+    for bad in (0, 600001):
+        with pytest.raises(hfp.HfpError) as e:
+            hfp.ctx_set_tuning(c, wait_timeout_ms=bad)
+        assert e.value.status == hfp.ERR_INVALID
+    assert hfp.ctx_get_tuning(c)["wait_timeout_ms"] == 200   # a refused set changes nothing
+    inst = synth.instance("ring_n4096_geom", 4)
+    H, part, region = inst["H"], inst["part"], inst["region"]
+    onet = oracle.build_network(H, part, region)
+    gnet = _gpu_net(hfp, c, H, part, region)
+    _check_flow(hfp, gnet, onet)
+    gnet.close()
+    c.close()
+
+
 @pytest.fixture(scope="module")
 def ctx_dedup(hfp):
     c = hfp.ctx_create(0)

@@ -224,7 +224,15 @@ uint64_t hfp_kernel_launches(void);
  *                 waits, one-CTA loops), 1..600000 ms; a wait that runs out
  *                 sets the launch's error word, every CTA leaves, and the
  *                 call returns HFP_ERR_ITER_LIMIT with the context usable
- *                 [10000] */
+ *                 [10000]
+ *   prep_streams  k-way rounds prepare their block pairs (region growing,
+ *                 network construction; Section 6) on this many host threads
+ *                 (1..16), each with a stream and region scratch of its own,
+ *                 so that their host round trips overlap; 1: one after
+ *                 another on the context's stream.  The networks are the
+ *                 same.  Preparation of one round, 1 -> 8 threads: 8M
+ *                 vertices 255 -> 99 ms, a 2M-vertex sparse ring 181 -> 49 ms
+ *                 [8] */
 typedef struct {
   uint32_t gr_work_x100;
   uint32_t stall_rounds;
@@ -250,6 +258,7 @@ typedef struct {
   uint32_t batch_gr_work_x100;
   uint32_t batch_stall_rounds_pierce;
   uint32_t wait_timeout_ms;
+  uint32_t prep_streams;
 } hfp_tuning;
 hfp_status hfp_ctx_get_tuning(hfp_ctx* ctx, hfp_tuning* tuning);
 hfp_status hfp_ctx_set_tuning(hfp_ctx* ctx, const hfp_tuning* tuning);

@@ -260,6 +260,7 @@ static void ctx_release(hfp_ctx* c) {
   if (c->refs.fetch_sub(1) != 1) return;
   cudaSetDevice(c->device);
   cudaStreamSynchronize(c->stream);
+  if (c->owns_stream) cudaStreamDestroy(c->stream);
   if (c->pinned_ctl) cudaFreeHost(c->pinned_ctl);
   if (c->pinned_small) cudaFreeHost(c->pinned_small);
   if (c->ev0) cudaEventDestroy(c->ev0);
@@ -270,6 +271,50 @@ static void ctx_release(hfp_ctx* c) {
 HFP_API void hfp_ctx_destroy(hfp_ctx* c) {
   if (c) ctx_release(c);
 }
+
+namespace hfp {
+
+void ctx_copy_tuning(hfp_ctx* dst, const hfp_ctx* src) {
+  dst->params = src->params;
+  dst->gr_work_x100 = src->gr_work_x100;
+  dst->batch_cluster = src->batch_cluster;
+  dst->batch_big_ctas = src->batch_big_ctas;
+  dst->batch_big_groups = src->batch_big_groups;
+  dst->identical_nets = src->identical_nets;
+  dst->batch_fused_rounds = src->batch_fused_rounds;
+  dst->batch_async_gr = src->batch_async_gr;
+  dst->construction = src->construction;
+  dst->batch_gr_work_x100 = src->batch_gr_work_x100;
+  dst->batch_stall_rounds_pierce = src->batch_stall_rounds_pierce;
+  dst->prep_streams = src->prep_streams;
+}
+
+hfp_status ctx_fork(hfp_ctx* parent, hfp_ctx** out) {
+  *out = nullptr;
+  CK(cudaSetDevice(parent->device));
+  cudaStream_t s = nullptr;
+  CK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  hfp_ctx* c = nullptr;
+  const hfp_status r = hfp_ctx_create(&c, parent->device, (void*)s);
+  if (r != HFP_OK) {
+    cudaStreamDestroy(s);
+    return r;
+  }
+  c->owns_stream = true;
+  ctx_copy_tuning(c, parent);
+  *out = c;
+  return HFP_OK;
+}
+
+void net_rehome(hfp_net* net, hfp_ctx* to) {
+  if (!net || net->ctx == to) return;
+  to->refs.fetch_add(1);
+  hfp_ctx* from = net->ctx;
+  net->ctx = to;
+  ctx_release(from);
+}
+
+}  // namespace hfp
 
 HFP_API void hfp_net_destroy(hfp_net* net) {
   if (!net) return;
@@ -875,6 +920,7 @@ HFP_API hfp_status hfp_ctx_get_tuning(hfp_ctx* ctx, hfp_tuning* t) {
   t->batch_gr_work_x100 = ctx->batch_gr_work_x100;
   t->batch_stall_rounds_pierce = ctx->batch_stall_rounds_pierce;
   t->wait_timeout_ms = (uint32_t)(ctx->params.timeout_ns / 1000000ull);
+  t->prep_streams = ctx->prep_streams;
   return HFP_OK;
 }
 
@@ -882,7 +928,8 @@ HFP_API hfp_status hfp_ctx_set_tuning(hfp_ctx* ctx, const hfp_tuning* t) {
   if (!ctx || !t) return fail(HFP_ERR_INVALID, "NULL argument");
   if (t->gr_work_x100 == 0 || t->stall_rounds == 0 || t->max_rounds == 0 ||
       t->tail_exit < t->tail_enter || t->bfs_exit < t->bfs_enter || t->batch_gr_work_x100 == 0 ||
-      t->wait_timeout_ms == 0 || t->wait_timeout_ms > 600000)
+      t->wait_timeout_ms == 0 || t->wait_timeout_ms > 600000 || t->prep_streams == 0 ||
+      t->prep_streams > 16)
     return fail(HFP_ERR_INVALID, "bad tuning values");
   ctx->gr_work_x100 = t->gr_work_x100;
   ctx->params.stall_rounds = t->stall_rounds;
@@ -908,6 +955,7 @@ HFP_API hfp_status hfp_ctx_set_tuning(hfp_ctx* ctx, const hfp_tuning* t) {
   ctx->batch_gr_work_x100 = t->batch_gr_work_x100;
   ctx->batch_stall_rounds_pierce = t->batch_stall_rounds_pierce;
   ctx->params.timeout_ns = (unsigned long long)t->wait_timeout_ms * 1000000ull;
+  ctx->prep_streams = t->prep_streams;
   return HFP_OK;
 }
 

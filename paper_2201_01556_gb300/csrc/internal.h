@@ -6,6 +6,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <string>
+#include <vector>
 
 #include "hfp.h"
 #include "kernels.cuh"
@@ -75,6 +76,8 @@ struct hfp_ctx {
   uint32_t construction = 1;       // hfp_tuning.construction
   uint32_t batch_gr_work_x100 = 100;       // hfp_tuning.batch_gr_work_x100
   uint32_t batch_stall_rounds_pierce = 30; // hfp_tuning.batch_stall_rounds_pierce
+  uint32_t prep_streams = 8;       // hfp_tuning.prep_streams
+  bool owns_stream = false;        // a helper context's stream (destroyed with it)
   // group time per engine state of the batched launches since the last reset
   uint64_t batch_ns[hfp::kStateSlots] = {};
   uint64_t batch_cnt[hfp::kStateSlots] = {};
@@ -131,6 +134,7 @@ struct hfp_hgraph {
   int32_t tuned_group = 0;        // CTAs per FlowCutter problem picked by hfp_autotune_round
   bool tuned_engine = false;      // engine knobs picked by hfp_autotune_round_engine
   hfp::BatchTune tuned{};
+  std::vector<hfp_ctx*> prep;     // helper contexts of the pair preparation threads
 };
 
 namespace hfp {
@@ -171,6 +175,15 @@ hfp_status build_network_impl(hfp_ctx* ctx, const hfp_hypergraph* H, hfp_mem mem
                               const int32_t* dist_from_cut, const int32_t* nets, int32_t n_nets,
                               const int32_t* verts, int32_t n_verts, hfp_net** out,
                               const SortBuildIn* sb = nullptr);
+
+// A helper context of `parent` for another host thread: the same device and
+// tuning, a non-blocking stream of its own that is destroyed with it
+// (hfp_ctx_destroy).  ctx_copy_tuning refreshes its tuning from the parent.
+hfp_status ctx_fork(hfp_ctx* parent, hfp_ctx** out);
+void ctx_copy_tuning(hfp_ctx* dst, const hfp_ctx* src);
+// Moves a network to context `to` (its later work and frees go to `to`'s
+// stream).  Every operation on the network's old stream must have finished.
+void net_rehome(hfp_net* net, hfp_ctx* to);
 
 // Allocates the buffers of one-phase rounds (P.fused_rounds) and queue-driven
 // global relabels (P.async_gr) that the network does not have yet (api.cu).

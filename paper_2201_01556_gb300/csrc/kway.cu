@@ -15,9 +15,12 @@
 // dropping stale moves, skipping a set that would push a growing block past
 // the bound, and reverting a set whose actual gain is negative.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cstring>
 #include <deque>
+#include <string>
+#include <thread>
 #include <vector>
 
 #include "internal.h"
@@ -581,6 +584,7 @@ HFP_API void hfp_hgraph_destroy(hfp_hgraph* hg) {
   if (!hg) return;
   hfp_ctx* c = hg->ctx;
   cudaSetDevice(c->device);
+  for (hfp_ctx* h : hg->prep) hfp_ctx_destroy(h);
   if (hg->arena) cudaFreeAsync(hg->arena, c->stream);
   cudaStreamSynchronize(c->stream);
   delete hg;
@@ -596,8 +600,7 @@ namespace {
 // back (-1, 0, 0) when its network is built.
 struct RegionScratch {
   DevBuf side, lev, flag, pos, cand, wts, scr, tot, inb, taken, cut, rv, nets2, netlist, vlist;
-  hfp_status alloc(hfp_hgraph* hg) {
-    cudaStream_t st = hg->ctx->stream;
+  hfp_status alloc(hfp_hgraph* hg, cudaStream_t st) {
     const size_t n = hg->n > 0 ? hg->n : 1, m = hg->m > 0 ? hg->m : 1;
     const size_t nm = n > m ? n : m;
     CK(side.alloc(sizeof(int32_t) * n, st));
@@ -728,17 +731,17 @@ struct PairWork {
 
 // Compaction of list[i] for flag[i] != 0 into out (list order), optionally
 // with the vertex weights; returns the count (synchronises).
-hfp_status compact_list(hfp_hgraph* hg, unsigned cnt, const int32_t* list, unsigned* flag,
-                        unsigned* pos, int32_t* out, unsigned* wout, unsigned* scr, unsigned* tot,
-                        unsigned* count) {
-  cudaStream_t st = hg->ctx->stream;
+hfp_status compact_list(hfp_ctx* ctx, hfp_hgraph* hg, unsigned cnt, const int32_t* list,
+                        unsigned* flag, unsigned* pos, int32_t* out, unsigned* wout, unsigned* scr,
+                        unsigned* tot, unsigned* count) {
+  cudaStream_t st = ctx->stream;
   if (cnt == 0) {
     *count = 0;
     return HFP_OK;
   }
   CK(cudaMemcpyAsync(pos, flag, sizeof(unsigned) * cnt, cudaMemcpyDeviceToDevice, st));
   scan_exclusive(pos, cnt, scr, tot, st);
-  k_list_scatter<<<nb(cnt, 256, hg->ctx->sms * 8), 256, 0, st>>>(cnt, list, flag, pos, out,
+  k_list_scatter<<<nb(cnt, 256, ctx->sms * 8), 256, 0, st>>>(cnt, list, flag, pos, out,
                                                                  hg->node_w, wout);
   count_launches(1);
   CK(cudaMemcpyAsync(count, tot, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
@@ -746,13 +749,22 @@ hfp_status compact_list(hfp_hgraph* hg, unsigned cnt, const int32_t* list, unsig
   return HFP_OK;
 }
 
+// Whether block-pair networks use the second construction algorithm
+// (Section 6): always (mode 2), never (1), or as the paper decides (0: for
+// sparse hypergraphs, |E| / |V| <= 0.5, or large nets, average size >= 100).
+bool sorted_construction(const hfp_hgraph* hg, uint32_t cmode) {
+  return cmode == 2 ||
+         (cmode == 0 && ((long long)hg->m * 2 <= (long long)hg->n || hg->p >= 100ll * hg->m));
+}
+
 // Region of the pair (Section 6), its flow network and the pair's original
-// cut on the network's nets.  Everything but the flow network's own
-// construction works on the two blocks' vertex and net lists.
-hfp_status prepare_pair(hfp_hgraph* hg, const int32_t* part, int32_t k, int32_t bi, int32_t bj,
-                        const hfp_refine_params* prm, RegionScratch& sc, BlockLists& bl,
-                        PairWork& w) {
-  hfp_ctx* ctx = hg->ctx;
+// cut on the network's nets, on the stream of ctx (the hypergraph's context
+// or a helper context of it; sc belongs to that stream).  Everything but the
+// flow network's own construction works on the two blocks' vertex and net
+// lists.
+hfp_status prepare_pair(hfp_hgraph* hg, hfp_ctx* ctx, const int32_t* part, int32_t k, int32_t bi,
+                        int32_t bj, const hfp_refine_params* prm, RegionScratch& sc,
+                        BlockLists& bl, PairWork& w) {
   cudaStream_t st = ctx->stream;
   const int n = hg->n, m = hg->m, sms = ctx->sms;
   hfp_pair_result* res = &w.r;
@@ -794,8 +806,8 @@ hfp_status prepare_pair(hfp_hgraph* hg, const int32_t* part, int32_t k, int32_t 
       k_list_flag<<<nb(nv[s], 256, sms * 8), 256, 0, st>>>(nv[s], V[s], lev, inb, d,
                                                            sc.flag.as<unsigned>());
       count_launches(1);
-      hfp_status r = compact_list(hg, nv[s], V[s], sc.flag.as<unsigned>(), sc.pos.as<unsigned>(),
-                                  sc.cand.as<int32_t>(), sc.wts.as<unsigned>(),
+      hfp_status r = compact_list(ctx, hg, nv[s], V[s], sc.flag.as<unsigned>(),
+                                  sc.pos.as<unsigned>(), sc.cand.as<int32_t>(), sc.wts.as<unsigned>(),
                                   sc.scr.as<unsigned>(), sc.tot.as<unsigned>(), &h_cnt);
       if (r != HFP_OK) return r;
       if (h_cnt == 0) break;
@@ -827,8 +839,8 @@ hfp_status prepare_pair(hfp_hgraph* hg, const int32_t* part, int32_t k, int32_t 
     k_list_flag<<<nb(nv[s], 256, sms * 8), 256, 0, st>>>(nv[s], V[s], lev, inb, -1,
                                                          sc.flag.as<unsigned>());
     count_launches(1);
-    hfp_status r = compact_list(hg, nv[s], V[s], sc.flag.as<unsigned>(), sc.pos.as<unsigned>(),
-                                rv + rc[0], nullptr, sc.scr.as<unsigned>(), sc.tot.as<unsigned>(),
+    hfp_status r = compact_list(ctx, hg, nv[s], V[s], sc.flag.as<unsigned>(),
+                                sc.pos.as<unsigned>(), rv + rc[0], nullptr, sc.scr.as<unsigned>(), sc.tot.as<unsigned>(),
                                 &rc[s]);
     if (r != HFP_OK) return r;
   }
@@ -846,12 +858,8 @@ hfp_status prepare_pair(hfp_hgraph* hg, const int32_t* part, int32_t k, int32_t 
   w.nr = (int32_t)nr;
   res->region_size = (int32_t)nr;
   // Construction (Section 6): the first algorithm scans the nets of the two
-  // blocks, the second sorts the region's incidences by net; the paper takes
-  // the second for sparse hypergraphs (|E| / |V| <= 0.5) or large nets
-  // (average size >= 100), and so does the automatic choice here
-  const uint32_t cmode = ctx->construction;
-  const bool sorted_build =
-      cmode == 2 || (cmode == 0 && ((long long)m * 2 <= (long long)n || hg->p >= 100ll * m));
+  // blocks, the second sorts the region's incidences by net
+  const bool sorted_build = sorted_construction(hg, ctx->construction);
   SortBuildIn sbi{};
   if (sorted_build) {
     if (hfp_status r0 = bl.build_counts(hg, part)) return r0;
@@ -866,8 +874,8 @@ hfp_status prepare_pair(hfp_hgraph* hg, const int32_t* part, int32_t k, int32_t 
     k_net_not_in<<<nb(nnj, 256, sms * 8), 256, 0, st>>>(nnj, Nj, nmask, bi,
                                                         sc.flag.as<unsigned>());
     count_launches(1);
-    hfp_status r = compact_list(hg, nnj, Nj, sc.flag.as<unsigned>(), sc.pos.as<unsigned>(),
-                                sc.nets2.as<int32_t>(), nullptr, sc.scr.as<unsigned>(),
+    hfp_status r = compact_list(ctx, hg, nnj, Nj, sc.flag.as<unsigned>(),
+                                sc.pos.as<unsigned>(), sc.nets2.as<int32_t>(), nullptr, sc.scr.as<unsigned>(),
                                 sc.tot.as<unsigned>(), &nj2);
     if (r != HFP_OK) return r;
   }
@@ -905,6 +913,83 @@ hfp_status prepare_pair(hfp_hgraph* hg, const int32_t* part, int32_t k, int32_t 
   CK(cudaMemcpyAsync(&hc, sc.cut.p, sizeof(hc), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   res->original_cut = (int64_t)hc;
+  return HFP_OK;
+}
+
+// Prepares the pairs of a batched round into works (one entry per pair, in
+// pair order).  With prep_streams > 1 the pairs go to that many host
+// threads, each with a helper context (stream, pinned staging) and region
+// scratch of its own, which take the next pair from a shared counter, so that
+// the host round trips of different pairs overlap.  A network does not
+// depend on which thread built it.  Once every helper stream has finished,
+// the networks move to the hypergraph's context.
+hfp_status prepare_pairs(hfp_hgraph* hg, const int32_t* part, int32_t k,
+                         const hfp_refine_params* prm,
+                         const std::vector<std::pair<int, int>>& pairs, RegionScratch& sc,
+                         BlockLists& bl, std::deque<PairWork>& works) {
+  hfp_ctx* ctx = hg->ctx;
+  const int n = (int)pairs.size();
+  const int base = (int)works.size();
+  for (int t = 0; t < n; t++) works.emplace_back();
+  const int W = std::min<int>((int)ctx->prep_streams, n);
+  if (W <= 1) {
+    for (int t = 0; t < n; t++) {
+      hfp_status s = prepare_pair(hg, ctx, part, k, pairs[t].first, pairs[t].second, prm, sc, bl,
+                                  works[base + t]);
+      if (s != HFP_OK) return s;
+    }
+    return HFP_OK;
+  }
+  if (sorted_construction(hg, ctx->construction))
+    if (hfp_status s = bl.build_counts(hg, part)) return s;
+  // the block lists and the partition are complete before the helpers start
+  CK(cudaStreamSynchronize(ctx->stream));
+  while ((int)hg->prep.size() < W) {
+    hfp_ctx* c = nullptr;
+    if (hfp_status s = ctx_fork(ctx, &c)) return s;
+    hg->prep.push_back(c);
+  }
+  for (int w = 0; w < W; w++) ctx_copy_tuning(hg->prep[w], ctx);
+  std::atomic<int> next{0}, stop{0};
+  std::vector<hfp_status> status(W, HFP_OK);
+  std::vector<std::string> msg(W);
+  auto body = [&](int w) {
+    hfp_ctx* c = hg->prep[w];
+    hfp_status s = cudaSetDevice(c->device) == cudaSuccess
+                       ? HFP_OK
+                       : fail(HFP_ERR_CUDA, "pair preparation: cudaSetDevice failed");
+    {
+      RegionScratch wsc;
+      if (s == HFP_OK) s = wsc.alloc(hg, c->stream);
+      while (s == HFP_OK && !stop.load()) {
+        const int t = next.fetch_add(1);
+        if (t >= n) break;
+        s = prepare_pair(hg, c, part, k, pairs[t].first, pairs[t].second, prm, wsc, bl,
+                         works[base + t]);
+      }
+    }
+    const cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (s == HFP_OK && e != cudaSuccess)
+      s = fail(HFP_ERR_CUDA, "pair preparation: %s", cudaGetErrorString(e));
+    if (s != HFP_OK) {
+      stop.store(1);
+      status[w] = s;
+      msg[w] = hfp_last_error();
+    }
+  };
+  std::vector<std::thread> th;
+  for (int w = 1; w < W; w++) th.emplace_back(body, w);
+  body(0);
+  for (auto& x : th) x.join();
+  for (int t = 0; t < n; t++) {
+    net_rehome(works[base + t].net, ctx);
+    works[base + t].region.st = ctx->stream;
+  }
+  for (int w = 0; w < W; w++)
+    if (status[w] != HFP_OK) {
+      set_last_error(msg[w].c_str());
+      return status[w];
+    }
   return HFP_OK;
 }
 
@@ -973,7 +1058,7 @@ hfp_status refine_pair(hfp_hgraph* hg, const int32_t* part, int32_t k, int32_t b
                        const hfp_refine_params* prm, RegionScratch& sc, BlockLists& bl,
                        DevBuf& moves_dev, hfp_pair_result* res) {
   PairWork w;
-  hfp_status s = prepare_pair(hg, part, k, bi, bj, prm, sc, bl, w);
+  hfp_status s = prepare_pair(hg, hg->ctx, part, k, bi, bj, prm, sc, bl, w);
   if (s != HFP_OK) return s;
   const hfp_fc_params fp = pair_fc_params(hg, k, prm, w);
   hfp_fc_result fr{};
@@ -994,7 +1079,7 @@ HFP_API hfp_status hfp_refine_block_pair(hfp_hgraph* hg, const int32_t* part, in
   hfp_status s = hg_set_device(hg);
   if (s != HFP_OK) return s;
   RegionScratch sc;
-  if ((s = sc.alloc(hg)) != HFP_OK) return s;
+  if ((s = sc.alloc(hg, hg->ctx->stream)) != HFP_OK) return s;
   BlockLists bl;
   if ((s = bl.build(hg, part, k)) != HFP_OK) return s;
   DevBuf mv;
@@ -1093,7 +1178,7 @@ hfp_status refine_pairs(hfp_hgraph* hg, const int32_t* part, int32_t k,
                         bool batched, int32_t group_ctas, std::deque<Item>& items,
                         float* flow_ms, hfp_round_stats* stats) {
   RegionScratch sc;
-  hfp_status s = sc.alloc(hg);
+  hfp_status s = sc.alloc(hg, hg->ctx->stream);
   if (s != HFP_OK) return s;
   auto t0 = std::chrono::steady_clock::now();
   BlockLists bl;
@@ -1110,11 +1195,7 @@ hfp_status refine_pairs(hfp_hgraph* hg, const int32_t* part, int32_t k,
     return HFP_OK;
   }
   std::deque<PairWork> works;
-  for (const auto& pr : pairs) {
-    works.emplace_back();
-    if ((s = prepare_pair(hg, part, k, pr.first, pr.second, prm, sc, bl, works.back())) != HFP_OK)
-      return s;
-  }
+  if ((s = prepare_pairs(hg, part, k, prm, pairs, sc, bl, works)) != HFP_OK) return s;
   CK(cudaStreamSynchronize(hg->ctx->stream));
   stats->ms_prepare = ms_since(t0);
   t0 = std::chrono::steady_clock::now();
@@ -1299,7 +1380,7 @@ HFP_API hfp_status hfp_autotune_round(hfp_hgraph* hg, const int32_t* part, int32
   std::vector<std::pair<int, int>> pl;
   if ((s = round_pairs(hg, part, k, nullptr, 0.f, &st, pl)) != HFP_OK) return s;
   RegionScratch sc;
-  if ((s = sc.alloc(hg)) != HFP_OK) return s;
+  if ((s = sc.alloc(hg, hg->ctx->stream)) != HFP_OK) return s;
   BlockLists bl;
   if ((s = bl.build(hg, part, k)) != HFP_OK) return s;
   float best_ms = 0.f;
@@ -1307,12 +1388,7 @@ HFP_API hfp_status hfp_autotune_round(hfp_hgraph* hg, const int32_t* part, int32
   for (int c = 0; c < n_candidates; c++) {
     // the same networks, rebuilt for every candidate
     std::deque<PairWork> works;
-    for (const auto& pr : pl) {
-      works.emplace_back();
-      if ((s = prepare_pair(hg, part, k, pr.first, pr.second, prm, sc, bl, works.back())) !=
-          HFP_OK)
-        return s;
-    }
+    if ((s = prepare_pairs(hg, part, k, prm, pl, sc, bl, works)) != HFP_OK) return s;
     const int n = (int)works.size();
     std::vector<BatchItem> bi(n);
     for (int t = 0; t < n; t++) {
@@ -1368,7 +1444,7 @@ HFP_API hfp_status hfp_autotune_round_engine(hfp_hgraph* hg, const int32_t* part
   std::vector<std::pair<int, int>> pl;
   if ((s = round_pairs(hg, part, k, nullptr, 0.f, &st, pl)) != HFP_OK) return s;
   RegionScratch sc;
-  if ((s = sc.alloc(hg)) != HFP_OK) return s;
+  if ((s = sc.alloc(hg, hg->ctx->stream)) != HFP_OK) return s;
   BlockLists bl;
   if ((s = bl.build(hg, part, k)) != HFP_OK) return s;
   const int G = group_ctas > 0 ? group_ctas : hg->tuned_group;
@@ -1385,12 +1461,7 @@ HFP_API hfp_status hfp_autotune_round_engine(hfp_hgraph* hg, const int32_t* part
     apply_knob(cand, kKnobTries[t]);
     // the same networks, rebuilt for every try
     std::deque<PairWork> works;
-    for (const auto& pr : pl) {
-      works.emplace_back();
-      if ((s = prepare_pair(hg, part, k, pr.first, pr.second, prm, sc, bl, works.back())) !=
-          HFP_OK)
-        return s;
-    }
+    if ((s = prepare_pairs(hg, part, k, prm, pl, sc, bl, works)) != HFP_OK) return s;
     const int n = (int)works.size();
     std::vector<BatchItem> bi(n);
     for (int q = 0; q < n; q++) {

@@ -58,7 +58,8 @@ class Tuning(ctypes.Structure):
                                                "identical_nets", "batch_fused_rounds",
                                                "batch_async_gr", "parpr_block",
                                                "construction", "batch_gr_work_x100",
-                                               "batch_stall_rounds_pierce", "wait_timeout_ms")]
+                                               "batch_stall_rounds_pierce", "wait_timeout_ms",
+                                               "prep_streams")]
 
 
 class RefineParams(ctypes.Structure):

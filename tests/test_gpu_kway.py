@@ -202,3 +202,27 @@ def test_engine_autotuner_keeps_outcomes(env):
     stats, _, _ = hfp.refine_round_batched(hg, pd, 64, hfp.refine_params(seed=5), group_ctas=4)
     assert stats.gain == total
     assert np.array_equal(pd.cpu().numpy(), newp)
+
+
+@pytest.mark.parametrize("streams,construction", [(1, 1), (3, 1), (16, 1), (5, 2)])
+def test_prepare_streams_match_oracle(env, streams, construction):
+    """Pair preparation on several host threads (each with a stream and
+    region scratch of its own; pairs that share a block are prepared at the
+    same time) gives the oracle's round: the same final partition and gain,
+    and the same per-pair results, for the one-thread path, thread counts
+    that do not divide the pair count, more threads than a round needs, and
+    the second construction algorithm."""
+    torch, hfp, ctx = env
+    H, part, hg, pd = _setup(env, 11, 24000, 36000, 32)
+    newp, total, res, _ = oracle.refine_round(H, part, 32, seed=5)
+    base = hfp.ctx_get_tuning(ctx)
+    try:
+        hfp.ctx_set_tuning(ctx, prep_streams=streams, construction=construction)
+        stats, pres, _ = hfp.refine_round_batched(hg, pd, 32, hfp.refine_params(seed=5),
+                                                  group_ctas=4)
+    finally:
+        hfp.ctx_set_tuning(ctx, **base)
+    assert stats.gain == total
+    assert np.array_equal(pd.cpu().numpy(), newp)
+    assert [(g.bi, g.bj, g.status, g.region_size, g.delta_exp, g.n_moves) for g in pres] == [
+        (o.bi, o.bj, o.status, o.region_size, o.delta_exp, len(o.moves)) for o in res]

@@ -181,17 +181,23 @@ __device__ __forceinline__ NodeArcs node_arcs(const NetDev& N, int x) {
 
 // The light nodes nodes[0 .. count) (count <= 32) of a breadth-first level
 // by one warp: every lane loads one node, and the warp walks the
-// concatenated arc groups of the 32 nodes, 32 per step, so that a step costs
-// one chain of dependent loads for up to 32 arc groups of different nodes
-// (a team of lanes per node would wait once per node).  fn(g, k, w, fb) is
-// called by every lane of the warp with the arc group k of node arcs g
-// (k == kNoArc: none for this lane in this step); w and fb are the net's
-// weight and bridge flow for net nodes.
+// concatenated arc groups of the 32 nodes, 64 per step, so that a step costs
+// one chain of dependent loads for up to 64 arc groups of different nodes
+// (a team of lanes per node would wait once per node).  fn2(A, B) is called
+// by every lane of the warp with two arc groups, positions q and q + 32 of
+// the walk (k == kNoArc: none), and issues the loads of both before it waits
+// on either; w and fb are the net's weight and bridge flow for net nodes.
 constexpr unsigned kNoArc = 0xffffffffu;
 
-template <class Fn>
+struct WalkArc {
+  NodeArcs g;
+  unsigned k;
+  int w, fb;
+};
+
+template <class Fn2>
 __device__ __forceinline__ void warp_walk_arcs(const NetDev& N, const int32_t* nodes,
-                                               unsigned count, unsigned lane, Fn fn) {
+                                               unsigned count, unsigned lane, Fn2 fn2) {
   NodeArcs g{0, 0, 0, 0};
   int w = 0, fb = 0;
   if (lane < count) {
@@ -209,9 +215,9 @@ __device__ __forceinline__ void warp_walk_arcs(const NetDev& N, const int32_t* n
   }
   const unsigned total = __shfl_sync(FULL, incl, 31);
   const unsigned excl = incl - g.items;
-  for (unsigned q0 = 0; q0 < total; q0 += 32) {
-    const unsigned q = q0 + lane;
-    // owner: the number of lanes whose arcs end at or before q
+  // arc group at walk position q: its owner is the number of lanes whose
+  // arcs end at or before q
+  auto at = [&](unsigned q) {
     int own = 0;
 #pragma unroll
     for (int step = 16; step > 0; step >>= 1) {
@@ -219,19 +225,26 @@ __device__ __forceinline__ void warp_walk_arcs(const NetDev& N, const int32_t* n
       if (v <= q) own += step;
     }
     own = own < 31 ? own : 31;
-    NodeArcs og;
-    og.kind = __shfl_sync(FULL, g.kind, own);
-    og.e = __shfl_sync(FULL, g.e, own);
-    og.beg = __shfl_sync(FULL, g.beg, own);
-    og.items = __shfl_sync(FULL, g.items, own);
-    const int ow = __shfl_sync(FULL, w, own), ofb = __shfl_sync(FULL, fb, own);
+    WalkArc r;
+    r.g.kind = __shfl_sync(FULL, g.kind, own);
+    r.g.e = __shfl_sync(FULL, g.e, own);
+    r.g.beg = __shfl_sync(FULL, g.beg, own);
+    r.g.items = __shfl_sync(FULL, g.items, own);
+    r.w = __shfl_sync(FULL, w, own);
+    r.fb = __shfl_sync(FULL, fb, own);
     const unsigned oex = __shfl_sync(FULL, excl, own);
-    fn(og, q < total ? q - oex : kNoArc, ow, ofb);
+    r.k = q < total ? q - oex : kNoArc;
+    return r;
+  };
+  for (unsigned q0 = 0; q0 < total; q0 += 64) {
+    const WalkArc A = at(q0 + lane);
+    const WalkArc B = at(q0 + 32 + lane);
+    fn2(A, B);
   }
 }
 
 // Node x (x < 0: idle team) by a team of kTeam lanes, kTeam arc groups per
-// step; fn as in warp_walk_arcs.
+// step; fn(g, k, w, fb) gets one arc group (k == kNoArc: none).
 template <class Fn>
 __device__ __forceinline__ void team_walk_arcs(const NetDev& N, int x, unsigned lane, Fn fn) {
   const unsigned tl = lane & (kTeam - 1);
@@ -252,22 +265,23 @@ __device__ __forceinline__ void team_walk_arcs(const NetDev& N, int x, unsigned 
 }
 
 // The light nodes nodes[0 .. count) of a breadth-first level over the warps
-// of T: 32 per warp (warp_walk_arcs) when the level has more than kWalkMin
-// nodes per warp, taken from the phase counter *grab (zero at the phase's
-// start) so that the warps finish together; else one per team, so that a
-// small level still keeps every warp busy.
+// of T: 32 per warp (warp_walk_arcs with fn2) when the level has more than
+// kWalkMin nodes per warp, taken from the phase counter *grab (zero at the
+// phase's start) so that the warps finish together; else one per team (fn),
+// so that a small level still keeps every warp busy.
 constexpr unsigned kWalkMin = 8;
 
-template <class Fn>
+template <class Fn, class Fn2>
 __device__ __forceinline__ void level_light(const NetDev& N, const int32_t* nodes, unsigned count,
-                                            const Team& T, unsigned lane, unsigned* grab, Fn fn) {
+                                            const Team& T, unsigned lane, unsigned* grab, Fn fn,
+                                            Fn2 fn2) {
   if (count > kWalkMin * T.nwarps) {
     for (;;) {
       unsigned base = 0;
       if (lane == 0) base = atomicAdd(grab, 32u);
       base = __shfl_sync(FULL, base, 0);
       if (base >= count) break;
-      warp_walk_arcs(N, nodes + base, min(32u, count - base), lane, fn);
+      warp_walk_arcs(N, nodes + base, min(32u, count - base), lane, fn2);
     }
   } else {
     constexpr unsigned TPW = 32 / kTeam;
@@ -284,7 +298,7 @@ __device__ __forceinline__ void level_light(const NetDev& N, const int32_t* node
 // and the CTA walks the concatenated arc groups of those nodes blockDim.x per
 // step.  (A CTA per node would leave most threads idle for the typical heavy
 // node of a few dozen arc groups and take the nodes one after another.)  fn
-// as in warp_walk_arcs; every thread of the CTA must call this.
+// as in team_walk_arcs; every thread of the CTA must call this.
 struct HeavyStep {
   NodeArcs g[32];
   int w[32], fb[32];
@@ -1524,43 +1538,50 @@ __device__ __forceinline__ void rev_arcs(const NetDev& N, const NodeArcs& g, uns
   }
 }
 
-// The two tails c1, c2 of one arc group (-1: none; distinct when both are
-// given) claimed with label d1: a node still unlabelled (label N_L) that is
-// not a source takes d1 by compare-and-swap, joins the next level, T_r's
-// weight, and the frontier when it has excess.  The loads of both are issued
-// before either claim, and both appends share one ballot pass.
-__device__ __forceinline__ void gr_emit2(const NetDev& N, const Sched& L, const Slot& S, int c1,
-                                         int c2, int d1, Acc& a) {
+// The tails c[0 .. K) of K arc groups (-1: none; a node may appear twice)
+// claimed with label d1: a node still unlabelled (label N_L) that is not a
+// source takes d1 by compare-and-swap (the one winning swap decides), joins
+// the next level, T_r's weight, and the frontier when it has excess.  The
+// loads of all K are issued before any claim, and the appends go in ballot
+// passes of two per lane.
+template <int K>
+__device__ __forceinline__ void gr_emit(const NetDev& N, const Sched& L, const Slot& S,
+                                        const int (&c)[K], int d1, Acc& a) {
   const int NL = N.NL;
-  int l1 = 0, l2 = 0;
-  uint8_t f1 = 0, f2 = 0;
-  if (c1 >= 0) {
-    l1 = N.lab0[c1];
-    f1 = N.flags[c1];
+  int l[K];
+  uint8_t f[K];
+  bool k[K], act[K], h[K];
+#pragma unroll
+  for (int i = 0; i < K; i++) {
+    l[i] = 0;
+    f[i] = 0;
+    if (c[i] >= 0) {
+      l[i] = N.lab0[c[i]];
+      f[i] = N.flags[c[i]];
+    }
   }
-  if (c2 >= 0) {
-    l2 = N.lab0[c2];
-    f2 = N.flags[c2];
+#pragma unroll
+  for (int i = 0; i < K; i++) {
+    k[i] = c[i] >= 0 && l[i] == NL && !(f[i] & kSource);
+    if (k[i]) k[i] = atomicCAS(&N.lab0[c[i]], NL, d1) == NL;
   }
-  bool k1 = c1 >= 0 && l1 == NL && !(f1 & kSource);
-  bool k2 = c2 >= 0 && l2 == NL && !(f2 & kSource);
-  if (k1) k1 = atomicCAS(&N.lab0[c1], NL, d1) == NL;
-  if (k2) k2 = atomicCAS(&N.lab0[c2], NL, d1) == NL;
-  bool a1 = false, a2 = false;
-  if (k1) {
-    N.lab1[c1] = d1;
-    a1 = N.excess[c1] > 0;
-    if (c1 < N.n_nodes) a.w += N.node_w[c1];
+#pragma unroll
+  for (int i = 0; i < K; i++) {
+    act[i] = false;
+    h[i] = (f[i] & kHeavy) != 0;
+    if (k[i]) {
+      N.lab1[c[i]] = d1;
+      act[i] = N.excess[c[i]] > 0;
+      if (c[i] < N.n_nodes) a.w += N.node_w[c[i]];
+    }
   }
-  if (k2) {
-    N.lab1[c2] = d1;
-    a2 = N.excess[c2] > 0;
-    if (c2 < N.n_nodes) a.w += N.node_w[c2];
+#pragma unroll
+  for (int i = 0; i < K; i += 2) {
+    append_split2(k[i], c[i], h[i], k[i + 1], c[i + 1], h[i + 1], N.list[L_BFS], S.c[C_BFS],
+                  S.c[C_BFSH], L.bfs_end, L.bfsh_end, NL);
+    append_split2(act[i], c[i], h[i], act[i + 1], c[i + 1], h[i + 1], N.list[L_FRONT], S.act[0],
+                  S.act[1], 0, 0, NL);
   }
-  const bool h1 = (f1 & kHeavy) != 0, h2 = (f2 & kHeavy) != 0;
-  append_split2(k1, c1, h1, k2, c2, h2, N.list[L_BFS], S.c[C_BFS], S.c[C_BFSH], L.bfs_end,
-                L.bfsh_end, NL);
-  append_split2(a1, c1, h1, a2, c2, h2, N.list[L_FRONT], S.act[0], S.act[1], 0, 0, NL);
 }
 
 // Global relabel, one level: reverse BFS over residual arcs of the capped
@@ -1571,18 +1592,19 @@ __device__ void gr_level(const NetDev& N, EngineCtl* E, const Sched& L, const Te
   const int d1 = L.level + 1;
   const int32_t* bl = N.list[L_BFS];
   const unsigned nlight = L.bfs_end - L.bfs_begin, nheavy = L.bfsh_end - L.bfsh_begin;
-  level_light(N, bl + L.bfs_begin, nlight, T, lane, S.c[C_RELAB],
-              [&](const NodeArcs& g, unsigned k, int w, int fb) {
-                int c1 = -1, c2 = -1;
-                if (k != kNoArc) rev_arcs(N, g, k, w, fb, c1, c2, a);
-                gr_emit2(N, L, S, c1, c2, d1, a);
+  auto one = [&](const NodeArcs& g, unsigned k, int w, int fb) {
+    int c[2] = {-1, -1};
+    if (k != kNoArc) rev_arcs(N, g, k, w, fb, c[0], c[1], a);
+    gr_emit<2>(N, L, S, c, d1, a);
+  };
+  level_light(N, bl + L.bfs_begin, nlight, T, lane, S.c[C_RELAB], one,
+              [&](const WalkArc& A, const WalkArc& B) {
+                int c[4] = {-1, -1, -1, -1};
+                if (A.k != kNoArc) rev_arcs(N, A.g, A.k, A.w, A.fb, c[0], c[1], a);
+                if (B.k != kNoArc) rev_arcs(N, B.g, B.k, B.w, B.fb, c[2], c[3], a);
+                gr_emit<4>(N, L, S, c, d1, a);
               });
-  block_walk_heavy(N, bl, L.bfsh_begin, nheavy, T, S.c[C_NEXT],
-                   [&](const NodeArcs& g, unsigned k, int w, int fb) {
-                     int c1 = -1, c2 = -1;
-                     if (k != kNoArc) rev_arcs(N, g, k, w, fb, c1, c2, a);
-                     gr_emit2(N, L, S, c1, c2, d1, a);
-                   });
+  block_walk_heavy(N, bl, L.bfsh_begin, nheavy, T, S.c[C_NEXT], one);
 }
 
 // ---------------------------------------------------------------------------
@@ -1878,32 +1900,39 @@ __device__ __forceinline__ void fwd_arcs(const NetDev& N, const NodeArcs& g, uns
   }
 }
 
-// sr_emit for the two heads c1, c2 of one arc group (distinct when both are
-// given): the loads of both first, one ballot pass for both appends.
-__device__ __forceinline__ void sr_emit2(const NetDev& N, const Sched& L, const Slot& S, int c1,
-                                         int c2, Acc& a) {
-  uint8_t i1 = 1, i2 = 1, f1 = 0, f2 = 0;
-  if (c1 >= 0) {
-    i1 = N.insr[c1];
-    f1 = N.flags[c1];
+// The heads c[0 .. K) of K arc groups (-1: none; a node may appear twice)
+// that are not yet in S_r join it: the stamp exchange of the search's epoch
+// decides which visit wins.  The loads of all K are issued first, and the
+// appends go in ballot passes of two per lane.
+template <int K>
+__device__ __forceinline__ void sr_emit(const NetDev& N, const Sched& L, const Slot& S,
+                                        const int (&c)[K], Acc& a) {
+  uint8_t in[K], f[K];
+  bool k[K];
+#pragma unroll
+  for (int i = 0; i < K; i++) {
+    in[i] = 1;
+    f[i] = 0;
+    if (c[i] >= 0) {
+      in[i] = N.insr[c[i]];
+      f[i] = N.flags[c[i]];
+    }
   }
-  if (c2 >= 0) {
-    i2 = N.insr[c2];
-    f2 = N.flags[c2];
+#pragma unroll
+  for (int i = 0; i < K; i++) {
+    k[i] = !in[i];
+    if (k[i]) k[i] = atomicExch(&N.stamp[c[i]], L.epoch) != L.epoch;
   }
-  bool k1 = !i1, k2 = !i2;
-  if (k1) k1 = atomicExch(&N.stamp[c1], L.epoch) != L.epoch;
-  if (k2) k2 = atomicExch(&N.stamp[c2], L.epoch) != L.epoch;
-  if (k1) {
-    N.insr[c1] = 1;
-    if (c1 < N.n_nodes) a.w += N.node_w[c1];
-  }
-  if (k2) {
-    N.insr[c2] = 1;
-    if (c2 < N.n_nodes) a.w += N.node_w[c2];
-  }
-  append_split2(k1, c1, (f1 & kHeavy) != 0, k2, c2, (f2 & kHeavy) != 0, N.list[L_BFS],
-                S.c[C_BFS], S.c[C_BFSH], L.bfs_end, L.bfsh_end, N.NL);
+#pragma unroll
+  for (int i = 0; i < K; i++)
+    if (k[i]) {
+      N.insr[c[i]] = 1;
+      if (c[i] < N.n_nodes) a.w += N.node_w[c[i]];
+    }
+#pragma unroll
+  for (int i = 0; i < K; i += 2)
+    append_split2(k[i], c[i], (f[i] & kHeavy) != 0, k[i + 1], c[i + 1], (f[i + 1] & kHeavy) != 0,
+                  N.list[L_BFS], S.c[C_BFS], S.c[C_BFSH], L.bfs_end, L.bfsh_end, N.NL);
 }
 
 // Source-side cut, one level: forward BFS over residual arcs with (u, e_in)
@@ -1912,18 +1941,19 @@ __device__ void sr_level(const NetDev& N, const Sched& L, const Team& T, const S
                          unsigned lane, Acc& a) {
   const int32_t* bl = N.list[L_BFS];
   const unsigned nlight = L.bfs_end - L.bfs_begin, nheavy = L.bfsh_end - L.bfsh_begin;
-  level_light(N, bl + L.bfs_begin, nlight, T, lane, S.c[C_RELAB],
-              [&](const NodeArcs& g, unsigned k, int w, int fb) {
-                int c1 = -1, c2 = -1;
-                if (k != kNoArc) fwd_arcs(N, g, k, w, fb, c1, c2, a);
-                sr_emit2(N, L, S, c1, c2, a);
+  auto one = [&](const NodeArcs& g, unsigned k, int w, int fb) {
+    int c[2] = {-1, -1};
+    if (k != kNoArc) fwd_arcs(N, g, k, w, fb, c[0], c[1], a);
+    sr_emit<2>(N, L, S, c, a);
+  };
+  level_light(N, bl + L.bfs_begin, nlight, T, lane, S.c[C_RELAB], one,
+              [&](const WalkArc& A, const WalkArc& B) {
+                int c[4] = {-1, -1, -1, -1};
+                if (A.k != kNoArc) fwd_arcs(N, A.g, A.k, A.w, A.fb, c[0], c[1], a);
+                if (B.k != kNoArc) fwd_arcs(N, B.g, B.k, B.w, B.fb, c[2], c[3], a);
+                sr_emit<4>(N, L, S, c, a);
               });
-  block_walk_heavy(N, bl, L.bfsh_begin, nheavy, T, S.c[C_NEXT],
-                   [&](const NodeArcs& g, unsigned k, int w, int fb) {
-                     int c1 = -1, c2 = -1;
-                     if (k != kNoArc) fwd_arcs(N, g, k, w, fb, c1, c2, a);
-                     sr_emit2(N, L, S, c1, c2, a);
-                   });
+  block_walk_heavy(N, bl, L.bfsh_begin, nheavy, T, S.c[C_NEXT], one);
 }
 
 // Distance from the original cut (reading of Section 6 "Region Growing" and

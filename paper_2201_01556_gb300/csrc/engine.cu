@@ -293,27 +293,30 @@ __device__ __forceinline__ void level_light(const NetDev& N, const int32_t* node
 }
 
 // The heavy nodes of a breadth-first level (heavy entries hb .. hb + count
-// of a split list), up to 32 per CTA step (taken from the phase counter
-// *grab, zero at the phase's start): warp 0 loads one node per lane,
-// and the CTA walks the concatenated arc groups of those nodes blockDim.x per
-// step.  (A CTA per node would leave most threads idle for the typical heavy
-// node of a few dozen arc groups and take the nodes one after another.)  fn
-// as in team_walk_arcs; every thread of the CTA must call this.
+// of a split list), taken from the phase counter *grab (zero at the phase's
+// start) count / CTAs at a time (at least 1, at most 32), so that a level's
+// heavy nodes spread over all CTAs: warp 0 loads one node per lane, and the
+// CTA walks the concatenated arc groups of those nodes 2 x blockDim.x per
+// step, two per thread (fn2 as in warp_walk_arcs).  (A CTA per node would
+// leave most threads idle for the typical heavy node of a few dozen arc
+// groups and take the nodes one after another.)  Every thread of the CTA
+// must call this.
 struct HeavyStep {
   NodeArcs g[32];
   int w[32], fb[32];
   unsigned incl[32];
 };
 
-template <class Fn>
+template <class Fn2>
 __device__ __forceinline__ void block_walk_heavy(const NetDev& N, const int32_t* list, unsigned hb,
                                                  unsigned count, const Team& T, unsigned* grab,
-                                                 Fn fn) {
+                                                 Fn2 fn2) {
   __shared__ HeavyStep H;
   __shared__ unsigned h0_sh;
+  const unsigned take = min(32u, max(1u, (count + T.nblocks - 1) / T.nblocks));
   for (;;) {
-    // the next 32 entries for this CTA, from the phase counter *grab
-    if (threadIdx.x == 0) h0_sh = count ? atomicAdd(grab, 32u) : count;
+    // the next entries for this CTA, from the phase counter *grab
+    if (threadIdx.x == 0) h0_sh = count ? atomicAdd(grab, take) : count;
     __syncthreads();
     const unsigned h0 = h0_sh;
     if (h0 >= count) break;
@@ -321,7 +324,7 @@ __device__ __forceinline__ void block_walk_heavy(const NetDev& N, const int32_t*
       const unsigned t = threadIdx.x;
       NodeArcs g{0, 0, 0, 0};
       int w = 0, fb = 0;
-      if (h0 + t < count) {
+      if (t < take && h0 + t < count) {
         g = node_arcs(N, list[N.NL - 1 - (hb + h0 + t)]);
         if (g.kind) {
           w = N.net_w[g.e];
@@ -341,15 +344,23 @@ __device__ __forceinline__ void block_walk_heavy(const NetDev& N, const int32_t*
     }
     __syncthreads();
     const unsigned total = H.incl[31];
-    for (unsigned q0 = 0; q0 < total; q0 += blockDim.x) {
-      const unsigned q = q0 + threadIdx.x;
+    auto at = [&](unsigned q) {
       int own = 0;
 #pragma unroll
       for (int step = 16; step > 0; step >>= 1)
         if (H.incl[own + step - 1] <= q) own += step;
       own = own < 31 ? own : 31;
-      const NodeArcs og = H.g[own];
-      fn(og, q < total ? q - (H.incl[own] - og.items) : kNoArc, H.w[own], H.fb[own]);
+      WalkArc r;
+      r.g = H.g[own];
+      r.k = q < total ? q - (H.incl[own] - r.g.items) : kNoArc;
+      r.w = H.w[own];
+      r.fb = H.fb[own];
+      return r;
+    };
+    for (unsigned q0 = 0; q0 < total; q0 += 2 * blockDim.x) {
+      const WalkArc A = at(q0 + threadIdx.x);
+      const WalkArc B = at(q0 + blockDim.x + threadIdx.x);
+      fn2(A, B);
     }
     __syncthreads();   // H is rewritten by the next step
   }
@@ -1597,14 +1608,14 @@ __device__ void gr_level(const NetDev& N, EngineCtl* E, const Sched& L, const Te
     if (k != kNoArc) rev_arcs(N, g, k, w, fb, c[0], c[1], a);
     gr_emit<2>(N, L, S, c, d1, a);
   };
-  level_light(N, bl + L.bfs_begin, nlight, T, lane, S.c[C_RELAB], one,
-              [&](const WalkArc& A, const WalkArc& B) {
-                int c[4] = {-1, -1, -1, -1};
-                if (A.k != kNoArc) rev_arcs(N, A.g, A.k, A.w, A.fb, c[0], c[1], a);
-                if (B.k != kNoArc) rev_arcs(N, B.g, B.k, B.w, B.fb, c[2], c[3], a);
-                gr_emit<4>(N, L, S, c, d1, a);
-              });
-  block_walk_heavy(N, bl, L.bfsh_begin, nheavy, T, S.c[C_NEXT], one);
+  auto two = [&](const WalkArc& A, const WalkArc& B) {
+    int c[4] = {-1, -1, -1, -1};
+    if (A.k != kNoArc) rev_arcs(N, A.g, A.k, A.w, A.fb, c[0], c[1], a);
+    if (B.k != kNoArc) rev_arcs(N, B.g, B.k, B.w, B.fb, c[2], c[3], a);
+    gr_emit<4>(N, L, S, c, d1, a);
+  };
+  level_light(N, bl + L.bfs_begin, nlight, T, lane, S.c[C_RELAB], one, two);
+  block_walk_heavy(N, bl, L.bfsh_begin, nheavy, T, S.c[C_NEXT], two);
 }
 
 // ---------------------------------------------------------------------------
@@ -1946,14 +1957,14 @@ __device__ void sr_level(const NetDev& N, const Sched& L, const Team& T, const S
     if (k != kNoArc) fwd_arcs(N, g, k, w, fb, c[0], c[1], a);
     sr_emit<2>(N, L, S, c, a);
   };
-  level_light(N, bl + L.bfs_begin, nlight, T, lane, S.c[C_RELAB], one,
-              [&](const WalkArc& A, const WalkArc& B) {
-                int c[4] = {-1, -1, -1, -1};
-                if (A.k != kNoArc) fwd_arcs(N, A.g, A.k, A.w, A.fb, c[0], c[1], a);
-                if (B.k != kNoArc) fwd_arcs(N, B.g, B.k, B.w, B.fb, c[2], c[3], a);
-                sr_emit<4>(N, L, S, c, a);
-              });
-  block_walk_heavy(N, bl, L.bfsh_begin, nheavy, T, S.c[C_NEXT], one);
+  auto two = [&](const WalkArc& A, const WalkArc& B) {
+    int c[4] = {-1, -1, -1, -1};
+    if (A.k != kNoArc) fwd_arcs(N, A.g, A.k, A.w, A.fb, c[0], c[1], a);
+    if (B.k != kNoArc) fwd_arcs(N, B.g, B.k, B.w, B.fb, c[2], c[3], a);
+    sr_emit<4>(N, L, S, c, a);
+  };
+  level_light(N, bl + L.bfs_begin, nlight, T, lane, S.c[C_RELAB], one, two);
+  block_walk_heavy(N, bl, L.bfsh_begin, nheavy, T, S.c[C_NEXT], two);
 }
 
 // Distance from the original cut (reading of Section 6 "Region Growing" and

@@ -191,8 +191,12 @@ uint64_t hfp_kernel_launches(void);
  *   batch_cluster  batched FlowCutter: launch groups of at most 16 CTAs as
  *                 thread-block clusters (group barriers in distributed
  *                 shared memory) when as many such clusters can be resident
- *                 as there would be groups; 0: always one cooperative launch
- *                 with barriers in global memory [1]
+ *                 as there would be groups; 2: also when fewer can, with
+ *                 only that many groups; 0: always one cooperative launch
+ *                 with barriers in global memory.  With two CTAs per SM a
+ *                 full grid of groups does not fit as clusters on GB300
+ *                 (a GPC of ~19 SMs holds two 16-CTA clusters), so 1 runs
+ *                 cooperative there [1]
  *   batch_big_ctas, batch_big_groups  batched FlowCutter: the first
  *                 batch_big_groups groups get batch_big_ctas CTAs each (the
  *                 largest problems start on them), the others the launch's
@@ -435,6 +439,13 @@ hfp_status hfp_flowcutter_batch(hfp_ctx* ctx, hfp_fc_task* tasks, int32_t n, int
 hfp_status hfp_ctx_batch_profile(hfp_ctx* ctx, uint64_t* state_ns, uint64_t* state_cnt,
                                  uint64_t* light_in, uint64_t* heavy_in, int32_t n_states,
                                  int32_t reset);
+
+/* Layout of the context's last batched FlowCutter launch: the number of
+ * groups, CTAs per group, and 1 when the groups were thread-block clusters
+ * (0: one cooperative launch).  Host pointers, any may be NULL.  No paper
+ * counterpart. */
+hfp_status hfp_ctx_last_batch_layout(hfp_ctx* ctx, int32_t* groups, int32_t* group_ctas,
+                                     int32_t* cluster);
 
 /* Failure path of the device waits: one launch of 2 CTAs whose barrier
  * (barrier 0: the engine's grid barrier; 1: a batched group's barrier in

@@ -945,7 +945,7 @@ HFP_API hfp_status hfp_ctx_set_tuning(hfp_ctx* ctx, const hfp_tuning* t) {
   ctx->params.gr_warps = t->gr_warps < 1 ? 1 : (t->gr_warps > 16 ? 16 : t->gr_warps);
   ctx->params.fused_rounds = t->fused_rounds ? 1 : 0;
   ctx->identical_nets = t->identical_nets ? 1 : 0;
-  ctx->batch_cluster = t->batch_cluster ? 1 : 0;
+  ctx->batch_cluster = t->batch_cluster <= 2 ? t->batch_cluster : 1;
   ctx->batch_big_ctas = t->batch_big_ctas;
   ctx->batch_big_groups = t->batch_big_groups;
   ctx->batch_fused_rounds = t->batch_fused_rounds ? 1 : 0;

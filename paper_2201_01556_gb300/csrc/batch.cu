@@ -58,7 +58,9 @@ hfp_status run_fc_batch(hfp_ctx* ctx, BatchItem* items, int n, int group_ctas, f
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
   if (cluster) {
-    // clusters only when as many of them can be resident as there are groups
+    // clusters when as many of them can be resident as there are groups; with
+    // batch_cluster = 2 the launch has only as many groups as can be resident
+    // clusters (fewer groups, every barrier in distributed shared memory)
     CK(cudaFuncSetAttribute(fc_batch_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
     cfg.gridDim = dim3(groups * G);
     cfg.blockDim = dim3(kEngineThreads);
@@ -72,8 +74,15 @@ hfp_status run_fc_batch(hfp_ctx* ctx, BatchItem* items, int n, int group_ctas, f
     cfg.numAttrs = 1;
     int resident = 0;
     CK(cudaOccupancyMaxActiveClusters(&resident, fc_batch_kernel, &cfg));
+    if (resident < groups && ctx->batch_cluster == 2 && resident >= 1) {
+      groups = resident;
+      cfg.gridDim = dim3(groups * G);
+    }
     cluster = resident >= groups;
   }
+  ctx->last_groups = groups;
+  ctx->last_group_ctas = G;
+  ctx->last_cluster = cluster ? 1 : 0;
   if (groups > kMaxGroups) return fail(HFP_ERR_INVALID, "too many groups");
   const int launch = big * Gb + (groups - big) * G;
   if (launch > kMaxBatchCtas) return fail(HFP_ERR_INVALID, "grid above %d CTAs", kMaxBatchCtas);
@@ -262,6 +271,15 @@ HFP_API hfp_status hfp_ctx_batch_profile(hfp_ctx* ctx, uint64_t* state_ns, uint6
     for (int i = 0; i < kStateSlots; i++)
       ctx->batch_ns[i] = ctx->batch_cnt[i] = ctx->batch_lin[i] = ctx->batch_hin[i] = 0;
   }
+  return HFP_OK;
+}
+
+HFP_API hfp_status hfp_ctx_last_batch_layout(hfp_ctx* ctx, int32_t* groups, int32_t* group_ctas,
+                                            int32_t* cluster) {
+  if (!ctx) return fail(HFP_ERR_INVALID, "ctx is NULL");
+  if (groups) *groups = ctx->last_groups;
+  if (group_ctas) *group_ctas = ctx->last_group_ctas;
+  if (cluster) *cluster = ctx->last_cluster;
   return HFP_OK;
 }
 

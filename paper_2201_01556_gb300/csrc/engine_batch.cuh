@@ -206,8 +206,8 @@ __device__ void fc_mark_sinks(const NetDev& N, const Team& T, const Slot& S, int
 // group reduces its entries after the barrier; keys of distinct candidates
 // differ in the hash bits, so the maximum has one holder).  A warp takes 32
 // consecutive nets, one per lane, and walks the concatenated pin lists of the
-// reachable ones 32 pins per step, so a step costs one chain of dependent
-// loads for up to 32 nets.  A reachable net whose pins all lie in the
+// reachable ones 64 pins per step (two per lane, loads issued together), so
+// a step costs one chain of dependent loads for up to 64 pins of 32 nets.  A reachable net whose pins all lie in the
 // growing side's reachable set gets its net_done flag: the marking that
 // follows this selection makes all of them terminals, so the net never has
 // a candidate again and later scans skip it.  Every thread of the CTA must
@@ -250,10 +250,9 @@ __device__ void fc_pierce_select(const NetDev& N, const Team& T, BatchCtl* B, co
     const unsigned total = __shfl_sync(FULL, incl, 31);
     const unsigned excl = incl - sz;
     bool outside = false;   // this lane's net has a pin outside the reachable set
-    for (unsigned q0 = 0; q0 < total; q0 += 32) {
-      const unsigned q = q0 + lane;
-      // owner = number of lanes whose inclusive end is <= q
-      int own = 0;
+    // pin q of the walk: its slot (0xffffffff: none)
+    auto slot_of = [&](unsigned q) {
+      int own = 0;   // owner = number of lanes whose inclusive end is <= q
 #pragma unroll
       for (int step = 16; step > 0; step >>= 1) {
         const unsigned v = __shfl_sync(FULL, incl, own + step - 1);
@@ -261,26 +260,39 @@ __device__ void fc_pierce_select(const NetDev& N, const Team& T, BatchCtl* B, co
       }
       own = own < 31 ? own : 31;
       const unsigned ob = __shfl_sync(FULL, beg, own), oe = __shfl_sync(FULL, excl, own);
-      bool out = false;
-      if (q < total) {
-        const int h = N.pin[ob + (q - oe)];
-        out = F.grow_s ? N.insr[h] == 0 : N.lab0[h] >= NL;
-        if (out) {
-          const unsigned long long k = batch_pierce_key(N, h, F.grow_s, J.max_w, w_reach, J.seed);
-          if (k > best) {
-            best = k;
-            bnode = h;
-          }
+      return q < total ? ob + (q - oe) : 0xffffffffu;
+    };
+    // whether this lane's net has pins among lanes [lo, hi) of window q0
+    auto mine = [&](unsigned q0, unsigned ballot) {
+      if (!sz || excl >= q0 + 32 || incl <= q0) return false;
+      const unsigned lo = excl > q0 ? excl - q0 : 0u;
+      const unsigned hi = incl - q0 < 32u ? incl - q0 : 32u;
+      const unsigned mask = (hi == 32u ? FULL : ((1u << hi) - 1u)) & ~((1u << lo) - 1u);
+      return (ballot & mask) != 0;
+    };
+    for (unsigned q0 = 0; q0 < total; q0 += 64) {
+      const unsigned pa = slot_of(q0 + lane), pb = slot_of(q0 + 32 + lane);
+      const int ha = pa != 0xffffffffu ? N.pin[pa] : -1;
+      const int hb = pb != 0xffffffffu ? N.pin[pb] : -1;
+      bool oa = false, ob2 = false;
+      if (ha >= 0) oa = F.grow_s ? N.insr[ha] == 0 : N.lab0[ha] >= NL;
+      if (hb >= 0) ob2 = F.grow_s ? N.insr[hb] == 0 : N.lab0[hb] >= NL;
+      if (oa) {
+        const unsigned long long k = batch_pierce_key(N, ha, F.grow_s, J.max_w, w_reach, J.seed);
+        if (k > best) {
+          best = k;
+          bnode = ha;
         }
       }
-      // this step's lanes [lo, hi) hold pins of this lane's net
-      const unsigned ob_out = __ballot_sync(FULL, out);
-      if (sz && excl < q0 + 32 && incl > q0) {
-        const unsigned lo = excl > q0 ? excl - q0 : 0u;
-        const unsigned hi = incl - q0 < 32u ? incl - q0 : 32u;
-        const unsigned mask = (hi == 32u ? FULL : ((1u << hi) - 1u)) & ~((1u << lo) - 1u);
-        if (ob_out & mask) outside = true;
+      if (ob2) {
+        const unsigned long long k = batch_pierce_key(N, hb, F.grow_s, J.max_w, w_reach, J.seed);
+        if (k > best) {
+          best = k;
+          bnode = hb;
+        }
       }
+      const unsigned ba = __ballot_sync(FULL, oa), bb = __ballot_sync(FULL, ob2);
+      if (mine(q0, ba) || mine(q0 + 32, bb)) outside = true;
     }
     if (sz && !outside && N.net_done) N.net_done[e] = 1;
   };

@@ -77,6 +77,7 @@ struct hfp_ctx {
   uint32_t batch_gr_work_x100 = 100;       // hfp_tuning.batch_gr_work_x100
   uint32_t batch_stall_rounds_pierce = 30; // hfp_tuning.batch_stall_rounds_pierce
   uint32_t prep_streams = 8;       // hfp_tuning.prep_streams
+  int32_t last_groups = 0, last_group_ctas = 0, last_cluster = 0;   // last batched launch
   bool owns_stream = false;        // a helper context's stream (destroyed with it)
   // group time per engine state of the batched launches since the last reset
   uint64_t batch_ns[hfp::kStateSlots] = {};

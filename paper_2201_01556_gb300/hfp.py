@@ -169,6 +169,7 @@ def load():
         "hfp_flowcutter_batch": (i32, [P, P, i32, i32]),
         "hfp_ctx_batch_profile": (i32, [P, P, P, P, P, i32, i32]),
         "hfp_ctx_wait_selftest": (i32, [P, i32, ctypes.POINTER(ctypes.c_float)]),
+        "hfp_ctx_last_batch_layout": (i32, [P, P, P, P]),
         "hfp_refine_round_batched": (i32, [P, P, i32, ctypes.POINTER(RefineParams), P,
                                            ctypes.c_float, i32, ctypes.POINTER(RoundStats), P,
                                            i32, P, P]),
@@ -392,6 +393,15 @@ def ctx_batch_profile(ctx: Context, reset: bool = True) -> dict:
             name = ENGINE_STATES[i] if i < len(ENGINE_STATES) else f"state{i}"
             out[name] = (int(ns[i]), int(cnt[i]), int(li[i]), int(hi[i]))
     return out
+
+
+def ctx_last_batch_layout(ctx: Context) -> dict:
+    """hfp_ctx_last_batch_layout -> {groups, group_ctas, cluster} of the
+    context's last batched FlowCutter launch."""
+    g, c, cl = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _check(load().hfp_ctx_last_batch_layout(ctx.h, ctypes.byref(g), ctypes.byref(c),
+                                            ctypes.byref(cl)))
+    return {"groups": g.value, "group_ctas": c.value, "cluster": cl.value}
 
 
 def ctx_wait_selftest(ctx: Context, barrier: int) -> tuple[int, float]:

@@ -127,11 +127,13 @@ def test_batched_round_equals_plain_round(env, seed, n, k, group):
 
 
 @pytest.mark.parametrize("group,big_ctas,big_groups,cluster", [(4, 16, 3, 1), (2, 32, 2, 1),
-                                                                (4, 0, 0, 0), (8, 0, 0, 1)])
+                                                                (4, 0, 0, 0), (8, 0, 0, 1),
+                                                                (16, 0, 0, 2), (4, 0, 0, 2)])
 def test_batched_round_group_layouts(env, group, big_ctas, big_groups, cluster):
     """Mixed group sizes (big groups for the largest problems), and uniform
     groups as clusters or in one cooperative launch, give the plain round's
-    outcome and report per-pair device times."""
+    outcome and report per-pair device times.  batch_cluster = 2 always
+    launches clusters (as many groups as can be resident), 0 never does."""
     torch, hfp, ctx = env
     H, part, hg = _kway(env, 6, 30000, 16)
     base = hfp.ctx_get_tuning(ctx)
@@ -143,8 +145,14 @@ def test_batched_round_group_layouts(env, group, big_ctas, big_groups, cluster):
                            batch_cluster=cluster)
         s2, r2, ms = hfp.refine_round_batched(hg, p2, 16, hfp.refine_params(seed=2),
                                               group_ctas=group)
+        layout = hfp.ctx_last_batch_layout(ctx)
     finally:
         hfp.ctx_set_tuning(ctx, **base)
+    assert layout["group_ctas"] == group
+    if cluster == 2:
+        assert layout["cluster"] == 1 and layout["groups"] >= 1
+    if cluster == 0 or big_groups:
+        assert layout["cluster"] == 0
     assert np.array_equal(p1.cpu().numpy(), p2.cpu().numpy())
     assert s1.connectivity_after == s2.connectivity_after and s1.pairs == s2.pairs
     for a, b in zip(r1, r2):

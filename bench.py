@@ -218,14 +218,22 @@ def kway_batched(hfp, ctx, args, world):
     pd = torch.from_numpy(part.copy()).cuda()
     conn = [hfp.connectivity(hg, pd, 64)]
     cert = [km1_host(H, part) == conn[0]]
+    G, tune = args.kway_group, None
+    if G <= 0:
+        # CTAs per FlowCutter problem: hfp_autotune_round times the first
+        # round's batched launch per candidate (untimed here; outcomes do not
+        # depend on the group size)
+        cands = (4, 8, 16)
+        G, tms = hfp.autotune_round(hg, pd, 64, cands)
+        tune = {"candidates": list(cands), "launch_ms": [round(float(x), 1) for x in tms]}
     secs, pairs, fc_ms, parts = [], [], [], []
     for _ in range(args.kway_rounds):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         if world > 1:
-            st, _ = sharded.refine_round_sharded(hg, pd, 64, group_ctas=args.kway_group)
+            st, _ = sharded.refine_round_sharded(hg, pd, 64, group_ctas=G)
         else:
-            st, _, ms = hfp.refine_round_batched(hg, pd, 64, group_ctas=args.kway_group)
+            st, _, ms = hfp.refine_round_batched(hg, pd, 64, group_ctas=G)
             fc_ms.append(round(ms, 1))
         torch.cuda.synchronize()
         secs.append(round(time.perf_counter() - t0, 3))
@@ -237,7 +245,8 @@ def kway_batched(hfp, ctx, args, world):
                       for f in ("pairs", "prepare", "flow", "finish", "apply")})
     hg.close()
     out = {"workload": f"ring n={n} m={n * 3 // 2} k=64 (2+Zipf(2.5) <= 10000, 5% moved)",
-           "pins_H": int(H.p), "group_ctas": args.kway_group, "pairs_split_over_ranks": world,
+           "pins_H": int(H.p), "group_ctas": G, "group_autotune": tune,
+           "pairs_split_over_ranks": world,
            "seconds_per_round": secs, "connectivity_minus_1": conn, "pairs_per_round": pairs,
            "round_parts_ms": parts, "certificate": all(cert)}
     if fc_ms:
@@ -352,8 +361,8 @@ def main():
     ap.add_argument("--kway-rounds", type=int, default=2,
                     help="k-way refinement rounds to time (0: none)")
     ap.add_argument("--kway-n", type=int, default=8_000_000)
-    ap.add_argument("--kway-group", type=int, default=16,
-                    help="CTAs per FlowCutter problem (hfp_autotune_round's pick at 8M, k=64)")
+    ap.add_argument("--kway-group", type=int, default=0,
+                    help="CTAs per FlowCutter problem; 0: hfp_autotune_round picks from 4, 8, 16")
     ap.add_argument("--compare-n", type=int, default=200_000,
                     help="ring size of the plain / batched / learned comparison (0: skip)")
     ap.add_argument("--compare-rounds", type=int, default=3)

@@ -198,8 +198,10 @@ def km1_host(H, part):
     64-bit block mask per net, its population count minus one, times w(e)."""
     bits = np.left_shift(np.uint64(1), part[H.pins].astype(np.uint64))
     off = H.net_off.astype(np.int64)
-    masks = np.bitwise_or.reduceat(bits, off[:-1]) if len(off) > 1 else np.zeros(0, np.uint64)
-    masks[off[1:] == off[:-1]] = 0
+    masks = np.zeros(H.m, np.uint64)
+    full = off[1:] > off[:-1]          # empty nets keep mask 0
+    if full.any():
+        masks[full] = np.bitwise_or.reduceat(bits, off[:-1][full])
     lam = np.unpackbits(masks.view(np.uint8).reshape(-1, 8), axis=1).sum(1).astype(np.int64)
     return int((np.maximum(lam - 1, 0) * H.net_w.astype(np.int64)).sum())
 
